@@ -1,0 +1,121 @@
+"""Dense discrete-ordinates stepper (oracle; test infrastructure).
+
+A plain full-tensor implementation of one time step of the paper's scheme,
+written directly from its definitions with no tensor train involved:
+
+* transport (Sec. 3.1): explicit RK1 finite-volume update, Eq. lhs, applied
+  unsplit over the spatial axes, with the upwind interface flux of Eq. upwind
+  (F = c n_a U_L if n_a >= 0 else c n_a U_R, piecewise-constant states);
+* boundaries (Sec. 4.5): ghost cells, periodic = copy of the opposite edge,
+  vacuum = zero ghost (no inflow);
+* source (Sec. 3.2): backward-Euler absorption/emission/scattering, Eq.
+  couple_a / couple_b, with T-dagger from ``quartic.t_dagger``;
+* temperature (Sec. 3.2, energy-conserving update): C_v (T^{m+1} - T^m) equals
+  E* - E^{m+1}, where E* is the radiation energy entering the source stage
+  (the post-transport moment) and E^{m+1} the energy after it.
+
+The intensity array has shape (N_x[, N_y[, N_z]], N_theta, N_phi); spatial
+fields have shape (N_x[, N_y[, N_z]]).
+"""
+import numpy as np
+
+from . import angles
+from .quartic import t_dagger
+
+PERIODIC = 0
+VACUUM = 1
+
+
+class DenseSN:
+    def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
+                 I0, sigma_s=None):
+        self.ndim = len(n)
+        self.n = tuple(n)
+        self.dx = [L[a] / n[a] for a in range(self.ndim)]
+        self.c, self.a_r, self.dt = float(c), float(a_r), float(dt)
+        self.bc = list(bc)  # one entry per axis (same rule on both faces)
+        self.g = angles.grid(n_theta, n_phi)
+        self.nvec = angles.normals(self.g)
+        self.dOmega = angles.solid_angles(self.g)
+        self.sigma_a = np.array(sigma_a, float).reshape(self.n)
+        self.sigma_s = (np.zeros(self.n) if sigma_s is None
+                        else np.array(sigma_s, float).reshape(self.n))
+        self.cv = np.array(cv, float).reshape(self.n)
+        self.T = np.array(T0, float).reshape(self.n).copy()
+        self.I = np.array(I0, float).reshape(self.n + (n_theta, n_phi)).copy()
+
+    # -- Sec. 3 discrete energy density: E_i = (1/c) sum_lp I_ilp dOmega_lp
+    def energy_density(self, I=None):
+        I = self.I if I is None else I
+        return np.einsum("...lp,lp->...", I, self.dOmega) / self.c
+
+    def _ghost_pad(self, I, axis):
+        """Add one ghost cell on each side of ``axis`` (Sec. 4.5)."""
+        pad = [(0, 0)] * I.ndim
+        pad[axis] = (1, 1)
+        P = np.pad(I, pad)  # zeros: vacuum ghosts
+        if self.bc[axis] == PERIODIC:
+            lo = [slice(None)] * I.ndim
+            hi = [slice(None)] * I.ndim
+            lo[axis] = 0
+            hi[axis] = -1
+            src_last = [slice(None)] * I.ndim
+            src_first = [slice(None)] * I.ndim
+            src_last[axis] = -1
+            src_first[axis] = 0
+            P[tuple(lo)] = I[tuple(src_last)]
+            P[tuple(hi)] = I[tuple(src_first)]
+        return P
+
+    def transport(self, I):
+        """One explicit upwind step of Eq. lhs summed over the spatial axes."""
+        out = I.copy()
+        for a in range(self.ndim):
+            na = self.nvec[a]  # (N_theta, N_phi)
+            P = self._ghost_pad(I, a)
+            N = self.n[a]
+            # face k (k = 0..N) sits between padded cells k and k+1, i.e. at i-1/2
+            # for interior cell i = k; U_L = padded[k], U_R = padded[k+1].
+            sl_L = [slice(None)] * I.ndim
+            sl_R = [slice(None)] * I.ndim
+            sl_L[a] = slice(0, N + 1)
+            sl_R[a] = slice(1, N + 2)
+            UL = P[tuple(sl_L)]
+            UR = P[tuple(sl_R)]
+            F = np.where(na >= 0.0, self.c * na * UL, self.c * na * UR)
+            hi = [slice(None)] * I.ndim
+            lo = [slice(None)] * I.ndim
+            hi[a] = slice(1, N + 1)   # F_{i+1/2}
+            lo[a] = slice(0, N)       # F_{i-1/2}
+            out -= (self.dt / self.dx[a]) * (F[tuple(hi)] - F[tuple(lo)])
+        return out
+
+    def source(self, Istar):
+        """Backward-Euler source stage (Eq. couple_a / couple_b); returns
+        (I^{m+1}, T^{m+1}, T_dagger, E_star)."""
+        c, a_r, dt = self.c, self.a_r, self.dt
+        k_a = c * dt * self.sigma_a
+        k_s = c * dt * self.sigma_s
+        E_star = self.energy_density(Istar)
+        J_star = c * E_star / (4.0 * np.pi)
+        Td = t_dagger(self.T, E_star, k_a, self.cv, a_r)
+        B = c * a_r * Td ** 4 / (4.0 * np.pi)
+        J_new = (J_star + k_a * B) / (1.0 + k_a)
+        num = Istar + (k_s * J_new + k_a * B)[..., None, None]
+        I_new = num / (1.0 + k_a + k_s)[..., None, None]
+        E_new = self.energy_density(I_new)
+        T_new = self.T + (E_star - E_new) / self.cv
+        return I_new, T_new, Td, E_star
+
+    def step(self, with_source=True):
+        Istar = self.transport(self.I)
+        if with_source:
+            self.I, self.T, _, _ = self.source(Istar)
+        else:
+            self.I = Istar
+        return self.I
+
+    def total_energy(self):
+        """sum_i (E_i + C_v,i T_i) dV."""
+        dV = float(np.prod(self.dx))
+        return float(np.sum(self.energy_density() + self.cv * self.T) * dV)

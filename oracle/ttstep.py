@@ -1,0 +1,160 @@
+"""Step-then-truncate TT-S_N stepper (oracle; test infrastructure).
+
+Layout: the paper's three cores (Eq. tensor_decomp), I_ilp = X_i Theta_l Phi_p,
+with all spatial axes grouped into the first core (cell index in C order of
+the (N_x[, N_y[, N_z]]) grid, x slowest).  One time step:
+
+1. transport (Sec. 4.3): the upwind update of Eq. lhs / Eq. upwind written as
+   a TT sum I - sum_a nu_a [D^-_a I (.) n_a^+ + D^+_a I (.) n_a^-], nu_a =
+   c dt / dx_a, where D^-_a X_i = X_i - X_{i-1} and D^+_a X_i = X_{i+1} - X_i act
+   on the spatial core with ghost rows (Sec. 4.5: zero rows for vacuum, copied
+   rows for periodic) and the masked direction cosines are rank one:
+   n_x^+- = sin(theta) * max/min(cos(phi), 0), n_y^+- = sin(theta) *
+   max/min(sin(phi), 0), n_z^+- = max/min(cos(theta), 0) * 1.  Terms are summed
+   with the addition of Sec. 4.1 in the order [I, x+, x-, y+, y-, z+, z-];
+2. source (Sec. 3.2 and 4.4): E* by TT integration (Eq. tt_energy_density),
+   T-dagger from the quartic, then I^{m+1} = s (.) I* + e (x) 1 (x) 1 with
+   s = 1/(1 + k_a + k_s) a rank-one Hadamard factor and
+   e = s (k_s J^{m+1} + k_a c a_r T-dagger^4 / 4 pi) a rank-one addition;
+3. rounding (Sec. 4.2, App. A) to tolerance eps -- once per step after the
+   source by default, or after transport and again after the source
+   (``rounds_per_step=2``, the schedule Sec. 4.2 describes);
+4. temperature: C_v (T^{m+1} - T^m) = E* - E^{m+1}, E^{m+1} integrated from the
+   rounded TT, so that sum(E + C_v T) is conserved through the source stage
+   and the rounding.
+"""
+import numpy as np
+
+from . import angles, tt
+from .quartic import t_dagger
+from .rounding import round_gram, round_ttsvd
+
+PERIODIC = 0
+VACUUM = 1
+
+
+class TTSN:
+    def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
+                 cores, sigma_s=None, eps=0.0, max_rank=None,
+                 rounds_per_step=1, rounding="gram"):
+        self.ndim = len(n)
+        self.n = tuple(n)
+        self.nc = int(np.prod(n))
+        self.dx = [L[a] / n[a] for a in range(self.ndim)]
+        self.c, self.a_r, self.dt = float(c), float(a_r), float(dt)
+        self.bc = list(bc)
+        self.g = angles.grid(n_theta, n_phi)
+        self.sigma_a = np.array(sigma_a, float).reshape(-1)
+        self.sigma_s = (np.zeros(self.nc) if sigma_s is None
+                        else np.array(sigma_s, float).reshape(-1))
+        self.cv = np.array(cv, float).reshape(-1)
+        self.T = np.array(T0, float).reshape(-1).copy()
+        self.cores = [np.array(G, float) for G in cores]
+        self.eps, self.max_rank = eps, max_rank
+        self.rounds_per_step = rounds_per_step
+        self.rounding = rounding
+        self.last_sigmas = []
+
+    @staticmethod
+    def isotropic_cores(I_field, n_theta, n_phi):
+        """Rank-one TT of an isotropic intensity field I(x)."""
+        return [np.asarray(I_field, float).reshape(1, -1, 1),
+                np.ones((1, n_theta, 1)), np.ones((1, n_phi, 1))]
+
+    # -- spatial difference operators on the grouped core (Sec. 4.5 ghosts)
+    def _neighbour(self, X, axis, offset):
+        """Row i of the result is X at cell i + offset along ``axis``
+        (periodic wrap, or a zero ghost row for vacuum)."""
+        r = X.shape[-1]
+        Y = X.reshape(self.n + (r,))
+        if self.bc[axis] == PERIODIC:
+            Z = np.roll(Y, -offset, axis=axis)
+        else:
+            Z = np.zeros_like(Y)
+            N = self.n[axis]
+            src = [slice(None)] * Y.ndim
+            dst = [slice(None)] * Y.ndim
+            if offset > 0:
+                src[axis] = slice(offset, N)
+                dst[axis] = slice(0, N - offset)
+            else:
+                src[axis] = slice(0, N + offset)
+                dst[axis] = slice(-offset, N)
+            Z[tuple(dst)] = Y[tuple(src)]
+        return Z.reshape(X.shape)
+
+    def _masks(self, axis):
+        g = self.g
+        if axis == 0:
+            cphi = np.cos(g["phi"])
+            return (g["sin_theta"], np.maximum(cphi, 0.0)), (g["sin_theta"], np.minimum(cphi, 0.0))
+        if axis == 1:
+            sphi = np.sin(g["phi"])
+            return (g["sin_theta"], np.maximum(sphi, 0.0)), (g["sin_theta"], np.minimum(sphi, 0.0))
+        one = np.ones_like(g["phi"])
+        return (np.maximum(g["mu"], 0.0), one), (np.minimum(g["mu"], 0.0), one)
+
+    def transport(self, cores):
+        X, Th, Ph = cores
+        Xm = X[0]
+        terms = [cores]
+        for a in range(self.ndim):
+            nu = self.c * self.dt / self.dx[a]
+            Dm = Xm - self._neighbour(Xm, a, -1)
+            Dp = self._neighbour(Xm, a, +1) - Xm
+            (tp, pp), (tm, pm) = self._masks(a)
+            terms.append([(-nu * Dm)[None], Th * tp[None, :, None], Ph * pp[None, :, None]])
+            terms.append([(-nu * Dp)[None], Th * tm[None, :, None], Ph * pm[None, :, None]])
+        return tt.add_many(terms)
+
+    def energy_density(self, cores=None):
+        cores = self.cores if cores is None else cores
+        return tt.energy_density_grouped(cores, self.g["w"], self.g["v"], self.c)
+
+    def source(self, cores):
+        c, a_r, dt = self.c, self.a_r, self.dt
+        k_a = c * dt * self.sigma_a
+        k_s = c * dt * self.sigma_s
+        E_star = self.energy_density(cores)
+        Td = t_dagger(self.T, E_star, k_a, self.cv, a_r)
+        B = c * a_r * Td ** 4 / (4.0 * np.pi)
+        J_new = (c * E_star / (4.0 * np.pi) + k_a * B) / (1.0 + k_a)
+        s = 1.0 / (1.0 + k_a + k_s)
+        e = s * (k_s * J_new + k_a * B)
+        nt, npf = len(self.g["mu"]), len(self.g["phi"])
+        ones_t, ones_p = np.ones(nt), np.ones(npf)
+        scaled = tt.hadamard(cores, tt.rank_one([s, ones_t, ones_p]))
+        return tt.add(scaled, tt.rank_one([e, ones_t, ones_p])), E_star, Td
+
+    def round(self, cores, forced=None):
+        if self.rounding is None:
+            return cores
+        fn = round_gram if self.rounding == "gram" else round_ttsvd
+        out, sig = fn(cores, self.eps, self.max_rank, forced)
+        self.last_sigmas.append(sig)
+        return out
+
+    def step(self, forced=None, forced2=None, with_source=True):
+        """One time step.  ``forced``: ranks for the (last) rounding of the step;
+        ``forced2``: ranks for the post-transport rounding when rounding twice."""
+        self.last_sigmas = []
+        cur = self.transport(self.cores)
+        if not with_source:
+            self.cores = self.round(cur, forced)
+            return self.cores
+        if self.rounds_per_step == 2:
+            cur = self.round(cur, forced2)
+        cur, E_star, Td = self.source(cur)
+        cur = self.round(cur, forced)
+        E_new = self.energy_density(cur)
+        self.T = self.T + (E_star - E_new) / self.cv
+        self.cores = cur
+        self.last_T_dagger = Td
+        return self.cores
+
+    def full(self):
+        return tt.full(self.cores).reshape(self.n + (self.cores[1].shape[1], self.cores[2].shape[1]))
+
+    def total_energy(self):
+        dV = float(np.prod(self.dx))
+        return float(np.sum(self.energy_density() + self.cv * self.T) * dV)

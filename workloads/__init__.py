@@ -1,0 +1,125 @@
+"""Seeded synthetic inputs for the TT-S_N step (shared by the CUDA path's tests
+and bench and by the oracle's tests).
+
+This module only *generates inputs*: grids, material fields, initial
+temperatures, random tensor-train cores.  It contains none of the method's
+arithmetic (no transport, quadrature, source or rounding).  The initial
+radiation field is described by a radiation temperature ``Tr0``; each side
+builds its own initial intensity from it.
+
+Workloads (unit box [0,1]^ndim, cell-centred, c = a_r = 1, C_v = 1):
+
+* ``small_2d``    2D 32x32 cells, 8x16 ordinates, sigma_a = 1, Gaussian T pulse
+                  (peak 1, width 0.1, background 0.01), periodic, CFL 0.5,
+                  10 steps, eps = 1e-8.
+* ``blob_3d``     3D 128^3 cells, 32x64 ordinates, sigma_a = 1e2 inside a union
+                  of 16 random spheres (seed 0, centres U[0,1]^3, radii
+                  U[0.05, 0.15]) and 1e-2 elsewhere, T = 1 in a sphere of radius
+                  0.1 at the centre and 1e-3 outside, vacuum, CFL 0.5,
+                  100 steps, eps = 1e-6, rank cap 128.
+* ``scaled``      any of the above with other cell / ordinate counts (for tests).
+"""
+import numpy as np
+
+PERIODIC = 0
+VACUUM = 1
+
+
+def cell_centres(n, L):
+    axes = [(np.arange(n[a]) + 0.5) * (L[a] / n[a]) for a in range(len(n))]
+    return np.meshgrid(*axes, indexing="ij")
+
+
+def gaussian_pulse(n, L, peak=1.0, width=0.1, background=0.01, centre=None):
+    X = cell_centres(n, L)
+    if centre is None:
+        centre = [0.5 * L[a] for a in range(len(n))]
+    r2 = sum((X[a] - centre[a]) ** 2 for a in range(len(n)))
+    return background + peak * np.exp(-r2 / (2.0 * width * width))
+
+
+def sphere_mask(n, L, centre, radius):
+    X = cell_centres(n, L)
+    r2 = sum((X[a] - centre[a]) ** 2 for a in range(len(n)))
+    return r2 <= radius * radius
+
+
+def blob_mask(n, L, seed=0, count=16, rmin=0.05, rmax=0.15):
+    rng = np.random.default_rng(seed)
+    ndim = len(n)
+    mask = np.zeros(tuple(n), bool)
+    X = cell_centres(n, L)
+    for _ in range(count):
+        c = rng.uniform(0.0, 1.0, ndim) * np.asarray(L[:ndim])
+        r = rng.uniform(rmin, rmax)
+        r2 = sum((X[a] - c[a]) ** 2 for a in range(ndim))
+        mask |= r2 <= r * r
+    return mask
+
+
+def problem(name="small_2d", n=None, n_theta=None, n_phi=None, **over):
+    """Return a dict describing a problem: grid, ordinates, constants, fields
+    (fp64 numpy arrays of shape ``n`` in C order), bc per axis, eps, rank cap,
+    step count and dt = CFL * min(dx) / c."""
+    if name == "small_2d":
+        p = dict(n=(32, 32), n_theta=8, n_phi=16, bc=PERIODIC, eps=1e-8,
+                 max_rank=128, steps=10, cfl=0.5)
+    elif name == "blob_3d":
+        p = dict(n=(128, 128, 128), n_theta=32, n_phi=64, bc=VACUUM, eps=1e-6,
+                 max_rank=128, steps=100, cfl=0.5)
+    else:
+        raise ValueError(name)
+    if n is not None:
+        p["n"] = tuple(n)
+    if n_theta is not None:
+        p["n_theta"] = n_theta
+    if n_phi is not None:
+        p["n_phi"] = n_phi
+    nn = p["n"]
+    ndim = len(nn)
+    L = (1.0,) * ndim
+    p.update(L=L, c=1.0, a_r=1.0, name=name)
+    if name == "small_2d":
+        T0 = gaussian_pulse(nn, L, 1.0, 0.1, 0.01)
+        sigma_a = np.ones(nn)
+    else:
+        centre = [0.5] * ndim
+        T0 = np.where(sphere_mask(nn, L, centre, 0.1), 1.0, 1e-3)
+        sigma_a = np.where(blob_mask(nn, L, seed=0), 1e2, 1e-2)
+    p.update(T0=T0, Tr0=T0.copy(), sigma_a=sigma_a, sigma_s=np.zeros(nn),
+             cv=np.ones(nn))
+    p.update(over)
+    dx = min(p["L"][a] / p["n"][a] for a in range(ndim))
+    p["dt"] = p["cfl"] * dx / p["c"]
+    if np.isscalar(p["bc"]):
+        p["bc"] = [int(p["bc"])] * ndim
+    return p
+
+
+def random_fields(n, seed, sigma_range=(0.1, 10.0), T_range=(0.2, 1.0)):
+    """Random positive material fields for parity tests."""
+    rng = np.random.default_rng(seed)
+    nn = tuple(n)
+    return dict(
+        sigma_a=np.exp(rng.uniform(np.log(sigma_range[0]), np.log(sigma_range[1]), nn)),
+        sigma_s=np.zeros(nn),
+        cv=rng.uniform(0.5, 2.0, nn),
+        T0=rng.uniform(T_range[0], T_range[1], nn),
+    )
+
+
+def random_tt(n_modes, ranks, seed, scale=1.0):
+    """Random TT cores with N(0,1) entries: core k has shape
+    (ranks[k-1], n_modes[k], ranks[k]) with ranks[-1] = ranks[d] = 1."""
+    rng = np.random.default_rng(seed)
+    d = len(n_modes)
+    r = [1] + list(ranks) + [1]
+    return [scale * rng.standard_normal((r[k], n_modes[k], r[k + 1])) for k in range(d)]
+
+
+def random_positive_tt(n_modes, ranks, seed):
+    """Random TT with positive entries in [0.5, 1.5) (a positive intensity)."""
+    rng = np.random.default_rng(seed)
+    d = len(n_modes)
+    r = [1] + list(ranks) + [1]
+    return [rng.uniform(0.5, 1.5, (r[k], n_modes[k], r[k + 1])) / r[k] for k in range(d)]
