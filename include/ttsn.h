@@ -1,0 +1,237 @@
+/*
+ * ttsn.h -- C ABI of libttsn, a GB300 (sm_103a) implementation of the
+ * tensor-train discrete-ordinates (TT-S_N) step-then-truncate time step for
+ * gray thermal radiation transport of arXiv 2503.18056 ("Thermal radiation
+ * transport with tensor trains").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named *_dev are CUDA device pointers on the current device;
+ *   pointers named *_host are host pointers.  No entry point takes ownership
+ *   of a caller pointer: inputs are copied in, outputs are written into
+ *   caller-allocated buffers.
+ * - Every call is ordered on the CUDA stream given at creation (or passed to
+ *   the kernel-level calls).  Calls that return host data (ranks, totals,
+ *   step info, sweep counts) synchronise that stream before returning.
+ * - Nothing throws across the ABI.  Each call returns a tt_status; on an error
+ *   tt_last_error() returns a thread-local message describing it.  Device-side
+ *   failures (eigensolver sweep limit, a bounded wait that ran out) are latched
+ *   in a device status word and reported by the next call that synchronises.
+ * - Floating-point data are IEEE binary64 ("double").  All arrays are
+ *   row-major (C order).  A TT core k has shape (r_{k-1}, n_k, r_k) with
+ *   r_0 = r_d = 1 and is stored contiguously with r_k fastest.
+ */
+#ifndef TTSN_H
+#define TTSN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_MAX_D 8
+
+typedef struct tt_ctx* tt_handle;
+
+typedef enum {
+    TT_OK = 0,
+    TT_WARN_RANK_CAPPED = 1,   /* a rank cap bound: the eps guarantee is void   */
+    TT_ERR_ARG = -1,           /* invalid argument (message says which)         */
+    TT_ERR_OOM = -2,           /* device allocation failed                      */
+    TT_ERR_CUDA = -3,          /* a CUDA runtime call failed                    */
+    TT_ERR_NOT_CONVERGED = -4, /* Jacobi eigensolver hit its sweep limit        */
+    TT_ERR_TIMEOUT = -5,       /* a bounded device-side wait ran out            */
+    TT_ERR_STATE = -6,         /* call not valid for this handle                */
+    TT_ERR_TOO_LARGE = -7      /* output buffer too small / size over a limit   */
+} tt_status;
+
+enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1 };
+enum { TT_FP64 = 0 };
+
+/* step flags for tt_sn_step_ex */
+enum {
+    TT_STEP_NO_SOURCE = 1, /* transport only (no absorption/emission stage)   */
+    TT_STEP_NO_ROUND = 2   /* keep the rank-grown TT (untruncated step)       */
+};
+
+/*
+ * Problem description for tt_create (Sec. 2-3 of the paper).
+ *
+ * Grid: ndim in {1,2,3} axes with n[a] cells over [0, L[a]], cell-centred;
+ * cells are numbered in C order of the (n[0], n[1], n[2]) array (axis 0
+ * slowest), N_c = prod n[a].  Ordinates: the latitude-longitude grid of Sec. 3,
+ * n_theta cells uniform in mu = cos(theta) on [-1, 1] and n_phi cells uniform
+ * in phi on [0, 2 pi), ordinates at cell centres, dOmega = 4 pi/(n_theta n_phi).
+ * Constants: speed of light c, radiation constant a_r.  Time step: dt if > 0,
+ * otherwise cfl * min(L[a]/n[a]) / c (Sec. 3.1).  bc[a]: TT_BC_PERIODIC or
+ * TT_BC_VACUUM (zero incoming intensity), the same on both faces of axis a
+ * (Sec. 4.5).
+ * Fields (device pointers, N_c doubles each, copied in at creation):
+ *   sigma_a = rho kappa_a, sigma_s = rho kappa_s (NULL = 0), cv = rho c_v,
+ *   T0 = initial material temperature, Tr0 = initial radiation temperature
+ *   (the intensity starts isotropic, I = c a_r Tr0^4 / 4 pi; NULL = T0).
+ * Rounding (Sec. 4.2, App. A): relative Frobenius tolerance eps balanced over
+ * the bonds, ranks capped at max_rank (<= 0: no cap); rounds_per_step = 1
+ * rounds once after the source stage, 2 also rounds after transport.
+ * precision: TT_FP64.
+ * The intensity is held in the paper's three-core layout (Eq. tensor_decomp):
+ * X (1, N_c, r1), Theta (r1, n_theta, r2), Phi (r2, n_phi, 1).
+ */
+typedef struct {
+    int ndim;
+    int n[3];
+    double L[3];
+    int n_theta, n_phi;
+    double c, a_r, cfl, dt;
+    int bc[3];
+    const double* sigma_a;
+    const double* sigma_s;
+    const double* cv;
+    const double* T0;
+    const double* Tr0;
+    double eps;
+    int max_rank;
+    int rounds_per_step;
+    int precision;
+} tt_problem_desc;
+
+/* Diagnostics of the last rounding performed by a call (host struct). */
+typedef struct {
+    int d;                         /* number of cores                          */
+    int ranks[TT_MAX_D + 1];       /* r_0..r_d after the call                  */
+    int grown[TT_MAX_D + 1];       /* ranks entering the last rounding         */
+    double discarded[TT_MAX_D];    /* sqrt(sum of discarded sigma^2) per bond  */
+    double norm;                   /* ||X||_F entering the last rounding       */
+    int capped;                    /* 1 if max_rank bound at some bond         */
+    int sweeps;                    /* most Jacobi sweeps used by one eigensolve */
+} tt_step_info;
+
+/*
+ * tt_create: build a TT-S_N problem (Sec. 3, Sec. 4.1 layout) on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  Returns TT_ERR_ARG on an
+ * invalid description, TT_ERR_OOM if device memory runs out.
+ */
+tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out);
+
+/*
+ * tt_create_tt: a bare TT with d cores of mode sizes n[0..d-1] and ranks
+ * ranks[0..d] (ranks[0] = ranks[d] = 1), all cores zero; used with
+ * tt_set_cores / tt_round / tt_to_full.  Physics calls return TT_ERR_STATE.
+ */
+tt_status tt_create_tt(int d, const int* n, const int* ranks, void* stream, tt_handle* out);
+
+/*
+ * tt_sn_step: advance nsteps time steps (Sec. 3-4): upwind transport applied
+ * as a TT sum of 1 + 2 ndim rank-one-masked terms (Sec. 4.3, Eq. upwind),
+ * backward-Euler absorption/emission with the quartic temperature solve
+ * (Sec. 3.2, Eq. couple_a/couple_b) assembled as a row scaling of the spatial
+ * core plus one rank-one emission term (Sec. 4.4), Gram-SVD rounding to eps
+ * (App. A.2), and the energy-conserving temperature update (Sec. 3.2).
+ * info (nullable) receives the diagnostics of the last step.
+ * Returns TT_WARN_RANK_CAPPED if max_rank bound in any step.
+ */
+tt_status tt_sn_step(tt_handle h, int nsteps, tt_step_info* info);
+
+/*
+ * tt_sn_step_ex: as tt_sn_step with flags (TT_STEP_NO_SOURCE,
+ * TT_STEP_NO_ROUND) and optional forced ranks (host; NULL = use eps) that
+ * replace the tolerance rule: d-1 ints for the one rounding of a step, or
+ * 2(d-1) ints when rounds_per_step = 2 (post-transport rounding first), used
+ * in every step of the call.
+ */
+tt_status tt_sn_step_ex(tt_handle h, int nsteps, int flags, const int* forced_ranks_host,
+                        tt_step_info* info);
+
+/*
+ * tt_round: round the current TT in place with Algorithm 1 and the Gram-SVD
+ * truncation (App. A.2) to relative tolerance eps, rank cap max_rank (<= 0:
+ * none) or forced ranks (d-1 ints, host; NULL = eps rule).
+ */
+tt_status tt_round(tt_handle h, double eps, int max_rank, const int* forced_ranks_host,
+                   tt_step_info* info);
+
+/*
+ * tt_energy: radiation energy density E_i = (1/c) sum_lp I_ilp dOmega_lp by
+ * TT integration (Eq. tt_energy_density) into E_dev (N_c doubles, nullable),
+ * the material temperature into T_dev (nullable), and totals_host[0] =
+ * sum_i E_i dV, totals_host[1] = sum_i cv_i T_i dV (nullable).
+ */
+tt_status tt_energy(tt_handle h, double* E_dev, double* T_dev, double* totals_host);
+
+/*
+ * tt_to_full: expand the TT into out_dev (prod n_k doubles, C order of
+ * (n_1, ..., n_d)); TT_ERR_TOO_LARGE if out_len is smaller.
+ */
+tt_status tt_to_full(tt_handle h, double* out_dev, size_t out_len);
+
+/* tt_get_ranks: copy r_0..r_d into ranks_host (cap entries at most). */
+tt_status tt_get_ranks(tt_handle h, int* ranks_host, int cap);
+
+/* tt_get_dims: d and the mode sizes n_1..n_d (n_host holds TT_MAX_D ints). */
+tt_status tt_get_dims(tt_handle h, int* d_host, int* n_host);
+
+/*
+ * tt_get_core: copy core k (0-based) into out_dev (r_{k-1} n_k r_k doubles);
+ * TT_ERR_TOO_LARGE if out_len is smaller.
+ */
+tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len);
+
+/*
+ * tt_set_cores: replace the TT by the d cores cores_dev[k] (device, shapes
+ * (ranks[k], n_k, ranks[k+1])), copied in; ranks_host has d+1 entries.
+ */
+tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* ranks_host);
+
+/* tt_set_T: replace the material temperature (N_c doubles, device). */
+tt_status tt_set_T(tt_handle h, const double* T_dev);
+
+/* tt_sync: wait for the handle's stream and report any latched device status. */
+tt_status tt_sync(tt_handle h);
+
+/* tt_last_error: thread-local message for the last failing call ("" if none). */
+const char* tt_last_error(void);
+
+/* tt_destroy: free the handle and its device memory (NULL is a no-op). */
+void tt_destroy(tt_handle h);
+
+/* ---------------------------------------------------------------------------
+ * Kernel-level calls (the building blocks of tt_round, exposed for testing and
+ * for callers that hold their own TT data).  All ordered on `stream`.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * tt_dgemm: C = alpha op(A) op(B) + beta C in FP64 on the FP64 tensor pipe
+ * (mma m8n8k4), row-major, op(X) = X if trans_x == 0 else X^T; op(A) is M x K,
+ * op(B) is K x N, C is M x N with leading dimensions lda, ldb, ldc.
+ */
+tt_status tt_dgemm(int trans_a, int trans_b, int M, int N, int K, double alpha,
+                   const double* A_dev, int lda, const double* B_dev, int ldb, double beta,
+                   double* C_dev, int ldc, void* stream);
+
+/*
+ * tt_gram: G = A^T A for a tall row-major A (m x n, leading dimension lda), the
+ * left Gram matrix of App. A.2 (G_A = A^T A).  Split over the m rows with a
+ * fixed-order reduction, so the result is bitwise reproducible; G (n x n,
+ * leading dimension ldg) is exactly symmetric.  Uses device scratch of
+ * (number of row splits) * n * n doubles allocated by the library.
+ */
+tt_status tt_gram(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg, void* stream);
+
+/*
+ * tt_syev: eigendecomposition G = V diag(lam) V^T of a symmetric n x n matrix
+ * (the "small symmetric eigensolves" of App. A.2) by cyclic parallel Jacobi in
+ * FP64.  lam_dev receives the n eigenvalues in descending order; Vt_dev
+ * (n x n, leading dimension ldv) receives the eigenvectors as ROWS (row j is
+ * the eigenvector of lam[j]).  G is not modified.  sweeps_host (nullable)
+ * receives the number of Jacobi sweeps; TT_ERR_NOT_CONVERGED if the sweep
+ * limit was reached (results are then approximate).
+ */
+tt_status tt_syev(int n, const double* G_dev, int ldg, double* lam_dev, double* Vt_dev, int ldv,
+                  void* stream, int* sweeps_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTSN_H */

@@ -54,6 +54,7 @@ class TTSN:
         self.rounds_per_step = rounds_per_step
         self.rounding = rounding
         self.last_sigmas = []
+        self.last_ranks = []
 
     @staticmethod
     def isotropic_cores(I_field, n_theta, n_phi):
@@ -132,12 +133,14 @@ class TTSN:
         fn = round_gram if self.rounding == "gram" else round_ttsvd
         out, sig = fn(cores, self.eps, self.max_rank, forced)
         self.last_sigmas.append(sig)
+        self.last_ranks.append(tt.ranks(out))
         return out
 
     def step(self, forced=None, forced2=None, with_source=True):
         """One time step.  ``forced``: ranks for the (last) rounding of the step;
         ``forced2``: ranks for the post-transport rounding when rounding twice."""
         self.last_sigmas = []
+        self.last_ranks = []
         cur = self.transport(self.cores)
         if not with_source:
             self.cores = self.round(cur, forced)

@@ -1,0 +1,216 @@
+"""GB300 (sm_103a) tensor-train discrete-ordinates thermal radiation transport.
+
+A thin PyTorch-facing wrapper over libttsn (include/ttsn.h).  PyTorch supplies
+device memory and the CUDA stream; the TT-S_N step itself (transport core
+apply, quadrature, quartic temperature solve, source assembly, Gram sweeps,
+Jacobi eigensolves, truncation and core updates) runs in the library's kernels.
+There is no CPU fallback: importing this package without the built library
+raises ImportError.
+"""
+import ctypes
+
+import torch
+
+from . import _native
+from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE,
+                      TTError, StepInfo, check, lib)
+
+__all__ = ["TTSN", "TensorTrain", "dgemm", "gram", "syev", "TTError", "TT_BC_PERIODIC",
+           "TT_BC_VACUUM", "TT_STEP_NO_SOURCE", "TT_STEP_NO_ROUND"]
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x, n=None):
+    t = torch.as_tensor(x, dtype=torch.float64, device="cuda").contiguous()
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d values, got %d" % (n, t.numel()))
+    return t
+
+
+def _int_array(vals):
+    if vals is None:
+        return None
+    arr = (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+class _Handle:
+    def __init__(self):
+        self._h = ctypes.c_void_p()
+        self.stream = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.tt_destroy(h)
+            self._h = None
+
+    # -- common TT access
+    def ranks(self):
+        d, n = self.dims()
+        buf = (ctypes.c_int * (d + 1))()
+        check(lib.tt_get_ranks(self._h, buf, d + 1))
+        return list(buf)
+
+    def dims(self):
+        d = ctypes.c_int()
+        n = (ctypes.c_int * _native.TT_MAX_D)()
+        check(lib.tt_get_dims(self._h, ctypes.byref(d), n))
+        return d.value, list(n[: d.value])
+
+    def cores(self):
+        d, n = self.dims()
+        r = self.ranks()
+        out = []
+        for k in range(d):
+            t = torch.empty((r[k], n[k], r[k + 1]), dtype=torch.float64, device="cuda")
+            check(lib.tt_get_core(self._h, k, ctypes.c_void_p(t.data_ptr()), t.numel()))
+            out.append(t)
+        return out
+
+    def set_cores(self, cores):
+        ts = [_dev(c) for c in cores]
+        ranks = [1] + [int(t.shape[2]) for t in ts[:-1]] + [1]
+        ptrs = (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+        check(lib.tt_set_cores(self._h, ptrs, _int_array(ranks)))
+
+    def full(self):
+        d, n = self.dims()
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        check(lib.tt_to_full(self._h, ctypes.c_void_p(out.data_ptr()), out.numel()))
+        return out
+
+    def round(self, eps=0.0, max_rank=0, forced=None):
+        info = StepInfo()
+        check(lib.tt_round(self._h, float(eps), int(max_rank or 0), _int_array(forced),
+                           ctypes.byref(info)))
+        return info.as_dict()
+
+    def sync(self):
+        check(lib.tt_sync(self._h))
+
+
+class TensorTrain(_Handle):
+    """A bare TT (no physics) for the rounding entry points."""
+
+    def __init__(self, cores, stream=None):
+        super().__init__()
+        ts = [_dev(c) for c in cores]
+        d = len(ts)
+        n = [int(t.shape[1]) for t in ts]
+        ranks = [1] + [int(t.shape[2]) for t in ts[:-1]] + [1]
+        self.stream = stream
+        check(lib.tt_create_tt(d, _int_array(n), _int_array(ranks), _stream_ptr(stream),
+                               ctypes.byref(self._h)))
+        self.set_cores(ts)
+
+
+class TTSN(_Handle):
+    """A TT-S_N problem (paper's three-core layout) on the current CUDA stream.
+
+    Fields are array-likes of N_c values in C order of the grid (axis 0
+    slowest); they are copied to the device and then into the library.
+    """
+
+    def __init__(self, n, L, n_theta, n_phi, sigma_a, cv, T0, Tr0=None, sigma_s=None, c=1.0,
+                 a_r=1.0, dt=0.0, cfl=0.5, bc=TT_BC_PERIODIC, eps=1e-6, max_rank=0,
+                 rounds_per_step=1, stream=None):
+        super().__init__()
+        ndim = len(n)
+        nc = 1
+        for m in n:
+            nc *= int(m)
+        if isinstance(bc, int):
+            bc = [bc] * ndim
+        self.nc = nc
+        self.n = tuple(int(m) for m in n)
+        self.n_theta, self.n_phi = int(n_theta), int(n_phi)
+        self.stream = stream
+        f = {"sigma_a": _dev(sigma_a, nc), "cv": _dev(cv, nc), "T0": _dev(T0, nc)}
+        f["Tr0"] = _dev(Tr0, nc) if Tr0 is not None else None
+        f["sigma_s"] = _dev(sigma_s, nc) if sigma_s is not None else None
+        desc = _native.ProblemDesc()
+        desc.ndim = ndim
+        for a in range(3):
+            desc.n[a] = self.n[a] if a < ndim else 1
+            desc.L[a] = float(L[a]) if a < ndim else 1.0
+            desc.bc[a] = int(bc[a]) if a < ndim else 0
+        desc.n_theta, desc.n_phi = self.n_theta, self.n_phi
+        desc.c, desc.a_r, desc.cfl, desc.dt = float(c), float(a_r), float(cfl), float(dt)
+        for key in ("sigma_a", "cv", "T0", "Tr0", "sigma_s"):
+            setattr(desc, key, f[key].data_ptr() if f[key] is not None else None)
+        desc.eps, desc.max_rank = float(eps), int(max_rank or 0)
+        desc.rounds_per_step, desc.precision = int(rounds_per_step), 0
+        check(lib.tt_create(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(self._h)))
+        self._keep = f  # inputs stay alive until creation finished (copied in)
+
+    @classmethod
+    def from_problem(cls, p, **over):
+        kw = dict(n=p["n"], L=p["L"], n_theta=p["n_theta"], n_phi=p["n_phi"],
+                  sigma_a=p["sigma_a"].reshape(-1), cv=p["cv"].reshape(-1),
+                  T0=p["T0"].reshape(-1), Tr0=p["Tr0"].reshape(-1),
+                  sigma_s=p["sigma_s"].reshape(-1), c=p["c"], a_r=p["a_r"], dt=p["dt"],
+                  bc=list(p["bc"]), eps=p["eps"], max_rank=p.get("max_rank", 0))
+        kw.update(over)
+        return cls(**kw)
+
+    def step(self, nsteps=1, flags=0, forced=None):
+        info = StepInfo()
+        check(lib.tt_sn_step_ex(self._h, int(nsteps), int(flags), _int_array(forced),
+                                ctypes.byref(info)))
+        return info.as_dict()
+
+    def energy(self):
+        E = torch.empty(self.nc, dtype=torch.float64, device="cuda")
+        T = torch.empty(self.nc, dtype=torch.float64, device="cuda")
+        tot = (ctypes.c_double * 2)()
+        check(lib.tt_energy(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(T.data_ptr()), tot))
+        return E, T, (tot[0], tot[1])
+
+    def set_T(self, T):
+        t = _dev(T, self.nc)
+        check(lib.tt_set_T(self._h, ctypes.c_void_p(t.data_ptr())))
+
+    def full(self):
+        return super().full().reshape(self.n + (self.n_theta, self.n_phi))
+
+
+def dgemm(A, B, trans_a=False, trans_b=False, alpha=1.0, stream=None):
+    """C = alpha op(A) op(B) on the FP64 tensor pipe (library kernel)."""
+    A, B = _dev(A), _dev(B)
+    M = A.shape[1] if trans_a else A.shape[0]
+    K = A.shape[0] if trans_a else A.shape[1]
+    N = B.shape[0] if trans_b else B.shape[1]
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    check(lib.tt_dgemm(int(trans_a), int(trans_b), M, N, K, float(alpha),
+                       ctypes.c_void_p(A.data_ptr()), A.shape[1], ctypes.c_void_p(B.data_ptr()),
+                       B.shape[1], 0.0, ctypes.c_void_p(C.data_ptr()), N, _stream_ptr(stream)))
+    return C
+
+
+def gram(A, stream=None):
+    """G = A^T A (library split-K Gram kernel)."""
+    A = _dev(A)
+    m, n = A.shape
+    G = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    check(lib.tt_gram(m, n, ctypes.c_void_p(A.data_ptr()), n, ctypes.c_void_p(G.data_ptr()), n,
+                      _stream_ptr(stream)))
+    return G
+
+
+def syev(G, stream=None, allow_unconverged=False):
+    """(lam descending, Vt with eigenvectors as rows, sweeps) by parallel Jacobi."""
+    G = _dev(G)
+    n = G.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    Vt = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    sweeps = ctypes.c_int()
+    st = lib.tt_syev(n, ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
+                     ctypes.c_void_p(Vt.data_ptr()), n, _stream_ptr(stream), ctypes.byref(sweeps))
+    if not (allow_unconverged and st == -4):
+        check(st)
+    return lam, Vt, sweeps.value

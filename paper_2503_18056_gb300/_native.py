@@ -1,0 +1,103 @@
+"""ctypes declarations for libttsn.so (the C ABI of include/ttsn.h).
+
+Argument marshalling only: every step of the TT-S_N path runs in the library's
+CUDA kernels.  Importing this module fails loudly if the library has not been
+built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libttsn.so")
+
+TT_MAX_D = 8
+TT_OK, TT_WARN_RANK_CAPPED = 0, 1
+STATUS_NAMES = {0: "TT_OK", 1: "TT_WARN_RANK_CAPPED", -1: "TT_ERR_ARG", -2: "TT_ERR_OOM",
+                -3: "TT_ERR_CUDA", -4: "TT_ERR_NOT_CONVERGED", -5: "TT_ERR_TIMEOUT",
+                -6: "TT_ERR_STATE", -7: "TT_ERR_TOO_LARGE"}
+TT_BC_PERIODIC, TT_BC_VACUUM = 0, 1
+TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3),
+        ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
+        ("c", ctypes.c_double), ("a_r", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("dt", ctypes.c_double), ("bc", ctypes.c_int * 3),
+        ("sigma_a", ctypes.c_void_p), ("sigma_s", ctypes.c_void_p), ("cv", ctypes.c_void_p),
+        ("T0", ctypes.c_void_p), ("Tr0", ctypes.c_void_p),
+        ("eps", ctypes.c_double), ("max_rank", ctypes.c_int),
+        ("rounds_per_step", ctypes.c_int), ("precision", ctypes.c_int),
+    ]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("ranks", ctypes.c_int * (TT_MAX_D + 1)),
+        ("grown", ctypes.c_int * (TT_MAX_D + 1)), ("discarded", ctypes.c_double * TT_MAX_D),
+        ("norm", ctypes.c_double), ("capped", ctypes.c_int), ("sweeps", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        d = self.d
+        return {"ranks": list(self.ranks[: d + 1]), "grown": list(self.grown[: d + 1]),
+                "discarded": list(self.discarded[: max(d - 1, 0)]), "norm": self.norm,
+                "capped": bool(self.capped), "sweeps": self.sweeps}
+
+
+class TTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libttsn.so is not built at %s; run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    ip = ctypes.POINTER(ctypes.c_int)
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "tt_create": [ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(vp)],
+        "tt_create_tt": [i, ip, ip, vp, ctypes.POINTER(vp)],
+        "tt_sn_step": [vp, i, ctypes.POINTER(StepInfo)],
+        "tt_sn_step_ex": [vp, i, i, ip, ctypes.POINTER(StepInfo)],
+        "tt_round": [vp, d, i, ip, ctypes.POINTER(StepInfo)],
+        "tt_energy": [vp, vp, vp, dp],
+        "tt_to_full": [vp, vp, sz],
+        "tt_get_ranks": [vp, ip, i],
+        "tt_get_dims": [vp, ip, ip],
+        "tt_get_core": [vp, i, vp, sz],
+        "tt_set_cores": [vp, ctypes.POINTER(vp), ip],
+        "tt_set_T": [vp, vp],
+        "tt_sync": [vp],
+        "tt_dgemm": [i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp],
+        "tt_gram": [i, i, vp, i, vp, i, vp],
+        "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.tt_last_error.argtypes = []
+    lib.tt_last_error.restype = ctypes.c_char_p
+    lib.tt_destroy.argtypes = [vp]
+    lib.tt_destroy.restype = None
+    return lib
+
+
+lib = _load()
+
+#: every symbol the header declares (checked by the CPU test suite)
+EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_round", "tt_energy",
+            "tt_to_full", "tt_get_ranks", "tt_get_dims", "tt_get_core", "tt_set_cores",
+            "tt_set_T", "tt_sync", "tt_last_error", "tt_destroy", "tt_dgemm", "tt_gram",
+            "tt_syev"]
+
+
+def check(status, allow_warn=True):
+    if status == TT_OK or (allow_warn and status == TT_WARN_RANK_CAPPED):
+        return status
+    raise TTError(status, lib.tt_last_error().decode())

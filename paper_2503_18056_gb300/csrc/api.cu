@@ -1,0 +1,798 @@
+// Host runtime and C ABI of libttsn (declared in include/ttsn.h).
+//
+// The step (arXiv 2503.18056, Sec. 3-4) on one CUDA stream:
+//   1. transport_source_rows: grown spatial core X* = [X | -nu D X ... | e]
+//      (Sec. 4.3 TT sum + Sec. 4.4 source), grown angular cores, E*;
+//   2. Gram-SVD rounding (Algorithm 1 with the App. A.2 truncation):
+//      backward sweep of right Grams G_B, their eigendecompositions, then per
+//      bond the left Gram G_A = A^T A, the rank decision and the core update;
+//   3. energy_rows: E^{m+1} from the rounded TT and the energy-conserving
+//      temperature update (Sec. 3.2).
+//
+// Rounding per bond.  App. A.2 forms M = S_A V_A^T V_B S_B from two
+// eigendecompositions and takes the SVD of M.  Here the same quantities come
+// from one eigendecomposition fewer: with W = S_B V_B^T (floored eigenpairs of
+// G_B removed), K = W G_A W^T equals M^T M, so eig(K) = V~ S~^2 V~^T gives the
+// singular values and right singular vectors of M, and
+//   A'    = A P_A,   P_A^T = S~_r^{-1} V~_r^T W,
+//   M_upd = P_A^T G_A = A'^T A,
+// which equal App. A.2's A V_A S_A^{-1} U~ and (V_B S_B^{-1} V~ S~)^T in exact
+// arithmetic.  Neither S_A^{-1} nor S_B^{-1} is formed, so tensor components
+// whose left singular values fall below sqrt(eps_mach) of the largest (where
+// App. A.4 notes Gram eigenvalues lose their precision) are kept instead of
+// being discarded with the floored eigenpairs of G_A.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace ttsn {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* get_error() { return g_err.c_str(); }
+
+tt_status DevBuf::ensure(size_t n, cudaStream_t s, bool keep) {
+    if (n <= cap) return TT_OK;
+    size_t want = std::max(n, cap + cap / 2);
+    double* np = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&np, want * sizeof(double), s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        want = n;
+        e = cudaMallocAsync((void**)&np, want * sizeof(double), s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error(std::string("device allocation of ") + std::to_string(want * 8) +
+                      " bytes failed: " + cudaGetErrorString(e));
+            return TT_ERR_OOM;
+        }
+    }
+    if (keep && p && cap) TT_CUDA_TRY(cudaMemcpyAsync(np, p, cap * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (p) TT_CUDA_TRY(cudaFreeAsync(p, s));
+    p = np;
+    cap = want;
+    return TT_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+}  // namespace ttsn
+
+using namespace ttsn;
+
+// host-side slots of the pinned readback block
+enum { HI_KB = 0, HI_DEC = 16, HI_STATUS = 20, HI_SWEEPS = 24, HI_N = 64 };
+enum { HD_DEC = 0, HD_DELTA2 = 4, HD_TOT = 8, HD_N = 16 };
+
+struct tt_ctx {
+    cudaStream_t stream = nullptr;
+    bool physics = false;
+    int d = 0;
+    int n[TT_MAX_D] = {0};
+    int r[TT_MAX_D + 1] = {0};
+    DevBuf core[TT_MAX_D];
+    DevBuf gcore[TT_MAX_D];
+    int gr[TT_MAX_D + 1] = {0};
+
+    // rounding workspace
+    DevBuf GB[TT_MAX_D], lamB[TT_MAX_D], VtB[TT_MAX_D];
+    DevBuf GA, W, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd;
+    EigWork eig;
+    int* d_int = nullptr;      // device ints (HI_* layout)
+    double* d_dbl = nullptr;   // device doubles (HD_* layout)
+    int* h_int = nullptr;      // pinned host mirror
+    double* h_dbl = nullptr;
+    int sweeps_slot = 0;
+
+    // physics
+    Grid grid{};
+    Angular ang{};
+    Fields fields{};
+    DevBuf f_sigma_a, f_sigma_s, f_cv, f_T, f_Estar, f_E, thbar, red, ang_buf;
+    bool has_sigma_s = false;
+    double eps = 0.0;
+    int max_rank = 0;
+    int rounds = 1;
+    double dV = 1.0;
+
+    tt_status init_common(cudaStream_t s) {
+        stream = s;
+        TT_CUDA_TRY(cudaMalloc(&d_int, HI_N * sizeof(int)));
+        TT_CUDA_TRY(cudaMalloc(&d_dbl, HD_N * sizeof(double)));
+        TT_CUDA_TRY(cudaMallocHost(&h_int, HI_N * sizeof(int)));
+        TT_CUDA_TRY(cudaMallocHost(&h_dbl, HD_N * sizeof(double)));
+        TT_CUDA_TRY(cudaMemsetAsync(d_int, 0, HI_N * sizeof(int), s));
+        return TT_OK;
+    }
+    ~tt_ctx() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (int k = 0; k < TT_MAX_D; ++k) {
+            core[k].release();
+            gcore[k].release();
+            GB[k].release();
+            lamB[k].release();
+            VtB[k].release();
+        }
+        DevBuf* bufs[] = {&GA, &W, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
+                          &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
+                          &thbar, &red, &ang_buf};
+        for (DevBuf* b : bufs) b->release();
+        eig.release();
+        if (d_int) cudaFree(d_int);
+        if (d_dbl) cudaFree(d_dbl);
+        if (h_int) cudaFreeHost(h_int);
+        if (h_dbl) cudaFreeHost(h_dbl);
+    }
+    size_t core_len(int k, const int* rr) const { return (size_t)rr[k] * n[k] * rr[k + 1]; }
+};
+
+namespace {
+
+tt_status fail(tt_status st, const std::string& msg) {
+    set_error(msg);
+    return st;
+}
+
+tt_status read_status(tt_ctx* h) {
+    TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_STATUS, h->d_int + HI_STATUS, sizeof(int),
+                                cudaMemcpyDeviceToHost, h->stream));
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const int st = h->h_int[HI_STATUS];
+    if (st) TT_CUDA_TRY(cudaMemsetAsync(h->d_int + HI_STATUS, 0, sizeof(int), h->stream));
+    if (st & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "device: a bounded grid barrier wait ran out");
+    if (st & DEV_NOT_CONVERGED)
+        return fail(TT_ERR_NOT_CONVERGED, "device: Jacobi eigensolver reached its sweep limit");
+    return TT_OK;
+}
+
+int next_sweep_slot(tt_ctx* h) {
+    const int slot = HI_SWEEPS + (h->sweeps_slot % (HI_N - HI_SWEEPS));
+    h->sweeps_slot++;
+    return slot;
+}
+
+// Set dst to a rank-one zero TT (the rounding of a zero tensor).
+tt_status zero_tt(tt_ctx* h, DevBuf* dst, int* rr) {
+    for (int k = 0; k < h->d; ++k) {
+        TT_TRY(dst[k].ensure((size_t)h->n[k], h->stream));
+        fill(h->stream, dst[k].p, (size_t)h->n[k], 0.0);
+        rr[k] = 1;
+    }
+    rr[0] = rr[h->d] = 1;
+    return TT_OK;
+}
+
+// Algorithm 1 (App. A) with the Gram truncation.  Reads cores src[k] with ranks
+// R[0..d]; writes the rounded cores into dst (h->core) with ranks rr.
+tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr, double eps,
+                      int max_rank, const int* forced, tt_step_info* info) {
+    cudaStream_t s = h->stream;
+    const int d = h->d;
+    const int* n = h->n;
+    h->sweeps_slot = 0;
+    TT_CUDA_TRY(cudaMemsetAsync(h->d_int + HI_SWEEPS, 0, (HI_N - HI_SWEEPS) * sizeof(int), s));
+    if (info) {
+        info->d = d;
+        for (int k = 0; k <= d; ++k) info->grown[k] = R[k];
+        info->capped = 0;
+        info->norm = 0.0;
+        for (int k = 0; k < TT_MAX_D; ++k) info->discarded[k] = 0.0;
+    }
+    if (d == 1) {  // nothing to round
+        TT_TRY(dst[0].ensure((size_t)n[0], s));
+        TT_CUDA_TRY(cudaMemcpyAsync(dst[0].p, src[0].p, n[0] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        rr[0] = rr[1] = 1;
+        return TT_OK;
+    }
+    // ---- backward sweep: right Grams GB[k] = B_k^T B_k for bond k
+    {
+        const int Rl = R[d - 1];
+        TT_TRY(h->GB[d - 2].ensure((size_t)Rl * Rl, s));
+        TT_TRY(dgemm(s, false, true, Rl, Rl, n[d - 1], 1.0, src[d - 1].p, n[d - 1], src[d - 1].p,
+                     n[d - 1], 0.0, h->GB[d - 2].p, Rl));
+        for (int k = d - 3; k >= 0; --k) {
+            const int Ra = R[k + 1], nn = n[k + 1], Rb = R[k + 2];
+            TT_TRY(h->bwd.ensure((size_t)Ra * nn * Rb, s));
+            TT_TRY(h->GB[k].ensure((size_t)Ra * Ra, s));
+            TT_TRY(dgemm(s, false, false, Ra * nn, Rb, Rb, 1.0, src[k + 1].p, Rb, h->GB[k + 1].p,
+                         Rb, 0.0, h->bwd.p, Rb));
+            TT_TRY(dgemm(s, false, true, Ra, Ra, nn * Rb, 1.0, h->bwd.p, (long)nn * Rb,
+                         src[k + 1].p, (long)nn * Rb, 0.0, h->GB[k].p, Ra));
+        }
+        for (int k = 0; k <= d - 2; ++k) {
+            const int Rk = R[k + 1];
+            TT_TRY(h->lamB[k].ensure((size_t)Rk, s));
+            TT_TRY(h->VtB[k].ensure((size_t)Rk * Rk, s));
+            TT_TRY(syev(s, Rk, h->GB[k].p, Rk, h->lamB[k].p, h->VtB[k].p, Rk, h->eig,
+                        h->d_int + HI_STATUS, h->d_int + next_sweep_slot(h)));
+            count_above_floor(s, h->lamB[k].p, Rk, h->d_int + HI_KB + k);
+        }
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_KB, h->d_int + HI_KB, (d - 1) * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    int kBs[TT_MAX_D];
+    for (int k = 0; k < d - 1; ++k) kBs[k] = h->h_int[HI_KB + k];
+
+    // delta^2 is set from the first bond's ||X||^2
+    h->h_dbl[HD_DELTA2] = -1.0;
+    TT_CUDA_TRY(cudaMemcpyAsync(h->d_dbl + HD_DELTA2, h->h_dbl + HD_DELTA2, sizeof(double),
+                                cudaMemcpyHostToDevice, s));
+    rr[0] = 1;
+    const double* A = src[0].p;
+    int rprev = 1;
+    int tmp_idx = 0;
+    bool any_capped = false;
+    for (int k = 0; k <= d - 2; ++k) {
+        const int Rk = R[k + 1];
+        const int kB = kBs[k];
+        const long m = (long)rprev * n[k];
+        if (kB == 0) return zero_tt(h, dst, rr);
+        // G_A = A^T A
+        TT_TRY(h->GA.ensure((size_t)Rk * Rk, s));
+        TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
+        // W = S_B V_B^T (kB x Rk)
+        TT_TRY(h->W.ensure((size_t)kB * Rk, s));
+        scale_rows(s, kB, Rk, h->VtB[k].p, Rk, h->lamB[k].p, 1, h->W.p, Rk);
+        // K = W G_A W^T
+        TT_TRY(h->T1.ensure((size_t)Rk * kB, s));
+        TT_TRY(h->K.ensure((size_t)kB * kB, s));
+        TT_TRY(dgemm(s, false, true, Rk, kB, Rk, 1.0, h->GA.p, Rk, h->W.p, Rk, 0.0, h->T1.p, kB));
+        TT_TRY(dgemm(s, false, false, kB, kB, Rk, 1.0, h->W.p, Rk, h->T1.p, kB, 0.0, h->K.p, kB));
+        TT_TRY(h->lamK.ensure((size_t)kB, s));
+        TT_TRY(h->VtK.ensure((size_t)kB * kB, s));
+        TT_TRY(syev(s, kB, h->K.p, kB, h->lamK.p, h->VtK.p, kB, h->eig, h->d_int + HI_STATUS,
+                    h->d_int + next_sweep_slot(h)));
+        const int fk = forced ? forced[k] : 0;
+        truncation_decision(s, h->lamK.p, kB, eps, d - 1, fk, max_rank, h->d_dbl + HD_DELTA2,
+                            h->d_int + HI_DEC, h->d_dbl + HD_DEC);
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_DEC, h->d_int + HI_DEC, 4 * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_DEC, h->d_dbl + HD_DEC, 4 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+        const int rk = h->h_int[HI_DEC];
+        if (h->h_int[HI_DEC + 1]) any_capped = true;
+        if (info) {
+            info->discarded[k] = sqrt(std::max(h->h_dbl[HD_DEC + 1], 0.0));
+            if (k == 0) info->norm = sqrt(std::max(h->h_dbl[HD_DEC + 2], 0.0));
+        }
+        if (rk == 0) return zero_tt(h, dst, rr);
+        // P_A^T = S~^{-1} V~_r^T W  (rk x Rk);   A' = A P_A -> dst[k]
+        TT_TRY(h->Vts.ensure((size_t)rk * kB, s));
+        scale_rows(s, rk, kB, h->VtK.p, kB, h->lamK.p, 2, h->Vts.p, kB);
+        TT_TRY(h->PAt.ensure((size_t)rk * Rk, s));
+        TT_TRY(dgemm(s, false, false, rk, Rk, kB, 1.0, h->Vts.p, kB, h->W.p, Rk, 0.0, h->PAt.p, Rk));
+        TT_TRY(dst[k].ensure((size_t)m * rk, s));
+        TT_TRY(dgemm(s, false, true, (int)m, rk, Rk, 1.0, A, Rk, h->PAt.p, Rk, 0.0, dst[k].p, rk));
+        // M_upd = P_A^T G_A = A'^T A  (rk x Rk): B'^T = A'^T A B^T, the orthogonal
+        // projection of A B^T onto span(A'); equals App. A.2's (V_B S_B^{-1} V~ S~)^T
+        // on the retained eigenspace of G_B without forming S_B^{-1}
+        TT_TRY(h->Mupd.ensure((size_t)rk * Rk, s));
+        TT_TRY(dgemm(s, false, false, rk, Rk, Rk, 1.0, h->PAt.p, Rk, h->GA.p, Rk, 0.0, h->Mupd.p, Rk));
+        // next core = M_upd x_1 G_{k+1}
+        const long ncols = (long)n[k + 1] * R[k + 2];
+        double* next;
+        if (k == d - 2) {
+            TT_TRY(dst[d - 1].ensure((size_t)rk * ncols, s));
+            next = dst[d - 1].p;
+        } else {
+            TT_TRY(h->tmp[tmp_idx].ensure((size_t)rk * ncols, s));
+            next = h->tmp[tmp_idx].p;
+            tmp_idx ^= 1;
+        }
+        TT_TRY(dgemm(s, false, false, rk, (int)ncols, Rk, 1.0, h->Mupd.p, Rk, src[k + 1].p, ncols,
+                     0.0, next, ncols));
+        rr[k + 1] = rk;
+        A = next;
+        rprev = rk;
+    }
+    rr[d] = 1;
+    if (info) {
+        info->capped = any_capped ? 1 : 0;
+        const int nslots = std::min(h->sweeps_slot, HI_N - HI_SWEEPS);
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_SWEEPS, h->d_int + HI_SWEEPS, nslots * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+        int mx = 0;
+        for (int i = 0; i < nslots; ++i) mx = std::max(mx, h->h_int[HI_SWEEPS + i]);
+        info->sweeps = mx;
+    }
+    return any_capped ? TT_WARN_RANK_CAPPED : TT_OK;
+}
+
+// Build the grown TT (transport terms and/or source) from h->core into h->gcore.
+tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
+    cudaStream_t s = h->stream;
+    const int r1 = h->r[1], r2 = h->r[2];
+    const int nterms = transport ? 1 + 2 * h->grid.ndim : 1;
+    const int sc = source ? 1 : 0;
+    const int R1 = nterms * r1 + sc, R2 = nterms * r2 + sc;
+    const long nc = h->grid.nc;
+    TT_TRY(h->gcore[0].ensure((size_t)nc * R1, s));
+    TT_TRY(h->gcore[1].ensure((size_t)R1 * h->ang.n_theta * R2, s));
+    TT_TRY(h->gcore[2].ensure((size_t)R2 * h->ang.n_phi, s));
+    if (source) {
+        TT_TRY(h->thbar.ensure((size_t)nterms * (r1 + r2), s));
+        grown_thbar(s, h->ang, h->grid.ndim, transport, r1, r2, h->core[1].p, h->core[2].p,
+                    h->thbar.p);
+    }
+    build_grown_angular(s, h->ang, h->grid.ndim, transport, source, r1, r2, h->core[1].p,
+                        h->core[2].p, h->gcore[1].p, h->gcore[2].p, R1, R2);
+    h->fields.T = h->f_T.p;
+    h->fields.E_star = h->f_Estar.p;
+    transport_source_rows(s, h->grid, h->fields, transport, source, r1, h->core[0].p, r1,
+                          source ? h->thbar.p : nullptr, h->gcore[0].p, R1);
+    TT_CUDA_TRY(cudaGetLastError());
+    h->gr[0] = 1;
+    h->gr[1] = R1;
+    h->gr[2] = R2;
+    h->gr[3] = 1;
+    return TT_OK;
+}
+
+void swap_grown_into_current(tt_ctx* h) {
+    for (int k = 0; k < h->d; ++k) std::swap(h->core[k], h->gcore[k]);
+    for (int k = 0; k <= h->d; ++k) h->r[k] = h->gr[k];
+}
+
+tt_status energy_update(tt_ctx* h) {
+    cudaStream_t s = h->stream;
+    const int r1 = h->r[1], r2 = h->r[2];
+    TT_TRY(h->thbar.ensure((size_t)(r1 + r2), s));
+    plain_thbar(s, h->ang, r1, r2, h->core[1].p, h->core[2].p, h->thbar.p);
+    energy_rows(s, h->grid.nc, r1, h->core[0].p, r1, h->thbar.p, h->fields.c, nullptr,
+                h->f_Estar.p, h->f_cv.p, h->f_T.p, true);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status step_once(tt_ctx* h, int flags, const int* forced, tt_step_info* info) {
+    const bool src = !(flags & TT_STEP_NO_SOURCE);
+    const bool rnd = !(flags & TT_STEP_NO_ROUND);
+    const bool two = (h->rounds == 2) && src && rnd;
+    tt_status result = TT_OK;
+    int rr[TT_MAX_D + 1];
+    TT_TRY(apply_terms(h, true, src && !two));
+    if (two) {
+        tt_status st = round_cores(h, h->gcore, h->gr, h->core, rr, h->eps, h->max_rank, forced, info);
+        if (forced) forced += h->d - 1;  // the second rounding takes the next d-1 entries
+        if (st < 0) return st;
+        if (st == TT_WARN_RANK_CAPPED) result = st;
+        for (int k = 0; k <= h->d; ++k) h->r[k] = rr[k];
+        TT_TRY(apply_terms(h, false, true));
+    }
+    if (rnd) {
+        tt_status st = round_cores(h, h->gcore, h->gr, h->core, rr, h->eps, h->max_rank, forced, info);
+        if (st < 0) return st;
+        if (st == TT_WARN_RANK_CAPPED) result = st;
+        for (int k = 0; k <= h->d; ++k) h->r[k] = rr[k];
+    } else {
+        swap_grown_into_current(h);
+        if (info) {
+            info->d = h->d;
+            for (int k = 0; k <= h->d; ++k) info->grown[k] = h->r[k];
+        }
+    }
+    if (src) TT_TRY(energy_update(h));
+    if (info)
+        for (int k = 0; k <= h->d; ++k) info->ranks[k] = h->r[k];
+    return result;
+}
+
+tt_status check_handle(tt_handle h, bool need_physics) {
+    if (!h) return fail(TT_ERR_ARG, "null handle");
+    if (need_physics && !h->physics) return fail(TT_ERR_STATE, "handle is a bare TT (no problem attached)");
+    return TT_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+const char* tt_last_error(void) { return get_error(); }
+
+tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
+    set_error("");
+    if (!desc || !out) return fail(TT_ERR_ARG, "tt_create: null argument");
+    *out = nullptr;
+    const tt_problem_desc& D = *desc;
+    if (D.ndim < 1 || D.ndim > 3) return fail(TT_ERR_ARG, "tt_create: ndim must be 1, 2 or 3");
+    long nc = 1;
+    for (int a = 0; a < D.ndim; ++a) {
+        if (D.n[a] < 1) return fail(TT_ERR_ARG, "tt_create: n[a] must be >= 1");
+        if (!(D.L[a] > 0.0)) return fail(TT_ERR_ARG, "tt_create: L[a] must be > 0");
+        if (D.bc[a] != TT_BC_PERIODIC && D.bc[a] != TT_BC_VACUUM)
+            return fail(TT_ERR_ARG, "tt_create: bc must be TT_BC_PERIODIC or TT_BC_VACUUM");
+        nc *= D.n[a];
+    }
+    if (nc > (1L << 31)) return fail(TT_ERR_TOO_LARGE, "tt_create: more than 2^31 cells");
+    if (D.n_theta < 1 || D.n_phi < 1) return fail(TT_ERR_ARG, "tt_create: n_theta, n_phi must be >= 1");
+    if (!(D.c > 0.0) || D.a_r < 0.0) return fail(TT_ERR_ARG, "tt_create: need c > 0, a_r >= 0");
+    if (!(D.dt > 0.0) && !(D.cfl > 0.0)) return fail(TT_ERR_ARG, "tt_create: need dt > 0 or cfl > 0");
+    if (!D.sigma_a || !D.cv || !D.T0) return fail(TT_ERR_ARG, "tt_create: sigma_a, cv, T0 are required");
+    if (D.eps < 0.0) return fail(TT_ERR_ARG, "tt_create: eps must be >= 0");
+    if (D.rounds_per_step != 1 && D.rounds_per_step != 2)
+        return fail(TT_ERR_ARG, "tt_create: rounds_per_step must be 1 or 2");
+    if (D.precision != TT_FP64) return fail(TT_ERR_ARG, "tt_create: precision must be TT_FP64");
+
+    tt_ctx* h = new tt_ctx();
+    cudaStream_t s = (cudaStream_t)stream;
+    tt_status st = h->init_common(s);
+    if (st < 0) {
+        delete h;
+        return st;
+    }
+    h->physics = true;
+    h->d = 3;
+    h->n[0] = (int)nc;
+    h->n[1] = D.n_theta;
+    h->n[2] = D.n_phi;
+    h->r[0] = h->r[1] = h->r[2] = h->r[3] = 1;
+    h->eps = D.eps;
+    h->max_rank = D.max_rank > 0 ? D.max_rank : 0;
+    h->rounds = D.rounds_per_step;
+    Grid& g = h->grid;
+    g.ndim = D.ndim;
+    g.nc = nc;
+    double dxmin = 1e300;
+    h->dV = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = a < D.ndim ? D.n[a] : 1;
+        g.dx[a] = a < D.ndim ? D.L[a] / D.n[a] : 1.0;
+        g.bc[a] = a < D.ndim ? D.bc[a] : TT_BC_PERIODIC;
+        if (a < D.ndim) {
+            dxmin = std::min(dxmin, g.dx[a]);
+            h->dV *= g.dx[a];
+        }
+    }
+    Fields& f = h->fields;
+    f.c = D.c;
+    f.a_r = D.a_r;
+    f.dt = D.dt > 0.0 ? D.dt : D.cfl * dxmin / D.c;
+
+    auto copy_field = [&](DevBuf& b, const double* srcp) -> tt_status {
+        TT_TRY(b.ensure((size_t)nc, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(b.p, srcp, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return TT_OK;
+    };
+#define TT_CREATE_TRY(expr)      \
+    do {                         \
+        tt_status _s2 = (expr);  \
+        if (_s2 < 0) {           \
+            delete h;            \
+            return _s2;          \
+        }                        \
+    } while (0)
+    TT_CREATE_TRY(copy_field(h->f_sigma_a, D.sigma_a));
+    TT_CREATE_TRY(copy_field(h->f_cv, D.cv));
+    TT_CREATE_TRY(copy_field(h->f_T, D.T0));
+    if (D.sigma_s) {
+        TT_CREATE_TRY(copy_field(h->f_sigma_s, D.sigma_s));
+        h->has_sigma_s = true;
+    }
+    TT_CREATE_TRY(h->f_Estar.ensure((size_t)nc, s));
+    TT_CREATE_TRY(h->f_E.ensure((size_t)nc, s));
+    TT_CREATE_TRY(h->red.ensure(4096, s));
+    f.sigma_a = h->f_sigma_a.p;
+    f.sigma_s = h->has_sigma_s ? h->f_sigma_s.p : nullptr;
+    f.cv = h->f_cv.p;
+    f.T = h->f_T.p;
+    f.E_star = h->f_Estar.p;
+
+    // angular grid (Sec. 3): mu and phi at cell centres, uniform weights
+    Angular& A = h->ang;
+    A.n_theta = D.n_theta;
+    A.n_phi = D.n_phi;
+    A.w = 2.0 / D.n_theta;
+    A.v = 2.0 * M_PI / D.n_phi;
+    std::vector<double> hbuf(2 * D.n_theta + 2 * D.n_phi);
+    for (int l = 0; l < D.n_theta; ++l) {
+        const double mu = -1.0 + (l + 0.5) * A.w;
+        hbuf[l] = mu;
+        hbuf[D.n_theta + l] = sqrt(1.0 - mu * mu);
+    }
+    for (int p = 0; p < D.n_phi; ++p) {
+        const double ph = (p + 0.5) * A.v;
+        hbuf[2 * D.n_theta + p] = cos(ph);
+        hbuf[2 * D.n_theta + D.n_phi + p] = sin(ph);
+    }
+    TT_CREATE_TRY(h->ang_buf.ensure(hbuf.size(), s));
+    A.mu = h->ang_buf.p;
+    A.sint = A.mu + D.n_theta;
+    A.cphi = A.sint + D.n_theta;
+    A.sphi = A.cphi + D.n_phi;
+    if (cudaMemcpyAsync(h->ang_buf.p, hbuf.data(), hbuf.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        delete h;
+        return fail(TT_ERR_CUDA, "tt_create: angular grid upload failed");
+    }
+    // initial TT: isotropic equilibrium intensity with Tr0, rank (1, 1)
+    TT_CREATE_TRY(h->core[0].ensure((size_t)nc, s));
+    TT_CREATE_TRY(h->core[1].ensure((size_t)D.n_theta, s));
+    TT_CREATE_TRY(h->core[2].ensure((size_t)D.n_phi, s));
+    init_isotropic(s, nc, D.Tr0 ? D.Tr0 : D.T0, D.c, D.a_r, h->core[0].p);
+    fill(s, h->core[1].p, D.n_theta, 1.0);
+    fill(s, h->core[2].p, D.n_phi, 1.0);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        delete h;
+        return fail(TT_ERR_CUDA, "tt_create: initialisation failed");
+    }
+#undef TT_CREATE_TRY
+    *out = h;
+    return TT_OK;
+}
+
+tt_status tt_create_tt(int d, const int* n, const int* ranks, void* stream, tt_handle* out) {
+    set_error("");
+    if (!out || !n || !ranks) return fail(TT_ERR_ARG, "tt_create_tt: null argument");
+    *out = nullptr;
+    if (d < 1 || d > TT_MAX_D) return fail(TT_ERR_ARG, "tt_create_tt: d out of range");
+    if (ranks[0] != 1 || ranks[d] != 1) return fail(TT_ERR_ARG, "tt_create_tt: ranks[0] and ranks[d] must be 1");
+    for (int k = 0; k < d; ++k) {
+        if (n[k] < 1) return fail(TT_ERR_ARG, "tt_create_tt: mode sizes must be >= 1");
+        if (ranks[k + 1] < 1) return fail(TT_ERR_ARG, "tt_create_tt: ranks must be >= 1");
+    }
+    tt_ctx* h = new tt_ctx();
+    cudaStream_t s = (cudaStream_t)stream;
+    tt_status st = h->init_common(s);
+    if (st < 0) {
+        delete h;
+        return st;
+    }
+    h->d = d;
+    for (int k = 0; k < d; ++k) h->n[k] = n[k];
+    for (int k = 0; k <= d; ++k) h->r[k] = ranks[k];
+    for (int k = 0; k < d; ++k) {
+        st = h->core[k].ensure(h->core_len(k, h->r), s);
+        if (st < 0) {
+            delete h;
+            return st;
+        }
+        fill(s, h->core[k].p, h->core_len(k, h->r), 0.0);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        delete h;
+        return fail(TT_ERR_CUDA, "tt_create_tt: initialisation failed");
+    }
+    *out = h;
+    return TT_OK;
+}
+
+tt_status tt_sn_step_ex(tt_handle h, int nsteps, int flags, const int* forced, tt_step_info* info) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    if (nsteps < 0) return fail(TT_ERR_ARG, "tt_sn_step: nsteps < 0");
+    if (flags & ~(TT_STEP_NO_SOURCE | TT_STEP_NO_ROUND)) return fail(TT_ERR_ARG, "tt_sn_step: unknown flag");
+    const int nforced = (h->rounds == 2 && !(flags & (TT_STEP_NO_SOURCE | TT_STEP_NO_ROUND))) ? 2 * (h->d - 1) : h->d - 1;
+    if (forced)
+        for (int k = 0; k < nforced; ++k)
+            if (forced[k] < 1) return fail(TT_ERR_ARG, "tt_sn_step: forced ranks must be >= 1");
+    tt_status result = TT_OK;
+    for (int it = 0; it < nsteps; ++it) {
+        tt_status st = step_once(h, flags, forced, info);
+        if (st < 0) return st;
+        if (st == TT_WARN_RANK_CAPPED) result = st;
+    }
+    tt_status st = read_status(h);
+    if (st < 0) return st;
+    return result;
+}
+
+tt_status tt_sn_step(tt_handle h, int nsteps, tt_step_info* info) {
+    return tt_sn_step_ex(h, nsteps, 0, nullptr, info);
+}
+
+tt_status tt_round(tt_handle h, double eps, int max_rank, const int* forced, tt_step_info* info) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (eps < 0.0) return fail(TT_ERR_ARG, "tt_round: eps < 0");
+    if (forced)
+        for (int k = 0; k < h->d - 1; ++k)
+            if (forced[k] < 1) return fail(TT_ERR_ARG, "tt_round: forced ranks must be >= 1");
+    // current TT becomes the rounding source
+    for (int k = 0; k < h->d; ++k) std::swap(h->core[k], h->gcore[k]);
+    for (int k = 0; k <= h->d; ++k) h->gr[k] = h->r[k];
+    int rr[TT_MAX_D + 1];
+    tt_status st = round_cores(h, h->gcore, h->gr, h->core, rr, eps, max_rank > 0 ? max_rank : 0,
+                               forced, info);
+    if (st < 0) return st;
+    for (int k = 0; k <= h->d; ++k) h->r[k] = rr[k];
+    if (info)
+        for (int k = 0; k <= h->d; ++k) info->ranks[k] = h->r[k];
+    tt_status st2 = read_status(h);
+    if (st2 < 0) return st2;
+    return st;
+}
+
+tt_status tt_energy(tt_handle h, double* E_dev, double* T_dev, double* totals_host) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    cudaStream_t s = h->stream;
+    const long nc = h->grid.nc;
+    const int r1 = h->r[1], r2 = h->r[2];
+    TT_TRY(h->thbar.ensure((size_t)(r1 + r2), s));
+    plain_thbar(s, h->ang, r1, r2, h->core[1].p, h->core[2].p, h->thbar.p);
+    double* E = E_dev ? E_dev : h->f_E.p;
+    energy_rows(s, nc, r1, h->core[0].p, r1, h->thbar.p, h->fields.c, E, nullptr, nullptr, nullptr,
+                false);
+    if (T_dev)
+        TT_CUDA_TRY(cudaMemcpyAsync(T_dev, h->f_T.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (totals_host) {
+        energy_totals(s, nc, E, h->f_cv.p, h->f_T.p, h->red.p + 2048, h->red.p);
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_TOT, h->red.p + 2048, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    TT_CUDA_TRY(cudaGetLastError());
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (totals_host) {
+        totals_host[0] = h->h_dbl[HD_TOT] * h->dV;
+        totals_host[1] = h->h_dbl[HD_TOT + 1] * h->dV;
+    }
+    return TT_OK;
+}
+
+tt_status tt_to_full(tt_handle h, double* out_dev, size_t out_len) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (!out_dev) return fail(TT_ERR_ARG, "tt_to_full: null output");
+    cudaStream_t s = h->stream;
+    const int d = h->d;
+    size_t total = 1;
+    for (int k = 0; k < d; ++k) total *= (size_t)h->n[k];
+    if (out_len < total) return fail(TT_ERR_TOO_LARGE, "tt_to_full: output buffer too small");
+    if (d == 1) {
+        TT_CUDA_TRY(cudaMemcpyAsync(out_dev, h->core[0].p, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return TT_OK;
+    }
+    // right-to-left: T_k = core_k (r_k n_k x r_{k+1}) * T_{k+1} (r_{k+1} x prod n_{k+1:})
+    long cols = h->n[d - 1];
+    const double* T = h->core[d - 1].p;  // (r_{d-1} x n_{d-1})
+    int ti = 0;
+    for (int k = d - 2; k >= 0; --k) {
+        const long rows = (long)h->r[k] * h->n[k];
+        double* outp;
+        if (k == 0) {
+            outp = out_dev;
+        } else {
+            TT_TRY(h->tmp[ti].ensure((size_t)rows * cols, s));
+            outp = h->tmp[ti].p;
+            ti ^= 1;
+        }
+        TT_TRY(dgemm(s, false, false, (int)rows, (int)cols, h->r[k + 1], 1.0, h->core[k].p,
+                     h->r[k + 1], T, cols, 0.0, outp, cols));
+        T = outp;
+        cols *= h->n[k];
+    }
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    return TT_OK;
+}
+
+tt_status tt_get_ranks(tt_handle h, int* ranks_host, int cap) {
+    TT_TRY(check_handle(h, false));
+    if (!ranks_host) return fail(TT_ERR_ARG, "tt_get_ranks: null output");
+    for (int k = 0; k <= h->d && k < cap; ++k) ranks_host[k] = h->r[k];
+    return TT_OK;
+}
+
+tt_status tt_get_dims(tt_handle h, int* d_host, int* n_host) {
+    TT_TRY(check_handle(h, false));
+    if (d_host) *d_host = h->d;
+    if (n_host)
+        for (int k = 0; k < h->d; ++k) n_host[k] = h->n[k];
+    return TT_OK;
+}
+
+tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (k < 0 || k >= h->d) return fail(TT_ERR_ARG, "tt_get_core: k out of range");
+    const size_t len = h->core_len(k, h->r);
+    if (out_len < len) return fail(TT_ERR_TOO_LARGE, "tt_get_core: output buffer too small");
+    TT_CUDA_TRY(cudaMemcpyAsync(out_dev, h->core[k].p, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return TT_OK;
+}
+
+tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* ranks_host) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (!cores_dev || !ranks_host) return fail(TT_ERR_ARG, "tt_set_cores: null argument");
+    if (ranks_host[0] != 1 || ranks_host[h->d] != 1)
+        return fail(TT_ERR_ARG, "tt_set_cores: ranks[0] and ranks[d] must be 1");
+    for (int k = 1; k < h->d; ++k)
+        if (ranks_host[k] < 1) return fail(TT_ERR_ARG, "tt_set_cores: ranks must be >= 1");
+    for (int k = 0; k < h->d; ++k) {
+        const size_t len = h->core_len(k, ranks_host);
+        TT_TRY(h->core[k].ensure(len, h->stream));
+        TT_CUDA_TRY(cudaMemcpyAsync(h->core[k].p, cores_dev[k], len * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, h->stream));
+    }
+    for (int k = 0; k <= h->d; ++k) h->r[k] = ranks_host[k];
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return TT_OK;
+}
+
+tt_status tt_set_T(tt_handle h, const double* T_dev) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    if (!T_dev) return fail(TT_ERR_ARG, "tt_set_T: null input");
+    TT_CUDA_TRY(cudaMemcpyAsync(h->f_T.p, T_dev, h->grid.nc * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return TT_OK;
+}
+
+tt_status tt_sync(tt_handle h) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
+void tt_destroy(tt_handle h) { delete h; }
+
+tt_status tt_dgemm(int trans_a, int trans_b, int M, int N, int K, double alpha, const double* A,
+                   int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                   void* stream) {
+    set_error("");
+    if (M < 0 || N < 0 || K < 0) return fail(TT_ERR_ARG, "tt_dgemm: negative size");
+    if ((M && N && K) && (!A || !B || !C)) return fail(TT_ERR_ARG, "tt_dgemm: null pointer");
+    return dgemm((cudaStream_t)stream, trans_a != 0, trans_b != 0, M, N, K, alpha, A, lda, B, ldb,
+                 beta, C, ldc);
+}
+
+tt_status tt_gram(int m, int n, const double* A, int lda, double* G, int ldg, void* stream) {
+    set_error("");
+    if (m < 0 || n < 0) return fail(TT_ERR_ARG, "tt_gram: negative size");
+    if (n == 0) return TT_OK;
+    if (!A || !G) return fail(TT_ERR_ARG, "tt_gram: null pointer");
+    if (lda < n || ldg < n) return fail(TT_ERR_ARG, "tt_gram: leading dimension smaller than n");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf scratch;
+    tt_status st = gram(s, m, n, A, lda, G, ldg, scratch);
+    if (scratch.p) cudaFreeAsync(scratch.p, s);
+    if (st < 0) return st;
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status tt_syev(int n, const double* G, int ldg, double* lam, double* Vt, int ldv, void* stream,
+                  int* sweeps_host) {
+    set_error("");
+    if (n < 0) return fail(TT_ERR_ARG, "tt_syev: negative size");
+    if (n == 0) return TT_OK;
+    if (!G || !lam || !Vt) return fail(TT_ERR_ARG, "tt_syev: null pointer");
+    if (ldg < n || ldv < n) return fail(TT_ERR_ARG, "tt_syev: leading dimension smaller than n");
+    cudaStream_t s = (cudaStream_t)stream;
+    EigWork w;
+    int* d_small = nullptr;
+    TT_CUDA_TRY(cudaMallocAsync((void**)&d_small, 2 * sizeof(int), s));
+    TT_CUDA_TRY(cudaMemsetAsync(d_small, 0, 2 * sizeof(int), s));
+    tt_status st = syev(s, n, G, ldg, lam, Vt, ldv, w, d_small, d_small + 1);
+    int hs[2] = {0, 0};
+    cudaMemcpyAsync(hs, d_small, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d_small, s);
+    w.release();
+    if (st < 0) return st;
+    if (e != cudaSuccess) return fail(TT_ERR_CUDA, std::string("tt_syev: ") + cudaGetErrorString(e));
+    if (sweeps_host) *sweeps_host = hs[1];
+    if (hs[0] & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_syev: grid barrier wait ran out");
+    if (hs[0] & DEV_NOT_CONVERGED) return fail(TT_ERR_NOT_CONVERGED, "tt_syev: sweep limit reached");
+    return TT_OK;
+}
+
+}  // extern "C"

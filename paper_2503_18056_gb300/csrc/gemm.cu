@@ -1,0 +1,275 @@
+// FP64 contractions of the Gram-SVD rounding (App. A.2 of arXiv 2503.18056):
+// a general row-major GEMM and the tall-skinny left Gram G_A = A^T A, both on
+// the FP64 tensor pipe (mma.sync m8n8k4.f64).  On GB300 the FP64 tensor pipe
+// is about 4x the FP64 FMA pipe, and the contractions are deeply compute
+// bound (about 14 flop per clock per SM), so a 64x64x16 shared-memory tile
+// with four warps of 32x32 each keeps the pipe fed; operand staging is plain
+// coalesced loads.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace ttsn {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, PADM = 4;
+constexpr int THREADS = 128;
+
+__device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
+    asm volatile(
+        "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+        : "+d"(c[0]), "+d"(c[1])
+        : "d"(a), "d"(b));
+}
+
+// grid: x = N tiles, y = M tiles, z = batch * ksplit.
+// Batch entry b, split ks: rows of K in [ks*kchunk, min(K,(ks+1)*kchunk)), output
+// to C + b*sC + ks*sCsplit.  upper_only: skip tiles strictly below the diagonal.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(THREADS)
+dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, long lda, long sA,
+             const double* __restrict__ B, long ldb, long sB, double beta, double* __restrict__ C,
+             long ldc, long sC, int ksplit, int kchunk, long sCsplit, int upper_only) {
+    const int tn = blockIdx.x, tm = blockIdx.y;
+    if (upper_only && tn < tm) return;
+    const int b = blockIdx.z / ksplit, ks = blockIdx.z % ksplit;
+    A += b * sA;
+    B += b * sB;
+    C += b * sC + ks * sCsplit;
+    const int kbeg = ks * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    const int m0 = tm * BM, n0 = tn * BN;
+
+    __shared__ double As[BK][BM + PADM];
+    __shared__ double Bs[BK][BN + PADM];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    double acc[4][4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        // stage op(A) tile: (kk, mm) = op(A)(m0+mm, k0+kk)
+#pragma unroll
+        for (int it = 0; it < (BM * BK) / THREADS; ++it) {
+            const int idx = tid + it * THREADS;
+            int kk, mm;
+            if (TA) { mm = idx % BM; kk = idx / BM; }
+            else    { kk = idx % BK; mm = idx / BK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < M && gk < kend) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
+            As[kk][mm] = v;
+        }
+#pragma unroll
+        for (int it = 0; it < (BN * BK) / THREADS; ++it) {
+            const int idx = tid + it * THREADS;
+            int kk, nn;
+            if (TB) { kk = idx % BK; nn = idx / BK; }
+            else    { nn = idx % BN; kk = idx / BN; }
+            const int gn = n0 + nn, gk = k0 + kk;
+            double v = 0.0;
+            if (gn < N && gk < kend) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 4) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk + (lane & 3)][wm + i * 8 + (lane >> 2)];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk + (lane & 3)][wn + j * 8 + (lane >> 2)];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dmma(acc[i][j], a[i], bb[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + wm + i * 8 + (lane >> 2);
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int gn = n0 + wn + j * 8 + (lane & 3) * 2 + e;
+                if (gn >= N) continue;
+                double* dst = C + (long)gm * ldc + gn;
+                const double v = alpha * acc[i][j][e];
+                *dst = (beta == 0.0) ? v : v + beta * (*dst);
+            }
+        }
+    }
+}
+
+// G[i][j] = sum_z P[z][min(i,j)][max(i,j)]  (fixed order => reproducible, symmetric)
+__global__ void gram_reduce_kernel(int n, int ksplit, const double* __restrict__ P, double* G,
+                                   long ldg) {
+    const long total = (long)n * n;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        const int a = min(i, j), b = max(i, j);
+        double s = 0.0;
+        for (int z = 0; z < ksplit; ++z) s += P[(long)z * n * n + (long)a * n + b];
+        G[(long)i * ldg + j] = s;
+    }
+}
+
+__global__ void scale_rows_kernel(int rows, int cols, const double* in, long ldi, const double* v,
+                                  int mode, double* out, long ldo) {
+    const long total = (long)rows * cols;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / cols), j = (int)(t % cols);
+        const double x = v[i];
+        double f;
+        switch (mode) {
+            case 0: f = x; break;
+            case 1: f = sqrt(x); break;
+            case 2: f = 1.0 / sqrt(x); break;
+            default: f = 1.0 / x; break;
+        }
+        out[(long)i * ldo + j] = in[(long)i * ldi + j] * f;
+    }
+}
+
+__global__ void fill_kernel(double* p, size_t n, double value) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+         t += (size_t)gridDim.x * blockDim.x)
+        p[t] = value;
+}
+
+__global__ void copy2d_kernel(int rows, int cols, const double* in, long ldi, double* out,
+                              long ldo) {
+    const long total = (long)rows * cols;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / cols), j = (int)(t % cols);
+        out[(long)i * ldo + j] = in[(long)i * ldi + j];
+    }
+}
+
+inline int grid_for(long total, int threads = 256) {
+    long b = (total + threads - 1) / threads;
+    return (int)std::max<long>(1, std::min<long>(b, 152L * 32));
+}
+
+tt_status launch_gemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                      const double* A, long lda, long sA, const double* B, long ldb, long sB,
+                      double beta, double* C, long ldc, long sC, int batch, int ksplit,
+                      int kchunk, long sCsplit, int upper) {
+    if (M <= 0 || N <= 0 || batch <= 0) return TT_OK;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * ksplit);
+    if (grid.y > 65535 || grid.z > 65535) {
+        set_error("dgemm: problem too large for the tile grid");
+        return TT_ERR_TOO_LARGE;
+    }
+    if (ta && tb)
+        dgemm_kernel<true, true><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ksplit, kchunk, sCsplit, upper);
+    else if (ta)
+        dgemm_kernel<true, false><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ksplit, kchunk, sCsplit, upper);
+    else if (tb)
+        dgemm_kernel<false, true><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ksplit, kchunk, sCsplit, upper);
+    else
+        dgemm_kernel<false, false><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ksplit, kchunk, sCsplit, upper);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+}  // namespace
+
+tt_status dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                const double* A, long lda, const double* B, long ldb, double beta, double* C,
+                long ldc, int batch, long strideA, long strideB, long strideC) {
+    if (M < 0 || N < 0 || K < 0) {
+        set_error("dgemm: negative size");
+        return TT_ERR_ARG;
+    }
+    if (K == 0) {  // C = beta C
+        if (beta == 0.0) {
+            for (int b = 0; b < batch; ++b)
+                for (int i = 0; i < M; ++i) fill(s, C + b * strideC + (long)i * ldc, N, 0.0);
+        }
+        return TT_OK;
+    }
+    return launch_gemm(s, ta, tb, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc,
+                       strideC, batch, 1, K, 0, 0);
+}
+
+namespace {
+int gram_ksplit(int m, int n) {
+    const long T = (n + BN - 1) / BN;
+    const long tiles = T * (T + 1) / 2;
+    const long target = 152L * 4;
+    long ks = (target + tiles - 1) / tiles;
+    ks = std::min<long>(ks, std::max<long>(1, m / 256));
+    ks = std::max<long>(1, std::min<long>(ks, 1024));
+    return (int)ks;
+}
+}  // namespace
+
+size_t gram_scratch_doubles(int m, int n) {
+    return (size_t)gram_ksplit(m, n) * (size_t)n * (size_t)n;
+}
+
+tt_status gram_with_scratch(cudaStream_t s, int m, int n, const double* A, long lda, double* G,
+                            long ldg, double* scratch, size_t scratch_doubles) {
+    if (m < 0 || n < 0) {
+        set_error("gram: negative size");
+        return TT_ERR_ARG;
+    }
+    if (n == 0) return TT_OK;
+    if (m == 0) {
+        for (int i = 0; i < n; ++i) fill(s, G + (long)i * ldg, n, 0.0);
+        return TT_OK;
+    }
+    const int ks = gram_ksplit(m, n);
+    if (scratch_doubles < (size_t)ks * n * n) {
+        set_error("gram: scratch too small");
+        return TT_ERR_TOO_LARGE;
+    }
+    int kchunk = (m + ks - 1) / ks;
+    kchunk = ((kchunk + BK - 1) / BK) * BK;
+    // op(A) = A^T (stored m x n => trans), op(B) = A (not trans): (n x m)(m x n)
+    TT_TRY(launch_gemm(s, true, false, n, n, m, 1.0, A, lda, 0, A, lda, 0, 0.0, scratch, n, 0, 1,
+                       ks, kchunk, (long)n * n, 1));
+    gram_reduce_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, ks, scratch, G, ldg);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
+               DevBuf& partials) {
+    if (n <= 0) return TT_OK;
+    const size_t need = gram_scratch_doubles(std::max(m, 1), n);
+    TT_TRY(partials.ensure(need, s));
+    return gram_with_scratch(s, m, n, A, lda, G, ldg, partials.p, partials.cap);
+}
+
+void scale_rows(cudaStream_t s, int rows, int cols, const double* in, long ldi, const double* v,
+                int mode, double* out, long ldo) {
+    if (rows <= 0 || cols <= 0) return;
+    scale_rows_kernel<<<grid_for((long)rows * cols), 256, 0, s>>>(rows, cols, in, ldi, v, mode,
+                                                                 out, ldo);
+}
+
+void fill(cudaStream_t s, double* p, size_t n, double value) {
+    if (n == 0) return;
+    fill_kernel<<<grid_for((long)n), 256, 0, s>>>(p, n, value);
+}
+
+void copy2d(cudaStream_t s, int rows, int cols, const double* in, long ldi, double* out,
+            long ldo) {
+    if (rows <= 0 || cols <= 0) return;
+    copy2d_kernel<<<grid_for((long)rows * cols), 256, 0, s>>>(rows, cols, in, ldi, out, ldo);
+}
+
+}  // namespace ttsn

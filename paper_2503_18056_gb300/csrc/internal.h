@@ -1,0 +1,147 @@
+// Internal declarations shared by the libttsn translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ttsn.h"
+
+namespace ttsn {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+const char* get_error();
+
+#define TT_CUDA_TRY(expr)                                                           \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) {                                                    \
+            ::ttsn::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+            return (_e == cudaErrorMemoryAllocation) ? TT_ERR_OOM : TT_ERR_CUDA;    \
+        }                                                                           \
+    } while (0)
+
+#define TT_TRY(expr)                         \
+    do {                                     \
+        tt_status _s = (expr);               \
+        if (_s < 0) return _s;               \
+    } while (0)
+
+// Device status word values (latched by kernels, read by the host).
+enum : int { DEV_OK = 0, DEV_NOT_CONVERGED = 1, DEV_TIMEOUT = 2 };
+
+// ---------------------------------------------------------------- device buffer
+// A growable device buffer: capacity only grows; contents are not preserved
+// across a grow unless `keep` is set.
+struct DevBuf {
+    double* p = nullptr;
+    size_t cap = 0;  // in doubles
+    tt_status ensure(size_t n, cudaStream_t s, bool keep = false);
+    void release();
+};
+
+// ---------------------------------------------------------------- GEMM (gemm.cu)
+// C = alpha op(A) op(B) + beta C, row-major FP64 on mma.m8n8k4.
+// batch > 1: A, B, C advance by strideA/B/C per batch entry.
+tt_status dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                const double* A, long lda, const double* B, long ldb, double beta, double* C,
+                long ldc, int batch = 1, long strideA = 0, long strideB = 0, long strideC = 0);
+
+// G = A^T A (A: m x n row-major, lda); split over rows with fixed-order reduction.
+// `partials` is scratch grown as needed (ksplit * n * n doubles).
+tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
+               DevBuf& partials);
+// The same with caller-provided scratch of `scratch_doubles` entries (no allocation).
+tt_status gram_with_scratch(cudaStream_t s, int m, int n, const double* A, long lda, double* G,
+                            long ldg, double* scratch, size_t scratch_doubles);
+size_t gram_scratch_doubles(int m, int n);
+
+// Row scaling: out[i][j] = in[i][j] * f(v[i]) for i < rows, j < cols, where
+// mode 0: v, 1: sqrt(v), 2: 1/sqrt(v), 3: 1/v.  out may alias in.
+void scale_rows(cudaStream_t s, int rows, int cols, const double* in, long ldi, const double* v,
+                int mode, double* out, long ldo);
+void fill(cudaStream_t s, double* p, size_t n, double value);
+void copy2d(cudaStream_t s, int rows, int cols, const double* in, long ldi, double* out, long ldo);
+
+// ---------------------------------------------------------------- eigensolver (jacobi.cu)
+struct EigWork {
+    DevBuf g0, g1;          // double-buffered matrix
+    DevBuf lam_unsorted;
+    DevBuf vt_unsorted;
+    int* d_ctrl = nullptr;  // barrier counters, sweep counters, status
+    int ctrl_cap = 0;
+    void release();
+};
+// Eigendecomposition of symmetric n x n G (ldg): lam descending (n), Vt rows = eigvecs.
+// *status_dev receives DEV_* codes (or-ed in); sweeps written to sweeps_dev[0].
+tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, double* Vt,
+               long ldv, EigWork& w, int* status_dev, int* sweeps_dev);
+
+// ---------------------------------------------------------------- rounding helpers (jacobi.cu)
+// Truncation decision for one bond (App. A, note on rank truncation).
+// Inputs: lamK (kB, descending, eigenvalues of M^T M), kB; mode: eps rule with
+// delta2 (if delta2 < 0 it is set from this bond: delta2 = eps^2 ||X||^2/(d-1)),
+// or forced rank (>0), and max_rank cap (<=0 none).
+// Output (device int/double array `dec`): dec_i[0] = r', dec_i[1] = capped,
+// dec_d[0] = delta2 used, dec_d[1] = discarded tail (sum sigma^2), dec_d[2] = ||X||^2.
+void truncation_decision(cudaStream_t s, const double* lamK, int kB, double eps, int dm1,
+                         int forced, int max_rank, double* delta2_dev, int* dec_i,
+                         double* dec_d);
+// Count of eigenvalues above the floor n * eps_mach * lam_max (lam descending).
+void count_above_floor(cudaStream_t s, const double* lam, int n, int* out_dev);
+
+// ---------------------------------------------------------------- physics (transport.cu)
+struct Angular {
+    int n_theta, n_phi;
+    double* mu = nullptr;   // device, n_theta
+    double* sint = nullptr; // device, n_theta
+    double* cphi = nullptr; // device, n_phi
+    double* sphi = nullptr; // device, n_phi
+    double w, v;            // quadrature weights (uniform)
+};
+
+// Build the grown angular cores for the TT sum of transport (+ source) terms.
+// nterms = 1 + 2 ndim if transport else 1; source adds one unit block.
+void build_grown_angular(cudaStream_t s, const Angular& ang, int ndim, bool transport,
+                         bool source, int r1, int r2, const double* Th, const double* Ph,
+                         double* Thg, double* Phg, int R1, int R2);
+// thbar[a] = sum_l w thfac_j[l] sum_b Th[a,l,b] phibar_j[b] for the grown core
+// blocks (first nterms*r1 entries), phibar_j[b] = sum_p v phfac_j[p] Ph[b,p].
+void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, int r1, int r2,
+                 const double* Th, const double* Ph, double* thbar);
+// Plain quadrature vector of a 3-core TT: thbar[a] = sum_l w sum_b Th[a,l,b] sum_p v Ph[b,p].
+void plain_thbar(cudaStream_t s, const Angular& ang, int r1, int r2, const double* Th,
+                 const double* Ph, double* thbar);
+
+struct Grid {
+    int ndim;
+    int n[3];
+    double dx[3];
+    int bc[3];
+    long nc;
+};
+struct Fields {
+    double *sigma_a, *sigma_s, *cv, *T, *E_star;
+    double c, a_r, dt;
+};
+// Fused transport + source row kernel (Sec. 4.3-4.4).  Writes Xg (nc x R1,
+// ld = ldg): transport blocks then (if source) scaled by s_i and the emission
+// column.  Computes E* (the post-transport energy) into fields.E_star when
+// source is set.  thbar: grown quadrature vector (nterms*r1 entries).
+void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool transport,
+                           bool source, int r1, const double* X, long ldx, const double* thbar,
+                           double* Xg, long ldg);
+// E_i = X_i . thbar / c (r entries); if update_T: T_i += (E*_i - E_i) / cv_i.
+void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
+                 double c, double* E_out, const double* E_star, const double* cv, double* T,
+                 bool update_T);
+// Isotropic initial intensity I = c a_r Tr^4 / 4 pi into X (nc x 1).
+void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X);
+// totals[0] = sum E, totals[1] = sum cv T (deterministic two-pass reduction).
+void energy_totals(cudaStream_t s, long nc, const double* E, const double* cv, const double* T,
+                   double* totals_dev, double* scratch /* >= 2*1024 doubles */);
+
+}  // namespace ttsn
