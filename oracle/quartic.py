@@ -11,47 +11,55 @@ whose left side is strictly increasing for T >= T_b = -(4 gamma a_r)^(-1/3).
 The root is taken on that branch: it lies in [0, min(rhs, (rhs/(gamma a_r))^(1/4))]
 when rhs >= 0, in [T_b, rhs] when 0.75 T_b <= rhs < 0, and T_b is returned when
 rhs < 0.75 T_b (no root on the branch; unphysical inputs only).  The oracle
-finds it by plain bisection to the last representable bit.
+finds it by plain bisection to the last representable bit, elementwise over
+the cells (each cell stops when its midpoint equals an end point).
 """
 import numpy as np
+
+
+def _f(T, ga, rhs):
+    T2 = T * T
+    return ga * (T2 * T2) + T - rhs
 
 
 def t_dagger(T_m, E_star, k_a, C_v, a_r):
     T_m, E_star, k_a, C_v = np.broadcast_arrays(
         np.asarray(T_m, float), np.asarray(E_star, float),
         np.asarray(k_a, float), np.asarray(C_v, float))
-    gamma = k_a / ((1.0 + k_a) * C_v)
-    rhs = T_m + gamma * E_star
-    out = np.empty(rhs.shape)
-    for idx in np.ndindex(rhs.shape):
-        out[idx] = _root(float(rhs[idx]), float(gamma[idx]) * float(a_r))
-    return out
-
-
-def _f(T, ga, rhs):
-    return ga * T ** 4 + T - rhs
-
-
-def _root(rhs, ga):
-    if ga == 0.0:
-        return rhs
-    Tb = -(4.0 * ga) ** (-1.0 / 3.0)
-    if rhs >= 0.0:
-        lo, hi = 0.0, min(rhs, (rhs / ga) ** 0.25)
-    elif rhs >= 0.75 * Tb:
-        lo, hi = Tb, rhs
-    else:
-        return Tb
-    # widen hi by one ulp-scale step in case the bound itself rounded low
-    while _f(hi, ga, rhs) < 0.0:
-        hi = np.nextafter(hi, np.inf) + 1e-300
+    shape = T_m.shape
+    gamma = (k_a / ((1.0 + k_a) * C_v)).reshape(-1)
+    rhs = (T_m + (k_a / ((1.0 + k_a) * C_v)) * E_star).reshape(-1)
+    ga = gamma * float(a_r)
+    out = rhs.copy()                      # ga == 0: the equation is linear, T = rhs
+    lo = np.zeros_like(rhs)
+    hi = np.zeros_like(rhs)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Tb = np.where(ga > 0, -(4.0 * np.where(ga > 0, ga, 1.0)) ** (-1.0 / 3.0), -np.inf)
+        pos = (ga > 0) & (rhs >= 0)
+        neg = (ga > 0) & (rhs < 0) & (rhs >= 0.75 * Tb)
+        none = (ga > 0) & (rhs < 0.75 * Tb)
+        hi[pos] = np.minimum(rhs[pos], (rhs[pos] / ga[pos]) ** 0.25)
+    lo[neg] = Tb[neg]
+    hi[neg] = rhs[neg]
+    out[none] = Tb[none]
+    act = pos | neg
+    # widen hi by a step in case the bound itself rounded low
+    bad = act & (_f(hi, ga, rhs) < 0.0)
+    while bad.any():
+        hi[bad] = np.nextafter(hi[bad], np.inf) + 1e-300
+        bad = act & (_f(hi, ga, rhs) < 0.0)
     for _ in range(4000):
-        mid = 0.5 * (lo + hi)
-        if mid <= lo or mid >= hi:
+        if not act.any():
             break
-        if _f(mid, ga, rhs) < 0.0:
-            lo = mid
-        else:
-            hi = mid
-    # return the endpoint with the smaller residual
-    return lo if abs(_f(lo, ga, rhs)) <= abs(_f(hi, ga, rhs)) else hi
+        mid = 0.5 * (lo + hi)
+        stop = act & ((mid <= lo) | (mid >= hi))
+        act = act & ~stop
+        below = act & (_f(mid, ga, rhs) < 0.0)
+        above = act & ~below
+        lo[below] = mid[below]
+        hi[above] = mid[above]
+    sel = pos | neg
+    flo = np.abs(_f(lo, ga, rhs))
+    fhi = np.abs(_f(hi, ga, rhs))
+    out[sel] = np.where(flo[sel] <= fhi[sel], lo[sel], hi[sel])
+    return out.reshape(shape)
