@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the TT-S_N step-then-truncate time step on GB300.
+
+Workload (default ``blob_3d``): 3D 128^3 cells on [0,1]^3, 32 x 64 ordinates
+(2048), sigma_a = 1e2 inside a seeded union of 16 spheres and 1e-2 elsewhere,
+T = 1 in a sphere of radius 0.1 at the centre and 1e-3 outside, radiation in
+equilibrium with T, vacuum boundaries, CFL 0.5, eps = 1e-6, ranks capped at
+128, FP64.  The intensity is held in the paper's three-core layout
+(X: N_c x r1, Theta: r1 x 32 x r2, Phi: r2 x 64).
+
+A "step" is one full time step (transport core apply, quadrature, quartic,
+source assembly, Gram-SVD rounding, energy-conserving temperature update).
+Warm-up: W steps of the same trajectory on the same handle, after which the
+state is reset to t = 0; then exactly K steps (steps 1..K of the trajectory)
+are timed with CUDA events on the library's stream, bracketed by a barrier and
+torch.cuda.synchronize().  The grown spatial core (>= N_c x 8 doubles = 134 MB
+from the first step, GBs later) is larger than L2, so no flush is added.
+
+Reported: steps/s (value), equivalent cell-ordinate updates/s, an end-to-end
+number through the public API with host-resident state, per-phase GPU times,
+the roofline of the dominant kernel family, SM clocks sampled during the timed
+region, the library's kernel launches, and the FP64 oracle timed on a bounded
+sample on the host cores (``cpu_baseline``).  ``--impl reference`` times the
+oracle itself (the slow CPU program) on the same metric.
+
+Multi-GPU: the step does not shard here (one problem per GPU); ``--gpus N``
+under torchrun runs N independent replicas ("scaling": "weak").
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "TT-SN steps/s (equiv. cell·ordinate updates/s), mixed vs FP64 at stated err"
+DEFAULT_STEPS = 12
+DEFAULT_WARMUP = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=DEFAULT_STEPS)
+    ap.add_argument("--warmup", type=int, default=DEFAULT_WARMUP)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="blob_3d", choices=["blob_3d", "small_2d"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=120.0,
+                    help="seconds of oracle stepping for --impl reference")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def workload_desc(p):
+    nd = len(p["n"])
+    return ("%s: %dD %s cells, %dx%d ordinates, layout grouped-space 3 cores (X,Theta,Phi), "
+            "eps=%g, rank cap %s, %s boundaries, CFL %g, FP64" % (
+                p["name"], nd, "x".join(str(m) for m in p["n"]), p["n_theta"], p["n_phi"],
+                p["eps"], p.get("max_rank"), "vacuum" if p["bc"][0] == 1 else "periodic", p["cfl"]))
+
+
+def cells_ordinates(p):
+    return int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"]
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2503_18056_gb300 as ttsn
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p = workloads.problem(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        g = ttsn.TTSN.from_problem(p, max_rank=p.get("max_rank", 0), stream=stream)
+        init_cores = [c.clone() for c in g.cores()]
+        _, T0, _ = g.energy()
+        T0 = T0.clone()
+        g.profile(False)
+
+        def reset():
+            g.set_cores(init_cores)
+            g.set_T(T0)
+
+        # warm-up: the first W steps of the trajectory, then back to t = 0
+        for _ in range(args.warmup):
+            g.step()
+        reset()
+        fp64_peak = ttsn.fp64_mma_peak(stream) if rank == 0 else None
+        torch.cuda.synchronize()
+
+        g.profile(True)
+        clocks = ClockSampler(local_rank)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ranks_hist = []
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        l0 = ttsn.kernel_launches()
+        ev[0].record(stream)
+        for k in range(args.steps):
+            info = g.step()
+            ev[k + 1].record(stream)
+            ranks_hist.append(info["ranks"][1:-1])
+        torch.cuda.synchronize()
+        launches = ttsn.kernel_launches() - l0
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[args.steps])
+        prof = g.profile_read()
+        g.profile(False)
+        E, T, tot = g.energy()
+
+        # end to end through the public API: the state lives on the host between
+        # steps (pinned), copied in before and out after every step
+        e2e = None
+        if not args.no_e2e:
+            host_cores = [c.cpu().pin_memory() for c in init_cores]
+            host_T = T0.cpu().pin_memory()
+            h2d = d2h = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                g.set_cores(host_cores)
+                g.set_T(host_T)
+                h2d += sum(c.numel() for c in host_cores) * 8 + host_T.numel() * 8
+                g.step()
+                dev_cores = g.cores()
+                host_cores = [c.to("cpu", non_blocking=False) for c in dev_cores]
+                _, Td, _ = g.energy()
+                host_T = Td.cpu()
+                d2h += sum(c.numel() for c in host_cores) * 8 + host_T.numel() * 8
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            e2e = {"value": args.steps / e2e_s, "unit": "steps/s",
+                   "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+    res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
+               clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p)
+    return res
+
+
+def roofline_of(prof, fp64_peak, peaks):
+    # dominant phase by GPU time
+    name = max(prof, key=lambda k: prof[k]["ms"])
+    ph = prof[name]
+    if ph["ms"] <= 0 or ph["launches"] <= 0:
+        return name, None
+    avg_ms = ph["ms"] / max(ph["calls"], 1)
+    if ph["flops"] > 0:
+        achieved = ph["flops"] / (ph["ms"] * 1e-3) / 1e12
+        peak = fp64_peak
+        return name, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                      "frac": achieved / peak if peak else None, "traffic": None,
+                      "kernel": name, "dtype": "f64", "avg_phase_ms": avg_ms,
+                      "launches": ph["launches"], "calls": ph["calls"],
+                      "peak_source": "measured FP64 tensor pipe (mma.m8n8k4.f64 chains on all SMs, "
+                                     "tt_bench_fp64_mma); MEASURED_PEAKS.json has no FP64 figure"}
+    achieved = ph["bytes"] / (ph["ms"] * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return name, {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                  "frac": achieved / peak, "traffic": None, "kernel": name, "avg_phase_ms": avg_ms,
+                  "launches": ph["launches"], "calls": ph["calls"],
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
+
+def cpu_baseline(p, budget_s, gpu_step_ms):
+    """The FP64 oracle (paper-form Gram-SVD rounding) as it stands, on the host
+    cores: the first m steps of the same trajectory, m bounded by budget_s."""
+    from oracle.ttstep import TTSN as OracleTTSN
+
+    I0 = p["c"] * p["a_r"] * p["Tr0"] ** 4 / (4 * np.pi)
+    ref = OracleTTSN(p["n"], p["L"], p["n_theta"], p["n_phi"], p["c"], p["a_r"], p["dt"], p["bc"],
+                     p["sigma_a"], p["cv"], p["T0"],
+                     OracleTTSN.isotropic_cores(I0.reshape(-1), p["n_theta"], p["n_phi"]),
+                     eps=p["eps"], max_rank=p.get("max_rank"), rounding="gram")
+    t_total, m, last = 0.0, 0, 0.0
+    # stop before a step whose predicted cost (ranks grow, so costs grow ~3x per
+    # step early on) would overshoot the budget
+    while m < len(gpu_step_ms) and (m == 0 or t_total + 3.0 * last <= budget_s):
+        t0 = time.perf_counter()
+        ref.step()
+        last = time.perf_counter() - t0
+        t_total += last
+        m += 1
+    cores = _blas_threads()
+    gpu_same = m / (sum(gpu_step_ms[:m]) * 1e-3) if m else None
+    return {"value": m / t_total if t_total else None, "unit": "steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": "steps 1..%d of the same trajectory (oracle TT stepper, NumPy FP64, paper-form "
+                      "Gram-SVD rounding), %.1f s of host time" % (m, t_total),
+            "gpu_value_same_steps": gpu_same}
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- reference (oracle) arm
+def run_reference(args):
+    from oracle.ttstep import TTSN as OracleTTSN
+
+    p = workloads.problem(args.workload)
+    I0 = p["c"] * p["a_r"] * p["Tr0"] ** 4 / (4 * np.pi)
+
+    def fresh():
+        return OracleTTSN(p["n"], p["L"], p["n_theta"], p["n_phi"], p["c"], p["a_r"], p["dt"], p["bc"],
+                          p["sigma_a"], p["cv"], p["T0"],
+                          OracleTTSN.isotropic_cores(I0.reshape(-1), p["n_theta"], p["n_phi"]),
+                          eps=p["eps"], max_rank=p.get("max_rank"), rounding="gram")
+
+    # warm-up: W repetitions of the first step from fresh states (the oracle has
+    # nothing to compile; this pages in NumPy/BLAS)
+    for _ in range(args.warmup):
+        fresh().step()
+    # timed: steps 1..m of the same trajectory as our arm, m <= K, stopping once
+    # the reference budget is spent (a step at the rank cap costs minutes here)
+    ref = fresh()
+    t0 = time.perf_counter()
+    m = 0
+    while m < args.steps and (m == 0 or time.perf_counter() - t0 < args.ref_budget):
+        ref.step()
+        m += 1
+    dt = time.perf_counter() - t0
+    v = m / dt
+    cores = _blas_threads()
+    sample = ("steps 1..%d of the same trajectory (of %d requested; %.0f s budget), NumPy FP64 oracle "
+              "with the paper-form Gram-SVD rounding" % (m, args.steps, args.ref_budget))
+    line = {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus, "steps": m,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / m, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_desc(p), "steps_timed": "1..%d" % m},
+            "updates_per_s": v * cells_ordinates(p),
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        line = run_reference(args)
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    total_ms = res["total_ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    p = res["p"]
+    steps = args.steps
+    value = world * steps / (total_ms * 1e-3)
+    peaks = read_peaks()
+    dom, roof = roofline_of(res["prof"], res["fp64_peak"], peaks)
+    prof_out = {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "calls": v["calls"],
+                    "share": round(v["ms"] / max(sum(x["ms"] for x in res["prof"].values()), 1e-9), 4),
+                    "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 and v["flops"] > 0 else None,
+                    "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
+                for k, v in res["prof"].items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(p), "parallelism": "replicas" if world > 1 else "single",
+                   "steps_timed": "steps 1..%d of the trajectory from t=0 (state reset after warm-up)" % steps,
+                   "ranks_first": res["ranks"][0], "ranks_last": res["ranks"][-1],
+                   "l2": "inputs larger than L2 (grown spatial core >= 134 MB from step 1)"},
+        "updates_per_s": value * cells_ordinates(p),
+        "step_ms": [round(x, 3) for x in res["step_ms"]],
+        "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"],
+        "roofline": roof, "phases": prof_out,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
+    s = json.dumps(line)
+    print(s)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(s + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

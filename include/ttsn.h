@@ -230,6 +230,50 @@ tt_status tt_gram(int m, int n, const double* A_dev, int lda, double* G_dev, int
 tt_status tt_syev(int n, const double* G_dev, int ldg, double* lam_dev, double* Vt_dev, int ldv,
                   void* stream, int* sweeps_host);
 
+/* ---------------------------------------------------------------------------
+ * Measurement calls (no counterpart in the paper; used by the benchmark to
+ * attribute time to the phases of the step and to count kernel launches).
+ * ------------------------------------------------------------------------ */
+
+/* Phases of the step timed with CUDA events on the handle's stream. */
+enum {
+    TT_PH_TRANSPORT = 0,  /* grown cores: transport terms + source (Sec. 4.3-4.4)  */
+    TT_PH_GRAM_RIGHT = 1, /* backward sweep: right Gram matrices (App. A, Alg. 1)  */
+    TT_PH_EIG = 2,        /* Jacobi eigensolves and rank decisions                */
+    TT_PH_GRAM_LEFT = 3,  /* left Gram G_A = A^T A of each bond (App. A.2)        */
+    TT_PH_SMALL = 4,      /* R x R products: W G_A W^T, P_A, M_upd                */
+    TT_PH_UPDATE = 5,     /* core updates A' = A P_A and M_upd x_1 G_{k+1}        */
+    TT_PH_ENERGY = 6,     /* quadrature of the rounded TT + temperature update    */
+    TT_NPHASES = 7
+};
+
+/*
+ * tt_profile: enable (1, also resets the accumulators) or disable (0) phase
+ * timing on the handle.  While enabled every phase is bracketed by CUDA events
+ * on the handle's stream; totals are resolved at the synchronisation points
+ * of each call.
+ */
+tt_status tt_profile(tt_handle h, int enable);
+
+/*
+ * tt_profile_read: accumulated totals of one phase since the last reset: GPU
+ * time in ms, kernel launches, phase occurrences, algorithmic flops and
+ * algorithmic DRAM bytes (each nullable).  The algorithmic counts are those of
+ * the operation (e.g. m R (R+1) flops for a symmetric m x R Gram), not of the
+ * kernels' implementation.
+ */
+tt_status tt_profile_read(tt_handle h, int phase, double* ms, long long* launches,
+                          long long* calls, double* flops, double* bytes);
+
+/* tt_kernel_launches: kernels launched by the library since the process started. */
+unsigned long long tt_kernel_launches(void);
+
+/*
+ * tt_bench_fp64_mma: measured throughput of the FP64 tensor pipe (dependent
+ * chains of mma.m8n8k4.f64 on every SM) in TFLOP/s, written to tflops_host.
+ */
+tt_status tt_bench_fp64_mma(double* tflops_host, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

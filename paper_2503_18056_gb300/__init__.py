@@ -93,6 +93,20 @@ class _Handle:
     def sync(self):
         check(lib.tt_sync(self._h))
 
+    def profile(self, enable=True):
+        check(lib.tt_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        out = {}
+        for k, name in enumerate(_native.PHASES):
+            ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            la, ca = ctypes.c_longlong(), ctypes.c_longlong()
+            check(lib.tt_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(la),
+                                      ctypes.byref(ca), ctypes.byref(fl), ctypes.byref(by)))
+            out[name] = {"ms": ms.value, "launches": la.value, "calls": ca.value,
+                         "flops": fl.value, "bytes": by.value}
+        return out
+
 
 class TensorTrain(_Handle):
     """A bare TT (no physics) for the rounding entry points."""
@@ -214,3 +228,15 @@ def syev(G, stream=None, allow_unconverged=False):
     if not (allow_unconverged and st == -4):
         check(st)
     return lam, Vt, sweeps.value
+
+
+def kernel_launches():
+    """Kernels launched by libttsn in this process so far."""
+    return int(lib.tt_kernel_launches())
+
+
+def fp64_mma_peak(stream=None):
+    """Measured FP64 tensor-pipe throughput of this GPU in TFLOP/s."""
+    v = ctypes.c_double()
+    check(lib.tt_bench_fp64_mma(ctypes.byref(v), _stream_ptr(stream)))
+    return v.value

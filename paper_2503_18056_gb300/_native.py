@@ -76,6 +76,10 @@ def _load():
         "tt_dgemm": [i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp],
         "tt_gram": [i, i, vp, i, vp, i, vp],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
+        "tt_profile": [vp, i],
+        "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
+                            ctypes.POINTER(ctypes.c_longlong), dp, dp],
+        "tt_bench_fp64_mma": [dp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -85,6 +89,8 @@ def _load():
     lib.tt_last_error.restype = ctypes.c_char_p
     lib.tt_destroy.argtypes = [vp]
     lib.tt_destroy.restype = None
+    lib.tt_kernel_launches.argtypes = []
+    lib.tt_kernel_launches.restype = ctypes.c_ulonglong
     return lib
 
 
@@ -94,7 +100,9 @@ lib = _load()
 EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_round", "tt_energy",
             "tt_to_full", "tt_get_ranks", "tt_get_dims", "tt_get_core", "tt_set_cores",
             "tt_set_T", "tt_sync", "tt_last_error", "tt_destroy", "tt_dgemm", "tt_gram",
-            "tt_syev"]
+            "tt_syev", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma"]
+
+PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 
 
 def check(status, allow_warn=True):

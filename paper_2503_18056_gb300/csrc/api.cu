@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -35,6 +36,8 @@
 namespace ttsn {
 
 static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void set_error(const std::string& msg) { g_err = msg; }
 const char* get_error() { return g_err.c_str(); }
 
@@ -95,6 +98,20 @@ struct tt_ctx {
     double* h_dbl = nullptr;
     int sweeps_slot = 0;
 
+    // phase profiler (CUDA events on the handle's stream)
+    struct PhaseAcc {
+        double ms = 0, flops = 0, bytes = 0;
+        long long launches = 0, calls = 0;
+    };
+    struct Pending {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    PhaseAcc ph[TT_NPHASES];
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+
     // physics
     Grid grid{};
     Angular ang{};
@@ -108,6 +125,15 @@ struct tt_ctx {
 
     tt_status init_common(cudaStream_t s) {
         stream = s;
+        // keep freed stream-ordered blocks cached in the device pool so capacity
+        // growth does not return memory to the OS between steps
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        (void)cudaGetLastError();
         TT_CUDA_TRY(cudaMalloc(&d_int, HI_N * sizeof(int)));
         TT_CUDA_TRY(cudaMalloc(&d_dbl, HD_N * sizeof(double)));
         TT_CUDA_TRY(cudaMallocHost(&h_int, HI_N * sizeof(int)));
@@ -129,6 +155,11 @@ struct tt_ctx {
                           &thbar, &red, &ang_buf};
         for (DevBuf* b : bufs) b->release();
         eig.release();
+        for (auto& p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : ev_pool) cudaEventDestroy(e);
         if (d_int) cudaFree(d_int);
         if (d_dbl) cudaFree(d_dbl);
         if (h_int) cudaFreeHost(h_int);
@@ -144,10 +175,59 @@ tt_status fail(tt_status st, const std::string& msg) {
     return st;
 }
 
+cudaEvent_t get_event(tt_ctx* h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one phase occurrence with events when profiling is on; the
+// algorithmic flops/bytes and the library launches in between are accumulated.
+struct PhaseScope {
+    tt_ctx* h;
+    int phase;
+    cudaEvent_t a = nullptr;
+    unsigned long long l0;
+    PhaseScope(tt_ctx* hh, int p, double flops, double bytes) : h(hh), phase(p) {
+        l0 = g_launches.load(std::memory_order_relaxed);
+        if (!h->prof_on) return;
+        a = get_event(h);
+        cudaEventRecord(a, h->stream);
+        h->ph[p].flops += flops;
+        h->ph[p].bytes += bytes;
+        h->ph[p].calls += 1;
+    }
+    ~PhaseScope() {
+        if (!h->prof_on || !a) return;
+        cudaEvent_t b = get_event(h);
+        cudaEventRecord(b, h->stream);
+        h->ph[phase].launches += (long long)(g_launches.load(std::memory_order_relaxed) - l0);
+        h->pending.push_back({phase, a, b});
+    }
+};
+
+// Resolve finished event pairs (call after a stream synchronisation).
+void resolve_profile(tt_ctx* h) {
+    for (auto& p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->ph[p.phase].ms += ms;
+        h->ev_pool.push_back(p.a);
+        h->ev_pool.push_back(p.b);
+    }
+    h->pending.clear();
+    (void)cudaGetLastError();
+}
+
 tt_status read_status(tt_ctx* h) {
     TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_STATUS, h->d_int + HI_STATUS, sizeof(int),
                                 cudaMemcpyDeviceToHost, h->stream));
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    resolve_profile(h);
     const int st = h->h_int[HI_STATUS];
     if (st) TT_CUDA_TRY(cudaMemsetAsync(h->d_int + HI_STATUS, 0, sizeof(int), h->stream));
     if (st & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "device: a bounded grid barrier wait ran out");
@@ -197,6 +277,12 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
     }
     // ---- backward sweep: right Grams GB[k] = B_k^T B_k for bond k
     {
+        double fl = 2.0 * R[d - 1] * (double)R[d - 1] * n[d - 1];
+        for (int k = d - 3; k >= 0; --k)
+            fl += 2.0 * R[k + 1] * (double)n[k + 1] * R[k + 2] * (R[k + 2] + R[k + 1]);
+        double by = 0;
+        for (int k = 1; k < d; ++k) by += 8.0 * R[k] * (double)n[k] * R[k + 1];
+        PhaseScope ps(h, TT_PH_GRAM_RIGHT, fl, by);
         const int Rl = R[d - 1];
         TT_TRY(h->GB[d - 2].ensure((size_t)Rl * Rl, s));
         TT_TRY(dgemm(s, false, true, Rl, Rl, n[d - 1], 1.0, src[d - 1].p, n[d - 1], src[d - 1].p,
@@ -210,6 +296,9 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             TT_TRY(dgemm(s, false, true, Ra, Ra, nn * Rb, 1.0, h->bwd.p, (long)nn * Rb,
                          src[k + 1].p, (long)nn * Rb, 0.0, h->GB[k].p, Ra));
         }
+    }
+    {
+        PhaseScope ps(h, TT_PH_EIG, 0.0, 0.0);
         for (int k = 0; k <= d - 2; ++k) {
             const int Rk = R[k + 1];
             TT_TRY(h->lamB[k].ensure((size_t)Rk, s));
@@ -241,22 +330,31 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         if (kB == 0) return zero_tt(h, dst, rr);
         // G_A = A^T A
         TT_TRY(h->GA.ensure((size_t)Rk * Rk, s));
-        TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
-        // W = S_B V_B^T (kB x Rk)
-        TT_TRY(h->W.ensure((size_t)kB * Rk, s));
-        scale_rows(s, kB, Rk, h->VtB[k].p, Rk, h->lamB[k].p, 1, h->W.p, Rk);
-        // K = W G_A W^T
-        TT_TRY(h->T1.ensure((size_t)Rk * kB, s));
-        TT_TRY(h->K.ensure((size_t)kB * kB, s));
-        TT_TRY(dgemm(s, false, true, Rk, kB, Rk, 1.0, h->GA.p, Rk, h->W.p, Rk, 0.0, h->T1.p, kB));
-        TT_TRY(dgemm(s, false, false, kB, kB, Rk, 1.0, h->W.p, Rk, h->T1.p, kB, 0.0, h->K.p, kB));
+        {
+            PhaseScope ps(h, TT_PH_GRAM_LEFT, (double)m * Rk * (Rk + 1.0), 8.0 * ((double)m * Rk + (double)Rk * Rk));
+            TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
+        }
+        {
+            PhaseScope ps(h, TT_PH_SMALL, 2.0 * Rk * (double)Rk * kB + 2.0 * kB * (double)kB * Rk, 0.0);
+            // W = S_B V_B^T (kB x Rk)
+            TT_TRY(h->W.ensure((size_t)kB * Rk, s));
+            scale_rows(s, kB, Rk, h->VtB[k].p, Rk, h->lamB[k].p, 1, h->W.p, Rk);
+            // K = W G_A W^T
+            TT_TRY(h->T1.ensure((size_t)Rk * kB, s));
+            TT_TRY(h->K.ensure((size_t)kB * kB, s));
+            TT_TRY(dgemm(s, false, true, Rk, kB, Rk, 1.0, h->GA.p, Rk, h->W.p, Rk, 0.0, h->T1.p, kB));
+            TT_TRY(dgemm(s, false, false, kB, kB, Rk, 1.0, h->W.p, Rk, h->T1.p, kB, 0.0, h->K.p, kB));
+        }
         TT_TRY(h->lamK.ensure((size_t)kB, s));
         TT_TRY(h->VtK.ensure((size_t)kB * kB, s));
-        TT_TRY(syev(s, kB, h->K.p, kB, h->lamK.p, h->VtK.p, kB, h->eig, h->d_int + HI_STATUS,
-                    h->d_int + next_sweep_slot(h)));
-        const int fk = forced ? forced[k] : 0;
-        truncation_decision(s, h->lamK.p, kB, eps, d - 1, fk, max_rank, h->d_dbl + HD_DELTA2,
-                            h->d_int + HI_DEC, h->d_dbl + HD_DEC);
+        {
+            PhaseScope ps(h, TT_PH_EIG, 0.0, 0.0);
+            TT_TRY(syev(s, kB, h->K.p, kB, h->lamK.p, h->VtK.p, kB, h->eig, h->d_int + HI_STATUS,
+                        h->d_int + next_sweep_slot(h)));
+            const int fk = forced ? forced[k] : 0;
+            truncation_decision(s, h->lamK.p, kB, eps, d - 1, fk, max_rank, h->d_dbl + HD_DELTA2,
+                                h->d_int + HI_DEC, h->d_dbl + HD_DEC);
+        }
         TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_DEC, h->d_int + HI_DEC, 4 * sizeof(int),
                                     cudaMemcpyDeviceToHost, s));
         TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_DEC, h->d_dbl + HD_DEC, 4 * sizeof(double),
@@ -269,20 +367,27 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             if (k == 0) info->norm = sqrt(std::max(h->h_dbl[HD_DEC + 2], 0.0));
         }
         if (rk == 0) return zero_tt(h, dst, rr);
-        // P_A^T = S~^{-1} V~_r^T W  (rk x Rk);   A' = A P_A -> dst[k]
-        TT_TRY(h->Vts.ensure((size_t)rk * kB, s));
-        scale_rows(s, rk, kB, h->VtK.p, kB, h->lamK.p, 2, h->Vts.p, kB);
-        TT_TRY(h->PAt.ensure((size_t)rk * Rk, s));
-        TT_TRY(dgemm(s, false, false, rk, Rk, kB, 1.0, h->Vts.p, kB, h->W.p, Rk, 0.0, h->PAt.p, Rk));
-        TT_TRY(dst[k].ensure((size_t)m * rk, s));
-        TT_TRY(dgemm(s, false, true, (int)m, rk, Rk, 1.0, A, Rk, h->PAt.p, Rk, 0.0, dst[k].p, rk));
-        // M_upd = P_A^T G_A = A'^T A  (rk x Rk): B'^T = A'^T A B^T, the orthogonal
-        // projection of A B^T onto span(A'); equals App. A.2's (V_B S_B^{-1} V~ S~)^T
-        // on the retained eigenspace of G_B without forming S_B^{-1}
-        TT_TRY(h->Mupd.ensure((size_t)rk * Rk, s));
-        TT_TRY(dgemm(s, false, false, rk, Rk, Rk, 1.0, h->PAt.p, Rk, h->GA.p, Rk, 0.0, h->Mupd.p, Rk));
-        // next core = M_upd x_1 G_{k+1}
         const long ncols = (long)n[k + 1] * R[k + 2];
+        {
+            PhaseScope ps(h, TT_PH_SMALL, 2.0 * rk * (double)kB * Rk + 2.0 * rk * (double)Rk * Rk, 0.0);
+            // P_A^T = S~^{-1} V~_r^T W  (rk x Rk)
+            TT_TRY(h->Vts.ensure((size_t)rk * kB, s));
+            scale_rows(s, rk, kB, h->VtK.p, kB, h->lamK.p, 2, h->Vts.p, kB);
+            TT_TRY(h->PAt.ensure((size_t)rk * Rk, s));
+            TT_TRY(dgemm(s, false, false, rk, Rk, kB, 1.0, h->Vts.p, kB, h->W.p, Rk, 0.0, h->PAt.p, Rk));
+            // M_upd = P_A^T G_A = A'^T A  (rk x Rk): B'^T = A'^T A B^T, the orthogonal
+            // projection of A B^T onto span(A'); equals App. A.2's (V_B S_B^{-1} V~ S~)^T
+            // on the retained eigenspace of G_B without forming S_B^{-1}
+            TT_TRY(h->Mupd.ensure((size_t)rk * Rk, s));
+            TT_TRY(dgemm(s, false, false, rk, Rk, Rk, 1.0, h->PAt.p, Rk, h->GA.p, Rk, 0.0, h->Mupd.p, Rk));
+        }
+        // A' = A P_A -> dst[k]
+        TT_TRY(dst[k].ensure((size_t)m * rk, s));
+        {
+            PhaseScope ps(h, TT_PH_UPDATE, 2.0 * m * (double)Rk * rk, 8.0 * ((double)m * Rk + (double)m * rk));
+            TT_TRY(dgemm(s, false, true, (int)m, rk, Rk, 1.0, A, Rk, h->PAt.p, Rk, 0.0, dst[k].p, rk));
+        }
+        // next core = M_upd x_1 G_{k+1}
         double* next;
         if (k == d - 2) {
             TT_TRY(dst[d - 1].ensure((size_t)rk * ncols, s));
@@ -292,8 +397,12 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             next = h->tmp[tmp_idx].p;
             tmp_idx ^= 1;
         }
-        TT_TRY(dgemm(s, false, false, rk, (int)ncols, Rk, 1.0, h->Mupd.p, Rk, src[k + 1].p, ncols,
-                     0.0, next, ncols));
+        {
+            PhaseScope ps(h, TT_PH_UPDATE, 2.0 * rk * (double)Rk * ncols,
+                          8.0 * ((double)Rk * ncols + (double)rk * ncols));
+            TT_TRY(dgemm(s, false, false, rk, (int)ncols, Rk, 1.0, h->Mupd.p, Rk, src[k + 1].p, ncols,
+                         0.0, next, ncols));
+        }
         rr[k + 1] = rk;
         A = next;
         rprev = rk;
@@ -320,6 +429,10 @@ tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
     const int sc = source ? 1 : 0;
     const int R1 = nterms * r1 + sc, R2 = nterms * r2 + sc;
     const long nc = h->grid.nc;
+    const double fbytes = 8.0 * nc * ((source ? 4.0 : 0.0) + (h->has_sigma_s && source ? 1.0 : 0.0));
+    PhaseScope ps(h, TT_PH_TRANSPORT, 0.0,
+                  8.0 * nc * (double)(r1 + R1) + fbytes +
+                      8.0 * ((double)R1 * h->ang.n_theta * R2 + (double)R2 * h->ang.n_phi));
     TT_TRY(h->gcore[0].ensure((size_t)nc * R1, s));
     TT_TRY(h->gcore[1].ensure((size_t)R1 * h->ang.n_theta * R2, s));
     TT_TRY(h->gcore[2].ensure((size_t)R2 * h->ang.n_phi, s));
@@ -351,6 +464,7 @@ tt_status energy_update(tt_ctx* h) {
     cudaStream_t s = h->stream;
     const int r1 = h->r[1], r2 = h->r[2];
     TT_TRY(h->thbar.ensure((size_t)(r1 + r2), s));
+    PhaseScope ps(h, TT_PH_ENERGY, 0.0, 8.0 * h->grid.nc * (r1 + 4.0));
     plain_thbar(s, h->ang, r1, r2, h->core[1].p, h->core[2].p, h->thbar.p);
     energy_rows(s, h->grid.nc, r1, h->core[0].p, r1, h->thbar.p, h->fields.c, nullptr,
                 h->f_Estar.p, h->f_cv.p, h->f_T.p, true);
@@ -524,6 +638,28 @@ tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
     TT_CREATE_TRY(h->core[0].ensure((size_t)nc, s));
     TT_CREATE_TRY(h->core[1].ensure((size_t)D.n_theta, s));
     TT_CREATE_TRY(h->core[2].ensure((size_t)D.n_phi, s));
+    if (h->max_rank > 0) {
+        // capacity reservation for the capped case: the largest cores and Gram
+        // workspaces a step can need, so steps do not allocate while ranks grow
+        const long cap1 = std::min<long>(h->max_rank, std::min<long>(nc, (long)D.n_theta * D.n_phi));
+        const long cap2 = std::min<long>(h->max_rank, D.n_phi);
+        const long nterms = 1 + 2 * D.ndim;
+        const long R1 = nterms * cap1 + 1, R2 = nterms * cap2 + 1;
+        TT_CREATE_TRY(h->core[0].ensure((size_t)(nc * cap1), s));
+        TT_CREATE_TRY(h->core[1].ensure((size_t)(R1 * D.n_theta * R2), s));
+        TT_CREATE_TRY(h->core[2].ensure((size_t)(R2 * D.n_phi), s));
+        TT_CREATE_TRY(h->gcore[0].ensure((size_t)(nc * R1), s));
+        TT_CREATE_TRY(h->gcore[1].ensure((size_t)(R1 * D.n_theta * R2), s));
+        TT_CREATE_TRY(h->gcore[2].ensure((size_t)(R2 * D.n_phi), s));
+        TT_CREATE_TRY(h->GA.ensure((size_t)(R1 * R1), s));
+        TT_CREATE_TRY(h->partials.ensure(gram_scratch_doubles((int)nc, (int)R1), s));
+        for (int k = 0; k < 2; ++k) {
+            const long Rk = k == 0 ? R1 : R2;
+            TT_CREATE_TRY(h->GB[k].ensure((size_t)(Rk * Rk), s));
+            TT_CREATE_TRY(h->VtB[k].ensure((size_t)(Rk * Rk), s));
+            TT_CREATE_TRY(h->lamB[k].ensure((size_t)Rk, s));
+        }
+    }
     init_isotropic(s, nc, D.Tr0 ? D.Tr0 : D.T0, D.c, D.a_r, h->core[0].p);
     fill(s, h->core[1].p, D.n_theta, 1.0);
     fill(s, h->core[2].p, D.n_phi, 1.0);
@@ -793,6 +929,41 @@ tt_status tt_syev(int n, const double* G, int ldg, double* lam, double* Vt, int 
     if (hs[0] & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_syev: grid barrier wait ran out");
     if (hs[0] & DEV_NOT_CONVERGED) return fail(TT_ERR_NOT_CONVERGED, "tt_syev: sweep limit reached");
     return TT_OK;
+}
+
+tt_status tt_profile(tt_handle h, int enable) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    resolve_profile(h);
+    h->prof_on = enable != 0;
+    if (enable)
+        for (int p = 0; p < TT_NPHASES; ++p) h->ph[p] = tt_ctx::PhaseAcc();
+    return TT_OK;
+}
+
+tt_status tt_profile_read(tt_handle h, int phase, double* ms, long long* launches,
+                          long long* calls, double* flops, double* bytes) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (phase < 0 || phase >= TT_NPHASES) return fail(TT_ERR_ARG, "tt_profile_read: bad phase");
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    resolve_profile(h);
+    const auto& a = h->ph[phase];
+    if (ms) *ms = a.ms;
+    if (launches) *launches = a.launches;
+    if (calls) *calls = a.calls;
+    if (flops) *flops = a.flops;
+    if (bytes) *bytes = a.bytes;
+    return TT_OK;
+}
+
+unsigned long long tt_kernel_launches(void) { return g_launches.load(); }
+
+tt_status tt_bench_fp64_mma(double* tflops_host, void* stream) {
+    set_error("");
+    if (!tflops_host) return fail(TT_ERR_ARG, "tt_bench_fp64_mma: null output");
+    return bench_fp64_mma((cudaStream_t)stream, tflops_host);
 }
 
 }  // extern "C"

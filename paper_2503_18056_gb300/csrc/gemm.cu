@@ -172,6 +172,7 @@ tt_status launch_gemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, dou
         set_error("dgemm: problem too large for the tile grid");
         return TT_ERR_TOO_LARGE;
     }
+    note_launch();
     if (ta && tb)
         dgemm_kernel<true, true><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ksplit, kchunk, sCsplit, upper);
     else if (ta)
@@ -241,6 +242,7 @@ tt_status gram_with_scratch(cudaStream_t s, int m, int n, const double* A, long 
     // op(A) = A^T (stored m x n => trans), op(B) = A (not trans): (n x m)(m x n)
     TT_TRY(launch_gemm(s, true, false, n, n, m, 1.0, A, lda, 0, A, lda, 0, 0.0, scratch, n, 0, 1,
                        ks, kchunk, (long)n * n, 1));
+    note_launch();
     gram_reduce_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, ks, scratch, G, ldg);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
@@ -257,19 +259,69 @@ tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* 
 void scale_rows(cudaStream_t s, int rows, int cols, const double* in, long ldi, const double* v,
                 int mode, double* out, long ldo) {
     if (rows <= 0 || cols <= 0) return;
+    note_launch();
     scale_rows_kernel<<<grid_for((long)rows * cols), 256, 0, s>>>(rows, cols, in, ldi, v, mode,
                                                                  out, ldo);
 }
 
 void fill(cudaStream_t s, double* p, size_t n, double value) {
     if (n == 0) return;
+    note_launch();
     fill_kernel<<<grid_for((long)n), 256, 0, s>>>(p, n, value);
 }
 
 void copy2d(cudaStream_t s, int rows, int cols, const double* in, long ldi, double* out,
             long ldo) {
     if (rows <= 0 || cols <= 0) return;
+    note_launch();
     copy2d_kernel<<<grid_for((long)rows * cols), 256, 0, s>>>(rows, cols, in, ldi, out, ldo);
+}
+
+namespace {
+constexpr int PEAK_ITERS = 2048;
+__global__ void __launch_bounds__(256) fp64_mma_peak_kernel(double* out, double seed) {
+    const double a = seed * (threadIdx.x + 1), b = 1.0 + 1e-3 * threadIdx.x;
+    double c[8][2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = 0.0;
+    for (int i = 0; i < PEAK_ITERS; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dmma(c[j], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += c[j][0] + c[j][1];
+    if (s == 1234.5) out[threadIdx.x] = s;  // keeps the chains live; never true in practice
+}
+}  // namespace
+
+tt_status bench_fp64_mma(cudaStream_t s, double* tflops) {
+    int dev = 0, sms = 0;
+    TT_CUDA_TRY(cudaGetDevice(&dev));
+    TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    double* out = nullptr;
+    TT_CUDA_TRY(cudaMallocAsync((void**)&out, 256 * sizeof(double), s));
+    cudaEvent_t e0, e1;
+    TT_CUDA_TRY(cudaEventCreate(&e0));
+    TT_CUDA_TRY(cudaEventCreate(&e1));
+    const int blocks = sms * 8;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        TT_CUDA_TRY(cudaEventRecord(e0, s));
+        note_launch();
+        fp64_mma_peak_kernel<<<blocks, 256, 0, s>>>(out, 1e-3);
+        TT_CUDA_TRY(cudaEventRecord(e1, s));
+        TT_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, s);
+    const double flops = 2.0 * 8 * 8 * 4 * 8.0 * PEAK_ITERS * blocks * (256 / 32);
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return TT_OK;
 }
 
 }  // namespace ttsn

@@ -33,6 +33,11 @@ const char* get_error();
 // Device status word values (latched by kernels, read by the host).
 enum : int { DEV_OK = 0, DEV_NOT_CONVERGED = 1, DEV_TIMEOUT = 2 };
 
+// ---------------------------------------------------------------- launch accounting
+// Every kernel launch of the library goes through note_launch() so callers can
+// count the library's launches inside a timed region (tt_kernel_launches).
+void note_launch(unsigned n = 1);
+
 // ---------------------------------------------------------------- device buffer
 // A growable device buffer: capacity only grows; contents are not preserved
 // across a grow unless `keep` is set.
@@ -58,6 +63,8 @@ tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* 
 tt_status gram_with_scratch(cudaStream_t s, int m, int n, const double* A, long lda, double* G,
                             long ldg, double* scratch, size_t scratch_doubles);
 size_t gram_scratch_doubles(int m, int n);
+// Measured FP64 tensor-pipe throughput (TFLOP/s).
+tt_status bench_fp64_mma(cudaStream_t s, double* tflops);
 
 // Row scaling: out[i][j] = in[i][j] * f(v[i]) for i < rows, j < cols, where
 // mode 0: v, 1: sqrt(v), 2: 1/sqrt(v), 3: 1/v.  out may alias in.

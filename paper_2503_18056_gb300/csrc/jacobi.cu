@@ -325,6 +325,7 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     }
     if (n == 0) return TT_OK;
     if (n == 1) {
+        note_launch();
         trivial_eig_kernel<<<1, 1, 0, s>>>(G, lam, Vt, sweeps_dev);
         TT_CUDA_TRY(cudaGetLastError());
         return TT_OK;
@@ -342,6 +343,7 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     {
         const long total = (long)n * n;
         const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+        note_launch();
         jacobi_init_kernel<<<blocks, 256, 0, s>>>(n, G, ldg, w.g0.p, w.vt_unsorted.p, ld);
         TT_CUDA_TRY(cudaGetLastError());
     }
@@ -377,8 +379,10 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     int nn = n, NN = N;
     long ldl = ld;
     void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &lamu, &ctrl, &status_dev, &tol_rel, &tol_abs_rel};
+    note_launch();
     TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(JT), args,
                                             smem, s));
+    note_launch();
     jacobi_sort_kernel<<<n, 256, 0, s>>>(n, w.lam_unsorted.p, ld, w.vt_unsorted.p, lam, Vt, ldv,
                                          sweeps_dev, w.d_ctrl);
     TT_CUDA_TRY(cudaGetLastError());
@@ -388,11 +392,13 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
 void truncation_decision(cudaStream_t s, const double* lamK, int kB, double eps, int dm1,
                          int forced, int max_rank, double* delta2_dev, int* dec_i,
                          double* dec_d) {
+    note_launch();
     truncation_kernel<<<1, 1, 0, s>>>(lamK, kB, eps, dm1, forced, max_rank, delta2_dev, dec_i,
                                       dec_d);
 }
 
 void count_above_floor(cudaStream_t s, const double* lam, int n, int* out_dev) {
+    note_launch();
     count_floor_kernel<<<1, 1, 0, s>>>(lam, n, out_dev);
 }
 

@@ -311,8 +311,10 @@ void build_grown_angular(cudaStream_t s, const Angular& ang, int ndim, bool tran
                          bool source, int r1, int r2, const double* Th, const double* Ph,
                          double* Thg, double* Phg, int R1, int R2) {
     const int nterms = transport ? 1 + 2 * ndim : 1;
+    note_launch();
     grown_theta_kernel<<<blocks_for((long)R1 * ang.n_theta * R2), 256, 0, s>>>(
         nterms, source ? 1 : 0, r1, r2, ang.n_theta, Th, ang.mu, ang.sint, Thg, R1, R2);
+    note_launch();
     grown_phi_kernel<<<blocks_for((long)R2 * ang.n_phi), 256, 0, s>>>(
         nterms, source ? 1 : 0, r2, ang.n_phi, Ph, ang.cphi, ang.sphi, Phg, R2);
 }
@@ -322,8 +324,10 @@ void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, i
                  const double* Th, const double* Ph, double* thbar) {
     const int nterms = transport ? 1 + 2 * ndim : 1;
     double* phibar = thbar + nterms * r1;
+    note_launch();
     phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph,
                                                                ang.cphi, ang.sphi, ang.v, phibar);
+    note_launch();
     thbar_kernel<<<blocks_for((long)nterms * r1, 64), 64, 0, s>>>(
         nterms, r1, r2, ang.n_theta, Th, ang.mu, ang.sint, ang.w, phibar, thbar);
 }
@@ -338,6 +342,7 @@ void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool 
                            double* Xg, long ldg) {
     const long warps_needed = g.nc;
     const int blocks = (int)std::max<long>(1, std::min<long>((warps_needed + 7) / 8, 152L * 64));
+    note_launch();
     transport_source_kernel<<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1, X,
                                                    ldx, thbar, Xg, ldg);
 }
@@ -346,17 +351,21 @@ void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, cons
                  double c, double* E_out, const double* E_star, const double* cv, double* T,
                  bool update_T) {
     const int blocks = (int)std::max<long>(1, std::min<long>((nc + 7) / 8, 152L * 64));
+    note_launch();
     energy_rows_kernel<<<blocks, 256, 0, s>>>(nc, r, X, ldx, thbar, c, E_out, E_star, cv, T,
                                               update_T ? 1 : 0);
 }
 
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X) {
+    note_launch();
     init_iso_kernel<<<blocks_for(nc), 256, 0, s>>>(nc, Tr, c, a_r, X);
 }
 
 void energy_totals(cudaStream_t s, long nc, const double* E, const double* cv, const double* T,
                    double* totals_dev, double* scratch) {
+    note_launch();
     totals_partial_kernel<<<RED_BLOCKS, 256, 0, s>>>(nc, E, cv, T, scratch);
+    note_launch();
     totals_final_kernel<<<1, 32, 0, s>>>(scratch, totals_dev);
 }
 

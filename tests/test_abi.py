@@ -7,7 +7,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "ttsn.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:tt_status|const char\*|void)\s+(tt_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:tt_status|const char\*|void|unsigned long long)\s+(tt_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declarations_found():
