@@ -230,6 +230,26 @@ tt_status tt_gram(int m, int n, const double* A_dev, int lda, double* G_dev, int
 tt_status tt_syev(int n, const double* G_dev, int ldg, double* lam_dev, double* Vt_dev, int ldv,
                   void* stream, int* sweeps_host);
 
+/*
+ * tt_gram_noalloc: the same G = A^T A as tt_gram, for callers that must not
+ * allocate device memory (for example an application whose own allocator owns
+ * all device memory, or a latency-critical loop that cannot afford the
+ * synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart; this
+ * is a property of the library, not of the method.  It allocates nothing: its
+ * split-K scratch is a fixed 8 MiB array in device global memory that every
+ * GPU loading the library holds until the process exits, which limits n to
+ * 1024 (larger n returns TT_ERR_TOO_LARGE with a message; use tt_gram).  The
+ * caller passes A (m x n, leading dimension lda) and the output G (n x n,
+ * leading dimension ldg).  The first call on each device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture begins.  All calls share the array, so calls that overlap on
+ * the GPU race on it and must be serialised by the caller.  Results equal
+ * tt_gram's up to the order of the floating-point sums (the split-K factor may
+ * be smaller) and are exactly symmetric and reproducible.
+ */
+tt_status tt_gram_noalloc(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg,
+                          void* stream);
+
 /* ---------------------------------------------------------------------------
  * Measurement calls (no counterpart in the paper; used by the benchmark to
  * attribute time to the phases of the step and to count kernel launches).

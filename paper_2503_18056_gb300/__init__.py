@@ -216,6 +216,18 @@ def gram(A, stream=None):
     return G
 
 
+def gram_noalloc(A, G=None, stream=None):
+    """G = A^T A through tt_gram_noalloc: the library allocates nothing (the
+    caller provides A and, optionally, the output G; n <= 1024)."""
+    A = _dev(A)
+    m, n = A.shape
+    if G is None:
+        G = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    check(lib.tt_gram_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), n, ctypes.c_void_p(G.data_ptr()),
+                              n, _stream_ptr(stream)))
+    return G
+
+
 def syev(G, stream=None, allow_unconverged=False):
     """(lam descending, Vt with eigenvectors as rows, sweeps) by parallel Jacobi."""
     G = _dev(G)

@@ -75,6 +75,7 @@ def _load():
         "tt_sync": [vp],
         "tt_dgemm": [i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp],
         "tt_gram": [i, i, vp, i, vp, i, vp],
+        "tt_gram_noalloc": [i, i, vp, i, vp, i, vp],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
@@ -100,7 +101,7 @@ lib = _load()
 EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_round", "tt_energy",
             "tt_to_full", "tt_get_ranks", "tt_get_dims", "tt_get_core", "tt_set_cores",
             "tt_set_T", "tt_sync", "tt_last_error", "tt_destroy", "tt_dgemm", "tt_gram",
-            "tt_syev", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma"]
+            "tt_syev", "tt_gram_noalloc", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

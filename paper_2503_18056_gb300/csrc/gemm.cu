@@ -248,6 +248,29 @@ tt_status gram_with_scratch(cudaStream_t s, int m, int n, const double* A, long 
     return TT_OK;
 }
 
+tt_status gram_fixed_scratch(cudaStream_t s, int m, int n, const double* A, long lda, double* G,
+                             long ldg, double* scratch, size_t scratch_doubles) {
+    if (n == 0) return TT_OK;
+    if (m == 0) {
+        for (int i = 0; i < n; ++i) fill(s, G + (long)i * ldg, n, 0.0);
+        return TT_OK;
+    }
+    const size_t per = (size_t)n * n;
+    if (per > scratch_doubles) {
+        set_error("gram: scratch smaller than one n x n partial");
+        return TT_ERR_TOO_LARGE;
+    }
+    const int ks = (int)std::min<size_t>((size_t)gram_ksplit(m, n), scratch_doubles / per);
+    int kchunk = (m + ks - 1) / ks;
+    kchunk = ((kchunk + BK - 1) / BK) * BK;
+    TT_TRY(launch_gemm(s, true, false, n, n, m, 1.0, A, lda, 0, A, lda, 0, 0.0, scratch, n, 0, 1,
+                       ks, kchunk, (long)n * n, 1));
+    note_launch();
+    gram_reduce_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, ks, scratch, G, ldg);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
 tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
                DevBuf& partials) {
     if (n <= 0) return TT_OK;

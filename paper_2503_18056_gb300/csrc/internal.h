@@ -63,6 +63,10 @@ tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* 
 tt_status gram_with_scratch(cudaStream_t s, int m, int n, const double* A, long lda, double* G,
                             long ldg, double* scratch, size_t scratch_doubles);
 size_t gram_scratch_doubles(int m, int n);
+// The same Gram with a fixed scratch: the split-K factor is reduced so the
+// partials fit in scratch_doubles (needs scratch_doubles >= n * n).
+tt_status gram_fixed_scratch(cudaStream_t s, int m, int n, const double* A, long lda, double* G,
+                             long ldg, double* scratch, size_t scratch_doubles);
 // Measured FP64 tensor-pipe throughput (TFLOP/s).
 tt_status bench_fp64_mma(cudaStream_t s, double* tflops);
 
