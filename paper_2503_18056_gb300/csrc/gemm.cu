@@ -206,11 +206,29 @@ tt_status dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double al
 }
 
 namespace {
+// CTAs of dgemm_kernel<true,false> resident on the whole GPU at once.
+long resident_gram_ctas() {
+    static long cached = 0;
+    if (cached) return cached;
+    int dev = 0, sms = 152, per = 4;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dgemm_kernel<true, false>, THREADS, 0) !=
+            cudaSuccess || per < 1)
+        per = 4;
+    (void)cudaGetLastError();
+    cached = (long)sms * per;
+    return cached;
+}
+
+// Row-split factor of the Gram: the upper-triangle tiles times the splits fill
+// at most one wave of resident CTAs (a partial extra wave would run at a
+// fraction of the machine), and every split keeps at least 256 rows.
 int gram_ksplit(int m, int n) {
     const long T = (n + BN - 1) / BN;
     const long tiles = T * (T + 1) / 2;
-    const long target = 152L * 4;
-    long ks = (target + tiles - 1) / tiles;
+    const long resident = resident_gram_ctas();
+    long ks = std::max<long>(1, resident / tiles);
     ks = std::min<long>(ks, std::max<long>(1, m / 256));
     ks = std::max<long>(1, std::min<long>(ks, 1024));
     return (int)ks;
