@@ -11,9 +11,10 @@
 //
 // Rounding per bond.  App. A.2 forms M = S_A V_A^T V_B S_B from two
 // eigendecompositions and takes the SVD of M.  Here the same quantities come
-// from one eigendecomposition fewer: with W = S_B V_B^T (floored eigenpairs of
-// G_B removed), K = W G_A W^T equals M^T M, so eig(K) = V~ S~^2 V~^T gives the
-// singular values and right singular vectors of M, and
+// from one eigendecomposition: with any factor W of G_B (W^T W = G_B; a
+// pivoted Cholesky factor stopped at the floor n eps_mach max diag, or
+// equivalently S_B V_B^T), K = W G_A W^T has the eigenvalues of M^T M, so
+// eig(K) = V~ S~^2 V~^T gives the singular values of M and
 //   A'    = A P_A,   P_A^T = S~_r^{-1} V~_r^T W,
 //   M_upd = P_A^T G_A = A'^T A,
 // which equal App. A.2's A V_A S_A^{-1} U~ and (V_B S_B^{-1} V~ S~)^T in exact
@@ -90,7 +91,7 @@ struct tt_ctx {
 
     // rounding workspace
     DevBuf GB[TT_MAX_D], lamB[TT_MAX_D], VtB[TT_MAX_D];
-    DevBuf GA, W, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd;
+    DevBuf GA, Wc, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd;
     EigWork eig;
     int* d_int = nullptr;      // device ints (HI_* layout)
     double* d_dbl = nullptr;   // device doubles (HD_* layout)
@@ -150,7 +151,7 @@ struct tt_ctx {
             lamB[k].release();
             VtB[k].release();
         }
-        DevBuf* bufs[] = {&GA, &W, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
+        DevBuf* bufs[] = {&GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf};
         for (DevBuf* b : bufs) b->release();
@@ -298,14 +299,16 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         }
     }
     {
+        // W_k with W_k^T W_k = G_B (pivoted Cholesky): the one-sided truncation
+        // needs only this factor of the right Gram matrix
         PhaseScope ps(h, TT_PH_EIG, 0.0, 0.0);
         for (int k = 0; k <= d - 2; ++k) {
             const int Rk = R[k + 1];
-            TT_TRY(h->lamB[k].ensure((size_t)Rk, s));
             TT_TRY(h->VtB[k].ensure((size_t)Rk * Rk, s));
-            TT_TRY(syev(s, Rk, h->GB[k].p, Rk, h->lamB[k].p, h->VtB[k].p, Rk, h->eig,
-                        h->d_int + HI_STATUS, h->d_int + next_sweep_slot(h)));
-            count_above_floor(s, h->lamB[k].p, Rk, h->d_int + HI_KB + k);
+            TT_TRY(h->Wc.ensure((size_t)Rk * Rk, s));
+            TT_TRY(h->lamB[k].ensure((size_t)Rk, s));
+            TT_TRY(pchol(s, Rk, h->GB[k].p, Rk, h->VtB[k].p, h->Wc.p, h->lamB[k].p, h->eig,
+                         h->d_int + HI_STATUS, h->d_int + HI_KB + k));
         }
         TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_KB, h->d_int + HI_KB, (d - 1) * sizeof(int),
                                     cudaMemcpyDeviceToHost, s));
@@ -336,14 +339,12 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         }
         {
             PhaseScope ps(h, TT_PH_SMALL, 2.0 * Rk * (double)Rk * kB + 2.0 * kB * (double)kB * Rk, 0.0);
-            // W = S_B V_B^T (kB x Rk)
-            TT_TRY(h->W.ensure((size_t)kB * Rk, s));
-            scale_rows(s, kB, Rk, h->VtB[k].p, Rk, h->lamB[k].p, 1, h->W.p, Rk);
-            // K = W G_A W^T
+            // W (kB x Rk, W^T W = G_B) from the backward sweep; K = W G_A W^T
+            const double* Wk = h->VtB[k].p;
             TT_TRY(h->T1.ensure((size_t)Rk * kB, s));
             TT_TRY(h->K.ensure((size_t)kB * kB, s));
-            TT_TRY(dgemm(s, false, true, Rk, kB, Rk, 1.0, h->GA.p, Rk, h->W.p, Rk, 0.0, h->T1.p, kB));
-            TT_TRY(dgemm(s, false, false, kB, kB, Rk, 1.0, h->W.p, Rk, h->T1.p, kB, 0.0, h->K.p, kB));
+            TT_TRY(dgemm(s, false, true, Rk, kB, Rk, 1.0, h->GA.p, Rk, Wk, Rk, 0.0, h->T1.p, kB));
+            TT_TRY(dgemm(s, false, false, kB, kB, Rk, 1.0, Wk, Rk, h->T1.p, kB, 0.0, h->K.p, kB));
         }
         TT_TRY(h->lamK.ensure((size_t)kB, s));
         TT_TRY(h->VtK.ensure((size_t)kB * kB, s));
@@ -374,7 +375,7 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             TT_TRY(h->Vts.ensure((size_t)rk * kB, s));
             scale_rows(s, rk, kB, h->VtK.p, kB, h->lamK.p, 2, h->Vts.p, kB);
             TT_TRY(h->PAt.ensure((size_t)rk * Rk, s));
-            TT_TRY(dgemm(s, false, false, rk, Rk, kB, 1.0, h->Vts.p, kB, h->W.p, Rk, 0.0, h->PAt.p, Rk));
+            TT_TRY(dgemm(s, false, false, rk, Rk, kB, 1.0, h->Vts.p, kB, h->VtB[k].p, Rk, 0.0, h->PAt.p, Rk));
             // M_upd = P_A^T G_A = A'^T A  (rk x Rk): B'^T = A'^T A B^T, the orthogonal
             // projection of A B^T onto span(A'); equals App. A.2's (V_B S_B^{-1} V~ S~)^T
             // on the retained eigenspace of G_B without forming S_B^{-1}

@@ -82,6 +82,7 @@ struct EigWork {
     DevBuf g0, g1;          // double-buffered matrix
     DevBuf lam_unsorted;
     DevBuf vt_unsorted;
+    DevBuf abc;             // per-round pair entries (double-buffered)
     int* d_ctrl = nullptr;  // barrier counters, sweep counters, status
     int ctrl_cap = 0;
     void release();
@@ -90,6 +91,13 @@ struct EigWork {
 // *status_dev receives DEV_* codes (or-ed in); sweeps written to sweeps_dev[0].
 tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, double* Vt,
                long ldv, EigWork& w, int* status_dev, int* sweeps_dev);
+
+// Pivoted Cholesky of a symmetric positive semidefinite n x n G (ldg): writes
+// W (rows 0..rank-1 of an n x n row-major buffer) with W^T W = G up to the
+// floor eps_mach max(diag G), Wc (n x n scratch, the transpose) and uses
+// dwork (n doubles).  The rank is written to kB_dev.
+tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, double* Wc,
+                double* dwork, EigWork& w, int* status_dev, int* kB_dev);
 
 // ---------------------------------------------------------------- rounding helpers (jacobi.cu)
 // Truncation decision for one bond (App. A, note on rank truncation).

@@ -1,19 +1,27 @@
-// Symmetric eigensolver and rank decision of the Gram-SVD rounding
-// (App. A.2 of arXiv 2503.18056: "G_A = V_A S_A^2 V_A^T, G_B = V_B S_B^2 V_B^T"
-// and the truncation of App. A, note on rank truncation).
+// Small dense factorisations of the Gram-SVD rounding (App. A.2 of arXiv
+// 2503.18056) and the rank decision of App. A (note on rank truncation).
 //
-// Eigensolver: two-sided cyclic Jacobi with the parallel round-robin
-// ("circle") ordering.  Each round applies n/2 disjoint plane rotations at
-// once: G <- J^T G J, Vt <- J^T Vt.  The work unit is a row pair (p, q): the
-// two rows are loaded with coalesced L2 reads, rotated on the left by their own
-// J_k, then every column pair is rotated in shared memory, and the rows are
-// written to the other buffer (the matrix is double-buffered so a round needs
-// one grid-wide barrier).  The kernel is persistent: a cooperative launch
-// guarantees co-residency and the grid barrier is a bounded spin that latches
-// DEV_TIMEOUT in the status word instead of waiting forever.  Rotation angles
-// follow Golub & Van Loan, Alg. 8.4.1 (symSchur2); a rotation is skipped when
-// |g_pq| <= tol_rel sqrt(|g_pp g_qq|) or |g_pq| <= tol_abs, and the sweep loop
-// stops after a sweep that skipped every rotation.
+// 1. Symmetric eigensolver: two-sided cyclic Jacobi with the parallel
+//    round-robin ("circle") ordering.  Each round applies n/2 disjoint plane
+//    rotations at once: G <- J^T G J, Vt <- J^T Vt.  A CTA owns a few row pairs
+//    (p, q) per round: it loads those rows with coalesced L2 reads, rotates them
+//    on the left by their own J_k, rotates every column pair in shared memory,
+//    and writes them to the other buffer (the matrix is double-buffered, so a
+//    round needs one grid-wide barrier).  The three entries (g_pp, g_qq, g_pq)
+//    that define the next round's rotations are written by the row owners into
+//    a compact array, so every CTA reads them with one coalesced load.  Rotation
+//    angles follow Golub & Van Loan, Alg. 8.4.1 (symSchur2); a rotation is
+//    skipped when |g_pq| <= tol_rel sqrt(|g_pp g_qq|) or |g_pq| <= tol_abs, and
+//    the sweeps stop after one that skipped every rotation.
+// 2. Pivoted Cholesky of a positive semidefinite matrix, G = W^T W with W
+//    upper-trapezoidal in pivot order (left-looking, diagonal pivoting, stopped
+//    when the largest remaining diagonal entry is at eps_mach max(diag G)).  The rounding
+//    needs from G_B only a factor with W^T W = G_B, which this gives in n
+//    sequential steps instead of an eigendecomposition.
+//
+// Both kernels are persistent: a cooperative launch guarantees co-residency and
+// the grid barrier is a bounded spin that latches DEV_TIMEOUT in the status
+// word instead of waiting forever.
 #include <algorithm>
 
 #include "internal.h"
@@ -25,9 +33,10 @@ namespace {
 constexpr int JT = 256;
 constexpr int MAX_SWEEPS = 40;
 // control block (ints): [0] barrier count, [1] barrier generation, [2] sweeps,
-// [4 .. 4+MAX_SWEEPS) rotations applied per sweep
+// [3] pivoted-Cholesky rank, [4 .. 4+MAX_SWEEPS) rotations applied per sweep
 constexpr int CTRL_INTS = 8 + MAX_SWEEPS;
 constexpr long long SPIN_LIMIT = 1LL << 24;  // ~1-2 s with the 64 ns sleep
+constexpr int MAX_PAIRS_PER_CTA = 8;
 
 __device__ __forceinline__ void round_pair(int N, int r, int k, int& p, int& q) {
     const int m = N - 1;
@@ -42,6 +51,29 @@ __device__ __forceinline__ void round_pair(int N, int r, int k, int& p, int& q) 
         const int t = p;
         p = q;
         q = t;
+    }
+}
+
+// Pair index and partner of index x in round r (inverse of round_pair).
+__device__ __forceinline__ void pair_of(int N, int r, int x, int& k, int& partner) {
+    const int m = N - 1;
+    if (x == m) {
+        k = 0;
+        partner = r;
+        return;
+    }
+    if (x == r) {
+        k = 0;
+        partner = m;
+        return;
+    }
+    const int d = (x - r + m) % m;  // 1 .. m-1
+    if (d <= N / 2 - 1) {
+        k = d;
+        partner = (r - d + m) % m;
+    } else {
+        k = m - d;
+        partner = (r + k) % m;
     }
 }
 
@@ -82,8 +114,8 @@ __device__ bool grid_barrier(int* ctrl, int* status, unsigned nblocks) {
     return s_ok != 0;
 }
 
-__global__ void jacobi_init_kernel(int n, const double* __restrict__ G, long ldg, double* g0,
-                                   double* vt, long ld) {
+__global__ void jacobi_init_kernel(int n, int N, const double* __restrict__ G, long ldg, double* g0,
+                                   double* vt, long ld, double* abc) {
     const long total = (long)n * n;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
@@ -91,25 +123,39 @@ __global__ void jacobi_init_kernel(int n, const double* __restrict__ G, long ldg
         g0[(long)i * ld + j] = G[(long)i * ldg + j];
         vt[(long)i * ld + j] = (i == j) ? 1.0 : 0.0;
     }
+    // entries of the round-0 pairs
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N / 2; k += gridDim.x * blockDim.x) {
+        int p, q;
+        round_pair(N, 0, k, p, q);
+        if (q < n) {
+            abc[3 * k] = G[(long)p * ldg + p];
+            abc[3 * k + 1] = G[(long)q * ldg + q];
+            abc[3 * k + 2] = 0.5 * (G[(long)p * ldg + q] + G[(long)q * ldg + p]);
+        } else {
+            abc[3 * k] = abc[3 * k + 1] = abc[3 * k + 2] = 0.0;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(JT)
-jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double* lam_out,
-              int* ctrl, int* status, double tol_rel, double tol_abs_rel) {
+jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double* abc0,
+              double* abc1, double* lam_out, int* ctrl, int* status, double tol_rel,
+              double tol_abs_rel) {
     extern __shared__ double sm[];
     const int npairs = N / 2;
+    // pairs this CTA owns: k = blockIdx.x + i * gridDim.x < npairs
+    const int mine = max(0, (npairs - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
     double* cs = sm;
     double* sn = cs + npairs;
-    double* rp = sn + npairs;
-    double* rq = rp + n;
+    double* rows = sn + npairs;  // 2 * ppc rows of n
     __shared__ int s_cnt;
     __shared__ int s_done;
+    __shared__ double s_dmax;
 
     double* cur = g0;
     double* nxt = g1;
-    // absolute skip threshold relative to the largest diagonal entry: keeps
-    // rounding noise in a numerically null block from being chased forever
-    __shared__ double s_dmax;
+    double* abc_cur = abc0;
+    double* abc_nxt = abc1;
     if (threadIdx.x == 0) {
         double dm = 0.0;
         for (int i = 0; i < n; ++i) dm = fmax(dm, fabs(__ldcg(g0 + (long)i * ld + i)));
@@ -122,16 +168,16 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
         for (int r = 0; r < N - 1; ++r) {
-            // 1. every CTA computes all rotation angles of this round
+            const int rn = (r + 1 == N - 1) ? 0 : r + 1;  // next round (wraps to the next sweep)
+            // 1. all rotation angles of this round from the compact entries
             for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
                 int p, q;
                 round_pair(N, r, k, p, q);
                 double c = 1.0, s = 0.0;
                 if (q < n) {
-                    const double a = __ldcg(cur + (long)p * ld + p);
-                    const double b = __ldcg(cur + (long)q * ld + q);
-                    const double o =
-                        0.5 * (__ldcg(cur + (long)p * ld + q) + __ldcg(cur + (long)q * ld + p));
+                    const double a = __ldcg(abc_cur + 3 * k);
+                    const double b = __ldcg(abc_cur + 3 * k + 1);
+                    const double o = __ldcg(abc_cur + 3 * k + 2);
                     const double ao = fabs(o);
                     if (ao > tol_abs && ao > tol_rel * sqrt(fabs(a) * fabs(b))) {
                         const double tau = (b - a) / (2.0 * o);
@@ -146,43 +192,78 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
                 sn[k] = s;
             }
             __syncthreads();
-            // 2. row-pair work items
-            for (int k = blockIdx.x; k < npairs; k += gridDim.x) {
+            // 2. load and left-rotate every owned row pair
+            for (int i = 0; i < mine; ++i) {
+                const int k = blockIdx.x + i * gridDim.x;
                 int p, q;
                 round_pair(N, r, k, p, q);
-                const bool hq = q < n;  // p < q always, so p < n whenever q < n
-                const bool hp = p < n;
+                const bool hp = p < n, hq = q < n;
                 const double c = cs[k], s = sn[k];
+                double* rp = rows + (2 * i) * n;
+                double* rq = rp + n;
                 for (int j = threadIdx.x; j < n; j += blockDim.x) {
                     const double xp = hp ? __ldcg(cur + (long)p * ld + j) : 0.0;
                     const double xq = hq ? __ldcg(cur + (long)q * ld + j) : 0.0;
                     rp[j] = c * xp - s * xq;
                     rq[j] = s * xp + c * xq;
                 }
-                __syncthreads();
-                for (int kk = threadIdx.x; kk < npairs; kk += blockDim.x) {
-                    int pp, qq;
-                    round_pair(N, r, kk, pp, qq);
-                    if (qq < n) {
-                        const double c2 = cs[kk], s2 = sn[kk];
-                        double a0 = rp[pp], b0 = rp[qq];
-                        rp[pp] = c2 * a0 - s2 * b0;
-                        rp[qq] = s2 * a0 + c2 * b0;
-                        a0 = rq[pp];
-                        b0 = rq[qq];
-                        rq[pp] = c2 * a0 - s2 * b0;
-                        rq[qq] = s2 * a0 + c2 * b0;
-                    }
+            }
+            __syncthreads();
+            // 3. right rotations of every column pair, on all owned rows
+            const int nrows = 2 * mine;
+            for (int t = threadIdx.x; t < npairs * nrows; t += blockDim.x) {
+                const int kk = t % npairs, row = t / npairs;
+                int pp, qq;
+                round_pair(N, r, kk, pp, qq);
+                if (qq < n) {
+                    const double c2 = cs[kk], s2 = sn[kk];
+                    double* rr = rows + row * n;
+                    const double a0 = rr[pp], b0 = rr[qq];
+                    rr[pp] = c2 * a0 - s2 * b0;
+                    rr[qq] = s2 * a0 + c2 * b0;
                 }
-                __syncthreads();
-                if (threadIdx.x == 0 && hq && s != 0.0) {
-                    rp[q] = 0.0;
-                    rq[p] = 0.0;
+            }
+            __syncthreads();
+            // 4. exact zeros for the rotated pairs
+            if (threadIdx.x < mine) {
+                const int i = threadIdx.x;
+                const int k = blockIdx.x + i * gridDim.x;
+                int p, q;
+                round_pair(N, r, k, p, q);
+                if (q < n && sn[k] != 0.0) {
+                    rows[(2 * i) * n + q] = 0.0;
+                    rows[(2 * i + 1) * n + p] = 0.0;
                 }
-                __syncthreads();
+            }
+            __syncthreads();
+            // 5. store rows, publish next round's entries, rotate eigenvector rows
+            for (int i = 0; i < mine; ++i) {
+                const int k = blockIdx.x + i * gridDim.x;
+                int p, q;
+                round_pair(N, r, k, p, q);
+                const bool hp = p < n, hq = q < n;
+                const double c = cs[k], s = sn[k];
+                const double* rp = rows + (2 * i) * n;
+                const double* rq = rp + n;
                 for (int j = threadIdx.x; j < n; j += blockDim.x) {
                     if (hp) __stcg(nxt + (long)p * ld + j, rp[j]);
                     if (hq) __stcg(nxt + (long)q * ld + j, rq[j]);
+                }
+                if (threadIdx.x < 2) {
+                    const int x = threadIdx.x == 0 ? p : q;
+                    const double* rx = threadIdx.x == 0 ? rp : rq;
+                    if (x < n) {
+                        int k2, partner;
+                        pair_of(N, rn, x, k2, partner);
+                        if (partner < n) {
+                            if (x < partner) {
+                                __stcg(abc_nxt + 3 * k2, rx[x]);
+                                __stcg(abc_nxt + 3 * k2 + 2, rx[partner]);
+                            } else {
+                                __stcg(abc_nxt + 3 * k2 + 1, rx[x]);
+                            }
+                        }
+                    }
                 }
                 if (hq && s != 0.0) {
                     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -192,13 +273,15 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
                         __stcg(vt + (long)q * ld + j, s * vp + c * vq);
                     }
                 }
-                __syncthreads();
             }
             if (r == N - 2 && threadIdx.x == 0) atomicAdd(ctrl + 4 + sweep, s_cnt);
             if (!grid_barrier(ctrl, status, gridDim.x)) return;
             double* t = cur;
             cur = nxt;
             nxt = t;
+            t = abc_cur;
+            abc_cur = abc_nxt;
+            abc_nxt = t;
         }
         if (threadIdx.x == 0) s_done = (atomicAdd(ctrl + 4 + sweep, 0) == 0);
         __syncthreads();
@@ -245,11 +328,106 @@ __global__ void trivial_eig_kernel(const double* G, double* lam, double* Vt, int
     if (sweeps) *sweeps = 0;
 }
 
+// ------------------------------------------------------------ pivoted Cholesky
+// Left-looking: W[k][j] = (G[p][j] - sum_{m<k} Wc[p][m] Wc[j][m]) / sqrt(d_p) with
+// p = argmax of the remaining diagonal d.  W (n x n rows used: k < rank,
+// row-major) and its transpose Wc (n x n, Wc[j][m] = W[m][j]) are both written
+// so every dot product reads contiguous memory.  d[j] < 0 marks pivoted columns.
+__global__ void __launch_bounds__(JT)
+pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* Wc, double* d,
+             int* ctrl, int* status, double floor_rel) {
+    extern __shared__ double sm[];
+    double* colp = sm;  // Wc[p][0..k)
+    __shared__ double s_val[JT];
+    __shared__ int s_idx[JT];
+    __shared__ double s_dmax0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // every CTA reads the initial diagonal (G is an input and is not written)
+    double dm = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) dm = fmax(dm, G[(long)j * ldg + j]);
+    s_val[threadIdx.x] = dm;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_val[threadIdx.x] = fmax(s_val[threadIdx.x], s_val[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_dmax0 = s_val[0];
+    __syncthreads();
+    const double floor_abs = floor_rel * s_dmax0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        __stcg(d + j, G[(long)j * ldg + j]);
+    if (!grid_barrier(ctrl, status, gridDim.x)) return;
+    int k = 0;
+    for (; k < n; ++k) {
+        // argmax of the remaining diagonal (identical in every CTA; ties -> lowest index)
+        double best = -1.0;
+        int bi = n;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double v = __ldcg(d + j);
+            if (v > best) {
+                best = v;
+                bi = j;
+            }
+        }
+        s_val[threadIdx.x] = best;
+        s_idx[threadIdx.x] = bi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                const double v2 = s_val[threadIdx.x + o];
+                const int i2 = s_idx[threadIdx.x + o];
+                if (v2 > s_val[threadIdx.x] || (v2 == s_val[threadIdx.x] && i2 < s_idx[threadIdx.x])) {
+                    s_val[threadIdx.x] = v2;
+                    s_idx[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        const double dp = s_val[0];
+        const int p = s_idx[0];
+        __syncthreads();
+        if (!(dp > floor_abs) || p >= n) break;
+        const double l = sqrt(dp);
+        for (int m = threadIdx.x; m < k; m += blockDim.x) colp[m] = __ldcg(Wc + (long)p * n + m);
+        __syncthreads();
+        // this CTA's columns j = blockIdx.x + c * gridDim.x, one warp per column
+        for (int j = blockIdx.x + warp * gridDim.x; j < n; j += nwarps * gridDim.x) {
+            const double dj = __ldcg(d + j);
+            double acc = 0.0;
+            if (dj >= 0.0 && j != p)
+                for (int m = lane; m < k; m += 32) acc += colp[m] * __ldcg(Wc + (long)j * n + m);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                double w;
+                if (j == p) {
+                    w = l;
+                    __stcg(d + j, -1.0);
+                } else if (dj < 0.0) {
+                    w = 0.0;
+                } else {
+                    w = (G[(long)p * ldg + j] - acc) / l;
+                    __stcg(d + j, dj - w * w);
+                }
+                __stcg(W + (long)k * n + j, w);
+                __stcg(Wc + (long)j * n + k, w);
+            }
+        }
+        if (!grid_barrier(ctrl, status, gridDim.x)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[3] = k;
+}
+
+__global__ void pchol_finish_kernel(const int* ctrl, int* kB_out) { *kB_out = ctrl[3]; }
+
 __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm1, int forced,
                                   int max_rank, double* delta2_dev, int* dec_i, double* dec_d) {
     const double eps_mach = 2.220446049250313e-16;
+    // totals and tails are summed from the small end; eigenvalues are not clamped
+    // at zero, so the symmetric rounding noise of the Gram eigenvalues cancels
     double total = 0.0;
-    for (int j = kB - 1; j >= 0; --j) total += fmax(lamK[j], 0.0);
+    for (int j = kB - 1; j >= 0; --j) total += lamK[j];
+    total = fmax(total, 0.0);
     double delta2 = *delta2_dev;
     if (delta2 < 0.0) {
         delta2 = eps * eps * total / (double)(dm1 > 0 ? dm1 : 1);
@@ -270,7 +448,7 @@ __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm
         double t = 0.0;
         int rstar = 0;
         for (int j = kB - 1; j >= 0; --j) {
-            const double tn = t + fmax(lamK[j], 0.0);
+            const double tn = t + lamK[j];
             if (tn > delta2) {
                 rstar = j + 1;
                 break;
@@ -285,11 +463,11 @@ __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm
         r = min(r, navail);
     }
     double tail = 0.0;
-    for (int j = kB - 1; j >= r && j >= 0; --j) tail += fmax(lamK[j], 0.0);
+    for (int j = kB - 1; j >= r && j >= 0; --j) tail += lamK[j];
     dec_i[0] = r;
     dec_i[1] = capped;
     dec_d[0] = delta2;
-    dec_d[1] = tail;
+    dec_d[1] = fmax(tail, 0.0);
     dec_d[2] = total;
 }
 
@@ -303,7 +481,27 @@ __global__ void count_floor_kernel(const double* lam, int n, int* out) {
     *out = cnt;
 }
 
-int g_coop_blocks = 0;  // co-resident CTAs of jacobi_kernel at the smem size last queried
+tt_status coop_blocks(const void* fn, size_t smem, int want, int* out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    TT_CUDA_TRY(cudaGetDevice(&dev));
+    TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, JT, smem));
+    if (per_sm < 1) {
+        set_error("persistent kernel cannot be resident with its shared memory");
+        return TT_ERR_CUDA;
+    }
+    *out = std::max(1, std::min(want, std::min(sms, per_sm * sms)));
+    return TT_OK;
+}
+
+tt_status ensure_ctrl(EigWork& w, cudaStream_t s) {
+    if (!w.d_ctrl) {
+        TT_CUDA_TRY(cudaMalloc(&w.d_ctrl, CTRL_INTS * sizeof(int)));
+        w.ctrl_cap = CTRL_INTS;
+    }
+    TT_CUDA_TRY(cudaMemsetAsync(w.d_ctrl, 0, CTRL_INTS * sizeof(int), s));
+    return TT_OK;
+}
 
 }  // namespace
 
@@ -312,6 +510,7 @@ void EigWork::release() {
     g1.release();
     lam_unsorted.release();
     vt_unsorted.release();
+    abc.release();
     if (d_ctrl) cudaFree(d_ctrl);
     d_ctrl = nullptr;
     ctrl_cap = 0;
@@ -331,60 +530,95 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
         return TT_OK;
     }
     const int N = n + (n & 1);
+    const int npairs = N / 2;
     const long ld = n;
     TT_TRY(w.g0.ensure((size_t)n * n, s));
     TT_TRY(w.g1.ensure((size_t)n * n, s));
     TT_TRY(w.vt_unsorted.ensure((size_t)n * n, s));
-    if (!w.d_ctrl) {
-        TT_CUDA_TRY(cudaMalloc(&w.d_ctrl, CTRL_INTS * sizeof(int)));
-        w.ctrl_cap = CTRL_INTS;
+    TT_TRY(w.lam_unsorted.ensure((size_t)n, s));
+    TT_TRY(w.abc.ensure((size_t)6 * npairs, s));
+    TT_TRY(ensure_ctrl(w, s));
+    // about three row pairs per CTA, never more than MAX_PAIRS_PER_CTA
+    int want = std::max(1, (npairs + 2) / 3);
+    want = std::max(want, (npairs + MAX_PAIRS_PER_CTA - 1) / MAX_PAIRS_PER_CTA);
+    size_t smem = (size_t)(npairs * 2 + 2 * MAX_PAIRS_PER_CTA * n) * sizeof(double);
+    if (smem > 200 * 1024) {
+        // fall back to the pairs-per-CTA bound the shared memory allows
+        smem = (size_t)(npairs * 2 + 2 * ((npairs + want - 1) / want) * n) * sizeof(double);
     }
-    TT_CUDA_TRY(cudaMemsetAsync(w.d_ctrl, 0, CTRL_INTS * sizeof(int), s));
-    {
-        const long total = (long)n * n;
-        const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
-        note_launch();
-        jacobi_init_kernel<<<blocks, 256, 0, s>>>(n, G, ldg, w.g0.p, w.vt_unsorted.p, ld);
-        TT_CUDA_TRY(cudaGetLastError());
-    }
-    const size_t smem = (size_t)(N + 2 * n) * sizeof(double);
     if (smem > 200 * 1024) {
         set_error("syev: matrix too large for the shared-memory row buffers");
         return TT_ERR_TOO_LARGE;
     }
     TT_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
-    TT_CUDA_TRY(cudaGetDevice(&dev));
-    TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    TT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JT, smem));
-    if (per_sm < 1) {
-        set_error("syev: jacobi kernel cannot be resident");
-        return TT_ERR_CUDA;
+    int blocks = 1;
+    TT_TRY(coop_blocks((const void*)jacobi_kernel, smem, want, &blocks));
+    const int ppc = (npairs + blocks - 1) / blocks;
+    if (ppc > MAX_PAIRS_PER_CTA ||
+        (size_t)(npairs * 2 + 2 * ppc * n) * sizeof(double) > smem) {
+        set_error("syev: too few resident CTAs for this matrix size");
+        return TT_ERR_TOO_LARGE;
     }
-    g_coop_blocks = per_sm * sms;
-    // about two row-pair items per CTA; one CTA for small matrices
-    int blocks = std::max(1, std::min(N / 4, sms));
-    blocks = std::min(blocks, g_coop_blocks);
+    {
+        const long total = (long)n * n;
+        const int ib = (int)std::min<long>((total + 255) / 256, 152L * 16);
+        note_launch();
+        jacobi_init_kernel<<<ib, 256, 0, s>>>(n, N, G, ldg, w.g0.p, w.vt_unsorted.p, ld, w.abc.p);
+        TT_CUDA_TRY(cudaGetLastError());
+    }
     double* g0 = w.g0.p;
     double* g1 = w.g1.p;
     double* vt = w.vt_unsorted.p;
-    int* ctrl = w.d_ctrl;
-    TT_TRY(w.lam_unsorted.ensure((size_t)n, s));
+    double* abc0 = w.abc.p;
+    double* abc1 = w.abc.p + 3 * npairs;
     double* lamu = w.lam_unsorted.p;
+    int* ctrl = w.d_ctrl;
     // relative skip test as in high-relative-accuracy Jacobi; the absolute one
     // (1e-24 of the largest diagonal entry) is far below the Gram floor
     // n eps_mach lambda_max that the rounding applies afterwards
     double tol_rel = 1e-15, tol_abs_rel = 1e-24;
     int nn = n, NN = N;
     long ldl = ld;
-    void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &lamu, &ctrl, &status_dev, &tol_rel, &tol_abs_rel};
+    void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &abc0, &abc1, &lamu, &ctrl, &status_dev, &tol_rel, &tol_abs_rel};
     note_launch();
     TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(JT), args,
                                             smem, s));
     note_launch();
     jacobi_sort_kernel<<<n, 256, 0, s>>>(n, w.lam_unsorted.p, ld, w.vt_unsorted.p, lam, Vt, ldv,
                                          sweeps_dev, w.d_ctrl);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, double* Wc,
+                double* dwork, EigWork& w, int* status_dev, int* kB_dev) {
+    if (n <= 0) return TT_OK;
+    TT_TRY(ensure_ctrl(w, s));
+    const size_t smem = (size_t)n * sizeof(double);
+    if (smem > 200 * 1024) {
+        set_error("pchol: matrix too large");
+        return TT_ERR_TOO_LARGE;
+    }
+    TT_CUDA_TRY(cudaFuncSetAttribute(pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int blocks = 1;
+    // about eight columns per CTA (one warp each)
+    TT_TRY(coop_blocks((const void*)pchol_kernel, smem, std::max(1, (n + 7) / 8), &blocks));
+    int nn = n;
+    long ldgl = ldg;
+    const double* Gp = G;
+    int* ctrl = w.d_ctrl;
+    // stop at the rounding-noise level of G's entries (eps_mach max diag): a
+    // higher floor (n eps_mach, LAPACK's default for pivoted Cholesky) drops
+    // parts of G_B that still carry tensor components at the 1e-9 level
+    double fr = 2.220446049250313e-16;
+    void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr};
+    note_launch();
+    TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)pchol_kernel, dim3(blocks), dim3(JT), args,
+                                            smem, s));
+    note_launch();
+    pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
 }
