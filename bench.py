@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--workload", default="blob_3d", choices=["blob_3d", "small_2d"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form companion run")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle stepping for --impl reference")
@@ -177,6 +178,37 @@ def run_ours(args, rank, world, local_rank):
         g.profile(False)
         E, T, tot = g.energy()
 
+        # precision form on the same steps, replaying the FP64 run's ranks
+        mixed = None
+        if not args.no_mixed:
+            E64, T64 = E.clone(), T.clone()
+            gm = ttsn.TTSN.from_problem(p, max_rank=p.get("max_rank", 0), stream=stream,
+                                        precision=ttsn.TT_MIXED)
+            for _ in range(args.warmup):
+                gm.step()
+            gm.set_cores(init_cores)
+            gm.set_T(T0)
+            bf16_peak = ttsn.bf16_mma_peak(stream) if rank == 0 else None
+            torch.cuda.synchronize()
+            gm.profile(True)
+            evm = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            torch.cuda.synchronize()
+            evm[0].record(stream)
+            for k in range(args.steps):
+                gm.step(forced=ranks_hist[k])
+                evm[k + 1].record(stream)
+            torch.cuda.synchronize()
+            mx_ms = evm[0].elapsed_time(evm[args.steps])
+            mprof = gm.profile_read()
+            gm.profile(False)
+            Em, Tm, _ = gm.energy()
+            err_E = ((Em - E64).abs().max() / E64.abs().max()).item()
+            err_T = ((Tm - T64).abs().max() / T64.abs().max()).item()
+            mixed = dict(total_ms=mx_ms, step_ms=[evm[k].elapsed_time(evm[k + 1]) for k in range(args.steps)],
+                         prof=mprof, err_E=err_E, err_T=err_T, bf16_peak=bf16_peak)
+            del gm
+            torch.cuda.synchronize()
+
         # end to end through the public API: the state lives on the host between
         # steps (pinned), copied in before and out after every step
         e2e = None
@@ -201,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
             e2e = {"value": args.steps / e2e_s, "unit": "steps/s",
                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
-               clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p)
+               clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed)
     return res
 
 
@@ -372,6 +404,28 @@ def main():
         "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"],
         "roofline": roof, "phases": prof_out,
     }
+    mx = res["mixed"]
+    if mx is not None:
+        mv = world * steps / (mx["total_ms"] * 1e-3)
+        gl = mx["prof"]["gram_left"]
+        mroof = None
+        if gl["ms"] > 0 and mx["bf16_peak"]:
+            # executed BF16 MMA flops ~ 21 digit products x the algorithmic count
+            ex = 21.0 * gl["flops"] / (gl["ms"] * 1e-3) / 1e12
+            mroof = {"bound": "tensor", "kernel": "gram_left (slgram_kernel)", "dtype": "bf16 digits",
+                     "achieved": ex, "peak": mx["bf16_peak"], "unit": "TFLOP/s",
+                     "frac": ex / mx["bf16_peak"],
+                     "fp64_equivalent_tflops": gl["flops"] / (gl["ms"] * 1e-3) / 1e12,
+                     "peak_source": "measured mma.sync m16n8k16 bf16 chains (tt_bench_bf16_mma)"}
+        line["mixed"] = {
+            "value": mv, "unit": "steps/s", "speedup_vs_fp64": mv / value,
+            "updates_per_s": mv * cells_ordinates(p),
+            "ranks": "replayed from the FP64 run (forced), steps 1..%d" % steps,
+            "err_vs_fp64": {"E_max_rel": mx["err_E"], "T_max_rel": mx["err_T"]},
+            "dtype": "bf16 exact-split digits + fp32/double-float accumulation; fp64 eigensolves, decisions, T",
+            "step_ms": [round(x, 3) for x in mx["step_ms"]],
+            "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in mx["prof"].items()},
+            "roofline": mroof}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

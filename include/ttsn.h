@@ -47,7 +47,7 @@ typedef enum {
 } tt_status;
 
 enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1 };
-enum { TT_FP64 = 0 };
+enum { TT_FP64 = 0, TT_MIXED = 1 };
 
 /* step flags for tt_sn_step_ex */
 enum {
@@ -74,7 +74,11 @@ enum {
  * Rounding (Sec. 4.2, App. A): relative Frobenius tolerance eps balanced over
  * the bonds, ranks capped at max_rank (<= 0: no cap); rounds_per_step = 1
  * rounds once after the source stage, 2 also rounds after transport.
- * precision: TT_FP64.
+ * precision: TT_FP64, or TT_MIXED for the precision form: the left Gram
+ * matrices and the core updates A' = A P_A (the dominant contractions of
+ * App. A.4) run on the BF16 tensor pipe with exact split products
+ * (tt_gram_mixed); right Grams, eigensolves, rank decisions, the quartic and
+ * the temperature update stay FP64.
  * The intensity is held in the paper's three-core layout (Eq. tensor_decomp):
  * X (1, N_c, r1), Theta (r1, n_theta, r2), Phi (r2, n_phi, 1).
  */
@@ -183,6 +187,9 @@ tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len);
  */
 tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* ranks_host);
 
+/* tt_set_precision: TT_FP64 or TT_MIXED for the following roundings. */
+tt_status tt_set_precision(tt_handle h, int precision);
+
 /* tt_set_T: replace the material temperature (N_c doubles, device). */
 tt_status tt_set_T(tt_handle h, const double* T_dev);
 
@@ -229,6 +236,25 @@ tt_status tt_gram(int m, int n, const double* A_dev, int lda, double* G_dev, int
  */
 tt_status tt_syev(int n, const double* G_dev, int ldg, double* lam_dev, double* Vt_dev, int ldv,
                   void* stream, int* sweeps_host);
+
+/*
+ * tt_gram_mixed: G = A^T A (as tt_gram) on the BF16 tensor pipe.  Each column
+ * of A is scaled by a power of two and cut into six signed 8-bit digits (exact
+ * in BF16); digit products are exact in FP32, summed exactly over 32-row
+ * blocks, and accumulated in double-float (about 48 bits); products of digit
+ * levels s + t >= 6 are dropped.  Error about 2^-48 max|A_j| max|A_k| per row
+ * term.  Device scratch (row splits x n x n doubles) is allocated per call.
+ */
+tt_status tt_gram_mixed(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg,
+                        void* stream);
+
+/*
+ * tt_gemm_nt_mixed: C = A B^T (A: M x K, B: N x K, C: M x N, row-major) with the
+ * same exact split products, each row of A and of B scaled by its own power of
+ * two (error about 2^-48 max_k|A_ik| max_k|B_jk| per term).
+ */
+tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A_dev, int lda, const double* B_dev,
+                           int ldb, double* C_dev, int ldc, void* stream);
 
 /*
  * tt_gram_noalloc: the same G = A^T A as tt_gram, for callers that must not
@@ -293,6 +319,13 @@ unsigned long long tt_kernel_launches(void);
  * chains of mma.m8n8k4.f64 on every SM) in TFLOP/s, written to tflops_host.
  */
 tt_status tt_bench_fp64_mma(double* tflops_host, void* stream);
+
+/*
+ * tt_bench_bf16_mma: measured throughput of warp-level BF16 tensor MMA
+ * (dependent chains of mma.sync m16n8k16 with FP32 accumulation on every SM),
+ * the instruction the mixed contractions use, in TFLOP/s.
+ */
+tt_status tt_bench_bf16_mma(double* tflops_host, void* stream);
 
 #ifdef __cplusplus
 }

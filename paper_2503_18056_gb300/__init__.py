@@ -12,11 +12,12 @@ import ctypes
 import torch
 
 from . import _native
-from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE,
-                      TTError, StepInfo, check, lib)
+from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_MIXED, TT_STEP_NO_ROUND,
+                      TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TensorTrain", "dgemm", "gram", "syev", "TTError", "TT_BC_PERIODIC",
-           "TT_BC_VACUUM", "TT_STEP_NO_SOURCE", "TT_STEP_NO_ROUND"]
+__all__ = ["TTSN", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev",
+           "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
+           "TT_STEP_NO_ROUND"]
 
 
 def _stream_ptr(stream=None):
@@ -93,6 +94,9 @@ class _Handle:
     def sync(self):
         check(lib.tt_sync(self._h))
 
+    def set_precision(self, precision):
+        check(lib.tt_set_precision(self._h, int(precision)))
+
     def profile(self, enable=True):
         check(lib.tt_profile(self._h, int(bool(enable))))
 
@@ -132,7 +136,7 @@ class TTSN(_Handle):
 
     def __init__(self, n, L, n_theta, n_phi, sigma_a, cv, T0, Tr0=None, sigma_s=None, c=1.0,
                  a_r=1.0, dt=0.0, cfl=0.5, bc=TT_BC_PERIODIC, eps=1e-6, max_rank=0,
-                 rounds_per_step=1, stream=None):
+                 rounds_per_step=1, precision=TT_FP64, stream=None):
         super().__init__()
         ndim = len(n)
         nc = 1
@@ -158,7 +162,7 @@ class TTSN(_Handle):
         for key in ("sigma_a", "cv", "T0", "Tr0", "sigma_s"):
             setattr(desc, key, f[key].data_ptr() if f[key] is not None else None)
         desc.eps, desc.max_rank = float(eps), int(max_rank or 0)
-        desc.rounds_per_step, desc.precision = int(rounds_per_step), 0
+        desc.rounds_per_step, desc.precision = int(rounds_per_step), int(precision)
         check(lib.tt_create(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(self._h)))
         self._keep = f  # inputs stay alive until creation finished (copied in)
 
@@ -216,6 +220,27 @@ def gram(A, stream=None):
     return G
 
 
+def gram_mixed(A, stream=None):
+    """G = A^T A with exact BF16 digit products (library kernel, tt_gram_mixed)."""
+    A = _dev(A)
+    m, n = A.shape
+    G = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    check(lib.tt_gram_mixed(m, n, ctypes.c_void_p(A.data_ptr()), n, ctypes.c_void_p(G.data_ptr()), n,
+                            _stream_ptr(stream)))
+    return G
+
+
+def gemm_nt_mixed(A, B, stream=None):
+    """C = A B^T with exact BF16 digit products (library kernel, tt_gemm_nt_mixed)."""
+    A, B = _dev(A), _dev(B)
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    check(lib.tt_gemm_nt_mixed(M, N, K, ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(B.data_ptr()),
+                               K, ctypes.c_void_p(C.data_ptr()), N, _stream_ptr(stream)))
+    return C
+
+
 def gram_noalloc(A, G=None, stream=None):
     """G = A^T A through tt_gram_noalloc: the library allocates nothing (the
     caller provides A and, optionally, the output G; n <= 1024)."""
@@ -251,4 +276,11 @@ def fp64_mma_peak(stream=None):
     """Measured FP64 tensor-pipe throughput of this GPU in TFLOP/s."""
     v = ctypes.c_double()
     check(lib.tt_bench_fp64_mma(ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
+
+
+def bf16_mma_peak(stream=None):
+    """Measured warp-level BF16 tensor MMA (mma.sync) throughput in TFLOP/s."""
+    v = ctypes.c_double()
+    check(lib.tt_bench_bf16_mma(ctypes.byref(v), _stream_ptr(stream)))
     return v.value

@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "TT_OK", 1: "TT_WARN_RANK_CAPPED", -1: "TT_ERR_ARG", -2: "TT_
                 -3: "TT_ERR_CUDA", -4: "TT_ERR_NOT_CONVERGED", -5: "TT_ERR_TIMEOUT",
                 -6: "TT_ERR_STATE", -7: "TT_ERR_TOO_LARGE"}
 TT_BC_PERIODIC, TT_BC_VACUUM = 0, 1
+TT_FP64, TT_MIXED = 0, 1
 TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
 
 
@@ -76,11 +77,15 @@ def _load():
         "tt_dgemm": [i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp],
         "tt_gram": [i, i, vp, i, vp, i, vp],
         "tt_gram_noalloc": [i, i, vp, i, vp, i, vp],
+        "tt_gram_mixed": [i, i, vp, i, vp, i, vp],
+        "tt_gemm_nt_mixed": [i, i, i, vp, i, vp, i, vp, i, vp],
+        "tt_set_precision": [vp, i],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_longlong), dp, dp],
         "tt_bench_fp64_mma": [dp, vp],
+        "tt_bench_bf16_mma": [dp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -101,7 +106,9 @@ lib = _load()
 EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_round", "tt_energy",
             "tt_to_full", "tt_get_ranks", "tt_get_dims", "tt_get_core", "tt_set_cores",
             "tt_set_T", "tt_sync", "tt_last_error", "tt_destroy", "tt_dgemm", "tt_gram",
-            "tt_syev", "tt_gram_noalloc", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma"]
+            "tt_syev", "tt_gram_noalloc", "tt_gram_mixed", "tt_gemm_nt_mixed",
+            "tt_set_precision", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma",
+            "tt_bench_bf16_mma"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

@@ -91,7 +91,8 @@ struct tt_ctx {
 
     // rounding workspace
     DevBuf GB[TT_MAX_D], lamB[TT_MAX_D], VtB[TT_MAX_D];
-    DevBuf GA, Wc, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd;
+    DevBuf GA, Wc, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd, slscratch;
+    int precision = TT_FP64;
     EigWork eig;
     int* d_int = nullptr;      // device ints (HI_* layout)
     double* d_dbl = nullptr;   // device doubles (HD_* layout)
@@ -151,7 +152,7 @@ struct tt_ctx {
             lamB[k].release();
             VtB[k].release();
         }
-        DevBuf* bufs[] = {&GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
+        DevBuf* bufs[] = {&slscratch, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf};
         for (DevBuf* b : bufs) b->release();
@@ -335,7 +336,10 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         TT_TRY(h->GA.ensure((size_t)Rk * Rk, s));
         {
             PhaseScope ps(h, TT_PH_GRAM_LEFT, (double)m * Rk * (Rk + 1.0), 8.0 * ((double)m * Rk + (double)Rk * Rk));
-            TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
+            if (h->precision == TT_MIXED)
+                TT_TRY(slgram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
+            else
+                TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
         }
         {
             PhaseScope ps(h, TT_PH_SMALL, 2.0 * Rk * (double)Rk * kB + 2.0 * kB * (double)kB * Rk, 0.0);
@@ -386,7 +390,10 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         TT_TRY(dst[k].ensure((size_t)m * rk, s));
         {
             PhaseScope ps(h, TT_PH_UPDATE, 2.0 * m * (double)Rk * rk, 8.0 * ((double)m * Rk + (double)m * rk));
-            TT_TRY(dgemm(s, false, true, (int)m, rk, Rk, 1.0, A, Rk, h->PAt.p, Rk, 0.0, dst[k].p, rk));
+            if (h->precision == TT_MIXED)
+                TT_TRY(slgemm_nt(s, m, rk, Rk, A, Rk, h->PAt.p, Rk, dst[k].p, rk, h->slscratch));
+            else
+                TT_TRY(dgemm(s, false, true, (int)m, rk, Rk, 1.0, A, Rk, h->PAt.p, Rk, 0.0, dst[k].p, rk));
         }
         // next core = M_upd x_1 G_{k+1}
         double* next;
@@ -542,7 +549,8 @@ tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
     if (D.eps < 0.0) return fail(TT_ERR_ARG, "tt_create: eps must be >= 0");
     if (D.rounds_per_step != 1 && D.rounds_per_step != 2)
         return fail(TT_ERR_ARG, "tt_create: rounds_per_step must be 1 or 2");
-    if (D.precision != TT_FP64) return fail(TT_ERR_ARG, "tt_create: precision must be TT_FP64");
+    if (D.precision != TT_FP64 && D.precision != TT_MIXED)
+        return fail(TT_ERR_ARG, "tt_create: precision must be TT_FP64 or TT_MIXED");
 
     tt_ctx* h = new tt_ctx();
     cudaStream_t s = (cudaStream_t)stream;
@@ -560,6 +568,7 @@ tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
     h->eps = D.eps;
     h->max_rank = D.max_rank > 0 ? D.max_rank : 0;
     h->rounds = D.rounds_per_step;
+    h->precision = D.precision;
     Grid& g = h->grid;
     g.ndim = D.ndim;
     g.nc = nc;
@@ -863,6 +872,15 @@ tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* r
     return TT_OK;
 }
 
+tt_status tt_set_precision(tt_handle h, int precision) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (precision != TT_FP64 && precision != TT_MIXED)
+        return fail(TT_ERR_ARG, "tt_set_precision: precision must be TT_FP64 or TT_MIXED");
+    h->precision = precision;
+    return TT_OK;
+}
+
 tt_status tt_set_T(tt_handle h, const double* T_dev) {
     set_error("");
     TT_TRY(check_handle(h, true));
@@ -900,6 +918,37 @@ tt_status tt_gram(int m, int n, const double* A, int lda, double* G, int ldg, vo
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf scratch;
     tt_status st = gram(s, m, n, A, lda, G, ldg, scratch);
+    if (scratch.p) cudaFreeAsync(scratch.p, s);
+    if (st < 0) return st;
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status tt_gram_mixed(int m, int n, const double* A, int lda, double* G, int ldg, void* stream) {
+    set_error("");
+    if (m < 0 || n < 0) return fail(TT_ERR_ARG, "tt_gram_mixed: negative size");
+    if (n == 0) return TT_OK;
+    if (!A || !G) return fail(TT_ERR_ARG, "tt_gram_mixed: null pointer");
+    if (lda < n || ldg < n) return fail(TT_ERR_ARG, "tt_gram_mixed: leading dimension smaller than n");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf scratch;
+    tt_status st = slgram(s, m, n, A, lda, G, ldg, scratch);
+    if (scratch.p) cudaFreeAsync(scratch.p, s);
+    if (st < 0) return st;
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                           double* C, int ldc, void* stream) {
+    set_error("");
+    if (M < 0 || N < 0 || K < 0) return fail(TT_ERR_ARG, "tt_gemm_nt_mixed: negative size");
+    if (M == 0 || N == 0) return TT_OK;
+    if (!A || !B || !C) return fail(TT_ERR_ARG, "tt_gemm_nt_mixed: null pointer");
+    if (lda < K || ldb < K || ldc < N) return fail(TT_ERR_ARG, "tt_gemm_nt_mixed: leading dimension too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf scratch;
+    tt_status st = slgemm_nt(s, M, N, K, A, lda, B, ldb, C, ldc, scratch);
     if (scratch.p) cudaFreeAsync(scratch.p, s);
     if (st < 0) return st;
     TT_CUDA_TRY(cudaGetLastError());
@@ -965,6 +1014,12 @@ tt_status tt_bench_fp64_mma(double* tflops_host, void* stream) {
     set_error("");
     if (!tflops_host) return fail(TT_ERR_ARG, "tt_bench_fp64_mma: null output");
     return bench_fp64_mma((cudaStream_t)stream, tflops_host);
+}
+
+tt_status tt_bench_bf16_mma(double* tflops_host, void* stream) {
+    set_error("");
+    if (!tflops_host) return fail(TT_ERR_ARG, "tt_bench_bf16_mma: null output");
+    return bench_bf16_mma((cudaStream_t)stream, tflops_host);
 }
 
 }  // extern "C"

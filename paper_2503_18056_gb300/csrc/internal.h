@@ -69,6 +69,16 @@ tt_status gram_fixed_scratch(cudaStream_t s, int m, int n, const double* A, long
                              long ldg, double* scratch, size_t scratch_doubles);
 // Measured FP64 tensor-pipe throughput (TFLOP/s).
 tt_status bench_fp64_mma(cudaStream_t s, double* tflops);
+// Measured BF16 mma.sync (m16n8k16, FP32 accumulate) throughput (TFLOP/s).
+tt_status bench_bf16_mma(cudaStream_t s, double* tflops);
+
+// Mixed-precision (exact BF16 digit products, double-float accumulation) left
+// Gram G = A^T A and product C = A B^T (slice.cu).  scratch grows as needed.
+size_t slgram_scratch_doubles(int m, int n);
+tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
+                 DevBuf& scratch);
+tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
+                    long ldb, double* C, long ldc, DevBuf& scratch);
 
 // Row scaling: out[i][j] = in[i][j] * f(v[i]) for i < rows, j < cols, where
 // mode 0: v, 1: sqrt(v), 2: 1/sqrt(v), 3: 1/v.  out may alias in.
