@@ -19,9 +19,11 @@
 // the inner loop (GB300's FP64 pipe is ~1/70 of its FP32 pipe).
 //
 // Tiles: 64 x 64 outputs per CTA, four warps of 32 x 32, mma.sync m16n8k16
-// bf16 with FP32 accumulators.  Digits are produced on the fly from FP64 tiles
-// into shared memory ([S][64][40] per operand, K-contiguous, conflict-free
-// fragment loads).
+// bf16 with FP32 accumulators, shared-memory digit tiles [S][64][40] per
+// operand (K-contiguous, conflict-free fragment loads).  The Gram slices each
+// column once into digit planes in global memory and streams them with a
+// two-stage cp.async pipeline; the update GEMM produces digits on the fly
+// (its B operand is small and its A tile is read by few CTAs).
 #include <algorithm>
 
 #include "internal.h"
@@ -202,72 +204,6 @@ __device__ __forceinline__ void block_products(const SlTiles& TA, const SlTiles&
     }
 }
 
-// Gram: grid (T, T, ksplit) over upper tiles; partial[z] = this split's G tile.
-__global__ void __launch_bounds__(SL_THREADS)
-slgram_kernel(int m, int n, const double* __restrict__ A, long lda, const int* __restrict__ ecol,
-              int ksplit, int kchunk, double* __restrict__ partial) {
-    const int tn = blockIdx.x, tm = blockIdx.y, ks = blockIdx.z;
-    if (tn < tm) return;
-    extern __shared__ unsigned char smraw[];
-    SlTiles& TJ = *reinterpret_cast<SlTiles*>(smraw);
-    SlTiles& TK = *reinterpret_cast<SlTiles*>(smraw + sizeof(SlTiles));
-    const bool diag = (tn == tm);
-    const int J0 = tm * SL_BM, K0 = tn * SL_BN;
-    const int kbeg = ks * kchunk, kend = min(m, kbeg + kchunk);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float hi[2][4][4], lo[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) hi[a][b][c] = lo[a][b][c] = 0.f;
-    for (int k0 = kbeg; k0 < kend; k0 += SL_BK) {
-        // element (row i, column j): coalesced along j; written transposed [j][i]
-#pragma unroll 4
-        for (int it = 0; it < (SL_BK * SL_BM) / SL_THREADS; ++it) {
-            const int idx = tid + it * SL_THREADS;
-            const int j = idx % SL_BM, i = idx / SL_BM;
-            const int gi = k0 + i;
-            unsigned short dj[SL_S], dk[SL_S];
-            {
-                const int gj = J0 + j;
-                const double v = (gi < kend && gj < n) ? A[(long)gi * lda + gj] : 0.0;
-                digits(v, gj < n ? ecol[gj] : 0, dj);
-            }
-#pragma unroll
-            for (int s = 0; s < SL_S; ++s) TJ.d[s][j][i] = dj[s];
-            if (!diag) {
-                const int gk = K0 + j;
-                const double v = (gi < kend && gk < n) ? A[(long)gi * lda + gk] : 0.0;
-                digits(v, gk < n ? ecol[gk] : 0, dk);
-#pragma unroll
-                for (int s = 0; s < SL_S; ++s) TK.d[s][j][i] = dk[s];
-            }
-        }
-        __syncthreads();
-        block_products(TJ, diag ? TJ : TK, wm, wn, lane, hi, lo);
-        __syncthreads();
-    }
-    // epilogue: G_jk = 2^(e_j + e_k) 256^-2 (hi + lo)
-    double* out = partial + (long)ks * n * n;
-    const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int j = J0 + wm + mi * 16 + g + (c >= 2 ? 8 : 0);
-                const int k = K0 + wn + ni * 8 + t4 * 2 + (c & 1);
-                if (j < n && k < n) {
-                    const double v = (double)hi[mi][ni][c] + (double)lo[mi][ni][c];
-                    out[(long)j * n + k] = ldexp(v, ecol[j] + ecol[k] - 16);
-                }
-            }
-}
-
 // C (M x N) = A (M x K) B^T (B: N x K); both row-major FP64 with per-row exponents.
 __global__ void __launch_bounds__(SL_THREADS)
 slgemm_nt_kernel(int M, int N, int K, const double* __restrict__ A, long lda,
@@ -327,6 +263,119 @@ slgemm_nt_kernel(int M, int N, int K, const double* __restrict__ A, long lda,
             }
 }
 
+// Digit planes of the column-scaled operand: D[s][j][i] (n x mp, i contiguous),
+// rows i >= m padded with zero digits.  A CTA slices a 32 (i) x 64 (j) block,
+// coalesced along j on the FP64 read, and writes 64-byte runs along i through
+// a shared-memory transpose.
+__global__ void __launch_bounds__(256)
+slice_cols_kernel(int m, int n, long mp, const double* __restrict__ A, long lda,
+                  const int* __restrict__ ecol, unsigned short* __restrict__ D) {
+    __shared__ unsigned short t[SL_S][64][34];
+    const int j0 = blockIdx.x * 64;
+    for (long ib = blockIdx.y; ib < mp / 32; ib += gridDim.y) {
+    const long i0 = ib * 32;
+    __syncthreads();  // previous block's transpose reads are done
+    for (int idx = threadIdx.x; idx < 32 * 64; idx += blockDim.x) {
+        const int j = idx % 64, i = idx / 64;
+        const long gi = i0 + i;
+        const int gj = j0 + j;
+        const double v = (gi < m && gj < n) ? A[gi * lda + gj] : 0.0;
+        unsigned short d[SL_S];
+        digits(v, gj < n ? ecol[gj] : 0, d);
+#pragma unroll
+        for (int s = 0; s < SL_S; ++s) t[s][j][i] = d[s];
+    }
+    __syncthreads();
+    // write: for each (s, j), 32 consecutive i as 16 words of 2 digits
+    for (int idx = threadIdx.x; idx < SL_S * 64 * 16; idx += blockDim.x) {
+        const int w = idx % 16, j = (idx / 16) % 64, s = idx / (16 * 64);
+        const int gj = j0 + j;
+        if (gj >= n) continue;
+        const unsigned v = (unsigned)t[s][j][2 * w] | ((unsigned)t[s][j][2 * w + 1] << 16);
+        unsigned* dst = reinterpret_cast<unsigned*>(D + ((long)s * n + gj) * mp + i0) + w;
+        *dst = v;
+    }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+// Gram from digit planes: grid (T, T, ksplit) over upper tiles, 32-row blocks
+// streamed with a two-stage cp.async pipeline.  Stage layout: [2 operands]
+// SlTiles (64 x 40 bf16 rows, 16-byte aligned: 80-byte rows).
+__global__ void __launch_bounds__(SL_THREADS)
+slgram_planes_kernel(int n, long mp, const unsigned short* __restrict__ D,
+                     const int* __restrict__ ecol, int kchunk, double* __restrict__ partial) {
+    const int tn = blockIdx.x, tm = blockIdx.y, ks = blockIdx.z;
+    if (tn < tm) return;
+    extern __shared__ unsigned char smraw[];
+    SlTiles* stage = reinterpret_cast<SlTiles*>(smraw);  // [2 stages][2 operands]
+    const bool diag = (tn == tm);
+    const int J0 = tm * SL_BM, K0 = tn * SL_BN;
+    const long kbeg = (long)ks * kchunk;
+    const long kend = min(mp, kbeg + kchunk);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int nops = diag ? 1 : 2;
+    auto issue = [&](int st, long k0) {
+        // chunks: operand o, digit s, row r (64), 4 x 16 B along i
+        const int total = nops * SL_S * 64 * 4;
+        for (int c = tid; c < total; c += SL_THREADS) {
+            const int q = c & 3, r = (c >> 2) & 63, s = (c >> 8) % SL_S, o = c / (256 * SL_S);
+            const int gj = (o == 0 ? J0 : K0) + r;
+            SlTiles& T = stage[st * 2 + o];
+            unsigned short* dst = &T.d[s][r][q * 8];
+            if (gj < n) {
+                cp_async16(dst, D + ((long)s * n + gj) * mp + k0 + q * 8);
+            } else {
+                *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        cp_async_commit();
+    };
+    float hi[2][4][4], lo[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) hi[a][b][c] = lo[a][b][c] = 0.f;
+    if (kbeg < kend) issue(0, kbeg);
+    int st = 0;
+    for (long k0 = kbeg; k0 < kend; k0 += SL_BK) {
+        const bool more = k0 + SL_BK < kend;
+        if (more) issue(st ^ 1, k0 + SL_BK);
+        if (more) cp_async_wait<1>(); else cp_async_wait<0>();
+        __syncthreads();
+        const SlTiles& TJ = stage[st * 2];
+        const SlTiles& TK = diag ? stage[st * 2] : stage[st * 2 + 1];
+        block_products(TJ, TK, wm, wn, lane, hi, lo);
+        __syncthreads();
+        st ^= 1;
+    }
+    double* out = partial + (long)ks * n * n;
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = J0 + wm + mi * 16 + g + (c >= 2 ? 8 : 0);
+                const int k = K0 + wn + ni * 8 + t4 * 2 + (c & 1);
+                if (j < n && k < n) {
+                    const double v = (double)hi[mi][ni][c] + (double)lo[mi][ni][c];
+                    out[(long)j * n + k] = ldexp(v, ecol[j] + ecol[k] - 16);
+                }
+            }
+}
+
 __global__ void slgram_reduce_kernel(int n, int ksplit, const double* __restrict__ P, double* G,
                                      long ldg) {
     const long total = (long)n * n;
@@ -346,10 +395,10 @@ long sl_resident() {
     int dev = 0, sms = 152, per = 1;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(slgram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * sizeof(SlTiles)));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, slgram_kernel, SL_THREADS,
-                                                      2 * sizeof(SlTiles)) != cudaSuccess || per < 1)
+    cudaFuncSetAttribute(slgram_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(4 * sizeof(SlTiles)));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, slgram_planes_kernel, SL_THREADS,
+                                                      4 * sizeof(SlTiles)) != cudaSuccess || per < 1)
         per = 1;
     (void)cudaGetLastError();
     cached = (long)sms * per;
@@ -413,8 +462,10 @@ tt_status bench_bf16_mma(cudaStream_t s, double* tflops) {
 }
 
 size_t slgram_scratch_doubles(int m, int n) {
-    // split partials + per-column maxima (as 64-bit words) + exponents
-    return (size_t)sl_ksplit(std::max(m, 1), n) * n * n + 2 * (size_t)n + 8;
+    // split partials + per-column maxima (as 64-bit words) + exponents + digit planes
+    const size_t mp = ((size_t)std::max(m, 1) + SL_BK - 1) / SL_BK * SL_BK;
+    return ((size_t)sl_ksplit(std::max(m, 1), n) * n * n + 2 * (size_t)n + 8 + 31) / 32 * 32 +
+           (SL_S * (size_t)n * mp + 3) / 4;
 }
 
 tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
@@ -437,14 +488,25 @@ tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double
         note_launch();
         max_to_exp_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cmax, ecol);
     }
-    int kchunk = (m + ks - 1) / ks;
-    kchunk = ((kchunk + SL_BK - 1) / SL_BK) * SL_BK;
-    const size_t smem = 2 * sizeof(SlTiles);
-    TT_CUDA_TRY(cudaFuncSetAttribute(slgram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int T = (n + SL_BN - 1) / SL_BN;
-    note_launch();
-    slgram_kernel<<<dim3(T, T, ks), SL_THREADS, smem, s>>>(m, n, A, lda, ecol, ks, kchunk, partial);
-    TT_CUDA_TRY(cudaGetLastError());
+    const long mp = ((long)m + SL_BK - 1) / SL_BK * SL_BK;
+    // digit planes start on a 256-byte boundary (cp.async moves 16-byte chunks)
+    const size_t plane_off = ((size_t)ks * n * n + 2 * (size_t)n + 8 + 31) / 32 * 32;
+    unsigned short* planes = reinterpret_cast<unsigned short*>(scratch.p + plane_off);
+    {
+        dim3 grid((n + 63) / 64, (unsigned)std::min<long>(mp / 32, 16384));
+        note_launch();
+        slice_cols_kernel<<<grid, 256, 0, s>>>(m, n, mp, A, lda, ecol, planes);
+    }
+    {
+        long kchunk = (mp + ks - 1) / ks;
+        kchunk = ((kchunk + SL_BK - 1) / SL_BK) * SL_BK;
+        const size_t smem = 4 * sizeof(SlTiles);
+        TT_CUDA_TRY(cudaFuncSetAttribute(slgram_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int T = (n + SL_BN - 1) / SL_BN;
+        note_launch();
+        slgram_planes_kernel<<<dim3(T, T, ks), SL_THREADS, smem, s>>>(n, mp, planes, ecol, (int)kchunk, partial);
+        TT_CUDA_TRY(cudaGetLastError());
+    }
     const long total = (long)n * n;
     note_launch();
     slgram_reduce_kernel<<<(int)std::min<long>((total + 255) / 256, 152L * 32), 256, 0, s>>>(n, ks, partial, G, ldg);
