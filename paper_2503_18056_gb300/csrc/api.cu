@@ -662,13 +662,30 @@ tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
         TT_CREATE_TRY(h->gcore[1].ensure((size_t)(R1 * D.n_theta * R2), s));
         TT_CREATE_TRY(h->gcore[2].ensure((size_t)(R2 * D.n_phi), s));
         TT_CREATE_TRY(h->GA.ensure((size_t)(R1 * R1), s));
-        TT_CREATE_TRY(h->partials.ensure(gram_scratch_doubles((int)nc, (int)R1), s));
+        TT_CREATE_TRY(h->partials.ensure(D.precision == TT_MIXED
+                                              ? slgram_scratch_doubles((int)nc, (int)R1)
+                                              : gram_scratch_doubles((int)nc, (int)R1), s));
         for (int k = 0; k < 2; ++k) {
             const long Rk = k == 0 ? R1 : R2;
             TT_CREATE_TRY(h->GB[k].ensure((size_t)(Rk * Rk), s));
             TT_CREATE_TRY(h->VtB[k].ensure((size_t)(Rk * Rk), s));
             TT_CREATE_TRY(h->lamB[k].ensure((size_t)Rk, s));
         }
+        // rounding workspaces at their largest (bond 1 of a capped step)
+        const size_t RR = (size_t)(R1 * R1);
+        DevBuf* sq[] = {&h->Wc, &h->T1, &h->K, &h->VtK, &h->eig.g0, &h->eig.g1, &h->eig.vt_unsorted};
+        for (DevBuf* b : sq) TT_CREATE_TRY(b->ensure(RR, s));
+        TT_CREATE_TRY(h->lamK.ensure((size_t)R1, s));
+        TT_CREATE_TRY(h->eig.lam_unsorted.ensure((size_t)R1, s));
+        TT_CREATE_TRY(h->eig.abc.ensure((size_t)(3 * (R1 + 1)), s));
+        TT_CREATE_TRY(h->Vts.ensure((size_t)(cap1 * R1), s));
+        TT_CREATE_TRY(h->PAt.ensure((size_t)(cap1 * R1), s));
+        TT_CREATE_TRY(h->Mupd.ensure((size_t)(cap1 * R1), s));
+        TT_CREATE_TRY(h->bwd.ensure((size_t)(R1 * D.n_theta * R2), s));
+        TT_CREATE_TRY(h->tmp[0].ensure((size_t)(cap1 * D.n_theta * R2), s));
+        TT_CREATE_TRY(h->tmp[1].ensure((size_t)(cap1 * D.n_theta * R2), s));
+        TT_CREATE_TRY(h->thbar.ensure((size_t)(nterms * (cap1 + cap2) + 2), s));
+        if (D.precision == TT_MIXED) TT_CREATE_TRY(h->slscratch.ensure((size_t)(nc + R1) / 2 + 2, s));
     }
     init_isotropic(s, nc, D.Tr0 ? D.Tr0 : D.T0, D.c, D.a_r, h->core[0].p);
     fill(s, h->core[1].p, D.n_theta, 1.0);

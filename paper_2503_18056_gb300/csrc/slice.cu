@@ -19,8 +19,8 @@
 // the inner loop (GB300's FP64 pipe is ~1/70 of its FP32 pipe).
 //
 // Tiles: 64 x 64 outputs per CTA, four warps of 32 x 32, mma.sync m16n8k16
-// bf16 with FP32 accumulators, shared-memory digit tiles [S][64][40] per
-// operand (K-contiguous, conflict-free fragment loads).  The Gram slices each
+// bf16 with FP32 accumulators, shared-memory digit tiles [S][64][32] per
+// operand (K-contiguous, XOR-swizzled for conflict-free fragment loads).  The Gram slices each
 // column once into digit planes in global memory and streams them with a
 // two-stage cp.async pipeline; the update GEMM produces digits on the fly
 // (its B operand is small and its A tile is read by few CTAs).
@@ -33,7 +33,7 @@ namespace ttsn {
 namespace {
 
 constexpr int SL_S = 6;           // digits per value
-constexpr int SL_BM = 64, SL_BN = 64, SL_BK = 32, SL_LD = 40;  // smem row stride in bf16
+constexpr int SL_BM = 64, SL_BN = 64, SL_BK = 32, SL_LD = 32;  // smem row = 32 bf16 = 64 B
 constexpr int SL_THREADS = 128;
 
 __device__ __forceinline__ unsigned short bf16_bits_of_int(int v) {
@@ -147,10 +147,19 @@ __global__ void row_exp_kernel(long m, int n, const double* __restrict__ A, long
     }
 }
 
-// Shared-memory digit tiles: [S][64 rows][SL_LD] bf16, row = output index, col = K.
+// Shared-memory digit tiles: [S][64 rows][32] bf16, row = output index, col = K.
+// Rows are 64 bytes (16 words); 32-bit word w of row r is stored at word
+// w ^ 4 ((r >> 1) & 3), so the fragment loads of 8 rows x 4 words hit 32
+// distinct banks, and 16-byte chunks stay contiguous (the XOR is a multiple of
+// 4 words).
 struct SlTiles {
     unsigned short d[SL_S][SL_BM][SL_LD];
 };
+__device__ __forceinline__ int swz_word(int r, int w) { return w ^ (((r >> 1) & 3) << 2); }
+__device__ __forceinline__ int swz_elem(int r, int k) { return (swz_word(r, k >> 1) << 1) | (k & 1); }
+__device__ __forceinline__ unsigned ld_word(const SlTiles& T, int s, int r, int k) {
+    return *reinterpret_cast<const unsigned*>(&T.d[s][r][swz_word(r, k >> 1) << 1]);
+}
 
 // Fragment loads and the 21 digit products of one 32-row block for a warp's
 // 32 x 32 sub-tile, drained level by level into the double-float accumulators.
@@ -176,17 +185,17 @@ __device__ __forceinline__ void block_products(const SlTiles& TA, const SlTiles&
                 for (int mi = 0; mi < 2; ++mi) {
                     const int r0 = wm + mi * 16 + g;
                     const int c0 = kk + t4 * 2;
-                    af[mi][0] = *reinterpret_cast<const unsigned*>(&TA.d[s][r0][c0]);
-                    af[mi][1] = *reinterpret_cast<const unsigned*>(&TA.d[s][r0 + 8][c0]);
-                    af[mi][2] = *reinterpret_cast<const unsigned*>(&TA.d[s][r0][c0 + 8]);
-                    af[mi][3] = *reinterpret_cast<const unsigned*>(&TA.d[s][r0 + 8][c0 + 8]);
+                    af[mi][0] = ld_word(TA, s, r0, c0);
+                    af[mi][1] = ld_word(TA, s, r0 + 8, c0);
+                    af[mi][2] = ld_word(TA, s, r0, c0 + 8);
+                    af[mi][3] = ld_word(TA, s, r0 + 8, c0 + 8);
                 }
 #pragma unroll
                 for (int ni = 0; ni < 4; ++ni) {
                     const int nn = wn + ni * 8 + g;
                     const int k0 = kk + t4 * 2;
-                    bfr[ni][0] = *reinterpret_cast<const unsigned*>(&TB.d[t][nn][k0]);
-                    bfr[ni][1] = *reinterpret_cast<const unsigned*>(&TB.d[t][nn][k0 + 8]);
+                    bfr[ni][0] = ld_word(TB, t, nn, k0);
+                    bfr[ni][1] = ld_word(TB, t, nn, k0 + 8);
                 }
 #pragma unroll
                 for (int mi = 0; mi < 2; ++mi)
@@ -237,10 +246,11 @@ slgemm_nt_kernel(int M, int N, int K, const double* __restrict__ A, long lda,
             const int gc = N0 + r;
             const double vb = (gc < N && gk < K) ? B[(long)gc * ldb + gk] : 0.0;
             digits(vb, gc < N ? erowB[gc] : 0, db);
+            const int pk = swz_elem(r, kk);
 #pragma unroll
             for (int s = 0; s < SL_S; ++s) {
-                TA.d[s][r][kk] = da[s];
-                TB.d[s][r][kk] = db[s];
+                TA.d[s][r][pk] = da[s];
+                TB.d[s][r][pk] = db[s];
             }
         }
         __syncthreads();
@@ -330,7 +340,7 @@ slgram_planes_kernel(int n, long mp, const unsigned short* __restrict__ D,
             const int q = c & 3, r = (c >> 2) & 63, s = (c >> 8) % SL_S, o = c / (256 * SL_S);
             const int gj = (o == 0 ? J0 : K0) + r;
             SlTiles& T = stage[st * 2 + o];
-            unsigned short* dst = &T.d[s][r][q * 8];
+            unsigned short* dst = &T.d[s][r][swz_word(r, q * 4) << 1];
             if (gj < n) {
                 cp_async16(dst, D + ((long)s * n + gj) * mp + k0 + q * 8);
             } else {
