@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form companion run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle stepping for --impl reference")
@@ -232,9 +234,62 @@ def run_ours(args, rank, world, local_rank):
             e2e_s = time.perf_counter() - t0
             e2e = {"value": args.steps / e2e_s, "unit": "steps/s",
                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+    batched = None
+    if not args.no_batch:
+        batched = run_batch(args, torch, ttsn)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
-               clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed)
+               clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched)
     return res
+
+
+def run_batch(args, torch, ttsn):
+    """Batched form: the 64-problem workload (uneven 2D grids, ordinates, ranks,
+    tolerances), W warm-up batch steps, state reset, K_b timed batch steps."""
+    ps = workloads.batch_problems(64, seed=0)
+    batch = ttsn.TTSNBatch(ps)
+    init = []
+    for i in range(len(ps)):
+        pr = batch.problem(i)
+        init.append(([c.clone() for c in pr.cores()], pr.energy()[1].clone()))
+    batch.step(args.warmup)
+    for i, (cores, T0) in enumerate(init):
+        pr = batch.problem(i)
+        pr.set_cores(cores)
+        pr.set_T(T0)
+    batch.sync()
+    torch.cuda.synchronize()
+    kb = args.batch_steps
+    t0 = time.perf_counter()
+    infos = batch.step(kb)
+    batch.sync()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    upd = sum(int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"] for p in ps)
+    ranks = [inf["ranks"][1:-1] for inf in infos]
+    # the same K_b steps with one host thread (problems one after another)
+    seq = ttsn.TTSNBatch(ps, threads=1)
+    seq.step(args.warmup)
+    for i, (cores, T0) in enumerate(init):
+        pr = seq.problem(i)
+        pr.set_cores(cores)
+        pr.set_T(T0)
+    seq.sync()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    seq.step(kb)
+    seq.sync()
+    torch.cuda.synchronize()
+    dt_seq = time.perf_counter() - t1
+    del seq
+    return {"workload": "64 independent 2D problems, grids U{64^2,128^2,256^2}, ordinates U{16x32,32x64}, "
+                        "sigma_a log-U[1e-2,1e2], Gaussian T pulses, eps U{1e-4,1e-6}, rank caps U[8,96], "
+                        "periodic (seed 0); each problem on its own stream, host threads advance them",
+            "problem_steps_per_s": len(ps) * kb / dt, "batch_steps_per_s": kb / dt, "steps": kb,
+            "warmup": args.warmup, "updates_per_s": upd * kb / dt,
+            "timing": "host wall clock around tt_batch_step with device synchronisation on both sides",
+            "one_thread_problem_steps_per_s": len(ps) * kb / dt_seq,
+            "concurrency_speedup": dt_seq / dt,
+            "ranks_last_min_max": [min(min(r) for r in ranks), max(max(r) for r in ranks)]}
 
 
 def roofline_of(prof, fp64_peak, peaks):
@@ -426,6 +481,8 @@ def main():
             "step_ms": [round(x, 3) for x in mx["step_ms"]],
             "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in mx["prof"].items()},
             "roofline": mroof}
+    if res.get("batched") is not None:
+        line["batched"] = res["batched"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

@@ -203,6 +203,34 @@ const char* tt_last_error(void);
 void tt_destroy(tt_handle h);
 
 /* ---------------------------------------------------------------------------
+ * Batched form: many independent problems of uneven sizes stepped together.
+ * ------------------------------------------------------------------------ */
+typedef struct tt_batch_ctx* tt_batch;
+
+/*
+ * tt_batch_create: one problem per descs[i] (as tt_create), each on a CUDA
+ * stream the batch creates and owns, all on the current device.  threads
+ * (<= 0: min(count, 32)) host threads advance problems concurrently in
+ * tt_batch_step.
+ */
+tt_status tt_batch_create(const tt_problem_desc* descs, int count, int threads, tt_batch* out);
+
+/*
+ * tt_batch_step: advance every problem by nsteps time steps (as tt_sn_step);
+ * infos (nullable) receives count step infos.  The first failing problem's
+ * status is returned with its message.
+ */
+tt_status tt_batch_step(tt_batch b, int nsteps, tt_step_info* infos);
+
+/* tt_batch_size: number of problems.  tt_batch_handle: borrowed handle of
+ * problem i (valid until tt_batch_destroy; use it for tt_energy, tt_to_full,
+ * tt_get_core ...).  tt_batch_sync: wait for every problem's stream. */
+tt_status tt_batch_size(tt_batch b, int* count);
+tt_status tt_batch_handle(tt_batch b, int i, tt_handle* out);
+tt_status tt_batch_sync(tt_batch b);
+void tt_batch_destroy(tt_batch b);
+
+/* ---------------------------------------------------------------------------
  * Kernel-level calls (the building blocks of tt_round, exposed for testing and
  * for callers that hold their own TT data).  All ordered on `stream`.
  * ------------------------------------------------------------------------ */

@@ -9,13 +9,14 @@ raises ImportError.
 """
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _native
 from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_MIXED, TT_STEP_NO_ROUND,
                       TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev",
+__all__ = ["TTSN", "TTSNBatch", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev",
            "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
            "TT_STEP_NO_ROUND"]
 
@@ -195,6 +196,73 @@ class TTSN(_Handle):
 
     def full(self):
         return super().full().reshape(self.n + (self.n_theta, self.n_phi))
+
+
+class _BorrowedTTSN(TTSN):
+    """View of one problem of a batch (the batch owns the handle)."""
+
+    def __init__(self, h, n, n_theta, n_phi):
+        _Handle.__init__(self)
+        self._h = h
+        self.nc = 1
+        for m in n:
+            self.nc *= int(m)
+        self.n = tuple(int(m) for m in n)
+        self.n_theta, self.n_phi = int(n_theta), int(n_phi)
+
+    def __del__(self):
+        self._h = None  # owned by the batch
+
+
+class TTSNBatch:
+    """Independent TT-S_N problems of uneven sizes stepped together (each on its
+    own stream, advanced concurrently by host threads in the library)."""
+
+    def __init__(self, problems, threads=0, precision=TT_FP64):
+        keep = []
+        descs = (_native.ProblemDesc * len(problems))()
+        for i, p in enumerate(problems):
+            nc = int(np.prod(p["n"]))
+            f = {k: _dev(p[k].reshape(-1), nc) for k in ("sigma_a", "cv", "T0", "Tr0", "sigma_s")}
+            keep.append(f)
+            d = descs[i]
+            ndim = len(p["n"])
+            d.ndim = ndim
+            for a in range(3):
+                d.n[a] = int(p["n"][a]) if a < ndim else 1
+                d.L[a] = float(p["L"][a]) if a < ndim else 1.0
+                d.bc[a] = int(p["bc"][a]) if a < ndim else 0
+            d.n_theta, d.n_phi = int(p["n_theta"]), int(p["n_phi"])
+            d.c, d.a_r, d.cfl, d.dt = float(p["c"]), float(p["a_r"]), float(p.get("cfl", 0.5)), float(p["dt"])
+            for key in ("sigma_a", "cv", "T0", "Tr0", "sigma_s"):
+                setattr(d, key, f[key].data_ptr())
+            d.eps, d.max_rank = float(p["eps"]), int(p.get("max_rank") or 0)
+            d.rounds_per_step, d.precision = 1, int(precision)
+        torch.cuda.synchronize()
+        self._b = ctypes.c_void_p()
+        check(lib.tt_batch_create(descs, len(problems), int(threads), ctypes.byref(self._b)))
+        self.problems = problems
+        self.count = len(problems)
+
+    def __del__(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            lib.tt_batch_destroy(b)
+            self._b = None
+
+    def step(self, nsteps=1):
+        infos = (StepInfo * self.count)()
+        check(lib.tt_batch_step(self._b, int(nsteps), infos))
+        return [x.as_dict() for x in infos]
+
+    def sync(self):
+        check(lib.tt_batch_sync(self._b))
+
+    def problem(self, i):
+        h = ctypes.c_void_p()
+        check(lib.tt_batch_handle(self._b, int(i), ctypes.byref(h)))
+        p = self.problems[i]
+        return _BorrowedTTSN(h, p["n"], p["n_theta"], p["n_phi"])
 
 
 def dgemm(A, B, trans_a=False, trans_b=False, alpha=1.0, stream=None):

@@ -80,6 +80,11 @@ def _load():
         "tt_gram_mixed": [i, i, vp, i, vp, i, vp],
         "tt_gemm_nt_mixed": [i, i, i, vp, i, vp, i, vp, i, vp],
         "tt_set_precision": [vp, i],
+        "tt_batch_create": [ctypes.POINTER(ProblemDesc), i, i, ctypes.POINTER(vp)],
+        "tt_batch_step": [vp, i, ctypes.POINTER(StepInfo)],
+        "tt_batch_size": [vp, ip],
+        "tt_batch_handle": [vp, i, ctypes.POINTER(vp)],
+        "tt_batch_sync": [vp],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
@@ -95,6 +100,8 @@ def _load():
     lib.tt_last_error.restype = ctypes.c_char_p
     lib.tt_destroy.argtypes = [vp]
     lib.tt_destroy.restype = None
+    lib.tt_batch_destroy.argtypes = [vp]
+    lib.tt_batch_destroy.restype = None
     lib.tt_kernel_launches.argtypes = []
     lib.tt_kernel_launches.restype = ctypes.c_ulonglong
     return lib
@@ -108,7 +115,8 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_set_T", "tt_sync", "tt_last_error", "tt_destroy", "tt_dgemm", "tt_gram",
             "tt_syev", "tt_gram_noalloc", "tt_gram_mixed", "tt_gemm_nt_mixed",
             "tt_set_precision", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma",
-            "tt_bench_bf16_mma"]
+            "tt_bench_bf16_mma", "tt_batch_create", "tt_batch_step", "tt_batch_size",
+            "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

@@ -65,6 +65,23 @@ tt_status DevBuf::ensure(size_t n, cudaStream_t s, bool keep) {
     return TT_OK;
 }
 
+tt_status ensure_max_dynamic_smem(const void* kernel) {
+    static std::mutex mu;
+    static std::vector<const void*> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const void* k : done)
+        if (k == kernel) return TT_OK;
+    int dev = 0, optin = 0;
+    TT_CUDA_TRY(cudaGetDevice(&dev));
+    TT_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    TT_CUDA_TRY(cudaFuncGetAttributes(&fa, kernel));
+    TT_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes));
+    done.push_back(kernel);
+    return TT_OK;
+}
+
 void DevBuf::release() {
     if (p) cudaFree(p);
     p = nullptr;

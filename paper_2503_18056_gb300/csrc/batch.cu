@@ -1,0 +1,126 @@
+// Batched form: many independent TT-S_N problems of uneven sizes stepped
+// together.  Each problem is a full handle (tt_create) on its own CUDA stream;
+// a pool of host threads advances the problems concurrently, so the small
+// per-problem kernels of different problems overlap on the GPU and each
+// problem's rank decisions wait only for its own stream.
+#include <atomic>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ttsn;
+
+struct tt_batch_ctx {
+    int device = 0;
+    std::vector<tt_handle> h;
+    std::vector<cudaStream_t> streams;
+    int threads = 1;
+    ~tt_batch_ctx() {
+        for (tt_handle x : h) tt_destroy(x);
+        for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    }
+};
+
+extern "C" {
+
+tt_status tt_batch_create(const tt_problem_desc* descs, int count, int threads, tt_batch* out) {
+    set_error("");
+    if (!descs || !out || count <= 0) {
+        set_error("tt_batch_create: need descs, out and count > 0");
+        return TT_ERR_ARG;
+    }
+    *out = nullptr;
+    tt_batch_ctx* b = new tt_batch_ctx();
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        set_error("tt_batch_create: no current device");
+        return TT_ERR_CUDA;
+    }
+    b->threads = threads > 0 ? threads : std::min(count, 32);
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            set_error("tt_batch_create: stream creation failed");
+            return TT_ERR_CUDA;
+        }
+        b->streams.push_back(s);
+        tt_handle h = nullptr;
+        tt_status st = tt_create(&descs[i], s, &h);
+        if (st < 0) {
+            std::string msg = std::string("tt_batch_create: problem ") + std::to_string(i) + ": " + tt_last_error();
+            delete b;
+            set_error(msg);
+            return st;
+        }
+        b->h.push_back(h);
+    }
+    *out = b;
+    return TT_OK;
+}
+
+tt_status tt_batch_step(tt_batch b, int nsteps, tt_step_info* infos) {
+    set_error("");
+    if (!b) {
+        set_error("tt_batch_step: null batch");
+        return TT_ERR_ARG;
+    }
+    const int n = (int)b->h.size();
+    std::atomic<int> next{0};
+    std::vector<tt_status> status(n, TT_OK);
+    std::vector<std::string> errs(n);
+    auto worker = [&]() {
+        cudaSetDevice(b->device);
+        for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+            status[i] = tt_sn_step_ex(b->h[i], nsteps, 0, nullptr, infos ? &infos[i] : nullptr);
+            if (status[i] < 0) errs[i] = tt_last_error();
+        }
+    };
+    const int nt = std::max(1, std::min(b->threads, n));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    tt_status result = TT_OK;
+    for (int i = 0; i < n; ++i) {
+        if (status[i] < 0) {
+            set_error(std::string("problem ") + std::to_string(i) + ": " + errs[i]);
+            return status[i];
+        }
+        if (status[i] == TT_WARN_RANK_CAPPED) result = TT_WARN_RANK_CAPPED;
+    }
+    return result;
+}
+
+tt_status tt_batch_size(tt_batch b, int* count) {
+    if (!b || !count) {
+        set_error("tt_batch_size: null argument");
+        return TT_ERR_ARG;
+    }
+    *count = (int)b->h.size();
+    return TT_OK;
+}
+
+tt_status tt_batch_handle(tt_batch b, int i, tt_handle* out) {
+    if (!b || !out || i < 0 || i >= (int)b->h.size()) {
+        set_error("tt_batch_handle: bad batch or index");
+        return TT_ERR_ARG;
+    }
+    *out = b->h[i];
+    return TT_OK;
+}
+
+tt_status tt_batch_sync(tt_batch b) {
+    if (!b) {
+        set_error("tt_batch_sync: null batch");
+        return TT_ERR_ARG;
+    }
+    for (tt_handle h : b->h) TT_TRY(tt_sync(h));
+    return TT_OK;
+}
+
+void tt_batch_destroy(tt_batch b) { delete b; }
+
+}  // extern "C"

@@ -6,6 +6,7 @@
 // with four warps of 32x32 each keeps the pipe fed; operand staging is plain
 // coalesced loads.
 #include <algorithm>
+#include <atomic>
 
 #include "internal.h"
 
@@ -208,8 +209,8 @@ tt_status dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double al
 namespace {
 // CTAs of dgemm_kernel<true,false> resident on the whole GPU at once.
 long resident_gram_ctas() {
-    static long cached = 0;
-    if (cached) return cached;
+    static std::atomic<long> cached{0};  // the same value from any thread
+    if (cached.load()) return cached.load();
     int dev = 0, sms = 152, per = 4;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -217,8 +218,8 @@ long resident_gram_ctas() {
             cudaSuccess || per < 1)
         per = 4;
     (void)cudaGetLastError();
-    cached = (long)sms * per;
-    return cached;
+    cached.store((long)sms * per);
+    return cached.load();
 }
 
 // Row-split factor of the Gram: the upper-triangle tiles times the splits fill

@@ -38,6 +38,12 @@ enum : int { DEV_OK = 0, DEV_NOT_CONVERGED = 1, DEV_TIMEOUT = 2 };
 // count the library's launches inside a timed region (tt_kernel_launches).
 void note_launch(unsigned n = 1);
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per kernel and never lower (the attribute is process-wide, so setting it
+// per launch to the launch's own size races between host threads that step
+// different problems concurrently).
+tt_status ensure_max_dynamic_smem(const void* kernel);
+
 // ---------------------------------------------------------------- device buffer
 // A growable device buffer: capacity only grows; contents are not preserved
 // across a grow unless `keep` is set.

@@ -550,8 +550,7 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
         set_error("syev: matrix too large for the shared-memory row buffers");
         return TT_ERR_TOO_LARGE;
     }
-    TT_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    TT_TRY(ensure_max_dynamic_smem((const void*)jacobi_kernel));
     int blocks = 1;
     TT_TRY(coop_blocks((const void*)jacobi_kernel, smem, want, &blocks));
     const int ppc = (npairs + blocks - 1) / blocks;
@@ -600,8 +599,7 @@ tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, dou
         set_error("pchol: matrix too large");
         return TT_ERR_TOO_LARGE;
     }
-    TT_CUDA_TRY(cudaFuncSetAttribute(pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    TT_TRY(ensure_max_dynamic_smem((const void*)pchol_kernel));
     int blocks = 1;
     // about eight columns per CTA (one warp each)
     TT_TRY(coop_blocks((const void*)pchol_kernel, smem, std::max(1, (n + 7) / 8), &blocks));

@@ -25,6 +25,7 @@
 // two-stage cp.async pipeline; the update GEMM produces digits on the fly
 // (its B operand is small and its A tile is read by few CTAs).
 #include <algorithm>
+#include <atomic>
 
 #include "internal.h"
 
@@ -400,19 +401,18 @@ __global__ void slgram_reduce_kernel(int n, int ksplit, const double* __restrict
 }
 
 long sl_resident() {
-    static long cached = 0;
-    if (cached) return cached;
+    static std::atomic<long> cached{0};  // the same value from any thread
+    if (cached.load()) return cached.load();
     int dev = 0, sms = 152, per = 1;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(slgram_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(4 * sizeof(SlTiles)));
+    (void)ensure_max_dynamic_smem((const void*)slgram_planes_kernel);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, slgram_planes_kernel, SL_THREADS,
                                                       4 * sizeof(SlTiles)) != cudaSuccess || per < 1)
         per = 1;
     (void)cudaGetLastError();
-    cached = (long)sms * per;
-    return cached;
+    cached.store((long)sms * per);
+    return cached.load();
 }
 
 int sl_ksplit(int m, int n) {
@@ -511,7 +511,7 @@ tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double
         long kchunk = (mp + ks - 1) / ks;
         kchunk = ((kchunk + SL_BK - 1) / SL_BK) * SL_BK;
         const size_t smem = 4 * sizeof(SlTiles);
-        TT_CUDA_TRY(cudaFuncSetAttribute(slgram_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TT_TRY(ensure_max_dynamic_smem((const void*)slgram_planes_kernel));
         const int T = (n + SL_BN - 1) / SL_BN;
         note_launch();
         slgram_planes_kernel<<<dim3(T, T, ks), SL_THREADS, smem, s>>>(n, mp, planes, ecol, (int)kchunk, partial);
@@ -539,7 +539,7 @@ tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long 
     note_launch();
     row_exp_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, K, B, ldb, eB);
     const size_t smem = 2 * sizeof(SlTiles);
-    TT_CUDA_TRY(cudaFuncSetAttribute(slgemm_nt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TT_TRY(ensure_max_dynamic_smem((const void*)slgemm_nt_kernel));
     const long gy = (M + SL_BM - 1) / SL_BM;
     if (gy > 65535L) {
         set_error("slgemm_nt: too many rows");

@@ -123,3 +123,28 @@ def random_positive_tt(n_modes, ranks, seed):
     d = len(n_modes)
     r = [1] + list(ranks) + [1]
     return [rng.uniform(0.5, 1.5, (r[k], n_modes[k], r[k + 1])) / r[k] for k in range(d)]
+
+
+def batch_problems(count=64, seed=0):
+    """Independent 2D problems of uneven sizes: grids from {64^2, 128^2, 256^2},
+    ordinates from {16x32, 32x64}, uniform sigma_a log-uniform in [1e-2, 1e2],
+    a Gaussian T pulse (centre U[0.3,0.7]^2, width U[0.05,0.15], peak
+    U[0.5,1], background 0.01) in equilibrium with the radiation, eps from
+    {1e-4, 1e-6}, rank cap U{8..96}, periodic, CFL 0.5."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.choice([64, 128, 256]))
+        nt, npf = [(16, 32), (32, 64)][int(rng.integers(0, 2))]
+        n = (m, m)
+        L = (1.0, 1.0)
+        centre = rng.uniform(0.3, 0.7, 2)
+        T0 = gaussian_pulse(n, L, rng.uniform(0.5, 1.0), rng.uniform(0.05, 0.15), 0.01, centre)
+        sig = 10.0 ** rng.uniform(-2, 2)
+        p = dict(n=n, L=L, n_theta=nt, n_phi=npf, bc=[PERIODIC, PERIODIC],
+                 eps=float(rng.choice([1e-4, 1e-6])), max_rank=int(rng.integers(8, 97)),
+                 steps=10, cfl=0.5, c=1.0, a_r=1.0, name="batch",
+                 T0=T0, Tr0=T0.copy(), sigma_a=np.full(n, sig), sigma_s=np.zeros(n), cv=np.ones(n))
+        p["dt"] = p["cfl"] * (1.0 / m) / p["c"]
+        out.append(p)
+    return out
