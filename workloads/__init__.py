@@ -148,3 +148,33 @@ def batch_problems(count=64, seed=0):
         p["dt"] = p["cfl"] * (1.0 / m) / p["c"]
         out.append(p)
     return out
+
+
+def gaussian_random_field(n, seed=0, corr=0.1, L=None):
+    """Smooth random field: white noise (seeded) filtered in Fourier space by a
+    Gaussian kernel of correlation length ``corr`` (periodic), normalised to
+    mean 0 and standard deviation 1."""
+    rng = np.random.default_rng(seed)
+    n = tuple(n)
+    L = L or (1.0,) * len(n)
+    noise = rng.standard_normal(n)
+    F = np.fft.fftn(noise)
+    k2 = np.zeros(n)
+    for a, m in enumerate(n):
+        k = 2 * np.pi * np.fft.fftfreq(m, d=L[a] / m)
+        shape = [1] * len(n)
+        shape[a] = m
+        k2 = k2 + (k ** 2).reshape(shape)
+    g = np.real(np.fft.ifftn(F * np.exp(-0.5 * k2 * corr * corr)))
+    return (g - g.mean()) / g.std()
+
+
+def grf_problem(n=(128, 128), n_theta=32, n_phi=64, steps=20, eps=1e-6, max_rank=0, seed=0):
+    """Adjoint workload: sigma_a = exp(g) with g a Gaussian random field (corr.
+    length 0.1, seed), a Gaussian T pulse (peak 1, width 0.1, background 0.01)
+    in equilibrium, vacuum boundaries, CFL 0.5."""
+    p = problem("small_2d", n=n, n_theta=n_theta, n_phi=n_phi, eps=eps, bc=VACUUM,
+                max_rank=max_rank, steps=steps)
+    p["sigma_a"] = np.exp(gaussian_random_field(p["n"], seed=seed, corr=0.1))
+    p["name"] = "grf_2d"
+    return p
