@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision-form companion run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-form leg")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle stepping for --impl reference")
@@ -237,9 +238,53 @@ def run_ours(args, rank, world, local_rank):
     batched = None
     if not args.no_batch:
         batched = run_batch(args, torch, ttsn)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(args, torch, ttsn)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
-               clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched)
+               clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
+               adjoint=adjoint)
     return res
+
+
+def run_adjoint(args, torch, ttsn):
+    """Adjoint form: gradient of the boundary-escape energy of 20 steps of the
+    128^2 x (32 x 64) random-field problem (eps 1e-6, checkpoints every 5 steps)
+    with respect to sigma_a.  One untimed warm-up gradient, then the taped
+    forward, the reverse sweep and an untaped forward, each timed with CUDA
+    events on the problem's stream."""
+    p = workloads.grf_problem()
+    every = 5
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        def run(tape):
+            g = ttsn.TTSN.from_problem(p, stream=stream)
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            if tape:
+                g.tape_begin(every)
+            info = g.step(p["steps"])
+            e[1].record(stream)
+            out = None
+            if tape:
+                out = g.escape_gradient()
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            return g, info, e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), out
+
+        run(True)  # warm-up
+        l0 = ttsn.kernel_launches()
+        _, info, fwd_ms, bwd_ms, (q, grad) = run(True)
+        launches = ttsn.kernel_launches() - l0
+        _, _, plain_ms, _, _ = run(False)
+    return {"workload": "2D %dx%d cells, %dx%d ordinates, sigma_a = exp(Gaussian random field, corr. 0.1), "
+                        "vacuum, %d steps, eps %g, checkpoints every %d steps"
+                        % (p["n"][0], p["n"][1], p["n_theta"], p["n_phi"], p["steps"], p["eps"], every),
+            "gradients_per_s": 1e3 / (fwd_ms + bwd_ms), "forward_taped_ms": fwd_ms,
+            "backward_ms": bwd_ms, "forward_untaped_ms": plain_ms,
+            "backward_over_forward": bwd_ms / plain_ms, "gpu_launches": launches,
+            "Q": q, "grad_l2": float(grad.norm()), "ranks_last": info["ranks"][1:-1]}
 
 
 def run_batch(args, torch, ttsn):
@@ -483,6 +528,8 @@ def main():
             "roofline": mroof}
     if res.get("batched") is not None:
         line["batched"] = res["batched"]
+    if res.get("adjoint") is not None:
+        line["adjoint"] = res["adjoint"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

@@ -203,6 +203,57 @@ const char* tt_last_error(void);
 void tt_destroy(tt_handle h);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint form: gradient of the boundary-escape energy with respect to
+ * sigma_a by reverse mode through the step of Sec. 3.2 / 4.3-4.4 and the
+ * rounding of App. A.
+ *
+ * Objective: Q = sum over the taped steps m of the radiation energy that
+ * leaves through the faces of vacuum axes (Sec. 4.5) during the step,
+ *   Q_m = sum_faces sum_{cells i on the face} sum_{l,p}
+ *         dt dA (n_lp . n_out)^+ I^m_{ilp} dOmega_lp,
+ * I^m the state after step m, dA the face area (product of the other axes'
+ * cell widths), n_out the outward face normal.  Periodic axes have no faces.
+ *
+ * The gradient is that of the step map with each rounding's factors held
+ * fixed at their taped values (P_A^T and M_upd of every bond: the rounded
+ * cores are X_g P_1 and M_1 Theta_g P_2 and M_2 Phi_g).  It equals the
+ * derivative of the untruncated scheme wherever the truncated directions
+ * carry no perturbation, and differs from a finite difference of the rounded
+ * map at the level of the discarded singular values.  The temperature solve
+ * (quartic) is reversed by the implicit-function theorem.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * tt_tape_begin: start recording.  Every later tt_sn_step / tt_sn_step_ex step
+ * (flags 0; FP64 precision, rounds_per_step 1, no scattering, else
+ * TT_ERR_STATE) appends a record and adds its Q_m to the objective.  Records
+ * hold the step's input state (cores and T) every checkpoint_every (>= 1)
+ * steps and, when checkpoint_every == 1, the frozen factors of every step;
+ * otherwise tt_sn_step_adjoint re-runs each segment from its checkpoint.
+ * Device memory held: about (steps / checkpoint_every + checkpoint_every)
+ * states.  Clears any earlier tape and zeroes Q.  tt_round, tt_set_cores,
+ * tt_set_T and tt_set_precision end the tape (the recorded run is discarded).
+ */
+tt_status tt_tape_begin(tt_handle h, int checkpoint_every);
+
+/* tt_tape_objective: Q so far (host double) and, if steps_host is non-null,
+ * the number of taped steps.  Synchronises the handle's stream. */
+tt_status tt_tape_objective(tt_handle h, double* Q_host, int* steps_host);
+
+/*
+ * tt_sn_step_adjoint: run the reverse sweep over the taped steps.
+ * grad_sigma_a_dev (device, N_c doubles, cell order as tt_create's fields,
+ * nullable) receives dQ/dsigma_a; Q_host (nullable) receives Q.  The handle's
+ * state (cores, ranks, T) is left as it was after the last taped step; the
+ * tape is released and recording stops.  TT_ERR_STATE without a tape or if a
+ * replayed step's ranks differ from the taped ones.
+ */
+tt_status tt_sn_step_adjoint(tt_handle h, double* grad_sigma_a_dev, double* Q_host);
+
+/* tt_tape_clear: stop recording and release the tape. */
+tt_status tt_tape_clear(tt_handle h);
+
+/* ---------------------------------------------------------------------------
  * Batched form: many independent problems of uneven sizes stepped together.
  * ------------------------------------------------------------------------ */
 typedef struct tt_batch_ctx* tt_batch;

@@ -16,7 +16,7 @@ from . import _native
 from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_MIXED, TT_STEP_NO_ROUND,
                       TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TTSNBatch", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev",
+__all__ = ["TTSN", "TTSNBatch", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev",
            "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
            "TT_STEP_NO_ROUND"]
 
@@ -167,13 +167,21 @@ class TTSN(_Handle):
         check(lib.tt_create(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(self._h)))
         self._keep = f  # inputs stay alive until creation finished (copied in)
 
+    @staticmethod
+    def problem_kwargs(p):
+        """Constructor keywords from a problem dict (grid, ordinates, constants,
+        fields of shape n); an all-zero sigma_s is passed as absent."""
+        sig_s = p.get("sigma_s")
+        return dict(n=p["n"], L=p["L"], n_theta=p["n_theta"], n_phi=p["n_phi"],
+                    sigma_a=p["sigma_a"].reshape(-1), cv=p["cv"].reshape(-1),
+                    T0=p["T0"].reshape(-1), Tr0=p["Tr0"].reshape(-1),
+                    sigma_s=(sig_s.reshape(-1) if sig_s is not None and np.any(sig_s) else None),
+                    c=p["c"], a_r=p["a_r"], dt=p["dt"], bc=list(p["bc"]), eps=p["eps"],
+                    max_rank=p.get("max_rank", 0))
+
     @classmethod
     def from_problem(cls, p, **over):
-        kw = dict(n=p["n"], L=p["L"], n_theta=p["n_theta"], n_phi=p["n_phi"],
-                  sigma_a=p["sigma_a"].reshape(-1), cv=p["cv"].reshape(-1),
-                  T0=p["T0"].reshape(-1), Tr0=p["Tr0"].reshape(-1),
-                  sigma_s=p["sigma_s"].reshape(-1), c=p["c"], a_r=p["a_r"], dt=p["dt"],
-                  bc=list(p["bc"]), eps=p["eps"], max_rank=p.get("max_rank", 0))
+        kw = cls.problem_kwargs(p)
         kw.update(over)
         return cls(**kw)
 
@@ -196,6 +204,57 @@ class TTSN(_Handle):
 
     def full(self):
         return super().full().reshape(self.n + (self.n_theta, self.n_phi))
+
+    # -- adjoint form
+    def tape_begin(self, checkpoint_every=1):
+        """Record the following steps for the escape-energy gradient."""
+        check(lib.tt_tape_begin(self._h, int(checkpoint_every)))
+
+    def escape_energy(self):
+        """(Q, taped steps): the boundary-escape energy of the taped steps so far."""
+        q = ctypes.c_double()
+        m = ctypes.c_int()
+        check(lib.tt_tape_objective(self._h, ctypes.byref(q), ctypes.byref(m)))
+        return q.value, m.value
+
+    def escape_gradient(self):
+        """Reverse sweep over the taped steps: (Q, dQ/dsigma_a as a CUDA tensor of
+        N_c doubles).  Releases the tape; the state stays at the last step."""
+        g = torch.empty(self.nc, dtype=torch.float64, device="cuda")
+        q = ctypes.c_double()
+        check(lib.tt_sn_step_adjoint(self._h, ctypes.c_void_p(g.data_ptr()), ctypes.byref(q)))
+        return q.value, g
+
+    def tape_clear(self):
+        check(lib.tt_tape_clear(self._h))
+
+
+class EscapeEnergy(torch.autograd.Function):
+    """Q(sigma_a): the boundary-escape energy of ``steps`` TT-S_N steps from a
+    problem's initial state, differentiable in sigma_a (a CUDA float64 tensor of
+    N_c values).  ``problem`` holds TTSN keyword arguments other than sigma_a.
+    Forward tapes the run (checkpoints every ``checkpoint_every`` steps);
+    backward is the library's reverse sweep with the rounding factors frozen."""
+
+    @staticmethod
+    def forward(ctx, sigma_a, problem, steps, checkpoint_every=1):
+        tt = TTSN(sigma_a=sigma_a.detach(), **problem)
+        tt.tape_begin(checkpoint_every)
+        tt.step(int(steps))
+        q, _ = tt.escape_energy()
+        ctx.tt = tt  # the taped run, reversed in backward
+        return torch.tensor(q, dtype=torch.float64, device=sigma_a.device)
+
+    @staticmethod
+    def backward(ctx, gq):
+        _, grad = ctx.tt.escape_gradient()
+        ctx.tt = None
+        return gq * grad, None, None, None
+
+
+def escape_energy(sigma_a, problem, steps, checkpoint_every=1):
+    """Differentiable boundary-escape energy (see EscapeEnergy)."""
+    return EscapeEnergy.apply(sigma_a, problem, steps, checkpoint_every)
 
 
 class _BorrowedTTSN(TTSN):

@@ -91,6 +91,10 @@ def _load():
                             ctypes.POINTER(ctypes.c_longlong), dp, dp],
         "tt_bench_fp64_mma": [dp, vp],
         "tt_bench_bf16_mma": [dp, vp],
+        "tt_tape_begin": [vp, i],
+        "tt_tape_objective": [vp, dp, ip],
+        "tt_sn_step_adjoint": [vp, vp, dp],
+        "tt_tape_clear": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -116,7 +120,8 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_syev", "tt_gram_noalloc", "tt_gram_mixed", "tt_gemm_nt_mixed",
             "tt_set_precision", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma",
             "tt_bench_bf16_mma", "tt_batch_create", "tt_batch_step", "tt_batch_size",
-            "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy"]
+            "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
+            "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

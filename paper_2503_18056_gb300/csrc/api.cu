@@ -94,7 +94,7 @@ using namespace ttsn;
 
 // host-side slots of the pinned readback block
 enum { HI_KB = 0, HI_DEC = 16, HI_STATUS = 20, HI_SWEEPS = 24, HI_N = 64 };
-enum { HD_DEC = 0, HD_DELTA2 = 4, HD_TOT = 8, HD_N = 16 };
+enum { HD_DEC = 0, HD_DELTA2 = 4, HD_TOT = 8, HD_Q = 12, HD_N = 16 };
 
 struct tt_ctx {
     cudaStream_t stream = nullptr;
@@ -130,6 +130,44 @@ struct tt_ctx {
     PhaseAcc ph[TT_NPHASES];
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> ev_pool;
+
+    // adjoint tape: one record per taped step.  Checkpoint records hold the
+    // step's input state (X, Theta, Phi, T); with a checkpoint interval of one
+    // every record also holds the frozen rounding factors (P_A^T and M_upd of
+    // each bond), otherwise the reverse sweep re-runs each segment from its
+    // checkpoint to refill them before applying the transposed operations.
+    struct StepRec {
+        int r1 = 0, r2 = 0, R1 = 0, R2 = 0, o1 = 0, o2 = 0;
+        bool state = false, proj = false;
+        DevBuf X, Th, Ph, T, P[2], M[2];
+        void release_state() {
+            X.release();
+            Th.release();
+            Ph.release();
+            T.release();
+            state = false;
+        }
+        void release_proj() {
+            for (int k = 0; k < 2; ++k) {
+                P[k].release();
+                M[k].release();
+            }
+            proj = false;
+        }
+        void release() {
+            release_state();
+            release_proj();
+        }
+    };
+    bool taping = false;               // steps append records
+    int tape_every = 1;                // checkpoint interval in steps
+    std::vector<StepRec*> tape;
+    StepRec* replay_rec = nullptr;     // record a replayed step refills
+    StepRec* cur_rec = nullptr;        // record the running step fills
+    bool rec_state = false, rec_proj = false;
+    // reverse-sweep workspace
+    DevBuf aXb, aXbi, aThb, aThbi, aPhb, aPhbi, aTb, aTbi, aXgb, aThgb, aPhgb, aThtb, aybar, aY,
+        aEsb, aEsbo, ae1b, asigb, athbb, ascr, atb1, atb2, aq;
 
     // physics
     Grid grid{};
@@ -174,6 +212,14 @@ struct tt_ctx {
                           &thbar, &red, &ang_buf};
         for (DevBuf* b : bufs) b->release();
         eig.release();
+        for (StepRec* r : tape) {
+            r->release();
+            delete r;
+        }
+        DevBuf* abufs[] = {&aXb, &aXbi, &aThb, &aThbi, &aPhb, &aPhbi, &aTb, &aTbi, &aXgb, &aThgb,
+                           &aPhgb, &aThtb, &aybar, &aY, &aEsb, &aEsbo, &ae1b, &asigb, &athbb,
+                           &ascr, &atb1, &atb2, &aq};
+        for (DevBuf* b : abufs) b->release();
         for (auto& p : pending) {
             cudaEventDestroy(p.a);
             cudaEventDestroy(p.b);
@@ -403,6 +449,13 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             TT_TRY(h->Mupd.ensure((size_t)rk * Rk, s));
             TT_TRY(dgemm(s, false, false, rk, Rk, Rk, 1.0, h->PAt.p, Rk, h->GA.p, Rk, 0.0, h->Mupd.p, Rk));
         }
+        if (h->cur_rec && h->rec_proj && k < 2) {
+            tt_ctx::StepRec* rc = h->cur_rec;
+            TT_TRY(rc->P[k].ensure((size_t)rk * Rk, s));
+            TT_TRY(rc->M[k].ensure((size_t)rk * Rk, s));
+            TT_CUDA_TRY(cudaMemcpyAsync(rc->P[k].p, h->PAt.p, (size_t)rk * Rk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            TT_CUDA_TRY(cudaMemcpyAsync(rc->M[k].p, h->Mupd.p, (size_t)rk * Rk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
         // A' = A P_A -> dst[k]
         TT_TRY(dst[k].ensure((size_t)m * rk, s));
         {
@@ -497,12 +550,57 @@ tt_status energy_update(tt_ctx* h) {
     return TT_OK;
 }
 
+// Escape energy of a state (cores X, Th, Ph with ranks o1, o2) added into
+// d_dbl[HD_Q]: sum over vacuum boundary faces of dt dA (n . n_out)^+ I dOmega.
+tt_status add_escape_energy(tt_ctx* h, const double* X, const double* Th, const double* Ph, int o1,
+                            int o2) {
+    cudaStream_t s = h->stream;
+    const int nterms = 1 + 2 * h->grid.ndim;
+    TT_TRY(h->atb1.ensure((size_t)nterms * (o1 + o2), s));
+    TT_TRY(h->aq.ensure((size_t)h->grid.nc, s));
+    grown_thbar(s, h->ang, h->grid.ndim, true, o1, o2, Th, Ph, h->atb1.p);
+    escape_rows(s, h->grid, h->fields.dt, o1, X, o1, h->atb1.p, h->aq.p, nullptr, 0, false);
+    sum_into(s, h->grid.nc, h->aq.p, h->d_dbl + HD_Q);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status copy_dev(DevBuf& dst, const double* src, size_t n, cudaStream_t s) {
+    TT_TRY(dst.ensure(std::max<size_t>(n, 1), s));
+    TT_CUDA_TRY(cudaMemcpyAsync(dst.p, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return TT_OK;
+}
+
 tt_status step_once(tt_ctx* h, int flags, const int* forced, tt_step_info* info) {
     const bool src = !(flags & TT_STEP_NO_SOURCE);
     const bool rnd = !(flags & TT_STEP_NO_ROUND);
     const bool two = (h->rounds == 2) && src && rnd;
     tt_status result = TT_OK;
     int rr[TT_MAX_D + 1];
+    h->cur_rec = nullptr;
+    if (h->taping || h->replay_rec) {
+        if (!src || !rnd || two || h->precision != TT_FP64 || h->has_sigma_s || !h->physics)
+            return fail(TT_ERR_STATE, "adjoint tape: only plain FP64 transport steps (one rounding, "
+                                      "source on, no scattering) can be recorded");
+        tt_ctx::StepRec* rc = h->replay_rec;
+        if (h->taping) {
+            rc = new tt_ctx::StepRec();
+            h->tape.push_back(rc);
+            h->rec_state = ((h->tape.size() - 1) % (size_t)h->tape_every) == 0;
+            h->rec_proj = h->tape_every == 1;
+        }
+        rc->r1 = h->r[1];
+        rc->r2 = h->r[2];
+        if (h->rec_state) {
+            cudaStream_t s = h->stream;
+            TT_TRY(copy_dev(rc->X, h->core[0].p, (size_t)h->grid.nc * rc->r1, s));
+            TT_TRY(copy_dev(rc->Th, h->core[1].p, (size_t)rc->r1 * h->ang.n_theta * rc->r2, s));
+            TT_TRY(copy_dev(rc->Ph, h->core[2].p, (size_t)rc->r2 * h->ang.n_phi, s));
+            TT_TRY(copy_dev(rc->T, h->f_T.p, (size_t)h->grid.nc, s));
+            rc->state = true;
+        }
+        h->cur_rec = rc;
+    }
     TT_TRY(apply_terms(h, true, src && !two));
     if (two) {
         tt_status st = round_cores(h, h->gcore, h->gr, h->core, rr, h->eps, h->max_rank, forced, info);
@@ -525,6 +623,17 @@ tt_status step_once(tt_ctx* h, int flags, const int* forced, tt_step_info* info)
         }
     }
     if (src) TT_TRY(energy_update(h));
+    if (h->cur_rec) {
+        tt_ctx::StepRec* rc = h->cur_rec;
+        h->cur_rec = nullptr;
+        rc->R1 = h->gr[1];
+        rc->R2 = h->gr[2];
+        rc->o1 = h->r[1];
+        rc->o2 = h->r[2];
+        if (h->rec_proj) rc->proj = true;
+        if (h->taping)
+            TT_TRY(add_escape_energy(h, h->core[0].p, h->core[1].p, h->core[2].p, rc->o1, rc->o2));
+    }
     if (info)
         for (int k = 0; k <= h->d; ++k) info->ranks[k] = h->r[k];
     return result;
@@ -534,6 +643,209 @@ tt_status check_handle(tt_handle h, bool need_physics) {
     if (!h) return fail(TT_ERR_ARG, "null handle");
     if (need_physics && !h->physics) return fail(TT_ERR_STATE, "handle is a bare TT (no problem attached)");
     return TT_OK;
+}
+
+// ---------------------------------------------------------------- adjoint form
+// Reverse mode of the taped steps for the gradient of the escape energy
+// Q = sum_m Q(I^m) with respect to sigma_a.  The rounding's factors are held
+// fixed: X' = X_g P_1, C = M_1 Theta_g, Theta' = C P_2, Phi' = M_2 Phi_g (P_k
+// the transpose of the stored P_A^T), so the rounding is reversed by four
+// GEMMs with the stored factors.  The quartic of Sec. 3.2 is reversed by the
+// implicit-function theorem inside the source kernel.
+
+// Copy a state into the handle (cores with ranks r1, r2 and the temperature).
+tt_status load_state(tt_ctx* h, const double* X, const double* Th, const double* Ph, const double* T,
+                     int r1, int r2) {
+    cudaStream_t s = h->stream;
+    const size_t nx = (size_t)h->grid.nc * r1, nth = (size_t)r1 * h->ang.n_theta * r2,
+                 nph = (size_t)r2 * h->ang.n_phi;
+    TT_TRY(h->core[0].ensure(nx, s));
+    TT_TRY(h->core[1].ensure(nth, s));
+    TT_TRY(h->core[2].ensure(nph, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->core[0].p, X, nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->core[1].p, Th, nth * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->core[2].p, Ph, nph * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->f_T.p, T, (size_t)h->grid.nc * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    h->r[0] = 1;
+    h->r[1] = r1;
+    h->r[2] = r2;
+    h->r[3] = 1;
+    return TT_OK;
+}
+
+// One step reversed.  In: the adjoints of the step's output state (aXb: nc x o1,
+// aThb: o1 x nt x o2, aPhb: o2 x np, aTb: nc) and the output cores; out: the
+// adjoints of its input state (swapped into the same buffers), sigma_a's
+// gradient accumulated in asigb.
+tt_status reverse_step(tt_ctx* h, const tt_ctx::StepRec& rc, const double* Xo, const double* Tho,
+                       const double* Pho) {
+    cudaStream_t s = h->stream;
+    const Grid& g = h->grid;
+    const Angular& ang = h->ang;
+    const long nc = g.nc;
+    const int nt = ang.n_theta, np = ang.n_phi;
+    const int nterms = 1 + 2 * g.ndim;
+    const int r1 = rc.r1, r2 = rc.r2, R1 = rc.R1, R2 = rc.R2, o1 = rc.o1, o2 = rc.o2;
+    const int nr = nterms * r1;
+    const double c = h->fields.c;
+    TT_TRY(h->atb1.ensure((size_t)nterms * (std::max(o1, r1) + std::max(o2, r2)), s));
+    TT_TRY(h->atb2.ensure((size_t)nterms * (r1 + r2), s));
+    TT_TRY(h->aq.ensure((size_t)nc, s));
+    TT_TRY(h->athbb.ensure((size_t)nterms * std::max(o1, r1), s));
+    TT_TRY(h->ascr.ensure((size_t)2 * nterms * std::max(o2, r2), s));
+    TT_TRY(h->ae1b.ensure((size_t)nc, s));
+    TT_TRY(h->aEsb.ensure((size_t)nc, s));
+    TT_TRY(h->aEsbo.ensure((size_t)nc, s));
+    TT_TRY(h->aTbi.ensure((size_t)nc, s));
+    TT_TRY(h->aPhgb.ensure((size_t)R2 * np, s));
+    TT_TRY(h->aThtb.ensure((size_t)o1 * nt * R2, s));
+    TT_TRY(h->aThgb.ensure((size_t)R1 * nt * R2, s));
+    TT_TRY(h->aXgb.ensure((size_t)nc * R1, s));
+    TT_TRY(h->aThbi.ensure((size_t)r1 * nt * r2, s));
+    TT_TRY(h->aPhbi.ensure((size_t)r2 * np, s));
+    TT_TRY(h->aybar.ensure((size_t)nc * nr, s));
+    TT_TRY(h->aY.ensure((size_t)nc * nr, s));
+    TT_TRY(h->aXbi.ensure((size_t)nc * r1, s));
+
+    // (1) this step's term of Q, a linear functional of the output cores
+    grown_thbar(s, ang, g.ndim, true, o1, o2, Tho, Pho, h->atb1.p);
+    escape_rows(s, g, h->fields.dt, o1, Xo, o1, h->atb1.p, h->aq.p, h->aXb.p, o1, true);
+    fill(s, h->athbb.p, (size_t)nterms * o1, 0.0);
+    escape_thbb(s, g, h->fields.dt, o1, Xo, o1, h->athbb.p);
+    thbar_adjoint(s, ang, nterms, 1, o1, o2, Tho, Pho, h->athbb.p, h->ascr.p, h->aThb.p, h->aPhb.p);
+
+    // (2) T' = T + (E* - E')/C_v with E' = X' . thbar'/c
+    plain_thbar(s, ang, o1, o2, Tho, Pho, h->atb1.p);
+    energy_adjoint_rows(s, nc, o1, h->atb1.p, c, h->f_cv.p, h->aTb.p, h->aXb.p, o1, h->ae1b.p,
+                        h->aEsb.p);
+    TT_TRY(dgemm(s, true, false, o1, 1, (int)nc, 1.0, Xo, o1, h->ae1b.p, 1, 0.0, h->athbb.p, 1));
+    thbar_adjoint(s, ang, 1, 0, o1, o2, Tho, Pho, h->athbb.p, h->ascr.p, h->aThb.p, h->aPhb.p);
+
+    // (3) rounding with frozen factors, reversed
+    TT_TRY(dgemm(s, true, false, R2, np, o2, 1.0, rc.M[1].p, R2, h->aPhb.p, np, 0.0, h->aPhgb.p, np));
+    TT_TRY(dgemm(s, false, false, o1 * nt, R2, o2, 1.0, h->aThb.p, o2, rc.P[1].p, R2, 0.0,
+                 h->aThtb.p, R2));
+    TT_TRY(dgemm(s, true, false, R1, nt * R2, o1, 1.0, rc.M[0].p, R1, h->aThtb.p, (long)nt * R2,
+                 0.0, h->aThgb.p, (long)nt * R2));
+    TT_TRY(dgemm(s, false, false, (int)nc, R1, o1, 1.0, h->aXb.p, o1, rc.P[0].p, R1, 0.0,
+                 h->aXgb.p, R1));
+
+    // (4) grown angular cores (block-diagonal with the term factors), reversed
+    fill(s, h->aThbi.p, (size_t)r1 * nt * r2, 0.0);
+    fill(s, h->aPhbi.p, (size_t)r2 * np, 0.0);
+    grown_angular_adjoint(s, ang, g.ndim, r1, r2, h->aThgb.p, h->aPhgb.p, R1, R2, h->aThbi.p,
+                          h->aPhbi.p);
+
+    // (5) source stage and the quartic, reversed per cell
+    grown_thbar(s, ang, g.ndim, true, r1, r2, rc.Th.p, rc.Ph.p, h->atb2.p);
+    source_adjoint_rows(s, g, h->fields, r1, rc.X.p, r1, h->atb2.p, rc.T.p, h->aXgb.p, R1,
+                        h->aEsb.p, h->aTb.p, h->aybar.p, h->aY.p, nr, h->aEsbo.p, h->aTbi.p,
+                        h->asigb.p);
+
+    // (6) E* = y . thbar / c: the quadrature vectors' adjoint
+    TT_TRY(dgemm(s, true, false, nr, 1, (int)nc, 1.0 / c, h->aY.p, nr, h->aEsbo.p, 1, 0.0,
+                 h->athbb.p, 1));
+    thbar_adjoint(s, ang, nterms, 0, r1, r2, rc.Th.p, rc.Ph.p, h->athbb.p, h->ascr.p, h->aThbi.p,
+                  h->aPhbi.p);
+
+    // (7) the transport stencil, transposed
+    stencil_adjoint_rows(s, g, h->fields, r1, h->aybar.p, nr, h->aXbi.p, r1);
+    TT_CUDA_TRY(cudaGetLastError());
+    std::swap(h->aXb, h->aXbi);
+    std::swap(h->aThb, h->aThbi);
+    std::swap(h->aPhb, h->aPhbi);
+    std::swap(h->aTb, h->aTbi);
+    return TT_OK;
+}
+
+void clear_tape(tt_ctx* h) {
+    for (tt_ctx::StepRec* r : h->tape) {
+        r->release();
+        delete r;
+    }
+    h->tape.clear();
+    h->taping = false;
+    h->replay_rec = nullptr;
+    h->cur_rec = nullptr;
+}
+
+tt_status adjoint_run(tt_ctx* h, double* grad_dev, double* Q_host) {
+    cudaStream_t s = h->stream;
+    const long nc = h->grid.nc;
+    const int M = (int)h->tape.size();
+    if (M == 0) return fail(TT_ERR_STATE, "tt_sn_step_adjoint: no taped steps");
+    const int every = std::max(1, h->tape_every);
+    h->taping = false;
+    // the final state, restored after the replays
+    tt_ctx::StepRec fin;
+    fin.r1 = h->r[1];
+    fin.r2 = h->r[2];
+    TT_TRY(copy_dev(fin.X, h->core[0].p, (size_t)nc * fin.r1, s));
+    TT_TRY(copy_dev(fin.Th, h->core[1].p, (size_t)fin.r1 * h->ang.n_theta * fin.r2, s));
+    TT_TRY(copy_dev(fin.Ph, h->core[2].p, (size_t)fin.r2 * h->ang.n_phi, s));
+    TT_TRY(copy_dev(fin.T, h->f_T.p, (size_t)nc, s));
+    tt_status st = TT_OK;
+    do {
+        // adjoint of the final state: zero
+        if ((st = h->aXb.ensure((size_t)nc * fin.r1, s)) < 0) break;
+        if ((st = h->aThb.ensure((size_t)fin.r1 * h->ang.n_theta * fin.r2, s)) < 0) break;
+        if ((st = h->aPhb.ensure((size_t)fin.r2 * h->ang.n_phi, s)) < 0) break;
+        if ((st = h->aTb.ensure((size_t)nc, s)) < 0) break;
+        if ((st = h->asigb.ensure((size_t)nc, s)) < 0) break;
+        fill(s, h->aXb.p, (size_t)nc * fin.r1, 0.0);
+        fill(s, h->aThb.p, (size_t)fin.r1 * h->ang.n_theta * fin.r2, 0.0);
+        fill(s, h->aPhb.p, (size_t)fin.r2 * h->ang.n_phi, 0.0);
+        fill(s, h->aTb.p, (size_t)nc, 0.0);
+        fill(s, h->asigb.p, (size_t)nc, 0.0);
+        for (int seg_end = M; seg_end > 0 && st >= 0;) {
+            const int seg_start = ((seg_end - 1) / every) * every;
+            bool need = false;
+            for (int m = seg_start; m < seg_end; ++m)
+                need = need || !h->tape[m]->state || !h->tape[m]->proj;
+            if (need) {  // re-run the segment from its checkpoint, refilling the records
+                tt_ctx::StepRec* c0 = h->tape[seg_start];
+                if ((st = load_state(h, c0->X.p, c0->Th.p, c0->Ph.p, c0->T.p, c0->r1, c0->r2)) < 0)
+                    break;
+                for (int m = seg_start; m < seg_end && st >= 0; ++m) {
+                    tt_ctx::StepRec* rc = h->tape[m];
+                    const int forced[2] = {rc->o1, rc->o2};
+                    h->replay_rec = rc;
+                    h->rec_state = !rc->state;
+                    h->rec_proj = true;
+                    st = step_once(h, 0, forced, nullptr);
+                    h->replay_rec = nullptr;
+                    if (st >= 0 && (h->r[1] != rc->o1 || h->r[2] != rc->o2))
+                        st = fail(TT_ERR_STATE, "adjoint replay: ranks differ from the taped run");
+                }
+                if (st < 0) break;
+            }
+            for (int m = seg_end - 1; m >= seg_start && st >= 0; --m) {
+                const tt_ctx::StepRec* out = (m + 1 < M) ? h->tape[m + 1] : &fin;
+                st = reverse_step(h, *h->tape[m], out->X.p, out->Th.p, out->Ph.p);
+            }
+            if (every > 1)
+                for (int m = seg_start; m < seg_end; ++m) {
+                    if (m != seg_start) h->tape[m]->release_state();
+                    h->tape[m]->release_proj();
+                }
+            seg_end = seg_start;
+        }
+        if (st < 0) break;
+        if (grad_dev)
+            TT_CUDA_TRY(cudaMemcpyAsync(grad_dev, h->asigb.p, (size_t)nc * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, s));
+    } while (false);
+    tt_status st2 = load_state(h, fin.X.p, fin.Th.p, fin.Ph.p, fin.T.p, fin.r1, fin.r2);
+    if (st >= 0 && Q_host) {
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_Q, h->d_dbl + HD_Q, sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st >= 0 && Q_host) *Q_host = h->h_dbl[HD_Q];
+    fin.release();
+    clear_tape(h);
+    return st < 0 ? st : st2;
 }
 
 }  // namespace
@@ -776,9 +1088,55 @@ tt_status tt_sn_step(tt_handle h, int nsteps, tt_step_info* info) {
     return tt_sn_step_ex(h, nsteps, 0, nullptr, info);
 }
 
+tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
+    if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3)
+        return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs FP64 precision, one rounding "
+                                  "per step and no scattering");
+    clear_tape(h);
+    h->taping = true;
+    h->tape_every = checkpoint_every;
+    h->h_dbl[HD_Q] = 0.0;
+    TT_CUDA_TRY(cudaMemcpyAsync(h->d_dbl + HD_Q, h->h_dbl + HD_Q, sizeof(double),
+                                cudaMemcpyHostToDevice, h->stream));
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return TT_OK;
+}
+
+tt_status tt_tape_objective(tt_handle h, double* Q_host, int* steps_host) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    if (!Q_host) return fail(TT_ERR_ARG, "tt_tape_objective: null Q");
+    TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_Q, h->d_dbl + HD_Q, sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream));
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *Q_host = h->h_dbl[HD_Q];
+    if (steps_host) *steps_host = (int)h->tape.size();
+    return TT_OK;
+}
+
+tt_status tt_sn_step_adjoint(tt_handle h, double* grad_sigma_a_dev, double* Q_host) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    if (!h->taping && h->tape.empty()) return fail(TT_ERR_STATE, "tt_sn_step_adjoint: no tape");
+    tt_status st = adjoint_run(h, grad_sigma_a_dev, Q_host);
+    if (st < 0) return st;
+    return read_status(h);
+}
+
+tt_status tt_tape_clear(tt_handle h) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    clear_tape(h);
+    return TT_OK;
+}
+
 tt_status tt_round(tt_handle h, double eps, int max_rank, const int* forced, tt_step_info* info) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    clear_tape(h);  // a change of state outside a step ends the tape
     if (eps < 0.0) return fail(TT_ERR_ARG, "tt_round: eps < 0");
     if (forced)
         for (int k = 0; k < h->d - 1; ++k)
@@ -890,6 +1248,7 @@ tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len) {
 tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* ranks_host) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    clear_tape(h);  // a change of state outside a step ends the tape
     if (!cores_dev || !ranks_host) return fail(TT_ERR_ARG, "tt_set_cores: null argument");
     if (ranks_host[0] != 1 || ranks_host[h->d] != 1)
         return fail(TT_ERR_ARG, "tt_set_cores: ranks[0] and ranks[d] must be 1");
@@ -909,6 +1268,7 @@ tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* r
 tt_status tt_set_precision(tt_handle h, int precision) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    clear_tape(h);  // a change of state outside a step ends the tape
     if (precision != TT_FP64 && precision != TT_MIXED)
         return fail(TT_ERR_ARG, "tt_set_precision: precision must be TT_FP64 or TT_MIXED");
     h->precision = precision;
@@ -918,6 +1278,7 @@ tt_status tt_set_precision(tt_handle h, int precision) {
 tt_status tt_set_T(tt_handle h, const double* T_dev) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    clear_tape(h);  // a change of state outside a step ends the tape
     if (!T_dev) return fail(TT_ERR_ARG, "tt_set_T: null input");
     TT_CUDA_TRY(cudaMemcpyAsync(h->f_T.p, T_dev, h->grid.nc * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));

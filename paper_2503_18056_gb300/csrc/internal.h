@@ -175,6 +175,29 @@ void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, cons
                  bool update_T);
 // Isotropic initial intensity I = c a_r Tr^4 / 4 pi into X (nc x 1).
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X);
+// Adjoint form (reverse mode with the rounding's projections frozen).
+void source_adjoint_rows(cudaStream_t s, const Grid& g, const Fields& f, int r1, const double* X,
+                         long ldx, const double* thbar, const double* Tin, const double* Xgb,
+                         long ldgb, const double* Esb_in, const double* Tb_out, double* ybar,
+                         double* Y, long ldy, double* Esb_out, double* Tb_in, double* sigb);
+void stencil_adjoint_rows(cudaStream_t s, const Grid& g, const Fields& f, int r1, const double* ybar,
+                          long ldy, double* Xb, long ldxb);
+void grown_angular_adjoint(cudaStream_t s, const Angular& ang, int ndim, int r1, int r2,
+                           const double* Thgb, const double* Phgb, int R1, int R2, double* Thb,
+                           double* Phb);
+// Adds the adjoint of quadrature vectors thbar_j (j in [j0, nterms)) to Thb/Phb;
+// scratch holds 2 * nterms * r2 doubles.
+void thbar_adjoint(cudaStream_t s, const Angular& ang, int nterms, int j0, int r1, int r2,
+                   const double* Th, const double* Ph, const double* thbb, double* scratch,
+                   double* Thb, double* Phb);
+void escape_rows(cudaStream_t s, const Grid& g, double dt, int r, const double* X, long ldx,
+                 const double* thbar_terms, double* qcell, double* Xb, long ldxb, bool add_grad);
+void escape_thbb(cudaStream_t s, const Grid& g, double dt, int r, const double* X, long ldx,
+                 double* thbb);
+void energy_adjoint_rows(cudaStream_t s, long nc, int r, const double* thbar, double c,
+                         const double* cv, const double* Tb, double* Xb, long ldxb, double* e1b,
+                         double* Esb);
+void sum_into(cudaStream_t s, long n, const double* x, double* out);
 // totals[0] = sum E, totals[1] = sum cv T (deterministic two-pass reduction).
 void energy_totals(cudaStream_t s, long nc, const double* E, const double* cv, const double* T,
                    double* totals_dev, double* scratch /* >= 2*1024 doubles */);

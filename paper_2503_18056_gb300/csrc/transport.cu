@@ -123,6 +123,33 @@ __global__ void thbar_kernel(int nterms, int r1, int r2, int nt, const double* T
     }
 }
 
+// Neighbour rows of cell i along each axis (C order, axis 0 slowest):
+// nb[a][0] = lower, nb[a][1] = upper; -1 marks a zero ghost (vacuum edge),
+// periodic edges wrap (Sec. 4.5).
+__device__ __forceinline__ void cell_neighbours(const Grid& g, long i, long (&nb)[3][2]) {
+    long rem = i, stride = 1;
+    int coord[3] = {0, 0, 0};
+    for (int a = g.ndim - 1; a >= 0; --a) {
+        coord[a] = (int)(rem % g.n[a]);
+        rem /= g.n[a];
+    }
+    for (int a = g.ndim - 1; a >= 0; --a) {
+        const int ca = coord[a];
+        const int na = g.n[a];
+        long lo, hi;
+        if (g.bc[a] == TT_BC_PERIODIC) {
+            lo = i + (long)((ca == 0) ? (na - 1) : -1) * stride;
+            hi = i + (long)((ca == na - 1) ? -(na - 1) : 1) * stride;
+        } else {
+            lo = (ca == 0) ? -1 : i - stride;
+            hi = (ca == na - 1) ? -1 : i + stride;
+        }
+        nb[a][0] = lo;
+        nb[a][1] = hi;
+        stride *= na;
+    }
+}
+
 // Quartic of Sec. 3.2 on the increasing branch T >= T_b = -(4 gamma a_r)^(-1/3):
 // gamma a_r T^4 + T = rhs.  Newton from the upper bracket end; f is convex and
 // increasing there, so the iterates decrease monotonically onto the root.
@@ -162,29 +189,8 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     const int nterms = transport ? 1 + 2 * g.ndim : 1;
     for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < g.nc; i += warps) {
-        // cell coordinates (C order, axis 0 slowest) and neighbour rows (-1 = zero ghost)
         long nb[3][2];
-        long rem = i, stride = 1;
-        int coord[3] = {0, 0, 0};
-        for (int a = g.ndim - 1; a >= 0; --a) {
-            coord[a] = (int)(rem % g.n[a]);
-            rem /= g.n[a];
-        }
-        for (int a = g.ndim - 1; a >= 0; --a) {
-            const int ca = coord[a];
-            const int na = g.n[a];
-            long lo, hi;
-            if (g.bc[a] == TT_BC_PERIODIC) {
-                lo = i + (long)((ca == 0) ? (na - 1) : -1) * stride;
-                hi = i + (long)((ca == na - 1) ? -(na - 1) : 1) * stride;
-            } else {
-                lo = (ca == 0) ? -1 : i - stride;
-                hi = (ca == na - 1) ? -1 : i + stride;
-            }
-            nb[a][0] = lo;
-            nb[a][1] = hi;
-            stride *= na;
-        }
+        cell_neighbours(g, i, nb);
         double nu[3];
         for (int a = 0; a < g.ndim; ++a) nu[a] = f.c * f.dt / g.dx[a];
 
@@ -259,6 +265,303 @@ __global__ void init_iso_kernel(long nc, const double* Tr, double c, double a_r,
         const double t2 = Tr[i] * Tr[i];
         X[i] = c * a_r * t2 * t2 / FOUR_PI;
     }
+}
+
+// ------------------------------------------------------------------ adjoint
+// Reverse mode of the step with the rounding's projections frozen (the
+// adjoint form).  Names: Xb = adjoint of X, and so on.
+
+// Source stage and quadrature, reversed per cell (one warp per cell): from the
+// adjoint of the grown spatial core Xgb (nc x R1) and the adjoint of E* coming
+// from the temperature update (Esb_in), give ybar = adjoint of the transport
+// rows y (nc x nr), the rows Y themselves (for the quadrature adjoint), the
+// total adjoint of E* (Esb_out), the adjoint of the input temperature (Tb_in =
+// Tb_out + ...) and accumulate the sigma_a gradient.
+__global__ void __launch_bounds__(256)
+source_adjoint_kernel(Grid g, Fields f, int r1, const double* __restrict__ X, long ldx,
+                      const double* __restrict__ thbar, const double* __restrict__ Tin,
+                      const double* __restrict__ Xgb, long ldgb, const double* __restrict__ Esb_in,
+                      const double* __restrict__ Tb_out, double* __restrict__ ybar,
+                      double* __restrict__ Y, long ldy, double* __restrict__ Esb_out,
+                      double* __restrict__ Tb_in, double* __restrict__ sigb) {
+    const int lane = threadIdx.x & 31;
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    const int nterms = 1 + 2 * g.ndim;
+    const int nr = nterms * r1;
+    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < g.nc; i += warps) {
+        long nb[3][2];
+        cell_neighbours(g, i, nb);
+        double nu[3];
+        for (int a = 0; a < g.ndim; ++a) nu[a] = f.c * f.dt / g.dx[a];
+        double dot = 0.0, sb = 0.0;
+        const double* xg = Xgb + i * ldgb;
+        for (int col = lane; col < r1; col += 32) {
+            const double x0 = X[i * ldx + col];
+            dot += x0 * thbar[col];
+            sb += xg[col] * x0;
+            for (int a = 0; a < g.ndim; ++a) {
+                const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
+                const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
+                const double yp = -nu[a] * (x0 - xm), ym = -nu[a] * (xp - x0);
+                dot += yp * thbar[(1 + 2 * a) * r1 + col] + ym * thbar[(2 + 2 * a) * r1 + col];
+                sb += xg[(1 + 2 * a) * r1 + col] * yp + xg[(2 + 2 * a) * r1 + col] * ym;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        const double Es = dot / f.c;
+        const double ka = f.c * f.dt * f.sigma_a[i];
+        const double cv = f.cv[i];
+        const double Td = t_dagger(Tin[i], Es, ka, cv, f.a_r);
+        const double s = 1.0 / (1.0 + ka);
+        const double T3 = Td * Td * Td;
+        const double B = f.c * f.a_r * T3 * Td / FOUR_PI;
+        const double gamma = ka / ((1.0 + ka) * cv);
+        const double fp = 4.0 * gamma * f.a_r * T3 + 1.0;
+        const double eb = xg[nr];
+        // e = s k B, s = 1/(1+k); B = c a_r T^4 / 4 pi; T from the quartic
+        const double gB = eb * s * ka;
+        double gk = eb * s * s * B - sb * s * s;
+        const double gTd = gB * 4.0 * f.c * f.a_r * T3 / FOUR_PI;
+        const double gEs = Esb_in[i] + gTd * gamma / fp;
+        gk += gTd * (Es - f.a_r * T3 * Td) / fp * (s * s / cv);
+        for (int col = lane; col < r1; col += 32) {
+            const double x0 = X[i * ldx + col];
+            ybar[i * ldy + col] = s * xg[col] + gEs * thbar[col] / f.c;
+            Y[i * ldy + col] = x0;
+            for (int a = 0; a < g.ndim; ++a) {
+                const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
+                const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
+                const int cp = (1 + 2 * a) * r1 + col, cm = (2 + 2 * a) * r1 + col;
+                ybar[i * ldy + cp] = s * xg[cp] + gEs * thbar[cp] / f.c;
+                ybar[i * ldy + cm] = s * xg[cm] + gEs * thbar[cm] / f.c;
+                Y[i * ldy + cp] = -nu[a] * (x0 - xm);
+                Y[i * ldy + cm] = -nu[a] * (xp - x0);
+            }
+        }
+        if (lane == 0) {
+            Esb_out[i] = gEs;
+            Tb_in[i] = Tb_out[i] + gTd / fp;
+            sigb[i] += gk * f.c * f.dt;
+        }
+    }
+}
+
+// Transpose of the transport stencil: Xb_i from the adjoints of the rows y.
+// y_j[x+] = -nu (X_j - X_lo(j)), y_j[x-] = -nu (X_hi(j) - X_j): cell i collects
+// its own terms and those of the cells whose lower / upper neighbour it is.
+__global__ void __launch_bounds__(256)
+stencil_adjoint_kernel(Grid g, Fields f, int r1, const double* __restrict__ ybar, long ldy,
+                       double* __restrict__ Xb, long ldxb) {
+    const int lane = threadIdx.x & 31;
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < g.nc; i += warps) {
+        long nb[3][2];
+        cell_neighbours(g, i, nb);
+        for (int col = lane; col < r1; col += 32) {
+            double v = ybar[i * ldy + col];
+            for (int a = 0; a < g.ndim; ++a) {
+                const double nu = f.c * f.dt / g.dx[a];
+                const int cp = (1 + 2 * a) * r1 + col, cm = (2 + 2 * a) * r1 + col;
+                v += -nu * ybar[i * ldy + cp] + nu * ybar[i * ldy + cm];
+                if (nb[a][1] >= 0) v += nu * ybar[nb[a][1] * ldy + cp];
+                if (nb[a][0] >= 0) v -= nu * ybar[nb[a][0] * ldy + cm];
+            }
+            Xb[i * ldxb + col] = v;
+        }
+    }
+}
+
+// Grown angular cores reversed: Thb[a,l,b] += sum_j thfac_j[l] Thgb[j r1 + a, l, j r2 + b],
+// Phb[b,p] += sum_j phfac_j[p] Phgb[j r2 + b, p].
+__global__ void grown_theta_adjoint_kernel(int nterms, int r1, int r2, int nt, const double* Thgb,
+                                           int R1, int R2, const double* mu, const double* sint,
+                                           double* Thb) {
+    const long total = (long)r1 * nt * r2;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(t % r2);
+        const int l = (int)((t / r2) % nt);
+        const int a = (int)(t / ((long)r2 * nt));
+        double v = 0.0;
+        for (int j = 0; j < nterms; ++j)
+            v += TermFactors::th(j, l, mu, sint) * Thgb[((long)(j * r1 + a) * nt + l) * R2 + j * r2 + b];
+        Thb[t] += v;
+    }
+}
+
+__global__ void grown_phi_adjoint_kernel(int nterms, int r2, int np, const double* Phgb,
+                                         const double* cphi, const double* sphi, double* Phb) {
+    const long total = (long)r2 * np;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int p = (int)(t % np), b = (int)(t / np);
+        double v = 0.0;
+        for (int j = 0; j < nterms; ++j) v += TermFactors::ph(j, p, cphi, sphi) * Phgb[(long)(j * r2 + b) * np + p];
+        Phb[t] += v;
+    }
+}
+
+// Quadrature vectors reversed (thbar_j[a] = w sum_l thf_j sum_b Th[a,l,b] phibar_j[b],
+// phibar_j[b] = v sum_p phf_j Ph[b,p]): given thbb (nterms x r1, scaled by sgn_j),
+// add to Thb and Phb.  phibar (nterms x r2) and phibb (nterms x r2) are scratch.
+__global__ void thbar_adjoint_theta_kernel(int j0, int nterms, int r1, int r2, int nt,
+                                           const double* thbb, const double* phibar,
+                                           const double* mu, const double* sint, double w,
+                                           double* Thb) {
+    const long total = (long)r1 * nt * r2;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(t % r2);
+        const int l = (int)((t / r2) % nt);
+        const int a = (int)(t / ((long)r2 * nt));
+        double v = 0.0;
+        for (int j = j0; j < nterms; ++j)
+            v += TermFactors::th(j, l, mu, sint) * thbb[j * r1 + a] * phibar[j * r2 + b];
+        Thb[t] += w * v;
+    }
+}
+
+__global__ void thbar_adjoint_phibb_kernel(int j0, int nterms, int r1, int r2, int nt,
+                                           const double* thbb, const double* Th, const double* mu,
+                                           const double* sint, double w, double* phibb) {
+    const int total = nterms * r2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int j = t / r2, b = t % r2;
+        double v = 0.0;
+        if (j >= j0)
+            for (int a = 0; a < r1; ++a) {
+                const double q = thbb[j * r1 + a];
+                if (q == 0.0) continue;
+                double inner = 0.0;
+                for (int l = 0; l < nt; ++l)
+                    inner += TermFactors::th(j, l, mu, sint) * Th[((long)a * nt + l) * r2 + b];
+                v += q * inner;
+            }
+        phibb[t] = w * v;
+    }
+}
+
+__global__ void thbar_adjoint_phi_kernel(int j0, int nterms, int r2, int np, const double* phibb,
+                                         const double* cphi, const double* sphi, double v,
+                                         double* Phb) {
+    const long total = (long)r2 * np;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int p = (int)(t % np), b = (int)(t / np);
+        double acc = 0.0;
+        for (int j = j0; j < nterms; ++j) acc += TermFactors::ph(j, p, cphi, sphi) * phibb[j * r2 + b];
+        Phb[t] += v * acc;
+    }
+}
+
+// Escape-energy objective on the boundary faces of vacuum axes (Sec. 4.5): for
+// the high face of axis a the outward factor pair is term 1 + 2a (n_a^+), for
+// the low face it is minus term 2 + 2a (-n_a^-).  Per cell: q_i = sum over its
+// faces sgn dt dA_a X_i . thbar_j; Xb_i += sgn dt dA_a thbar_j.
+__global__ void __launch_bounds__(256)
+escape_rows_kernel(Grid g, double dt, int r, const double* __restrict__ X, long ldx,
+                   const double* __restrict__ thbar_terms, double* __restrict__ qcell,
+                   double* __restrict__ Xb, long ldxb, int add_grad) {
+    const int lane = threadIdx.x & 31;
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < g.nc; i += warps) {
+        long rem = i;
+        int coord[3] = {0, 0, 0};
+        for (int a = g.ndim - 1; a >= 0; --a) {
+            coord[a] = (int)(rem % g.n[a]);
+            rem /= g.n[a];
+        }
+        double q = 0.0;
+        for (int a = 0; a < g.ndim; ++a) {
+            if (g.bc[a] != TT_BC_VACUUM) continue;
+            double dA = 1.0;
+            for (int b2 = 0; b2 < g.ndim; ++b2)
+                if (b2 != a) dA *= g.dx[b2];
+            for (int side = 0; side < 2; ++side) {
+                const bool on = side ? (coord[a] == g.n[a] - 1) : (coord[a] == 0);
+                if (!on) continue;
+                const int j = side ? 1 + 2 * a : 2 + 2 * a;
+                const double wgt = (side ? 1.0 : -1.0) * dt * dA;
+                const double* tb = thbar_terms + j * r;
+                double dot = 0.0;
+                for (int col = lane; col < r; col += 32) {
+                    dot += X[i * ldx + col] * tb[col];
+                    if (add_grad) Xb[i * ldxb + col] += wgt * tb[col];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                q += wgt * dot;
+            }
+        }
+        if (lane == 0) qcell[i] = q;
+    }
+}
+
+// thbb_j[col] = sgn dt dA_a sum_{cells i on the face} X_i[col] (fixed order: one
+// block per (face, 32-column chunk) walking the face cells sequentially).
+__global__ void escape_thbb_kernel(Grid g, double dt, int r, const double* __restrict__ X, long ldx,
+                                   double* __restrict__ thbb) {
+    const int face = blockIdx.y;  // 2 * axis + side
+    const int a = face >> 1, side = face & 1;
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    if (a >= g.ndim || g.bc[a] != TT_BC_VACUUM || col >= r) return;
+    double dA = 1.0;
+    for (int b2 = 0; b2 < g.ndim; ++b2)
+        if (b2 != a) dA *= g.dx[b2];
+    const int j = side ? 1 + 2 * a : 2 + 2 * a;
+    const double wgt = (side ? 1.0 : -1.0) * dt * dA;
+    // enumerate the face cells: all coords with coord_a fixed
+    const long nface = g.nc / g.n[a];
+    double acc = 0.0;
+    for (long t = 0; t < nface; ++t) {
+        long rem = t, i = 0, stride = 1;
+        for (int b2 = g.ndim - 1; b2 >= 0; --b2) {
+            int cb;
+            if (b2 == a) {
+                cb = side ? g.n[a] - 1 : 0;
+            } else {
+                cb = (int)(rem % g.n[b2]);
+                rem /= g.n[b2];
+            }
+            i += (long)cb * stride;
+            stride *= g.n[b2];
+        }
+        acc += X[i * ldx + col];
+    }
+    thbb[j * r + col] = wgt * acc;
+}
+
+__global__ void energy_adjoint_kernel(long nc, int r, const double* __restrict__ thbar, double c,
+                                      const double* __restrict__ cv, const double* __restrict__ Tb,
+                                      double* __restrict__ Xb, long ldxb, double* __restrict__ e1b,
+                                      double* __restrict__ Esb) {
+    const int lane = threadIdx.x & 31;
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < nc; i += warps) {
+        const double E1b = -Tb[i] / cv[i];
+        for (int col = lane; col < r; col += 32) Xb[i * ldxb + col] += E1b * thbar[col] / c;
+        if (lane == 0) {
+            e1b[i] = E1b / c;
+            Esb[i] = Tb[i] / cv[i];
+        }
+    }
+}
+
+__global__ void sum_kernel(long n, const double* x, double* out) {
+    __shared__ double sh[256];
+    double a = 0.0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out += sh[0];
 }
 
 constexpr int RED_BLOCKS = 1024;
@@ -359,6 +662,81 @@ void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, cons
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X) {
     note_launch();
     init_iso_kernel<<<blocks_for(nc), 256, 0, s>>>(nc, Tr, c, a_r, X);
+}
+
+void source_adjoint_rows(cudaStream_t s, const Grid& g, const Fields& f, int r1, const double* X,
+                         long ldx, const double* thbar, const double* Tin, const double* Xgb,
+                         long ldgb, const double* Esb_in, const double* Tb_out, double* ybar,
+                         double* Y, long ldy, double* Esb_out, double* Tb_in, double* sigb) {
+    const int blocks = (int)std::max<long>(1, std::min<long>((g.nc + 7) / 8, 152L * 64));
+    note_launch();
+    source_adjoint_kernel<<<blocks, 256, 0, s>>>(g, f, r1, X, ldx, thbar, Tin, Xgb, ldgb, Esb_in,
+                                                 Tb_out, ybar, Y, ldy, Esb_out, Tb_in, sigb);
+}
+
+void stencil_adjoint_rows(cudaStream_t s, const Grid& g, const Fields& f, int r1, const double* ybar,
+                          long ldy, double* Xb, long ldxb) {
+    const int blocks = (int)std::max<long>(1, std::min<long>((g.nc + 7) / 8, 152L * 64));
+    note_launch();
+    stencil_adjoint_kernel<<<blocks, 256, 0, s>>>(g, f, r1, ybar, ldy, Xb, ldxb);
+}
+
+void grown_angular_adjoint(cudaStream_t s, const Angular& ang, int ndim, int r1, int r2,
+                           const double* Thgb, const double* Phgb, int R1, int R2, double* Thb,
+                           double* Phb) {
+    const int nterms = 1 + 2 * ndim;
+    note_launch();
+    grown_theta_adjoint_kernel<<<blocks_for((long)r1 * ang.n_theta * r2), 256, 0, s>>>(
+        nterms, r1, r2, ang.n_theta, Thgb, R1, R2, ang.mu, ang.sint, Thb);
+    note_launch();
+    grown_phi_adjoint_kernel<<<blocks_for((long)r2 * ang.n_phi), 256, 0, s>>>(
+        nterms, r2, ang.n_phi, Phgb, ang.cphi, ang.sphi, Phb);
+}
+
+void thbar_adjoint(cudaStream_t s, const Angular& ang, int nterms, int j0, int r1, int r2,
+                   const double* Th, const double* Ph, const double* thbb, double* scratch,
+                   double* Thb, double* Phb) {
+    double* phibar = scratch;                 // nterms * r2
+    double* phibb = scratch + nterms * r2;    // nterms * r2
+    note_launch();
+    phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph, ang.cphi,
+                                                               ang.sphi, ang.v, phibar);
+    note_launch();
+    thbar_adjoint_theta_kernel<<<blocks_for((long)r1 * ang.n_theta * r2), 256, 0, s>>>(
+        j0, nterms, r1, r2, ang.n_theta, thbb, phibar, ang.mu, ang.sint, ang.w, Thb);
+    note_launch();
+    thbar_adjoint_phibb_kernel<<<blocks_for((long)nterms * r2, 64), 64, 0, s>>>(
+        j0, nterms, r1, r2, ang.n_theta, thbb, Th, ang.mu, ang.sint, ang.w, phibb);
+    note_launch();
+    thbar_adjoint_phi_kernel<<<blocks_for((long)r2 * ang.n_phi), 256, 0, s>>>(
+        j0, nterms, r2, ang.n_phi, phibb, ang.cphi, ang.sphi, ang.v, Phb);
+}
+
+void escape_rows(cudaStream_t s, const Grid& g, double dt, int r, const double* X, long ldx,
+                 const double* thbar_terms, double* qcell, double* Xb, long ldxb, bool add_grad) {
+    const int blocks = (int)std::max<long>(1, std::min<long>((g.nc + 7) / 8, 152L * 64));
+    note_launch();
+    escape_rows_kernel<<<blocks, 256, 0, s>>>(g, dt, r, X, ldx, thbar_terms, qcell, Xb, ldxb,
+                                              add_grad ? 1 : 0);
+}
+
+void escape_thbb(cudaStream_t s, const Grid& g, double dt, int r, const double* X, long ldx,
+                 double* thbb) {
+    note_launch();
+    escape_thbb_kernel<<<dim3((r + 31) / 32, 6), 32, 0, s>>>(g, dt, r, X, ldx, thbb);
+}
+
+void energy_adjoint_rows(cudaStream_t s, long nc, int r, const double* thbar, double c,
+                         const double* cv, const double* Tb, double* Xb, long ldxb, double* e1b,
+                         double* Esb) {
+    const int blocks = (int)std::max<long>(1, std::min<long>((nc + 7) / 8, 152L * 64));
+    note_launch();
+    energy_adjoint_kernel<<<blocks, 256, 0, s>>>(nc, r, thbar, c, cv, Tb, Xb, ldxb, e1b, Esb);
+}
+
+void sum_into(cudaStream_t s, long n, const double* x, double* out) {
+    note_launch();
+    sum_kernel<<<1, 256, 0, s>>>(n, x, out);
 }
 
 void energy_totals(cudaStream_t s, long nc, const double* E, const double* cv, const double* T,

@@ -169,12 +169,22 @@ def gaussian_random_field(n, seed=0, corr=0.1, L=None):
     return (g - g.mean()) / g.std()
 
 
-def grf_problem(n=(128, 128), n_theta=32, n_phi=64, steps=20, eps=1e-6, max_rank=0, seed=0):
+def grf_problem(n=(128, 128), n_theta=32, n_phi=64, steps=20, eps=1e-6, max_rank=0, seed=0,
+                centre=None):
     """Adjoint workload: sigma_a = exp(g) with g a Gaussian random field (corr.
     length 0.1, seed), a Gaussian T pulse (peak 1, width 0.1, background 0.01)
-    in equilibrium, vacuum boundaries, CFL 0.5."""
+    in equilibrium, vacuum boundaries, CFL 0.5.  The pulse sits at 0.8 of the
+    last axis (0.5 of the others) by default, 0.15 + 1.5 widths from that face,
+    so part of it reaches the face within the run and the escape energy is not
+    only the background's."""
     p = problem("small_2d", n=n, n_theta=n_theta, n_phi=n_phi, eps=eps, bc=VACUUM,
                 max_rank=max_rank, steps=steps)
+    ndim = len(p["n"])
+    if centre is None:
+        centre = [0.5] * (ndim - 1) + [0.8]
+    centre = [c * p["L"][a] for a, c in enumerate(centre)]
+    p["T0"] = gaussian_pulse(p["n"], p["L"], 1.0, 0.1, 0.01, centre)
+    p["Tr0"] = p["T0"].copy()
     p["sigma_a"] = np.exp(gaussian_random_field(p["n"], seed=seed, corr=0.1))
     p["name"] = "grf_2d"
     return p
