@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-form leg")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint-form leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle stepping for --impl reference")
@@ -462,6 +464,13 @@ def main():
         print(json.dumps(line))
         return 0
 
+    if args.adjoint_only:
+        import torch
+
+        import paper_2503_18056_gb300 as ttsn
+
+        print(json.dumps({"adjoint": run_adjoint(args, torch, ttsn)}))
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist

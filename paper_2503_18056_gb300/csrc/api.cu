@@ -167,7 +167,7 @@ struct tt_ctx {
     bool rec_state = false, rec_proj = false;
     // reverse-sweep workspace
     DevBuf aXb, aXbi, aThb, aThbi, aPhb, aPhbi, aTb, aTbi, aXgb, aThgb, aPhgb, aThtb, aybar, aY,
-        aEsb, aEsbo, ae1b, asigb, athbb, ascr, atb1, atb2, aq;
+        aEsb, aEsbo, ae1b, asigb, athbb, ascr, atb1, atb2, aq, agv;
 
     // physics
     Grid grid{};
@@ -218,7 +218,7 @@ struct tt_ctx {
         }
         DevBuf* abufs[] = {&aXb, &aXbi, &aThb, &aThbi, &aPhb, &aPhbi, &aTb, &aTbi, &aXgb, &aThgb,
                            &aPhgb, &aThtb, &aybar, &aY, &aEsb, &aEsbo, &ae1b, &asigb, &athbb,
-                           &ascr, &atb1, &atb2, &aq};
+                           &ascr, &atb1, &atb2, &aq, &agv};
         for (DevBuf* b : abufs) b->release();
         for (auto& p : pending) {
             cudaEventDestroy(p.a);
@@ -719,7 +719,7 @@ tt_status reverse_step(tt_ctx* h, const tt_ctx::StepRec& rc, const double* Xo, c
     plain_thbar(s, ang, o1, o2, Tho, Pho, h->atb1.p);
     energy_adjoint_rows(s, nc, o1, h->atb1.p, c, h->f_cv.p, h->aTb.p, h->aXb.p, o1, h->ae1b.p,
                         h->aEsb.p);
-    TT_TRY(dgemm(s, true, false, o1, 1, (int)nc, 1.0, Xo, o1, h->ae1b.p, 1, 0.0, h->athbb.p, 1));
+    TT_TRY(gemv_t(s, nc, o1, 1.0, Xo, o1, h->ae1b.p, h->athbb.p, h->agv));
     thbar_adjoint(s, ang, 1, 0, o1, o2, Tho, Pho, h->athbb.p, h->ascr.p, h->aThb.p, h->aPhb.p);
 
     // (3) rounding with frozen factors, reversed
@@ -744,8 +744,7 @@ tt_status reverse_step(tt_ctx* h, const tt_ctx::StepRec& rc, const double* Xo, c
                         h->asigb.p);
 
     // (6) E* = y . thbar / c: the quadrature vectors' adjoint
-    TT_TRY(dgemm(s, true, false, nr, 1, (int)nc, 1.0 / c, h->aY.p, nr, h->aEsbo.p, 1, 0.0,
-                 h->athbb.p, 1));
+    TT_TRY(gemv_t(s, nc, nr, 1.0 / c, h->aY.p, nr, h->aEsbo.p, h->athbb.p, h->agv));
     thbar_adjoint(s, ang, nterms, 0, r1, r2, rc.Th.p, rc.Ph.p, h->athbb.p, h->ascr.p, h->aThbi.p,
                   h->aPhbi.p);
 

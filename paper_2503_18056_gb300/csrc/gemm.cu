@@ -158,6 +158,44 @@ __global__ void copy2d_kernel(int rows, int cols, const double* in, long ldi, do
     }
 }
 
+// out[j] = alpha sum_i A[i][j] v[i] for tall A (m x ncols, m >> ncols): block b
+// sums its chunk of rows for every column (row groups of the block split the
+// chunk and meet in shared memory in a fixed order), a second kernel adds the
+// block partials in block order -- deterministic, one pass over A.
+constexpr int GEMV_THREADS = 256;
+__global__ void __launch_bounds__(GEMV_THREADS)
+gemv_t_partial_kernel(long m, int ncols, const double* __restrict__ A, long lda,
+                      const double* __restrict__ v, long chunk, double* __restrict__ part) {
+    __shared__ double red[GEMV_THREADS];
+    const int cw = min(GEMV_THREADS, ((ncols + 31) / 32) * 32);
+    const int rg = GEMV_THREADS / cw;
+    const int t = threadIdx.x, c0 = t % cw, g = t / cw;
+    const long i0 = blockIdx.x * chunk, i1 = min(m, i0 + chunk);
+    for (int cb = 0; cb < ncols; cb += cw) {
+        const int col = cb + c0;
+        double acc = 0.0;
+        if (g < rg && col < ncols)
+            for (long i = i0 + g; i < i1; i += rg) acc += A[i * lda + col] * v[i];
+        red[t] = acc;
+        __syncthreads();
+        if (g == 0 && col < ncols) {
+            double s = red[c0];
+            for (int q = 1; q < rg; ++q) s += red[q * cw + c0];
+            part[(long)blockIdx.x * ncols + col] = s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void gemv_t_final_kernel(int nblk, int ncols, double alpha, const double* part,
+                                    double* out) {
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < ncols; col += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(long)b * ncols + col];
+        out[col] = alpha * s;
+    }
+}
+
 inline int grid_for(long total, int threads = 256) {
     long b = (total + threads - 1) / threads;
     return (int)std::max<long>(1, std::min<long>(b, 152L * 32));
@@ -304,6 +342,26 @@ void scale_rows(cudaStream_t s, int rows, int cols, const double* in, long ldi, 
     note_launch();
     scale_rows_kernel<<<grid_for((long)rows * cols), 256, 0, s>>>(rows, cols, in, ldi, v, mode,
                                                                  out, ldo);
+}
+
+tt_status gemv_t(cudaStream_t s, long m, int ncols, double alpha, const double* A, long lda,
+                 const double* v, double* out, DevBuf& scratch) {
+    if (ncols <= 0) return TT_OK;
+    if (m <= 0) {
+        fill(s, out, (size_t)ncols, 0.0);
+        return TT_OK;
+    }
+    // about 4 blocks per SM, at least 64 rows each
+    const long chunk = std::max<long>(64, (m + 152L * 4 - 1) / (152L * 4));
+    const int nblk = (int)((m + chunk - 1) / chunk);
+    TT_TRY(scratch.ensure((size_t)nblk * ncols, s));
+    note_launch();
+    gemv_t_partial_kernel<<<nblk, GEMV_THREADS, 0, s>>>(m, ncols, A, lda, v, chunk, scratch.p);
+    note_launch();
+    gemv_t_final_kernel<<<std::max(1, std::min(152, (ncols + 127) / 128)), 128, 0, s>>>(
+        nblk, ncols, alpha, scratch.p, out);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
 }
 
 void fill(cudaStream_t s, double* p, size_t n, double value) {

@@ -91,6 +91,10 @@ tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long 
 void scale_rows(cudaStream_t s, int rows, int cols, const double* in, long ldi, const double* v,
                 int mode, double* out, long ldo);
 void fill(cudaStream_t s, double* p, size_t n, double value);
+// out[j] = alpha sum_i A[i][j] v[i], A m x ncols (lda), m large: row-split with
+// a fixed-order reduction; scratch grows as needed.
+tt_status gemv_t(cudaStream_t s, long m, int ncols, double alpha, const double* A, long lda,
+                 const double* v, double* out, DevBuf& scratch);
 void copy2d(cudaStream_t s, int rows, int cols, const double* in, long ldi, double* out, long ldo);
 
 // ---------------------------------------------------------------- eigensolver (jacobi.cu)

@@ -105,21 +105,26 @@ __global__ void phibar_kernel(int nterms, int r2, int np, const double* Ph, cons
     }
 }
 
-// thbar[j r1 + a] = sum_l w thfac_j[l] sum_b Th[a][l][b] phibar[j][b]
+// thbar[j r1 + a] = sum_l w thfac_j[l] sum_b Th[a][l][b] phibar[j][b]: one warp
+// per output, lanes striding over the contiguous (l, b) block of row a.
 __global__ void thbar_kernel(int nterms, int r1, int r2, int nt, const double* Th,
                              const double* mu, const double* sint, double w, const double* phibar,
                              double* thbar) {
+    const int lane = threadIdx.x & 31;
     const int total = nterms * r1;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int len = nt * r2;
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total; t += warps) {
         const int j = t / r1, a = t % r1;
+        const double* row = Th + (long)a * len;
         double acc = 0.0;
-        for (int l = 0; l < nt; ++l) {
-            double inner = 0.0;
-            const double* row = Th + ((long)a * nt + l) * r2;
-            for (int b = 0; b < r2; ++b) inner += row[b] * phibar[j * r2 + b];
-            acc += TermFactors::th(j, l, mu, sint) * inner;
+        for (int idx = lane; idx < len; idx += 32) {
+            const int l = idx / r2, b = idx - l * r2;
+            acc += TermFactors::th(j, l, mu, sint) * row[idx] * phibar[j * r2 + b];
         }
-        thbar[t] = w * acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) thbar[t] = w * acc;
     }
 }
 
@@ -425,23 +430,26 @@ __global__ void thbar_adjoint_theta_kernel(int j0, int nterms, int r1, int r2, i
     }
 }
 
+// phibb[j r2 + b] = w sum_a thbb[j r1 + a] sum_l thfac_j[l] Th[a][l][b]: one warp
+// per output, lanes striding over (a, l).
 __global__ void thbar_adjoint_phibb_kernel(int j0, int nterms, int r1, int r2, int nt,
                                            const double* thbb, const double* Th, const double* mu,
                                            const double* sint, double w, double* phibb) {
+    const int lane = threadIdx.x & 31;
     const int total = nterms * r2;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total; t += warps) {
         const int j = t / r2, b = t % r2;
         double v = 0.0;
         if (j >= j0)
-            for (int a = 0; a < r1; ++a) {
-                const double q = thbb[j * r1 + a];
-                if (q == 0.0) continue;
-                double inner = 0.0;
-                for (int l = 0; l < nt; ++l)
-                    inner += TermFactors::th(j, l, mu, sint) * Th[((long)a * nt + l) * r2 + b];
-                v += q * inner;
+            for (int idx = lane; idx < r1 * nt; idx += 32) {
+                const int a = idx / nt, l = idx - a * nt;
+                v += thbb[j * r1 + a] * TermFactors::th(j, l, mu, sint) *
+                     Th[((long)a * nt + l) * r2 + b];
             }
-        phibb[t] = w * v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) phibb[t] = w * v;
     }
 }
 
@@ -631,7 +639,7 @@ void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, i
     phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph,
                                                                ang.cphi, ang.sphi, ang.v, phibar);
     note_launch();
-    thbar_kernel<<<blocks_for((long)nterms * r1, 64), 64, 0, s>>>(
+    thbar_kernel<<<blocks_for((long)nterms * r1 * 32, 128), 128, 0, s>>>(
         nterms, r1, r2, ang.n_theta, Th, ang.mu, ang.sint, ang.w, phibar, thbar);
 }
 
@@ -705,7 +713,7 @@ void thbar_adjoint(cudaStream_t s, const Angular& ang, int nterms, int j0, int r
     thbar_adjoint_theta_kernel<<<blocks_for((long)r1 * ang.n_theta * r2), 256, 0, s>>>(
         j0, nterms, r1, r2, ang.n_theta, thbb, phibar, ang.mu, ang.sint, ang.w, Thb);
     note_launch();
-    thbar_adjoint_phibb_kernel<<<blocks_for((long)nterms * r2, 64), 64, 0, s>>>(
+    thbar_adjoint_phibb_kernel<<<blocks_for((long)nterms * r2 * 32, 128), 128, 0, s>>>(
         j0, nterms, r1, r2, ang.n_theta, thbb, Th, ang.mu, ang.sint, ang.w, phibb);
     note_launch();
     thbar_adjoint_phi_kernel<<<blocks_for((long)r2 * ang.n_phi), 256, 0, s>>>(
