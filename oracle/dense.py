@@ -12,7 +12,10 @@ written directly from its definitions with no tensor train involved:
   couple_a / couple_b, with T-dagger from ``quartic.t_dagger``;
 * temperature (Sec. 3.2, energy-conserving update): C_v (T^{m+1} - T^m) equals
   E* - E^{m+1}, where E* is the radiation energy entering the source stage
-  (the post-transport moment) and E^{m+1} the energy after it.
+  (the post-transport moment) and E^{m+1} the energy after it;
+* fixed external sources (optional): S = sum_k x_k(cell) theta_k(l) phi_k(p),
+  an inhomogeneous term of the transport equation taken explicitly with the
+  streaming, so the transport stage gives I* = L I + c dt S.
 
 The intensity array has shape (N_x[, N_y[, N_z]], N_theta, N_phi); spatial
 fields have shape (N_x[, N_y[, N_z]]).
@@ -28,7 +31,7 @@ VACUUM = 1
 
 class DenseSN:
     def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
-                 I0, sigma_s=None):
+                 I0, sigma_s=None, sources=None):
         self.ndim = len(n)
         self.n = tuple(n)
         self.dx = [L[a] / n[a] for a in range(self.ndim)]
@@ -43,6 +46,11 @@ class DenseSN:
         self.cv = np.array(cv, float).reshape(self.n)
         self.T = np.array(T0, float).reshape(self.n).copy()
         self.I = np.array(I0, float).reshape(self.n + (n_theta, n_phi)).copy()
+        # S[i..., l, p] = sum_k x_k[i...] theta_k[l] phi_k[p]
+        self.S = np.zeros_like(self.I)
+        for x, th, ph in (sources or []):
+            self.S += (np.asarray(x, float).reshape(self.n)[..., None, None]
+                       * np.outer(np.asarray(th, float), np.asarray(ph, float)))
 
     # -- Sec. 3 discrete energy density: E_i = (1/c) sum_lp I_ilp dOmega_lp
     def energy_density(self, I=None):
@@ -88,7 +96,7 @@ class DenseSN:
             hi[a] = slice(1, N + 1)   # F_{i+1/2}
             lo[a] = slice(0, N)       # F_{i-1/2}
             out -= (self.dt / self.dx[a]) * (F[tuple(hi)] - F[tuple(lo)])
-        return out
+        return out + self.c * self.dt * self.S
 
     def source(self, Istar):
         """Backward-Euler source stage (Eq. couple_a / couple_b); returns

@@ -22,6 +22,10 @@ the (N_x[, N_y[, N_z]]) grid, x slowest).  One time step:
 4. temperature: C_v (T^{m+1} - T^m) = E* - E^{m+1}, E^{m+1} integrated from the
    rounded TT, so that sum(E + C_v T) is conserved through the source stage
    and the rounding.
+
+Fixed external sources S = sum_k x_k (x) theta_k (x) phi_k (optional) enter
+the transport stage explicitly, I* = L I + c dt S: each is one more rank-one
+term of the TT sum, after the streaming terms.
 """
 import numpy as np
 
@@ -36,7 +40,7 @@ VACUUM = 1
 class TTSN:
     def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
                  cores, sigma_s=None, eps=0.0, max_rank=None,
-                 rounds_per_step=1, rounding="gram"):
+                 rounds_per_step=1, rounding="gram", sources=None):
         self.ndim = len(n)
         self.n = tuple(n)
         self.nc = int(np.prod(n))
@@ -53,6 +57,8 @@ class TTSN:
         self.eps, self.max_rank = eps, max_rank
         self.rounds_per_step = rounds_per_step
         self.rounding = rounding
+        self.sources = [(np.asarray(x, float).reshape(-1), np.asarray(th, float),
+                         np.asarray(ph, float)) for x, th, ph in (sources or [])]
         self.last_sigmas = []
         self.last_ranks = []
 
@@ -106,6 +112,8 @@ class TTSN:
             (tp, pp), (tm, pm) = self._masks(a)
             terms.append([(-nu * Dm)[None], Th * tp[None, :, None], Ph * pp[None, :, None]])
             terms.append([(-nu * Dp)[None], Th * tm[None, :, None], Ph * pm[None, :, None]])
+        for x, th, ph in self.sources:
+            terms.append(tt.rank_one([self.c * self.dt * x, th, ph]))
         return tt.add_many(terms)
 
     def energy_density(self, cores=None):
