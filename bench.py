@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-form leg")
+    ap.add_argument("--no-beams", action="store_true", help="skip the crossing-beam precision leg")
+    ap.add_argument("--beams-preroll", type=int, default=100)
+    ap.add_argument("--beams-steps", type=int, default=20)
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint-form leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
@@ -243,10 +246,71 @@ def run_ours(args, rank, world, local_rank):
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(args, torch, ttsn)
+    beams = None
+    if not args.no_beams:
+        beams = run_beams(args, torch, ttsn, fp64_peak, mixed["bf16_peak"] if mixed else None)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
-               adjoint=adjoint)
+               adjoint=adjoint, beams=beams)
     return res
+
+
+def run_beams(args, torch, ttsn, fp64_peak, bf16_peak):
+    """Precision form on the crossing-beam workload (256^2 cells, 64 x 128
+    ordinates, two collimated sources, eps 1e-5, ranks <= 96): P untimed FP64
+    steps into the crossing regime, then K_p FP64 steps and the same K_p steps
+    in the precision form from the same state at the FP64 ranks, each timed
+    with CUDA events on its handle's stream; E and T compared after them."""
+    p = workloads.crossing_beams()
+    stream = torch.cuda.Stream()
+    kp = args.beams_steps
+    with torch.cuda.stream(stream):
+        g = ttsn.TTSN.from_problem(p, stream=stream)
+        g.step(args.beams_preroll)
+        start = [c.clone() for c in g.cores()]
+        T0 = g.energy()[1].clone()
+        gm = ttsn.TTSN.from_problem(p, stream=stream, precision=ttsn.TT_MIXED)
+        gm.step(3)  # warm-up of the precision form's kernels
+        out = {}
+        ranks = []
+        for name, h in (("fp64", g), ("mixed", gm)):
+            h.set_cores(start)
+            h.set_T(T0)
+            torch.cuda.synchronize()
+            h.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(kp):
+                if name == "fp64":
+                    ranks.append(h.step()["ranks"][1:-1])
+                else:
+                    h.step(forced=ranks[k])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name] = (e0.elapsed_time(e1), h.profile_read())
+            h.profile(False)
+        E64, T64, _ = g.energy()
+        Em, Tm, _ = gm.energy()
+    upd = int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"]
+    v64 = kp / (out["fp64"][0] * 1e-3)
+    vmx = kp / (out["mixed"][0] * 1e-3)
+    gl = out["mixed"][1]["gram_left"]
+    roof = None
+    if gl["ms"] > 0 and bf16_peak:
+        ex = 21.0 * gl["flops"] / (gl["ms"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "gram_left (slgram_planes_kernel)", "achieved": ex,
+                "peak": bf16_peak, "unit": "TFLOP/s", "frac": ex / bf16_peak}
+    return {"workload": "crossing beams: 2D 256^2 cells, 64x128 ordinates, two collimated 4x4-cell "
+                        "sources (x=0 edge toward +x, y=0 edge toward +y, +-10 deg windows, strengths "
+                        "1 and 0.5), sigma_a 1e-3, T 1e-3, vacuum, eps 1e-5, ranks <= 96; steps %d..%d"
+                        % (args.beams_preroll + 1, args.beams_preroll + kp),
+            "fp64_steps_per_s": v64, "mixed_steps_per_s": vmx, "speedup": vmx / v64,
+            "fp64_updates_per_s": v64 * upd, "mixed_updates_per_s": vmx * upd,
+            "err_vs_fp64": {"E_max_rel": float((Em - E64).abs().max() / E64.abs().max()),
+                            "T_max_rel": float((Tm - T64).abs().max() / T64.abs().max())},
+            "ranks_last": ranks[-1],
+            "phases_ms": {n: {k: round(v["ms"], 3) for k, v in out[n][1].items()} for n in out},
+            "mixed_roofline": roof}
 
 
 def run_adjoint(args, torch, ttsn):
@@ -539,6 +603,8 @@ def main():
         line["batched"] = res["batched"]
     if res.get("adjoint") is not None:
         line["adjoint"] = res["adjoint"]
+    if res.get("beams") is not None:
+        line["beams"] = res["beams"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

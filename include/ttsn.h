@@ -31,6 +31,7 @@ extern "C" {
 #endif
 
 #define TT_MAX_D 8
+#define TT_MAX_SOURCES 16
 
 typedef struct tt_ctx* tt_handle;
 
@@ -192,6 +193,20 @@ tt_status tt_set_precision(tt_handle h, int precision);
 
 /* tt_set_T: replace the material temperature (N_c doubles, device). */
 tt_status tt_set_T(tt_handle h, const double* T_dev);
+
+/*
+ * tt_set_sources: fixed external sources S = sum_k x_k (x) theta_k (x) phi_k,
+ * k < count (0 <= count <= TT_MAX_SOURCES; 0 removes them), an inhomogeneous
+ * term of the transport equation (Sec. 3) taken explicitly with the
+ * streaming: every step's transport stage gives I* = L I + c dt S, and each
+ * source is one more rank-one term of the TT sum (the grown ranks become
+ * (1 + 2 ndim) r + count (+1 for the emission term)).  Device arrays, copied
+ * in: x_dev count x N_c (cell order as the fields), theta_dev count x n_theta,
+ * phi_dev count x n_phi, row-major.  Ends any adjoint tape; the adjoint form
+ * does not take sources (tt_tape_begin returns TT_ERR_STATE while any are set).
+ */
+tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const double* theta_dev,
+                         const double* phi_dev);
 
 /* tt_sync: wait for the handle's stream and report any latched device status. */
 tt_status tt_sync(tt_handle h);

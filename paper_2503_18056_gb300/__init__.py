@@ -183,7 +183,23 @@ class TTSN(_Handle):
     def from_problem(cls, p, **over):
         kw = cls.problem_kwargs(p)
         kw.update(over)
-        return cls(**kw)
+        obj = cls(**kw)
+        if p.get("sources"):
+            obj.set_sources(p["sources"])
+        return obj
+
+    def set_sources(self, sources):
+        """Fixed external sources: a list of (x (N_c), theta (n_theta), phi (n_phi))
+        array-likes, S = sum_k x_k (x) theta_k (x) phi_k added as c dt S per step."""
+        k = len(sources)
+        if k == 0:
+            check(lib.tt_set_sources(self._h, 0, None, None, None))
+            return
+        x = torch.stack([_dev(np.asarray(s[0]).reshape(-1), self.nc) for s in sources]).contiguous()
+        th = torch.stack([_dev(s[1], self.n_theta) for s in sources]).contiguous()
+        ph = torch.stack([_dev(s[2], self.n_phi) for s in sources]).contiguous()
+        check(lib.tt_set_sources(self._h, k, ctypes.c_void_p(x.data_ptr()),
+                                 ctypes.c_void_p(th.data_ptr()), ctypes.c_void_p(ph.data_ptr())))
 
     def step(self, nsteps=1, flags=0, forced=None):
         info = StepInfo()

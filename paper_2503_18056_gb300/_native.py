@@ -95,6 +95,7 @@ def _load():
         "tt_tape_objective": [vp, dp, ip],
         "tt_sn_step_adjoint": [vp, vp, dp],
         "tt_tape_clear": [vp],
+        "tt_set_sources": [vp, i, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -121,7 +122,7 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_set_precision", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma",
             "tt_bench_bf16_mma", "tt_batch_create", "tt_batch_step", "tt_batch_size",
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
-            "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear"]
+            "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

@@ -174,6 +174,8 @@ struct tt_ctx {
     Angular ang{};
     Fields fields{};
     DevBuf f_sigma_a, f_sigma_s, f_cv, f_T, f_Estar, f_E, thbar, red, ang_buf;
+    DevBuf src_x, src_th, src_ph, src_q;  // fixed external sources
+    int nsrc = 0;
     bool has_sigma_s = false;
     double eps = 0.0;
     int max_rank = 0;
@@ -209,7 +211,7 @@ struct tt_ctx {
         }
         DevBuf* bufs[] = {&slscratch, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
-                          &thbar, &red, &ang_buf};
+                          &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q};
         for (DevBuf* b : bufs) b->release();
         eig.release();
         for (StepRec* r : tape) {
@@ -358,8 +360,8 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             TT_TRY(h->GB[k].ensure((size_t)Ra * Ra, s));
             TT_TRY(dgemm(s, false, false, Ra * nn, Rb, Rb, 1.0, src[k + 1].p, Rb, h->GB[k + 1].p,
                          Rb, 0.0, h->bwd.p, Rb));
-            TT_TRY(dgemm(s, false, true, Ra, Ra, nn * Rb, 1.0, h->bwd.p, (long)nn * Rb,
-                         src[k + 1].p, (long)nn * Rb, 0.0, h->GB[k].p, Ra));
+            TT_TRY(dgemm_sk(s, false, true, Ra, Ra, nn * Rb, 1.0, h->bwd.p, (long)nn * Rb,
+                            src[k + 1].p, (long)nn * Rb, h->GB[k].p, Ra, h->partials));
         }
     }
     {
@@ -505,7 +507,15 @@ tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
     const int r1 = h->r[1], r2 = h->r[2];
     const int nterms = transport ? 1 + 2 * h->grid.ndim : 1;
     const int sc = source ? 1 : 0;
-    const int R1 = nterms * r1 + sc, R2 = nterms * r2 + sc;
+    Sources ext;
+    if (transport && h->nsrc > 0) {
+        ext.n = h->nsrc;
+        ext.x = h->src_x.p;
+        ext.th = h->src_th.p;
+        ext.ph = h->src_ph.p;
+        ext.q = h->src_q.p;
+    }
+    const int R1 = nterms * r1 + ext.n + sc, R2 = nterms * r2 + ext.n + sc;
     const long nc = h->grid.nc;
     const double fbytes = 8.0 * nc * ((source ? 4.0 : 0.0) + (h->has_sigma_s && source ? 1.0 : 0.0));
     PhaseScope ps(h, TT_PH_TRANSPORT, 0.0,
@@ -520,11 +530,11 @@ tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
                     h->thbar.p);
     }
     build_grown_angular(s, h->ang, h->grid.ndim, transport, source, r1, r2, h->core[1].p,
-                        h->core[2].p, h->gcore[1].p, h->gcore[2].p, R1, R2);
+                        h->core[2].p, h->gcore[1].p, h->gcore[2].p, R1, R2, ext);
     h->fields.T = h->f_T.p;
     h->fields.E_star = h->f_Estar.p;
     transport_source_rows(s, h->grid, h->fields, transport, source, r1, h->core[0].p, r1,
-                          source ? h->thbar.p : nullptr, h->gcore[0].p, R1);
+                          source ? h->thbar.p : nullptr, h->gcore[0].p, R1, ext);
     TT_CUDA_TRY(cudaGetLastError());
     h->gr[0] = 1;
     h->gr[1] = R1;
@@ -1091,9 +1101,9 @@ tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
     set_error("");
     TT_TRY(check_handle(h, true));
     if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
-    if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3)
+    if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0)
         return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs FP64 precision, one rounding "
-                                  "per step and no scattering");
+                                  "per step, no scattering and no external sources");
     clear_tape(h);
     h->taping = true;
     h->tape_every = checkpoint_every;
@@ -1261,6 +1271,50 @@ tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* r
     }
     for (int k = 0; k <= h->d; ++k) h->r[k] = ranks_host[k];
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return TT_OK;
+}
+
+tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const double* theta_dev,
+                         const double* phi_dev) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    if (count < 0 || count > TT_MAX_SOURCES)
+        return fail(TT_ERR_ARG, "tt_set_sources: count out of range");
+    if (count > 0 && (!x_dev || !theta_dev || !phi_dev))
+        return fail(TT_ERR_ARG, "tt_set_sources: null source array");
+    clear_tape(h);  // a change of state outside a step ends the tape
+    cudaStream_t s = h->stream;
+    const long nc = h->grid.nc;
+    const int nt = h->ang.n_theta, np = h->ang.n_phi;
+    h->nsrc = 0;
+    if (count == 0) return TT_OK;
+    TT_TRY(h->src_x.ensure((size_t)count * nc, s));
+    TT_TRY(h->src_th.ensure((size_t)count * nt, s));
+    TT_TRY(h->src_ph.ensure((size_t)count * np, s));
+    TT_TRY(h->src_q.ensure((size_t)count, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->src_x.p, x_dev, (size_t)count * nc * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->src_th.p, theta_dev, (size_t)count * nt * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->src_ph.p, phi_dev, (size_t)count * np * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    // q_k = (w sum_l theta_k[l]) (v sum_p phi_k[p]): the uniform weights factor
+    std::vector<double> th((size_t)count * nt), ph((size_t)count * np), q(count);
+    TT_CUDA_TRY(cudaMemcpyAsync(th.data(), theta_dev, th.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(ph.data(), phi_dev, ph.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = 0; k < count; ++k) {
+        double a = 0.0, b = 0.0;
+        for (int l = 0; l < nt; ++l) a += th[(size_t)k * nt + l];
+        for (int p = 0; p < np; ++p) b += ph[(size_t)k * np + p];
+        q[k] = (h->ang.w * a) * (h->ang.v * b);
+    }
+    TT_CUDA_TRY(cudaMemcpyAsync(h->src_q.p, q.data(), count * sizeof(double),
+                                cudaMemcpyHostToDevice, s));
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    h->nsrc = count;
     return TT_OK;
 }
 

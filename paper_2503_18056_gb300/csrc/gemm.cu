@@ -110,6 +110,18 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, lo
     }
 }
 
+// C[i][j] = alpha sum_z P[z][i][j] (fixed order => reproducible)
+__global__ void splitk_reduce_kernel(int M, int N, int ksplit, const double* __restrict__ P,
+                                     double alpha, double* C, long ldc) {
+    const long total = (long)M * N;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < ksplit; ++z) s += P[(long)z * total + t];
+        C[(t / N) * ldc + t % N] = alpha * s;
+    }
+}
+
 // G[i][j] = sum_z P[z][min(i,j)][max(i,j)]  (fixed order => reproducible, symmetric)
 __global__ void gram_reduce_kernel(int n, int ksplit, const double* __restrict__ P, double* G,
                                    long ldg) {
@@ -242,6 +254,31 @@ tt_status dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double al
     }
     return launch_gemm(s, ta, tb, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc,
                        strideC, batch, 1, K, 0, 0);
+}
+
+tt_status dgemm_sk(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                   const double* A, long lda, const double* B, long ldb, double* C, long ldc,
+                   DevBuf& scratch) {
+    const long tiles = (long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    // split K only where the tile grid leaves most SMs idle and K is long
+    int ks = 1;
+    if (tiles < 152 && K >= 8 * BK * 16) {
+        ks = (int)std::min<long>((456 + tiles - 1) / tiles, K / (8 * BK));
+        ks = std::max(1, std::min(ks, 64));
+    }
+    if (ks == 1 || M <= 0 || N <= 0)
+        return dgemm(s, ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, C, ldc);
+    int kchunk = (K + ks - 1) / ks;
+    kchunk = (kchunk + BK - 1) / BK * BK;
+    ks = (K + kchunk - 1) / kchunk;
+    const long per = (long)M * N;
+    TT_TRY(scratch.ensure((size_t)ks * per, s));
+    TT_TRY(launch_gemm(s, ta, tb, M, N, K, 1.0, A, lda, 0, B, ldb, 0, 0.0, scratch.p, N, 0, 1, ks,
+                       kchunk, per, 0));
+    note_launch();
+    splitk_reduce_kernel<<<grid_for(per), 256, 0, s>>>(M, N, ks, scratch.p, alpha, C, ldc);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
 }
 
 namespace {

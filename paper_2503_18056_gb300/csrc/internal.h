@@ -61,6 +61,13 @@ tt_status dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double al
                 const double* A, long lda, const double* B, long ldb, double beta, double* C,
                 long ldc, int batch = 1, long strideA = 0, long strideB = 0, long strideC = 0);
 
+// beta = 0 GEMM that splits K over CTAs (fixed-order reduction through
+// scratch) when the M x N tile grid alone would leave most SMs idle and K is
+// long; otherwise the plain dgemm.
+tt_status dgemm_sk(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                   const double* A, long lda, const double* B, long ldb, double* C, long ldc,
+                   DevBuf& scratch);
+
 // G = A^T A (A: m x n row-major, lda); split over rows with fixed-order reduction.
 // `partials` is scratch grown as needed (ksplit * n * n doubles).
 tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
@@ -142,11 +149,23 @@ struct Angular {
     double w, v;            // quadrature weights (uniform)
 };
 
+// Fixed external sources S = sum_k x_k (x) theta_k (x) phi_k (device arrays:
+// x n x N_c, th n x N_theta, ph n x N_phi, q n = the quadrature of each
+// angular profile, sum_lp theta_k[l] phi_k[p] dOmega_lp); n = 0: none.
+struct Sources {
+    int n = 0;
+    const double* x = nullptr;
+    const double* th = nullptr;
+    const double* ph = nullptr;
+    const double* q = nullptr;
+};
+
 // Build the grown angular cores for the TT sum of transport (+ source) terms.
-// nterms = 1 + 2 ndim if transport else 1; source adds one unit block.
+// nterms = 1 + 2 ndim if transport else 1; then one block per external source
+// (ext.n of them, transport only), and source adds one unit block.
 void build_grown_angular(cudaStream_t s, const Angular& ang, int ndim, bool transport,
                          bool source, int r1, int r2, const double* Th, const double* Ph,
-                         double* Thg, double* Phg, int R1, int R2);
+                         double* Thg, double* Phg, int R1, int R2, const Sources& ext = Sources());
 // thbar[a] = sum_l w thfac_j[l] sum_b Th[a,l,b] phibar_j[b] for the grown core
 // blocks (first nterms*r1 entries), phibar_j[b] = sum_p v phfac_j[p] Ph[b,p].
 void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, int r1, int r2,
@@ -170,9 +189,11 @@ struct Fields {
 // ld = ldg): transport blocks then (if source) scaled by s_i and the emission
 // column.  Computes E* (the post-transport energy) into fields.E_star when
 // source is set.  thbar: grown quadrature vector (nterms*r1 entries).
+// External sources (transport only) add columns nterms r1 + k = s_i c dt x_k[i]
+// and c dt x_k[i] q_k / c to E*; the emission column follows them.
 void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool transport,
                            bool source, int r1, const double* X, long ldx, const double* thbar,
-                           double* Xg, long ldg);
+                           double* Xg, long ldg, const Sources& ext = Sources());
 // E_i = X_i . thbar / c (r entries); if update_T: T_i += (E*_i - E_i) / cv_i.
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
                  double c, double* E_out, const double* E_star, const double* cv, double* T,

@@ -51,10 +51,12 @@ struct TermFactors {
     }
 };
 
-// Thg: (R1, nt, R2) with R1 >= nterms r1 (+1 if src), R2 >= nterms r2 (+1 if src)
+// Thg: (R1, nt, R2), R1 = nterms r1 + ns (+1 if src), R2 = nterms r2 + ns (+1 if
+// src): the term blocks, then one block per external source (its theta
+// profile), then the unit block of the emission term.
 __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, const double* Th,
-                                   const double* mu, const double* sint, double* Thg, int R1,
-                                   int R2) {
+                                   const double* mu, const double* sint, int ns,
+                                   const double* s_th, double* Thg, int R1, int R2) {
     const long total = (long)R1 * nt * R2;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
@@ -64,9 +66,12 @@ __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, 
         const int a = (int)(t2 / nt);
         double v = 0.0;
         const int ja = a / r1, jb = b / r2;
+        const int ka = a - nterms * r1, kb = b - nterms * r2;
         if (ja == jb && ja < nterms) {
             v = TermFactors::th(ja, l, mu, sint) *
                 Th[((long)(a - ja * r1) * nt + l) * r2 + (b - jb * r2)];
+        } else if (ka >= 0 && ka == kb && ka < ns) {
+            v = s_th[(long)ka * nt + l];
         } else if (src && a == R1 - 1 && b == R2 - 1) {
             v = 1.0;
         }
@@ -76,7 +81,8 @@ __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, 
 
 // Phg: (R2, np)
 __global__ void grown_phi_kernel(int nterms, int src, int r2, int np, const double* Ph,
-                                 const double* cphi, const double* sphi, double* Phg, int R2) {
+                                 const double* cphi, const double* sphi, int ns,
+                                 const double* s_ph, double* Phg, int R2) {
     const long total = (long)R2 * np;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
@@ -84,8 +90,11 @@ __global__ void grown_phi_kernel(int nterms, int src, int r2, int np, const doub
         const int b = (int)(t / np);
         double v = 0.0;
         const int jb = b / r2;
+        const int kb = b - nterms * r2;
         if (jb < nterms) {
             v = TermFactors::ph(jb, p, cphi, sphi) * Ph[(long)(b - jb * r2) * np + p];
+        } else if (kb >= 0 && kb < ns) {
+            v = s_ph[(long)kb * np + p];
         } else if (src && b == R2 - 1) {
             v = 1.0;
         }
@@ -183,64 +192,96 @@ __device__ double t_dagger(double Tm, double Estar, double ka, double Cv, double
     return T;
 }
 
-// One warp per cell.  Pass 1 computes the transport block values for the
-// quadrature dot product (E*), the source scalars follow, pass 2 recomputes and
-// writes the scaled values.
+// Row value of the transport terms of cell i at column col (the upwind
+// differences of Sec. 4.3 with the ghost rows of Sec. 4.5): the quadrature
+// dot product with thbar over all term blocks.
+__device__ __forceinline__ double transport_dot(const Grid& g, const double* nu, const long (&nb)[3][2],
+                                                int transport, int r1, const double* X, long ldx,
+                                                long i, int col, const double* thbar) {
+    const double x0 = X[i * ldx + col];
+    double dot = x0 * thbar[col];
+    if (transport)
+        for (int a = 0; a < g.ndim; ++a) {
+            const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
+            const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
+            dot += -nu[a] * (x0 - xm) * thbar[(1 + 2 * a) * r1 + col];
+            dot += -nu[a] * (xp - x0) * thbar[(2 + 2 * a) * r1 + col];
+        }
+    return dot;
+}
+
+// A warp takes G <= 32 consecutive cells.  Pass 1: for each cell the lanes split
+// the columns of the quadrature dot product (E*) and lane j keeps cell j's
+// sum; then every lane solves the source stage (quartic, s, e) of its own
+// cell, so the per-cell scalar FP64 work is done once, not once per lane.
+// Pass 2: for each cell the lanes write the scaled row, the external-source
+// columns and the emission column (scale and emission broadcast by shuffle).
 __global__ void __launch_bounds__(256)
 transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                         const double* __restrict__ X, long ldx, const double* __restrict__ thbar,
-                        double* __restrict__ Xg, long ldg) {
+                        Sources ext, double* __restrict__ Xg, long ldg, int G) {
     const int lane = threadIdx.x & 31;
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     const int nterms = transport ? 1 + 2 * g.ndim : 1;
-    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < g.nc; i += warps) {
-        long nb[3][2];
-        cell_neighbours(g, i, nb);
-        double nu[3];
-        for (int a = 0; a < g.ndim; ++a) nu[a] = f.c * f.dt / g.dx[a];
-
+    double nu[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < g.ndim; ++a) nu[a] = f.c * f.dt / g.dx[a];
+    for (long i0 = (blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5)) * G; i0 < g.nc;
+         i0 += warps * G) {
+        const int cnt = (int)min((long)G, g.nc - i0);
         double scale = 1.0, emit = 0.0;
         if (source) {
-            double dot = 0.0;
+            double mine = 0.0;
+            for (int j = 0; j < cnt; ++j) {
+                const long i = i0 + j;
+                long nb[3][2];
+                cell_neighbours(g, i, nb);
+                double dot = 0.0;
+                for (int col = lane; col < r1; col += 32)
+                    dot += transport_dot(g, nu, nb, transport, r1, X, ldx, i, col, thbar);
+                // external sources: c dt x_k[i] times their quadrature q_k
+                for (int k = lane; k < ext.n; k += 32)
+                    dot += f.c * f.dt * ext.x[(long)k * g.nc + i] * ext.q[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                if (lane == j) mine = dot;
+            }
+            if (lane < cnt) {
+                const long i = i0 + lane;
+                const double Estar = mine / f.c;
+                const double ka = f.c * f.dt * f.sigma_a[i];
+                const double ks = f.sigma_s ? f.c * f.dt * f.sigma_s[i] : 0.0;
+                const double Td = t_dagger(f.T[i], Estar, ka, f.cv[i], f.a_r);
+                const double Td2 = Td * Td;
+                const double B = f.c * f.a_r * Td2 * Td2 / FOUR_PI;
+                const double Jnew = (f.c * Estar / FOUR_PI + ka * B) / (1.0 + ka);
+                scale = 1.0 / (1.0 + ka + ks);
+                emit = scale * (ks * Jnew + ka * B);
+                f.E_star[i] = Estar;
+            }
+        }
+        for (int j = 0; j < cnt; ++j) {
+            const long i = i0 + j;
+            const double sc = __shfl_sync(0xffffffffu, scale, j);
+            const double em = __shfl_sync(0xffffffffu, emit, j);
+            long nb[3][2];
+            cell_neighbours(g, i, nb);
+            double* out = Xg + i * ldg;
             for (int col = lane; col < r1; col += 32) {
                 const double x0 = X[i * ldx + col];
-                dot += x0 * thbar[col];
+                out[col] = sc * x0;
                 if (transport) {
                     for (int a = 0; a < g.ndim; ++a) {
                         const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
                         const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-                        dot += -nu[a] * (x0 - xm) * thbar[(1 + 2 * a) * r1 + col];
-                        dot += -nu[a] * (xp - x0) * thbar[(2 + 2 * a) * r1 + col];
+                        out[(1 + 2 * a) * r1 + col] = sc * (-nu[a] * (x0 - xm));
+                        out[(2 + 2 * a) * r1 + col] = sc * (-nu[a] * (xp - x0));
                     }
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-            const double Estar = dot / f.c;
-            const double ka = f.c * f.dt * f.sigma_a[i];
-            const double ks = f.sigma_s ? f.c * f.dt * f.sigma_s[i] : 0.0;
-            const double Td = t_dagger(f.T[i], Estar, ka, f.cv[i], f.a_r);
-            const double Td2 = Td * Td;
-            const double B = f.c * f.a_r * Td2 * Td2 / FOUR_PI;
-            const double Jnew = (f.c * Estar / FOUR_PI + ka * B) / (1.0 + ka);
-            scale = 1.0 / (1.0 + ka + ks);
-            emit = scale * (ks * Jnew + ka * B);
-            if (lane == 0) f.E_star[i] = Estar;
+            for (int k = lane; k < ext.n; k += 32)
+                out[nterms * r1 + k] = sc * (f.c * f.dt * ext.x[(long)k * g.nc + i]);
+            if (source && lane == 0) out[nterms * r1 + ext.n] = em;
         }
-        double* out = Xg + i * ldg;
-        for (int col = lane; col < r1; col += 32) {
-            const double x0 = X[i * ldx + col];
-            out[col] = scale * x0;
-            if (transport) {
-                for (int a = 0; a < g.ndim; ++a) {
-                    const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
-                    const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-                    out[(1 + 2 * a) * r1 + col] = scale * (-nu[a] * (x0 - xm));
-                    out[(2 + 2 * a) * r1 + col] = scale * (-nu[a] * (xp - x0));
-                }
-            }
-        }
-        if (source && lane == 0) out[nterms * r1] = emit;
     }
 }
 
@@ -620,14 +661,15 @@ inline int blocks_for(long total, int threads = 256) {
 
 void build_grown_angular(cudaStream_t s, const Angular& ang, int ndim, bool transport,
                          bool source, int r1, int r2, const double* Th, const double* Ph,
-                         double* Thg, double* Phg, int R1, int R2) {
+                         double* Thg, double* Phg, int R1, int R2, const Sources& ext) {
     const int nterms = transport ? 1 + 2 * ndim : 1;
     note_launch();
     grown_theta_kernel<<<blocks_for((long)R1 * ang.n_theta * R2), 256, 0, s>>>(
-        nterms, source ? 1 : 0, r1, r2, ang.n_theta, Th, ang.mu, ang.sint, Thg, R1, R2);
+        nterms, source ? 1 : 0, r1, r2, ang.n_theta, Th, ang.mu, ang.sint, ext.n, ext.th, Thg,
+        R1, R2);
     note_launch();
     grown_phi_kernel<<<blocks_for((long)R2 * ang.n_phi), 256, 0, s>>>(
-        nterms, source ? 1 : 0, r2, ang.n_phi, Ph, ang.cphi, ang.sphi, Phg, R2);
+        nterms, source ? 1 : 0, r2, ang.n_phi, Ph, ang.cphi, ang.sphi, ext.n, ext.ph, Phg, R2);
 }
 
 // phibar scratch: thbar + nterms*r1 (caller allocates (nterms*(r1+r2)) doubles at thbar)
@@ -650,12 +692,15 @@ void plain_thbar(cudaStream_t s, const Angular& ang, int r1, int r2, const doubl
 
 void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool transport,
                            bool source, int r1, const double* X, long ldx, const double* thbar,
-                           double* Xg, long ldg) {
-    const long warps_needed = g.nc;
+                           double* Xg, long ldg, const Sources& ext) {
+    // cells per warp: up to 32 (the scalar source stage then fills every lane),
+    // fewer on small grids so that about 32 warps per SM stay busy
+    const int G = (int)std::max<long>(1, std::min<long>(32, g.nc / (152L * 32)));
+    const long warps_needed = (g.nc + G - 1) / G;
     const int blocks = (int)std::max<long>(1, std::min<long>((warps_needed + 7) / 8, 152L * 64));
     note_launch();
     transport_source_kernel<<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1, X,
-                                                   ldx, thbar, Xg, ldg);
+                                                   ldx, thbar, ext, Xg, ldg, G);
 }
 
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,

@@ -84,7 +84,7 @@ def test_untruncated_tt_step_with_sources_equals_dense(n, bc):
 def test_crossing_beams_workload_shape():
     p = workloads.crossing_beams(n=(32, 32), n_theta=16, n_phi=32)
     (x1, th1, ph1), (x2, th2, ph2) = p["sources"]
-    assert x1.sum() == 16 and x2.sum() == 16
+    assert x1.sum() == 16 and x2.sum() == 8
     assert x1[0:4, 14:18].all() and x2[14:18, 0:4].all()
     # theta window: mu within sin(10 deg) of 0; phi windows around 0 and 90 deg
     mu = -1 + (np.arange(16) + 0.5) / 8

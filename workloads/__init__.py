@@ -194,34 +194,42 @@ def cone_window(n_theta, n_phi, phi0, half_angle=10.0):
     """Angular window of a collimated source in (theta, phi) index space:
     1 on ordinates with |theta_l - 90 deg| <= half_angle and phi_p within
     half_angle of phi0 (degrees, circular), else 0 -- a (theta) x (phi)
-    product, so the source is rank one in angle."""
+    product, so the source is rank one in angle.  Where no ordinate lies
+    inside (coarse grids) the nearest ones (all at the least distance) are
+    taken."""
     mu = -1.0 + (np.arange(n_theta) + 0.5) * (2.0 / n_theta)
     theta = np.degrees(np.arccos(mu))
     phi = (np.arange(n_phi) + 0.5) * (360.0 / n_phi)
-    th = (np.abs(theta - 90.0) <= half_angle).astype(float)
-    d = np.abs((phi - phi0 + 180.0) % 360.0 - 180.0)
-    ph = (d <= half_angle).astype(float)
-    return th, ph
+    dth = np.abs(theta - 90.0)
+    dph = np.abs((phi - phi0 + 180.0) % 360.0 - 180.0)
+
+    def window(d):
+        lim = max(half_angle, d.min() + 1e-9)
+        return (d <= lim).astype(float)
+
+    return window(dth), window(dph)
 
 
 def crossing_beams(n=(256, 256), n_theta=64, n_phi=128, eps=1e-5, max_rank=96, steps=400,
-                   strength=1.0, half_angle=10.0):
+                   strength=(1.0, 0.5), half_angle=10.0):
     """Precision-form workload: two fixed collimated sources whose beams cross.
     Source 1: a 4x4-cell patch at the centre of the x = 0 edge emitting toward
     +x (phi0 = 0); source 2: a 4x4 patch at the centre of the y = 0 edge toward
     +y (phi0 = 90 deg); each isotropic inside a +-half_angle window in
-    (theta, phi) with intensity ``strength`` per unit length (added as
-    c dt S per step).  sigma_a = 1e-3 uniform, T = 1e-3 in equilibrium, C_v = 1,
-    vacuum, CFL 0.5, eps 1e-5, ranks <= 96."""
+    (theta, phi) with intensities ``strength`` (per unit length, added as
+    c dt S per step).  The unequal strengths break the x <-> y mirror symmetry,
+    which would otherwise pair the singular values and make a rank cut inside
+    a pair ambiguous.  sigma_a = 1e-3 uniform, T = 1e-3 in equilibrium,
+    C_v = 1, vacuum, CFL 0.5, eps 1e-5, ranks <= 96."""
     nx, ny = n
     p = problem("small_2d", n=n, n_theta=n_theta, n_phi=n_phi, eps=eps, bc=VACUUM,
                 max_rank=max_rank, steps=steps)
     T0 = np.full(n, 1e-3)
     p.update(T0=T0, Tr0=T0.copy(), sigma_a=np.full(n, 1e-3), name="crossing_beams")
     x1 = np.zeros(n)
-    x1[0:4, ny // 2 - 2:ny // 2 + 2] = strength
+    x1[0:4, ny // 2 - 2:ny // 2 + 2] = strength[0]
     x2 = np.zeros(n)
-    x2[nx // 2 - 2:nx // 2 + 2, 0:4] = strength
+    x2[nx // 2 - 2:nx // 2 + 2, 0:4] = strength[1]
     th1, ph1 = cone_window(n_theta, n_phi, 0.0, half_angle)
     th2, ph2 = cone_window(n_theta, n_phi, 90.0, half_angle)
     p["sources"] = [(x1, th1, ph1), (x2, th2, ph2)]
