@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--no-beams", action="store_true", help="skip the crossing-beam precision leg")
     ap.add_argument("--beams-preroll", type=int, default=100)
     ap.add_argument("--beams-steps", type=int, default=20)
-    ap.add_argument("--adjoint-only", action="store_true",
-                    help="run only the adjoint-form leg and print its JSON (profiling)")
+    ap.add_argument("--only", choices=["adjoint", "beams", "batch"], default=None,
+                    help="run only this companion leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle stepping for --impl reference")
@@ -528,12 +528,18 @@ def main():
         print(json.dumps(line))
         return 0
 
-    if args.adjoint_only:
+    if args.only:
         import torch
 
         import paper_2503_18056_gb300 as ttsn
 
-        print(json.dumps({"adjoint": run_adjoint(args, torch, ttsn)}))
+        if args.only == "adjoint":
+            out = run_adjoint(args, torch, ttsn)
+        elif args.only == "beams":
+            out = run_beams(args, torch, ttsn, ttsn.fp64_mma_peak(), ttsn.bf16_mma_peak())
+        else:
+            out = run_batch(args, torch, ttsn)
+        print(json.dumps({args.only: out}))
         return 0
     if world > 1:
         import torch

@@ -538,9 +538,10 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     TT_TRY(w.lam_unsorted.ensure((size_t)n, s));
     TT_TRY(w.abc.ensure((size_t)6 * npairs, s));
     TT_TRY(ensure_ctrl(w, s));
-    // about three row pairs per CTA, never more than MAX_PAIRS_PER_CTA
-    int want = std::max(1, (npairs + 2) / 3);
-    want = std::max(want, (npairs + MAX_PAIRS_PER_CTA - 1) / MAX_PAIRS_PER_CTA);
+    // one row pair per CTA where the GPU holds that many CTAs: a round's FP64
+    // work per CTA (about 18 n flops per owned pair) is what bounds the round
+    // on GB300's FP64 pipe, so the pairs are spread over as many SMs as exist
+    int want = npairs;
     size_t smem = (size_t)(npairs * 2 + 2 * MAX_PAIRS_PER_CTA * n) * sizeof(double);
     if (smem > 200 * 1024) {
         // fall back to the pairs-per-CTA bound the shared memory allows
