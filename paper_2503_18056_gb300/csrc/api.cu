@@ -402,7 +402,7 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         {
             PhaseScope ps(h, TT_PH_GRAM_LEFT, (double)m * Rk * (Rk + 1.0), 8.0 * ((double)m * Rk + (double)Rk * Rk));
             if (h->precision == TT_MIXED)
-                TT_TRY(slgram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
+                TT_TRY(slgram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials, h->d_int + HI_STATUS));
             else
                 TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
         }

@@ -89,7 +89,13 @@ tt_status bench_bf16_mma(cudaStream_t s, double* tflops);
 // Gram G = A^T A and product C = A B^T (slice.cu).  scratch grows as needed.
 size_t slgram_scratch_doubles(int m, int n);
 tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
-                 DevBuf& scratch);
+                 DevBuf& scratch, int* status_dev = nullptr);
+// The left Gram on tcgen05 tensor cores (7-digit split, exact 128-row level
+// sums, TMEM accumulators): what slgram runs.  status_dev (nullable) latches
+// DEV_TIMEOUT if a bounded wait ran out.
+size_t tcgram_scratch_doubles(int m, int n);
+tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
+                 DevBuf& scratch, int* status_dev);
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
                     long ldb, double* C, long ldc, DevBuf& scratch);
 

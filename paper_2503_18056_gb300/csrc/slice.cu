@@ -1,29 +1,30 @@
 // Mixed-precision contractions of the rounding (precision form): the left Gram
-// G = A^T A and the core update C = A B^T on the BF16 tensor pipe with exact
+// G = A^T A and the core update C = A B^T on the BF16 tensor cores with exact
 // split products, for the contractions App. A.4 names as the dominant cost.
 //
 // Split.  Each FP64 operand is scaled by a power of two per column (Gram: the
 // contraction runs over rows, so only columns may carry their own scale) or
-// per row (update: rows i of A and rows c of B are not summed), so every scaled
-// value lies in (-1, 1), and is cut into S signed base-256 digits:
-//   a = 2^e sum_{s<S} d_s 256^-(s+1) + r,   |r| <= 2^e 256^-S / 2,
-// balanced digits d_0 in [0, 256], d_1..d_5 in [-128, 127] (with a's sign).
-// Every digit is exact in BF16.  A digit product is at most 2^16 and exact in
-// FP32; the products of level w = s + t (weight 256^-(w+2)) summed over a
-// 32-row block stay below 2^22, so the FP32 block sums are exact; then
-// each block sum is scaled by 256^-w (exact) and added into a double-float
-// accumulator (hi + lo in FP32, TwoSum + renormalisation: about 48 bits).  Levels
-// with s + t >= S are dropped, so the result carries about 2^-8S relative to
-// the column (row) scale: 21 BF16 products for S = 6, accurate to ~1e-13 of
-// max|a| max|b| per term, against 2^-53 for FP64.  No FP64 arithmetic runs in
-// the inner loop (GB300's FP64 pipe is ~1/70 of its FP32 pipe).
+// per row (update: rows i of A and rows c of B are not summed) and cut into
+// signed digits that are exact in BF16, so every digit product is exact in
+// FP32.  Products of the same level w = s + t share the weight base^-(w+2);
+// summed over a block of rows they stay below 2^22, so the tensor cores' FP32
+// block sums are exact integers; each block sum is scaled by base^-w (exact)
+// and added into a double-float accumulator (hi + lo in FP32, TwoSum +
+// renormalisation: about 48 bits).  Levels w >= S are dropped, leaving about
+// 2^-48 of max|a| max|b| per term against 2^-53 for FP64.  No FP64 arithmetic
+// runs in the inner loops (GB300's FP64 pipe is ~1/70 of its FP32 pipe).
 //
-// Tiles: 64 x 64 outputs per CTA, four warps of 32 x 32, mma.sync m16n8k16
-// bf16 with FP32 accumulators, shared-memory digit tiles [S][64][32] per
-// operand (K-contiguous, XOR-swizzled for conflict-free fragment loads).  The Gram slices each
-// column once into digit planes in global memory and streams them with a
-// two-stage cp.async pipeline; the update GEMM produces digits on the fly
-// (its B operand is small and its A tile is read by few CTAs).
+// Core update (warp level): S = 6 base-256 digits (d_0 in [0, 256], d_1..d_5
+// in [-128, 127]), 21 products per term, exact sums over 32-row blocks;
+// 64 x 64 outputs per CTA, four warps of 32 x 32, mma.sync m16n8k16 bf16,
+// shared-memory digit tiles [S][64][32] per operand (K-contiguous,
+// XOR-swizzled), digits produced on the fly from the FP64 operands.
+//
+// Left Gram (tcgen05): S = 7 base-128 digits, 28 products per term, exact
+// sums over 128-row blocks, accumulators in tensor memory -- see the second
+// half of this file.
+#include <cuda.h>
+
 #include <algorithm>
 #include <atomic>
 
@@ -129,11 +130,6 @@ __global__ void col_max_kernel(int m, int n, const double* __restrict__ A, long 
     if (j < n)
         for (long i = r0 + rlane; i < r1; i += rstride) mx = fmax(mx, fabs(A[i * lda + j]));
     if (j < n && mx > 0.0) atomicMax(cmax + j, (unsigned long long)__double_as_longlong(mx));
-}
-
-__global__ void max_to_exp_kernel(int n, const unsigned long long* cmax, int* e) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        e[j] = exp_bound(__longlong_as_double((long long)cmax[j]));
 }
 
 __global__ void row_exp_kernel(long m, int n, const double* __restrict__ A, long lda, int* e) {
@@ -274,119 +270,6 @@ slgemm_nt_kernel(int M, int N, int K, const double* __restrict__ A, long lda,
             }
 }
 
-// Digit planes of the column-scaled operand: D[s][j][i] (n x mp, i contiguous),
-// rows i >= m padded with zero digits.  A CTA slices a 32 (i) x 64 (j) block,
-// coalesced along j on the FP64 read, and writes 64-byte runs along i through
-// a shared-memory transpose.
-__global__ void __launch_bounds__(256)
-slice_cols_kernel(int m, int n, long mp, const double* __restrict__ A, long lda,
-                  const int* __restrict__ ecol, unsigned short* __restrict__ D) {
-    __shared__ unsigned short t[SL_S][64][34];
-    const int j0 = blockIdx.x * 64;
-    for (long ib = blockIdx.y; ib < mp / 32; ib += gridDim.y) {
-    const long i0 = ib * 32;
-    __syncthreads();  // previous block's transpose reads are done
-    for (int idx = threadIdx.x; idx < 32 * 64; idx += blockDim.x) {
-        const int j = idx % 64, i = idx / 64;
-        const long gi = i0 + i;
-        const int gj = j0 + j;
-        const double v = (gi < m && gj < n) ? A[gi * lda + gj] : 0.0;
-        unsigned short d[SL_S];
-        digits(v, gj < n ? ecol[gj] : 0, d);
-#pragma unroll
-        for (int s = 0; s < SL_S; ++s) t[s][j][i] = d[s];
-    }
-    __syncthreads();
-    // write: for each (s, j), 32 consecutive i as 16 words of 2 digits
-    for (int idx = threadIdx.x; idx < SL_S * 64 * 16; idx += blockDim.x) {
-        const int w = idx % 16, j = (idx / 16) % 64, s = idx / (16 * 64);
-        const int gj = j0 + j;
-        if (gj >= n) continue;
-        const unsigned v = (unsigned)t[s][j][2 * w] | ((unsigned)t[s][j][2 * w + 1] << 16);
-        unsigned* dst = reinterpret_cast<unsigned*>(D + ((long)s * n + gj) * mp + i0) + w;
-        *dst = v;
-    }
-    }
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
-
-// Gram from digit planes: grid (T, T, ksplit) over upper tiles, 32-row blocks
-// streamed with a two-stage cp.async pipeline.  Stage layout: [2 operands]
-// SlTiles (64 x 40 bf16 rows, 16-byte aligned: 80-byte rows).
-__global__ void __launch_bounds__(SL_THREADS)
-slgram_planes_kernel(int n, long mp, const unsigned short* __restrict__ D,
-                     const int* __restrict__ ecol, int kchunk, double* __restrict__ partial) {
-    const int tn = blockIdx.x, tm = blockIdx.y, ks = blockIdx.z;
-    if (tn < tm) return;
-    extern __shared__ unsigned char smraw[];
-    SlTiles* stage = reinterpret_cast<SlTiles*>(smraw);  // [2 stages][2 operands]
-    const bool diag = (tn == tm);
-    const int J0 = tm * SL_BM, K0 = tn * SL_BN;
-    const long kbeg = (long)ks * kchunk;
-    const long kend = min(mp, kbeg + kchunk);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int nops = diag ? 1 : 2;
-    auto issue = [&](int st, long k0) {
-        // chunks: operand o, digit s, row r (64), 4 x 16 B along i
-        const int total = nops * SL_S * 64 * 4;
-        for (int c = tid; c < total; c += SL_THREADS) {
-            const int q = c & 3, r = (c >> 2) & 63, s = (c >> 8) % SL_S, o = c / (256 * SL_S);
-            const int gj = (o == 0 ? J0 : K0) + r;
-            SlTiles& T = stage[st * 2 + o];
-            unsigned short* dst = &T.d[s][r][swz_word(r, q * 4) << 1];
-            if (gj < n) {
-                cp_async16(dst, D + ((long)s * n + gj) * mp + k0 + q * 8);
-            } else {
-                *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-            }
-        }
-        cp_async_commit();
-    };
-    float hi[2][4][4], lo[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) hi[a][b][c] = lo[a][b][c] = 0.f;
-    if (kbeg < kend) issue(0, kbeg);
-    int st = 0;
-    for (long k0 = kbeg; k0 < kend; k0 += SL_BK) {
-        const bool more = k0 + SL_BK < kend;
-        if (more) issue(st ^ 1, k0 + SL_BK);
-        if (more) cp_async_wait<1>(); else cp_async_wait<0>();
-        __syncthreads();
-        const SlTiles& TJ = stage[st * 2];
-        const SlTiles& TK = diag ? stage[st * 2] : stage[st * 2 + 1];
-        block_products(TJ, TK, wm, wn, lane, hi, lo);
-        __syncthreads();
-        st ^= 1;
-    }
-    double* out = partial + (long)ks * n * n;
-    const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int j = J0 + wm + mi * 16 + g + (c >= 2 ? 8 : 0);
-                const int k = K0 + wn + ni * 8 + t4 * 2 + (c & 1);
-                if (j < n && k < n) {
-                    const double v = (double)hi[mi][ni][c] + (double)lo[mi][ni][c];
-                    out[(long)j * n + k] = ldexp(v, ecol[j] + ecol[k] - 16);
-                }
-            }
-}
-
 __global__ void slgram_reduce_kernel(int n, int ksplit, const double* __restrict__ P, double* G,
                                      long ldg) {
     const long total = (long)n * n;
@@ -398,29 +281,6 @@ __global__ void slgram_reduce_kernel(int n, int ksplit, const double* __restrict
         for (int z = 0; z < ksplit; ++z) s += P[(long)z * n * n + (long)a * n + b];
         G[(long)i * ldg + j] = s;
     }
-}
-
-long sl_resident() {
-    static std::atomic<long> cached{0};  // the same value from any thread
-    if (cached.load()) return cached.load();
-    int dev = 0, sms = 152, per = 1;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    (void)ensure_max_dynamic_smem((const void*)slgram_planes_kernel);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, slgram_planes_kernel, SL_THREADS,
-                                                      4 * sizeof(SlTiles)) != cudaSuccess || per < 1)
-        per = 1;
-    (void)cudaGetLastError();
-    cached.store((long)sms * per);
-    return cached.load();
-}
-
-int sl_ksplit(int m, int n) {
-    const long T = (n + SL_BN - 1) / SL_BN;
-    const long tiles = T * (T + 1) / 2;
-    long ks = std::max<long>(1, sl_resident() / tiles);
-    ks = std::min<long>(ks, std::max<long>(1, m / 256));
-    return (int)std::max<long>(1, std::min<long>(ks, 1024));
 }
 
 constexpr int BF16_PEAK_ITERS = 2048;
@@ -440,7 +300,516 @@ __global__ void __launch_bounds__(256) bf16_mma_peak_kernel(float* out, unsigned
     if (s == 1234.5f) out[threadIdx.x] = s;  // keeps the chains live
 }
 
+
+// ======================================================================
+// Left Gram on the 5th-generation tensor cores (tcgen05, TMEM, TMA).
+//
+// Split.  Column-scaled values |a| 2^-e < 1/2 are rounded to 48-bit fixed
+// point and cut into S7 = 7 balanced base-128 digits (d_0 in [0, 64],
+// d_1..d_6 in [-64, 63]), a = 2^e sum_s d_s 128^-(s+1); every digit is exact
+// in BF16 and |d_s d_t| <= 2^12.  The products of level w = s + t (weight
+// 128^-(w+2)) summed over a 128-row block stay below 128 * 7 * 2^12 < 2^22,
+// so the tensor core's FP32 sums of them are exact integers; levels w >= 7
+// are dropped (about 2^-48 of the column scales per term, as the 8-bit form).
+// Exact sums over 128 rows instead of 32 cut the double-float drain work
+// four-fold; that drain runs on the FP32 pipe and is what bounds the
+// warp-level (mma.sync) kernel above.
+//
+// Tile.  A CTA owns a 128 (columns j) x 64 (columns k) tile of G and a range
+// of rows.  Seven FP32 accumulators (one per level, 128 lanes x 64 columns
+// each, 448 of the 512 TMEM columns) receive, per 32-row stage, 28 digit-pair
+// products x 2 K-steps of tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+// M = 128, N = 64, K = 16) issued by one thread with operands described in
+// shared memory (K-major, 64-byte swizzle).  A TMA producer thread streams
+// the stages (all 7 digit planes of the tile's 128 + 64 columns in two
+// 3-D boxes per stage, double-buffered, mbarrier-tracked).  After every
+// 128-row block eight drain warps read the accumulators (tcgen05.ld, one TMEM
+// lane and half the columns per thread), scale level w by 128^-w and add into double-float
+// accumulators.  Every wait is bounded and latches DEV_TIMEOUT.
+constexpr int TC_S = 7;
+constexpr int TC_M = 128, TC_N = 64, TC_K = 32;
+constexpr int TC_BLK = 4;  // stages per exact block (128 rows)
+constexpr int TC_STAGES = 2;
+constexpr int TC_A_BYTES = TC_S * TC_M * TC_K * 2;  // 57344
+constexpr int TC_B_BYTES = TC_S * TC_N * TC_K * 2;  // 28672
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_THREADS = 320;  // warp 0 TMA, warp 1 TMEM + MMA, warps 2-9 drain
+constexpr int TC_DRAIN_WARPS = 8;
+constexpr int TC_DN = TC_N / 2;  // accumulator columns per drain thread
+constexpr unsigned TC_TMEM_COLS = 512;
+constexpr long long TC_SPIN = 1LL << 26;
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 /* barriers */ + 1024 /* align */;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned a, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false (and DEV_TIMEOUT latched) if it ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity, int* status) {
+    for (long long it = 0; it < TC_SPIN; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if (it > 32) __nanosleep(64);
+    }
+    if (status) atomicOr(status, DEV_TIMEOUT);
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const void* map, int c0, int c1, int c2,
+                                            unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row
+// groups 512 bytes apart (SBO); LBO is unused for K-major swizzled layouts
+// whose K-step (32 bytes) stays inside the 64-byte swizzle span.
+__device__ __forceinline__ unsigned long long tc_sdesc(unsigned addr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)(16u >> 4) << 16;
+    d |= (unsigned long long)(512u >> 4) << 32;
+    d |= 1ull << 46;  // descriptor version
+    d |= 4ull << 61;  // 64-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 64, M = 128.
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_N >> 3) << 17) |
+                              ((unsigned)(TC_M >> 4) << 24);
+__device__ __forceinline__ void tc_mma(unsigned d_tmem, unsigned long long a, unsigned long long b,
+                                       unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned mbar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+        : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane (no wait: the caller
+// issues tc_wait_ld before reading r).
+__device__ __forceinline__ void tc_ld16(unsigned taddr, unsigned (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Seven balanced base-128 digits of v 2^-e (|v| 2^-e < 1/2): |v| 2^(49-e) =
+// M 2^(ev - e - 3) is rounded to the integer F (< 2^48), written as
+// F = sum_s d_s 128^(6-s), digits carrying the sign of v, as BF16 bit patterns.
+__device__ __forceinline__ void digits7(double v, int e, unsigned short (&out)[TC_S]) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    unsigned long long F = 0ull;
+    if (ex != 0) {
+        const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int shift = e + 3 - (ex - 1023);
+        if (shift <= 0)
+            F = 1ull << 48;  // not reached when e bounds |v|
+        else if (shift < 55)
+            F = (M + (1ull << (shift - 1))) >> shift;
+    }
+    const unsigned short sign = (unsigned short)((bits >> 48) & 0x8000u);
+    int d[TC_S];
+#pragma unroll
+    for (int s = TC_S - 1; s >= 1; --s) {
+        int x = (int)(F & 0x7Full);
+        F >>= 7;
+        if (x >= 64) {
+            x -= 128;
+            F += 1;
+        }
+        d[s] = x;
+    }
+    d[0] = (int)F;  // 0 .. 64
+#pragma unroll
+    for (int s = 0; s < TC_S; ++s) {
+        const int x = d[s];
+        if (x == 0) {
+            out[s] = 0;
+        } else {
+            const unsigned short b = bf16_bits_of_int(x < 0 ? -x : x);
+            out[s] = (unsigned short)(b | (x < 0 ? (sign ^ 0x8000u) : sign));
+        }
+    }
+}
+
+// Column exponents for the 7-digit split: |v| < 2^(e-1).
+__global__ void max_to_exp7_kernel(int n, const unsigned long long* cmax, int* e) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        e[j] = exp_bound(__longlong_as_double((long long)cmax[j])) + 1;
+}
+
+// Digit planes D[s][j][i] (n x mp, i contiguous) of the 7-digit split, rows
+// i >= m zero; a CTA slices a 32 (i) x 64 (j) block through a shared-memory
+// transpose (writes of 64-byte runs along i).
+__global__ void __launch_bounds__(256)
+slice7_cols_kernel(int m, int n, long mp, const double* __restrict__ A, long lda,
+                   const int* __restrict__ ecol, unsigned short* __restrict__ D) {
+    __shared__ unsigned short t[TC_S][64][34];
+    const int j0 = blockIdx.x * 64;
+    for (long ib = blockIdx.y; ib < mp / 32; ib += gridDim.y) {
+        const long i0 = ib * 32;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 32 * 64; idx += blockDim.x) {
+            const int j = idx % 64, i = idx / 64;
+            const long gi = i0 + i;
+            const int gj = j0 + j;
+            const double v = (gi < m && gj < n) ? A[gi * lda + gj] : 0.0;
+            unsigned short d[TC_S];
+            digits7(v, gj < n ? ecol[gj] : 0, d);
+#pragma unroll
+            for (int s = 0; s < TC_S; ++s) t[s][j][i] = d[s];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < TC_S * 64 * 16; idx += blockDim.x) {
+            const int w = idx % 16, j = (idx / 16) % 64, s = idx / (16 * 64);
+            const int gj = j0 + j;
+            if (gj >= n) continue;
+            const unsigned v = (unsigned)t[s][j][2 * w] | ((unsigned)t[s][j][2 * w + 1] << 16);
+            unsigned* dst = reinterpret_cast<unsigned*>(D + ((long)s * n + gj) * mp + i0) + w;
+            *dst = v;
+        }
+    }
+}
+
+// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned a, unsigned parity, int* status,
+                                                   volatile int* abort_flag) {
+    for (long long it = 0; it < TC_SPIN; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if (*abort_flag) return false;
+        if (it > 32) __nanosleep(64);
+    }
+    if (status) atomicOr(status, DEV_TIMEOUT);
+    *abort_flag = 1;
+    return false;
+}
+
+// Tile t -> (jt, kt): the 128 x 64 tiles holding some j <= k (kt >= 2 jt),
+// enumerated row by row; jt = -1 past the end.
+__device__ __forceinline__ void tc_tile(int t, int KT, int& jt, int& kt) {
+    for (jt = 0;; ++jt) {
+        const int cnt = KT - 2 * jt;
+        if (cnt <= 0) {
+            jt = -1;
+            return;
+        }
+        if (t < cnt) {
+            kt = 2 * jt + t;
+            return;
+        }
+        t -= cnt;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tcgram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              int n, long mp, const int* __restrict__ ecol, long kchunk,
+              double* __restrict__ partial, int* status) {
+    extern __shared__ unsigned char tc_raw[];
+    const unsigned raw_s = smem_u32(tc_raw);
+    const unsigned pad = ((raw_s + 1023u) & ~1023u) - raw_s;
+    unsigned char* sbase = tc_raw + pad;
+    const unsigned sb = raw_s + pad;  // 1024-byte aligned: stage st at sb + st * TC_STAGE_BYTES
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbase + TC_STAGES * TC_STAGE_BYTES);
+    // bars: [0,1] stage full, [2,3] stage empty, [4] accumulators full, [5] accumulators
+    // drained, [6] all MMAs done
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 8);
+    volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 2);  // abort, issued, consumed
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int KT = (n + TC_N - 1) / TC_N;
+    int jt, kt;
+    tc_tile(blockIdx.x, KT, jt, kt);
+    if (jt < 0) return;
+    const int j0 = jt * TC_M, kc0 = kt * TC_N;
+    const long kbeg = (long)blockIdx.y * kchunk;
+    const long kend = min(mp, kbeg + kchunk);
+    const int nslices = kend > kbeg ? (int)((kend - kbeg) / TC_K) : 0;
+    double* out = partial + (long)blockIdx.y * n * n;
+    if (nslices == 0) {
+        for (int idx = threadIdx.x; idx < TC_M * TC_N; idx += blockDim.x) {
+            const int j = j0 + idx / TC_N, k = kc0 + idx % TC_N;
+            if (j < n && k < n) out[(long)j * n + k] = 0.0;
+        }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 7; ++i) mbar_init(smem_u32(&bars[i]), i == 5 ? (unsigned)TC_DRAIN_WARPS : 1u);
+        flags[0] = 0;
+        flags[1] = 0;
+        flags[2] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+    const int nblocks = (nslices + TC_BLK - 1) / TC_BLK;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            for (int it = 0; it < nslices; ++it) {
+                const int st = it % TC_STAGES;
+                const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
+                if (!mbar_wait_or_abort(smem_u32(&bars[2 + st]), ph ^ 1u, status, flags)) break;
+                const unsigned full = smem_u32(&bars[st]);
+                mbar_expect_tx(full, (unsigned)TC_STAGE_BYTES);
+                const unsigned dA = sb + (unsigned)(st * TC_STAGE_BYTES);
+                const int kx = (int)(kbeg + (long)it * TC_K);
+                tma_load_3d(dA, &tmA, kx, j0, 0, full);
+                tma_load_3d(dA + TC_A_BYTES, &tmB, kx, kc0, 0, full);
+                flags[1] = it + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            for (int it = 0; it < nslices; ++it) {
+                const int st = it % TC_STAGES;
+                const unsigned ph = (unsigned)(it / TC_STAGES) & 1u;
+                const int b = it / TC_BLK;
+                const bool first = (it % TC_BLK) == 0;
+                if (first && b > 0) {
+                    if (!mbar_wait_or_abort(smem_u32(&bars[5]), (unsigned)(b - 1) & 1u, status, flags))
+                        break;
+                    tc_fence_after();
+                }
+                if (!mbar_wait_or_abort(smem_u32(&bars[st]), ph, status, flags)) break;
+                tc_fence_after();
+                const unsigned aB = sb + (unsigned)(st * TC_STAGE_BYTES);
+                const unsigned bB = aB + TC_A_BYTES;
+                // A digit s outermost: consecutive MMAs share their A operand
+#pragma unroll 1
+                for (int s = 0; s < TC_S; ++s) {
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const unsigned long long ad =
+                            tc_sdesc(aB + (unsigned)(s * TC_M * TC_K * 2 + kk * 32));
+#pragma unroll 1
+                        for (int t = 0; t < TC_S - s; ++t) {
+                            const unsigned long long bd =
+                                tc_sdesc(bB + (unsigned)(t * TC_N * TC_K * 2 + kk * 32));
+                            // the first product of each level in a block overwrites
+                            const unsigned acc = (first && s == 0 && kk == 0) ? 0u : 1u;
+                            tc_mma(tmem + (unsigned)((s + t) * TC_N), ad, bd, acc);
+                        }
+                    }
+                }
+                tc_commit(smem_u32(&bars[2 + st]));  // the stage is free once these MMAs finish
+                flags[2] = it + 1;
+                if ((it % TC_BLK) == TC_BLK - 1 || it == nslices - 1) tc_commit(smem_u32(&bars[4]));
+            }
+            tc_commit(smem_u32(&bars[6]));  // every issued MMA done before teardown
+            mbar_wait(smem_u32(&bars[6]), 0u, status);
+        }
+    } else {  // drain warps: TMEM lanes 32 q .. 32 q + 31, columns c0 .. c0 + TC_DN - 1
+        const int q = warp & 3;
+        const int c0 = ((warp - 2) >> 2) * TC_DN;
+        float hi[TC_DN], lo[TC_DN];
+#pragma unroll
+        for (int c = 0; c < TC_DN; ++c) hi[c] = lo[c] = 0.f;
+        for (int b = 0; b < nblocks; ++b) {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bars[4]),
+                                                                      (unsigned)b & 1u, status, flags));
+            if (!ok) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int w = 0; w < TC_S; ++w) {
+                const float scale = __int_as_float((127 - 7 * w) << 23);  // 128^-w, exact
+                unsigned r[2][16];
+                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(w * TC_N + c0);
+                tc_ld16(ta, r[0]);
+                tc_ld16(ta + 16, r[1]);
+                tc_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        df_add(hi[16 * c + e], lo[16 * c + e], __uint_as_float(r[c][e]) * scale);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars[5]));
+        }
+        const int j = j0 + 32 * q + lane;
+        if (j < n && !flags[0]) {
+#pragma unroll
+            for (int c = 0; c < TC_DN; ++c) {
+                const int k = kc0 + c0 + c;
+                if (k < n)
+                    out[(long)j * n + k] =
+                        ldexp((double)hi[c] + (double)lo[c], ecol[j] + ecol[k] - 14);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // copies issued but never consumed (after an abort) land before the CTA exits
+        const int issued = flags[1], consumed = flags[2];
+        for (int it = consumed; it < issued; ++it)
+            mbar_wait(smem_u32(&bars[it % TC_STAGES]), (unsigned)(it / TC_STAGES) & 1u, status);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+int tc_tiles(int n) {
+    const int KT = (n + TC_N - 1) / TC_N;
+    int t = 0;
+    for (int jt = 0; KT - 2 * jt > 0; ++jt) t += KT - 2 * jt;
+    return t;
+}
+
+int tc_ksplit(int m, int n) {
+    const long mp = ((long)std::max(m, 1) + TC_K - 1) / TC_K * TC_K;
+    const long blocks = (mp + TC_K * TC_BLK - 1) / (TC_K * TC_BLK);
+    long ks = std::max(1L, 152L / tc_tiles(n));
+    return (int)std::max(1L, std::min(ks, blocks));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static std::atomic<EncodeTiledFn> fn{nullptr};
+    if (fn.load()) return fn.load();
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        p = nullptr;
+    (void)cudaGetLastError();
+    fn.store(reinterpret_cast<EncodeTiledFn>(p));
+    return fn.load();
+}
+
 }  // namespace
+
+size_t tcgram_scratch_doubles(int m, int n) {
+    const size_t mp = ((size_t)std::max(m, 1) + TC_K - 1) / TC_K * TC_K;
+    return ((size_t)tc_ksplit(std::max(m, 1), n) * n * n + 2 * (size_t)n + 8 + 127) / 128 * 128 +
+           (TC_S * (size_t)n * mp + 3) / 4;
+}
+
+tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
+                 DevBuf& scratch, int* status_dev) {
+    if (n <= 0) return TT_OK;
+    if (m <= 0) {
+        for (int i = 0; i < n; ++i) fill(s, G + (long)i * ldg, n, 0.0);
+        return TT_OK;
+    }
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) {
+        set_error("tcgram: cuTensorMapEncodeTiled is not available from the driver");
+        return TT_ERR_CUDA;
+    }
+    const int ks = tc_ksplit(m, n);
+    TT_TRY(scratch.ensure(tcgram_scratch_doubles(m, n), s));
+    double* partial = scratch.p;
+    unsigned long long* cmax = reinterpret_cast<unsigned long long*>(scratch.p + (size_t)ks * n * n);
+    int* ecol = reinterpret_cast<int*>(cmax + n);
+    TT_CUDA_TRY(cudaMemsetAsync(cmax, 0, n * sizeof(unsigned long long), s));
+    {
+        dim3 grid((n + 31) / 32, (unsigned)std::min<long>(std::max<long>(1, m / 4096), 256));
+        note_launch();
+        col_max_kernel<<<grid, 256, 0, s>>>(m, n, A, lda, cmax);
+        note_launch();
+        max_to_exp7_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cmax, ecol);
+    }
+    const long mp = ((long)m + TC_K - 1) / TC_K * TC_K;
+    // planes start on a 1024-byte boundary (TMA wants 16)
+    const size_t plane_off = ((size_t)ks * n * n + 2 * (size_t)n + 8 + 127) / 128 * 128;
+    unsigned short* planes = reinterpret_cast<unsigned short*>(scratch.p + plane_off);
+    {
+        dim3 grid((n + 63) / 64, (unsigned)std::min<long>(mp / 32, 16384));
+        note_launch();
+        slice7_cols_kernel<<<grid, 256, 0, s>>>(m, n, mp, A, lda, ecol, planes);
+    }
+    CUtensorMap mapA, mapB;
+    {
+        const cuuint64_t gdim[3] = {(cuuint64_t)mp, (cuuint64_t)n, (cuuint64_t)TC_S};
+        const cuuint64_t gstr[2] = {(cuuint64_t)mp * 2, (cuuint64_t)n * (cuuint64_t)mp * 2};
+        const cuuint32_t boxA[3] = {TC_K, TC_M, TC_S}, boxB[3] = {TC_K, TC_N, TC_S};
+        const cuuint32_t est[3] = {1, 1, 1};
+        CUresult r1 = enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes, gdim, gstr, boxA, est,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r2 = enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes, gdim, gstr, boxB, est,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+            set_error("tcgram: tensor map encoding failed");
+            return TT_ERR_CUDA;
+        }
+    }
+    {
+        long kchunk = (mp + ks - 1) / ks;
+        kchunk = (kchunk + TC_K * TC_BLK - 1) / (TC_K * TC_BLK) * (TC_K * TC_BLK);
+        TT_TRY(ensure_max_dynamic_smem((const void*)tcgram_kernel));
+        note_launch();
+        tcgram_kernel<<<dim3(tc_tiles(n), ks), TC_THREADS, TC_SMEM, s>>>(
+            mapA, mapB, n, mp, ecol, kchunk, partial, status_dev);
+        TT_CUDA_TRY(cudaGetLastError());
+    }
+    const long total = (long)n * n;
+    note_launch();
+    slgram_reduce_kernel<<<(int)std::min<long>((total + 255) / 256, 152L * 32), 256, 0, s>>>(
+        n, ks, partial, G, ldg);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
 
 tt_status bench_bf16_mma(cudaStream_t s, double* tflops) {
     int dev = 0, sms = 0;
@@ -471,57 +840,11 @@ tt_status bench_bf16_mma(cudaStream_t s, double* tflops) {
     return TT_OK;
 }
 
-size_t slgram_scratch_doubles(int m, int n) {
-    // split partials + per-column maxima (as 64-bit words) + exponents + digit planes
-    const size_t mp = ((size_t)std::max(m, 1) + SL_BK - 1) / SL_BK * SL_BK;
-    return ((size_t)sl_ksplit(std::max(m, 1), n) * n * n + 2 * (size_t)n + 8 + 31) / 32 * 32 +
-           (SL_S * (size_t)n * mp + 3) / 4;
-}
+size_t slgram_scratch_doubles(int m, int n) { return tcgram_scratch_doubles(m, n); }
 
 tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
-                 DevBuf& scratch) {
-    if (n <= 0) return TT_OK;
-    if (m <= 0) {
-        for (int i = 0; i < n; ++i) fill(s, G + (long)i * ldg, n, 0.0);
-        return TT_OK;
-    }
-    const int ks = sl_ksplit(m, n);
-    TT_TRY(scratch.ensure(slgram_scratch_doubles(m, n), s));
-    double* partial = scratch.p;
-    unsigned long long* cmax = reinterpret_cast<unsigned long long*>(scratch.p + (size_t)ks * n * n);
-    int* ecol = reinterpret_cast<int*>(cmax + n);
-    TT_CUDA_TRY(cudaMemsetAsync(cmax, 0, n * sizeof(unsigned long long), s));
-    {
-        dim3 grid((n + 31) / 32, (unsigned)std::min<long>(std::max<long>(1, m / 4096), 256));
-        note_launch();
-        col_max_kernel<<<grid, 256, 0, s>>>(m, n, A, lda, cmax);
-        note_launch();
-        max_to_exp_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cmax, ecol);
-    }
-    const long mp = ((long)m + SL_BK - 1) / SL_BK * SL_BK;
-    // digit planes start on a 256-byte boundary (cp.async moves 16-byte chunks)
-    const size_t plane_off = ((size_t)ks * n * n + 2 * (size_t)n + 8 + 31) / 32 * 32;
-    unsigned short* planes = reinterpret_cast<unsigned short*>(scratch.p + plane_off);
-    {
-        dim3 grid((n + 63) / 64, (unsigned)std::min<long>(mp / 32, 16384));
-        note_launch();
-        slice_cols_kernel<<<grid, 256, 0, s>>>(m, n, mp, A, lda, ecol, planes);
-    }
-    {
-        long kchunk = (mp + ks - 1) / ks;
-        kchunk = ((kchunk + SL_BK - 1) / SL_BK) * SL_BK;
-        const size_t smem = 4 * sizeof(SlTiles);
-        TT_TRY(ensure_max_dynamic_smem((const void*)slgram_planes_kernel));
-        const int T = (n + SL_BN - 1) / SL_BN;
-        note_launch();
-        slgram_planes_kernel<<<dim3(T, T, ks), SL_THREADS, smem, s>>>(n, mp, planes, ecol, (int)kchunk, partial);
-        TT_CUDA_TRY(cudaGetLastError());
-    }
-    const long total = (long)n * n;
-    note_launch();
-    slgram_reduce_kernel<<<(int)std::min<long>((total + 255) / 256, 152L * 32), 256, 0, s>>>(n, ks, partial, G, ldg);
-    TT_CUDA_TRY(cudaGetLastError());
-    return TT_OK;
+                 DevBuf& scratch, int* status_dev) {
+    return tcgram(s, m, n, A, lda, G, ldg, scratch, status_dev);
 }
 
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
