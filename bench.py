@@ -128,8 +128,10 @@ class ClockSampler:
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_median": statistics.median(pw) if pw else None}
 
 
 # ---------------------------------------------------------------- ours
@@ -200,12 +202,15 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             gm.profile(True)
             evm = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            mclocks = ClockSampler(local_rank)
             torch.cuda.synchronize()
+            mclocks.start()
             evm[0].record(stream)
             for k in range(args.steps):
                 gm.step(forced=ranks_hist[k])
                 evm[k + 1].record(stream)
             torch.cuda.synchronize()
+            mclk = mclocks.stop()
             mx_ms = evm[0].elapsed_time(evm[args.steps])
             mprof = gm.profile_read()
             gm.profile(False)
@@ -213,7 +218,7 @@ def run_ours(args, rank, world, local_rank):
             err_E = ((Em - E64).abs().max() / E64.abs().max()).item()
             err_T = ((Tm - T64).abs().max() / T64.abs().max()).item()
             mixed = dict(total_ms=mx_ms, step_ms=[evm[k].elapsed_time(evm[k + 1]) for k in range(args.steps)],
-                         prof=mprof, err_E=err_E, err_T=err_T, bf16_peak=bf16_peak)
+                         prof=mprof, err_E=err_E, err_T=err_T, bf16_peak=bf16_peak, clocks=mclk)
             del gm
             torch.cuda.synchronize()
 
@@ -607,7 +612,7 @@ def main():
             "dtype": "bf16 exact-split digits + fp32/double-float accumulation; fp64 eigensolves, decisions, T",
             "step_ms": [round(x, 3) for x in mx["step_ms"]],
             "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in mx["prof"].items()},
-            "roofline": mroof}
+            "clocks": mx.get("clocks"), "roofline": mroof}
     if res.get("batched") is not None:
         line["batched"] = res["batched"]
     if res.get("adjoint") is not None:

@@ -1,28 +1,28 @@
-// Mixed-precision contractions of the rounding (precision form): the left Gram
-// G = A^T A and the core update C = A B^T on the BF16 tensor cores with exact
-// split products, for the contractions App. A.4 names as the dominant cost.
+// Mixed-precision contractions of the rounding (precision form) on the
+// 5th-generation tensor cores: the left Gram G = A^T A and the core update
+// C = A B^T, for the contractions App. A.4 names as the dominant cost.
 //
 // Split.  Each FP64 operand is scaled by a power of two per column (Gram: the
 // contraction runs over rows, so only columns may carry their own scale) or
-// per row (update: rows i of A and rows c of B are not summed) and cut into
-// signed digits that are exact in BF16, so every digit product is exact in
-// FP32.  Products of the same level w = s + t share the weight base^-(w+2);
-// summed over a block of rows they stay below 2^22, so the tensor cores' FP32
-// block sums are exact integers; each block sum is scaled by base^-w (exact)
-// and added into a double-float accumulator (hi + lo in FP32, TwoSum +
-// renormalisation: about 48 bits).  Levels w >= S are dropped, leaving about
+// per row (update: rows i of A and rows c of B are not summed) so that
+// |a| 2^-e < 1/2, rounded to 48-bit fixed point and cut into S = 7 balanced
+// base-128 digits (d_0 in [0, 64], d_1..d_6 in [-64, 63]),
+//   a = 2^e sum_s d_s 128^-(s+1),
+// every digit exact in BF16 and every digit product (|d_s d_t| <= 2^12)
+// exact in FP32.  Products of the same level w = s + t share the weight
+// 128^-(w+2); summed over a block of 128 contraction indices they stay below
+// 128 * 7 * 2^12 < 2^22, so the tensor cores' FP32 block sums are exact
+// integers.  Each block sum is scaled by 128^-w (exact) and added into a
+// double-float accumulator (hi + lo in FP32, TwoSum + renormalisation: about
+// 48 bits).  Levels w >= 7 are dropped: 28 BF16 products per term, about
 // 2^-48 of max|a| max|b| per term against 2^-53 for FP64.  No FP64 arithmetic
 // runs in the inner loops (GB300's FP64 pipe is ~1/70 of its FP32 pipe).
 //
-// Core update (warp level): S = 6 base-256 digits (d_0 in [0, 256], d_1..d_5
-// in [-128, 127]), 21 products per term, exact sums over 32-row blocks;
-// 64 x 64 outputs per CTA, four warps of 32 x 32, mma.sync m16n8k16 bf16,
-// shared-memory digit tiles [S][64][32] per operand (K-contiguous,
-// XOR-swizzled), digits produced on the fly from the FP64 operands.
-//
-// Left Gram (tcgen05): S = 7 base-128 digits, 28 products per term, exact
-// sums over 128-row blocks, accumulators in tensor memory -- see the second
-// half of this file.
+// Both kernels keep seven per-level FP32 accumulators of a 128 x 64 output
+// tile in tensor memory (448 of 512 columns), issue tcgen05.mma (kind::f16,
+// BF16 x BF16 -> FP32, M = 128, N = 64, K = 16) from one thread with both
+// operands K-major in shared memory (64-byte swizzle), and drain the
+// accumulators with tcgen05.ld every 128 contraction indices.
 #include <cuda.h>
 
 #include <algorithm>
@@ -34,9 +34,6 @@ namespace ttsn {
 
 namespace {
 
-constexpr int SL_S = 6;           // digits per value
-constexpr int SL_BM = 64, SL_BN = 64, SL_BK = 32, SL_LD = 32;  // smem row = 32 bf16 = 64 B
-constexpr int SL_THREADS = 128;
 
 __device__ __forceinline__ unsigned short bf16_bits_of_int(int v) {
     // |v| <= 255: exact in bf16; take the top 16 bits of the fp32 value
@@ -64,53 +61,6 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     const float h2 = s + e;
     lo = e - (h2 - s);
     hi = h2;
-}
-
-// Digits of v * 2^-e (|v| 2^-e < 1) into out[0..S), from the bit pattern with
-// integer operations only.  |v| 2^(8S-e) = M 2^(ev-e-4) for S = 6 (M the 53-bit
-// significand) is rounded to the nearest integer F (a right shift by
-// e + 4 - ev >= 5 with rounding), then written in balanced base 256: digits
-// d_1..d_5 in [-128, 127] and d_0 in [0, 256], F = sum_s d_s 256^(5-s), all
-// carrying the sign of v.  Rounding and balanced digits make both the residual
-// and the dropped high-level products zero-mean, so they do not bias sums of
-// squares.  Every digit (|d| <= 256) is exact in BF16.  Subnormal inputs
-// (|v| < 2^-1022) contribute zero digits.
-__device__ __forceinline__ void digits(double v, int e, unsigned short (&out)[SL_S]) {
-    static_assert(SL_S == 6, "fixed-point width is 8 * SL_S = 48 bits");
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    unsigned long long F = 0ull;
-    if (ex != 0) {
-        const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int shift = e + 4 - (ex - 1023);
-        if (shift <= 0)
-            F = 1ull << 48;  // not reached when e bounds |v|; saturate at 2^48
-        else if (shift < 55)
-            F = (M + (1ull << (shift - 1))) >> shift;
-    }
-    const unsigned short sign = (unsigned short)((bits >> 48) & 0x8000u);
-    int d[SL_S];
-#pragma unroll
-    for (int s = SL_S - 1; s >= 1; --s) {
-        int x = (int)(F & 0xFFull);
-        F >>= 8;
-        if (x >= 128) {
-            x -= 256;
-            F += 1;
-        }
-        d[s] = x;
-    }
-    d[0] = (int)F;  // 0 .. 256
-#pragma unroll
-    for (int s = 0; s < SL_S; ++s) {
-        const int x = d[s];
-        if (x == 0) {
-            out[s] = 0;
-        } else {
-            const unsigned short b = bf16_bits_of_int(x < 0 ? -x : x);
-            out[s] = (unsigned short)(b | (x < 0 ? (sign ^ 0x8000u) : sign));
-        }
-    }
 }
 
 // Exponent e with |v| < 2^e for the largest |v| (0 for a zero maximum).
@@ -142,132 +92,6 @@ __global__ void row_exp_kernel(long m, int n, const double* __restrict__ A, long
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) e[i] = exp_bound(mx);
     }
-}
-
-// Shared-memory digit tiles: [S][64 rows][32] bf16, row = output index, col = K.
-// Rows are 64 bytes (16 words); 32-bit word w of row r is stored at word
-// w ^ 4 ((r >> 1) & 3), so the fragment loads of 8 rows x 4 words hit 32
-// distinct banks, and 16-byte chunks stay contiguous (the XOR is a multiple of
-// 4 words).
-struct SlTiles {
-    unsigned short d[SL_S][SL_BM][SL_LD];
-};
-__device__ __forceinline__ int swz_word(int r, int w) { return w ^ (((r >> 1) & 3) << 2); }
-__device__ __forceinline__ int swz_elem(int r, int k) { return (swz_word(r, k >> 1) << 1) | (k & 1); }
-__device__ __forceinline__ unsigned ld_word(const SlTiles& T, int s, int r, int k) {
-    return *reinterpret_cast<const unsigned*>(&T.d[s][r][swz_word(r, k >> 1) << 1]);
-}
-
-// Fragment loads and the 21 digit products of one 32-row block for a warp's
-// 32 x 32 sub-tile, drained level by level into the double-float accumulators.
-__device__ __forceinline__ void block_products(const SlTiles& TA, const SlTiles& TB, int wm, int wn,
-                                               int lane, float (&hi)[2][4][4], float (&lo)[2][4][4]) {
-    const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll 1
-    for (int w = 0; w < SL_S; ++w) {
-        float acc[2][4][4];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-#pragma unroll 1
-        for (int s = 0; s <= w; ++s) {
-            const int t = w - s;
-#pragma unroll
-            for (int kk = 0; kk < SL_BK; kk += 16) {
-                unsigned af[2][4], bfr[4][2];
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi) {
-                    const int r0 = wm + mi * 16 + g;
-                    const int c0 = kk + t4 * 2;
-                    af[mi][0] = ld_word(TA, s, r0, c0);
-                    af[mi][1] = ld_word(TA, s, r0 + 8, c0);
-                    af[mi][2] = ld_word(TA, s, r0, c0 + 8);
-                    af[mi][3] = ld_word(TA, s, r0 + 8, c0 + 8);
-                }
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) {
-                    const int nn = wn + ni * 8 + g;
-                    const int k0 = kk + t4 * 2;
-                    bfr[ni][0] = ld_word(TB, t, nn, k0);
-                    bfr[ni][1] = ld_word(TB, t, nn, k0 + 8);
-                }
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
-            }
-        }
-        const float scale = __int_as_float((127 - 8 * w) << 23);  // 256^-w, exact
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) df_add(hi[a][b][c], lo[a][b][c], acc[a][b][c] * scale);
-    }
-}
-
-// C (M x N) = A (M x K) B^T (B: N x K); both row-major FP64 with per-row exponents.
-__global__ void __launch_bounds__(SL_THREADS)
-slgemm_nt_kernel(int M, int N, int K, const double* __restrict__ A, long lda,
-                 const int* __restrict__ erowA, const double* __restrict__ B, long ldb,
-                 const int* __restrict__ erowB, double* __restrict__ C, long ldc) {
-    extern __shared__ unsigned char smraw[];
-    SlTiles& TA = *reinterpret_cast<SlTiles*>(smraw);
-    SlTiles& TB = *reinterpret_cast<SlTiles*>(smraw + sizeof(SlTiles));
-    const long M0 = (long)blockIdx.y * SL_BM;
-    const int N0 = blockIdx.x * SL_BN;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float hi[2][4][4], lo[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) hi[a][b][c] = lo[a][b][c] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += SL_BK) {
-        // element (row r, k): coalesced along k; stored [r][k]
-#pragma unroll 4
-        for (int it = 0; it < (SL_BK * SL_BM) / SL_THREADS; ++it) {
-            const int idx = tid + it * SL_THREADS;
-            const int kk = idx % SL_BK, r = idx / SL_BK;
-            const int gk = k0 + kk;
-            unsigned short da[SL_S], db[SL_S];
-            const long gr = M0 + r;
-            const double va = (gr < M && gk < K) ? A[gr * lda + gk] : 0.0;
-            digits(va, gr < M ? erowA[gr] : 0, da);
-            const int gc = N0 + r;
-            const double vb = (gc < N && gk < K) ? B[(long)gc * ldb + gk] : 0.0;
-            digits(vb, gc < N ? erowB[gc] : 0, db);
-            const int pk = swz_elem(r, kk);
-#pragma unroll
-            for (int s = 0; s < SL_S; ++s) {
-                TA.d[s][r][pk] = da[s];
-                TB.d[s][r][pk] = db[s];
-            }
-        }
-        __syncthreads();
-        block_products(TA, TB, wm, wn, lane, hi, lo);
-        __syncthreads();
-    }
-    const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const long i = M0 + wm + mi * 16 + g + (c >= 2 ? 8 : 0);
-                const int j = N0 + wn + ni * 8 + t4 * 2 + (c & 1);
-                if (i < M && j < N) {
-                    const double v = (double)hi[mi][ni][c] + (double)lo[mi][ni][c];
-                    C[i * ldc + j] = ldexp(v, erowA[i] + erowB[j] - 16);
-                }
-            }
 }
 
 __global__ void slgram_reduce_kernel(int n, int ksplit, const double* __restrict__ P, double* G,
@@ -702,6 +526,291 @@ tcgram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     }
 }
 
+// ----------------------------------------------------------------------
+// Core update C (M x N) = A (M x K) B^T on tcgen05, rows of A and B with their
+// own exponents (the contraction runs along rows).  Same 7-digit split,
+// exact 128-column level sums, seven TMEM accumulators per 128 x 64 tile and
+// one MMA-issuing thread as the Gram; A is sliced on the fly: eight warps
+// read 32 K-columns of the tile's 128 A rows per stage (coalesced FP64
+// loads, one stage ahead), write the digits in the MMA's 64-byte
+// swizzled K-major layout (16-byte chunk index XOR (row / 2) mod 4), make them
+// visible to the tensor core (fence.proxy.async) and, after every fourth stage,
+// drain the accumulators.  B (a few hundred rows) is sliced once beforehand
+// into ready-made shared-memory images, one bulk copy per stage.  A persistent
+// CTA walks (row block, column block) items.
+constexpr int TU_WORK_WARPS = 8;
+constexpr int TU_THREADS = 32 * (2 + TU_WORK_WARPS);  // warp 1 TMEM + MMA, warps 2-9 slice + drain
+constexpr size_t TU_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 + 1024;
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Byte offset of element (row r, k) in a swizzled K-major digit tile (64-byte rows).
+__device__ __forceinline__ unsigned tc_swz(int r, int k) {
+    return (unsigned)(r * 64 + ((((k >> 3) ^ ((r >> 1) & 3))) << 4) + (k & 7) * 2);
+}
+
+// B (N x K, per-row exponents) as ready-made shared-memory images: for n-block
+// nb and stage st the 7 digit tiles of rows nb*64 .. +63, columns st*32 .. +31,
+// each 64 rows x 64 bytes in the MMA's 64-byte swizzled K-major layout, so one
+// bulk copy per stage places them.  Bt[(nb * nst + st) * 7 + s] is one tile.
+__global__ void __launch_bounds__(256)
+slice7_btiles_kernel(int N, int K, int nst, const double* __restrict__ B, long ldb,
+                     const int* __restrict__ erowB, unsigned char* __restrict__ Bt) {
+    const int nbt = (N + TC_N - 1) / TC_N;
+    const long total = (long)nbt * nst * TC_N * TC_K;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(t % TC_K);
+        const int r = (int)((t / TC_K) % TC_N);
+        const long ts = t / ((long)TC_K * TC_N);  // nb * nst + st
+        const int st = (int)(ts % nst), nb = (int)(ts / nst);
+        const int c = nb * TC_N + r, kc = st * TC_K + k;
+        const double v = (c < N && kc < K) ? B[(long)c * ldb + kc] : 0.0;
+        unsigned short d[TC_S];
+        digits7(v, c < N ? erowB[c] + 1 : 0, d);
+        const unsigned off = tc_swz(r, k);
+#pragma unroll
+        for (int s = 0; s < TC_S; ++s)
+            *reinterpret_cast<unsigned short*>(Bt + (ts * TC_S + s) * (TC_N * TC_K * 2) + off) = d[s];
+    }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, unsigned bytes,
+                                              unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"((unsigned long long)src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(TU_THREADS, 1)
+tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
+             const int* __restrict__ erowA, const unsigned char* __restrict__ Bt,
+             const int* __restrict__ erowB, double* __restrict__ C, long ldc, int* status) {
+    extern __shared__ unsigned char tc_raw[];
+    const unsigned raw_s = smem_u32(tc_raw);
+    const unsigned pad = ((raw_s + 1023u) & ~1023u) - raw_s;
+    unsigned char* sbase = tc_raw + pad;
+    const unsigned sb = raw_s + pad;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbase + TC_STAGES * TC_STAGE_BYTES);
+    // bars: [0,1] stage's A digits written (8 slicing warps), [2,3] stage empty,
+    // [4] accumulators full, [5] accumulators drained, [6] all MMAs done,
+    // [7,8] stage's B tiles landed (bulk copy)
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 12);
+    volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 2);  // abort, issued, consumed
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long mblocks = (M + TC_M - 1) / TC_M;
+    const int nblk = (N + TC_N - 1) / TC_N;
+    const long items = mblocks * nblk;
+    const int nst = (K + TC_K - 1) / TC_K;  // stages per item
+    if ((long)blockIdx.x >= items) return;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 9; ++i)
+            mbar_init(smem_u32(&bars[i]), (i <= 1 || i == 5) ? (unsigned)TU_WORK_WARPS : 1u);
+        flags[0] = 0;
+        flags[1] = 0;
+        flags[2] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {  // B digit tiles: one bulk copy per stage
+            long g = 0;
+            bool stop = false;
+            for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
+                const int nb = (int)(item % nblk);
+                for (int it = 0; it < nst; ++it, ++g) {
+                    const int st = (int)(g % TC_STAGES);
+                    const unsigned ph = (unsigned)(g / TC_STAGES) & 1u;
+                    if (!mbar_wait_or_abort(smem_u32(&bars[2 + st]), ph ^ 1u, status, flags)) {
+                        stop = true;
+                        break;
+                    }
+                    const unsigned bfull = smem_u32(&bars[7 + st]);
+                    mbar_expect_tx(bfull, (unsigned)TC_B_BYTES);
+                    bulk_copy_g2s(sb + (unsigned)(st * TC_STAGE_BYTES + TC_A_BYTES),
+                                  Bt + ((long)nb * nst + it) * TC_B_BYTES, (unsigned)TC_B_BYTES, bfull);
+                    flags[1] = (int)(g + 1);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            long g = 0, gb = 0;  // stages and blocks issued by this CTA so far
+            bool stop = false;
+            for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
+                for (int it = 0; it < nst; ++it, ++g) {
+                    const int st = (int)(g % TC_STAGES);
+                    const unsigned ph = (unsigned)(g / TC_STAGES) & 1u;
+                    const bool first = (it % TC_BLK) == 0;
+                    if (first && gb > 0) {
+                        if (!mbar_wait_or_abort(smem_u32(&bars[5]), (unsigned)(gb - 1) & 1u, status, flags)) {
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    if (!mbar_wait_or_abort(smem_u32(&bars[st]), ph, status, flags) ||
+                        !mbar_wait_or_abort(smem_u32(&bars[7 + st]), ph, status, flags)) {
+                        stop = true;
+                        break;
+                    }
+                    flags[2] = (int)(g + 1);
+                    tc_fence_after();
+                    const unsigned aB = sb + (unsigned)(st * TC_STAGE_BYTES);
+                    const unsigned bB = aB + TC_A_BYTES;
+#pragma unroll 1
+                    for (int s = 0; s < TC_S; ++s) {
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const unsigned long long ad =
+                                tc_sdesc(aB + (unsigned)(s * TC_M * TC_K * 2 + kk * 32));
+#pragma unroll 1
+                            for (int t = 0; t < TC_S - s; ++t) {
+                                const unsigned long long bd =
+                                    tc_sdesc(bB + (unsigned)(t * TC_N * TC_K * 2 + kk * 32));
+                                const unsigned acc = (first && s == 0 && kk == 0) ? 0u : 1u;
+                                tc_mma(tmem + (unsigned)((s + t) * TC_N), ad, bd, acc);
+                            }
+                        }
+                    }
+                    tc_commit(smem_u32(&bars[2 + st]));
+                    if ((it % TC_BLK) == TC_BLK - 1 || it == nst - 1) {
+                        tc_commit(smem_u32(&bars[4]));
+                        ++gb;
+                    }
+                }
+            }
+            tc_commit(smem_u32(&bars[6]));
+            mbar_wait(smem_u32(&bars[6]), 0u, status);
+        }
+    } else if (warp >= 2) {  // slicing + drain warps
+        const int ww = warp - 2;        // 0..7
+        const int q = warp & 3;         // TMEM lane quarter
+        const int c0 = (ww >> 2) * TC_DN;
+        long g = 0, gb = 0;
+        bool stop = false;
+        // the next stage's A values, loaded while the tensor cores work on the
+        // current one (16 loads per thread in flight)
+        double va[16];
+#define TU_LOAD_STAGE(I0L, N0L, ITL)                                               \
+    do {                                                                           \
+        const int k_ = (ITL) * TC_K + lane;                                        \
+        _Pragma("unroll") for (int rr = 0; rr < 16; ++rr) {                        \
+            const long i_ = (I0L) + ww * 16 + rr;                                  \
+            va[rr] = (i_ < M && k_ < K) ? A[i_ * lda + k_] : 0.0;                  \
+        }                                                                          \
+    } while (0)
+        if ((long)blockIdx.x < items)
+            TU_LOAD_STAGE((blockIdx.x / nblk) * TC_M, (int)(blockIdx.x % nblk) * TC_N, 0);
+        for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
+            const long i0 = (item / nblk) * TC_M;
+            const int n0 = (int)(item % nblk) * TC_N;
+            float hi[TC_DN], lo[TC_DN];
+#pragma unroll
+            for (int c = 0; c < TC_DN; ++c) hi[c] = lo[c] = 0.f;
+            for (int it = 0; it < nst; ++it, ++g) {
+                const int st = (int)(g % TC_STAGES);
+                const unsigned ph = (unsigned)(g / TC_STAGES) & 1u;
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait_or_abort(smem_u32(&bars[2 + st]), ph ^ 1u, status, flags))) {
+                    stop = true;
+                    break;
+                }
+                unsigned char* sA = sbase + st * TC_STAGE_BYTES;
+                // A: rows 16 ww .. 16 ww + 15 of the tile, one column per lane
+#pragma unroll
+                for (int rr = 0; rr < 16; ++rr) {
+                    const int r = ww * 16 + rr;
+                    const long i = i0 + r;
+                    unsigned short d[TC_S];
+                    digits7(va[rr], i < M ? erowA[i] + 1 : 0, d);
+                    const unsigned off = tc_swz(r, lane);
+#pragma unroll
+                    for (int s = 0; s < TC_S; ++s)
+                        *reinterpret_cast<unsigned short*>(sA + s * (TC_M * TC_K * 2) + off) = d[s];
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars[st]));
+                {  // load the next stage (this item's next, or the next item's first) while
+                   // the tensor cores work on this one
+                    const long nitem = it + 1 < nst ? item : item + gridDim.x;
+                    if (nitem < items)
+                        TU_LOAD_STAGE((nitem / nblk) * TC_M, (int)(nitem % nblk) * TC_N,
+                                      it + 1 < nst ? it + 1 : 0);
+                }
+                if ((it % TC_BLK) == TC_BLK - 1 || it == nst - 1) {  // drain this block
+                    if (!__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bars[4]),
+                                                                     (unsigned)gb & 1u, status, flags))) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll 1
+                    for (int w = 0; w < TC_S; ++w) {
+                        const float scale = __int_as_float((127 - 7 * w) << 23);
+                        unsigned r2[2][16];
+                        const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(w * TC_N + c0);
+                        tc_ld16(ta, r2[0]);
+                        tc_ld16(ta + 16, r2[1]);
+                        tc_wait_ld();
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+#pragma unroll
+                            for (int e = 0; e < 16; ++e)
+                                df_add(hi[16 * c + e], lo[16 * c + e], __uint_as_float(r2[c][e]) * scale);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bars[5]));
+                    ++gb;
+                }
+            }
+            if (stop) break;
+            const long i = i0 + 32 * q + lane;
+            if (i < M && !flags[0]) {
+                const int ea = erowA[i] + 1;
+#pragma unroll
+                for (int c = 0; c < TC_DN; ++c) {
+                    const int col = n0 + c0 + c;
+                    if (col < N)
+                        C[i * ldc + col] = ldexp((double)hi[c] + (double)lo[c], ea + erowB[col] + 1 - 14);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // bulk copies issued but never consumed (after an abort) land before the CTA exits
+        const long issued = flags[1], consumed = flags[2];
+        for (long g2 = consumed; g2 < issued; ++g2)
+            mbar_wait(smem_u32(&bars[7 + g2 % TC_STAGES]), (unsigned)(g2 / TC_STAGES) & 1u, status);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+#undef TU_LOAD_STAGE
+
 int tc_tiles(int n) {
     const int KT = (n + TC_N - 1) / TC_N;
     int t = 0;
@@ -848,29 +957,38 @@ tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double
 }
 
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
-                    long ldb, double* C, long ldc, DevBuf& scratch) {
+                    long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev) {
     if (M <= 0 || N <= 0) return TT_OK;
     if (K <= 0) {
         for (long i = 0; i < M; ++i) fill(s, C + i * ldc, N, 0.0);
         return TT_OK;
     }
-    TT_TRY(scratch.ensure((size_t)(M + N + 1) / 2 + 2, s));
+    const int nst = (K + TC_K - 1) / TC_K;
+    const int nbt = (N + TC_N - 1) / TC_N;
+    const size_t e_dbl = ((size_t)(M + N + 1) / 2 + 2 + 15) / 16 * 16;  // exponents, 128-byte aligned
+    const size_t bt_bytes = (size_t)nbt * nst * TC_B_BYTES;
+    TT_TRY(scratch.ensure(e_dbl + bt_bytes / 8, s));
     int* eA = reinterpret_cast<int*>(scratch.p);
     int* eB = eA + M;
+    unsigned char* Bt = reinterpret_cast<unsigned char*>(scratch.p + e_dbl);
     note_launch();
     row_exp_kernel<<<(int)std::max<long>(1, std::min<long>((M + 7) / 8, 152L * 64)), 256, 0, s>>>(M, K, A, lda, eA);
     note_launch();
     row_exp_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, K, B, ldb, eB);
-    const size_t smem = 2 * sizeof(SlTiles);
-    TT_TRY(ensure_max_dynamic_smem((const void*)slgemm_nt_kernel));
-    const long gy = (M + SL_BM - 1) / SL_BM;
-    if (gy > 65535L) {
-        set_error("slgemm_nt: too many rows");
-        return TT_ERR_TOO_LARGE;
+    {
+        const long tot = (long)nbt * nst * TC_N * TC_K;
+        note_launch();
+        slice7_btiles_kernel<<<(int)std::min<long>((tot + 255) / 256, 152L * 16), 256, 0, s>>>(
+            N, K, nst, B, ldb, eB, Bt);
     }
+    int dev = 0, sms = 152;
+    TT_CUDA_TRY(cudaGetDevice(&dev));
+    TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long items = ((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
+    const int grid = (int)std::min<long>(items, sms);
+    TT_TRY(ensure_max_dynamic_smem((const void*)tcupd_kernel));
     note_launch();
-    slgemm_nt_kernel<<<dim3((N + SL_BN - 1) / SL_BN, (unsigned)gy), SL_THREADS, smem, s>>>(
-        (int)M, N, K, A, lda, eA, B, ldb, eB, C, ldc);
+    tcupd_kernel<<<grid, TU_THREADS, TU_SMEM, s>>>(M, N, K, A, lda, eA, Bt, eB, C, ldc, status_dev);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
 }
