@@ -75,11 +75,13 @@ enum {
  * Rounding (Sec. 4.2, App. A): relative Frobenius tolerance eps balanced over
  * the bonds, ranks capped at max_rank (<= 0: no cap); rounds_per_step = 1
  * rounds once after the source stage, 2 also rounds after transport.
- * precision: TT_FP64, or TT_MIXED for the precision form: the left Gram
- * matrices and the core updates A' = A P_A (the dominant contractions of
- * App. A.4) run on the BF16 tensor pipe with exact split products
- * (tt_gram_mixed); right Grams, eigensolves, rank decisions, the quartic and
- * the temperature update stay FP64.
+ * precision: TT_FP64, or TT_MIXED for the precision form: the Gram sweeps
+ * (left Grams, and the right-Gram products of all but the last core) and the
+ * core updates A' = A P_A (the dominant contractions of App. A.4) run on the
+ * BF16 tensor cores with exact split products (tt_gram_mixed,
+ * tt_gemm_nt_mixed: about 2^-48 of the operands' scales per term);
+ * eigensolves, rank decisions, the small R x R products, the quartic and the
+ * temperature update stay FP64.
  * The intensity is held in the paper's three-core layout (Eq. tensor_decomp):
  * X (1, N_c, r1), Theta (r1, n_theta, r2), Phi (r2, n_phi, 1).
  */
@@ -332,20 +334,22 @@ tt_status tt_syev(int n, const double* G_dev, int ldg, double* lam_dev, double* 
                   void* stream, int* sweeps_host);
 
 /*
- * tt_gram_mixed: G = A^T A (as tt_gram) on the BF16 tensor pipe.  Each column
- * of A is scaled by a power of two and cut into six signed 8-bit digits (exact
- * in BF16); digit products are exact in FP32, summed exactly over 32-row
- * blocks, and accumulated in double-float (about 48 bits); products of digit
- * levels s + t >= 6 are dropped.  Error about 2^-48 max|A_j| max|A_k| per row
- * term.  Device scratch (row splits x n x n doubles) is allocated per call.
+ * tt_gram_mixed: G = A^T A (as tt_gram) on the BF16 tensor cores (tcgen05).
+ * Each column of A is scaled by a power of two and cut into seven signed
+ * 7-bit digits (exact in BF16); digit products are exact in FP32, summed
+ * exactly over 128-row blocks in tensor memory, and accumulated in
+ * double-float (about 48 bits); products of digit levels s + t >= 7 are
+ * dropped.  Error about 2^-48 max|A_j| max|A_k| per row term.  Device scratch
+ * (row splits x n x n doubles and the digit planes, 14 bytes per element of
+ * A) is allocated per call.
  */
 tt_status tt_gram_mixed(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg,
                         void* stream);
 
 /*
  * tt_gemm_nt_mixed: C = A B^T (A: M x K, B: N x K, C: M x N, row-major) with the
- * same exact split products, each row of A and of B scaled by its own power of
- * two (error about 2^-48 max_k|A_ik| max_k|B_jk| per term).
+ * same exact split products on the tensor cores, each row of A and of B scaled
+ * by its own power of two (error about 2^-48 max_k|A_ik| max_k|B_jk| per term).
  */
 tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A_dev, int lda, const double* B_dev,
                            int ldb, double* C_dev, int ldc, void* stream);
