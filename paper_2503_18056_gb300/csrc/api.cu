@@ -475,8 +475,9 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         {
             PhaseScope ps(h, TT_PH_UPDATE, 2.0 * m * (double)Rk * rk, 8.0 * ((double)m * Rk + (double)m * rk));
             if (h->precision == TT_MIXED)
+                // A's digit images go to the left Gram's scratch, free until the next bond
                 TT_TRY(slgemm_nt(s, m, rk, Rk, A, Rk, h->PAt.p, Rk, dst[k].p, rk, h->slscratch,
-                                 h->d_int + HI_STATUS));
+                                 h->d_int + HI_STATUS, &h->partials));
             else
                 TT_TRY(dgemm(s, false, true, (int)m, rk, Rk, 1.0, A, Rk, h->PAt.p, Rk, 0.0, dst[k].p, rk));
         }

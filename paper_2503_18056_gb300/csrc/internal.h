@@ -96,8 +96,12 @@ tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double
 size_t tcgram_scratch_doubles(int m, int n);
 tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
                  DevBuf& scratch, int* status_dev);
+// planes (nullable): where A's digit images go (14 bytes per element of A,
+// padded to 128 rows x 32 columns), e.g. a buffer that is free at the time;
+// null puts them in scratch.
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
-                    long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev = nullptr);
+                    long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev = nullptr,
+                    DevBuf* planes = nullptr);
 
 // Row scaling: out[i][j] = in[i][j] * f(v[i]) for i < rows, j < cols, where
 // mode 0: v, 1: sqrt(v), 2: 1/sqrt(v), 3: 1/v.  out may alias in.

@@ -530,24 +530,57 @@ tcgram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 // Core update C (M x N) = A (M x K) B^T on tcgen05, rows of A and B with their
 // own exponents (the contraction runs along rows).  Same 7-digit split,
 // exact 128-column level sums, seven TMEM accumulators per 128 x 64 tile and
-// one MMA-issuing thread as the Gram; A is sliced on the fly: eight warps
-// read 32 K-columns of the tile's 128 A rows per stage (coalesced FP64
-// loads, one stage ahead), write the digits in the MMA's 64-byte
-// swizzled K-major layout (16-byte chunk index XOR (row / 2) mod 4), make them
-// visible to the tensor core (fence.proxy.async) and, after every fourth stage,
-// drain the accumulators.  B (a few hundred rows) is sliced once beforehand
-// into ready-made shared-memory images, one bulk copy per stage.  A persistent
-// CTA walks (row block, column block) items.
-constexpr int TU_WORK_WARPS = 8;
-constexpr int TU_THREADS = 32 * (2 + TU_WORK_WARPS);  // warp 1 TMEM + MMA, warps 2-9 slice + drain
+// one MMA-issuing thread as the Gram.  Both operands are sliced once
+// beforehand into ready-made shared-memory images -- per (row block, stage)
+// the seven 128 x 32 digit tiles of A, per (column block, stage) the seven
+// 64 x 32 tiles of B, each in the MMA's 64-byte swizzled K-major layout
+// (16-byte chunk index XOR (row / 2) mod 4) -- so one thread brings a stage in
+// with two bulk copies, one thread issues its 56 MMAs, and eight warps drain
+// the accumulators every fourth stage.  A persistent CTA walks (row block,
+// column block) items.
+constexpr int TU_DRAIN_WARPS = 8;
+constexpr int TU_THREADS = 32 * (2 + TU_DRAIN_WARPS);  // warp 0 copies, warp 1 TMEM + MMA, 2-9 drain
 constexpr size_t TU_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024 + 1024;
 
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 // Byte offset of element (row r, k) in a swizzled K-major digit tile (64-byte rows).
 __device__ __forceinline__ unsigned tc_swz(int r, int k) {
     return (unsigned)(r * 64 + ((((k >> 3) ^ ((r >> 1) & 3))) << 4) + (k & 7) * 2);
+}
+
+// A (M x K, per-row exponents) as shared-memory images: for row block mb and
+// stage st the seven tiles of rows mb*128 .. +127, columns st*32 .. +31;
+// At + ((mb * nst + st) * 7 + s) * 8192 is one tile.  A thread slices two
+// adjacent columns of one row and stores 32-bit words: a warp writes two
+// whole 64-byte rows per digit, without bank conflicts.
+__global__ void __launch_bounds__(256)
+slice7_atiles_kernel(long M, int K, int nst, const double* __restrict__ A, long lda,
+                     const int* __restrict__ erowA, unsigned char* __restrict__ At) {
+    const long mblocks = (M + TC_M - 1) / TC_M;
+    const long total = mblocks * nst * TC_M * (TC_K / 2);
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int kw = (int)(t % (TC_K / 2));
+        const int r = (int)((t / (TC_K / 2)) % TC_M);
+        const long ts = t / ((long)(TC_K / 2) * TC_M);  // mb * nst + st
+        const int st = (int)(ts % nst);
+        const long i = (ts / nst) * TC_M + r;
+        const int k = st * TC_K + 2 * kw;
+        double v0 = 0.0, v1 = 0.0;
+        int e = 0;
+        if (i < M) {
+            e = erowA[i] + 1;
+            if (k < K) v0 = A[i * lda + k];
+            if (k + 1 < K) v1 = A[i * lda + k + 1];
+        }
+        unsigned short d0[TC_S], d1[TC_S];
+        digits7(v0, e, d0);
+        digits7(v1, e, d1);
+        const unsigned off = tc_swz(r, 2 * kw);
+#pragma unroll
+        for (int s = 0; s < TC_S; ++s)
+            *reinterpret_cast<unsigned*>(At + (ts * TC_S + s) * (TC_M * TC_K * 2) + off) =
+                (unsigned)d0[s] | ((unsigned)d1[s] << 16);
+    }
 }
 
 // B (N x K, per-row exponents) as ready-made shared-memory images: for n-block
@@ -585,7 +618,7 @@ __device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, uns
 }
 
 __global__ void __launch_bounds__(TU_THREADS, 1)
-tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
+tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
              const int* __restrict__ erowA, const unsigned char* __restrict__ Bt,
              const int* __restrict__ erowB, double* __restrict__ C, long ldc, int* status) {
     extern __shared__ unsigned char tc_raw[];
@@ -594,10 +627,9 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
     unsigned char* sbase = tc_raw + pad;
     const unsigned sb = raw_s + pad;
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbase + TC_STAGES * TC_STAGE_BYTES);
-    // bars: [0,1] stage's A digits written (8 slicing warps), [2,3] stage empty,
-    // [4] accumulators full, [5] accumulators drained, [6] all MMAs done,
-    // [7,8] stage's B tiles landed (bulk copy)
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 12);
+    // bars: [0,1] stage landed (bulk copies), [2,3] stage empty, [4] accumulators
+    // full, [5] accumulators drained, [6] all MMAs done
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + 8);
     volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 2);  // abort, issued, consumed
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -607,8 +639,7 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
     const int nst = (K + TC_K - 1) / TC_K;  // stages per item
     if ((long)blockIdx.x >= items) return;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 9; ++i)
-            mbar_init(smem_u32(&bars[i]), (i <= 1 || i == 5) ? (unsigned)TU_WORK_WARPS : 1u);
+        for (int i = 0; i < 7; ++i) mbar_init(smem_u32(&bars[i]), i == 5 ? (unsigned)TU_DRAIN_WARPS : 1u);
         flags[0] = 0;
         flags[1] = 0;
         flags[2] = 0;
@@ -627,10 +658,11 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
     const unsigned tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {  // B digit tiles: one bulk copy per stage
+        if (lane == 0) {  // copies: A and B images of each stage
             long g = 0;
             bool stop = false;
             for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
+                const long mb = item / nblk;
                 const int nb = (int)(item % nblk);
                 for (int it = 0; it < nst; ++it, ++g) {
                     const int st = (int)(g % TC_STAGES);
@@ -639,10 +671,12 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
                         stop = true;
                         break;
                     }
-                    const unsigned bfull = smem_u32(&bars[7 + st]);
-                    mbar_expect_tx(bfull, (unsigned)TC_B_BYTES);
-                    bulk_copy_g2s(sb + (unsigned)(st * TC_STAGE_BYTES + TC_A_BYTES),
-                                  Bt + ((long)nb * nst + it) * TC_B_BYTES, (unsigned)TC_B_BYTES, bfull);
+                    const unsigned full = smem_u32(&bars[st]);
+                    mbar_expect_tx(full, (unsigned)TC_STAGE_BYTES);
+                    const unsigned dA = sb + (unsigned)(st * TC_STAGE_BYTES);
+                    bulk_copy_g2s(dA, At + (mb * nst + it) * (long)TC_A_BYTES, (unsigned)TC_A_BYTES, full);
+                    bulk_copy_g2s(dA + TC_A_BYTES, Bt + ((long)nb * nst + it) * TC_B_BYTES,
+                                  (unsigned)TC_B_BYTES, full);
                     flags[1] = (int)(g + 1);
                 }
             }
@@ -663,8 +697,7 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
                         }
                         tc_fence_after();
                     }
-                    if (!mbar_wait_or_abort(smem_u32(&bars[st]), ph, status, flags) ||
-                        !mbar_wait_or_abort(smem_u32(&bars[7 + st]), ph, status, flags)) {
+                    if (!mbar_wait_or_abort(smem_u32(&bars[st]), ph, status, flags)) {
                         stop = true;
                         break;
                     }
@@ -697,88 +730,42 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
             tc_commit(smem_u32(&bars[6]));
             mbar_wait(smem_u32(&bars[6]), 0u, status);
         }
-    } else if (warp >= 2) {  // slicing + drain warps
-        const int ww = warp - 2;        // 0..7
-        const int q = warp & 3;         // TMEM lane quarter
-        const int c0 = (ww >> 2) * TC_DN;
-        long g = 0, gb = 0;
+    } else {  // drain warps: TMEM lanes 32 q .. 32 q + 31, columns c0 .. c0 + TC_DN - 1
+        const int q = warp & 3;
+        const int c0 = ((warp - 2) >> 2) * TC_DN;
+        const int nb_per_item = (nst + TC_BLK - 1) / TC_BLK;
+        long gb = 0;
         bool stop = false;
-        // the next stage's A values, loaded while the tensor cores work on the
-        // current one (16 loads per thread in flight)
-        double va[16];
-#define TU_LOAD_STAGE(I0L, N0L, ITL)                                               \
-    do {                                                                           \
-        const int k_ = (ITL) * TC_K + lane;                                        \
-        _Pragma("unroll") for (int rr = 0; rr < 16; ++rr) {                        \
-            const long i_ = (I0L) + ww * 16 + rr;                                  \
-            va[rr] = (i_ < M && k_ < K) ? A[i_ * lda + k_] : 0.0;                  \
-        }                                                                          \
-    } while (0)
-        if ((long)blockIdx.x < items)
-            TU_LOAD_STAGE((blockIdx.x / nblk) * TC_M, (int)(blockIdx.x % nblk) * TC_N, 0);
         for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
             const long i0 = (item / nblk) * TC_M;
             const int n0 = (int)(item % nblk) * TC_N;
             float hi[TC_DN], lo[TC_DN];
 #pragma unroll
             for (int c = 0; c < TC_DN; ++c) hi[c] = lo[c] = 0.f;
-            for (int it = 0; it < nst; ++it, ++g) {
-                const int st = (int)(g % TC_STAGES);
-                const unsigned ph = (unsigned)(g / TC_STAGES) & 1u;
-                if (!__all_sync(0xffffffffu,
-                                mbar_wait_or_abort(smem_u32(&bars[2 + st]), ph ^ 1u, status, flags))) {
+            for (int b = 0; b < nb_per_item; ++b, ++gb) {
+                if (!__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bars[4]), (unsigned)gb & 1u,
+                                                                 status, flags))) {
                     stop = true;
                     break;
                 }
-                unsigned char* sA = sbase + st * TC_STAGE_BYTES;
-                // A: rows 16 ww .. 16 ww + 15 of the tile, one column per lane
-#pragma unroll
-                for (int rr = 0; rr < 16; ++rr) {
-                    const int r = ww * 16 + rr;
-                    const long i = i0 + r;
-                    unsigned short d[TC_S];
-                    digits7(va[rr], i < M ? erowA[i] + 1 : 0, d);
-                    const unsigned off = tc_swz(r, lane);
-#pragma unroll
-                    for (int s = 0; s < TC_S; ++s)
-                        *reinterpret_cast<unsigned short*>(sA + s * (TC_M * TC_K * 2) + off) = d[s];
-                }
-                fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bars[st]));
-                {  // load the next stage (this item's next, or the next item's first) while
-                   // the tensor cores work on this one
-                    const long nitem = it + 1 < nst ? item : item + gridDim.x;
-                    if (nitem < items)
-                        TU_LOAD_STAGE((nitem / nblk) * TC_M, (int)(nitem % nblk) * TC_N,
-                                      it + 1 < nst ? it + 1 : 0);
-                }
-                if ((it % TC_BLK) == TC_BLK - 1 || it == nst - 1) {  // drain this block
-                    if (!__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bars[4]),
-                                                                     (unsigned)gb & 1u, status, flags))) {
-                        stop = true;
-                        break;
-                    }
-                    tc_fence_after();
+                tc_fence_after();
 #pragma unroll 1
-                    for (int w = 0; w < TC_S; ++w) {
-                        const float scale = __int_as_float((127 - 7 * w) << 23);
-                        unsigned r2[2][16];
-                        const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(w * TC_N + c0);
-                        tc_ld16(ta, r2[0]);
-                        tc_ld16(ta + 16, r2[1]);
-                        tc_wait_ld();
+                for (int w = 0; w < TC_S; ++w) {
+                    const float scale = __int_as_float((127 - 7 * w) << 23);
+                    unsigned r2[2][16];
+                    const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(w * TC_N + c0);
+                    tc_ld16(ta, r2[0]);
+                    tc_ld16(ta + 16, r2[1]);
+                    tc_wait_ld();
 #pragma unroll
-                        for (int c = 0; c < 2; ++c)
+                    for (int c = 0; c < 2; ++c)
 #pragma unroll
-                            for (int e = 0; e < 16; ++e)
-                                df_add(hi[16 * c + e], lo[16 * c + e], __uint_as_float(r2[c][e]) * scale);
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&bars[5]));
-                    ++gb;
+                        for (int e = 0; e < 16; ++e)
+                            df_add(hi[16 * c + e], lo[16 * c + e], __uint_as_float(r2[c][e]) * scale);
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars[5]));
             }
             if (stop) break;
             const long i = i0 + 32 * q + lane;
@@ -798,7 +785,7 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
         // bulk copies issued but never consumed (after an abort) land before the CTA exits
         const long issued = flags[1], consumed = flags[2];
         for (long g2 = consumed; g2 < issued; ++g2)
-            mbar_wait(smem_u32(&bars[7 + g2 % TC_STAGES]), (unsigned)(g2 / TC_STAGES) & 1u, status);
+            mbar_wait(smem_u32(&bars[g2 % TC_STAGES]), (unsigned)(g2 / TC_STAGES) & 1u, status);
     }
     __syncthreads();
     if (warp == 1) {
@@ -808,8 +795,6 @@ tcupd_kernel(long M, int N, int K, const double* __restrict__ A, long lda,
                      : "memory");
     }
 }
-
-#undef TU_LOAD_STAGE
 
 int tc_tiles(int n) {
     const int KT = (n + TC_N - 1) / TC_N;
@@ -957,7 +942,7 @@ tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double
 }
 
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
-                    long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev) {
+                    long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev, DevBuf* planes) {
     if (M <= 0 || N <= 0) return TT_OK;
     if (K <= 0) {
         for (long i = 0; i < M; ++i) fill(s, C + i * ldc, N, 0.0);
@@ -965,12 +950,17 @@ tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long 
     }
     const int nst = (K + TC_K - 1) / TC_K;
     const int nbt = (N + TC_N - 1) / TC_N;
+    const long mblocks = (M + TC_M - 1) / TC_M;
     const size_t e_dbl = ((size_t)(M + N + 1) / 2 + 2 + 15) / 16 * 16;  // exponents, 128-byte aligned
     const size_t bt_bytes = (size_t)nbt * nst * TC_B_BYTES;
-    TT_TRY(scratch.ensure(e_dbl + bt_bytes / 8, s));
+    const size_t at_bytes = (size_t)mblocks * nst * TC_A_BYTES;
+    const bool own = planes == nullptr;  // A's images in `scratch` too
+    TT_TRY(scratch.ensure(e_dbl + bt_bytes / 8 + (own ? at_bytes / 8 : 0), s));
+    if (!own) TT_TRY(planes->ensure(at_bytes / 8, s));
     int* eA = reinterpret_cast<int*>(scratch.p);
     int* eB = eA + M;
     unsigned char* Bt = reinterpret_cast<unsigned char*>(scratch.p + e_dbl);
+    unsigned char* At = own ? Bt + bt_bytes : reinterpret_cast<unsigned char*>(planes->p);
     note_launch();
     row_exp_kernel<<<(int)std::max<long>(1, std::min<long>((M + 7) / 8, 152L * 64)), 256, 0, s>>>(M, K, A, lda, eA);
     note_launch();
@@ -980,15 +970,19 @@ tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long 
         note_launch();
         slice7_btiles_kernel<<<(int)std::min<long>((tot + 255) / 256, 152L * 16), 256, 0, s>>>(
             N, K, nst, B, ldb, eB, Bt);
+        const long tota = mblocks * nst * TC_M * (TC_K / 2);
+        note_launch();
+        slice7_atiles_kernel<<<(int)std::min<long>((tota + 255) / 256, 152L * 32), 256, 0, s>>>(
+            M, K, nst, A, lda, eA, At);
     }
     int dev = 0, sms = 152;
     TT_CUDA_TRY(cudaGetDevice(&dev));
     TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const long items = ((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
+    const long items = mblocks * nbt;
     const int grid = (int)std::min<long>(items, sms);
     TT_TRY(ensure_max_dynamic_smem((const void*)tcupd_kernel));
     note_launch();
-    tcupd_kernel<<<grid, TU_THREADS, TU_SMEM, s>>>(M, N, K, A, lda, eA, Bt, eB, C, ldc, status_dev);
+    tcupd_kernel<<<grid, TU_THREADS, TU_SMEM, s>>>(M, N, K, At, eA, Bt, eB, C, ldc, status_dev);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
 }
