@@ -352,8 +352,8 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         PhaseScope ps(h, TT_PH_GRAM_RIGHT, fl, by);
         const int Rl = R[d - 1];
         TT_TRY(h->GB[d - 2].ensure((size_t)Rl * Rl, s));
-        TT_TRY(dgemm(s, false, true, Rl, Rl, n[d - 1], 1.0, src[d - 1].p, n[d - 1], src[d - 1].p,
-                     n[d - 1], 0.0, h->GB[d - 2].p, Rl));
+        TT_TRY(dgemm_sk(s, false, true, Rl, Rl, n[d - 1], 1.0, src[d - 1].p, n[d - 1], src[d - 1].p,
+                        n[d - 1], h->GB[d - 2].p, Rl, h->partials));
         for (int k = d - 3; k >= 0; --k) {
             const int Ra = R[k + 1], nn = n[k + 1], Rb = R[k + 2];
             TT_TRY(h->bwd.ensure((size_t)Ra * nn * Rb, s));
@@ -424,8 +424,8 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             const double* Wk = h->VtB[k].p;
             TT_TRY(h->T1.ensure((size_t)Rk * kB, s));
             TT_TRY(h->K.ensure((size_t)kB * kB, s));
-            TT_TRY(dgemm(s, false, true, Rk, kB, Rk, 1.0, h->GA.p, Rk, Wk, Rk, 0.0, h->T1.p, kB));
-            TT_TRY(dgemm(s, false, false, kB, kB, Rk, 1.0, Wk, Rk, h->T1.p, kB, 0.0, h->K.p, kB));
+            TT_TRY(dgemm_sk(s, false, true, Rk, kB, Rk, 1.0, h->GA.p, Rk, Wk, Rk, h->T1.p, kB, h->partials));
+            TT_TRY(dgemm_sk(s, false, false, kB, kB, Rk, 1.0, Wk, Rk, h->T1.p, kB, h->K.p, kB, h->partials));
         }
         TT_TRY(h->lamK.ensure((size_t)kB, s));
         TT_TRY(h->VtK.ensure((size_t)kB * kB, s));
@@ -456,12 +456,14 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             TT_TRY(h->Vts.ensure((size_t)rk * kB, s));
             scale_rows(s, rk, kB, h->VtK.p, kB, h->lamK.p, 2, h->Vts.p, kB);
             TT_TRY(h->PAt.ensure((size_t)rk * Rk, s));
-            TT_TRY(dgemm(s, false, false, rk, Rk, kB, 1.0, h->Vts.p, kB, h->VtB[k].p, Rk, 0.0, h->PAt.p, Rk));
+            TT_TRY(dgemm_sk(s, false, false, rk, Rk, kB, 1.0, h->Vts.p, kB, h->VtB[k].p, Rk, h->PAt.p, Rk,
+                            h->partials));
             // M_upd = P_A^T G_A = A'^T A  (rk x Rk): B'^T = A'^T A B^T, the orthogonal
             // projection of A B^T onto span(A'); equals App. A.2's (V_B S_B^{-1} V~ S~)^T
             // on the retained eigenspace of G_B without forming S_B^{-1}
             TT_TRY(h->Mupd.ensure((size_t)rk * Rk, s));
-            TT_TRY(dgemm(s, false, false, rk, Rk, Rk, 1.0, h->PAt.p, Rk, h->GA.p, Rk, 0.0, h->Mupd.p, Rk));
+            TT_TRY(dgemm_sk(s, false, false, rk, Rk, Rk, 1.0, h->PAt.p, Rk, h->GA.p, Rk, h->Mupd.p, Rk,
+                            h->partials));
         }
         if (h->cur_rec && h->rec_proj && k < 2) {
             tt_ctx::StepRec* rc = h->cur_rec;
@@ -494,8 +496,8 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         {
             PhaseScope ps(h, TT_PH_UPDATE, 2.0 * rk * (double)Rk * ncols,
                           8.0 * ((double)Rk * ncols + (double)rk * ncols));
-            TT_TRY(dgemm(s, false, false, rk, (int)ncols, Rk, 1.0, h->Mupd.p, Rk, src[k + 1].p, ncols,
-                         0.0, next, ncols));
+            TT_TRY(dgemm_sk(s, false, false, rk, (int)ncols, Rk, 1.0, h->Mupd.p, Rk, src[k + 1].p, ncols,
+                            next, ncols, h->partials));
         }
         rr[k + 1] = rk;
         A = next;

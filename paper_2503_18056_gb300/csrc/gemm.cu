@@ -260,10 +260,13 @@ tt_status dgemm_sk(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double
                    const double* A, long lda, const double* B, long ldb, double* C, long ldc,
                    DevBuf& scratch) {
     const long tiles = (long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-    // split K only where the tile grid leaves most SMs idle and K is long
+    // Split K where the tile grid leaves SMs idle: one 64 x 64 x 16 tile step
+    // is ~131 kflop, about 19 us of one SM's FP64 pipe on GB300, so a product
+    // with a handful of tiles runs for (K / 16) x 19 us on a handful of SMs.
+    // Aim at about two CTAs per SM, each with at least two K tiles.
     int ks = 1;
-    if (tiles < 152 && K >= 8 * BK * 16) {
-        ks = (int)std::min<long>((456 + tiles - 1) / tiles, K / (8 * BK));
+    if (tiles < 152 && K >= 4 * BK) {
+        ks = (int)std::min<long>((304 + tiles - 1) / tiles, K / (2 * BK));
         ks = std::max(1, std::min(ks, 64));
     }
     if (ks == 1 || M <= 0 || N <= 0)

@@ -122,9 +122,11 @@ def test_mixed_matches_fp64_with_sources_at_fp64_ranks(ttsn):
         gmx.step(forced=info["ranks"][1:-1])
     E64, T64, _ = g64.energy()
     Em, Tm, _ = gmx.energy()
-    # measured: E 1e-10, T 4e-10 of their maxima (T sits near the 1e-3 background)
-    assert float((Em - E64).abs().max() / E64.abs().max()) <= 1e-9
-    assert float((Tm - T64).abs().max() / T64.abs().max()) <= 2e-9
+    # measured 1e-10 .. 2.2e-9 of their maxima depending on the summation order
+    # of the FP64 products (T sits near the 1e-3 background); the precision
+    # form's stated bound is 1e-6
+    assert float((Em - E64).abs().max() / E64.abs().max()) <= 1e-8
+    assert float((Tm - T64).abs().max() / T64.abs().max()) <= 1e-8
 
 
 @pytest.fixture(scope="module")
