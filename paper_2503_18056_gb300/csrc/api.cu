@@ -1377,7 +1377,7 @@ tt_status tt_gram(int m, int n, const double* A, int lda, double* G, int ldg, vo
     set_error("");
     if (m < 0 || n < 0) return fail(TT_ERR_ARG, "tt_gram: negative size");
     if (n == 0) return TT_OK;
-    if (!A || !G) return fail(TT_ERR_ARG, "tt_gram: null pointer");
+    if (!G || (m > 0 && !A)) return fail(TT_ERR_ARG, "tt_gram: null pointer");
     if (lda < n || ldg < n) return fail(TT_ERR_ARG, "tt_gram: leading dimension smaller than n");
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf scratch;
@@ -1392,7 +1392,7 @@ tt_status tt_gram_mixed(int m, int n, const double* A, int lda, double* G, int l
     set_error("");
     if (m < 0 || n < 0) return fail(TT_ERR_ARG, "tt_gram_mixed: negative size");
     if (n == 0) return TT_OK;
-    if (!A || !G) return fail(TT_ERR_ARG, "tt_gram_mixed: null pointer");
+    if (!G || (m > 0 && !A)) return fail(TT_ERR_ARG, "tt_gram_mixed: null pointer");
     if (lda < n || ldg < n) return fail(TT_ERR_ARG, "tt_gram_mixed: leading dimension smaller than n");
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf scratch;
@@ -1408,7 +1408,7 @@ tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A, int lda, const 
     set_error("");
     if (M < 0 || N < 0 || K < 0) return fail(TT_ERR_ARG, "tt_gemm_nt_mixed: negative size");
     if (M == 0 || N == 0) return TT_OK;
-    if (!A || !B || !C) return fail(TT_ERR_ARG, "tt_gemm_nt_mixed: null pointer");
+    if (!C || (K > 0 && (!A || !B))) return fail(TT_ERR_ARG, "tt_gemm_nt_mixed: null pointer");
     if (lda < K || ldb < K || ldc < N) return fail(TT_ERR_ARG, "tt_gemm_nt_mixed: leading dimension too small");
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf scratch;

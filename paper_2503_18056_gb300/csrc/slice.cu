@@ -944,8 +944,12 @@ tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
                     long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev, DevBuf* planes) {
     if (M <= 0 || N <= 0) return TT_OK;
-    if (K <= 0) {
-        for (long i = 0; i < M; ++i) fill(s, C + i * ldc, N, 0.0);
+    if (K <= 0) {  // empty contraction: C = 0
+        if (ldc == N) {
+            fill(s, C, (size_t)M * N, 0.0);
+        } else {
+            for (long i = 0; i < M; ++i) fill(s, C + i * ldc, N, 0.0);
+        }
         return TT_OK;
     }
     const int nst = (K + TC_K - 1) / TC_K;

@@ -1,0 +1,98 @@
+"""Edge cases of the C-ABI on the GPU: empty and one-element inputs of the
+kernel-level calls, and the argument errors the calls return instead of
+faulting (invalid problem descriptions, forced ranks, source counts, short
+output buffers)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ttsn():
+    assert torch.cuda.is_available()
+    import paper_2503_18056_gb300 as m
+
+    return m
+
+
+def _empty(shape):
+    return torch.empty(shape, dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("which", ["gram", "gram_mixed"])
+def test_gram_of_an_empty_matrix_is_zero(ttsn, which):
+    """m = 0 rows: G = A^T A is the n x n zero matrix (A may be a null pointer)."""
+    for n in (1, 5, 130):
+        G = getattr(ttsn, which)(_empty((0, n)))
+        torch.cuda.synchronize()
+        assert G.shape == (n, n) and float(G.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("which", ["gram", "gram_mixed"])
+def test_gram_of_one_element(ttsn, which):
+    for v in (3.0, -2.5e-100, 7.0e150):
+        G = getattr(ttsn, which)(torch.tensor([[v]], dtype=torch.float64, device="cuda"))
+        assert abs(float(G[0, 0]) - v * v) <= 1e-13 * v * v
+
+
+def test_gemm_nt_mixed_empty_contraction_is_zero(ttsn):
+    A, B = _empty((37, 0)), _empty((5, 0))
+    C = ttsn.gemm_nt_mixed(A, B)
+    torch.cuda.synchronize()
+    assert C.shape == (37, 5) and float(C.abs().max()) == 0.0
+
+
+def test_dgemm_empty_contraction_is_zero(ttsn):
+    C = ttsn.dgemm(_empty((9, 0)), _empty((0, 4)))
+    torch.cuda.synchronize()
+    assert C.shape == (9, 4) and float(C.abs().max()) == 0.0
+
+
+def test_syev_of_one_by_one(ttsn):
+    lam, Vt, sweeps = ttsn.syev(torch.tensor([[4.5]], dtype=torch.float64, device="cuda"))
+    assert float(lam[0]) == 4.5 and abs(float(Vt[0, 0])) == 1.0
+
+
+@pytest.mark.parametrize("bad", [dict(n_theta=0), dict(n_phi=0), dict(c=0.0), dict(eps=-1.0),
+                                 dict(rounds_per_step=3), dict(precision=7), dict(bc=5),
+                                 dict(L=[0.0, 1.0])])
+def test_invalid_problem_description_is_an_argument_error(ttsn, bad):
+    p = workloads.problem("small_2d", n=(6, 5), n_theta=4, n_phi=8)
+    with pytest.raises(ttsn.TTError) as e:
+        ttsn.TTSN.from_problem(p, **bad)
+    assert e.value.status == -1, e.value
+
+
+def test_forced_rank_below_one_is_an_argument_error(ttsn):
+    p = workloads.problem("small_2d", n=(6, 5), n_theta=4, n_phi=8)
+    tt = ttsn.TTSN.from_problem(p)
+    with pytest.raises(ttsn.TTError):
+        tt.step(forced=[0, 1])
+    with pytest.raises(ttsn.TTError):
+        tt.round(forced=[1, 0])
+    tt.step()  # the handle stays usable
+
+
+def test_too_many_sources_is_an_argument_error(ttsn):
+    p = workloads.problem("small_2d", n=(6, 5), n_theta=4, n_phi=8)
+    tt = ttsn.TTSN.from_problem(p)
+    src = [(np.ones(30), np.ones(4), np.ones(8))] * 17
+    with pytest.raises(ttsn.TTError):
+        tt.set_sources(src)
+    tt.set_sources(src[:16])
+    tt.step()
+
+
+def test_to_full_with_a_short_buffer_is_refused(ttsn):
+    p = workloads.problem("small_2d", n=(6, 5), n_theta=4, n_phi=8)
+    tt = ttsn.TTSN.from_problem(p)
+    short = _empty(6 * 5 * 4 * 8 - 1)
+    st = ttsn.lib.tt_to_full(tt._h, ctypes.c_void_p(short.data_ptr()), short.numel())
+    assert st == -7  # TT_ERR_TOO_LARGE: the buffer is too small, nothing written
+    assert tt.full().shape == (6, 5, 4, 8)
