@@ -122,6 +122,31 @@ typedef struct {
 tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out);
 
 /*
+ * A caller-supplied device allocator: alloc returns
+ * `bytes` of device memory usable on `stream` (a cudaStream_t) or NULL on
+ * failure; free returns a block that alloc gave, with the same size and the
+ * stream of its last use.  The library frees a block only after enqueuing the
+ * work that uses it on that stream, so a stream-ordered (caching) allocator
+ * may hand the block out again for later work on the same stream.  ctx is
+ * passed through unchanged.
+ */
+typedef struct {
+    void* ctx;
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+} tt_allocator;
+
+/*
+ * tt_create_ex: as tt_create, with every device buffer of the handle (cores,
+ * workspaces, scratch, tape) taken from `alloc` instead of the CUDA
+ * stream-ordered pool; alloc (nullable: as tt_create) is copied, and its ctx
+ * and functions must stay valid until tt_destroy.  Kernel-level calls
+ * (tt_gram, tt_dgemm, ...) keep using the pool.
+ */
+tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_allocator* alloc,
+                       tt_handle* out);
+
+/*
  * tt_create_tt: a bare TT with d cores of mode sizes n[0..d-1] and ranks
  * ranks[0..d] (ranks[0] = ranks[d] = 1), all cores zero; used with
  * tt_set_cores / tt_round / tt_to_full.  Physics calls return TT_ERR_STATE.
@@ -183,6 +208,15 @@ tt_status tt_get_dims(tt_handle h, int* d_host, int* n_host);
  * TT_ERR_TOO_LARGE if out_len is smaller.
  */
 tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len);
+
+/*
+ * tt_get_cores: borrowed device views of the cores: cores_dev[k] (host array
+ * of d pointers) receives core k's device address, shapes_host[3k..3k+2] its
+ * shape (r_{k-1}, n_k, r_k).  Synchronises the stream first; the views stay
+ * valid until the next call that changes the TT (steps, rounding, set calls,
+ * tt_destroy).  Use tt_get_core for an owned copy.
+ */
+tt_status tt_get_cores(tt_handle h, double** cores_dev, int* shapes_host);
 
 /*
  * tt_set_cores: replace the TT by the d cores cores_dev[k] (device, shapes

@@ -58,6 +58,15 @@ class _Handle:
         check(lib.tt_get_ranks(self._h, buf, d + 1))
         return list(buf)
 
+    def core_views(self):
+        """Borrowed device views (pointer, shape) of the cores (tt_get_cores);
+        valid until the TT next changes."""
+        d, _ = self.dims()
+        ptrs = (ctypes.c_void_p * d)()
+        shapes = (ctypes.c_int * (3 * d))()
+        check(lib.tt_get_cores(self._h, ptrs, shapes))
+        return [(ptrs[k], tuple(shapes[3 * k:3 * k + 3])) for k in range(d)]
+
     def dims(self):
         d = ctypes.c_int()
         n = (ctypes.c_int * _native.TT_MAX_D)()
@@ -128,6 +137,27 @@ class TensorTrain(_Handle):
         self.set_cores(ts)
 
 
+def _torch_allocator():
+    """A tt_allocator backed by torch's CUDA caching allocator: the handle's
+    buffers then count in torch.cuda.memory_allocated() and share torch's
+    cached blocks.  The callbacks run on the calling thread (ctypes takes the
+    GIL for them)."""
+    def alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ctx, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = _native.Allocator()
+    a.ctx = None
+    a.alloc = _native.ALLOC_FN(alloc)
+    a.free = _native.FREE_FN(free)
+    return a
+
+
 class TTSN(_Handle):
     """A TT-S_N problem (paper's three-core layout) on the current CUDA stream.
 
@@ -137,7 +167,7 @@ class TTSN(_Handle):
 
     def __init__(self, n, L, n_theta, n_phi, sigma_a, cv, T0, Tr0=None, sigma_s=None, c=1.0,
                  a_r=1.0, dt=0.0, cfl=0.5, bc=TT_BC_PERIODIC, eps=1e-6, max_rank=0,
-                 rounds_per_step=1, precision=TT_FP64, stream=None):
+                 rounds_per_step=1, precision=TT_FP64, stream=None, allocator=None):
         super().__init__()
         ndim = len(n)
         nc = 1
@@ -164,7 +194,14 @@ class TTSN(_Handle):
             setattr(desc, key, f[key].data_ptr() if f[key] is not None else None)
         desc.eps, desc.max_rank = float(eps), int(max_rank or 0)
         desc.rounds_per_step, desc.precision = int(rounds_per_step), int(precision)
-        check(lib.tt_create(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(self._h)))
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _torch_allocator()
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
+        check(lib.tt_create_ex(ctypes.byref(desc), _stream_ptr(stream),
+                               ctypes.byref(self._alloc) if self._alloc is not None else None,
+                               ctypes.byref(self._h)))
         self._keep = f  # inputs stay alive until creation finished (copied in)
 
     @staticmethod

@@ -20,6 +20,14 @@ TT_FP64, TT_MIXED = 0, 1
 TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
 class ProblemDesc(ctypes.Structure):
     _fields_ = [
         ("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3),
@@ -96,6 +104,8 @@ def _load():
         "tt_sn_step_adjoint": [vp, vp, dp],
         "tt_tape_clear": [vp],
         "tt_set_sources": [vp, i, vp, vp, vp],
+        "tt_create_ex": [ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(Allocator), ctypes.POINTER(vp)],
+        "tt_get_cores": [vp, ctypes.POINTER(vp), ip],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -122,7 +132,8 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_set_precision", "tt_profile", "tt_profile_read", "tt_kernel_launches", "tt_bench_fp64_mma",
             "tt_bench_bf16_mma", "tt_batch_create", "tt_batch_step", "tt_batch_size",
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
-            "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources"]
+            "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
+            "tt_create_ex", "tt_get_cores"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

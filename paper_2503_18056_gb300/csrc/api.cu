@@ -42,15 +42,43 @@ void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed
 void set_error(const std::string& msg) { g_err = msg; }
 const char* get_error() { return g_err.c_str(); }
 
+static thread_local const tt_allocator* g_alloc = nullptr;
+const tt_allocator* current_allocator() { return g_alloc; }
+AllocScope::AllocScope(const tt_allocator* a) : prev(g_alloc) { g_alloc = a; }
+AllocScope::~AllocScope() { g_alloc = prev; }
+
+namespace {
+// One device allocation through allocator a (null: the stream-ordered pool).
+cudaError_t dev_alloc(const tt_allocator* a, double** out, size_t bytes, cudaStream_t s) {
+    if (!a) return cudaMallocAsync((void**)out, bytes, s);
+    *out = static_cast<double*>(a->alloc(a->ctx, bytes, (void*)s));
+    return *out ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+void dev_free(const tt_allocator* a, double* p, size_t bytes, cudaStream_t s, bool async) {
+    if (!p) return;
+    if (a) {
+        a->free(a->ctx, p, bytes, (void*)s);
+    } else if (async) {
+        cudaFreeAsync(p, s);
+    } else {
+        cudaFree(p);
+    }
+}
+}  // namespace
+
 tt_status DevBuf::ensure(size_t n, cudaStream_t s, bool keep) {
     if (n <= cap) return TT_OK;
+    if (!p) {  // the first allocation fixes the allocator this buffer uses
+        alloc = current_allocator();
+        astream = s;
+    }
     size_t want = std::max(n, cap + cap / 2);
     double* np = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&np, want * sizeof(double), s);
+    cudaError_t e = dev_alloc(alloc, &np, want * sizeof(double), s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         want = n;
-        e = cudaMallocAsync((void**)&np, want * sizeof(double), s);
+        e = dev_alloc(alloc, &np, want * sizeof(double), s);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             set_error(std::string("device allocation of ") + std::to_string(want * 8) +
@@ -59,9 +87,10 @@ tt_status DevBuf::ensure(size_t n, cudaStream_t s, bool keep) {
         }
     }
     if (keep && p && cap) TT_CUDA_TRY(cudaMemcpyAsync(np, p, cap * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (p) TT_CUDA_TRY(cudaFreeAsync(p, s));
+    dev_free(alloc, p, cap * sizeof(double), s, true);
     p = np;
     cap = want;
+    astream = s;
     return TT_OK;
 }
 
@@ -83,9 +112,10 @@ tt_status ensure_max_dynamic_smem(const void* kernel) {
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    dev_free(alloc, p, cap * sizeof(double), astream, false);
     p = nullptr;
     cap = 0;
+    alloc = nullptr;
 }
 
 }  // namespace ttsn
@@ -111,6 +141,7 @@ struct tt_ctx {
     DevBuf GA, Wc, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd, slscratch;
     int precision = TT_FP64;
     EigWork eig;
+    DevBuf small_buf;          // holds d_dbl then d_int
     int* d_int = nullptr;      // device ints (HI_* layout)
     double* d_dbl = nullptr;   // device doubles (HD_* layout)
     int* h_int = nullptr;      // pinned host mirror
@@ -180,6 +211,11 @@ struct tt_ctx {
     double eps = 0.0;
     int max_rank = 0;
     int rounds = 1;
+    // caller's device allocator (tt_create_ex), copied; every buffer of the
+    // handle comes from it when has_allocator is set
+    tt_allocator allocator{};
+    bool has_allocator = false;
+    const tt_allocator* alloc_ptr() const { return has_allocator ? &allocator : nullptr; }
     double dV = 1.0;
 
     tt_status init_common(cudaStream_t s) {
@@ -193,8 +229,9 @@ struct tt_ctx {
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
         (void)cudaGetLastError();
-        TT_CUDA_TRY(cudaMalloc(&d_int, HI_N * sizeof(int)));
-        TT_CUDA_TRY(cudaMalloc(&d_dbl, HD_N * sizeof(double)));
+        TT_TRY(small_buf.ensure((size_t)HD_N + (HI_N * sizeof(int) + 7) / 8, s));
+        d_dbl = small_buf.p;
+        d_int = reinterpret_cast<int*>(small_buf.p + HD_N);
         TT_CUDA_TRY(cudaMallocHost(&h_int, HI_N * sizeof(int)));
         TT_CUDA_TRY(cudaMallocHost(&h_dbl, HD_N * sizeof(double)));
         TT_CUDA_TRY(cudaMemsetAsync(d_int, 0, HI_N * sizeof(int), s));
@@ -227,8 +264,7 @@ struct tt_ctx {
             cudaEventDestroy(p.b);
         }
         for (auto e : ev_pool) cudaEventDestroy(e);
-        if (d_int) cudaFree(d_int);
-        if (d_dbl) cudaFree(d_dbl);
+        small_buf.release();
         if (h_int) cudaFreeHost(h_int);
         if (h_dbl) cudaFreeHost(h_dbl);
     }
@@ -882,8 +918,15 @@ extern "C" {
 const char* tt_last_error(void) { return get_error(); }
 
 tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
+    return tt_create_ex(desc, stream, nullptr, out);
+}
+
+tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_allocator* alloc,
+                       tt_handle* out) {
     set_error("");
     if (!desc || !out) return fail(TT_ERR_ARG, "tt_create: null argument");
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail(TT_ERR_ARG, "tt_create_ex: allocator needs both alloc and free");
     *out = nullptr;
     const tt_problem_desc& D = *desc;
     if (D.ndim < 1 || D.ndim > 3) return fail(TT_ERR_ARG, "tt_create: ndim must be 1, 2 or 3");
@@ -907,6 +950,11 @@ tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
         return fail(TT_ERR_ARG, "tt_create: precision must be TT_FP64 or TT_MIXED");
 
     tt_ctx* h = new tt_ctx();
+    if (alloc) {
+        h->allocator = *alloc;
+        h->has_allocator = true;
+    }
+    AllocScope alloc_scope_(h->alloc_ptr());
     cudaStream_t s = (cudaStream_t)stream;
     tt_status st = h->init_common(s);
     if (st < 0) {
@@ -1092,6 +1140,7 @@ tt_status tt_create_tt(int d, const int* n, const int* ranks, void* stream, tt_h
 tt_status tt_sn_step_ex(tt_handle h, int nsteps, int flags, const int* forced, tt_step_info* info) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (nsteps < 0) return fail(TT_ERR_ARG, "tt_sn_step: nsteps < 0");
     if (flags & ~(TT_STEP_NO_SOURCE | TT_STEP_NO_ROUND)) return fail(TT_ERR_ARG, "tt_sn_step: unknown flag");
     const int nforced = (h->rounds == 2 && !(flags & (TT_STEP_NO_SOURCE | TT_STEP_NO_ROUND))) ? 2 * (h->d - 1) : h->d - 1;
@@ -1116,6 +1165,7 @@ tt_status tt_sn_step(tt_handle h, int nsteps, tt_step_info* info) {
 tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
     if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0)
         return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs FP64 precision, one rounding "
@@ -1133,6 +1183,7 @@ tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
 tt_status tt_tape_objective(tt_handle h, double* Q_host, int* steps_host) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (!Q_host) return fail(TT_ERR_ARG, "tt_tape_objective: null Q");
     TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_Q, h->d_dbl + HD_Q, sizeof(double),
                                 cudaMemcpyDeviceToHost, h->stream));
@@ -1145,6 +1196,7 @@ tt_status tt_tape_objective(tt_handle h, double* Q_host, int* steps_host) {
 tt_status tt_sn_step_adjoint(tt_handle h, double* grad_sigma_a_dev, double* Q_host) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (!h->taping && h->tape.empty()) return fail(TT_ERR_STATE, "tt_sn_step_adjoint: no tape");
     tt_status st = adjoint_run(h, grad_sigma_a_dev, Q_host);
     if (st < 0) return st;
@@ -1154,6 +1206,7 @@ tt_status tt_sn_step_adjoint(tt_handle h, double* grad_sigma_a_dev, double* Q_ho
 tt_status tt_tape_clear(tt_handle h) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     clear_tape(h);
     return TT_OK;
 }
@@ -1161,6 +1214,7 @@ tt_status tt_tape_clear(tt_handle h) {
 tt_status tt_round(tt_handle h, double eps, int max_rank, const int* forced, tt_step_info* info) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     clear_tape(h);  // a change of state outside a step ends the tape
     if (eps < 0.0) return fail(TT_ERR_ARG, "tt_round: eps < 0");
     if (forced)
@@ -1184,6 +1238,7 @@ tt_status tt_round(tt_handle h, double eps, int max_rank, const int* forced, tt_
 tt_status tt_energy(tt_handle h, double* E_dev, double* T_dev, double* totals_host) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
     cudaStream_t s = h->stream;
     const long nc = h->grid.nc;
     const int r1 = h->r[1], r2 = h->r[2];
@@ -1211,6 +1266,7 @@ tt_status tt_energy(tt_handle h, double* E_dev, double* T_dev, double* totals_ho
 tt_status tt_to_full(tt_handle h, double* out_dev, size_t out_len) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (!out_dev) return fail(TT_ERR_ARG, "tt_to_full: null output");
     cudaStream_t s = h->stream;
     const int d = h->d;
@@ -1246,6 +1302,7 @@ tt_status tt_to_full(tt_handle h, double* out_dev, size_t out_len) {
 
 tt_status tt_get_ranks(tt_handle h, int* ranks_host, int cap) {
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (!ranks_host) return fail(TT_ERR_ARG, "tt_get_ranks: null output");
     for (int k = 0; k <= h->d && k < cap; ++k) ranks_host[k] = h->r[k];
     return TT_OK;
@@ -1253,6 +1310,7 @@ tt_status tt_get_ranks(tt_handle h, int* ranks_host, int cap) {
 
 tt_status tt_get_dims(tt_handle h, int* d_host, int* n_host) {
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (d_host) *d_host = h->d;
     if (n_host)
         for (int k = 0; k < h->d; ++k) n_host[k] = h->n[k];
@@ -1262,6 +1320,7 @@ tt_status tt_get_dims(tt_handle h, int* d_host, int* n_host) {
 tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (k < 0 || k >= h->d) return fail(TT_ERR_ARG, "tt_get_core: k out of range");
     const size_t len = h->core_len(k, h->r);
     if (out_len < len) return fail(TT_ERR_TOO_LARGE, "tt_get_core: output buffer too small");
@@ -1270,9 +1329,24 @@ tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len) {
     return TT_OK;
 }
 
+tt_status tt_get_cores(tt_handle h, double** cores_dev, int* shapes_host) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (!cores_dev || !shapes_host) return fail(TT_ERR_ARG, "tt_get_cores: null argument");
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < h->d; ++k) {
+        cores_dev[k] = h->core[k].p;
+        shapes_host[3 * k] = h->r[k];
+        shapes_host[3 * k + 1] = h->n[k];
+        shapes_host[3 * k + 2] = h->r[k + 1];
+    }
+    return TT_OK;
+}
+
 tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* ranks_host) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     clear_tape(h);  // a change of state outside a step ends the tape
     if (!cores_dev || !ranks_host) return fail(TT_ERR_ARG, "tt_set_cores: null argument");
     if (ranks_host[0] != 1 || ranks_host[h->d] != 1)
@@ -1294,6 +1368,7 @@ tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const doub
                          const double* phi_dev) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (count < 0 || count > TT_MAX_SOURCES)
         return fail(TT_ERR_ARG, "tt_set_sources: count out of range");
     if (count > 0 && (!x_dev || !theta_dev || !phi_dev))
@@ -1337,6 +1412,7 @@ tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const doub
 tt_status tt_set_precision(tt_handle h, int precision) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     clear_tape(h);  // a change of state outside a step ends the tape
     if (precision != TT_FP64 && precision != TT_MIXED)
         return fail(TT_ERR_ARG, "tt_set_precision: precision must be TT_FP64 or TT_MIXED");
@@ -1347,6 +1423,7 @@ tt_status tt_set_precision(tt_handle h, int precision) {
 tt_status tt_set_T(tt_handle h, const double* T_dev) {
     set_error("");
     TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
     clear_tape(h);  // a change of state outside a step ends the tape
     if (!T_dev) return fail(TT_ERR_ARG, "tt_set_T: null input");
     TT_CUDA_TRY(cudaMemcpyAsync(h->f_T.p, T_dev, h->grid.nc * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -1357,6 +1434,7 @@ tt_status tt_set_T(tt_handle h, const double* T_dev) {
 tt_status tt_sync(tt_handle h) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return read_status(h);
 }
@@ -1448,6 +1526,7 @@ tt_status tt_syev(int n, const double* G, int ldg, double* lam, double* Vt, int 
 tt_status tt_profile(tt_handle h, int enable) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     resolve_profile(h);
     h->prof_on = enable != 0;
@@ -1460,6 +1539,7 @@ tt_status tt_profile_read(tt_handle h, int phase, double* ms, long long* launche
                           long long* calls, double* flops, double* bytes) {
     set_error("");
     TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
     if (phase < 0 || phase >= TT_NPHASES) return fail(TT_ERR_ARG, "tt_profile_read: bad phase");
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     resolve_profile(h);

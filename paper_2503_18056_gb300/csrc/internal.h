@@ -50,8 +50,22 @@ tt_status ensure_max_dynamic_smem(const void* kernel);
 struct DevBuf {
     double* p = nullptr;
     size_t cap = 0;  // in doubles
+    // the allocator that provided p (null: cudaMallocAsync / cudaFree) and the
+    // stream it was requested on; taken from the calling thread's current
+    // allocator (AllocScope) when the buffer first allocates
+    const tt_allocator* alloc = nullptr;
+    cudaStream_t astream = nullptr;
     tt_status ensure(size_t n, cudaStream_t s, bool keep = false);
     void release();
+};
+
+// The device allocator a handle was created with, current on this thread for
+// the duration of a call on that handle (null: the stream-ordered pool).
+const tt_allocator* current_allocator();
+struct AllocScope {
+    const tt_allocator* prev;
+    explicit AllocScope(const tt_allocator* a);
+    ~AllocScope();
 };
 
 // ---------------------------------------------------------------- GEMM (gemm.cu)
@@ -120,7 +134,8 @@ struct EigWork {
     DevBuf lam_unsorted;
     DevBuf vt_unsorted;
     DevBuf abc;             // per-round pair entries (double-buffered)
-    int* d_ctrl = nullptr;  // barrier counters, sweep counters, status
+    DevBuf ctrl_buf;
+    int* d_ctrl = nullptr;  // barrier counters, sweep counters, status (in ctrl_buf)
     int ctrl_cap = 0;
     void release();
 };

@@ -496,7 +496,8 @@ tt_status coop_blocks(const void* fn, size_t smem, int want, int* out) {
 
 tt_status ensure_ctrl(EigWork& w, cudaStream_t s) {
     if (!w.d_ctrl) {
-        TT_CUDA_TRY(cudaMalloc(&w.d_ctrl, CTRL_INTS * sizeof(int)));
+        TT_TRY(w.ctrl_buf.ensure((CTRL_INTS * sizeof(int) + 7) / 8, s));
+        w.d_ctrl = reinterpret_cast<int*>(w.ctrl_buf.p);
         w.ctrl_cap = CTRL_INTS;
     }
     TT_CUDA_TRY(cudaMemsetAsync(w.d_ctrl, 0, CTRL_INTS * sizeof(int), s));
@@ -511,7 +512,7 @@ void EigWork::release() {
     lam_unsorted.release();
     vt_unsorted.release();
     abc.release();
-    if (d_ctrl) cudaFree(d_ctrl);
+    ctrl_buf.release();
     d_ctrl = nullptr;
     ctrl_cap = 0;
 }
