@@ -19,6 +19,9 @@ Modules (each function cites the passage of arXiv 2503.18056 it follows):
                   the Gram-SVD truncation (App. A.2, Eq. gramfinal).
 * ``ttstep``   -- the step-then-truncate TT stepper of Sec. 4.3-4.5 on the
                   paper's grouped-space three-core layout (Eq. tensor_decomp).
+* ``split``    -- the same step on the split-space layout (one core per
+                  spatial axis, then theta and phi; Sec. 4.1, Sec. 7), with
+                  the spatial fields s and e entering as TT-SVDs of the field.
 
 Every function here is pinned by ``-m "not gpu"`` tests against closed forms,
 invariants and brute force; none is "parity unpinned".

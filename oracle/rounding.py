@@ -82,8 +82,11 @@ def right_grams(cores):
     last = cores[d - 1][:, :, 0]
     GB[d - 2] = last @ last.T
     for k in range(d - 3, -1, -1):
+        # the two contractions of App. A.2's backward sweep:
+        # W = G_{k+1} x_3 GB[k+1], then GB[k] = W x_{2,3} G_{k+1}
         C = cores[k + 1]
-        GB[k] = np.einsum("aic,cd,bid->ab", C, GB[k + 1], C)
+        W = np.tensordot(C, GB[k + 1], axes=([2], [0]))
+        GB[k] = np.tensordot(W, C, axes=([1, 2], [1, 2]))
     return GB
 
 
