@@ -64,7 +64,9 @@ def parse():
     ap.add_argument("--no-beams", action="store_true", help="skip the crossing-beam precision leg")
     ap.add_argument("--beams-preroll", type=int, default=100)
     ap.add_argument("--beams-steps", type=int, default=20)
-    ap.add_argument("--only", choices=["adjoint", "beams", "batch"], default=None,
+    ap.add_argument("--no-split", action="store_true", help="skip the split-layout leg")
+    ap.add_argument("--split-steps", type=int, default=5, help="timed steps of the 3D split-layout run")
+    ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split"], default=None,
                     help="run only this companion leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
@@ -251,12 +253,15 @@ def run_ours(args, rank, world, local_rank):
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(args, torch, ttsn)
+    split = None
+    if not args.no_split:
+        split = run_split(args, torch, ttsn)
     beams = None
     if not args.no_beams:
         beams = run_beams(args, torch, ttsn, fp64_peak, mixed["bf16_peak"] if mixed else None)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
-               adjoint=adjoint, beams=beams)
+               adjoint=adjoint, beams=beams, split=split)
     return res
 
 
@@ -311,6 +316,67 @@ def run_beams(args, torch, ttsn, fp64_peak, bf16_peak):
             "ranks_last": ranks[-1],
             "phases_ms": {n: {k: round(v["ms"], 3) for k, v in out[n][1].items()} for n in out},
             "mixed_roofline": roof}
+
+
+def run_split(args, torch, ttsn):
+    """Split-space layout (one core per spatial axis, then theta and phi).
+    (a) The 2D 32^2 x (8 x 16) Gaussian-pulse problem as four cores (x, y,
+    theta, phi), 10 steps from t = 0 at eps 1e-8, beside the same steps in the
+    grouped three-core layout; (b) a 3D 128^3 x (32 x 64) problem as five cores
+    with uniform sigma_a = 1 (the split layout needs a uniform absorption
+    factor), the hot sphere, vacuum, eps 1e-6, ranks <= 128: 2 warm-up steps,
+    then K_s timed steps.  CUDA events on each handle's stream."""
+    out = {}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        p = workloads.problem("small_2d")
+        res2 = {}
+        for name, layout in (("split", ttsn.TT_LAYOUT_SPLIT), ("grouped", ttsn.TT_LAYOUT_GROUPED)):
+            ttsn.TTSN.from_problem(p, layout=layout, stream=stream).step(p["steps"])  # warm-up
+            g = ttsn.TTSN.from_problem(p, layout=layout, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = ttsn.kernel_launches()
+            e0.record(stream)
+            info = g.step(p["steps"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            res2[name] = {"steps_per_s": p["steps"] / (ms * 1e-3), "ms_per_step": ms / p["steps"],
+                          "gpu_launches": ttsn.kernel_launches() - l0,
+                          "ranks_last": info["ranks"][1:-1]}
+        upd = int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"]
+        for v in res2.values():
+            v["updates_per_s"] = v["steps_per_s"] * upd
+        out["small_2d"] = dict(workload="2D 32^2 cells, 8x16 ordinates, sigma_a 1, Gaussian T pulse, "
+                                        "periodic, CFL 0.5, eps 1e-8, steps 1..10; split = 4 cores "
+                                        "(x, y, theta, phi), grouped = 3 cores", **res2)
+        n = (128, 128, 128)
+        p3 = workloads.problem("blob_3d", sigma_a=np.ones(n))
+        g = ttsn.TTSN.from_problem(p3, layout=ttsn.TT_LAYOUT_SPLIT, stream=stream)
+        r0 = g.ranks()
+        g.step(2)
+        torch.cuda.synchronize()
+        g.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ranks = []
+        for _ in range(args.split_steps):
+            ranks.append(g.step()["ranks"][1:-1])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = g.profile_read()
+        g.profile(False)
+        upd3 = int(np.prod(n)) * p3["n_theta"] * p3["n_phi"]
+        v = args.split_steps / (ms * 1e-3)
+        out["sphere_3d"] = {"workload": "3D 128^3 cells, 32x64 ordinates, 5 cores (x, y, z, theta, phi), "
+                                        "uniform sigma_a 1, hot sphere T 1 (r 0.1) in 1e-3, vacuum, CFL 0.5, "
+                                        "eps 1e-6, ranks <= 128; steps 3..%d" % (2 + args.split_steps),
+                            "steps_per_s": v, "updates_per_s": v * upd3, "ms_per_step": ms / args.split_steps,
+                            "ranks_initial": r0[1:-1], "ranks": ranks,
+                            "phases_ms": {k: round(x["ms"], 3) for k, x in prof.items()}}
+    return out
 
 
 def run_adjoint(args, torch, ttsn):
@@ -554,6 +620,8 @@ def main():
             out = run_adjoint(args, torch, ttsn)
         elif args.only == "beams":
             out = run_beams(args, torch, ttsn, ttsn.fp64_mma_peak(), ttsn.bf16_mma_peak())
+        elif args.only == "split":
+            out = run_split(args, torch, ttsn)
         else:
             out = run_batch(args, torch, ttsn)
         print(json.dumps({args.only: out}))
@@ -619,6 +687,8 @@ def main():
         line["adjoint"] = res["adjoint"]
     if res.get("beams") is not None:
         line["beams"] = res["beams"]
+    if res.get("split") is not None:
+        line["split"] = res["split"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

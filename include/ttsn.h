@@ -49,6 +49,7 @@ typedef enum {
 
 enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1 };
 enum { TT_FP64 = 0, TT_MIXED = 1 };
+enum { TT_LAYOUT_GROUPED = 0, TT_LAYOUT_SPLIT = 1 };
 
 /* step flags for tt_sn_step_ex */
 enum {
@@ -82,8 +83,19 @@ enum {
  * tt_gemm_nt_mixed: about 2^-48 of the operands' scales per term);
  * eigensolves, rank decisions, the small R x R products, the quartic and the
  * temperature update stay FP64.
- * The intensity is held in the paper's three-core layout (Eq. tensor_decomp):
- * X (1, N_c, r1), Theta (r1, n_theta, r2), Phi (r2, n_phi, 1).
+ * layout: TT_LAYOUT_GROUPED holds the intensity in the paper's three-core
+ * layout (Eq. tensor_decomp, all spatial axes in one core so that arbitrary
+ * material fields cost nothing): X (1, N_c, r1), Theta (r1, n_theta, r2),
+ * Phi (r2, n_phi, 1).  TT_LAYOUT_SPLIT holds one core per spatial axis, then
+ * Theta and Phi (the split-space alternative of Sec. 4.1 / Sec. 7; d = ndim +
+ * 2 cores, core a of shape (r_a, n[a], r_{a+1})).  In the split layout every
+ * transport term is a TT with D^-/+ on one spatial core, the emission field e
+ * enters as one more TT term holding e exactly (ranks N_x[, N_z] at the
+ * spatial bonds before rounding), and the initial intensity is held the same
+ * way and rounded to eps at creation.  It needs uniform sigma_a and sigma_s
+ * (TT_ERR_ARG otherwise: a varying absorption factor would multiply every
+ * spatial rank) and takes neither fixed sources nor the adjoint tape
+ * (TT_ERR_STATE).
  */
 typedef struct {
     int ndim;
@@ -101,6 +113,7 @@ typedef struct {
     int max_rank;
     int rounds_per_step;
     int precision;
+    int layout;
 } tt_problem_desc;
 
 /* Diagnostics of the last rounding performed by a call (host struct). */
@@ -240,6 +253,7 @@ tt_status tt_set_T(tt_handle h, const double* T_dev);
  * in: x_dev count x N_c (cell order as the fields), theta_dev count x n_theta,
  * phi_dev count x n_phi, row-major.  Ends any adjoint tape; the adjoint form
  * does not take sources (tt_tape_begin returns TT_ERR_STATE while any are set).
+ * Grouped layout only (TT_ERR_STATE on a split-layout handle).
  */
 tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const double* theta_dev,
                          const double* phi_dev);
@@ -354,6 +368,18 @@ tt_status tt_dgemm(int trans_a, int trans_b, int M, int N, int K, double alpha,
  * (number of row splits) * n * n doubles allocated by the library.
  */
 tt_status tt_gram(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg, void* stream);
+
+/*
+ * tt_pchol: pivoted Cholesky factor of a symmetric positive semidefinite n x n
+ * matrix G (leading dimension ldg), the factor of the right Gram matrix that
+ * the one-sided truncation uses (W^T W = G_B, App. A.2): the pivot is the
+ * largest remaining diagonal entry and the factorisation stops when it falls
+ * to eps_mach times the largest initial diagonal entry.  W_dev (n x n,
+ * row-major, leading dimension n) receives the rank_host rows of W (rows
+ * beyond it are unspecified); G is not modified.  TT_ERR_TOO_LARGE if n x 8
+ * bytes exceed the shared-memory limit of one CTA (n > 25600).
+ */
+tt_status tt_pchol(int n, const double* G_dev, int ldg, double* W_dev, void* stream, int* rank_host);
 
 /*
  * tt_syev: eigendecomposition G = V diag(lam) V^T of a symmetric n x n matrix

@@ -13,12 +13,12 @@ import numpy as np
 import torch
 
 from . import _native
-from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_MIXED, TT_STEP_NO_ROUND,
-                      TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
+from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT,
+                      TT_MIXED, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TTSNBatch", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev",
+__all__ = ["TTSN", "TTSNBatch", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
            "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
-           "TT_STEP_NO_ROUND"]
+           "TT_STEP_NO_ROUND", "TT_LAYOUT_GROUPED", "TT_LAYOUT_SPLIT"]
 
 
 def _stream_ptr(stream=None):
@@ -159,7 +159,9 @@ def _torch_allocator():
 
 
 class TTSN(_Handle):
-    """A TT-S_N problem (paper's three-core layout) on the current CUDA stream.
+    """A TT-S_N problem on the current CUDA stream, in the paper's three-core
+    layout (``layout=TT_LAYOUT_GROUPED``) or with one core per spatial axis
+    (``TT_LAYOUT_SPLIT``; uniform sigma_a and sigma_s).
 
     Fields are array-likes of N_c values in C order of the grid (axis 0
     slowest); they are copied to the device and then into the library.
@@ -167,7 +169,8 @@ class TTSN(_Handle):
 
     def __init__(self, n, L, n_theta, n_phi, sigma_a, cv, T0, Tr0=None, sigma_s=None, c=1.0,
                  a_r=1.0, dt=0.0, cfl=0.5, bc=TT_BC_PERIODIC, eps=1e-6, max_rank=0,
-                 rounds_per_step=1, precision=TT_FP64, stream=None, allocator=None):
+                 rounds_per_step=1, precision=TT_FP64, stream=None, allocator=None,
+                 layout=TT_LAYOUT_GROUPED):
         super().__init__()
         ndim = len(n)
         nc = 1
@@ -194,6 +197,8 @@ class TTSN(_Handle):
             setattr(desc, key, f[key].data_ptr() if f[key] is not None else None)
         desc.eps, desc.max_rank = float(eps), int(max_rank or 0)
         desc.rounds_per_step, desc.precision = int(rounds_per_step), int(precision)
+        desc.layout = int(layout)
+        self.layout = int(layout)
         self._alloc = None
         if allocator == "torch":
             self._alloc = _torch_allocator()
@@ -431,6 +436,18 @@ def gram_noalloc(A, G=None, stream=None):
     check(lib.tt_gram_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), n, ctypes.c_void_p(G.data_ptr()),
                               n, _stream_ptr(stream)))
     return G
+
+
+def pchol(G, stream=None):
+    """(W with W^T W = G, rank): pivoted Cholesky of a symmetric PSD matrix,
+    stopped at eps_mach times the largest diagonal entry (tt_pchol)."""
+    G = _dev(G)
+    n = G.shape[0]
+    W = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    rank = ctypes.c_int()
+    check(lib.tt_pchol(n, ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(W.data_ptr()),
+                       _stream_ptr(stream), ctypes.byref(rank)))
+    return W[: rank.value].clone(), rank.value
 
 
 def syev(G, stream=None, allow_unconverged=False):

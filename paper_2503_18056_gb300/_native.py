@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "TT_OK", 1: "TT_WARN_RANK_CAPPED", -1: "TT_ERR_ARG", -2: "TT_
                 -6: "TT_ERR_STATE", -7: "TT_ERR_TOO_LARGE"}
 TT_BC_PERIODIC, TT_BC_VACUUM = 0, 1
 TT_FP64, TT_MIXED = 0, 1
+TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT = 0, 1
 TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
 
 
@@ -38,6 +39,7 @@ class ProblemDesc(ctypes.Structure):
         ("T0", ctypes.c_void_p), ("Tr0", ctypes.c_void_p),
         ("eps", ctypes.c_double), ("max_rank", ctypes.c_int),
         ("rounds_per_step", ctypes.c_int), ("precision", ctypes.c_int),
+        ("layout", ctypes.c_int),
     ]
 
 
@@ -94,6 +96,7 @@ def _load():
         "tt_batch_handle": [vp, i, ctypes.POINTER(vp)],
         "tt_batch_sync": [vp],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
+        "tt_pchol": [i, vp, i, vp, vp, ip],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_longlong), dp, dp],
@@ -133,7 +136,7 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_bench_bf16_mma", "tt_batch_create", "tt_batch_step", "tt_batch_size",
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
             "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
-            "tt_create_ex", "tt_get_cores"]
+            "tt_create_ex", "tt_get_cores", "tt_pchol"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

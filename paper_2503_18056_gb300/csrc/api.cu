@@ -124,7 +124,7 @@ using namespace ttsn;
 
 // host-side slots of the pinned readback block
 enum { HI_KB = 0, HI_DEC = 16, HI_STATUS = 20, HI_SWEEPS = 24, HI_N = 64 };
-enum { HD_DEC = 0, HD_DELTA2 = 4, HD_TOT = 8, HD_Q = 12, HD_N = 16 };
+enum { HD_DEC = 0, HD_DELTA2 = 4, HD_TOT = 8, HD_Q = 12, HD_ONE = 14, HD_N = 16 };
 
 struct tt_ctx {
     cudaStream_t stream = nullptr;
@@ -207,6 +207,14 @@ struct tt_ctx {
     DevBuf f_sigma_a, f_sigma_s, f_cv, f_T, f_Estar, f_E, thbar, red, ang_buf;
     DevBuf src_x, src_th, src_ph, src_q;  // fixed external sources
     int nsrc = 0;
+    // split-space layout (cores x[, y[, z]], theta, phi): per-term angular
+    // factors (theta rows then phi rows, 1 + 2 ndim terms each), the uniform
+    // absorption factor s, the spatial contractions F (nc x terms) and the
+    // contraction chain's intermediates
+    int layout = TT_LAYOUT_GROUPED;
+    DevBuf split_fac, sp_F, sp_tmp[2];
+    double split_s = 1.0;
+    bool split() const { return layout == TT_LAYOUT_SPLIT; }
     bool has_sigma_s = false;
     double eps = 0.0;
     int max_rank = 0;
@@ -235,6 +243,7 @@ struct tt_ctx {
         TT_CUDA_TRY(cudaMallocHost(&h_int, HI_N * sizeof(int)));
         TT_CUDA_TRY(cudaMallocHost(&h_dbl, HD_N * sizeof(double)));
         TT_CUDA_TRY(cudaMemsetAsync(d_int, 0, HI_N * sizeof(int), s));
+        fill(s, d_dbl + HD_ONE, 1, 1.0);
         return TT_OK;
     }
     ~tt_ctx() {
@@ -248,7 +257,8 @@ struct tt_ctx {
         }
         DevBuf* bufs[] = {&slscratch, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
-                          &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q};
+                          &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
+                          &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1]};
         for (DevBuf* b : bufs) b->release();
         eig.release();
         for (StepRec* r : tape) {
@@ -420,7 +430,7 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             const int Rk = R[k + 1];
             TT_TRY(h->VtB[k].ensure((size_t)Rk * Rk, s));
             TT_TRY(h->Wc.ensure((size_t)Rk * Rk, s));
-            TT_TRY(h->lamB[k].ensure((size_t)Rk, s));
+            TT_TRY(h->lamB[k].ensure((size_t)2 * Rk, s));
             TT_TRY(pchol(s, Rk, h->GB[k].p, Rk, h->VtB[k].p, h->Wc.p, h->lamB[k].p, h->eig,
                          h->d_int + HI_STATUS, h->d_int + HI_KB + k));
         }
@@ -554,7 +564,146 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
 }
 
 // Build the grown TT (transport terms and/or source) from h->core into h->gcore.
+// ---------------------------------------------------------------- split-space layout
+// Ranks of the emission term's TT at bonds 0..d (Sec. 3.2 e (x) 1 (x) 1 with
+// e held exactly: 1D a column; 2D [I_{N_x}][e]; 3D [I_{N_x}][e][I_{N_z}]).
+void split_emission_ranks(const tt_ctx* h, int* er) {
+    const int nd = h->grid.ndim, d = h->d;
+    for (int k = 0; k <= d; ++k) er[k] = 1;
+    if (nd >= 2) er[1] = h->grid.n[0];
+    if (nd == 3) er[2] = h->grid.n[2];
+}
+
+// Core k's spec in a grown split TT with K transport terms (ranks r -> R)
+// and, if emission, the emission term's block.
+SplitCoreSpec split_spec(const tt_ctx* h, int k, int K, bool emission, const int* r, const int* R,
+                         double tscale) {
+    const int nd = h->grid.ndim;
+    SplitCoreSpec c{};
+    c.kind = k < nd ? SPLIT_SPATIAL : (k == nd ? SPLIT_THETA : SPLIT_PHI);
+    c.axis = k < nd ? k : -1;
+    c.bc = k < nd ? h->grid.bc[k] : TT_BC_PERIODIC;
+    c.first = k == 0;
+    c.last = k == h->d - 1;
+    c.K = K;
+    c.ra = r[k];
+    c.n = h->n[k];
+    c.rb = r[k + 1];
+    c.Ra = R[k];
+    c.Rb = R[k + 1];
+    c.tscale = c.kind == SPLIT_PHI ? tscale : 1.0;
+    c.ekind = SPLIT_E_NONE;
+    if (emission) {
+        if (k >= nd)
+            c.ekind = SPLIT_E_ONES;
+        else if (nd == 1 || k == 1)
+            c.ekind = SPLIT_E_FIELD;
+        else if (k == 0)
+            c.ekind = SPLIT_E_IDENT_COL;
+        else
+            c.ekind = SPLIT_E_IDENT_ROW;  // 3D z core
+    }
+    return c;
+}
+
+// Where e_i of cell (c0, c1, c2) goes in the grown core that holds the field
+// block (core 0 in 1D, core 1 otherwise): base pointer and coordinate strides.
+double* split_eblock(tt_ctx* h, int K, const int* r, const int* R, long* st) {
+    const int nd = h->grid.ndim;
+    if (nd == 1) {  // first core (1 x N_x x R1), block column K r1
+        st[0] = R[1];
+        st[1] = st[2] = 0;
+        return h->gcore[0].p + (long)K * r[1];
+    }
+    const long n1 = h->n[1];
+    st[0] = n1 * R[2];
+    st[1] = R[2];
+    st[2] = 1;
+    return h->gcore[1].p + ((long)K * r[1] * n1) * R[2] + (long)K * r[2];
+}
+
+// out (nc x P, cell-major) = the spatial cores of the current TT contracted
+// with P right vectors of the last spatial bond (U: P x r_ndim, row-major),
+// by one GEMM per spatial core from the right: Z <- G_k (r_{k-1} n_k x r_k) Z.
+tt_status split_contract(tt_ctx* h, const double* U, int P, double* out) {
+    cudaStream_t s = h->stream;
+    const int nd = h->grid.ndim;
+    long cols = P;
+    const double* Z = U;
+    bool zt = true;  // the first right factor is U^T
+    int ti = 0;
+    for (int k = nd - 1; k >= 0; --k) {
+        const long rows = (long)h->r[k] * h->n[k];
+        double* dst;
+        if (k == 0) {
+            dst = out;
+        } else {
+            TT_TRY(h->sp_tmp[ti].ensure((size_t)(rows * cols), s));
+            dst = h->sp_tmp[ti].p;
+            ti ^= 1;
+        }
+        TT_TRY(dgemm(s, false, zt, (int)rows, (int)cols, h->r[k + 1], 1.0, h->core[k].p, h->r[k + 1], Z,
+                     zt ? h->r[k + 1] : cols, 0.0, dst, cols));
+        Z = dst;
+        zt = false;
+        cols *= h->n[k];
+    }
+    return TT_OK;
+}
+
+// E-field of the current TT times c (F_i = sum_lp I_ilp dOmega) into sp_F.
+tt_status split_energy_field(tt_ctx* h) {
+    cudaStream_t s = h->stream;
+    const int nd = h->grid.ndim;
+    const int ra = h->r[nd], rb = h->r[nd + 1];
+    TT_TRY(h->thbar.ensure((size_t)(ra + rb), s));
+    plain_thbar(s, h->ang, ra, rb, h->core[nd].p, h->core[nd + 1].p, h->thbar.p);
+    TT_TRY(h->sp_F.ensure((size_t)h->grid.nc, s));
+    return split_contract(h, h->thbar.p, 1, h->sp_F.p);
+}
+
+// Grown split TT (transport terms and/or emission) from h->core into h->gcore.
+tt_status split_apply_terms(tt_ctx* h, bool transport, bool source) {
+    cudaStream_t s = h->stream;
+    const int nd = h->grid.ndim, d = h->d;
+    const int K = transport ? 1 + 2 * nd : 1;
+    int er[TT_MAX_D + 1], R[TT_MAX_D + 1];
+    split_emission_ranks(h, er);
+    R[0] = R[d] = 1;
+    for (int k = 1; k < d; ++k) R[k] = K * h->r[k] + (source ? er[k] : 0);
+    double by = 0.0;
+    for (int k = 0; k < d; ++k) by += 8.0 * ((double)h->core_len(k, h->r) + (double)R[k] * h->n[k] * R[k + 1]);
+    PhaseScope ps(h, TT_PH_TRANSPORT, 0.0, by + (source ? 8.0 * 6.0 * h->grid.nc : 0.0));
+    if (source) {
+        // E* pieces: term j's angular cores integrated (U: K x r_ndim), then
+        // the spatial cores contracted with each (F: nc x K)
+        const int ra = h->r[nd], rb = h->r[nd + 1];
+        TT_TRY(h->thbar.ensure((size_t)K * (ra + rb), s));
+        grown_thbar(s, h->ang, nd, transport, ra, rb, h->core[nd].p, h->core[nd + 1].p, h->thbar.p);
+        TT_TRY(h->sp_F.ensure((size_t)h->grid.nc * K, s));
+        TT_TRY(split_contract(h, h->thbar.p, K, h->sp_F.p));
+    }
+    const double* thf = h->split_fac.p;
+    const double* phf = thf + (size_t)(1 + 2 * nd) * h->ang.n_theta;
+    for (int k = 0; k < d; ++k) {
+        TT_TRY(h->gcore[k].ensure((size_t)R[k] * h->n[k] * R[k + 1], s));
+        const SplitCoreSpec c = split_spec(h, k, K, source, h->r, R, source ? h->split_s : 1.0);
+        split_grow_core(s, c, h->core[k].p, k == nd ? thf : phf, h->gcore[k].p);
+    }
+    if (source) {
+        long st[3];
+        double* eb = split_eblock(h, K, h->r, R, st);
+        h->fields.T = h->f_T.p;
+        h->fields.E_star = h->f_Estar.p;
+        split_source_cells(s, h->grid, h->fields, transport, K, h->sp_F.p, eb, st[0], st[1], st[2]);
+    }
+    TT_CUDA_TRY(cudaGetLastError());
+    for (int k = 0; k <= d; ++k) h->gr[k] = R[k];
+    return TT_OK;
+}
+
 tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
+    if (h->split()) return split_apply_terms(h, transport, source);
     cudaStream_t s = h->stream;
     const int r1 = h->r[1], r2 = h->r[2];
     const int nterms = transport ? 1 + 2 * h->grid.ndim : 1;
@@ -602,6 +751,14 @@ void swap_grown_into_current(tt_ctx* h) {
 
 tt_status energy_update(tt_ctx* h) {
     cudaStream_t s = h->stream;
+    if (h->split()) {
+        PhaseScope ps(h, TT_PH_ENERGY, 0.0, 8.0 * h->grid.nc * 5.0);
+        TT_TRY(split_energy_field(h));
+        energy_rows(s, h->grid.nc, 1, h->sp_F.p, 1, h->d_dbl + HD_ONE, h->fields.c, nullptr,
+                    h->f_Estar.p, h->f_cv.p, h->f_T.p, true);
+        TT_CUDA_TRY(cudaGetLastError());
+        return TT_OK;
+    }
     const int r1 = h->r[1], r2 = h->r[2];
     TT_TRY(h->thbar.ensure((size_t)(r1 + r2), s));
     PhaseScope ps(h, TT_PH_ENERGY, 0.0, 8.0 * h->grid.nc * (r1 + 4.0));
@@ -641,9 +798,11 @@ tt_status step_once(tt_ctx* h, int flags, const int* forced, tt_step_info* info)
     int rr[TT_MAX_D + 1];
     h->cur_rec = nullptr;
     if (h->taping || h->replay_rec) {
-        if (!src || !rnd || two || h->precision != TT_FP64 || h->has_sigma_s || !h->physics)
-            return fail(TT_ERR_STATE, "adjoint tape: only plain FP64 transport steps (one rounding, "
-                                      "source on, no scattering) can be recorded");
+        if (!src || !rnd || two || h->precision != TT_FP64 || h->has_sigma_s || !h->physics ||
+            h->split())
+            return fail(TT_ERR_STATE, "adjoint tape: only plain FP64 transport steps (grouped "
+                                      "layout, one rounding, source on, no scattering) can be "
+                                      "recorded");
         tt_ctx::StepRec* rc = h->replay_rec;
         if (h->taping) {
             rc = new tt_ctx::StepRec();
@@ -948,6 +1107,27 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         return fail(TT_ERR_ARG, "tt_create: rounds_per_step must be 1 or 2");
     if (D.precision != TT_FP64 && D.precision != TT_MIXED)
         return fail(TT_ERR_ARG, "tt_create: precision must be TT_FP64 or TT_MIXED");
+    if (D.layout != TT_LAYOUT_GROUPED && D.layout != TT_LAYOUT_SPLIT)
+        return fail(TT_ERR_ARG, "tt_create: layout must be TT_LAYOUT_GROUPED or TT_LAYOUT_SPLIT");
+    double sig_a_uniform = 0.0, sig_s_uniform = 0.0;
+    if (D.layout == TT_LAYOUT_SPLIT) {
+        // the absorption factor s multiplies every spatial rank unless it is
+        // one number, so the split layout takes uniform sigma_a and sigma_s
+        std::vector<double> hv((size_t)nc);
+        for (int pass = 0; pass < 2; ++pass) {
+            const double* src = pass == 0 ? D.sigma_a : D.sigma_s;
+            if (!src) continue;
+            if (cudaMemcpy(hv.data(), src, nc * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(TT_ERR_ARG, "tt_create: sigma_a / sigma_s are not readable device arrays");
+            }
+            for (long i = 1; i < nc; ++i)
+                if (hv[i] != hv[0])
+                    return fail(TT_ERR_ARG, "tt_create: the split layout needs uniform sigma_a and "
+                                            "sigma_s (use the grouped layout for varying fields)");
+            (pass == 0 ? sig_a_uniform : sig_s_uniform) = hv[0];
+        }
+    }
 
     tt_ctx* h = new tt_ctx();
     if (alloc) {
@@ -1046,6 +1226,68 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         delete h;
         return fail(TT_ERR_CUDA, "tt_create: angular grid upload failed");
     }
+    if (D.layout == TT_LAYOUT_SPLIT) {
+        // cores x[, y[, z]], theta, phi
+        h->layout = TT_LAYOUT_SPLIT;
+        const int nd = D.ndim;
+        h->d = nd + 2;
+        for (int a = 0; a < nd; ++a) h->n[a] = D.n[a];
+        h->n[nd] = D.n_theta;
+        h->n[nd + 1] = D.n_phi;
+        for (int k = 0; k <= h->d; ++k) h->r[k] = 1;
+        // per-term angular factors (term order [I, x+, x-, y+, y-, z+, z-]):
+        // theta carries -nu_a times the masked theta factor, phi the masked
+        // phi factor (the direction cosines of Sec. 4.3)
+        const int K = 1 + 2 * nd;
+        std::vector<double> fac((size_t)K * (D.n_theta + D.n_phi));
+        double* thf = fac.data();
+        double* phf = thf + (size_t)K * D.n_theta;
+        for (int j = 0; j < K; ++j) {
+            const int axis = (j - 1) >> 1;
+            const bool plus = ((j - 1) & 1) == 0;
+            const double nu = j == 0 ? 0.0 : f.c * f.dt / g.dx[axis];
+            for (int l = 0; l < D.n_theta; ++l) {
+                const double mu = hbuf[l], st = hbuf[D.n_theta + l];
+                double v = 1.0;
+                if (j > 0) v = -nu * (axis < 2 ? st : (plus ? std::max(mu, 0.0) : std::min(mu, 0.0)));
+                thf[(size_t)j * D.n_theta + l] = v;
+            }
+            for (int p = 0; p < D.n_phi; ++p) {
+                const double cp = hbuf[2 * D.n_theta + p], sp = hbuf[2 * D.n_theta + D.n_phi + p];
+                double v = 1.0;
+                if (j > 0 && axis == 0) v = plus ? std::max(cp, 0.0) : std::min(cp, 0.0);
+                if (j > 0 && axis == 1) v = plus ? std::max(sp, 0.0) : std::min(sp, 0.0);
+                phf[(size_t)j * D.n_phi + p] = v;
+            }
+        }
+        TT_CREATE_TRY(h->split_fac.ensure(fac.size(), s));
+        if (cudaMemcpyAsync(h->split_fac.p, fac.data(), fac.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            delete h;
+            return fail(TT_ERR_CUDA, "tt_create: split factor upload failed");
+        }
+        h->split_s = 1.0 / (1.0 + f.c * f.dt * sig_a_uniform + f.c * f.dt * sig_s_uniform);
+        // initial TT: the isotropic equilibrium intensity held exactly (the
+        // emission term's block structure with I0 in the field block), then
+        // rounded to the problem's tolerance and rank cap
+        int er[TT_MAX_D + 1];
+        split_emission_ranks(h, er);
+        for (int k = 0; k < h->d; ++k) {
+            TT_CREATE_TRY(h->gcore[k].ensure((size_t)er[k] * h->n[k] * er[k + 1], s));
+            const SplitCoreSpec c = split_spec(h, k, 0, true, h->r, er, 1.0);
+            split_grow_core(s, c, nullptr, nullptr, h->gcore[k].p);
+        }
+        init_isotropic(s, nc, D.Tr0 ? D.Tr0 : D.T0, D.c, D.a_r, h->gcore[nd == 1 ? 0 : 1].p);
+        int rr[TT_MAX_D + 1];
+        TT_CREATE_TRY(round_cores(h, h->gcore, er, h->core, rr, h->eps, h->max_rank, nullptr, nullptr));
+        for (int k = 0; k <= h->d; ++k) h->r[k] = rr[k];
+        if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            delete h;
+            return fail(TT_ERR_CUDA, "tt_create: initialisation failed");
+        }
+        *out = h;
+        return TT_OK;
+    }
     // initial TT: isotropic equilibrium intensity with Tr0, rank (1, 1)
     TT_CREATE_TRY(h->core[0].ensure((size_t)nc, s));
     TT_CREATE_TRY(h->core[1].ensure((size_t)D.n_theta, s));
@@ -1071,7 +1313,7 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
             const long Rk = k == 0 ? R1 : R2;
             TT_CREATE_TRY(h->GB[k].ensure((size_t)(Rk * Rk), s));
             TT_CREATE_TRY(h->VtB[k].ensure((size_t)(Rk * Rk), s));
-            TT_CREATE_TRY(h->lamB[k].ensure((size_t)Rk, s));
+            TT_CREATE_TRY(h->lamB[k].ensure((size_t)(2 * Rk), s));
         }
         // rounding workspaces at their largest (bond 1 of a capped step)
         const size_t RR = (size_t)(R1 * R1);
@@ -1167,9 +1409,11 @@ tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
     TT_TRY(check_handle(h, true));
     AllocScope alloc_scope_(h->alloc_ptr());
     if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
-    if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0)
-        return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs FP64 precision, one rounding "
-                                  "per step, no scattering and no external sources");
+    if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0 ||
+        h->split())
+        return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs the grouped layout, FP64 "
+                                  "precision, one rounding per step, no scattering and no external "
+                                  "sources");
     clear_tape(h);
     h->taping = true;
     h->tape_every = checkpoint_every;
@@ -1241,12 +1485,18 @@ tt_status tt_energy(tt_handle h, double* E_dev, double* T_dev, double* totals_ho
     AllocScope alloc_scope_(h->alloc_ptr());
     cudaStream_t s = h->stream;
     const long nc = h->grid.nc;
-    const int r1 = h->r[1], r2 = h->r[2];
-    TT_TRY(h->thbar.ensure((size_t)(r1 + r2), s));
-    plain_thbar(s, h->ang, r1, r2, h->core[1].p, h->core[2].p, h->thbar.p);
     double* E = E_dev ? E_dev : h->f_E.p;
-    energy_rows(s, nc, r1, h->core[0].p, r1, h->thbar.p, h->fields.c, E, nullptr, nullptr, nullptr,
-                false);
+    if (h->split()) {
+        TT_TRY(split_energy_field(h));
+        energy_rows(s, nc, 1, h->sp_F.p, 1, h->d_dbl + HD_ONE, h->fields.c, E, nullptr, nullptr,
+                    nullptr, false);
+    } else {
+        const int r1 = h->r[1], r2 = h->r[2];
+        TT_TRY(h->thbar.ensure((size_t)(r1 + r2), s));
+        plain_thbar(s, h->ang, r1, r2, h->core[1].p, h->core[2].p, h->thbar.p);
+        energy_rows(s, nc, r1, h->core[0].p, r1, h->thbar.p, h->fields.c, E, nullptr, nullptr,
+                    nullptr, false);
+    }
     if (T_dev)
         TT_CUDA_TRY(cudaMemcpyAsync(T_dev, h->f_T.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (totals_host) {
@@ -1373,6 +1623,8 @@ tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const doub
         return fail(TT_ERR_ARG, "tt_set_sources: count out of range");
     if (count > 0 && (!x_dev || !theta_dev || !phi_dev))
         return fail(TT_ERR_ARG, "tt_set_sources: null source array");
+    if (count > 0 && h->split())
+        return fail(TT_ERR_STATE, "tt_set_sources: fixed sources need the grouped layout");
     clear_tape(h);  // a change of state outside a step ends the tape
     cudaStream_t s = h->stream;
     const long nc = h->grid.nc;
@@ -1494,6 +1746,35 @@ tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A, int lda, const 
     if (scratch.p) cudaFreeAsync(scratch.p, s);
     if (st < 0) return st;
     TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status tt_pchol(int n, const double* G, int ldg, double* W, void* stream, int* rank_host) {
+    set_error("");
+    if (n < 0) return fail(TT_ERR_ARG, "tt_pchol: negative size");
+    if (rank_host) *rank_host = 0;
+    if (n == 0) return TT_OK;
+    if (!G || !W) return fail(TT_ERR_ARG, "tt_pchol: null pointer");
+    if (ldg < n) return fail(TT_ERR_ARG, "tt_pchol: leading dimension smaller than n");
+    cudaStream_t s = (cudaStream_t)stream;
+    EigWork w;
+    DevBuf scratch;  // Wc (n x n) and the double-buffered residual diagonal (2 n)
+    int* d_small = nullptr;
+    tt_status st = scratch.ensure((size_t)n * n + 2 * (size_t)n, s);
+    if (st < 0) return st;
+    TT_CUDA_TRY(cudaMallocAsync((void**)&d_small, 2 * sizeof(int), s));
+    TT_CUDA_TRY(cudaMemsetAsync(d_small, 0, 2 * sizeof(int), s));
+    st = pchol(s, n, G, ldg, W, scratch.p, scratch.p + (size_t)n * n, w, d_small, d_small + 1);
+    int hs[2] = {0, 0};
+    cudaMemcpyAsync(hs, d_small, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d_small, s);
+    scratch.release();
+    w.release();
+    if (st < 0) return st;
+    if (e != cudaSuccess) return fail(TT_ERR_CUDA, std::string("tt_pchol: ") + cudaGetErrorString(e));
+    if (hs[0] & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_pchol: grid barrier wait ran out");
+    if (rank_host) *rank_host = hs[1];
     return TT_OK;
 }
 

@@ -147,7 +147,8 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
 // Pivoted Cholesky of a symmetric positive semidefinite n x n G (ldg): writes
 // W (rows 0..rank-1 of an n x n row-major buffer) with W^T W = G up to the
 // floor eps_mach max(diag G), Wc (n x n scratch, the transpose) and uses
-// dwork (n doubles).  The rank is written to kB_dev.
+// dwork (2 n doubles, the double-buffered residual diagonal).  The rank is
+// written to kB_dev.
 tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, double* Wc,
                 double* dwork, EigWork& w, int* status_dev, int* kB_dev);
 
@@ -223,6 +224,33 @@ void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool 
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
                  double c, double* E_out, const double* E_star, const double* cv, double* T,
                  bool update_T);
+// ---------------------------------------------------------------- split-space layout (split.cu)
+// One core of the grown TT in the split layout (cores x[, y[, z]], theta,
+// phi): the K transport terms (K = 0: none) summed by Sec. 4.1's addition,
+// plus the emission term's block (ekind, shape ea x n x eb) after them.
+enum { SPLIT_SPATIAL = 0, SPLIT_THETA = 1, SPLIT_PHI = 2 };
+enum { SPLIT_E_NONE = 0, SPLIT_E_IDENT_COL = 1, SPLIT_E_IDENT_ROW = 2, SPLIT_E_ONES = 3,
+       SPLIT_E_FIELD = 4 };
+struct SplitCoreSpec {
+    int kind, axis, bc;    // core kind; spatial axis and its boundary rule
+    int first, last;       // position in the train
+    int K;                 // transport terms
+    int ra, n, rb;         // input core (ra x n x rb)
+    int Ra, Rb;            // grown core
+    int ekind;             // emission block kind (SPLIT_E_*)
+    double tscale;         // factor on the transport blocks
+};
+// fac: K x n per-term factors of an angular core (theta: -nu_a times the mask,
+// phi: the mask; row 0 = ones).  G may be null when K = 0.
+void split_grow_core(cudaStream_t s, const SplitCoreSpec& c, const double* G, const double* fac,
+                     double* out);
+// Per-cell source stage of the split layout: E*_i from the K spatial
+// contractions F (nc x K, term-major columns: the identity term, then the
+// upwind differences of the (a, +/-) terms taken here on F), T-dagger from the
+// quartic, e_i written to eblk[c0 st0 + c1 st1 + c2 st2] (cell coordinates),
+// E*_i to f.E_star.
+void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, bool transport, int K,
+                        const double* F, double* eblk, long st0, long st1, long st2);
 // Isotropic initial intensity I = c a_r Tr^4 / 4 pi into X (nc x 1).
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X);
 // Adjoint form (reverse mode with the rounding's projections frozen).

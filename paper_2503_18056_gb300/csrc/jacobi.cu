@@ -332,7 +332,14 @@ __global__ void trivial_eig_kernel(const double* G, double* lam, double* Vt, int
 // Left-looking: W[k][j] = (G[p][j] - sum_{m<k} Wc[p][m] Wc[j][m]) / sqrt(d_p) with
 // p = argmax of the remaining diagonal d.  W (n x n rows used: k < rank,
 // row-major) and its transpose Wc (n x n, Wc[j][m] = W[m][j]) are both written
-// so every dot product reads contiguous memory.  d[j] < 0 marks pivoted columns.
+// so every dot product reads contiguous memory.  d[j] = -inf marks pivoted
+// columns; a residual that rounds below zero is only never chosen as a pivot
+// (its later entries of W are still formed: treating it as pivoted would drop
+// them, up to sqrt(eps_mach) of the pivots' scale each).
+// The residual diagonal is double-buffered (2 n entries): step k reads
+// d[k & 1] and writes d[(k + 1) & 1], so a CTA that still searches step k's
+// pivot never sees another CTA's step-k updates (with one buffer a slow CTA
+// could pick a different pivot once the fast ones had marked theirs).
 __global__ void __launch_bounds__(JT)
 pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* Wc, double* d,
              int* ctrl, int* status, double floor_rel) {
@@ -359,11 +366,13 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
     if (!grid_barrier(ctrl, status, gridDim.x)) return;
     int k = 0;
     for (; k < n; ++k) {
+        const double* dcur = d + (size_t)(k & 1) * n;
+        double* dnext = d + (size_t)((k + 1) & 1) * n;
         // argmax of the remaining diagonal (identical in every CTA; ties -> lowest index)
         double best = -1.0;
         int bi = n;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double v = __ldcg(d + j);
+            const double v = __ldcg(dcur + j);
             if (v > best) {
                 best = v;
                 bi = j;
@@ -392,9 +401,10 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
         __syncthreads();
         // this CTA's columns j = blockIdx.x + c * gridDim.x, one warp per column
         for (int j = blockIdx.x + warp * gridDim.x; j < n; j += nwarps * gridDim.x) {
-            const double dj = __ldcg(d + j);
+            const double dj = __ldcg(dcur + j);
+            const bool pivoted = dj == -INFINITY;
             double acc = 0.0;
-            if (dj >= 0.0 && j != p)
+            if (!pivoted && j != p)
                 for (int m = lane; m < k; m += 32) acc += colp[m] * __ldcg(Wc + (long)j * n + m);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -402,12 +412,13 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
                 double w;
                 if (j == p) {
                     w = l;
-                    __stcg(d + j, -1.0);
-                } else if (dj < 0.0) {
+                    __stcg(dnext + j, -INFINITY);
+                } else if (pivoted) {
                     w = 0.0;
+                    __stcg(dnext + j, dj);
                 } else {
                     w = (G[(long)p * ldg + j] - acc) / l;
-                    __stcg(d + j, dj - w * w);
+                    __stcg(dnext + j, dj - w * w);
                 }
                 __stcg(W + (long)k * n + j, w);
                 __stcg(Wc + (long)j * n + k, w);

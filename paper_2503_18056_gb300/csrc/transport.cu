@@ -285,6 +285,45 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
     }
 }
 
+// Split layout, one thread per cell: E*_i from the K spatial contractions F
+// (F[i][j] = the field of term j with the angular cores integrated, before
+// the spatial difference of term j is applied), then the same source stage
+// as the grouped kernel (quartic, s, e); e goes to the emission block of the
+// spatial core that holds it, at the cell's coordinates.
+__global__ void __launch_bounds__(256)
+split_source_kernel(Grid g, Fields f, int transport, int K, const double* __restrict__ F,
+                    double* __restrict__ eblk, long st0, long st1, long st2) {
+    double nu[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < g.ndim; ++a) nu[a] = f.c * f.dt / g.dx[a];
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nc;
+         i += (long)gridDim.x * blockDim.x) {
+        double dot = F[i * K];
+        if (transport) {
+            long nb[3][2];
+            cell_neighbours(g, i, nb);
+            for (int a = 0; a < g.ndim; ++a) {
+                const int jp = 1 + 2 * a, jm = 2 + 2 * a;
+                const double fm = nb[a][0] >= 0 ? F[nb[a][0] * K + jp] : 0.0;
+                const double fp = nb[a][1] >= 0 ? F[nb[a][1] * K + jm] : 0.0;
+                dot += -nu[a] * (F[i * K + jp] - fm);
+                dot += -nu[a] * (fp - F[i * K + jm]);
+            }
+        }
+        const double Estar = dot / f.c;
+        const double ka = f.c * f.dt * f.sigma_a[i];
+        const double ks = f.sigma_s ? f.c * f.dt * f.sigma_s[i] : 0.0;
+        const double Td = t_dagger(f.T[i], Estar, ka, f.cv[i], f.a_r);
+        const double Td2 = Td * Td;
+        const double B = f.c * f.a_r * Td2 * Td2 / FOUR_PI;
+        const double Jnew = (f.c * Estar / FOUR_PI + ka * B) / (1.0 + ka);
+        const double sc = 1.0 / (1.0 + ka + ks);
+        f.E_star[i] = Estar;
+        const long c2 = i % g.n[2], q = i / g.n[2];
+        const long c1 = q % g.n[1], c0 = q / g.n[1];
+        eblk[c0 * st0 + c1 * st1 + c2 * st2] = sc * (ks * Jnew + ka * B);
+    }
+}
+
 __global__ void __launch_bounds__(256)
 energy_rows_kernel(long nc, int r, const double* __restrict__ X, long ldx,
                    const double* __restrict__ thbar, double c, double* E_out,
@@ -710,6 +749,13 @@ void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, cons
     note_launch();
     energy_rows_kernel<<<blocks, 256, 0, s>>>(nc, r, X, ldx, thbar, c, E_out, E_star, cv, T,
                                               update_T ? 1 : 0);
+}
+
+void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, bool transport, int K,
+                        const double* F, double* eblk, long st0, long st1, long st2) {
+    note_launch();
+    split_source_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, f, transport ? 1 : 0, K, F, eblk, st0,
+                                                        st1, st2);
 }
 
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X) {

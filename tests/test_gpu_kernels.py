@@ -75,3 +75,30 @@ def test_syev_diagonal_and_degenerate(ttsn):
     G = np.ones((6, 6))
     lam, _, _ = ttsn.syev(G)
     assert np.allclose(lam.cpu().numpy(), [6, 0, 0, 0, 0, 0], atol=1e-14)
+
+
+@pytest.mark.parametrize("n,rank", [(1, 1), (51, 15), (61, 16), (200, 57), (897, 128)])
+@pytest.mark.parametrize("spread", [1e-2, 1e-7])
+def test_pchol_reconstructs_rank_deficient_gram(ttsn, n, rank, spread):
+    """Pivoted Cholesky of G = B^T B with B (rank x n) of singular values from 1
+    down to `spread`: W^T W reproduces G to the eps_mach max(diag G) floor at
+    which the factorisation stops (pivots at the rounding-noise level above
+    that floor may add rows beyond the true rank).  Columns whose
+    residual rounds below zero must keep their later entries; dropping them
+    leaves errors of sqrt(eps_mach) times the pivots' scale."""
+    import torch
+
+    rng = np.random.default_rng(n + rank)
+    U, _ = np.linalg.qr(rng.standard_normal((rank, rank)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, rank)))
+    S = np.geomspace(1.0, spread, rank)
+    B = (U * S) @ V.T
+    G = B.T @ B
+    G = 0.5 * (G + G.T)
+    for _ in range(3):
+        W, k = ttsn.pchol(torch.tensor(G, device="cuda"))
+        W = W.cpu().numpy()
+        assert 1 <= k <= n
+        # Cholesky backward error (k + 1) eps |W^T| |W| plus the neglected
+        # Schur complement, whose entries are below the eps max(diag) floor
+        assert np.abs(W.T @ W - G).max() <= 4 * (rank + 1) * np.finfo(float).eps * np.abs(np.diag(G)).max()
