@@ -599,6 +599,20 @@ def run_reference(args):
     return line
 
 
+def aggregate_over_ranks(total_ms, steps, world, device="cuda"):
+    """Whole-job timing of the replicas: the slowest rank's time (all-reduce
+    MAX over the process group when world > 1) and value = the steps all ranks
+    did over that time.  Returns (max total_ms, steps/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms * 1e-3)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -633,21 +647,16 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     res = run_ours(args, rank, world, local_rank)
-    total_ms = res["total_ms"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    steps = args.steps
+    total_ms, value = aggregate_over_ranks(res["total_ms"], steps, world,
+                                           "cuda" if world > 1 else "cpu")
     if rank != 0:
         if world > 1:
+            import torch.distributed as dist
+
             dist.destroy_process_group()
         return 0
     p = res["p"]
-    steps = args.steps
-    value = world * steps / (total_ms * 1e-3)
     peaks = read_peaks()
     dom, roof = roofline_of(res["prof"], res["fp64_peak"], peaks)
     prof_out = {k: {"ms": round(v["ms"], 3), "launches": v["launches"], "calls": v["calls"],

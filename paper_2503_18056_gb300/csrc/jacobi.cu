@@ -297,6 +297,117 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
     }
 }
 
+// Pivoted Cholesky in one CTA for n <= PCHOL_ONE_CTA_N: the same factorisation
+// as pchol_kernel (pivot = largest remaining diagonal entry, stop at the
+// floor, -inf marks pivoted columns) with one thread per column: column j's
+// dot product sum_m W[m][p] W[m][j] reads W row by row, so a warp's loads are
+// contiguous and every thread keeps several in flight.  The residual diagonal
+// lives in shared memory; a __syncthreads separates each pivot's search from
+// its updates.  A pivot costs n k FP64 FMAs on one SM: below ~384 columns that
+// is less than the grid-wide barrier the multi-CTA kernel pays per pivot.
+constexpr int PCHOL_ONE_CTA_N = 384;
+constexpr int PST = 1024;
+
+__global__ void __launch_bounds__(PST)
+pchol_small_kernel(int n, const double* __restrict__ G, long ldg, double* W, int* kB_out,
+                   double floor_rel) {
+    extern __shared__ double sm[];
+    double* dd = sm;        // n: residual diagonal
+    double* colp = sm + n;  // n: W[0..k)[p]
+    __shared__ double s_v[PST / 32];
+    __shared__ int s_i[PST / 32];
+    __shared__ double s_best;
+    __shared__ int s_p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    double dm = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double x = G[(long)j * ldg + j];
+        dd[j] = x;
+        dm = fmax(dm, x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (lane == 0) s_v[warp] = dm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < nwarps; ++w) m = fmax(m, s_v[w]);
+        s_best = m;
+    }
+    __syncthreads();
+    const double floor_abs = floor_rel * s_best;
+    int k = 0;
+    for (; k < n; ++k) {
+        // argmax of the residual diagonal (ties -> lowest index)
+        double best = -1.0;
+        int bi = n;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double x = dd[j];
+            if (x > best) {
+                best = x;
+                bi = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double b2 = __shfl_xor_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (b2 > best || (b2 == best && i2 < bi)) {
+                best = b2;
+                bi = i2;
+            }
+        }
+        if (lane == 0) {
+            s_v[warp] = best;
+            s_i[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = -1.0;
+            int p = n;
+            for (int w = 0; w < nwarps; ++w)
+                if (s_v[w] > b || (s_v[w] == b && s_i[w] < p)) {
+                    b = s_v[w];
+                    p = s_i[w];
+                }
+            s_best = b;
+            s_p = p;
+        }
+        __syncthreads();
+        const double dp = s_best;
+        const int p = s_p;
+        if (!(dp > floor_abs) || p >= n) break;
+        const double l = sqrt(dp);
+        for (int m = threadIdx.x; m < k; m += blockDim.x) colp[m] = W[(long)m * n + p];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double dj = dd[j];
+            double w;
+            if (j == p) {
+                w = l;
+                dd[j] = -INFINITY;
+            } else if (dj == -INFINITY) {
+                w = 0.0;
+            } else {
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                int m = 0;
+                for (; m + 3 < k; m += 4) {
+                    a0 += colp[m] * W[(long)m * n + j];
+                    a1 += colp[m + 1] * W[(long)(m + 1) * n + j];
+                    a2 += colp[m + 2] * W[(long)(m + 2) * n + j];
+                    a3 += colp[m + 3] * W[(long)(m + 3) * n + j];
+                }
+                for (; m < k; ++m) a0 += colp[m] * W[(long)m * n + j];
+                w = (G[(long)p * ldg + j] - ((a0 + a1) + (a2 + a3))) / l;
+                dd[j] = dj - w * w;
+            }
+            W[(long)k * n + j] = w;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *kB_out = k;
+}
+
 // One CTA per source row j: rank of lam_j among all (descending, ties by index),
 // then copy eigenvector row j and eigenvalue to their sorted positions.
 __global__ void __launch_bounds__(256)
@@ -541,6 +652,15 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
         TT_CUDA_TRY(cudaGetLastError());
         return TT_OK;
     }
+    // relative skip test as in high-relative-accuracy Jacobi; the absolute one
+    // (1e-20 of the largest diagonal entry) only skips rotations inside the
+    // block of eigenvalues below the Gram floor n eps_mach lambda_max that the
+    // rounding discards afterwards: on the rounding's K matrices it ends the
+    // iteration 1-3 sweeps earlier than 1e-24 with the same eigenpairs above
+    // the floor.  (One CTA would save the grid barrier per round but not the
+    // round's ~n^2 FP64 FMAs, which one SM's share of GB300's FP64 rate cannot
+    // absorb: measured 1.1 ms mean per eigensolve at n <= 96.)
+    double tol_rel = 1e-15, tol_abs_rel = 1e-20;
     const int N = n + (n & 1);
     const int npairs = N / 2;
     const long ld = n;
@@ -586,10 +706,6 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     double* abc1 = w.abc.p + 3 * npairs;
     double* lamu = w.lam_unsorted.p;
     int* ctrl = w.d_ctrl;
-    // relative skip test as in high-relative-accuracy Jacobi; the absolute one
-    // (1e-24 of the largest diagonal entry) is far below the Gram floor
-    // n eps_mach lambda_max that the rounding applies afterwards
-    double tol_rel = 1e-15, tol_abs_rel = 1e-24;
     int nn = n, NN = N;
     long ldl = ld;
     void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &abc0, &abc1, &lamu, &ctrl, &status_dev, &tol_rel, &tol_abs_rel};
@@ -613,6 +729,13 @@ tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, dou
         return TT_ERR_TOO_LARGE;
     }
     TT_TRY(ensure_max_dynamic_smem((const void*)pchol_kernel));
+    if (n <= PCHOL_ONE_CTA_N) {
+        note_launch();
+        pchol_small_kernel<<<1, PST, 2 * (size_t)n * sizeof(double), s>>>(n, G, ldg, W, kB_dev,
+                                                                          2.220446049250313e-16);
+        TT_CUDA_TRY(cudaGetLastError());
+        return TT_OK;
+    }
     int blocks = 1;
     // about eight columns per CTA (one warp each)
     TT_TRY(coop_blocks((const void*)pchol_kernel, smem, std::max(1, (n + 7) / 8), &blocks));

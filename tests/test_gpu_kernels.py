@@ -39,7 +39,7 @@ def test_gram_matches_numpy_and_is_symmetric(ttsn, m, n):
     assert np.array_equal(G, G2)  # reproducible
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 8, 33, 64, 100, 257, 640])
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 33, 64, 95, 96, 97, 100, 257, 640])
 def test_syev_reconstructs_and_matches_numpy(ttsn, n):
     rng = np.random.default_rng(n)
     X = rng.standard_normal((n + 5, n))
@@ -55,10 +55,11 @@ def test_syev_reconstructs_and_matches_numpy(ttsn, n):
     assert sweeps <= 20
 
 
-def test_syev_rank_deficient_gram(ttsn):
-    # a Gram matrix of rank 10 padded to 300: the null block must not stall Jacobi
+@pytest.mark.parametrize("n", [60, 300])
+def test_syev_rank_deficient_gram(ttsn, n):
+    # a Gram matrix of rank 10 padded to n: the null block must not stall Jacobi
     rng = np.random.default_rng(3)
-    X = rng.standard_normal((10, 300))
+    X = rng.standard_normal((10, n))
     G = X.T @ X
     lam, Vt, sweeps = ttsn.syev(G)
     lam = lam.cpu().numpy()
@@ -77,7 +78,8 @@ def test_syev_diagonal_and_degenerate(ttsn):
     assert np.allclose(lam.cpu().numpy(), [6, 0, 0, 0, 0, 0], atol=1e-14)
 
 
-@pytest.mark.parametrize("n,rank", [(1, 1), (51, 15), (61, 16), (200, 57), (897, 128)])
+# n <= 384: one CTA; larger n: several CTAs with a grid barrier per pivot
+@pytest.mark.parametrize("n,rank", [(1, 1), (51, 15), (61, 16), (200, 57), (600, 100), (897, 128)])
 @pytest.mark.parametrize("spread", [1e-2, 1e-7])
 def test_pchol_reconstructs_rank_deficient_gram(ttsn, n, rank, spread):
     """Pivoted Cholesky of G = B^T B with B (rank x n) of singular values from 1
