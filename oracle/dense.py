@@ -15,7 +15,13 @@ written directly from its definitions with no tensor train involved:
   (the post-transport moment) and E^{m+1} the energy after it;
 * fixed external sources (optional): S = sum_k x_k(cell) theta_k(l) phi_k(p),
   an inhomogeneous term of the transport equation taken explicitly with the
-  streaming, so the transport stage gives I* = L I + c dt S.
+  streaming, so the transport stage gives I* = L I + c dt S;
+* interface fluxes (Sec. 3.1): ``upwind`` (Eq. upwind), ``rusanov`` (Eq.
+  rusanov_flux_toro with S+ = rusanov_s c) or ``hll`` (Eq. hll with the wave
+  speeds S_L, S_R of Sec. 3.1's piecewise definitions and the harmonic-mean
+  optical depth of Eq. tauc, constants beta and tau_threshold).  The ghost
+  cell of a vacuum face takes the boundary cell's own opacity for Eq. tauc;
+  a face with S_R = S_L (n_a = 0) carries no flux.
 
 The intensity array has shape (N_x[, N_y[, N_z]], N_theta, N_phi); spatial
 fields have shape (N_x[, N_y[, N_z]]).
@@ -31,7 +37,11 @@ VACUUM = 1
 
 class DenseSN:
     def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
-                 I0, sigma_s=None, sources=None):
+                 I0, sigma_s=None, sources=None, flux="upwind", rusanov_s=1.0, hll_beta=1.0,
+                 hll_tau_threshold=1.0):
+        self.flux = flux
+        self.rusanov_s = float(rusanov_s)
+        self.hll_beta, self.hll_tau_threshold = float(hll_beta), float(hll_tau_threshold)
         self.ndim = len(n)
         self.n = tuple(n)
         self.dx = [L[a] / n[a] for a in range(self.ndim)]
@@ -75,8 +85,46 @@ class DenseSN:
             P[tuple(hi)] = I[tuple(src_first)]
         return P
 
+    def _face_tau(self, a):
+        """Eq. tauc at the N+1 faces of axis a: 2 beta dx / (1/sigma_L + 1/sigma_R),
+        sigma = sigma_a + sigma_s, with the ghost cells' opacity (periodic: the
+        wrapped cell, vacuum: the boundary cell itself); 0 if either is 0."""
+        sig = self.sigma_a + self.sigma_s
+        pad = [(0, 0)] * sig.ndim
+        pad[a] = (1, 1)
+        P = np.pad(sig, pad, mode="wrap" if self.bc[a] == PERIODIC else "edge")
+        N = self.n[a]
+        sl_L = [slice(None)] * sig.ndim
+        sl_R = [slice(None)] * sig.ndim
+        sl_L[a] = slice(0, N + 1)
+        sl_R[a] = slice(1, N + 2)
+        sL, sR = P[tuple(sl_L)], P[tuple(sl_R)]
+        tau = np.zeros_like(sL)
+        ok = (sL > 0.0) & (sR > 0.0)
+        tau[ok] = 2.0 * self.hll_beta * self.dx[a] / (1.0 / sL[ok] + 1.0 / sR[ok])
+        return tau
+
+    def _hll_speeds(self, na, tau):
+        """S_R, S_L of Sec. 3.1 (after Eq. hll) for normal component na (angles)
+        and face optical depth tau (cells), broadcast to cells x angles."""
+        c, thr = self.c, self.hll_tau_threshold
+        t = tau[..., None, None]
+        n = np.broadcast_to(na, t.shape[:-2] + na.shape)
+        big = t >= thr
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g2 = np.where(big, np.sqrt((1.0 - np.exp(-t ** 2)) / np.where(t > 0, t ** 2, 1.0)), 0.0)
+            g4 = np.where(big, np.sqrt((1.0 - np.exp(-t ** 4)) / np.where(t > 0, t ** 2, 1.0)), 0.0)
+        small_R = np.sqrt(np.maximum(1.0 - t ** 2 / 2.0, 0.0))
+        pos = n >= 0.0
+        S_R = np.where(pos, np.where(big, c * n * g2, c * n * small_R),
+                       np.where(big, -c * n * g4, -c * n * t))
+        S_L = np.where(pos, np.where(big, -c * n * g4, -c * n * t),
+                       np.where(big, c * n * g2, c * n * small_R))
+        return S_R, S_L
+
     def transport(self, I):
-        """One explicit upwind step of Eq. lhs summed over the spatial axes."""
+        """One explicit step of Eq. lhs with the chosen interface flux, summed
+        over the spatial axes."""
         out = I.copy()
         for a in range(self.ndim):
             na = self.nvec[a]  # (N_theta, N_phi)
@@ -90,7 +138,20 @@ class DenseSN:
             sl_R[a] = slice(1, N + 2)
             UL = P[tuple(sl_L)]
             UR = P[tuple(sl_R)]
-            F = np.where(na >= 0.0, self.c * na * UL, self.c * na * UR)
+            FL, FR = self.c * na * UL, self.c * na * UR
+            if self.flux == "upwind":
+                F = np.where(na >= 0.0, FL, FR)
+            elif self.flux == "rusanov":
+                F = 0.5 * (FL + FR) - 0.5 * self.rusanov_s * self.c * (UR - UL)
+            elif self.flux == "hll":
+                S_R, S_L = self._hll_speeds(na, self._face_tau(a))
+                den = S_R - S_L
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    F = np.where(den != 0.0,
+                                 (S_R * FL - S_L * FR + S_L * S_R * (UR - UL)) / np.where(den != 0.0, den, 1.0),
+                                 0.0)
+            else:
+                raise ValueError(self.flux)
             hi = [slice(None)] * I.ndim
             lo = [slice(None)] * I.ndim
             hi[a] = slice(1, N + 1)   # F_{i+1/2}

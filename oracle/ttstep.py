@@ -26,6 +26,24 @@ the (N_x[, N_y[, N_z]]) grid, x slowest).  One time step:
 Fixed external sources S = sum_k x_k (x) theta_k (x) phi_k (optional) enter
 the transport stage explicitly, I* = L I + c dt S: each is one more rank-one
 term of the TT sum, after the streaming terms.
+
+Interface fluxes (Sec. 3.1, Sec. 4.3): with piecewise-constant states every
+flux of the paper is, per axis a and face, c times a sum of two rank-one
+angular factors each multiplying a two-point combination w_L U_L + w_R U_R of
+the face's states, so the transport stage stays a TT sum of 1 + 2 ndim terms:
+term (a, 1) has angular factor g1 and face weights (w_L1, w_R1), term (a, 2)
+g2 and (w_L2, w_R2), and its spatial core is
+-nu_a [w_L(i+1/2) X_i + w_R(i+1/2) X_{i+1} - w_L(i-1/2) X_{i-1} - w_R(i-1/2) X_i]:
+* upwind (Eq. upwind): g = (n_a^+, n_a^-), w = (1, 0) and (0, 1);
+* Rusanov (Eq. rusanov_flux_toro, S+ = s c): g = (n_a, 1), w = (1/2, 1/2) and
+  (s/2, -s/2);
+* HLL (Eq. hll with Sec. 3.1's wave speeds): for n_a >= 0, S_R = c n_a A(tau),
+  S_L = -c n_a B(tau), and mirrored for n_a < 0, so g = (n_a^+, n_a^-) and
+  w = (A (1 + B), B (1 - A)) / (A + B) and (B (1 - A), A (1 + B)) / (A + B),
+  with A = sqrt((1 - exp(-tau^2)) / tau^2) or sqrt(1 - tau^2 / 2) and
+  B = sqrt((1 - exp(-tau^4)) / tau^2) or tau (tau >= or < tau_threshold),
+  tau the face optical depth of Eq. tauc (ghost opacity: wrapped cell for
+  periodic axes, the boundary cell for vacuum).
 """
 import numpy as np
 
@@ -40,7 +58,11 @@ VACUUM = 1
 class TTSN:
     def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
                  cores, sigma_s=None, eps=0.0, max_rank=None,
-                 rounds_per_step=1, rounding="gram", sources=None):
+                 rounds_per_step=1, rounding="gram", sources=None, flux="upwind",
+                 rusanov_s=1.0, hll_beta=1.0, hll_tau_threshold=1.0):
+        self.flux = flux
+        self.rusanov_s = float(rusanov_s)
+        self.hll_beta, self.hll_tau_threshold = float(hll_beta), float(hll_tau_threshold)
         self.ndim = len(n)
         self.n = tuple(n)
         self.nc = int(np.prod(n))
@@ -101,17 +123,81 @@ class TTSN:
         one = np.ones_like(g["phi"])
         return (np.maximum(g["mu"], 0.0), one), (np.minimum(g["mu"], 0.0), one)
 
+    def _face_weights(self, a):
+        """(w_L1, w_R1, w_L2, w_R2) at the faces below (lo) and above (hi) every
+        cell along axis a, each an (N_c,) array: returns ((lo1, hi1), (lo2, hi2))
+        with lo/hi = (w_L, w_R)."""
+        nc = int(np.prod(self.n))
+        if self.flux == "upwind":
+            w1, w2 = (1.0, 0.0), (0.0, 1.0)
+            const = True
+        elif self.flux == "rusanov":
+            s = self.rusanov_s
+            w1, w2 = (0.5, 0.5), (0.5 * s, -0.5 * s)
+            const = True
+        else:
+            const = False
+        if const:
+            f = lambda v: np.full(nc, v)
+            pair = lambda w: ((f(w[0]), f(w[1])), (f(w[0]), f(w[1])))
+            return pair(w1), pair(w2)
+        sig = (self.sigma_a + self.sigma_s).reshape(self.n)
+        N = self.n[a]
+
+        def shifted(off):
+            if self.bc[a] == PERIODIC:
+                return np.roll(sig, -off, axis=a)
+            idx = np.clip(np.arange(N) + off, 0, N - 1)
+            return np.take(sig, idx, axis=a)
+
+        def tau_with(other):
+            t = np.zeros_like(sig)
+            ok = (sig > 0.0) & (other > 0.0)
+            t[ok] = 2.0 * self.hll_beta * self.dx[a] / (1.0 / sig[ok] + 1.0 / other[ok])
+            return t
+
+        def AB(t):
+            thr = self.hll_tau_threshold
+            big = t >= thr
+            tt = np.where(t > 0.0, t, 1.0)
+            A = np.where(big, np.sqrt((1.0 - np.exp(-t ** 2)) / tt ** 2), np.sqrt(np.maximum(1.0 - t ** 2 / 2.0, 0.0)))
+            B = np.where(big, np.sqrt((1.0 - np.exp(-t ** 4)) / tt ** 2), t)
+            return A, B
+
+        out = []
+        for t in (tau_with(shifted(-1)), tau_with(shifted(+1))):  # lo face, hi face
+            A, B = AB(t.reshape(-1))
+            out.append(((A * (1.0 + B) / (A + B), B * (1.0 - A) / (A + B)),
+                        (B * (1.0 - A) / (A + B), A * (1.0 + B) / (A + B))))
+        (lo1, lo2), (hi1, hi2) = out
+        return (lo1, hi1), (lo2, hi2)
+
+    def _angular(self, a):
+        """Angular factors (theta, phi) of the two terms of axis a."""
+        if self.flux != "rusanov":
+            return self._masks(a)
+        g = self.g
+        one_t, one_p = np.ones_like(g["mu"]), np.ones_like(g["phi"])
+        if a == 0:
+            n1 = (g["sin_theta"], np.cos(g["phi"]))
+        elif a == 1:
+            n1 = (g["sin_theta"], np.sin(g["phi"]))
+        else:
+            n1 = (g["mu"], one_p)
+        return n1, (one_t, one_p)
+
     def transport(self, cores):
         X, Th, Ph = cores
         Xm = X[0]
         terms = [cores]
         for a in range(self.ndim):
             nu = self.c * self.dt / self.dx[a]
-            Dm = Xm - self._neighbour(Xm, a, -1)
-            Dp = self._neighbour(Xm, a, +1) - Xm
-            (tp, pp), (tm, pm) = self._masks(a)
-            terms.append([(-nu * Dm)[None], Th * tp[None, :, None], Ph * pp[None, :, None]])
-            terms.append([(-nu * Dp)[None], Th * tm[None, :, None], Ph * pm[None, :, None]])
+            Xlo = self._neighbour(Xm, a, -1)
+            Xhi = self._neighbour(Xm, a, +1)
+            for (lo, hi), (tf, pf) in zip(self._face_weights(a), self._angular(a)):
+                (wLlo, wRlo), (wLhi, wRhi) = lo, hi
+                D = ((wLhi - wRlo)[:, None] * Xm + wRhi[:, None] * Xhi - wLlo[:, None] * Xlo)
+                terms.append([(-nu * D)[None], Th * tf[None, :, None], Ph * pf[None, :, None]])
         for x, th, ph in self.sources:
             terms.append(tt.rank_one([self.c * self.dt * x, th, ph]))
         return tt.add_many(terms)

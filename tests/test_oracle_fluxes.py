@@ -1,0 +1,131 @@
+"""Pins for the Rusanov and HLL interface fluxes (Sec. 3.1, Sec. 4.3) in the
+oracle: the dense definitions against their limits and invariants, and the
+grouped TT stepper (every flux as 1 + 2 ndim rank-one-angular terms with
+face-weighted stencils) against the dense stepper."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import tt
+from oracle.dense import DenseSN
+from oracle.ttstep import PERIODIC, VACUUM, TTSN
+
+
+def _fields(n, seed, thick=False):
+    f = workloads.random_fields(n, seed)
+    if thick:
+        # opacities spanning thin and thick cells so that both branches of the
+        # HLL wave speeds (tau below and above the threshold) occur
+        rng = np.random.default_rng(seed + 7)
+        f["sigma_a"] = 10.0 ** rng.uniform(-2, 3, n)
+    return f
+
+
+def _pair(n, nt, npf, bc, seed, flux, **fk):
+    nc = int(np.prod(n))
+    cores = workloads.random_positive_tt([nc, nt, npf], [3, 2], seed)
+    f = _fields(n, seed + 100, thick=(flux == "hll"))
+    sigma_s = 0.5 * f["sigma_a"]
+    dt = 0.3 * min(1.0 / m for m in n)
+    args = dict(n=n, L=[1.0] * len(n), n_theta=nt, n_phi=npf, c=1.0, a_r=1.0, dt=dt,
+                bc=[bc] * len(n), sigma_a=f["sigma_a"], cv=f["cv"], T0=f["T0"], sigma_s=sigma_s,
+                flux=flux, **fk)
+    ttsn = TTSN(cores=cores, rounding=None, **args)
+    d = DenseSN(I0=tt.full(cores).reshape(tuple(n) + (nt, npf)), **args)
+    return ttsn, d
+
+
+FLUXES = [("rusanov", dict(rusanov_s=1.0)), ("rusanov", dict(rusanov_s=0.3)), ("rusanov", dict(rusanov_s=0.0)),
+          ("hll", dict(hll_beta=1.0, hll_tau_threshold=1.0)), ("hll", dict(hll_beta=5.0, hll_tau_threshold=0.5))]
+
+
+@pytest.mark.parametrize("n,bc", [((12,), VACUUM), ((8, 6), PERIODIC), ((8, 6), VACUUM),
+                                  ((5, 4, 3), VACUUM)])
+@pytest.mark.parametrize("flux,fk", FLUXES)
+def test_untruncated_tt_step_equals_dense_step_all_fluxes(n, bc, flux, fk):
+    ttsn, d = _pair(n, 4, 6, bc, seed=17, flux=flux, **fk)
+    for _ in range(2):
+        ttsn.step()
+        d.step()
+    F = ttsn.full()
+    assert np.abs(F - d.I).max() <= 1e-12 * np.abs(d.I).max()
+    assert np.abs(ttsn.T - d.T.reshape(-1)).max() <= 1e-12 * np.abs(d.T).max()
+    k = 1 + 2 * len(n)
+    assert tt.ranks(ttsn.cores)[0] == k * (k * 3 + 1) + 1
+
+
+def _dense(n, flux, bc=VACUUM, sigma=1.0, **fk):
+    nc = int(np.prod(n))
+    I0 = workloads.random_positive_tt([nc, 4, 8], [2, 2], 3)
+    return DenseSN(n, [1.0] * len(n), 4, 8, 1.0, 1.0, 0.2 / max(n), [bc] * len(n),
+                   np.full(n, sigma), np.ones(n), np.ones(n), tt.full(I0).reshape(tuple(n) + (4, 8)),
+                   flux=flux, **fk)
+
+
+def test_hll_without_opacity_is_upwind():
+    """tau -> 0 (no opacity): the HLL flux reduces to upwinding (Sec. 3.1)."""
+    for bc in (VACUUM, PERIODIC):
+        up = _dense((9, 7), "upwind", bc, sigma=0.0)
+        hl = _dense((9, 7), "hll", bc, sigma=0.0)
+        a, b = up.transport(up.I), hl.transport(hl.I)
+        assert np.abs(a - b).max() <= 1e-15 * np.abs(a).max()
+
+
+def test_hll_thick_limit_is_rusanov_with_speed_c_n_over_tau():
+    """tau -> infinity: HLL equals the Rusanov flux with S+ = c |n_x| / tau_c
+    (the series expansion stated after Eq. hll); exact once exp(-tau^2)
+    underflows."""
+    d = _dense((10,), "hll", VACUUM, sigma=1.0)
+    tau = np.array([40.0, 55.0, 1e3])
+    n = np.array([[0.3, -0.7, 0.9, -0.05]])
+    S_R, S_L = d._hll_speeds(n, tau)
+    UL, UR = 1.3, 0.4
+    FL, FR = d.c * n * UL, d.c * n * UR
+    F = (S_R * FL - S_L * FR + S_L * S_R * (UR - UL)) / (S_R - S_L)
+    Splus = d.c * np.abs(n) / tau[:, None, None]
+    rus = 0.5 * (FL + FR) - 0.5 * Splus * (UR - UL)
+    assert np.abs(F - rus).max() <= 1e-15
+
+
+def test_rusanov_with_unit_speed_is_upwind_for_unit_normals():
+    """S+ = c and |n_x| = 1: Eq. rusanov_flux_toro gives F_L for n = 1 and F_R
+    for n = -1, i.e. upwinding."""
+    up = _dense((11,), "upwind", VACUUM)
+    ru = _dense((11,), "rusanov", VACUUM, rusanov_s=1.0)
+    sign = np.where(np.arange(8) < 4, 1.0, -1.0)
+    for d in (up, ru):
+        d.nvec = [np.broadcast_to(sign, (4, 8)).copy()]
+    a, b = up.transport(up.I), ru.transport(ru.I)
+    assert np.abs(a - b).max() <= 1e-15 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("flux,fk", FLUXES)
+def test_periodic_transport_conserves_each_ordinate(flux, fk):
+    """Fluxes telescope on a periodic grid: sum_i I_ilp is unchanged."""
+    d = _dense((7, 6), flux, PERIODIC, sigma=2.0, **fk)
+    d.sigma_a = 10.0 ** np.random.default_rng(2).uniform(-2, 2, (7, 6))
+    out = d.transport(d.I)
+    assert np.abs(out.sum(axis=(0, 1)) - d.I.sum(axis=(0, 1))).max() <= 1e-13 * np.abs(d.I).sum()
+
+
+def test_rusanov_zero_speed_is_the_central_difference():
+    """S+ = 0: the flux is the average of F_L and F_R, a central difference."""
+    d = _dense((9,), "rusanov", PERIODIC, rusanov_s=0.0)
+    out = d.transport(d.I)
+    nu = d.c * d.dt / d.dx[0]
+    ref = d.I - 0.5 * nu * d.nvec[0] * (np.roll(d.I, -1, axis=0) - np.roll(d.I, 1, axis=0))
+    assert np.abs(out - ref).max() <= 1e-14 * np.abs(d.I).max()
+
+
+@pytest.mark.parametrize("flux,fk", FLUXES[::2])
+def test_energy_conserved_with_truncation_all_fluxes(flux, fk):
+    n, nt, npf = (8, 7), 4, 8
+    f = _fields(n, 33, thick=True)
+    I0 = f["T0"] ** 4 / (4 * np.pi)
+    t = TTSN(n, [1.0, 1.0], nt, npf, 1.0, 1.0, 0.04, [PERIODIC] * 2, f["sigma_a"].reshape(-1),
+             f["cv"].reshape(-1), f["T0"].reshape(-1), TTSN.isotropic_cores(I0.reshape(-1), nt, npf),
+             eps=1e-4, flux=flux, **fk)
+    e0 = t.total_energy()
+    for _ in range(4):
+        t.step()
+        assert abs(t.total_energy() - e0) <= 1e-13 * e0
