@@ -50,6 +50,7 @@ typedef enum {
 enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1 };
 enum { TT_FP64 = 0, TT_MIXED = 1 };
 enum { TT_LAYOUT_GROUPED = 0, TT_LAYOUT_SPLIT = 1 };
+enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_HLL = 2 };
 
 /* step flags for tt_sn_step_ex */
 enum {
@@ -96,6 +97,15 @@ enum {
  * (TT_ERR_ARG otherwise: a varying absorption factor would multiply every
  * spatial rank) and takes neither fixed sources nor the adjoint tape
  * (TT_ERR_STATE).
+ * flux: the interface flux of Sec. 3.1 with piecewise-constant states.
+ * TT_FLUX_UPWIND (Eq. upwind; flux_param unused); TT_FLUX_RUSANOV (Eq.
+ * rusanov_flux_toro with S+ = flux_param[0] * c, 0 <= flux_param[0]: 1 is
+ * the paper's optically thin choice, 0 the central difference);
+ * TT_FLUX_HLL (Eq. hll with the wave speeds that follow it and the optical
+ * depth of Eq. tauc: flux_param[0] = beta > 0, flux_param[1] =
+ * tau_threshold in (0, sqrt 2]; a vacuum face takes the boundary cell's own
+ * opacity for Eq. tauc).  Every flux adds 1 + 2 ndim terms to the TT sum,
+ * so the ranks grow as with upwinding.  The adjoint tape takes upwinding only.
  */
 typedef struct {
     int ndim;
@@ -114,6 +124,8 @@ typedef struct {
     int rounds_per_step;
     int precision;
     int layout;
+    int flux;
+    double flux_param[2];
 } tt_problem_desc;
 
 /* Diagnostics of the last rounding performed by a call (host struct). */

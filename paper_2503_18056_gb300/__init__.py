@@ -161,7 +161,8 @@ def _torch_allocator():
 class TTSN(_Handle):
     """A TT-S_N problem on the current CUDA stream, in the paper's three-core
     layout (``layout=TT_LAYOUT_GROUPED``) or with one core per spatial axis
-    (``TT_LAYOUT_SPLIT``; uniform sigma_a and sigma_s).
+    (``TT_LAYOUT_SPLIT``; uniform sigma_a and sigma_s), with the upwind,
+    Rusanov (S+ = rusanov_s c) or HLL (hll_beta, hll_tau_threshold) flux.
 
     Fields are array-likes of N_c values in C order of the grid (axis 0
     slowest); they are copied to the device and then into the library.
@@ -170,7 +171,8 @@ class TTSN(_Handle):
     def __init__(self, n, L, n_theta, n_phi, sigma_a, cv, T0, Tr0=None, sigma_s=None, c=1.0,
                  a_r=1.0, dt=0.0, cfl=0.5, bc=TT_BC_PERIODIC, eps=1e-6, max_rank=0,
                  rounds_per_step=1, precision=TT_FP64, stream=None, allocator=None,
-                 layout=TT_LAYOUT_GROUPED):
+                 layout=TT_LAYOUT_GROUPED, flux="upwind", rusanov_s=1.0, hll_beta=1.0,
+                 hll_tau_threshold=1.0):
         super().__init__()
         ndim = len(n)
         nc = 1
@@ -199,6 +201,13 @@ class TTSN(_Handle):
         desc.rounds_per_step, desc.precision = int(rounds_per_step), int(precision)
         desc.layout = int(layout)
         self.layout = int(layout)
+        kinds = {"upwind": _native.TT_FLUX_UPWIND, "rusanov": _native.TT_FLUX_RUSANOV,
+                 "hll": _native.TT_FLUX_HLL}
+        desc.flux = kinds[flux] if isinstance(flux, str) else int(flux)
+        if desc.flux == _native.TT_FLUX_RUSANOV:
+            desc.flux_param[0] = float(rusanov_s)
+        elif desc.flux == _native.TT_FLUX_HLL:
+            desc.flux_param[0], desc.flux_param[1] = float(hll_beta), float(hll_tau_threshold)
         self._alloc = None
         if allocator == "torch":
             self._alloc = _torch_allocator()

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "TT_OK", 1: "TT_WARN_RANK_CAPPED", -1: "TT_ERR_ARG", -2: "TT_
 TT_BC_PERIODIC, TT_BC_VACUUM = 0, 1
 TT_FP64, TT_MIXED = 0, 1
 TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT = 0, 1
+TT_FLUX_UPWIND, TT_FLUX_RUSANOV, TT_FLUX_HLL = 0, 1, 2
 TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
 
 
@@ -39,7 +40,7 @@ class ProblemDesc(ctypes.Structure):
         ("T0", ctypes.c_void_p), ("Tr0", ctypes.c_void_p),
         ("eps", ctypes.c_double), ("max_rank", ctypes.c_int),
         ("rounds_per_step", ctypes.c_int), ("precision", ctypes.c_int),
-        ("layout", ctypes.c_int),
+        ("layout", ctypes.c_int), ("flux", ctypes.c_int), ("flux_param", ctypes.c_double * 2),
     ]
 
 

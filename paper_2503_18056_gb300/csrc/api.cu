@@ -213,6 +213,8 @@ struct tt_ctx {
     // contraction chain's intermediates
     int layout = TT_LAYOUT_GROUPED;
     DevBuf split_fac, sp_F, sp_tmp[2];
+    StencilCo split_co{};  // the flux's stencil per axis (uniform opacities)
+    DevBuf f_fw;           // HLL face weights (grouped layout)
     double split_s = 1.0;
     bool split() const { return layout == TT_LAYOUT_SPLIT; }
     bool has_sigma_s = false;
@@ -258,7 +260,7 @@ struct tt_ctx {
         DevBuf* bufs[] = {&slscratch, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
-                          &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1]};
+                          &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw};
         for (DevBuf* b : bufs) b->release();
         eig.release();
         for (StepRec* r : tape) {
@@ -592,6 +594,9 @@ SplitCoreSpec split_spec(const tt_ctx* h, int k, int K, bool emission, const int
     c.Ra = R[k];
     c.Rb = R[k + 1];
     c.tscale = c.kind == SPLIT_PHI ? tscale : 1.0;
+    if (k < nd)
+        for (int t = 0; t < 2; ++t)
+            for (int q = 0; q < 3; ++q) c.co[t][q] = h->split_co.c[k][t][q];
     c.ekind = SPLIT_E_NONE;
     if (emission) {
         if (k >= nd)
@@ -695,7 +700,8 @@ tt_status split_apply_terms(tt_ctx* h, bool transport, bool source) {
         double* eb = split_eblock(h, K, h->r, R, st);
         h->fields.T = h->f_T.p;
         h->fields.E_star = h->f_Estar.p;
-        split_source_cells(s, h->grid, h->fields, transport, K, h->sp_F.p, eb, st[0], st[1], st[2]);
+        split_source_cells(s, h->grid, h->fields, h->split_co, transport, K, h->sp_F.p, eb, st[0], st[1],
+                           st[2]);
     }
     TT_CUDA_TRY(cudaGetLastError());
     for (int k = 0; k <= d; ++k) h->gr[k] = R[k];
@@ -1109,6 +1115,13 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         return fail(TT_ERR_ARG, "tt_create: precision must be TT_FP64 or TT_MIXED");
     if (D.layout != TT_LAYOUT_GROUPED && D.layout != TT_LAYOUT_SPLIT)
         return fail(TT_ERR_ARG, "tt_create: layout must be TT_LAYOUT_GROUPED or TT_LAYOUT_SPLIT");
+    if (D.flux != TT_FLUX_UPWIND && D.flux != TT_FLUX_RUSANOV && D.flux != TT_FLUX_HLL)
+        return fail(TT_ERR_ARG, "tt_create: flux must be TT_FLUX_UPWIND, TT_FLUX_RUSANOV or TT_FLUX_HLL");
+    if (D.flux == TT_FLUX_RUSANOV && !(D.flux_param[0] >= 0.0 && D.flux_param[0] < 1e300))
+        return fail(TT_ERR_ARG, "tt_create: Rusanov needs flux_param[0] = S+/c >= 0");
+    if (D.flux == TT_FLUX_HLL && !(D.flux_param[0] > 0.0 && D.flux_param[0] < 1e300 &&
+                                   D.flux_param[1] > 0.0 && D.flux_param[1] <= sqrt(2.0)))
+        return fail(TT_ERR_ARG, "tt_create: HLL needs flux_param = (beta > 0, 0 < tau_threshold <= sqrt 2)");
     double sig_a_uniform = 0.0, sig_s_uniform = 0.0;
     if (D.layout == TT_LAYOUT_SPLIT) {
         // the absorption factor s multiplies every spatial rank unless it is
@@ -1198,6 +1211,40 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
     f.cv = h->f_cv.p;
     f.T = h->f_T.p;
     f.E_star = h->f_Estar.p;
+    // interface flux: face weights (w_L1, w_R1, w_L2, w_R2) of Eq. upwind /
+    // Eq. rusanov_flux_toro, or per cell from Eq. hll (grouped layout)
+    f.flux = D.flux;
+    if (D.flux == TT_FLUX_RUSANOV) {
+        const double sp = D.flux_param[0];
+        f.wc[0] = 0.5;
+        f.wc[1] = 0.5;
+        f.wc[2] = 0.5 * sp;
+        f.wc[3] = -0.5 * sp;
+    }
+    if (D.flux == TT_FLUX_HLL && D.layout == TT_LAYOUT_GROUPED) {
+        TT_CREATE_TRY(h->f_fw.ensure((size_t)nc * D.ndim * 8, s));
+        hll_face_weights(s, g, h->f_sigma_a.p, h->has_sigma_s ? h->f_sigma_s.p : nullptr, D.flux_param[0],
+                         D.flux_param[1], h->f_fw.p);
+        f.fw = h->f_fw.p;
+    }
+    for (int a = 0; a < D.ndim; ++a) {
+        // the split layout's uniform stencils (all faces alike, opacities uniform)
+        double w[4] = {f.wc[0], f.wc[1], f.wc[2], f.wc[3]};
+        if (D.flux == TT_FLUX_HLL) {
+            const double sig = sig_a_uniform + sig_s_uniform, thr = D.flux_param[1];
+            const double tau = sig > 0.0 ? D.flux_param[0] * g.dx[a] * sig : 0.0;
+            const double A = tau >= thr ? sqrt((1.0 - exp(-tau * tau)) / (tau * tau))
+                                        : sqrt(std::max(1.0 - 0.5 * tau * tau, 0.0));
+            const double B = tau >= thr ? sqrt((1.0 - exp(-tau * tau * tau * tau)) / (tau * tau)) : tau;
+            w[0] = w[3] = A * (1.0 + B) / (A + B);
+            w[1] = w[2] = B * (1.0 - A) / (A + B);
+        }
+        for (int t = 0; t < 2; ++t) {
+            h->split_co.c[a][t][0] = w[2 * t] - w[2 * t + 1];
+            h->split_co.c[a][t][1] = w[2 * t + 1];
+            h->split_co.c[a][t][2] = w[2 * t];
+        }
+    }
 
     // angular grid (Sec. 3): mu and phi at cell centres, uniform weights
     Angular& A = h->ang;
@@ -1205,7 +1252,8 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
     A.n_phi = D.n_phi;
     A.w = 2.0 / D.n_theta;
     A.v = 2.0 * M_PI / D.n_phi;
-    std::vector<double> hbuf(2 * D.n_theta + 2 * D.n_phi);
+    const int KT = 1 + 2 * D.ndim;  // transport terms
+    std::vector<double> hbuf(2 * D.n_theta + 2 * D.n_phi + (size_t)KT * (D.n_theta + D.n_phi));
     for (int l = 0; l < D.n_theta; ++l) {
         const double mu = -1.0 + (l + 0.5) * A.w;
         hbuf[l] = mu;
@@ -1216,11 +1264,44 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         hbuf[2 * D.n_theta + p] = cos(ph);
         hbuf[2 * D.n_theta + D.n_phi + p] = sin(ph);
     }
+    {
+        // per-term angular factors (Sec. 4.3): term 0 is I itself; term (a, 1)
+        // and (a, 2) carry n_a^+ and n_a^- (upwind, HLL) or n_a and 1 (Rusanov),
+        // with n_x = sin(theta) cos(phi), n_y = sin(theta) sin(phi), n_z = mu
+        double* tf = hbuf.data() + 2 * D.n_theta + 2 * D.n_phi;
+        double* pf = tf + (size_t)KT * D.n_theta;
+        const bool rus = D.flux == TT_FLUX_RUSANOV;
+        for (int j = 0; j < KT; ++j) {
+            const int axis = (j - 1) >> 1, second = (j - 1) & 1;
+            for (int l = 0; l < D.n_theta; ++l) {
+                const double mu = hbuf[l], st = hbuf[D.n_theta + l];
+                double v = 1.0;
+                if (j > 0 && !(rus && second)) {
+                    if (axis < 2)
+                        v = st;
+                    else
+                        v = rus ? mu : (second ? std::min(mu, 0.0) : std::max(mu, 0.0));
+                }
+                tf[(size_t)j * D.n_theta + l] = v;
+            }
+            for (int p = 0; p < D.n_phi; ++p) {
+                const double cp = hbuf[2 * D.n_theta + p], sp = hbuf[2 * D.n_theta + D.n_phi + p];
+                double v = 1.0;
+                if (j > 0 && !(rus && second) && axis < 2) {
+                    const double n = axis == 0 ? cp : sp;
+                    v = rus ? n : (second ? std::min(n, 0.0) : std::max(n, 0.0));
+                }
+                pf[(size_t)j * D.n_phi + p] = v;
+            }
+        }
+    }
     TT_CREATE_TRY(h->ang_buf.ensure(hbuf.size(), s));
     A.mu = h->ang_buf.p;
     A.sint = A.mu + D.n_theta;
     A.cphi = A.sint + D.n_theta;
     A.sphi = A.cphi + D.n_phi;
+    A.tfac = A.sphi + D.n_phi;
+    A.pfac = A.tfac + (size_t)KT * D.n_theta;
     if (cudaMemcpyAsync(h->ang_buf.p, hbuf.data(), hbuf.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s) != cudaSuccess) {
         delete h;
@@ -1235,30 +1316,20 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         h->n[nd] = D.n_theta;
         h->n[nd + 1] = D.n_phi;
         for (int k = 0; k <= h->d; ++k) h->r[k] = 1;
-        // per-term angular factors (term order [I, x+, x-, y+, y-, z+, z-]):
-        // theta carries -nu_a times the masked theta factor, phi the masked
-        // phi factor (the direction cosines of Sec. 4.3)
+        // per-term angular factors of the split cores: theta carries -nu_a times
+        // the term's theta factor, phi the term's phi factor (the tables above)
         const int K = 1 + 2 * nd;
         std::vector<double> fac((size_t)K * (D.n_theta + D.n_phi));
         double* thf = fac.data();
         double* phf = thf + (size_t)K * D.n_theta;
+        const double* tf0 = hbuf.data() + 2 * D.n_theta + 2 * D.n_phi;
+        const double* pf0 = tf0 + (size_t)K * D.n_theta;
         for (int j = 0; j < K; ++j) {
             const int axis = (j - 1) >> 1;
-            const bool plus = ((j - 1) & 1) == 0;
             const double nu = j == 0 ? 0.0 : f.c * f.dt / g.dx[axis];
-            for (int l = 0; l < D.n_theta; ++l) {
-                const double mu = hbuf[l], st = hbuf[D.n_theta + l];
-                double v = 1.0;
-                if (j > 0) v = -nu * (axis < 2 ? st : (plus ? std::max(mu, 0.0) : std::min(mu, 0.0)));
-                thf[(size_t)j * D.n_theta + l] = v;
-            }
-            for (int p = 0; p < D.n_phi; ++p) {
-                const double cp = hbuf[2 * D.n_theta + p], sp = hbuf[2 * D.n_theta + D.n_phi + p];
-                double v = 1.0;
-                if (j > 0 && axis == 0) v = plus ? std::max(cp, 0.0) : std::min(cp, 0.0);
-                if (j > 0 && axis == 1) v = plus ? std::max(sp, 0.0) : std::min(sp, 0.0);
-                phf[(size_t)j * D.n_phi + p] = v;
-            }
+            for (int l = 0; l < D.n_theta; ++l)
+                thf[(size_t)j * D.n_theta + l] = j == 0 ? 1.0 : -nu * tf0[(size_t)j * D.n_theta + l];
+            for (int p = 0; p < D.n_phi; ++p) phf[(size_t)j * D.n_phi + p] = pf0[(size_t)j * D.n_phi + p];
         }
         TT_CREATE_TRY(h->split_fac.ensure(fac.size(), s));
         if (cudaMemcpyAsync(h->split_fac.p, fac.data(), fac.size() * sizeof(double),
@@ -1410,10 +1481,10 @@ tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
     AllocScope alloc_scope_(h->alloc_ptr());
     if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
     if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0 ||
-        h->split())
-        return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs the grouped layout, FP64 "
-                                  "precision, one rounding per step, no scattering and no external "
-                                  "sources");
+        h->split() || h->fields.flux != TT_FLUX_UPWIND)
+        return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs the grouped layout, "
+                                  "upwinding, FP64 precision, one rounding per step, no scattering "
+                                  "and no external sources");
     clear_tape(h);
     h->taping = true;
     h->tape_every = checkpoint_every;

@@ -172,6 +172,12 @@ struct Angular {
     double* sint = nullptr; // device, n_theta
     double* cphi = nullptr; // device, n_phi
     double* sphi = nullptr; // device, n_phi
+    // per-term angular factors of the transport terms [I, (x,1), (x,2), (y,1),
+    // (y,2), (z,1), (z,2)]: tfac (terms x n_theta), pfac (terms x n_phi);
+    // upwind and HLL: the masked direction cosines n_a^+, n_a^-; Rusanov: n_a
+    // and 1 (Sec. 4.3)
+    double* tfac = nullptr;
+    double* pfac = nullptr;
     double w, v;            // quadrature weights (uniform)
 };
 
@@ -210,6 +216,14 @@ struct Grid {
 struct Fields {
     double *sigma_a, *sigma_s, *cv, *T, *E_star;
     double c, a_r, dt;
+    // interface flux (Sec. 3.1): the two terms of each axis are
+    // -nu [w_L(i+1/2) X_i + w_R(i+1/2) X_{i+1} - w_L(i-1/2) X_{i-1} - w_R(i-1/2) X_i]
+    // with face weights (w_L1, w_R1, w_L2, w_R2) = wc (upwind, Rusanov) or, for
+    // HLL, per cell from fw (nc x ndim x 8: lo face w_L1 w_R1 w_L2 w_R2, then
+    // the hi face); flux == TT_FLUX_UPWIND keeps the plain differences
+    int flux = TT_FLUX_UPWIND;
+    double wc[4] = {1.0, 0.0, 0.0, 1.0};
+    const double* fw = nullptr;
 };
 // Fused transport + source row kernel (Sec. 4.3-4.4).  Writes Xg (nc x R1,
 // ld = ldg): transport blocks then (if source) scaled by s_i and the emission
@@ -229,6 +243,12 @@ void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, cons
 // phi): the K transport terms (K = 0: none) summed by Sec. 4.1's addition,
 // plus the emission term's block (ekind, shape ea x n x eb) after them.
 enum { SPLIT_SPATIAL = 0, SPLIT_THETA = 1, SPLIT_PHI = 2 };
+// Spatial stencil of the two transport terms of each axis in the split layout
+// (uniform opacities, so the flux's face weights are the same on every face):
+// term t of axis a is c[a][t][0] X_i + c[a][t][1] X_{i+1} - c[a][t][2] X_{i-1}.
+struct StencilCo {
+    double c[3][2][3];
+};
 enum { SPLIT_E_NONE = 0, SPLIT_E_IDENT_COL = 1, SPLIT_E_IDENT_ROW = 2, SPLIT_E_ONES = 3,
        SPLIT_E_FIELD = 4 };
 struct SplitCoreSpec {
@@ -239,6 +259,7 @@ struct SplitCoreSpec {
     int Ra, Rb;            // grown core
     int ekind;             // emission block kind (SPLIT_E_*)
     double tscale;         // factor on the transport blocks
+    double co[2][3];       // stencil of this core's axis (spatial cores)
 };
 // fac: K x n per-term factors of an angular core (theta: -nu_a times the mask,
 // phi: the mask; row 0 = ones).  G may be null when K = 0.
@@ -249,8 +270,15 @@ void split_grow_core(cudaStream_t s, const SplitCoreSpec& c, const double* G, co
 // upwind differences of the (a, +/-) terms taken here on F), T-dagger from the
 // quartic, e_i written to eblk[c0 st0 + c1 st1 + c2 st2] (cell coordinates),
 // E*_i to f.E_star.
-void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, bool transport, int K,
-                        const double* F, double* eblk, long st0, long st1, long st2);
+void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, const StencilCo& co,
+                        bool transport, int K, const double* F, double* eblk, long st0, long st1,
+                        long st2);
+// HLL face weights (Sec. 3.1, Eq. hll with the wave speeds after it and the
+// optical depth of Eq. tauc) of every cell's two faces per axis into fw
+// (nc x ndim x 8), from sigma_a + sigma_s (ghost opacity: the wrapped cell on
+// periodic axes, the cell itself on vacuum faces).
+void hll_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, const double* sigma_s,
+                      double beta, double tau_threshold, double* fw);
 // Isotropic initial intensity I = c a_r Tr^4 / 4 pi into X (nc x 1).
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X);
 // Adjoint form (reverse mode with the rounding's projections frozen).

@@ -7,8 +7,10 @@
 //   Sec. 4.1 -- the first core concatenates the terms' cores, middle cores are
 //   block diagonal, the last core stacks them.  Term (a, +/-) applies D^-/+
 //   along the mode of spatial core a (ghost slices of Sec. 4.5: zero for
-//   vacuum, wrapped for periodic); the theta core carries -nu_a times the
-//   masked theta factor and the phi core the masked phi factor;
+//   vacuum, wrapped for periodic; other fluxes: the face-weighted stencil
+//   of the flux, uniform here since the layout takes uniform opacities); the
+//   theta core carries -nu_a times the term's theta factor and the phi core
+//   the term's phi factor;
 //   emission (Sec. 3.2, 4.4): e (x) 1 (x) 1 with e a spatial field, appended as
 //   one more TT term whose spatial cores hold e exactly: 1D a column e;
 //   2D [I_{N_x}] [e as N_x x N_y x 1]; 3D [I_{N_x}] [e as N_x x N_y x N_z]
@@ -35,20 +37,19 @@ __device__ __forceinline__ double split_term_value(const SplitCoreSpec& c, const
         if (j == 0) return g;
         const int axis = (j - 1) >> 1;
         if (axis != c.axis) return g;
-        if (((j - 1) & 1) == 0) {  // D^-: I_i - I_{i-1}
-            double gm = 0.0;
-            if (i > 0)
-                gm = G[(row + i - 1) * c.rb + b];
-            else if (c.bc == TT_BC_PERIODIC)
-                gm = G[(row + c.n - 1) * c.rb + b];
-            return g - gm;
-        }
-        double gp = 0.0;  // D^+: I_{i+1} - I_i
+        // term (axis, t): c0 I_i + cp I_{i+1} - cm I_{i-1} (upwinding: I_i - I_{i-1}
+        // and I_{i+1} - I_i), ghost slices zero (vacuum) or wrapped (periodic)
+        const int t = (j - 1) & 1;
+        double gm = 0.0, gp = 0.0;
+        if (i > 0)
+            gm = G[(row + i - 1) * c.rb + b];
+        else if (c.bc == TT_BC_PERIODIC)
+            gm = G[(row + c.n - 1) * c.rb + b];
         if (i + 1 < c.n)
             gp = G[(row + i + 1) * c.rb + b];
         else if (c.bc == TT_BC_PERIODIC)
             gp = G[row * c.rb + b];
-        return gp - g;
+        return c.co[t][0] * g + c.co[t][1] * gp - c.co[t][2] * gm;
     }
     return fac[(long)j * c.n + i] * g * c.tscale;
 }

@@ -32,30 +32,12 @@ namespace {
 
 constexpr double FOUR_PI = 12.566370614359172953850573533118;
 
-struct TermFactors {
-    // thfac/phfac for term j at ordinate (l) / (p)
-    __device__ static double th(int j, int l, const double* mu, const double* sint) {
-        if (j == 0) return 1.0;
-        const int axis = (j - 1) >> 1;
-        const bool plus = ((j - 1) & 1) == 0;
-        if (axis < 2) return sint[l];
-        return plus ? fmax(mu[l], 0.0) : fmin(mu[l], 0.0);
-    }
-    __device__ static double ph(int j, int p, const double* cphi, const double* sphi) {
-        if (j == 0) return 1.0;
-        const int axis = (j - 1) >> 1;
-        const bool plus = ((j - 1) & 1) == 0;
-        if (axis == 0) return plus ? fmax(cphi[p], 0.0) : fmin(cphi[p], 0.0);
-        if (axis == 1) return plus ? fmax(sphi[p], 0.0) : fmin(sphi[p], 0.0);
-        return 1.0;
-    }
-};
 
 // Thg: (R1, nt, R2), R1 = nterms r1 + ns (+1 if src), R2 = nterms r2 + ns (+1 if
 // src): the term blocks, then one block per external source (its theta
 // profile), then the unit block of the emission term.
 __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, const double* Th,
-                                   const double* mu, const double* sint, int ns,
+                                   const double* tfac, int ns,
                                    const double* s_th, double* Thg, int R1, int R2) {
     const long total = (long)R1 * nt * R2;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
@@ -68,7 +50,7 @@ __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, 
         const int ja = a / r1, jb = b / r2;
         const int ka = a - nterms * r1, kb = b - nterms * r2;
         if (ja == jb && ja < nterms) {
-            v = TermFactors::th(ja, l, mu, sint) *
+            v = tfac[(long)ja * nt + l] *
                 Th[((long)(a - ja * r1) * nt + l) * r2 + (b - jb * r2)];
         } else if (ka >= 0 && ka == kb && ka < ns) {
             v = s_th[(long)ka * nt + l];
@@ -81,7 +63,7 @@ __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, 
 
 // Phg: (R2, np)
 __global__ void grown_phi_kernel(int nterms, int src, int r2, int np, const double* Ph,
-                                 const double* cphi, const double* sphi, int ns,
+                                 const double* pfac, int ns,
                                  const double* s_ph, double* Phg, int R2) {
     const long total = (long)R2 * np;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
@@ -92,7 +74,7 @@ __global__ void grown_phi_kernel(int nterms, int src, int r2, int np, const doub
         const int jb = b / r2;
         const int kb = b - nterms * r2;
         if (jb < nterms) {
-            v = TermFactors::ph(jb, p, cphi, sphi) * Ph[(long)(b - jb * r2) * np + p];
+            v = pfac[(long)jb * np + p] * Ph[(long)(b - jb * r2) * np + p];
         } else if (kb >= 0 && kb < ns) {
             v = s_ph[(long)kb * np + p];
         } else if (src && b == R2 - 1) {
@@ -103,13 +85,12 @@ __global__ void grown_phi_kernel(int nterms, int src, int r2, int np, const doub
 }
 
 // phibar[j][b] = sum_p v phfac_j[p] Ph[b][p]
-__global__ void phibar_kernel(int nterms, int r2, int np, const double* Ph, const double* cphi,
-                              const double* sphi, double v, double* phibar) {
+__global__ void phibar_kernel(int nterms, int r2, int np, const double* Ph, const double* pfac, double v, double* phibar) {
     const int total = nterms * r2;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int j = t / r2, b = t % r2;
         double acc = 0.0;
-        for (int p = 0; p < np; ++p) acc += TermFactors::ph(j, p, cphi, sphi) * Ph[(long)b * np + p];
+        for (int p = 0; p < np; ++p) acc += pfac[(long)j * np + p] * Ph[(long)b * np + p];
         phibar[t] = v * acc;
     }
 }
@@ -117,7 +98,7 @@ __global__ void phibar_kernel(int nterms, int r2, int np, const double* Ph, cons
 // thbar[j r1 + a] = sum_l w thfac_j[l] sum_b Th[a][l][b] phibar[j][b]: one warp
 // per output, lanes striding over the contiguous (l, b) block of row a.
 __global__ void thbar_kernel(int nterms, int r1, int r2, int nt, const double* Th,
-                             const double* mu, const double* sint, double w, const double* phibar,
+                             const double* tfac, double w, const double* phibar,
                              double* thbar) {
     const int lane = threadIdx.x & 31;
     const int total = nterms * r1;
@@ -129,7 +110,7 @@ __global__ void thbar_kernel(int nterms, int r1, int r2, int nt, const double* T
         double acc = 0.0;
         for (int idx = lane; idx < len; idx += 32) {
             const int l = idx / r2, b = idx - l * r2;
-            acc += TermFactors::th(j, l, mu, sint) * row[idx] * phibar[j * r2 + b];
+            acc += tfac[(long)j * nt + l] * row[idx] * phibar[j * r2 + b];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -195,17 +176,51 @@ __device__ double t_dagger(double Tm, double Estar, double ka, double Cv, double
 // Row value of the transport terms of cell i at column col (the upwind
 // differences of Sec. 4.3 with the ghost rows of Sec. 4.5): the quadrature
 // dot product with thbar over all term blocks.
+// Stencil coefficients of the two transport terms of every axis for cell i:
+// term t of axis a is c0 X_i + cp X_{i+1} - cm X_{i-1} with c0 = w_L(i+1/2) -
+// w_R(i-1/2), cp = w_R(i+1/2), cm = w_L(i-1/2) (the face weights of the flux;
+// upwinding gives exactly X_i - X_{i-1} and X_{i+1} - X_i).
+__device__ __forceinline__ void stencil_coefs(const Fields& f, int ndim, long i,
+                                              double (&co)[3][2][3]) {
+    for (int a = 0; a < ndim; ++a) {
+        double lo[4], hi[4];
+        if (f.fw) {
+            const double* p = f.fw + (i * ndim + a) * 8;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                lo[k] = p[k];
+                hi[k] = p[4 + k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lo[k] = hi[k] = f.wc[k];
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            co[a][t][0] = hi[2 * t] - lo[2 * t + 1];
+            co[a][t][1] = hi[2 * t + 1];
+            co[a][t][2] = lo[2 * t];
+        }
+    }
+}
+
+// Row value of the transport terms of cell i at column col (Sec. 4.3 with the
+// ghost rows of Sec. 4.5): the quadrature dot product with thbar over all
+// term blocks.
 __device__ __forceinline__ double transport_dot(const Grid& g, const double* nu, const long (&nb)[3][2],
-                                                int transport, int r1, const double* X, long ldx,
-                                                long i, int col, const double* thbar) {
+                                                const double (&co)[3][2][3], int transport, int r1,
+                                                const double* X, long ldx, long i, int col,
+                                                const double* thbar) {
     const double x0 = X[i * ldx + col];
     double dot = x0 * thbar[col];
     if (transport)
         for (int a = 0; a < g.ndim; ++a) {
             const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
             const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-            dot += -nu[a] * (x0 - xm) * thbar[(1 + 2 * a) * r1 + col];
-            dot += -nu[a] * (xp - x0) * thbar[(2 + 2 * a) * r1 + col];
+            dot += -nu[a] * (co[a][0][0] * x0 + co[a][0][1] * xp - co[a][0][2] * xm) *
+                   thbar[(1 + 2 * a) * r1 + col];
+            dot += -nu[a] * (co[a][1][0] * x0 + co[a][1][1] * xp - co[a][1][2] * xm) *
+                   thbar[(2 + 2 * a) * r1 + col];
         }
     return dot;
 }
@@ -235,9 +250,11 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                 const long i = i0 + j;
                 long nb[3][2];
                 cell_neighbours(g, i, nb);
+                double co[3][2][3];
+                stencil_coefs(f, g.ndim, i, co);
                 double dot = 0.0;
                 for (int col = lane; col < r1; col += 32)
-                    dot += transport_dot(g, nu, nb, transport, r1, X, ldx, i, col, thbar);
+                    dot += transport_dot(g, nu, nb, co, transport, r1, X, ldx, i, col, thbar);
                 // external sources: c dt x_k[i] times their quadrature q_k
                 for (int k = lane; k < ext.n; k += 32)
                     dot += f.c * f.dt * ext.x[(long)k * g.nc + i] * ext.q[k];
@@ -265,6 +282,8 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
             const double em = __shfl_sync(0xffffffffu, emit, j);
             long nb[3][2];
             cell_neighbours(g, i, nb);
+            double co[3][2][3];
+            stencil_coefs(f, g.ndim, i, co);
             double* out = Xg + i * ldg;
             for (int col = lane; col < r1; col += 32) {
                 const double x0 = X[i * ldx + col];
@@ -273,8 +292,10 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                     for (int a = 0; a < g.ndim; ++a) {
                         const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
                         const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-                        out[(1 + 2 * a) * r1 + col] = sc * (-nu[a] * (x0 - xm));
-                        out[(2 + 2 * a) * r1 + col] = sc * (-nu[a] * (xp - x0));
+                        out[(1 + 2 * a) * r1 + col] =
+                            sc * (-nu[a] * (co[a][0][0] * x0 + co[a][0][1] * xp - co[a][0][2] * xm));
+                        out[(2 + 2 * a) * r1 + col] =
+                            sc * (-nu[a] * (co[a][1][0] * x0 + co[a][1][1] * xp - co[a][1][2] * xm));
                     }
                 }
             }
@@ -291,7 +312,7 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
 // as the grouped kernel (quartic, s, e); e goes to the emission block of the
 // spatial core that holds it, at the cell's coordinates.
 __global__ void __launch_bounds__(256)
-split_source_kernel(Grid g, Fields f, int transport, int K, const double* __restrict__ F,
+split_source_kernel(Grid g, Fields f, StencilCo co, int transport, int K, const double* __restrict__ F,
                     double* __restrict__ eblk, long st0, long st1, long st2) {
     double nu[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < g.ndim; ++a) nu[a] = f.c * f.dt / g.dx[a];
@@ -301,13 +322,13 @@ split_source_kernel(Grid g, Fields f, int transport, int K, const double* __rest
         if (transport) {
             long nb[3][2];
             cell_neighbours(g, i, nb);
-            for (int a = 0; a < g.ndim; ++a) {
-                const int jp = 1 + 2 * a, jm = 2 + 2 * a;
-                const double fm = nb[a][0] >= 0 ? F[nb[a][0] * K + jp] : 0.0;
-                const double fp = nb[a][1] >= 0 ? F[nb[a][1] * K + jm] : 0.0;
-                dot += -nu[a] * (F[i * K + jp] - fm);
-                dot += -nu[a] * (fp - F[i * K + jm]);
-            }
+            for (int a = 0; a < g.ndim; ++a)
+                for (int t = 0; t < 2; ++t) {
+                    const int j = 1 + 2 * a + t;
+                    const double fm = nb[a][0] >= 0 ? F[nb[a][0] * K + j] : 0.0;
+                    const double fp = nb[a][1] >= 0 ? F[nb[a][1] * K + j] : 0.0;
+                    dot += -nu[a] * (co.c[a][t][0] * F[i * K + j] + co.c[a][t][1] * fp - co.c[a][t][2] * fm);
+                }
         }
         const double Estar = dot / f.c;
         const double ka = f.c * f.dt * f.sigma_a[i];
@@ -321,6 +342,44 @@ split_source_kernel(Grid g, Fields f, int transport, int K, const double* __rest
         const long c2 = i % g.n[2], q = i / g.n[2];
         const long c1 = q % g.n[1], c0 = q / g.n[1];
         eblk[c0 * st0 + c1 * st1 + c2 * st2] = sc * (ks * Jnew + ka * B);
+    }
+}
+
+// HLL wave-speed factors (Sec. 3.1, after Eq. hll): for n_a >= 0,
+// S_R = c n_a A(tau) and S_L = -c n_a B(tau) (mirrored for n_a < 0).
+__device__ __forceinline__ double hll_A(double t, double thr) {
+    if (t >= thr) return sqrt((1.0 - exp(-t * t)) / (t * t));
+    return sqrt(fmax(1.0 - 0.5 * t * t, 0.0));
+}
+__device__ __forceinline__ double hll_B(double t, double thr) {
+    if (t >= thr) return sqrt((1.0 - exp(-t * t * t * t)) / (t * t));
+    return t;
+}
+
+// Face weights of Eq. hll with those speeds: F = c n^+ (w_L1 U_L + w_R1 U_R) +
+// c n^- (w_L2 U_L + w_R2 U_R), w_L1 = A (1 + B) / (A + B), w_R1 = B (1 - A) / (A + B)
+// and the mirror image for n < 0; tau from Eq. tauc.
+__global__ void hll_weights_kernel(Grid g, const double* __restrict__ sa, const double* __restrict__ ss,
+                                   double beta, double thr, double* __restrict__ fw) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nc; i += (long)gridDim.x * blockDim.x) {
+        long nb[3][2];
+        cell_neighbours(g, i, nb);
+        const double si = sa[i] + (ss ? ss[i] : 0.0);
+        for (int a = 0; a < g.ndim; ++a) {
+            for (int side = 0; side < 2; ++side) {
+                const long j = nb[a][side] >= 0 ? nb[a][side] : i;
+                const double sj = sa[j] + (ss ? ss[j] : 0.0);
+                double tau = 0.0;
+                if (si > 0.0 && sj > 0.0) tau = 2.0 * beta * g.dx[a] / (1.0 / si + 1.0 / sj);
+                const double A = hll_A(tau, thr), B = hll_B(tau, thr);
+                const double den = A + B;
+                double* p = fw + (i * g.ndim + a) * 8 + side * 4;
+                p[0] = A * (1.0 + B) / den;
+                p[1] = B * (1.0 - A) / den;
+                p[2] = B * (1.0 - A) / den;
+                p[3] = A * (1.0 + B) / den;
+            }
+        }
     }
 }
 
@@ -463,7 +522,7 @@ stencil_adjoint_kernel(Grid g, Fields f, int r1, const double* __restrict__ ybar
 // Grown angular cores reversed: Thb[a,l,b] += sum_j thfac_j[l] Thgb[j r1 + a, l, j r2 + b],
 // Phb[b,p] += sum_j phfac_j[p] Phgb[j r2 + b, p].
 __global__ void grown_theta_adjoint_kernel(int nterms, int r1, int r2, int nt, const double* Thgb,
-                                           int R1, int R2, const double* mu, const double* sint,
+                                           int R1, int R2, const double* tfac,
                                            double* Thb) {
     const long total = (long)r1 * nt * r2;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
@@ -473,19 +532,19 @@ __global__ void grown_theta_adjoint_kernel(int nterms, int r1, int r2, int nt, c
         const int a = (int)(t / ((long)r2 * nt));
         double v = 0.0;
         for (int j = 0; j < nterms; ++j)
-            v += TermFactors::th(j, l, mu, sint) * Thgb[((long)(j * r1 + a) * nt + l) * R2 + j * r2 + b];
+            v += tfac[(long)j * nt + l] * Thgb[((long)(j * r1 + a) * nt + l) * R2 + j * r2 + b];
         Thb[t] += v;
     }
 }
 
 __global__ void grown_phi_adjoint_kernel(int nterms, int r2, int np, const double* Phgb,
-                                         const double* cphi, const double* sphi, double* Phb) {
+                                         const double* pfac, double* Phb) {
     const long total = (long)r2 * np;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
         const int p = (int)(t % np), b = (int)(t / np);
         double v = 0.0;
-        for (int j = 0; j < nterms; ++j) v += TermFactors::ph(j, p, cphi, sphi) * Phgb[(long)(j * r2 + b) * np + p];
+        for (int j = 0; j < nterms; ++j) v += pfac[(long)j * np + p] * Phgb[(long)(j * r2 + b) * np + p];
         Phb[t] += v;
     }
 }
@@ -495,7 +554,7 @@ __global__ void grown_phi_adjoint_kernel(int nterms, int r2, int np, const doubl
 // add to Thb and Phb.  phibar (nterms x r2) and phibb (nterms x r2) are scratch.
 __global__ void thbar_adjoint_theta_kernel(int j0, int nterms, int r1, int r2, int nt,
                                            const double* thbb, const double* phibar,
-                                           const double* mu, const double* sint, double w,
+                                           const double* tfac, double w,
                                            double* Thb) {
     const long total = (long)r1 * nt * r2;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
@@ -505,7 +564,7 @@ __global__ void thbar_adjoint_theta_kernel(int j0, int nterms, int r1, int r2, i
         const int a = (int)(t / ((long)r2 * nt));
         double v = 0.0;
         for (int j = j0; j < nterms; ++j)
-            v += TermFactors::th(j, l, mu, sint) * thbb[j * r1 + a] * phibar[j * r2 + b];
+            v += tfac[(long)j * nt + l] * thbb[j * r1 + a] * phibar[j * r2 + b];
         Thb[t] += w * v;
     }
 }
@@ -513,8 +572,7 @@ __global__ void thbar_adjoint_theta_kernel(int j0, int nterms, int r1, int r2, i
 // phibb[j r2 + b] = w sum_a thbb[j r1 + a] sum_l thfac_j[l] Th[a][l][b]: one warp
 // per output, lanes striding over (a, l).
 __global__ void thbar_adjoint_phibb_kernel(int j0, int nterms, int r1, int r2, int nt,
-                                           const double* thbb, const double* Th, const double* mu,
-                                           const double* sint, double w, double* phibb) {
+                                           const double* thbb, const double* Th, const double* tfac, double w, double* phibb) {
     const int lane = threadIdx.x & 31;
     const int total = nterms * r2;
     const int warps = gridDim.x * (blockDim.x >> 5);
@@ -524,7 +582,7 @@ __global__ void thbar_adjoint_phibb_kernel(int j0, int nterms, int r1, int r2, i
         if (j >= j0)
             for (int idx = lane; idx < r1 * nt; idx += 32) {
                 const int a = idx / nt, l = idx - a * nt;
-                v += thbb[j * r1 + a] * TermFactors::th(j, l, mu, sint) *
+                v += thbb[j * r1 + a] * tfac[(long)j * nt + l] *
                      Th[((long)a * nt + l) * r2 + b];
             }
 #pragma unroll
@@ -534,14 +592,14 @@ __global__ void thbar_adjoint_phibb_kernel(int j0, int nterms, int r1, int r2, i
 }
 
 __global__ void thbar_adjoint_phi_kernel(int j0, int nterms, int r2, int np, const double* phibb,
-                                         const double* cphi, const double* sphi, double v,
+                                         const double* pfac, double v,
                                          double* Phb) {
     const long total = (long)r2 * np;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
         const int p = (int)(t % np), b = (int)(t / np);
         double acc = 0.0;
-        for (int j = j0; j < nterms; ++j) acc += TermFactors::ph(j, p, cphi, sphi) * phibb[j * r2 + b];
+        for (int j = j0; j < nterms; ++j) acc += pfac[(long)j * np + p] * phibb[j * r2 + b];
         Phb[t] += v * acc;
     }
 }
@@ -704,11 +762,11 @@ void build_grown_angular(cudaStream_t s, const Angular& ang, int ndim, bool tran
     const int nterms = transport ? 1 + 2 * ndim : 1;
     note_launch();
     grown_theta_kernel<<<blocks_for((long)R1 * ang.n_theta * R2), 256, 0, s>>>(
-        nterms, source ? 1 : 0, r1, r2, ang.n_theta, Th, ang.mu, ang.sint, ext.n, ext.th, Thg,
+        nterms, source ? 1 : 0, r1, r2, ang.n_theta, Th, ang.tfac, ext.n, ext.th, Thg,
         R1, R2);
     note_launch();
     grown_phi_kernel<<<blocks_for((long)R2 * ang.n_phi), 256, 0, s>>>(
-        nterms, source ? 1 : 0, r2, ang.n_phi, Ph, ang.cphi, ang.sphi, ext.n, ext.ph, Phg, R2);
+        nterms, source ? 1 : 0, r2, ang.n_phi, Ph, ang.pfac, ext.n, ext.ph, Phg, R2);
 }
 
 // phibar scratch: thbar + nterms*r1 (caller allocates (nterms*(r1+r2)) doubles at thbar)
@@ -718,10 +776,10 @@ void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, i
     double* phibar = thbar + nterms * r1;
     note_launch();
     phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph,
-                                                               ang.cphi, ang.sphi, ang.v, phibar);
+                                                               ang.pfac, ang.v, phibar);
     note_launch();
     thbar_kernel<<<blocks_for((long)nterms * r1 * 32, 128), 128, 0, s>>>(
-        nterms, r1, r2, ang.n_theta, Th, ang.mu, ang.sint, ang.w, phibar, thbar);
+        nterms, r1, r2, ang.n_theta, Th, ang.tfac, ang.w, phibar, thbar);
 }
 
 void plain_thbar(cudaStream_t s, const Angular& ang, int r1, int r2, const double* Th,
@@ -751,11 +809,18 @@ void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, cons
                                               update_T ? 1 : 0);
 }
 
-void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, bool transport, int K,
-                        const double* F, double* eblk, long st0, long st1, long st2) {
+void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, const StencilCo& co,
+                        bool transport, int K, const double* F, double* eblk, long st0, long st1,
+                        long st2) {
     note_launch();
-    split_source_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, f, transport ? 1 : 0, K, F, eblk, st0,
+    split_source_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, f, co, transport ? 1 : 0, K, F, eblk, st0,
                                                         st1, st2);
+}
+
+void hll_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, const double* sigma_s,
+                      double beta, double tau_threshold, double* fw) {
+    note_launch();
+    hll_weights_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, sigma_a, sigma_s, beta, tau_threshold, fw);
 }
 
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X) {
@@ -786,10 +851,10 @@ void grown_angular_adjoint(cudaStream_t s, const Angular& ang, int ndim, int r1,
     const int nterms = 1 + 2 * ndim;
     note_launch();
     grown_theta_adjoint_kernel<<<blocks_for((long)r1 * ang.n_theta * r2), 256, 0, s>>>(
-        nterms, r1, r2, ang.n_theta, Thgb, R1, R2, ang.mu, ang.sint, Thb);
+        nterms, r1, r2, ang.n_theta, Thgb, R1, R2, ang.tfac, Thb);
     note_launch();
     grown_phi_adjoint_kernel<<<blocks_for((long)r2 * ang.n_phi), 256, 0, s>>>(
-        nterms, r2, ang.n_phi, Phgb, ang.cphi, ang.sphi, Phb);
+        nterms, r2, ang.n_phi, Phgb, ang.pfac, Phb);
 }
 
 void thbar_adjoint(cudaStream_t s, const Angular& ang, int nterms, int j0, int r1, int r2,
@@ -798,17 +863,16 @@ void thbar_adjoint(cudaStream_t s, const Angular& ang, int nterms, int j0, int r
     double* phibar = scratch;                 // nterms * r2
     double* phibb = scratch + nterms * r2;    // nterms * r2
     note_launch();
-    phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph, ang.cphi,
-                                                               ang.sphi, ang.v, phibar);
+    phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph, ang.pfac, ang.v, phibar);
     note_launch();
     thbar_adjoint_theta_kernel<<<blocks_for((long)r1 * ang.n_theta * r2), 256, 0, s>>>(
-        j0, nterms, r1, r2, ang.n_theta, thbb, phibar, ang.mu, ang.sint, ang.w, Thb);
+        j0, nterms, r1, r2, ang.n_theta, thbb, phibar, ang.tfac, ang.w, Thb);
     note_launch();
     thbar_adjoint_phibb_kernel<<<blocks_for((long)nterms * r2 * 32, 128), 128, 0, s>>>(
-        j0, nterms, r1, r2, ang.n_theta, thbb, Th, ang.mu, ang.sint, ang.w, phibb);
+        j0, nterms, r1, r2, ang.n_theta, thbb, Th, ang.tfac, ang.w, phibb);
     note_launch();
     thbar_adjoint_phi_kernel<<<blocks_for((long)r2 * ang.n_phi), 256, 0, s>>>(
-        j0, nterms, r2, ang.n_phi, phibb, ang.cphi, ang.sphi, ang.v, Phb);
+        j0, nterms, r2, ang.n_phi, phibb, ang.pfac, ang.v, Phb);
 }
 
 void escape_rows(cudaStream_t s, const Grid& g, double dt, int r, const double* X, long ldx,
