@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--beams-steps", type=int, default=20)
     ap.add_argument("--no-split", action="store_true", help="skip the split-layout leg")
     ap.add_argument("--split-steps", type=int, default=5, help="timed steps of the 3D split-layout run")
-    ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split"], default=None,
+    ap.add_argument("--no-fluxes", action="store_true", help="skip the Rusanov/HLL leg")
+    ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes"], default=None,
                     help="run only this companion leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
@@ -256,12 +257,15 @@ def run_ours(args, rank, world, local_rank):
     split = None
     if not args.no_split:
         split = run_split(args, torch, ttsn)
+    fluxes = None
+    if not args.no_fluxes:
+        fluxes = run_fluxes(args, torch, ttsn)
     beams = None
     if not args.no_beams:
         beams = run_beams(args, torch, ttsn, fp64_peak, mixed["bf16_peak"] if mixed else None)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
-               adjoint=adjoint, beams=beams, split=split)
+               adjoint=adjoint, beams=beams, split=split, fluxes=fluxes)
     return res
 
 
@@ -376,6 +380,42 @@ def run_split(args, torch, ttsn):
                             "steps_per_s": v, "updates_per_s": v * upd3, "ms_per_step": ms / args.split_steps,
                             "ranks_initial": r0[1:-1], "ranks": ranks,
                             "phases_ms": {k: round(x["ms"], 3) for k, x in prof.items()}}
+    return out
+
+
+def run_fluxes(args, torch, ttsn):
+    """The Rusanov and HLL fluxes on the paper's Gaussian-diffusion setup
+    (128^2 cells on 5 x 5, 8 x 16 ordinates, rho kappa_s = 1e3, no absorption,
+    t0 = 200, eps 1e-6): Rusanov at S+ = 0 (the paper's choice) and HLL
+    (beta 1, tau_threshold 1); K_f steps from the initial state timed with
+    CUDA events after an untimed run of the same length, then E compared
+    with the analytic solution A / (4 pi D (t0 + t)) exp(-r^2 / (4 D (t0 + t)))."""
+    p = workloads.gaussian_diffusion()
+    kf = 400
+    xc = workloads.cell_centres(p["n"], p["L"])
+    r2 = sum((x - c0) ** 2 for x, c0 in zip(xc, p["centre"]))
+    s4 = 4.0 * p["D"] * (p["t0"] + kf * p["dt"])
+    Ea = (p["amp"] / (np.pi * s4) * np.exp(-r2 / s4)).reshape(-1)
+    stream = torch.cuda.Stream()
+    out = {"workload": "Gaussian diffusion: 2D 128^2 cells on 5x5, 8x16 ordinates, sigma_s 1e3, sigma_a 0, "
+                       "t0 200, vacuum, CFL 0.5, eps 1e-6; steps 1..%d" % kf}
+    with torch.cuda.stream(stream):
+        for name, kw in (("rusanov_s0", dict(flux="rusanov", rusanov_s=0.0)),
+                         ("hll", dict(flux="hll", hll_beta=1.0, hll_tau_threshold=1.0))):
+            ttsn.TTSN.from_problem(p, stream=stream, **kw).step(kf)  # warm-up
+            g = ttsn.TTSN.from_problem(p, stream=stream, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = g.step(kf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            E, _, _ = g.energy()
+            v = kf / (ms * 1e-3)
+            out[name] = {"steps_per_s": v, "updates_per_s": v * int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"],
+                         "E_rel_l2_err_vs_analytic": float(np.linalg.norm(E.cpu().numpy() - Ea) / np.linalg.norm(Ea)),
+                         "ranks_last": info["ranks"][1:-1]}
     return out
 
 
@@ -636,6 +676,8 @@ def main():
             out = run_beams(args, torch, ttsn, ttsn.fp64_mma_peak(), ttsn.bf16_mma_peak())
         elif args.only == "split":
             out = run_split(args, torch, ttsn)
+        elif args.only == "fluxes":
+            out = run_fluxes(args, torch, ttsn)
         else:
             out = run_batch(args, torch, ttsn)
         print(json.dumps({args.only: out}))
@@ -698,6 +740,8 @@ def main():
         line["beams"] = res["beams"]
     if res.get("split") is not None:
         line["split"] = res["split"]
+    if res.get("fluxes") is not None:
+        line["fluxes"] = res["fluxes"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

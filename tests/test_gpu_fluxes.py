@@ -160,3 +160,43 @@ def test_adjoint_tape_needs_upwinding(ttsn):
     g = ttsn.TTSN(flux="rusanov", **a)
     assert ttsn.lib.tt_tape_begin(g._h, ctypes.c_int(1)) == -6
     g.step()
+
+
+def _gauss_E(p, t):
+    """The analytic E(t, x, y) of the Gaussian-diffusion test (Sec. 5)."""
+    xc = workloads.cell_centres(p["n"], p["L"])
+    r2 = sum((x - c0) ** 2 for x, c0 in zip(xc, p["centre"]))
+    s = 4.0 * p["D"] * (p["t0"] + t)
+    return p["amp"] / (np.pi * s) * np.exp(-r2 / s)
+
+
+def test_gaussian_diffusion_128_follows_the_analytic_solution(ttsn):
+    """The paper's Gaussian-diffusion setup (128^2 cells on 5 x 5, rho kappa_s =
+    1e3, Rusanov flux at S+ = 0) for 1024 steps (t0 = 200 -> 220): E stays
+    within 5e-3 of the analytic solution while that moves by more than 25x as
+    much from the initial state."""
+    p = workloads.gaussian_diffusion()
+    g = ttsn.TTSN.from_problem(p, flux="rusanov", rusanov_s=0.0)
+    steps = 1024
+    g.step(steps)
+    E, _, _ = g.energy()
+    Ea, E0 = _gauss_E(p, steps * p["dt"]).reshape(-1), _gauss_E(p, 0.0).reshape(-1)
+    err = np.linalg.norm(E.cpu().numpy() - Ea) / np.linalg.norm(Ea)
+    moved = np.linalg.norm(E0 - Ea) / np.linalg.norm(Ea)
+    assert err <= 5e-3 and err <= moved / 25, (err, moved)
+
+
+def test_gaussian_diffusion_32_matches_the_dense_oracle(ttsn):
+    p = workloads.gaussian_diffusion(n=(32, 32), eps=1e-9)
+    I0 = (p["c"] * p["a_r"] * p["Tr0"] ** 4 / (4 * np.pi))[..., None, None] * np.ones((p["n_theta"], p["n_phi"]))
+    d = DenseSN(p["n"], p["L"], p["n_theta"], p["n_phi"], p["c"], p["a_r"], p["dt"], p["bc"], p["sigma_a"],
+                p["cv"], p["T0"], I0, sigma_s=p["sigma_s"], flux="rusanov", rusanov_s=0.0)
+    g = ttsn.TTSN.from_problem(p, flux="rusanov", rusanov_s=0.0)
+    for _ in range(200):
+        d.step()
+    g.step(200)
+    E, _, _ = g.energy()
+    Ed = d.energy_density().reshape(-1)
+    # 200 roundings at eps = 1e-9 (each within eps of the tensor, Gram-SVD
+    # resolution ~1e-8 of the largest singular value)
+    assert np.abs(E.cpu().numpy() - Ed).max() <= 1e-6 * np.abs(Ed).max()

@@ -129,3 +129,31 @@ def test_energy_conserved_with_truncation_all_fluxes(flux, fk):
     for _ in range(4):
         t.step()
         assert abs(t.total_energy() - e0) <= 1e-13 * e0
+
+
+def _gauss_E(p, t):
+    """The analytic E(t, x, y) of the Gaussian-diffusion test (Sec. 5)."""
+    xc = workloads.cell_centres(p["n"], p["L"])
+    r2 = sum((x - c0) ** 2 for x, c0 in zip(xc, p["centre"]))
+    s = 4.0 * p["D"] * (p["t0"] + t)
+    return p["amp"] / (np.pi * s) * np.exp(-r2 / s)
+
+
+def test_gaussian_diffusion_dense_follows_the_analytic_solution():
+    """Pure isotropic scattering (rho kappa_s = 1e3) with the Rusanov flux at
+    S+ = 0 diffuses a Gaussian pulse as E = A / (4 pi D (t0 + t))
+    exp(-r^2 / (4 D (t0 + t))), D = c / (3 rho kappa_s) (Sec. 5).  On 32^2
+    cells after 200 steps the stepper stays within 1e-2 of it while the
+    solution itself moves by 5e-2 (a wrong diffusion coefficient, sign or
+    scattering term would not)."""
+    p = workloads.gaussian_diffusion(n=(32, 32))
+    I0 = (p["c"] * p["a_r"] * p["Tr0"] ** 4 / (4 * np.pi))[..., None, None] * np.ones((p["n_theta"], p["n_phi"]))
+    d = DenseSN(p["n"], p["L"], p["n_theta"], p["n_phi"], p["c"], p["a_r"], p["dt"], p["bc"], p["sigma_a"],
+                p["cv"], p["T0"], I0, sigma_s=p["sigma_s"], flux="rusanov", rusanov_s=0.0)
+    steps = 200
+    for _ in range(steps):
+        d.step()
+    Ea, E0 = _gauss_E(p, steps * p["dt"]), _gauss_E(p, 0.0)
+    err = np.linalg.norm(d.energy_density() - Ea) / np.linalg.norm(Ea)
+    moved = np.linalg.norm(E0 - Ea) / np.linalg.norm(Ea)
+    assert err <= 1e-2 and err <= 0.2 * moved, (err, moved)

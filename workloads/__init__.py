@@ -18,6 +18,11 @@ Workloads (unit box [0,1]^ndim, cell-centred, c = a_r = 1, C_v = 1):
                   0.1 at the centre and 1e-3 outside, vacuum, CFL 0.5,
                   100 steps, eps = 1e-6, rank cap 128.
 * ``scaled``      any of the above with other cell / ordinate counts (for tests).
+* ``gaussian_diffusion``  the 2D Gaussian-diffusion setup of Sec. 5 (domain
+                  5 x 5, 128^2 cells, pure isotropic scattering rho kappa_s = 1e3,
+                  no absorption, radiation initialised to a Gaussian E of
+                  amplitude A = 1 at t0 = 200 with D = c / (3 rho kappa_s));
+                  vacuum faces stand in for outflow.
 """
 import numpy as np
 
@@ -233,4 +238,24 @@ def crossing_beams(n=(256, 256), n_theta=64, n_phi=128, eps=1e-5, max_rank=96, s
     th1, ph1 = cone_window(n_theta, n_phi, 0.0, half_angle)
     th2, ph2 = cone_window(n_theta, n_phi, 90.0, half_angle)
     p["sources"] = [(x1, th1, ph1), (x2, th2, ph2)]
+    return p
+
+
+def gaussian_diffusion(n=(128, 128), n_theta=8, n_phi=16, sigma_s=1e3, t0=200.0, amp=1.0, L=5.0,
+                       eps=1e-6, max_rank=0, cfl=0.5):
+    """Scattering-dominated diffusion of a 2D Gaussian pulse: E(0, x, y) =
+    A / (4 pi D t0) exp(-r^2 / (4 D t0)) about the domain centre, D = c / (3
+    sigma_s), sigma_a = 0 (the material decouples), given through the
+    radiation temperature Tr0 = E^(1/4) (a_r = 1).  The paper runs it with the
+    Rusanov flux at S+ = 0."""
+    p = problem("small_2d", n=n, n_theta=n_theta, n_phi=n_phi, eps=eps, bc=VACUUM,
+                max_rank=max_rank, L=(L, L), cfl=cfl)
+    D = p["c"] / (3.0 * sigma_s)
+    xc = cell_centres(p["n"], p["L"])
+    centre = [0.5 * L, 0.5 * L]
+    r2 = sum((x - c0) ** 2 for x, c0 in zip(xc, centre))
+    E0 = amp / (4.0 * np.pi * D * t0) * np.exp(-r2 / (4.0 * D * t0))
+    p.update(sigma_a=np.zeros(p["n"]), sigma_s=np.full(p["n"], float(sigma_s)),
+             T0=np.full(p["n"], 1e-3), Tr0=E0 ** 0.25, name="gaussian_diffusion",
+             D=D, t0=t0, amp=amp, centre=centre)
     return p
