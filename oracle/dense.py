@@ -7,7 +7,7 @@ written directly from its definitions with no tensor train involved:
   unsplit over the spatial axes, with the upwind interface flux of Eq. upwind
   (F = c n_a U_L if n_a >= 0 else c n_a U_R, piecewise-constant states);
 * boundaries (Sec. 4.5): ghost cells, periodic = copy of the opposite edge,
-  vacuum = zero ghost (no inflow);
+  vacuum = zero ghost (no inflow), outflow = copy of the edge cell;
 * source (Sec. 3.2): backward-Euler absorption/emission/scattering, Eq.
   couple_a / couple_b, with T-dagger from ``quartic.t_dagger``;
 * temperature (Sec. 3.2, energy-conserving update): C_v (T^{m+1} - T^m) equals
@@ -33,6 +33,7 @@ from .quartic import t_dagger
 
 PERIODIC = 0
 VACUUM = 1
+OUTFLOW = 2
 
 
 class DenseSN:
@@ -68,9 +69,12 @@ class DenseSN:
         return np.einsum("...lp,lp->...", I, self.dOmega) / self.c
 
     def _ghost_pad(self, I, axis):
-        """Add one ghost cell on each side of ``axis`` (Sec. 4.5)."""
+        """Add one ghost cell on each side of ``axis`` (Sec. 4.5): zero (vacuum),
+        the opposite edge (periodic) or a copy of the edge cell (outflow)."""
         pad = [(0, 0)] * I.ndim
         pad[axis] = (1, 1)
+        if self.bc[axis] == OUTFLOW:
+            return np.pad(I, pad, mode="edge")
         P = np.pad(I, pad)  # zeros: vacuum ghosts
         if self.bc[axis] == PERIODIC:
             lo = [slice(None)] * I.ndim

@@ -35,6 +35,7 @@ from .rounding import round_gram, round_ttsvd
 
 PERIODIC = 0
 VACUUM = 1
+OUTFLOW = 2
 
 
 def field_tt(F, rel_tol=1e-15):
@@ -97,10 +98,13 @@ class SplitTTSN:
 
     # -- D^-/+ along the mode of one spatial core (Sec. 4.3, ghosts of Sec. 4.5)
     def _shift(self, G, axis, offset):
-        """Slice i of the result is slice i + offset of G's mode (periodic wrap
-        or a zero ghost slice)."""
+        """Slice i of the result is slice i + offset of G's mode (periodic wrap,
+        a zero ghost slice, or the edge slice for outflow)."""
         if self.bc[axis] == PERIODIC:
             return np.roll(G, -offset, axis=1)
+        if self.bc[axis] == OUTFLOW:
+            idx = np.clip(np.arange(G.shape[1]) + offset, 0, G.shape[1] - 1)
+            return G[:, idx]
         Z = np.zeros_like(G)
         N = G.shape[1]
         if offset > 0:

@@ -53,6 +53,7 @@ from .rounding import round_gram, round_ttsvd
 
 PERIODIC = 0
 VACUUM = 1
+OUTFLOW = 2
 
 
 class TTSN:
@@ -93,11 +94,14 @@ class TTSN:
     # -- spatial difference operators on the grouped core (Sec. 4.5 ghosts)
     def _neighbour(self, X, axis, offset):
         """Row i of the result is X at cell i + offset along ``axis``
-        (periodic wrap, or a zero ghost row for vacuum)."""
+        (periodic wrap, a zero ghost row for vacuum, the edge row for outflow)."""
         r = X.shape[-1]
         Y = X.reshape(self.n + (r,))
         if self.bc[axis] == PERIODIC:
             Z = np.roll(Y, -offset, axis=axis)
+        elif self.bc[axis] == OUTFLOW:
+            idx = np.clip(np.arange(self.n[axis]) + offset, 0, self.n[axis] - 1)
+            Z = np.take(Y, idx, axis=axis)
         else:
             Z = np.zeros_like(Y)
             N = self.n[axis]
