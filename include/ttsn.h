@@ -47,7 +47,7 @@ typedef enum {
     TT_ERR_TOO_LARGE = -7      /* output buffer too small / size over a limit   */
 } tt_status;
 
-enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1 };
+enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1, TT_BC_OUTFLOW = 2 };
 enum { TT_FP64 = 0, TT_MIXED = 1 };
 enum { TT_LAYOUT_GROUPED = 0, TT_LAYOUT_SPLIT = 1 };
 enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_HLL = 2 };
@@ -67,9 +67,10 @@ enum {
  * n_theta cells uniform in mu = cos(theta) on [-1, 1] and n_phi cells uniform
  * in phi on [0, 2 pi), ordinates at cell centres, dOmega = 4 pi/(n_theta n_phi).
  * Constants: speed of light c, radiation constant a_r.  Time step: dt if > 0,
- * otherwise cfl * min(L[a]/n[a]) / c (Sec. 3.1).  bc[a]: TT_BC_PERIODIC or
- * TT_BC_VACUUM (zero incoming intensity), the same on both faces of axis a
- * (Sec. 4.5).
+ * otherwise cfl * min(L[a]/n[a]) / c (Sec. 3.1).  bc[a]: TT_BC_PERIODIC,
+ * TT_BC_VACUUM (zero incoming intensity: zero ghost cells) or TT_BC_OUTFLOW
+ * (ghost cells copy the boundary cell, a zero-gradient face), the same on
+ * both faces of axis a (Sec. 4.5).
  * Fields (device pointers, N_c doubles each, copied in at creation):
  *   sigma_a = rho kappa_a, sigma_s = rho kappa_s (NULL = 0), cv = rho c_v,
  *   T0 = initial material temperature, Tr0 = initial radiation temperature

@@ -13,11 +13,11 @@ import numpy as np
 import torch
 
 from . import _native
-from ._native import (TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT,
+from ._native import (TT_BC_OUTFLOW, TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT,
                       TT_MIXED, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
 __all__ = ["TTSN", "TTSNBatch", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
-           "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
+           "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_BC_OUTFLOW", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
            "TT_STEP_NO_ROUND", "TT_LAYOUT_GROUPED", "TT_LAYOUT_SPLIT"]
 
 

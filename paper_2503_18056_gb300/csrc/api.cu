@@ -1099,8 +1099,8 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
     for (int a = 0; a < D.ndim; ++a) {
         if (D.n[a] < 1) return fail(TT_ERR_ARG, "tt_create: n[a] must be >= 1");
         if (!(D.L[a] > 0.0)) return fail(TT_ERR_ARG, "tt_create: L[a] must be > 0");
-        if (D.bc[a] != TT_BC_PERIODIC && D.bc[a] != TT_BC_VACUUM)
-            return fail(TT_ERR_ARG, "tt_create: bc must be TT_BC_PERIODIC or TT_BC_VACUUM");
+        if (D.bc[a] != TT_BC_PERIODIC && D.bc[a] != TT_BC_VACUUM && D.bc[a] != TT_BC_OUTFLOW)
+            return fail(TT_ERR_ARG, "tt_create: bc must be TT_BC_PERIODIC, TT_BC_VACUUM or TT_BC_OUTFLOW");
         nc *= D.n[a];
     }
     if (nc > (1L << 31)) return fail(TT_ERR_TOO_LARGE, "tt_create: more than 2^31 cells");
@@ -1481,10 +1481,11 @@ tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
     AllocScope alloc_scope_(h->alloc_ptr());
     if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
     if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0 ||
-        h->split() || h->fields.flux != TT_FLUX_UPWIND)
+        h->split() || h->fields.flux != TT_FLUX_UPWIND || h->grid.bc[0] == TT_BC_OUTFLOW ||
+        h->grid.bc[1] == TT_BC_OUTFLOW || h->grid.bc[2] == TT_BC_OUTFLOW)
         return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs the grouped layout, "
-                                  "upwinding, FP64 precision, one rounding per step, no scattering "
-                                  "and no external sources");
+                                  "upwinding, periodic or vacuum faces, FP64 precision, one rounding "
+                                  "per step, no scattering and no external sources");
     clear_tape(h);
     h->taping = true;
     h->tape_every = checkpoint_every;

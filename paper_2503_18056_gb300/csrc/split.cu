@@ -38,17 +38,22 @@ __device__ __forceinline__ double split_term_value(const SplitCoreSpec& c, const
         const int axis = (j - 1) >> 1;
         if (axis != c.axis) return g;
         // term (axis, t): c0 I_i + cp I_{i+1} - cm I_{i-1} (upwinding: I_i - I_{i-1}
-        // and I_{i+1} - I_i), ghost slices zero (vacuum) or wrapped (periodic)
+        // and I_{i+1} - I_i), ghost slices zero (vacuum), wrapped (periodic) or
+        // a copy of the boundary slice (outflow)
         const int t = (j - 1) & 1;
         double gm = 0.0, gp = 0.0;
         if (i > 0)
             gm = G[(row + i - 1) * c.rb + b];
         else if (c.bc == TT_BC_PERIODIC)
             gm = G[(row + c.n - 1) * c.rb + b];
+        else if (c.bc == TT_BC_OUTFLOW)
+            gm = g;
         if (i + 1 < c.n)
             gp = G[(row + i + 1) * c.rb + b];
         else if (c.bc == TT_BC_PERIODIC)
             gp = G[row * c.rb + b];
+        else if (c.bc == TT_BC_OUTFLOW)
+            gp = g;
         return c.co[t][0] * g + c.co[t][1] * gp - c.co[t][2] * gm;
     }
     return fac[(long)j * c.n + i] * g * c.tscale;

@@ -120,7 +120,7 @@ __global__ void thbar_kernel(int nterms, int r1, int r2, int nt, const double* T
 
 // Neighbour rows of cell i along each axis (C order, axis 0 slowest):
 // nb[a][0] = lower, nb[a][1] = upper; -1 marks a zero ghost (vacuum edge),
-// periodic edges wrap (Sec. 4.5).
+// periodic edges wrap, outflow edges point at the cell itself (Sec. 4.5).
 __device__ __forceinline__ void cell_neighbours(const Grid& g, long i, long (&nb)[3][2]) {
     long rem = i, stride = 1;
     int coord[3] = {0, 0, 0};
@@ -136,8 +136,9 @@ __device__ __forceinline__ void cell_neighbours(const Grid& g, long i, long (&nb
             lo = i + (long)((ca == 0) ? (na - 1) : -1) * stride;
             hi = i + (long)((ca == na - 1) ? -(na - 1) : 1) * stride;
         } else {
-            lo = (ca == 0) ? -1 : i - stride;
-            hi = (ca == na - 1) ? -1 : i + stride;
+            const long edge = g.bc[a] == TT_BC_OUTFLOW ? i : -1;
+            lo = (ca == 0) ? edge : i - stride;
+            hi = (ca == na - 1) ? edge : i + stride;
         }
         nb[a][0] = lo;
         nb[a][1] = hi;

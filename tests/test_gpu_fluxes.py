@@ -200,3 +200,27 @@ def test_gaussian_diffusion_32_matches_the_dense_oracle(ttsn):
     # 200 roundings at eps = 1e-9 (each within eps of the tensor, Gram-SVD
     # resolution ~1e-8 of the largest singular value)
     assert np.abs(E.cpu().numpy() - Ed).max() <= 1e-6 * np.abs(Ed).max()
+
+
+@pytest.mark.parametrize("layout", ["grouped", "split"])
+@pytest.mark.parametrize("n,bc", [((9, 7), [2, 2]), ((6, 5, 4), [2, 1, 0])])
+@pytest.mark.parametrize("flux,fk", [("upwind", {}), ("hll", dict(hll_beta=2.0, hll_tau_threshold=1.0))])
+def test_outflow_faces_untruncated_step_equals_dense(ttsn, layout, n, bc, flux, fk):
+    """Outflow faces (ghost cells copy the boundary cell, Sec. 4.5)."""
+    nt, npf = 4, 6
+    a = _args(n, nt, npf, 0, 35, uniform=(layout == "split"))
+    a["bc"] = bc
+    if layout == "split":
+        cores = workloads.random_positive_tt(list(n) + [nt, npf], [3, 2, 2, 3][: len(n) + 1], seed=36)
+        full = tt.full(cores)
+    else:
+        cores = workloads.random_positive_tt([int(np.prod(n)), nt, npf], [3, 2], seed=36)
+        full = tt.full(cores).reshape(tuple(n) + (nt, npf))
+    d = _dense(a, n, nt, npf, full, flux, fk)
+    g = ttsn.TTSN(eps=0.0, flux=flux, layout=ttsn.TT_LAYOUT_SPLIT if layout == "split" else 0, **fk, **a)
+    g.set_cores(cores)
+    for _ in range(2):
+        d.step()
+        g.step(flags=ttsn.TT_STEP_NO_ROUND)
+    F = g.full().cpu().numpy()
+    assert np.abs(F - d.I).max() <= 1e-12 * np.abs(d.I).max()
