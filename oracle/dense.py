@@ -7,7 +7,8 @@ written directly from its definitions with no tensor train involved:
   unsplit over the spatial axes, with the upwind interface flux of Eq. upwind
   (F = c n_a U_L if n_a >= 0 else c n_a U_R, piecewise-constant states);
 * boundaries (Sec. 4.5): ghost cells, periodic = copy of the opposite edge,
-  vacuum = zero ghost (no inflow), outflow = copy of the edge cell;
+  vacuum = zero ghost (no inflow) or a given rank-one inflow intensity,
+  outflow = copy of the edge cell;
 * source (Sec. 3.2): backward-Euler absorption/emission/scattering, Eq.
   couple_a / couple_b, with T-dagger from ``quartic.t_dagger``;
 * temperature (Sec. 3.2, energy-conserving update): C_v (T^{m+1} - T^m) equals
@@ -39,8 +40,13 @@ OUTFLOW = 2
 class DenseSN:
     def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
                  I0, sigma_s=None, sources=None, flux="upwind", rusanov_s=1.0, hll_beta=1.0,
-                 hll_tau_threshold=1.0):
+                 hll_tau_threshold=1.0, inflow=None):
         self.flux = flux
+        # inflow[(axis, side)] = (g, theta, phi): on that vacuum face the ghost
+        # cells hold the rank-one intensity g(cell) theta(l) phi(p) instead of
+        # zero (Sec. 4.5 ghost cells with a Dirichlet value); g is a field of
+        # the grid's shape, read on the face's layer of cells
+        self.inflow = {k: tuple(np.asarray(v, float) for v in vals) for k, vals in (inflow or {}).items()}
         self.rusanov_s = float(rusanov_s)
         self.hll_beta, self.hll_tau_threshold = float(hll_beta), float(hll_tau_threshold)
         self.ndim = len(n)
@@ -76,6 +82,14 @@ class DenseSN:
         if self.bc[axis] == OUTFLOW:
             return np.pad(I, pad, mode="edge")
         P = np.pad(I, pad)  # zeros: vacuum ghosts
+        for side in (0, 1):
+            if (axis, side) in self.inflow and self.bc[axis] == VACUUM:
+                g, th, ph = self.inflow[(axis, side)]
+                layer = [slice(None)] * (I.ndim - 2)
+                layer[axis] = 0 if side == 0 else self.n[axis] - 1
+                ghost = [slice(None)] * I.ndim
+                ghost[axis] = 0 if side == 0 else -1
+                P[tuple(ghost)] = g.reshape(self.n)[tuple(layer)][..., None, None] * np.outer(th, ph)
         if self.bc[axis] == PERIODIC:
             lo = [slice(None)] * I.ndim
             hi = [slice(None)] * I.ndim

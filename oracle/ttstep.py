@@ -60,8 +60,13 @@ class TTSN:
     def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
                  cores, sigma_s=None, eps=0.0, max_rank=None,
                  rounds_per_step=1, rounding="gram", sources=None, flux="upwind",
-                 rusanov_s=1.0, hll_beta=1.0, hll_tau_threshold=1.0):
+                 rusanov_s=1.0, hll_beta=1.0, hll_tau_threshold=1.0, inflow=None):
         self.flux = flux
+        # inflow faces: the ghost intensity g theta phi of a vacuum face enters
+        # the boundary cells' stencil as known values, i.e. as rank-one terms
+        # -nu (-w_L(lo) g theta phi) on the low face and -nu w_R(hi) g theta phi
+        # on the high face, times each term's angular factor
+        self.inflow = {k: tuple(np.asarray(v, float) for v in vals) for k, vals in (inflow or {}).items()}
         self.rusanov_s = float(rusanov_s)
         self.hll_beta, self.hll_tau_threshold = float(hll_beta), float(hll_tau_threshold)
         self.ndim = len(n)
@@ -204,6 +209,17 @@ class TTSN:
                 terms.append([(-nu * D)[None], Th * tf[None, :, None], Ph * pf[None, :, None]])
         for x, th, ph in self.sources:
             terms.append(tt.rank_one([self.c * self.dt * x, th, ph]))
+        for (a, side), (gf, th_f, ph_f) in sorted(self.inflow.items()):
+            if self.bc[a] != VACUUM:
+                continue
+            nu = self.c * self.dt / self.dx[a]
+            coord = np.indices(self.n)[a].reshape(-1)
+            on = coord == (0 if side == 0 else self.n[a] - 1)
+            g = np.where(on, gf.reshape(-1), 0.0)
+            for (lo, hi), (tf, pf) in zip(self._face_weights(a), self._angular(a)):
+                w = lo[0] if side == 0 else -hi[1]  # +w_L(i-1/2) or -w_R(i+1/2)
+                if np.any(w * g != 0.0):  # upwinding has one such term per face
+                    terms.append(tt.rank_one([nu * w * g, tf * th_f, pf * ph_f]))
         return tt.add_many(terms)
 
     def energy_density(self, cores=None):

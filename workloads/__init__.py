@@ -23,6 +23,9 @@ Workloads (unit box [0,1]^ndim, cell-centred, c = a_r = 1, C_v = 1):
                   no absorption, radiation initialised to a Gaussian E of
                   amplitude A = 1 at t0 = 200 with D = c / (3 rho kappa_s));
                   vacuum faces stand in for outflow.
+* ``hohlraum``    the 2D hohlraum of Sec. 5.1: [0, 2]^2, vacuum faces with
+                  isotropic unit inflow on x = 0 and y = 0, no material,
+                  empty start, to t = 0.75.
 """
 import numpy as np
 
@@ -258,4 +261,19 @@ def gaussian_diffusion(n=(128, 128), n_theta=8, n_phi=16, sigma_s=1e3, t0=200.0,
     p.update(sigma_a=np.zeros(p["n"]), sigma_s=np.full(p["n"], float(sigma_s)),
              T0=np.full(p["n"], 1e-3), Tr0=E0 ** 0.25, name="gaussian_diffusion",
              D=D, t0=t0, amp=amp, centre=centre)
+    return p
+
+
+def hohlraum(n=(256, 256), n_theta=32, n_phi=64, eps=1e-4, max_rank=0, t_lim=0.75, cfl=0.5):
+    """The 2D hohlraum of Sec. 5.1: domain [0, 2]^2, vacuum faces, isotropic
+    unit inflow (I = J = 1) through the x = 0 and y = 0 faces, no material
+    (sigma = 0), radiation initially absent, run to t = 0.75.  ``inflow`` maps
+    (axis, side) to the rank-one ghost intensity (face field, theta, phi)."""
+    p = problem("small_2d", n=n, n_theta=n_theta, n_phi=n_phi, eps=eps, bc=VACUUM,
+                max_rank=max_rank, L=(2.0, 2.0), cfl=cfl)
+    nn = p["n"]
+    p.update(sigma_a=np.zeros(nn), T0=np.full(nn, 1e-3), Tr0=np.zeros(nn), name="hohlraum",
+             t_lim=t_lim)
+    unit = (np.ones(nn), np.ones(n_theta), np.ones(n_phi))
+    p["inflow"] = {(0, 0): unit, (1, 0): unit}
     return p
