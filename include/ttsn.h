@@ -250,6 +250,24 @@ tt_status tt_get_cores(tt_handle h, double** cores_dev, int* shapes_host);
  */
 tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* ranks_host);
 
+/*
+ * tt_set_inflow: a given incoming intensity on one face (Sec. 4.5 ghost cells
+ * holding a Dirichlet value instead of zero): on face `side` (0: low, 1: high)
+ * of a TT_BC_VACUUM axis the ghost cells hold the rank-one intensity
+ * g(cell) theta(l) phi(p), g_dev N_c doubles in cell order (read on the face's
+ * layer of cells), theta_dev n_theta and phi_dev n_phi doubles, copied in.
+ * With the flux's face weights the known ghost enters the boundary cells'
+ * stencil as one rank-one term per face for upwinding (two for Rusanov and
+ * HLL), carried like a fixed source (tt_set_sources) that follows the
+ * caller's own sources; together at most TT_MAX_SOURCES.  g_dev = NULL
+ * removes the face's inflow.  TT_ERR_ARG for a bad axis/side, a face that is
+ * not vacuum or too many terms; TT_ERR_STATE on a split-layout handle.  The
+ * hohlraum problem of Sec. 5.1 is unit isotropic inflow on the low x and y
+ * faces.
+ */
+tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, const double* theta_dev,
+                        const double* phi_dev);
+
 /* tt_set_precision: TT_FP64 or TT_MIXED for the following roundings. */
 tt_status tt_set_precision(tt_handle h, int precision);
 

@@ -237,7 +237,20 @@ class TTSN(_Handle):
         obj = cls(**kw)
         if p.get("sources"):
             obj.set_sources(p["sources"])
+        for (axis, side), (g, th, ph) in sorted((p.get("inflow") or {}).items()):
+            obj.set_inflow(axis, side, g, th, ph)
         return obj
+
+    def set_inflow(self, axis, side, g=None, theta=None, phi=None):
+        """Incoming intensity g (x) theta (x) phi on face ``side`` (0 low, 1 high)
+        of a vacuum axis (tt_set_inflow); g=None removes it."""
+        if g is None:
+            check(lib.tt_set_inflow(self._h, int(axis), int(side), None, None, None))
+            return
+        gd = _dev(np.asarray(g).reshape(-1), self.nc)
+        td, pd = _dev(theta, self.n_theta), _dev(phi, self.n_phi)
+        check(lib.tt_set_inflow(self._h, int(axis), int(side), ctypes.c_void_p(gd.data_ptr()),
+                                ctypes.c_void_p(td.data_ptr()), ctypes.c_void_p(pd.data_ptr())))
 
     def set_sources(self, sources):
         """Fixed external sources: a list of (x (N_c), theta (n_theta), phi (n_phi))

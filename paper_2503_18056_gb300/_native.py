@@ -98,6 +98,7 @@ def _load():
         "tt_batch_sync": [vp],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
         "tt_pchol": [i, vp, i, vp, vp, ip],
+        "tt_set_inflow": [vp, i, i, vp, vp, vp],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_longlong), dp, dp],
@@ -137,7 +138,7 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_bench_bf16_mma", "tt_batch_create", "tt_batch_step", "tt_batch_size",
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
             "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
-            "tt_create_ex", "tt_get_cores", "tt_pchol"]
+            "tt_create_ex", "tt_get_cores", "tt_pchol", "tt_set_inflow"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

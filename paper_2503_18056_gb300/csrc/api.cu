@@ -205,8 +205,19 @@ struct tt_ctx {
     Angular ang{};
     Fields fields{};
     DevBuf f_sigma_a, f_sigma_s, f_cv, f_T, f_Estar, f_E, thbar, red, ang_buf;
-    DevBuf src_x, src_th, src_ph, src_q;  // fixed external sources
+    DevBuf src_x, src_th, src_ph, src_q;  // fixed external sources (all kinds)
     int nsrc = 0;
+    // the caller's own sources (tt_set_sources) and the inflow faces
+    // (tt_set_inflow); src_* holds the user sources followed by the inflow
+    // faces' rank-one terms
+    DevBuf usr_x, usr_th, usr_ph;
+    int nusr = 0;
+    struct InflowFace {
+        bool on = false;
+        DevBuf g;
+        std::vector<double> th, ph;
+    } inflow[3][2];
+    std::vector<double> h_tfac, h_pfac;  // host copies of the angular factor tables
     // split-space layout (cores x[, y[, z]], theta, phi): per-term angular
     // factors (theta rows then phi rows, 1 + 2 ndim terms each), the uniform
     // absorption factor s, the spatial contractions F (nc x terms) and the
@@ -260,8 +271,10 @@ struct tt_ctx {
         DevBuf* bufs[] = {&slscratch, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
-                          &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw};
+                          &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph};
         for (DevBuf* b : bufs) b->release();
+        for (auto& ax : inflow)
+            for (auto& face : ax) face.g.release();
         eig.release();
         for (StepRec* r : tape) {
             r->release();
@@ -1295,6 +1308,11 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
             }
         }
     }
+    {
+        const double* tf = hbuf.data() + 2 * D.n_theta + 2 * D.n_phi;
+        h->h_tfac.assign(tf, tf + (size_t)KT * D.n_theta);
+        h->h_pfac.assign(tf + (size_t)KT * D.n_theta, tf + (size_t)KT * (D.n_theta + D.n_phi));
+    }
     TT_CREATE_TRY(h->ang_buf.ensure(hbuf.size(), s));
     A.mu = h->ang_buf.p;
     A.sint = A.mu + D.n_theta;
@@ -1686,6 +1704,71 @@ tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* r
     return TT_OK;
 }
 
+namespace {
+// src_* = the caller's sources, then two rank-one terms per inflow face (one
+// for upwinding, whose other face weight is zero): column x from
+// inflow_source, angular profiles the term's angular factor times the face's,
+// and every profile's quadrature q_k = (w sum_l theta_k)(v sum_p phi_k).
+tt_status rebuild_sources(tt_ctx* h) {
+    cudaStream_t s = h->stream;
+    const long nc = h->grid.nc;
+    const int nt = h->ang.n_theta, np = h->ang.n_phi;
+    struct Item {
+        int a, side, t;
+    };
+    std::vector<Item> items;
+    for (int a = 0; a < h->grid.ndim; ++a)
+        for (int side = 0; side < 2; ++side) {
+            if (!h->inflow[a][side].on) continue;
+            for (int t = 0; t < 2; ++t) {
+                if (h->fields.flux == TT_FLUX_UPWIND && t != side) continue;  // w_L2 = w_R1 = 0
+                items.push_back({a, side, t});
+            }
+        }
+    const int count = h->nusr + (int)items.size();
+    h->nsrc = 0;
+    if (count > TT_MAX_SOURCES)
+        return fail(TT_ERR_ARG, "sources plus inflow-face terms exceed TT_MAX_SOURCES");
+    if (count == 0) return TT_OK;
+    TT_TRY(h->src_x.ensure((size_t)count * nc, s));
+    TT_TRY(h->src_th.ensure((size_t)count * nt, s));
+    TT_TRY(h->src_ph.ensure((size_t)count * np, s));
+    TT_TRY(h->src_q.ensure((size_t)count, s));
+    std::vector<double> th((size_t)count * nt), ph((size_t)count * np), q(count);
+    if (h->nusr > 0) {
+        const int u = h->nusr;
+        TT_CUDA_TRY(cudaMemcpyAsync(h->src_x.p, h->usr_x.p, (size_t)u * nc * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(th.data(), h->usr_th.p, (size_t)u * nt * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(ph.data(), h->usr_ph.p, (size_t)u * np * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    for (size_t k = 0; k < items.size(); ++k) {
+        const Item& it = items[k];
+        const tt_ctx::InflowFace& face = h->inflow[it.a][it.side];
+        const int col = h->nusr + (int)k, j = 1 + 2 * it.a + it.t;
+        inflow_source(s, h->grid, h->fields, it.a, it.side, it.t, face.g.p, h->src_x.p + (size_t)col * nc);
+        for (int l = 0; l < nt; ++l) th[(size_t)col * nt + l] = h->h_tfac[(size_t)j * nt + l] * face.th[l];
+        for (int p = 0; p < np; ++p) ph[(size_t)col * np + p] = h->h_pfac[(size_t)j * np + p] * face.ph[p];
+    }
+    TT_CUDA_TRY(cudaGetLastError());
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = 0; k < count; ++k) {
+        double a = 0.0, b = 0.0;
+        for (int l = 0; l < nt; ++l) a += th[(size_t)k * nt + l];
+        for (int p = 0; p < np; ++p) b += ph[(size_t)k * np + p];
+        q[k] = (h->ang.w * a) * (h->ang.v * b);
+    }
+    TT_CUDA_TRY(cudaMemcpyAsync(h->src_th.p, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->src_ph.p, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->src_q.p, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    h->nsrc = count;
+    return TT_OK;
+}
+}  // namespace
+
 tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const double* theta_dev,
                          const double* phi_dev) {
     set_error("");
@@ -1701,36 +1784,64 @@ tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const doub
     cudaStream_t s = h->stream;
     const long nc = h->grid.nc;
     const int nt = h->ang.n_theta, np = h->ang.n_phi;
-    h->nsrc = 0;
-    if (count == 0) return TT_OK;
-    TT_TRY(h->src_x.ensure((size_t)count * nc, s));
-    TT_TRY(h->src_th.ensure((size_t)count * nt, s));
-    TT_TRY(h->src_ph.ensure((size_t)count * np, s));
-    TT_TRY(h->src_q.ensure((size_t)count, s));
-    TT_CUDA_TRY(cudaMemcpyAsync(h->src_x.p, x_dev, (size_t)count * nc * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
-    TT_CUDA_TRY(cudaMemcpyAsync(h->src_th.p, theta_dev, (size_t)count * nt * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
-    TT_CUDA_TRY(cudaMemcpyAsync(h->src_ph.p, phi_dev, (size_t)count * np * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
-    // q_k = (w sum_l theta_k[l]) (v sum_p phi_k[p]): the uniform weights factor
-    std::vector<double> th((size_t)count * nt), ph((size_t)count * np), q(count);
-    TT_CUDA_TRY(cudaMemcpyAsync(th.data(), theta_dev, th.size() * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
-    TT_CUDA_TRY(cudaMemcpyAsync(ph.data(), phi_dev, ph.size() * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
-    TT_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int k = 0; k < count; ++k) {
-        double a = 0.0, b = 0.0;
-        for (int l = 0; l < nt; ++l) a += th[(size_t)k * nt + l];
-        for (int p = 0; p < np; ++p) b += ph[(size_t)k * np + p];
-        q[k] = (h->ang.w * a) * (h->ang.v * b);
+    int inflow_terms = 0;
+    for (auto& ax : h->inflow)
+        for (auto& face : ax) inflow_terms += face.on ? 2 : 0;
+    if (count + inflow_terms > TT_MAX_SOURCES)
+        return fail(TT_ERR_ARG, "tt_set_sources: sources plus inflow-face terms exceed TT_MAX_SOURCES");
+    h->nusr = 0;
+    if (count > 0) {
+        TT_TRY(h->usr_x.ensure((size_t)count * nc, s));
+        TT_TRY(h->usr_th.ensure((size_t)count * nt, s));
+        TT_TRY(h->usr_ph.ensure((size_t)count * np, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(h->usr_x.p, x_dev, (size_t)count * nc * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(h->usr_th.p, theta_dev, (size_t)count * nt * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(h->usr_ph.p, phi_dev, (size_t)count * np * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+        h->nusr = count;
     }
-    TT_CUDA_TRY(cudaMemcpyAsync(h->src_q.p, q.data(), count * sizeof(double),
-                                cudaMemcpyHostToDevice, s));
-    TT_CUDA_TRY(cudaStreamSynchronize(s));
-    h->nsrc = count;
-    return TT_OK;
+    return rebuild_sources(h);
+}
+
+tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, const double* theta_dev,
+                        const double* phi_dev) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
+    if (axis < 0 || axis >= h->grid.ndim || (side != 0 && side != 1))
+        return fail(TT_ERR_ARG, "tt_set_inflow: axis or side out of range");
+    if (h->grid.bc[axis] != TT_BC_VACUUM)
+        return fail(TT_ERR_ARG, "tt_set_inflow: the axis must have vacuum faces");
+    if (g_dev && (!theta_dev || !phi_dev)) return fail(TT_ERR_ARG, "tt_set_inflow: null angular profile");
+    if (g_dev && h->split())
+        return fail(TT_ERR_STATE, "tt_set_inflow: inflow faces need the grouped layout");
+    clear_tape(h);
+    cudaStream_t s = h->stream;
+    tt_ctx::InflowFace& face = h->inflow[axis][side];
+    const bool was_on = face.on;
+    face.on = false;
+    if (g_dev) {
+        int terms = h->nusr;
+        for (auto& ax : h->inflow)
+            for (auto& f2 : ax) terms += f2.on ? 2 : 0;
+        if (terms + 2 > TT_MAX_SOURCES) {
+            face.on = was_on;
+            return fail(TT_ERR_ARG, "tt_set_inflow: sources plus inflow-face terms exceed TT_MAX_SOURCES");
+        }
+        const long nc = h->grid.nc;
+        const int nt = h->ang.n_theta, np = h->ang.n_phi;
+        TT_TRY(face.g.ensure((size_t)nc, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(face.g.p, g_dev, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        face.th.resize(nt);
+        face.ph.resize(np);
+        TT_CUDA_TRY(cudaMemcpyAsync(face.th.data(), theta_dev, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(face.ph.data(), phi_dev, np * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+        face.on = true;
+    }
+    return rebuild_sources(h);
 }
 
 tt_status tt_set_precision(tt_handle h, int precision) {

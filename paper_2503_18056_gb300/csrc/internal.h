@@ -279,6 +279,12 @@ void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, const St
 // periodic axes, the cell itself on vacuum faces).
 void hll_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, const double* sigma_s,
                       double beta, double tau_threshold, double* fw);
+// Inflow face (axis, side) of a vacuum axis as a fixed-source column: x[i] =
+// w g[i] / dx_a on the face's layer of cells (0 elsewhere), w = +w_L(i-1/2) of
+// term t on the low face, -w_R(i+1/2) on the high face, so that c dt x is the
+// known ghost's contribution -nu (-w_L g) or -nu (w_R g) to the boundary cells.
+void inflow_source(cudaStream_t s, const Grid& g, const Fields& f, int axis, int side, int term,
+                   const double* gface, double* x);
 // Isotropic initial intensity I = c a_r Tr^4 / 4 pi into X (nc x 1).
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X);
 // Adjoint form (reverse mode with the rounding's projections frozen).

@@ -384,6 +384,33 @@ __global__ void hll_weights_kernel(Grid g, const double* __restrict__ sa, const 
     }
 }
 
+__global__ void inflow_source_kernel(Grid g, Fields f, int axis, int side, int term,
+                                     const double* __restrict__ gface, double* __restrict__ x) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nc; i += (long)gridDim.x * blockDim.x) {
+        long rem = i;
+        int coord[3] = {0, 0, 0};
+        for (int a = g.ndim - 1; a >= 0; --a) {
+            coord[a] = (int)(rem % g.n[a]);
+            rem /= g.n[a];
+        }
+        const bool on = coord[axis] == (side == 0 ? 0 : g.n[axis] - 1);
+        double v = 0.0;
+        if (on) {
+            // face weights (w_L1, w_R1, w_L2, w_R2) of the face on this side
+            double w4[4];
+            if (f.fw) {
+                const double* p = f.fw + (i * g.ndim + axis) * 8 + side * 4;
+                for (int k = 0; k < 4; ++k) w4[k] = p[k];
+            } else {
+                for (int k = 0; k < 4; ++k) w4[k] = f.wc[k];
+            }
+            const double w = side == 0 ? w4[2 * term] : -w4[2 * term + 1];
+            v = w * gface[i] / g.dx[axis];
+        }
+        x[i] = v;
+    }
+}
+
 __global__ void __launch_bounds__(256)
 energy_rows_kernel(long nc, int r, const double* __restrict__ X, long ldx,
                    const double* __restrict__ thbar, double c, double* E_out,
@@ -822,6 +849,12 @@ void hll_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, cons
                       double beta, double tau_threshold, double* fw) {
     note_launch();
     hll_weights_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, sigma_a, sigma_s, beta, tau_threshold, fw);
+}
+
+void inflow_source(cudaStream_t s, const Grid& g, const Fields& f, int axis, int side, int term,
+                   const double* gface, double* x) {
+    note_launch();
+    inflow_source_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, f, axis, side, term, gface, x);
 }
 
 void init_isotropic(cudaStream_t s, long nc, const double* Tr, double c, double a_r, double* X) {
