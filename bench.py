@@ -384,7 +384,8 @@ def run_split(args, torch, ttsn):
 
 
 def run_fluxes(args, torch, ttsn):
-    """The Rusanov and HLL fluxes on the paper's Gaussian-diffusion setup
+    """The Rusanov and HLL fluxes on the paper's Gaussian-diffusion setup, and
+    the hohlraum of Sec. 5.1 (inflow faces).  Diffusion:
     (128^2 cells on 5 x 5, 8 x 16 ordinates, rho kappa_s = 1e3, no absorption,
     t0 = 200, eps 1e-6): Rusanov at S+ = 0 (the paper's choice) and HLL
     (beta 1, tau_threshold 1); K_f steps from the initial state timed with
@@ -416,7 +417,43 @@ def run_fluxes(args, torch, ttsn):
             out[name] = {"steps_per_s": v, "updates_per_s": v * int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"],
                          "E_rel_l2_err_vs_analytic": float(np.linalg.norm(E.cpu().numpy() - Ea) / np.linalg.norm(Ea)),
                          "ranks_last": info["ranks"][1:-1]}
+        # the hohlraum of Sec. 5.1: inflow faces, upwinding, to t = 0.75
+        h = workloads.hohlraum()
+        steps = int(round(h["t_lim"] / h["dt"]))
+        ttsn.TTSN.from_problem(h, stream=stream).step(8)  # warm-up
+        g = ttsn.TTSN.from_problem(h, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = g.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        E, _, _ = g.energy()
+        J = h["c"] * E.cpu().numpy().reshape(h["n"]) / (4 * np.pi)
+        xc = workloads.cell_centres(h["n"], h["L"])
+        Ja = _hohlraum_J(steps * h["dt"], xc[0], xc[1], h["c"])
+        sub = (xc[0] < 1.0) & (xc[1] < 1.0)
+        v = steps / (ms * 1e-3)
+        out["hohlraum"] = {"workload": "hohlraum (Sec. 5.1): 2D 256^2 on [0,2]^2, 32x64 ordinates, unit isotropic "
+                                      "inflow on x = 0 and y = 0, vacuum, upwind, eps 1e-4, steps 1..%d (t = 0.75)" % steps,
+                           "steps_per_s": v, "updates_per_s": v * int(np.prod(h["n"])) * h["n_theta"] * h["n_phi"],
+                           "J_L1_err_vs_analytic": float(np.mean(np.abs(J - Ja)[sub])),
+                           "ranks_last": info["ranks"][1:-1]}
     return out
+
+
+def _hohlraum_J(t, x, y, c=1.0):
+    """Analytic mean intensity of the hohlraum (Sec. 5.1): unit isotropic
+    inflow through the x = 0 and y = 0 faces of an empty domain."""
+    def part(u, v):
+        ct = c * t
+        with np.errstate(invalid="ignore", divide="ignore"):
+            eta = np.arccos(np.minimum(v / np.sqrt(np.maximum(ct ** 2 - u ** 2, 1e-300)), 1.0))
+            r = np.sqrt(u ** 2 + v ** 2)
+            val = 0.5 - (np.pi - eta) * u / (2 * np.pi * ct) - np.arcsin(u * np.sin(eta) / r) / (2 * np.pi)
+        return np.where(u < ct, val, 0.0)
+    return part(x, y) + part(y, x)
 
 
 def run_adjoint(args, torch, ttsn):
