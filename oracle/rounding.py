@@ -1,6 +1,7 @@
 """TT rounding, Algorithm 1 of App. A (oracle; test infrastructure).
 
-Two truncation rules for Step "truncate" of Algorithm 1:
+Three truncation rules for Step "truncate" of Algorithm 1 (the randomized
+one, ``round_randomized``, App. A.3, takes its Gaussian sketch as an input):
 
 * ``round_ttsvd`` -- the traditional TT-SVD rounding of App. A.1
   (Oseledets 2011): QR orthogonalisation in the backward sweep, truncated SVD
@@ -129,3 +130,36 @@ def round_gram(cores, eps=0.0, max_rank=None, forced=None):
         G[k] = Aprime.reshape(r0, n, r)
         G[k + 1] = np.tensordot(Mupd, G[k + 1], axes=([1], [0]))
     return G, sig
+
+
+def sketch_right(cores, omega):
+    """Backward sweep of the randomized rounding (App. A.3, Eq. randprojection
+    W = B^T Omega for every bond): W[k] (R_k x l_k) is the right part of bond k
+    (cores k+1..d) contracted over all its modes with the random TT omega
+    (cores of shape (l_{k-1}, n_k, l_k)), computed from the last core back."""
+    d = len(cores)
+    W = [None] * (d - 1)
+    W[d - 2] = cores[d - 1][:, :, 0] @ omega[d - 1][:, :, 0].T
+    for k in range(d - 2, 0, -1):
+        T = np.tensordot(cores[k], W[k], axes=([2], [0]))          # (R_{k-1}, n_k, l_k)
+        W[k - 1] = np.tensordot(T, omega[k], axes=([1, 2], [1, 2]))  # (R_{k-1}, l_{k-1})
+    return W
+
+
+def round_randomized(cores, omega):
+    """Randomized rounding (App. A.3, Eq. randfinal): for each bond, left to
+    right, X = A B^T is replaced by Q (Q^T A) B^T with Q an orthonormal basis of
+    the sketch A W, W = B^T Omega from ``sketch_right``; A' = Q, M_upd = Q^T A.
+    The output ranks are the sketch ranks l_k (capped by the bond's size)."""
+    d = len(cores)
+    G = [np.array(c, float) for c in cores]
+    W = sketch_right(G, omega)
+    for k in range(d - 1):
+        r0, n, R = G[k].shape
+        A = G[k].reshape(r0 * n, R)
+        Y = A @ W[k]
+        Q, _ = np.linalg.qr(Y)
+        M = Q.T @ A
+        G[k] = Q.reshape(r0, n, Q.shape[1])
+        G[k + 1] = np.tensordot(M, G[k + 1], axes=([1], [0]))
+    return G

@@ -49,7 +49,7 @@ import numpy as np
 
 from . import angles, tt
 from .quartic import t_dagger
-from .rounding import round_gram, round_ttsvd
+from .rounding import round_gram, round_randomized, round_ttsvd
 
 PERIODIC = 0
 VACUUM = 1
@@ -60,8 +60,11 @@ class TTSN:
     def __init__(self, n, L, n_theta, n_phi, c, a_r, dt, bc, sigma_a, cv, T0,
                  cores, sigma_s=None, eps=0.0, max_rank=None,
                  rounds_per_step=1, rounding="gram", sources=None, flux="upwind",
-                 rusanov_s=1.0, hll_beta=1.0, hll_tau_threshold=1.0, inflow=None):
+                 rusanov_s=1.0, hll_beta=1.0, hll_tau_threshold=1.0, inflow=None, sketch=None):
         self.flux = flux
+        # rounding="randomized": Gaussian sketch TT (cores (L_{k-1}, n_k, L_k));
+        # a rounding to ranks l_k uses the leading l_{k-1} x n_k x l_k blocks
+        self.sketch = sketch
         # inflow faces: the ghost intensity g theta phi of a vacuum face enters
         # the boundary cells' stencil as known values, i.e. as rank-one terms
         # -nu (-w_L(lo) g theta phi) on the low face and -nu w_R(hi) g theta phi
@@ -244,6 +247,15 @@ class TTSN:
     def round(self, cores, forced=None):
         if self.rounding is None:
             return cores
+        if self.rounding == "randomized":
+            R = tt.ranks(cores)
+            ls = [min(forced[k] if forced else self.sketch[k].shape[2], R[k]) for k in range(len(R))]
+            r = [1] + ls + [1]
+            om = [self.sketch[k][: r[k], :, : r[k + 1]] for k in range(len(cores))]
+            out = round_randomized(cores, om)
+            self.last_sigmas.append([])
+            self.last_ranks.append(tt.ranks(out))
+            return out
         fn = round_gram if self.rounding == "gram" else round_ttsvd
         out, sig = fn(cores, self.eps, self.max_rank, forced)
         self.last_sigmas.append(sig)

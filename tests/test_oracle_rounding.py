@@ -5,7 +5,7 @@ import pytest
 
 import workloads
 from oracle import tt
-from oracle.rounding import EPS_MACH, choose_rank, round_gram, round_ttsvd
+from oracle.rounding import EPS_MACH, choose_rank, round_gram, round_randomized, round_ttsvd, sketch_right
 
 ROUNDERS = [("ttsvd", round_ttsvd, 1e-12), ("gram", round_gram, 1e-10)]
 
@@ -106,3 +106,63 @@ def test_zero_tensor_rounds_to_rank_one_zero():
     Z, _ = round_gram(X, eps=1e-6)
     assert tt.ranks(Z) == [1, 1]
     assert np.abs(tt.full(Z)).max() == 0.0
+
+
+def _omega(modes, ranks, seed):
+    rng = np.random.default_rng(seed)
+    r = [1] + list(ranks) + [1]
+    return [rng.standard_normal((r[k], m, r[k + 1])) for k, m in enumerate(modes)]
+
+
+def test_randomized_rounding_recovers_an_exact_low_rank_tt():
+    """A TT of ranks r written redundantly (X + X - X, ranks 3r): a sketch of
+    ranks >= r spans the exact column spaces with probability one, so the
+    randomized rounding returns the same tensor (App. A.3)."""
+    modes, ranks = [5, 6, 4, 7], [2, 3, 2]
+    A = workloads.random_tt(modes, ranks, seed=11)
+    X = tt.add(tt.add(A, A), tt.scale(A, -1.0))
+    for sketch in ([2, 3, 2], [4, 5, 3]):
+        Z = round_randomized(X, _omega(modes, sketch, 12))
+        assert tt.ranks(Z) == sketch
+        F = tt.full(A)
+        assert np.abs(tt.full(Z) - F).max() <= 1e-12 * np.abs(F).max()
+
+
+def test_randomized_rounding_error_near_optimal_with_oversampling():
+    """For a tensor with decaying unfolding spectra the randomized projection
+    at sketch rank r + p stays within a small factor of the best rank-r + p
+    truncation's error (TT-SVD at the same ranks), and left cores are
+    orthonormal."""
+    modes = [8, 7, 6, 5]
+    rng = np.random.default_rng(5)
+    cores = [rng.standard_normal((1 if k == 0 else 6, m, 1 if k == 3 else 6)) * np.geomspace(1, 1e-3, 6)[None, None, :]
+             if k < 3 else rng.standard_normal((6, m, 1)) for k, m in enumerate(modes)]
+    F = tt.full(cores)
+    sk = [4, 4, 4]
+    Z = round_randomized(cores, _omega(modes, sk, 6))
+    T, _ = round_ttsvd(cores, forced=sk)
+    e_rand = np.linalg.norm(tt.full(Z) - F)
+    e_opt = np.linalg.norm(tt.full(T) - F)
+    assert e_rand <= 20 * e_opt + 1e-14 * np.linalg.norm(F), (e_rand, e_opt)
+    for G in Z[:-1]:
+        M = G.reshape(-1, G.shape[2])
+        assert np.abs(M.T @ M - np.eye(M.shape[1])).max() <= 1e-12
+
+
+def test_sketch_right_equals_full_contraction():
+    """W_k of the backward sweep is the right unfolding of the tensor times the
+    random TT's right part, contracted over all modes after bond k."""
+    modes = [4, 3, 5, 2]
+    X = workloads.random_tt(modes, [2, 3, 2], seed=21)
+    Om = _omega(modes, [3, 2, 2], 22)
+    W = sketch_right(X, Om)
+    for k in range(3):
+        # reference: contract cores k+1..d of X and of Omega directly
+        Bx = X[k + 1]
+        Bo = Om[k + 1]
+        for j in range(k + 2, 4):
+            Bx = np.tensordot(Bx, X[j], axes=([Bx.ndim - 1], [0]))
+            Bo = np.tensordot(Bo, Om[j], axes=([Bo.ndim - 1], [0]))
+        ax = list(range(1, Bx.ndim))
+        ref = np.tensordot(Bx, Bo, axes=(ax, ax))
+        assert np.allclose(W[k], ref, rtol=1e-12, atol=1e-12)
