@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--no-split", action="store_true", help="skip the split-layout leg")
     ap.add_argument("--split-steps", type=int, default=5, help="timed steps of the 3D split-layout run")
     ap.add_argument("--no-fluxes", action="store_true", help="skip the Rusanov/HLL leg")
-    ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes"], default=None,
+    ap.add_argument("--no-schedule", action="store_true", help="skip the rounds-per-step leg")
+    ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes", "schedule"], default=None,
                     help="run only this companion leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
@@ -260,12 +261,15 @@ def run_ours(args, rank, world, local_rank):
     fluxes = None
     if not args.no_fluxes:
         fluxes = run_fluxes(args, torch, ttsn)
+    schedule = None
+    if not args.no_schedule:
+        schedule = run_schedule(args, torch, ttsn)
     beams = None
     if not args.no_beams:
         beams = run_beams(args, torch, ttsn, fp64_peak, mixed["bf16_peak"] if mixed else None)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
-               adjoint=adjoint, beams=beams, split=split, fluxes=fluxes)
+               adjoint=adjoint, beams=beams, split=split, fluxes=fluxes, schedule=schedule)
     return res
 
 
@@ -454,6 +458,32 @@ def _hohlraum_J(t, x, y, c=1.0):
             val = 0.5 - (np.pi - eta) * u / (2 * np.pi * ct) - np.arcsin(u * np.sin(eta) / r) / (2 * np.pi)
         return np.where(u < ct, val, 0.0)
     return part(x, y) + part(y, x)
+
+
+def run_schedule(args, torch, ttsn):
+    """Rounds per step (Sec. 4.2): the default single rounding after the source
+    stage against the paper's schedule of rounding after transport and again
+    after the source, on the 128^2 x (32 x 64) random-field problem (20
+    steps, eps 1e-6), each timed with CUDA events after an untimed run."""
+    p = workloads.grf_problem()
+    stream = torch.cuda.Stream()
+    out = {"workload": "2D 128^2, 32x64 ordinates, sigma_a = exp(GRF), vacuum, eps 1e-6, steps 1..%d" % p["steps"]}
+    E = {}
+    with torch.cuda.stream(stream):
+        for rounds in (1, 2):
+            ttsn.TTSN.from_problem(p, stream=stream, rounds_per_step=rounds).step(p["steps"])
+            g = ttsn.TTSN.from_problem(p, stream=stream, rounds_per_step=rounds)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = g.step(p["steps"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            E[rounds] = g.energy()[0]
+            out["rounds_%d" % rounds] = {"steps_per_s": p["steps"] / (ms * 1e-3), "ranks_last": info["ranks"][1:-1]}
+    out["E_max_rel_diff"] = float((E[2] - E[1]).abs().max() / E[1].abs().max())
+    return out
 
 
 def run_adjoint(args, torch, ttsn):
@@ -715,6 +745,8 @@ def main():
             out = run_split(args, torch, ttsn)
         elif args.only == "fluxes":
             out = run_fluxes(args, torch, ttsn)
+        elif args.only == "schedule":
+            out = run_schedule(args, torch, ttsn)
         else:
             out = run_batch(args, torch, ttsn)
         print(json.dumps({args.only: out}))
@@ -779,6 +811,8 @@ def main():
         line["split"] = res["split"]
     if res.get("fluxes") is not None:
         line["fluxes"] = res["fluxes"]
+    if res.get("schedule") is not None:
+        line["schedule"] = res["schedule"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

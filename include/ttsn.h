@@ -51,6 +51,7 @@ enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1, TT_BC_OUTFLOW = 2 };
 enum { TT_FP64 = 0, TT_MIXED = 1 };
 enum { TT_LAYOUT_GROUPED = 0, TT_LAYOUT_SPLIT = 1 };
 enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_HLL = 2 };
+enum { TT_ROUND_GRAM = 0, TT_ROUND_RANDOMIZED = 1 };
 
 /* step flags for tt_sn_step_ex */
 enum {
@@ -267,6 +268,24 @@ tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* r
  */
 tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, const double* theta_dev,
                         const double* phi_dev);
+
+/*
+ * tt_set_sketch: the Gaussian sketch TT of the randomized rounding (App. A.3):
+ * d device cores omega_dev[k] of shape (ranks_host[k], n_k, ranks_host[k+1])
+ * (ranks_host has d + 1 entries, the first and last 1), copied in; NULL
+ * removes it.  The caller draws the numbers (any Gaussian generator); a
+ * rounding to ranks l_k uses the cores' leading (l_{k-1}, n_k, l_k) blocks,
+ * so l_k <= ranks_host[k].
+ * tt_set_rounding: TT_ROUND_GRAM (default; the tolerance and cap rules of
+ * tt_round / steps) or TT_ROUND_RANDOMIZED for the following roundings of the
+ * handle (steps and tt_round): for every bond W = B^T Omega (backward sweep),
+ * then A' = Q, an orthonormal basis of A W, and M_upd = Q^T A (Eq.
+ * randfinal).  Its ranks are the forced ranks if a call gives them, else the
+ * sketch's ranks (both capped by the bond); eps and max_rank are not used.
+ * FP64 whatever the precision setting.  TT_ERR_STATE without a sketch.
+ */
+tt_status tt_set_sketch(tt_handle h, const double* const* omega_dev, const int* ranks_host);
+tt_status tt_set_rounding(tt_handle h, int method);
 
 /* tt_set_precision: TT_FP64 or TT_MIXED for the following roundings. */
 tt_status tt_set_precision(tt_handle h, int precision);

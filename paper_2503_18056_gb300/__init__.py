@@ -89,6 +89,21 @@ class _Handle:
         ptrs = (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
         check(lib.tt_set_cores(self._h, ptrs, _int_array(ranks)))
 
+    def set_sketch(self, cores):
+        """Gaussian sketch TT of the randomized rounding (tt_set_sketch); None removes it."""
+        if cores is None:
+            check(lib.tt_set_sketch(self._h, None, None))
+            return
+        ts = [_dev(c) for c in cores]
+        ranks = [1] + [int(t.shape[2]) for t in ts[:-1]] + [1]
+        ptrs = (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+        check(lib.tt_set_sketch(self._h, ptrs, _int_array(ranks)))
+
+    def set_rounding(self, method):
+        """'gram' (default) or 'randomized' for the following roundings (tt_set_rounding)."""
+        m = {"gram": _native.TT_ROUND_GRAM, "randomized": _native.TT_ROUND_RANDOMIZED}[method]
+        check(lib.tt_set_rounding(self._h, m))
+
     def full(self):
         d, n = self.dims()
         out = torch.empty(n, dtype=torch.float64, device="cuda")

@@ -19,6 +19,7 @@ TT_BC_PERIODIC, TT_BC_VACUUM, TT_BC_OUTFLOW = 0, 1, 2
 TT_FP64, TT_MIXED = 0, 1
 TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT = 0, 1
 TT_FLUX_UPWIND, TT_FLUX_RUSANOV, TT_FLUX_HLL = 0, 1, 2
+TT_ROUND_GRAM, TT_ROUND_RANDOMIZED = 0, 1
 TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
 
 
@@ -99,6 +100,8 @@ def _load():
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
         "tt_pchol": [i, vp, i, vp, vp, ip],
         "tt_set_inflow": [vp, i, i, vp, vp, vp],
+        "tt_set_sketch": [vp, ctypes.POINTER(vp), ip],
+        "tt_set_rounding": [vp, i],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_longlong), dp, dp],
@@ -138,7 +141,8 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_bench_bf16_mma", "tt_batch_create", "tt_batch_step", "tt_batch_size",
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
             "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
-            "tt_create_ex", "tt_get_cores", "tt_pchol", "tt_set_inflow"]
+            "tt_create_ex", "tt_get_cores", "tt_pchol", "tt_set_inflow", "tt_set_sketch",
+            "tt_set_rounding"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

@@ -218,6 +218,13 @@ struct tt_ctx {
         std::vector<double> th, ph;
     } inflow[3][2];
     std::vector<double> h_tfac, h_pfac;  // host copies of the angular factor tables
+    // randomized rounding (App. A.3): the caller's Gaussian sketch TT (cores
+    // (L_{k-1}, n_k, L_k)), its leading blocks at a rounding's target ranks,
+    // the right sketches W_k and the orthonormalisation workspace
+    int round_method = TT_ROUND_GRAM;
+    DevBuf sketch[TT_MAX_D], sk_sub[TT_MAX_D], sk_W[TT_MAX_D], sk_Y, sk_Q, sk_G, sk_lam, sk_Vt, sk_Vs;
+    int sk_L[TT_MAX_D + 1] = {0};
+    bool has_sketch = false;
     // split-space layout (cores x[, y[, z]], theta, phi): per-term angular
     // factors (theta rows then phi rows, 1 + 2 ndim terms each), the uniform
     // absorption factor s, the spatial contractions F (nc x terms) and the
@@ -262,6 +269,9 @@ struct tt_ctx {
     ~tt_ctx() {
         if (stream) cudaStreamSynchronize(stream);
         for (int k = 0; k < TT_MAX_D; ++k) {
+            sketch[k].release();
+            sk_sub[k].release();
+            sk_W[k].release();
             core[k].release();
             gcore[k].release();
             GB[k].release();
@@ -271,7 +281,8 @@ struct tt_ctx {
         DevBuf* bufs[] = {&slscratch, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
-                          &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph};
+                          &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph,
+                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs};
         for (DevBuf* b : bufs) b->release();
         for (auto& ax : inflow)
             for (auto& face : ax) face.g.release();
@@ -383,8 +394,141 @@ tt_status zero_tt(tt_ctx* h, DevBuf* dst, int* rr) {
 
 // Algorithm 1 (App. A) with the Gram truncation.  Reads cores src[k] with ranks
 // R[0..d]; writes the rounded cores into dst (h->core) with ranks rr.
+// Orthonormal basis of the columns of Y (m x l, row-major) into Q (m x k, k <=
+// l): eigendecomposition of the Gram matrix Y^T Y, Q = Y V diag(lambda)^(-1/2)
+// on the eigenpairs above the floor l eps_mach lambda_max; returns k (host).
+tt_status eig_orthonormalise(tt_ctx* h, long m, int l, const double* Y, DevBuf& Q, int* k_out) {
+    cudaStream_t s = h->stream;
+    TT_TRY(h->sk_G.ensure((size_t)l * l, s));
+    TT_TRY(h->sk_lam.ensure((size_t)l, s));
+    TT_TRY(h->sk_Vt.ensure((size_t)l * l, s));
+    TT_TRY(h->sk_Vs.ensure((size_t)l * l, s));
+    TT_TRY(gram(s, (int)m, l, Y, l, h->sk_G.p, l, h->partials));
+    TT_TRY(syev(s, l, h->sk_G.p, l, h->sk_lam.p, h->sk_Vt.p, l, h->eig, h->d_int + HI_STATUS,
+                h->d_int + next_sweep_slot(h)));
+    count_above_floor(s, h->sk_lam.p, l, h->d_int + HI_DEC);
+    TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_DEC, h->d_int + HI_DEC, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    const int k = h->h_int[HI_DEC];
+    *k_out = k;
+    if (k == 0) return TT_OK;
+    scale_rows(s, k, l, h->sk_Vt.p, l, h->sk_lam.p, 2, h->sk_Vs.p, l);  // rows v_j / sqrt(lambda_j)
+    TT_TRY(Q.ensure((size_t)m * k, s));
+    TT_TRY(dgemm(s, false, true, (int)m, k, l, 1.0, Y, l, h->sk_Vs.p, l, 0.0, Q.p, k));
+    return TT_OK;
+}
+
+// Randomized rounding (App. A.3): backward sweep W_b = B_b^T Omega (the right
+// part of bond b contracted with the sketch's leading blocks), then per bond
+// A' = Q with Q an orthonormal basis of A W_b (eig-based Cholesky-QR applied
+// twice, so that the basis is orthonormal to rounding for condition numbers
+// up to ~1/sqrt(eps_mach)), M_upd = Q^T A, next core = M_upd x_1 G_{b+1}.
+// Target ranks: forced[b] if given, else the sketch's rank, capped by both.
+tt_status round_randomized(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr,
+                           const int* forced, tt_step_info* info) {
+    cudaStream_t s = h->stream;
+    const int d = h->d;
+    const int* n = h->n;
+    if (!h->has_sketch) return fail(TT_ERR_STATE, "randomized rounding: no sketch set (tt_set_sketch)");
+    h->sweeps_slot = 0;
+    TT_CUDA_TRY(cudaMemsetAsync(h->d_int + HI_SWEEPS, 0, (HI_N - HI_SWEEPS) * sizeof(int), s));
+    if (info) {
+        info->d = d;
+        for (int k = 0; k <= d; ++k) info->grown[k] = R[k];
+        info->capped = 0;
+        info->norm = 0.0;
+        for (int k = 0; k < TT_MAX_D; ++k) info->discarded[k] = 0.0;
+    }
+    int l[TT_MAX_D + 1];
+    l[0] = l[d] = 1;
+    for (int b = 0; b < d - 1; ++b) {
+        int t = forced ? forced[b] : h->sk_L[b + 1];
+        l[b + 1] = std::max(1, std::min(t, std::min(h->sk_L[b + 1], R[b + 1])));
+    }
+    // leading blocks of the sketch cores at the target ranks
+    for (int k = 0; k < d; ++k) {
+        TT_TRY(h->sk_sub[k].ensure((size_t)l[k] * n[k] * l[k + 1], s));
+        copy2d(s, l[k] * n[k], l[k + 1], h->sketch[k].p, h->sk_L[k + 1], h->sk_sub[k].p, l[k + 1]);
+    }
+    {
+        double fl = 2.0 * R[d - 1] * (double)n[d - 1] * l[d - 1];
+        for (int c = d - 2; c >= 1; --c)
+            fl += 2.0 * R[c] * (double)n[c] * R[c + 1] * l[c + 1] + 2.0 * R[c] * (double)n[c] * l[c + 1] * l[c];
+        PhaseScope ps(h, TT_PH_GRAM_RIGHT, fl, 0.0);
+        TT_TRY(h->sk_W[d - 2].ensure((size_t)R[d - 1] * l[d - 1], s));
+        TT_TRY(dgemm_sk(s, false, true, R[d - 1], l[d - 1], n[d - 1], 1.0, src[d - 1].p, n[d - 1],
+                        h->sk_sub[d - 1].p, n[d - 1], h->sk_W[d - 2].p, l[d - 1], h->partials));
+        for (int c = d - 2; c >= 1; --c) {
+            // T = G_c W_c (R_c n_c x l_{c+1}); W_{c-1} = T (R_c x n_c l_{c+1}) Omega_c^T
+            TT_TRY(h->bwd.ensure((size_t)R[c] * n[c] * l[c + 1], s));
+            TT_TRY(dgemm(s, false, false, R[c] * n[c], l[c + 1], R[c + 1], 1.0, src[c].p, R[c + 1],
+                         h->sk_W[c].p, l[c + 1], 0.0, h->bwd.p, l[c + 1]));
+            TT_TRY(h->sk_W[c - 1].ensure((size_t)R[c] * l[c], s));
+            TT_TRY(dgemm_sk(s, false, true, R[c], l[c], n[c] * l[c + 1], 1.0, h->bwd.p, (long)n[c] * l[c + 1],
+                            h->sk_sub[c].p, (long)n[c] * l[c + 1], h->sk_W[c - 1].p, l[c], h->partials));
+        }
+    }
+    rr[0] = 1;
+    const double* A = src[0].p;
+    int rprev = 1, tmp_idx = 0;
+    for (int b = 0; b <= d - 2; ++b) {
+        const int Rk = R[b + 1], lb = l[b + 1];
+        const long m = (long)rprev * n[b];
+        // sketch Y = A W_b and its orthonormal basis
+        TT_TRY(h->sk_Y.ensure((size_t)m * lb, s));
+        {
+            PhaseScope ps(h, TT_PH_GRAM_LEFT, 2.0 * m * (double)Rk * lb + 2.0 * m * (double)lb * lb, 0.0);
+            TT_TRY(dgemm(s, false, false, (int)m, lb, Rk, 1.0, A, Rk, h->sk_W[b].p, lb, 0.0, h->sk_Y.p, lb));
+        }
+        int k1 = 0, k2 = 0;
+        {
+            PhaseScope ps(h, TT_PH_EIG, 4.0 * m * (double)lb * lb, 0.0);
+            TT_TRY(eig_orthonormalise(h, m, lb, h->sk_Y.p, h->sk_Q, &k1));
+            if (k1 == 0) return zero_tt(h, dst, rr);
+            TT_TRY(eig_orthonormalise(h, m, k1, h->sk_Q.p, dst[b], &k2));
+            if (k2 == 0) return zero_tt(h, dst, rr);
+        }
+        const int rk = k2;
+        const long ncols = (long)n[b + 1] * R[b + 2];
+        double* next;
+        if (b == d - 2) {
+            TT_TRY(dst[d - 1].ensure((size_t)rk * ncols, s));
+            next = dst[d - 1].p;
+        } else {
+            TT_TRY(h->tmp[tmp_idx].ensure((size_t)rk * ncols, s));
+            next = h->tmp[tmp_idx].p;
+            tmp_idx ^= 1;
+        }
+        {
+            PhaseScope ps(h, TT_PH_UPDATE, 2.0 * m * (double)rk * Rk + 2.0 * rk * (double)Rk * ncols, 0.0);
+            // M_upd = Q^T A (rk x Rk), then the next core M_upd x_1 G_{b+1}
+            TT_TRY(h->Mupd.ensure((size_t)rk * Rk, s));
+            TT_TRY(dgemm_sk(s, true, false, rk, Rk, (int)m, 1.0, dst[b].p, rk, A, Rk, h->Mupd.p, Rk,
+                            h->partials));
+            TT_TRY(dgemm_sk(s, false, false, rk, (int)ncols, Rk, 1.0, h->Mupd.p, Rk, src[b + 1].p, ncols,
+                            next, ncols, h->partials));
+        }
+        rr[b + 1] = rk;
+        A = next;
+        rprev = rk;
+    }
+    rr[d] = 1;
+    if (info) {
+        const int nslots = std::min(h->sweeps_slot, HI_N - HI_SWEEPS);
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_SWEEPS, h->d_int + HI_SWEEPS, nslots * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+        int mx = 0;
+        for (int i = 0; i < nslots; ++i) mx = std::max(mx, h->h_int[HI_SWEEPS + i]);
+        info->sweeps = mx;
+    }
+    return TT_OK;
+}
+
 tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr, double eps,
                       int max_rank, const int* forced, tt_step_info* info) {
+    if (h->round_method == TT_ROUND_RANDOMIZED && h->d > 1)
+        return round_randomized(h, src, R, dst, rr, forced, info);
     cudaStream_t s = h->stream;
     const int d = h->d;
     const int* n = h->n;
@@ -1499,7 +1643,8 @@ tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
     AllocScope alloc_scope_(h->alloc_ptr());
     if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
     if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0 ||
-        h->split() || h->fields.flux != TT_FLUX_UPWIND || h->grid.bc[0] == TT_BC_OUTFLOW ||
+        h->split() || h->round_method != TT_ROUND_GRAM || h->fields.flux != TT_FLUX_UPWIND ||
+        h->grid.bc[0] == TT_BC_OUTFLOW ||
         h->grid.bc[1] == TT_BC_OUTFLOW || h->grid.bc[2] == TT_BC_OUTFLOW)
         return fail(TT_ERR_STATE, "tt_tape_begin: the adjoint form needs the grouped layout, "
                                   "upwinding, periodic or vacuum faces, FP64 precision, one rounding "
@@ -1842,6 +1987,47 @@ tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, co
         face.on = true;
     }
     return rebuild_sources(h);
+}
+
+tt_status tt_set_sketch(tt_handle h, const double* const* omega_dev, const int* ranks_host) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    AllocScope alloc_scope_(h->alloc_ptr());
+    if (!omega_dev) {
+        h->has_sketch = false;
+        if (h->round_method == TT_ROUND_RANDOMIZED) h->round_method = TT_ROUND_GRAM;
+        return TT_OK;
+    }
+    if (!ranks_host) return fail(TT_ERR_ARG, "tt_set_sketch: null ranks");
+    const int d = h->d;
+    if (ranks_host[0] != 1 || ranks_host[d] != 1) return fail(TT_ERR_ARG, "tt_set_sketch: end ranks must be 1");
+    for (int k = 1; k < d; ++k)
+        if (ranks_host[k] < 1) return fail(TT_ERR_ARG, "tt_set_sketch: ranks must be >= 1");
+    for (int k = 0; k < d; ++k)
+        if (!omega_dev[k]) return fail(TT_ERR_ARG, "tt_set_sketch: null core");
+    cudaStream_t s = h->stream;
+    for (int k = 0; k < d; ++k) {
+        const size_t len = (size_t)ranks_host[k] * h->n[k] * ranks_host[k + 1];
+        TT_TRY(h->sketch[k].ensure(len, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(h->sketch[k].p, omega_dev[k], len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    for (int k = 0; k <= d; ++k) h->sk_L[k] = ranks_host[k];
+    TT_CUDA_TRY(cudaStreamSynchronize(s));
+    h->has_sketch = true;
+    return TT_OK;
+}
+
+tt_status tt_set_rounding(tt_handle h, int method) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (method != TT_ROUND_GRAM && method != TT_ROUND_RANDOMIZED)
+        return fail(TT_ERR_ARG, "tt_set_rounding: method must be TT_ROUND_GRAM or TT_ROUND_RANDOMIZED");
+    if (method == TT_ROUND_RANDOMIZED && !h->has_sketch)
+        return fail(TT_ERR_STATE, "tt_set_rounding: the randomized rounding needs a sketch (tt_set_sketch)");
+    if (method == TT_ROUND_RANDOMIZED && (h->taping || h->replay_rec))
+        return fail(TT_ERR_STATE, "tt_set_rounding: the adjoint tape records Gram-SVD roundings");
+    h->round_method = method;
+    return TT_OK;
 }
 
 tt_status tt_set_precision(tt_handle h, int precision) {
