@@ -46,6 +46,7 @@ import workloads  # noqa: E402
 METRIC = "TT-SN steps/s (equiv. cell·ordinate updates/s), mixed vs FP64 at stated err"
 DEFAULT_STEPS = 12
 DEFAULT_WARMUP = 3
+OVERSAMPLE = 8  # extra sketch columns of the randomized-rounding companion run
 
 
 def parse():
@@ -68,6 +69,7 @@ def parse():
     ap.add_argument("--split-steps", type=int, default=5, help="timed steps of the 3D split-layout run")
     ap.add_argument("--no-fluxes", action="store_true", help="skip the Rusanov/HLL leg")
     ap.add_argument("--no-schedule", action="store_true", help="skip the rounds-per-step leg")
+    ap.add_argument("--no-randomized", action="store_true", help="skip the randomized-rounding companion run")
     ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes", "schedule"], default=None,
                     help="run only this companion leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
@@ -226,6 +228,44 @@ def run_ours(args, rank, world, local_rank):
             del gm
             torch.cuda.synchronize()
 
+        # randomized rounding (App. A.3) on the same steps at the FP64 run's
+        # ranks, with a Gaussian sketch at the rank cap drawn on the device
+        randomized = None
+        if not args.no_randomized:
+            E64, T64 = E.clone(), T.clone()
+            gr = ttsn.TTSN.from_problem(p, max_rank=p.get("max_rank", 0), stream=stream)
+            d_, n_ = gr.dims()
+            cap = (p.get("max_rank") or 128) + OVERSAMPLE
+            sk = [1] + [min(cap, int(np.prod(n_[:k + 1])), int(np.prod(n_[k + 1:]))) for k in range(d_ - 1)] + [1]
+            r_over = [[min(r + OVERSAMPLE, sk[b + 1]) for b, r in enumerate(rk)] for rk in ranks_hist]
+            gen = torch.Generator(device=dev).manual_seed(1234)
+            omega = [torch.randn((sk[k], n_[k], sk[k + 1]), dtype=torch.float64, device=dev, generator=gen)
+                     for k in range(d_)]
+            gr.set_sketch(omega)
+            del omega
+            gr.set_rounding("randomized")
+            for k in range(args.warmup):
+                gr.step(forced=r_over[k])
+            gr.set_cores(init_cores)
+            gr.set_T(T0)
+            torch.cuda.synchronize()
+            gr.profile(True)
+            evr = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            evr[0].record(stream)
+            for k in range(args.steps):
+                gr.step(forced=r_over[k])
+                evr[k + 1].record(stream)
+            torch.cuda.synchronize()
+            rprof = gr.profile_read()
+            gr.profile(False)
+            Er, Tr, _ = gr.energy()
+            r_ms = evr[0].elapsed_time(evr[args.steps])
+            randomized = dict(total_ms=r_ms, prof=rprof,
+                              err_E=((Er - E64).abs().max() / E64.abs().max()).item(),
+                              err_T=((Tr - T64).abs().max() / T64.abs().max()).item())
+            del gr
+            torch.cuda.synchronize()
+
         # end to end through the public API: the state lives on the host between
         # steps (pinned), copied in before and out after every step
         e2e = None
@@ -269,7 +309,8 @@ def run_ours(args, rank, world, local_rank):
         beams = run_beams(args, torch, ttsn, fp64_peak, mixed["bf16_peak"] if mixed else None)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
-               adjoint=adjoint, beams=beams, split=split, fluxes=fluxes, schedule=schedule)
+               adjoint=adjoint, beams=beams, split=split, fluxes=fluxes, schedule=schedule,
+               randomized=randomized)
     return res
 
 
@@ -801,6 +842,16 @@ def main():
             "step_ms": [round(x, 3) for x in mx["step_ms"]],
             "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in mx["prof"].items()},
             "clocks": mx.get("clocks"), "roofline": mroof}
+    rz = res.get("randomized")
+    if rz is not None:
+        rv = world * steps / (rz["total_ms"] * 1e-3)
+        line["randomized"] = {
+            "value": rv, "unit": "steps/s", "speedup_vs_fp64_gram": rv / value,
+            "ranks": "the FP64 Gram-SVD run's ranks + %d (oversampled sketch, forced), steps 1..%d" % (OVERSAMPLE, steps),
+            "sketch": "Gaussian TT at the rank cap + %d (torch.randn, seed 1234), leading blocks at each step's ranks"
+                      % OVERSAMPLE,
+            "err_vs_fp64_gram": {"E_max_rel": rz["err_E"], "T_max_rel": rz["err_T"]},
+            "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in rz["prof"].items()}}
     if res.get("batched") is not None:
         line["batched"] = res["batched"]
     if res.get("adjoint") is not None:
