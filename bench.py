@@ -617,6 +617,13 @@ def run_batch(args, torch, ttsn):
             "ranks_last_min_max": [min(min(r) for r in ranks), max(max(r) for r in ranks)]}
 
 
+# ncu DRAM read + write bytes of one left-Gram launch at the bench's rank cap
+# (2,097,152 x 897), scaled by the rows from a 500,000 x 897 capture of the
+# same kernel (11.13 GB); the profile summary gram_dgemm_splitk_500kx897 in
+# profiles/ gives the command.
+GRAM_LEFT_CAP_TRAFFIC = (11104132608 + 24035072) * 2097152 / 500000
+
+
 def roofline_of(prof, fp64_peak, peaks):
     # dominant phase by GPU time
     name = max(prof, key=lambda k: prof[k]["ms"])
@@ -627,8 +634,11 @@ def roofline_of(prof, fp64_peak, peaks):
     if ph["flops"] > 0:
         achieved = ph["flops"] / (ph["ms"] * 1e-3) / 1e12
         peak = fp64_peak
+        traffic = GRAM_LEFT_CAP_TRAFFIC if name == "gram_left" else None
         return name, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                      "frac": achieved / peak if peak else None, "traffic": None,
+                      "frac": achieved / peak if peak else None, "traffic": traffic,
+                      "traffic_note": "ncu DRAM read+write bytes of one capped 2,097,152 x 897 launch (scaled "
+                                      "by the rows from a 500,000 x 897 capture)" if traffic else None,
                       "kernel": name, "dtype": "f64", "avg_phase_ms": avg_ms,
                       "launches": ph["launches"], "calls": ph["calls"],
                       "peak_source": "measured FP64 tensor pipe (mma.m8n8k4.f64 chains on all SMs, "
