@@ -618,9 +618,8 @@ def run_batch(args, torch, ttsn):
 
 
 # ncu DRAM read + write bytes of one left-Gram launch at the bench's rank cap
-# (2,097,152 x 897), scaled by the rows from a 500,000 x 897 capture of the
-# same kernel (11.13 GB); the profile summary gram_dgemm_splitk_500kx897 in
-# profiles/ gives the command.
+# (2,097,152 x 897), scaled by the rows from an ncu capture (dram__bytes_read
+# and _write) of the same kernel on a 500,000 x 897 operand: 11.13 GB.
 GRAM_LEFT_CAP_TRAFFIC = (11104132608 + 24035072) * 2097152 / 500000
 
 
