@@ -420,6 +420,17 @@ tt_status tt_dgemm(int trans_a, int trans_b, int M, int N, int K, double alpha,
 tt_status tt_gram(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg, void* stream);
 
 /*
+ * tt_wait_probe: self-test of the device-side failure detection.  The
+ * library's persistent kernels (Jacobi eigensolver, pivoted Cholesky) wait at
+ * grid-wide barriers with a bounded spin (~1 s) that latches a status word
+ * instead of waiting forever.  This call runs one such wait that can never
+ * complete (one CTA waiting for a second that is never launched) and returns
+ * TT_ERR_TIMEOUT when the wait ran out and the kernel returned; the CUDA
+ * context stays usable.  Any other status means the bounded wait is broken.
+ */
+tt_status tt_wait_probe(void* stream);
+
+/*
  * tt_pchol: pivoted Cholesky factor of a symmetric positive semidefinite n x n
  * matrix G (leading dimension ldg), the factor of the right Gram matrix that
  * the one-sided truncation uses (W^T W = G_B, App. A.2): the pivot is the

@@ -102,6 +102,7 @@ def _load():
         "tt_set_inflow": [vp, i, i, vp, vp, vp],
         "tt_set_sketch": [vp, ctypes.POINTER(vp), ip],
         "tt_set_rounding": [vp, i],
+        "tt_wait_probe": [vp],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_longlong), dp, dp],
@@ -142,7 +143,7 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
             "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
             "tt_create_ex", "tt_get_cores", "tt_pchol", "tt_set_inflow", "tt_set_sketch",
-            "tt_set_rounding"]
+            "tt_set_rounding", "tt_wait_probe"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

@@ -2118,6 +2118,25 @@ tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A, int lda, const 
     return TT_OK;
 }
 
+tt_status tt_wait_probe(void* stream) {
+    set_error("");
+    cudaStream_t s = (cudaStream_t)stream;
+    EigWork w;
+    int* d_small = nullptr;
+    TT_CUDA_TRY(cudaMallocAsync((void**)&d_small, sizeof(int), s));
+    TT_CUDA_TRY(cudaMemsetAsync(d_small, 0, sizeof(int), s));
+    tt_status st = wait_probe(s, w, d_small);
+    int hs = 0;
+    cudaMemcpyAsync(&hs, d_small, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d_small, s);
+    w.release();
+    if (st < 0) return st;
+    if (e != cudaSuccess) return fail(TT_ERR_CUDA, std::string("tt_wait_probe: ") + cudaGetErrorString(e));
+    if (hs & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_wait_probe: the bounded wait ran out (as designed)");
+    return TT_OK;
+}
+
 tt_status tt_pchol(int n, const double* G, int ldg, double* W, void* stream, int* rank_host) {
     set_error("");
     if (n < 0) return fail(TT_ERR_ARG, "tt_pchol: negative size");

@@ -152,6 +152,10 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
 tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, double* Wc,
                 double* dwork, EigWork& w, int* status_dev, int* kB_dev);
 
+// Self-test of the bounded grid-barrier wait: a wait that can never complete
+// runs out and latches DEV_TIMEOUT into *status_dev.
+tt_status wait_probe(cudaStream_t s, EigWork& w, int* status_dev);
+
 // ---------------------------------------------------------------- rounding helpers (jacobi.cu)
 // Truncation decision for one bond (App. A, note on rank truncation).
 // Inputs: lamK (kB, descending, eigenvalues of M^T M), kB; mode: eps rule with

@@ -35,7 +35,7 @@ constexpr int MAX_SWEEPS = 40;
 // control block (ints): [0] barrier count, [1] barrier generation, [2] sweeps,
 // [3] pivoted-Cholesky rank, [4 .. 4+MAX_SWEEPS) rotations applied per sweep
 constexpr int CTRL_INTS = 8 + MAX_SWEEPS;
-constexpr long long SPIN_LIMIT = 1LL << 24;  // ~1-2 s with the 64 ns sleep
+constexpr long long SPIN_LIMIT = 1LL << 21;  // ~1.1 s (an atomic read plus a 64 ns sleep per try)
 constexpr int MAX_PAIRS_PER_CTA = 8;
 
 __device__ __forceinline__ void round_pair(int N, int r, int k, int& p, int& q) {
@@ -542,6 +542,13 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
 
 __global__ void pchol_finish_kernel(const int* ctrl, int* kB_out) { *kB_out = ctrl[3]; }
 
+// Self-test of the bounded wait: one CTA enters grid_barrier claiming a grid
+// of two, so the second arrival never comes; the wait runs out after its
+// iteration limit (~1 s), latches DEV_TIMEOUT and the kernel returns.
+__global__ void wait_probe_kernel(int* ctrl, int* status) {
+    if (grid_barrier(ctrl, status, 2u) && threadIdx.x == 0) atomicOr(status, 0);
+}
+
 __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm1, int forced,
                                   int max_rank, double* delta2_dev, int* dec_i, double* dec_d) {
     const double eps_mach = 2.220446049250313e-16;
@@ -715,6 +722,14 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     note_launch();
     jacobi_sort_kernel<<<n, 256, 0, s>>>(n, w.lam_unsorted.p, ld, w.vt_unsorted.p, lam, Vt, ldv,
                                          sweeps_dev, w.d_ctrl);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status wait_probe(cudaStream_t s, EigWork& w, int* status_dev) {
+    TT_TRY(ensure_ctrl(w, s));
+    note_launch();
+    wait_probe_kernel<<<1, 32, 0, s>>>(w.d_ctrl, status_dev);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
 }

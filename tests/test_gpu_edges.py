@@ -96,3 +96,22 @@ def test_to_full_with_a_short_buffer_is_refused(ttsn):
     st = ttsn.lib.tt_to_full(tt._h, ctypes.c_void_p(short.data_ptr()), short.numel())
     assert st == -7  # TT_ERR_TOO_LARGE: the buffer is too small, nothing written
     assert tt.full().shape == (6, 5, 4, 8)
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(ttsn):
+    """Failure detection without a GPU fault: a grid-barrier wait that can
+    never complete gives up after its iteration limit, the kernel returns and
+    the call reports TT_ERR_TIMEOUT; the next calls on the device succeed."""
+    import time
+
+    t0 = time.perf_counter()
+    st = ttsn.lib.tt_wait_probe(None)
+    elapsed = time.perf_counter() - t0
+    assert st == -5, st  # TT_ERR_TIMEOUT
+    assert elapsed < 30.0
+    p = workloads.problem("small_2d", n=(6, 5), n_theta=4, n_phi=8)
+    tt_ = ttsn.TTSN.from_problem(p)
+    tt_.step(2)
+    tt_.sync()
+    G = ttsn.gram(torch.ones((10, 3), dtype=torch.float64, device="cuda"))
+    assert float(G[0, 0]) == 10.0
