@@ -208,6 +208,22 @@ __device__ __forceinline__ void stencil_coefs(const Fields& f, int ndim, long i,
 // Row value of the transport terms of cell i at column col (Sec. 4.3 with the
 // ghost rows of Sec. 4.5): the quadrature dot product with thbar over all
 // term blocks.
+// The two terms of axis a at one column: upwinding (GEN = false) takes the
+// plain differences x0 - xm and xp - x0 (fewer FP64 operations, the common
+// case); other fluxes the face-weighted stencil.
+template <bool GEN>
+__device__ __forceinline__ void axis_terms(const double (&co)[3][2][3], int a, double x0, double xm,
+                                           double xp, double& t1, double& t2) {
+    if (GEN) {
+        t1 = co[a][0][0] * x0 + co[a][0][1] * xp - co[a][0][2] * xm;
+        t2 = co[a][1][0] * x0 + co[a][1][1] * xp - co[a][1][2] * xm;
+    } else {
+        t1 = x0 - xm;
+        t2 = xp - x0;
+    }
+}
+
+template <bool GEN>
 __device__ __forceinline__ double transport_dot(const Grid& g, const double* nu, const long (&nb)[3][2],
                                                 const double (&co)[3][2][3], int transport, int r1,
                                                 const double* X, long ldx, long i, int col,
@@ -218,10 +234,10 @@ __device__ __forceinline__ double transport_dot(const Grid& g, const double* nu,
         for (int a = 0; a < g.ndim; ++a) {
             const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
             const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-            dot += -nu[a] * (co[a][0][0] * x0 + co[a][0][1] * xp - co[a][0][2] * xm) *
-                   thbar[(1 + 2 * a) * r1 + col];
-            dot += -nu[a] * (co[a][1][0] * x0 + co[a][1][1] * xp - co[a][1][2] * xm) *
-                   thbar[(2 + 2 * a) * r1 + col];
+            double t1, t2;
+            axis_terms<GEN>(co, a, x0, xm, xp, t1, t2);
+            dot += -nu[a] * t1 * thbar[(1 + 2 * a) * r1 + col];
+            dot += -nu[a] * t2 * thbar[(2 + 2 * a) * r1 + col];
         }
     return dot;
 }
@@ -232,6 +248,7 @@ __device__ __forceinline__ double transport_dot(const Grid& g, const double* nu,
 // cell, so the per-cell scalar FP64 work is done once, not once per lane.
 // Pass 2: for each cell the lanes write the scaled row, the external-source
 // columns and the emission column (scale and emission broadcast by shuffle).
+template <bool GEN>
 __global__ void __launch_bounds__(256)
 transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                         const double* __restrict__ X, long ldx, const double* __restrict__ thbar,
@@ -252,10 +269,10 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                 long nb[3][2];
                 cell_neighbours(g, i, nb);
                 double co[3][2][3];
-                stencil_coefs(f, g.ndim, i, co);
+                if (GEN) stencil_coefs(f, g.ndim, i, co);
                 double dot = 0.0;
                 for (int col = lane; col < r1; col += 32)
-                    dot += transport_dot(g, nu, nb, co, transport, r1, X, ldx, i, col, thbar);
+                    dot += transport_dot<GEN>(g, nu, nb, co, transport, r1, X, ldx, i, col, thbar);
                 // external sources: c dt x_k[i] times their quadrature q_k
                 for (int k = lane; k < ext.n; k += 32)
                     dot += f.c * f.dt * ext.x[(long)k * g.nc + i] * ext.q[k];
@@ -284,7 +301,7 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
             long nb[3][2];
             cell_neighbours(g, i, nb);
             double co[3][2][3];
-            stencil_coefs(f, g.ndim, i, co);
+            if (GEN) stencil_coefs(f, g.ndim, i, co);
             double* out = Xg + i * ldg;
             for (int col = lane; col < r1; col += 32) {
                 const double x0 = X[i * ldx + col];
@@ -293,10 +310,10 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                     for (int a = 0; a < g.ndim; ++a) {
                         const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
                         const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-                        out[(1 + 2 * a) * r1 + col] =
-                            sc * (-nu[a] * (co[a][0][0] * x0 + co[a][0][1] * xp - co[a][0][2] * xm));
-                        out[(2 + 2 * a) * r1 + col] =
-                            sc * (-nu[a] * (co[a][1][0] * x0 + co[a][1][1] * xp - co[a][1][2] * xm));
+                        double t1, t2;
+                        axis_terms<GEN>(co, a, x0, xm, xp, t1, t2);
+                        out[(1 + 2 * a) * r1 + col] = sc * (-nu[a] * t1);
+                        out[(2 + 2 * a) * r1 + col] = sc * (-nu[a] * t2);
                     }
                 }
             }
@@ -824,8 +841,12 @@ void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool 
     const long warps_needed = (g.nc + G - 1) / G;
     const int blocks = (int)std::max<long>(1, std::min<long>((warps_needed + 7) / 8, 152L * 64));
     note_launch();
-    transport_source_kernel<<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1, X,
-                                                   ldx, thbar, ext, Xg, ldg, G);
+    if (f.flux == TT_FLUX_UPWIND)
+        transport_source_kernel<false><<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1,
+                                                              X, ldx, thbar, ext, Xg, ldg, G);
+    else
+        transport_source_kernel<true><<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1,
+                                                             X, ldx, thbar, ext, Xg, ldg, G);
 }
 
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
