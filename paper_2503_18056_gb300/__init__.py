@@ -6,6 +6,16 @@ apply, quadrature, quartic temperature solve, source assembly, Gram sweeps,
 Jacobi eigensolves, truncation and core updates) runs in the library's kernels.
 There is no CPU fallback: importing this package without the built library
 raises ImportError.
+
+``TTSN`` is one problem: grouped (three cores) or split (one core per spatial
+axis) layout, FP64 or the BF16-digit precision form, upwind / Rusanov / HLL
+fluxes, periodic / vacuum / outflow faces, inflow faces (``set_inflow``),
+fixed sources (``set_sources``), Gram-SVD or randomized rounding
+(``set_sketch``, ``set_rounding``), the adjoint tape (``tape_begin``,
+``escape_gradient``) and ``EscapeEnergy`` as a torch.autograd.Function.
+``TTSNBatch`` steps many independent problems together; ``TensorTrain`` is a
+bare TT for the rounding entry points; ``dgemm``, ``gram``, ``gram_mixed``,
+``gemm_nt_mixed``, ``syev`` and ``pchol`` expose the kernel-level calls.
 """
 import ctypes
 

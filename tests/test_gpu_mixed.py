@@ -10,7 +10,6 @@ import pytest
 
 import workloads
 from oracle import tt
-from oracle.ttstep import TTSN as OracleTTSN
 
 pytestmark = pytest.mark.gpu
 

@@ -4,7 +4,6 @@ objective's closed form for free streaming of one ordinate."""
 import numpy as np
 import pytest
 
-import workloads
 from oracle import angles
 from oracle.adjoint import escape_energy, escape_energy_and_gradient, face_weights, transport_T
 from oracle.dense import PERIODIC, VACUUM, DenseSN

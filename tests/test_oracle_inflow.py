@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import workloads
-from oracle import angles, tt
+from oracle import tt
 from oracle.dense import DenseSN
 from oracle.ttstep import VACUUM, TTSN
 
