@@ -307,6 +307,17 @@ class TTSN(_Handle):
         t = _dev(T, self.nc)
         check(lib.tt_set_T(self._h, ctypes.c_void_p(t.data_ptr())))
 
+    def state_dict(self):
+        """Checkpoint of the evolving state: the TT cores and the material
+        temperature (device copies; torch.save-able).  Fields, constants, the
+        flux, sources and inflow faces are the problem's and are not saved."""
+        return {"cores": [c.clone() for c in self.cores()], "T": self.energy()[1].clone()}
+
+    def load_state_dict(self, state):
+        """Resume from ``state_dict()``: the following steps continue bit for bit."""
+        self.set_cores(state["cores"])
+        self.set_T(state["T"])
+
     def full(self):
         return super().full().reshape(self.n + (self.n_theta, self.n_phi))
 

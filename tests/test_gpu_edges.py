@@ -115,3 +115,21 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable(ttsn):
     tt_.sync()
     G = ttsn.gram(torch.ones((10, 3), dtype=torch.float64, device="cuda"))
     assert float(G[0, 0]) == 10.0
+
+
+def test_checkpoint_and_resume_continue_bit_for_bit(ttsn, tmp_path):
+    """state_dict / load_state_dict (cores and T through tt_get_core,
+    tt_set_cores, tt_set_T), saved with torch.save: a handle resumed from the
+    checkpoint takes the same next steps as the original."""
+    p = workloads.problem("small_2d", n=(16, 12), n_theta=4, n_phi=8, eps=1e-6)
+    a = ttsn.TTSN.from_problem(p)
+    a.step(3)
+    path = tmp_path / "ckpt.pt"
+    torch.save(a.state_dict(), path)
+    a.step(2)
+    b = ttsn.TTSN.from_problem(p)
+    b.load_state_dict(torch.load(path))
+    b.step(2)
+    assert a.ranks() == b.ranks()
+    assert torch.equal(a.full(), b.full())
+    assert torch.equal(a.energy()[1], b.energy()[1])
