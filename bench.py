@@ -68,8 +68,11 @@ def parse():
     ap.add_argument("--split-steps", type=int, default=5, help="timed steps of the 3D split-layout run")
     ap.add_argument("--no-fluxes", action="store_true", help="skip the Rusanov/HLL leg")
     ap.add_argument("--no-schedule", action="store_true", help="skip the rounds-per-step leg")
+    ap.add_argument("--no-line-source", action="store_true", help="skip the line-source leg")
+    ap.add_argument("--line-source-steps", type=int, default=200,
+                    help="timed steps of the line-source leg (0: to t = 1, 568 steps)")
     ap.add_argument("--no-randomized", action="store_true", help="skip the randomized-rounding companion run")
-    ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes", "schedule"], default=None,
+    ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes", "schedule", "line_source"], default=None,
                     help="run only this companion leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0,
@@ -303,12 +306,15 @@ def run_ours(args, rank, world, local_rank):
     schedule = None
     if not args.no_schedule:
         schedule = run_schedule(args, torch, ttsn)
+    line_source = None
+    if not args.no_line_source:
+        line_source = run_line_source(args, torch, ttsn)
     beams = None
     if not args.no_beams:
         beams = run_beams(args, torch, ttsn, fp64_peak, mixed["bf16_peak"] if mixed else None)
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
-               adjoint=adjoint, beams=beams, split=split, fluxes=fluxes, schedule=schedule,
+               adjoint=adjoint, beams=beams, split=split, fluxes=fluxes, schedule=schedule, line_source=line_source,
                randomized=randomized)
     return res
 
@@ -498,6 +504,42 @@ def _hohlraum_J(t, x, y, c=1.0):
             val = 0.5 - (np.pi - eta) * u / (2 * np.pi * ct) - np.arcsin(u * np.sin(eta) / r) / (2 * np.pi)
         return np.where(u < ct, val, 0.0)
     return part(x, y) + part(y, x)
+
+
+def run_line_source(args, torch, ttsn):
+    """The line source of Sec. 5.4 at the paper's size: 500^2 cells on
+    [-1.1, 1.1]^2, 32 x 64 ordinates, Gaussian pulse (width 0.03, U0 = 1), no
+    material, vacuum, CFL 0.4, eps 1e-4, the first K_ls steps (to t = 1 with
+    --line-source-steps 0), timed with CUDA events after a short untimed run.
+    Reported beside the paper's figures: the ranks after 120 steps and at the
+    end, and the change of the radiation energy sum_i E_i dV relative to U0
+    (rounding moves energy between E and T; the front stays inside the
+    domain)."""
+    p = workloads.line_source()
+    steps = int(round(p["t_lim"] / p["dt"]))
+    if args.line_source_steps > 0:
+        steps = max(121, min(steps, args.line_source_steps))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ttsn.TTSN.from_problem(p, stream=stream).step(8)  # warm-up
+        g = ttsn.TTSN.from_problem(p, stream=stream)
+        _, _, (e_rad0, _) = g.energy()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info120 = g.step(120)
+        info = g.step(steps - 120)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        _, _, (e_rad, _) = g.energy()
+    v = steps / (ms * 1e-3)
+    return {"workload": "line source (Sec. 5.4): 2D 500^2 on [-1.1,1.1]^2, 32x64 ordinates, Gaussian pulse "
+                        "width 0.03, U0 1, sigma 0, vacuum, upwind, CFL 0.4, eps 1e-4, steps 1..%d (t = %.3g)"
+                        % (steps, steps * p["dt"]),
+            "steps_per_s": v, "updates_per_s": v * int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"],
+            "ms_per_step": ms / steps, "ranks_step_120": info120["ranks"][1:-1], "ranks_last": info["ranks"][1:-1],
+            "radiation_energy_change_over_U0": float(abs(e_rad - e_rad0) / p["U0"])}
 
 
 def run_schedule(args, torch, ttsn):
@@ -796,6 +838,8 @@ def main():
             out = run_fluxes(args, torch, ttsn)
         elif args.only == "schedule":
             out = run_schedule(args, torch, ttsn)
+        elif args.only == "line_source":
+            out = run_line_source(args, torch, ttsn)
         else:
             out = run_batch(args, torch, ttsn)
         print(json.dumps({args.only: out}))
@@ -872,6 +916,8 @@ def main():
         line["fluxes"] = res["fluxes"]
     if res.get("schedule") is not None:
         line["schedule"] = res["schedule"]
+    if res.get("line_source") is not None:
+        line["line_source"] = res["line_source"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_budget, res["step_ms"])
     s = json.dumps(line)

@@ -22,6 +22,9 @@ Modules (each function cites the passage of arXiv 2503.18056 it follows):
 * ``split``    -- the same step on the split-space layout (one core per
                   spatial axis, then theta and phi; Sec. 4.1, Sec. 7), with
                   the spatial fields s and e entering as TT-SVDs of the field.
+* ``adjoint``  -- the escape-energy gradient (reverse sweep of the dense step).
+* ``analytic`` -- analytic solutions of the validation problems of Sec. 5
+                  (hohlraum mean intensity, Gaussian line source).
 
 Every function here is pinned by ``-m "not gpu"`` tests against closed forms,
 invariants and brute force; none is "parity unpinned".

@@ -1,19 +1,14 @@
 """Inflow faces on the GPU (tt_set_inflow: a rank-one Dirichlet ghost
 intensity on a vacuum face, Sec. 4.5) and the hohlraum problem of Sec. 5.1."""
-import sys
-from pathlib import Path
-
 import numpy as np
 import pytest
 import torch
 
 import workloads
 from oracle import tt
+from oracle.analytic import hohlraum_J
 from oracle.dense import DenseSN
 from oracle.ttstep import PERIODIC, VACUUM, TTSN as OracleTTSN
-
-sys.path.insert(0, str(Path(__file__).parent))
-from test_oracle_inflow import hohlraum_J  # noqa: E402  (analytic J of Sec. 5.1)
 
 pytestmark = pytest.mark.gpu
 

@@ -6,6 +6,7 @@ import pytest
 
 import workloads
 from oracle import tt
+from oracle.analytic import hohlraum_J
 from oracle.dense import DenseSN
 from oracle.ttstep import VACUUM, TTSN
 
@@ -32,19 +33,6 @@ def test_untruncated_tt_step_with_inflow_equals_dense(n, flux, fk):
         t.step()
         d.step()
     assert np.abs(t.full() - d.I).max() <= 1e-12 * np.abs(d.I).max()
-
-
-def hohlraum_J(t, x, y, c=1.0):
-    """Analytic mean intensity of the hohlraum test (Sec. 5.1, after White
-    2023): isotropic I = J = 1 on the x = 0 and y = 0 faces of a vacuum domain."""
-    def part(u, v):
-        ct = c * t
-        with np.errstate(invalid="ignore", divide="ignore"):
-            eta = np.arccos(np.minimum(v / np.sqrt(np.maximum(ct ** 2 - u ** 2, 1e-300)), 1.0))
-            r = np.sqrt(u ** 2 + v ** 2)
-            val = 0.5 - (np.pi - eta) * u / (2 * np.pi * ct) - np.arcsin(u * np.sin(eta) / r) / (2 * np.pi)
-        return np.where(u < ct, val, 0.0)
-    return part(x, y) + part(y, x)
 
 
 def test_hohlraum_analytic_solution_special_values():

@@ -26,6 +26,10 @@ Workloads (unit box [0,1]^ndim, cell-centred, c = a_r = 1, C_v = 1):
 * ``hohlraum``    the 2D hohlraum of Sec. 5.1: [0, 2]^2, vacuum faces with
                   isotropic unit inflow on x = 0 and y = 0, no material,
                   empty start, to t = 0.75.
+* ``line_source`` the 2D line source of Sec. 5.4: [-1.1, 1.1]^2 (stored as
+                  [0, 2.2]^2 about its centre), 500^2 cells, a Gaussian pulse of
+                  radiation (width 0.03, total energy 1) in an empty vacuum
+                  domain, CFL 0.4, to t = 1.
 """
 import numpy as np
 
@@ -276,4 +280,24 @@ def hohlraum(n=(256, 256), n_theta=32, n_phi=64, eps=1e-4, max_rank=0, t_lim=0.7
              t_lim=t_lim)
     unit = (np.ones(nn), np.ones(n_theta), np.ones(n_phi))
     p["inflow"] = {(0, 0): unit, (1, 0): unit}
+    return p
+
+
+def line_source(n=(500, 500), n_theta=32, n_phi=64, eps=1e-4, max_rank=0, omega=0.03, U0=1.0,
+                half_width=1.1, t_lim=1.0, cfl=0.4):
+    """The 2D line source of Sec. 5.4: an isotropic Gaussian pulse of
+    radiation, E(0) = U0 / (2 pi omega^2) exp(-r^2 / (2 omega^2)) sampled at
+    the cell centres, about the centre of the square [-h, h]^2 (held as
+    [0, 2h]^2), no material (sigma = 0, so the source stage leaves I and T
+    unchanged), vacuum faces, given through the radiation temperature
+    Tr0 = E^(1/4) (a_r = 1).  The front reaches radius c t_lim < h, so no
+    radiation leaves by t_lim up to the scheme's numerical spreading."""
+    L = 2.0 * half_width
+    p = problem("small_2d", n=n, n_theta=n_theta, n_phi=n_phi, eps=eps, bc=VACUUM,
+                max_rank=max_rank, L=(L, L), cfl=cfl)
+    xc = cell_centres(p["n"], p["L"])
+    r = np.sqrt(sum((x - half_width) ** 2 for x in xc))
+    E0 = U0 / (2.0 * np.pi * omega ** 2) * np.exp(-r ** 2 / (2.0 * omega ** 2))
+    p.update(sigma_a=np.zeros(p["n"]), T0=np.full(p["n"], 1e-3), Tr0=E0 ** 0.25, name="line_source",
+             omega=omega, U0=U0, radius=r, t_lim=t_lim)
     return p
