@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--no-fluxes", action="store_true", help="skip the Rusanov/HLL leg")
     ap.add_argument("--no-schedule", action="store_true", help="skip the rounds-per-step leg")
     ap.add_argument("--no-line-source", action="store_true", help="skip the line-source leg")
-    ap.add_argument("--line-source-steps", type=int, default=200,
+    ap.add_argument("--line-source-steps", type=int, default=121,
                     help="timed steps of the line-source leg (0: to t = 1, 568 steps)")
     ap.add_argument("--no-randomized", action="store_true", help="skip the randomized-rounding companion run")
     ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes", "schedule", "line_source"], default=None,

@@ -26,7 +26,7 @@ from . import _native
 from ._native import (TT_BC_OUTFLOW, TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT,
                       TT_MIXED, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TTSNBatch", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
+__all__ = ["TTSN", "TTSNBatch", "TorchAllocator", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
            "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_BC_OUTFLOW", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
            "TT_STEP_NO_ROUND", "TT_LAYOUT_GROUPED", "TT_LAYOUT_SPLIT"]
 
@@ -162,19 +162,35 @@ class TensorTrain(_Handle):
         self.set_cores(ts)
 
 
-def _torch_allocator():
-    """A tt_allocator backed by torch's CUDA caching allocator: the handle's
-    buffers then count in torch.cuda.memory_allocated() and share torch's
-    cached blocks.  The callbacks run on the calling thread (ctypes takes the
-    GIL for them)."""
-    def alloc(ctx, nbytes, stream):
+class TorchAllocator:
+    """Device memory from torch's CUDA caching allocator: the handle's buffers
+    then count in torch.cuda.memory_allocated() and share torch's cached
+    blocks.  Any object with the same two methods can serve as a handle's
+    allocator; ``alloc`` returns 0 when it cannot serve a request, which the
+    library reports as TT_ERR_OOM."""
+
+    def alloc(self, nbytes, stream):
         try:
             return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return 0
+
+    def free(self, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def _c_allocator(obj):
+    """Wrap an object with alloc(nbytes, stream) -> pointer (0: refused) and
+    free(ptr, nbytes, stream) as a tt_allocator.  The callbacks run on the
+    calling thread (ctypes takes the GIL for them)."""
+    def alloc(ctx, nbytes, stream):
+        try:
+            return int(obj.alloc(int(nbytes), stream)) or None
         except Exception:
             return None
 
     def free(ctx, ptr, nbytes, stream):
-        torch.cuda.caching_allocator_delete(int(ptr))
+        obj.free(int(ptr), int(nbytes), stream)
 
     a = _native.Allocator()
     a.ctx = None
@@ -235,9 +251,11 @@ class TTSN(_Handle):
             desc.flux_param[0], desc.flux_param[1] = float(hll_beta), float(hll_tau_threshold)
         self._alloc = None
         if allocator == "torch":
-            self._alloc = _torch_allocator()
-        elif allocator is not None:
-            raise ValueError("allocator must be None or 'torch'")
+            allocator = TorchAllocator()
+        if allocator is not None:
+            if not (hasattr(allocator, "alloc") and hasattr(allocator, "free")):
+                raise ValueError("allocator must be None, 'torch' or an object with alloc() and free()")
+            self._alloc = _c_allocator(allocator)
         check(lib.tt_create_ex(ctypes.byref(desc), _stream_ptr(stream),
                                ctypes.byref(self._alloc) if self._alloc is not None else None,
                                ctypes.byref(self._h)))

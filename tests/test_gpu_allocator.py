@@ -1,6 +1,7 @@
 """Handles created with a caller-supplied device allocator (tt_create_ex):
 results identical to the default pool, the memory visibly drawn from and
-returned to torch's caching allocator; borrowed core views (tt_get_cores)."""
+returned to torch's caching allocator; borrowed core views (tt_get_cores);
+refused allocations reported as TT_ERR_OOM."""
 import gc
 
 import pytest
@@ -64,3 +65,51 @@ def test_borrowed_core_views_match_ranks(ttsn):
     # the views are the same memory the owned copies come from
     cores = g.cores()
     assert [tuple(c.shape) for c in cores] == [shape for _, shape in views]
+
+
+class _Budget:
+    """Torch's caching allocator behind a byte budget: requests beyond it are
+    refused (alloc returns 0), as a full device would refuse them."""
+
+    def __init__(self, limit):
+        self.limit, self.held, self.peak, self.unknown = limit, {}, 0, 0
+
+    def alloc(self, nbytes, stream):
+        if sum(self.held.values()) + nbytes > self.limit:
+            return 0
+        ptr = torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        self.held[ptr] = nbytes
+        self.peak = max(self.peak, sum(self.held.values()))
+        return ptr
+
+    def free(self, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+        self.unknown += self.held.pop(ptr, None) is None
+
+
+def test_refused_allocation_is_out_of_memory_and_leaks_nothing(ttsn):
+    """Failure detection without a device fault: an allocator that refuses a
+    request makes the call that needed it return TT_ERR_OOM with a message;
+    the handle's memory is all returned when it is destroyed, and a handle
+    given just the memory the run needed computes the same result."""
+    p = _problem()
+    ample = _Budget(1 << 40)
+    ref = ttsn.TTSN.from_problem(p, allocator=ample)
+    for _ in range(4):
+        ref.step()
+    peak = ample.peak
+    for frac in (0.05, 0.25):
+        tight = _Budget(int(frac * peak))
+        with pytest.raises(ttsn.TTError) as e:
+            g = ttsn.TTSN.from_problem(p, allocator=tight)
+            for _ in range(4):
+                g.step()
+        assert e.value.status == -2 and "allocation" in str(e.value)
+        g = e = None  # the traceback holds the failed step's frame, and so the handle
+        gc.collect()
+        torch.cuda.synchronize()
+        assert not tight.held and tight.unknown == 0
+    again = ttsn.TTSN.from_problem(p, allocator=_Budget(peak))
+    for _ in range(4):
+        again.step()
+    assert torch.equal(again.full(), ref.full())
