@@ -510,36 +510,48 @@ def run_line_source(args, torch, ttsn):
     """The line source of Sec. 5.4 at the paper's size: 500^2 cells on
     [-1.1, 1.1]^2, 32 x 64 ordinates, Gaussian pulse (width 0.03, U0 = 1), no
     material, vacuum, CFL 0.4, eps 1e-4, the first K_ls steps (to t = 1 with
-    --line-source-steps 0), timed with CUDA events after a short untimed run.
-    Reported beside the paper's figures: the ranks after 120 steps and at the
-    end, and the change of the radiation energy sum_i E_i dV relative to U0
-    (rounding moves energy between E and T; the front stays inside the
-    domain)."""
+    --line-source-steps 0), timed with CUDA events after a short untimed run,
+    in FP64 and in the precision form (free ranks).  Reported beside the
+    paper's figures: the ranks after 120 steps and at the end, the change of
+    the radiation energy sum_i E_i dV relative to U0 (rounding moves energy
+    between E and T; the front stays inside the domain), and the phases of
+    two further profiled steps."""
     p = workloads.line_source()
     steps = int(round(p["t_lim"] / p["dt"]))
     if args.line_source_steps > 0:
         steps = max(121, min(steps, args.line_source_steps))
     stream = torch.cuda.Stream()
+    upd = int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"]
+    out = {"workload": "line source (Sec. 5.4): 2D 500^2 on [-1.1,1.1]^2, 32x64 ordinates, Gaussian pulse "
+                       "width 0.03, U0 1, sigma 0, vacuum, upwind, CFL 0.4, eps 1e-4, steps 1..%d (t = %.3g)"
+                       % (steps, steps * p["dt"])}
+    E = {}
     with torch.cuda.stream(stream):
-        ttsn.TTSN.from_problem(p, stream=stream).step(8)  # warm-up
-        g = ttsn.TTSN.from_problem(p, stream=stream)
-        _, _, (e_rad0, _) = g.energy()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        info120 = g.step(120)
-        info = g.step(steps - 120)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        _, _, (e_rad, _) = g.energy()
-    v = steps / (ms * 1e-3)
-    return {"workload": "line source (Sec. 5.4): 2D 500^2 on [-1.1,1.1]^2, 32x64 ordinates, Gaussian pulse "
-                        "width 0.03, U0 1, sigma 0, vacuum, upwind, CFL 0.4, eps 1e-4, steps 1..%d (t = %.3g)"
-                        % (steps, steps * p["dt"]),
-            "steps_per_s": v, "updates_per_s": v * int(np.prod(p["n"])) * p["n_theta"] * p["n_phi"],
-            "ms_per_step": ms / steps, "ranks_step_120": info120["ranks"][1:-1], "ranks_last": info["ranks"][1:-1],
-            "radiation_energy_change_over_U0": float(abs(e_rad - e_rad0) / p["U0"])}
+        for name, prec in (("fp64", ttsn.TT_FP64), ("mixed", ttsn.TT_MIXED)):
+            ttsn.TTSN.from_problem(p, stream=stream, precision=prec).step(8)  # warm-up
+            g = ttsn.TTSN.from_problem(p, stream=stream, precision=prec)
+            _, _, (e_rad0, _) = g.energy()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info120 = g.step(120)
+            info = g.step(steps - 120)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            E[name], _, (e_rad, _) = g.energy()
+            g.profile(True)
+            g.step(2)
+            prof = g.profile_read()
+            g.profile(False)
+            v = steps / (ms * 1e-3)
+            out[name] = {"steps_per_s": v, "updates_per_s": v * upd, "ms_per_step": ms / steps,
+                         "ranks_step_120": info120["ranks"][1:-1], "ranks_last": info["ranks"][1:-1],
+                         "radiation_energy_change_over_U0": float(abs(e_rad - e_rad0) / p["U0"]),
+                         "phases_ms_2_steps": {k: round(x["ms"], 3) for k, x in prof.items()}}
+    out["mixed"]["speedup_vs_fp64"] = out["mixed"]["steps_per_s"] / out["fp64"]["steps_per_s"]
+    out["mixed"]["E_max_rel_diff_vs_fp64_free_ranks"] = float((E["mixed"] - E["fp64"]).abs().max() / E["fp64"].abs().max())
+    return out
 
 
 def run_schedule(args, torch, ttsn):
