@@ -500,7 +500,10 @@ tt_status tt_gram_noalloc(int m, int n, const double* A_dev, int lda, double* G_
  * attribute time to the phases of the step and to count kernel launches).
  * ------------------------------------------------------------------------ */
 
-/* Phases of the step timed with CUDA events on the handle's stream. */
+/* Phases of the step timed with CUDA events on the handle's stream.  Every
+ * phase occurrence (and every step of tt_sn_step) is also an NVTX range named
+ * after it ("transport", "gram_right", "eig", "gram_left", "small", "update",
+ * "energy"; "tt_sn_step"), so a profiler can attribute kernels to phases. */
 enum {
     TT_PH_TRANSPORT = 0,  /* grown cores: transport terms + source (Sec. 4.3-4.4)  */
     TT_PH_GRAM_RIGHT = 1, /* backward sweep: right Gram matrices (App. A, Alg. 1)  */

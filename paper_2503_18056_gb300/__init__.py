@@ -18,6 +18,7 @@ bare TT for the rounding entry points; ``dgemm``, ``gram``, ``gram_mixed``,
 ``gemm_nt_mixed``, ``syev`` and ``pchol`` expose the kernel-level calls.
 """
 import ctypes
+import os
 
 import numpy as np
 import torch
@@ -26,7 +27,7 @@ from . import _native
 from ._native import (TT_BC_OUTFLOW, TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT,
                       TT_MIXED, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TTSNBatch", "TorchAllocator", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
+__all__ = ["TTSN", "TTSNBatch", "TorchAllocator", "compression_factor", "step_record", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
            "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_BC_OUTFLOW", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
            "TT_STEP_NO_ROUND", "TT_LAYOUT_GROUPED", "TT_LAYOUT_SPLIT"]
 
@@ -162,6 +163,33 @@ class TensorTrain(_Handle):
         self.set_cores(ts)
 
 
+def compression_factor(dims, ranks):
+    """The compression factor C of Sec. 5.1: entries of the full tensor over
+    entries of its TT cores, prod_k n_k / sum_k r_{k-1} n_k r_k (for the
+    three-core layout N_c N_theta N_phi / (r_1 N_c + r_1 r_2 N_theta + r_2 N_phi))."""
+    full = 1.0
+    for m in dims:
+        full *= float(m)
+    stored = sum(float(ranks[k]) * float(dims[k]) * float(ranks[k + 1]) for k in range(len(dims)))
+    return full / stored
+
+
+def step_record(step, t, info, totals, dims, ms=None):
+    """One line of a run log: step index and time, ranks entering and leaving
+    the rounding, discarded tail per bond, ||X||, rank-cap flag, Jacobi sweeps,
+    compression factor, radiation and material energy (sum E dV, sum C_v T dV),
+    and the step's GPU time in ms when measured."""
+    rec = {"step": int(step), "t": float(t), "ranks": list(info["ranks"]), "grown": list(info["grown"]),
+           "discarded": [float(x) for x in info["discarded"]], "norm": float(info["norm"]),
+           "capped": bool(info["capped"]), "sweeps": int(info["sweeps"]),
+           "compression": compression_factor(dims, info["ranks"]),
+           "E_rad": float(totals[0]), "E_mat": float(totals[1]),
+           "E_total": float(totals[0]) + float(totals[1])}
+    if ms is not None:
+        rec["ms"] = float(ms)
+    return rec
+
+
 class TorchAllocator:
     """Device memory from torch's CUDA caching allocator: the handle's buffers
     then count in torch.cuda.memory_allocated() and share torch's cached
@@ -225,6 +253,9 @@ class TTSN(_Handle):
         self.n = tuple(int(m) for m in n)
         self.n_theta, self.n_phi = int(n_theta), int(n_phi)
         self.stream = stream
+        # the library's rule for dt <= 0: CFL times the smallest cell width over c
+        self.dt = float(dt) if dt > 0 else float(cfl) * min(float(L[a]) / self.n[a] for a in range(ndim)) / float(c)
+        self.steps_taken = 0
         f = {"sigma_a": _dev(sigma_a, nc), "cv": _dev(cv, nc), "T0": _dev(T0, nc)}
         f["Tr0"] = _dev(Tr0, nc) if Tr0 is not None else None
         f["sigma_s"] = _dev(sigma_s, nc) if sigma_s is not None else None
@@ -312,6 +343,7 @@ class TTSN(_Handle):
         info = StepInfo()
         check(lib.tt_sn_step_ex(self._h, int(nsteps), int(flags), _int_array(forced),
                                 ctypes.byref(info)))
+        self.steps_taken += int(nsteps)
         return info.as_dict()
 
     def energy(self):
@@ -325,16 +357,55 @@ class TTSN(_Handle):
         t = _dev(T, self.nc)
         check(lib.tt_set_T(self._h, ctypes.c_void_p(t.data_ptr())))
 
+    def compression(self):
+        """Compression factor C of the current TT (Sec. 5.1)."""
+        return compression_factor(self.dims()[1], self.ranks())
+
+    def run(self, nsteps, log=None, time_steps=True):
+        """Take ``nsteps`` steps one at a time and return one ``step_record``
+        per step (ranks, discarded tails, compression, energies, GPU ms timed
+        with CUDA events on the handle's stream); with ``log`` (a path or a
+        writable file) the records are also written as JSON lines."""
+        import json
+
+        dims = self.dims()[1]
+        stream = self.stream if self.stream is not None else torch.cuda.current_stream()
+        out = []
+        fh = open(log, "a") if isinstance(log, (str, os.PathLike)) else log
+        try:
+            for _ in range(int(nsteps)):
+                ms = None
+                if time_steps:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                info = self.step()
+                if time_steps:
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms = e0.elapsed_time(e1)
+                _, _, totals = self.energy()
+                rec = step_record(self.steps_taken, self.steps_taken * self.dt, info, totals, dims, ms)
+                out.append(rec)
+                if fh is not None:
+                    fh.write(json.dumps(rec) + "\n")
+                    fh.flush()
+        finally:
+            if fh is not None and fh is not log:
+                fh.close()
+        return out
+
     def state_dict(self):
         """Checkpoint of the evolving state: the TT cores and the material
         temperature (device copies; torch.save-able).  Fields, constants, the
         flux, sources and inflow faces are the problem's and are not saved."""
-        return {"cores": [c.clone() for c in self.cores()], "T": self.energy()[1].clone()}
+        return {"cores": [c.clone() for c in self.cores()], "T": self.energy()[1].clone(),
+                "steps_taken": self.steps_taken}
 
     def load_state_dict(self, state):
         """Resume from ``state_dict()``: the following steps continue bit for bit."""
         self.set_cores(state["cores"])
         self.set_T(state["T"])
+        self.steps_taken = int(state.get("steps_taken", 0))
 
     def full(self):
         return super().full().reshape(self.n + (self.n_theta, self.n_phi))
@@ -394,7 +465,7 @@ def escape_energy(sigma_a, problem, steps, checkpoint_every=1):
 class _BorrowedTTSN(TTSN):
     """View of one problem of a batch (the batch owns the handle)."""
 
-    def __init__(self, h, n, n_theta, n_phi):
+    def __init__(self, h, n, n_theta, n_phi, dt=None):
         _Handle.__init__(self)
         self._h = h
         self.nc = 1
@@ -402,6 +473,8 @@ class _BorrowedTTSN(TTSN):
             self.nc *= int(m)
         self.n = tuple(int(m) for m in n)
         self.n_theta, self.n_phi = int(n_theta), int(n_phi)
+        self.dt = float(dt) if dt is not None else float("nan")
+        self.steps_taken = 0
 
     def __del__(self):
         self._h = None  # owned by the batch
@@ -455,7 +528,7 @@ class TTSNBatch:
         h = ctypes.c_void_p()
         check(lib.tt_batch_handle(self._b, int(i), ctypes.byref(h)))
         p = self.problems[i]
-        return _BorrowedTTSN(h, p["n"], p["n_theta"], p["n_phi"])
+        return _BorrowedTTSN(h, p["n"], p["n_theta"], p["n_phi"], p.get("dt"))
 
 
 def dgemm(A, B, trans_a=False, trans_b=False, alpha=1.0, stream=None):

@@ -24,6 +24,7 @@
 // being discarded with the floored eigenpairs of G_A.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <string.h>
 
 #include <algorithm>
@@ -325,14 +326,22 @@ cudaEvent_t get_event(tt_ctx* h) {
     return e;
 }
 
-// Brackets one phase occurrence with events when profiling is on; the
-// algorithmic flops/bytes and the library launches in between are accumulated.
+// NVTX range names of the phases (TT_PH_* order): profilers attribute the
+// kernels a phase launches to its range (e.g. ncu --nvtx --nvtx-include
+// "gram_left/").  Without a profiler attached the push/pop calls return at once.
+const char* const kPhaseNames[TT_NPHASES] = {"transport", "gram_right", "eig", "gram_left",
+                                              "small", "update", "energy"};
+
+// Brackets one phase occurrence with an NVTX range and, when profiling is on,
+// with events; the algorithmic flops/bytes and the library launches in
+// between are accumulated.
 struct PhaseScope {
     tt_ctx* h;
     int phase;
     cudaEvent_t a = nullptr;
     unsigned long long l0;
     PhaseScope(tt_ctx* hh, int p, double flops, double bytes) : h(hh), phase(p) {
+        nvtxRangePushA(kPhaseNames[p]);
         l0 = g_launches.load(std::memory_order_relaxed);
         if (!h->prof_on) return;
         a = get_event(h);
@@ -342,11 +351,13 @@ struct PhaseScope {
         h->ph[p].calls += 1;
     }
     ~PhaseScope() {
-        if (!h->prof_on || !a) return;
-        cudaEvent_t b = get_event(h);
-        cudaEventRecord(b, h->stream);
-        h->ph[phase].launches += (long long)(g_launches.load(std::memory_order_relaxed) - l0);
-        h->pending.push_back({phase, a, b});
+        if (h->prof_on && a) {
+            cudaEvent_t b = get_event(h);
+            cudaEventRecord(b, h->stream);
+            h->ph[phase].launches += (long long)(g_launches.load(std::memory_order_relaxed) - l0);
+            h->pending.push_back({phase, a, b});
+        }
+        nvtxRangePop();
     }
 };
 
@@ -1624,7 +1635,9 @@ tt_status tt_sn_step_ex(tt_handle h, int nsteps, int flags, const int* forced, t
             if (forced[k] < 1) return fail(TT_ERR_ARG, "tt_sn_step: forced ranks must be >= 1");
     tt_status result = TT_OK;
     for (int it = 0; it < nsteps; ++it) {
+        nvtxRangePushA("tt_sn_step");
         tt_status st = step_once(h, flags, forced, info);
+        nvtxRangePop();
         if (st < 0) return st;
         if (st == TT_WARN_RANK_CAPPED) result = st;
     }

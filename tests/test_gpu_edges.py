@@ -133,3 +133,26 @@ def test_checkpoint_and_resume_continue_bit_for_bit(ttsn, tmp_path):
     assert a.ranks() == b.ranks()
     assert torch.equal(a.full(), b.full())
     assert torch.equal(a.energy()[1], b.energy()[1])
+
+
+def test_run_log_records_each_step(ttsn, tmp_path):
+    """TTSN.run: one JSON line per step with the step's ranks (as step()
+    reports them), t = step dt, the compression factor of those ranks, and
+    total energy conserved on a periodic grid."""
+    import json
+
+    p = workloads.problem("small_2d", n=(16, 12), n_theta=4, n_phi=8, eps=1e-6)
+    a = ttsn.TTSN.from_problem(p)
+    b = ttsn.TTSN.from_problem(p)
+    path = tmp_path / "run.jsonl"
+    recs = a.run(3, log=str(path))
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert lines == recs and [r["step"] for r in recs] == [1, 2, 3]
+    for r in recs:
+        info = b.step()
+        assert r["ranks"] == info["ranks"] and r["discarded"] == info["discarded"]
+        assert r["t"] == r["step"] * p["dt"] and r["ms"] > 0
+        assert r["compression"] == ttsn.compression_factor([16 * 12, 4, 8], info["ranks"])
+    e0 = recs[0]["E_total"]
+    assert all(abs(r["E_total"] - e0) <= 1e-12 * e0 for r in recs)
+    assert a.compression() == recs[-1]["compression"]
