@@ -44,7 +44,10 @@ typedef enum {
     TT_ERR_NOT_CONVERGED = -4, /* Jacobi eigensolver hit its sweep limit        */
     TT_ERR_TIMEOUT = -5,       /* a bounded device-side wait ran out            */
     TT_ERR_STATE = -6,         /* call not valid for this handle                */
-    TT_ERR_TOO_LARGE = -7      /* output buffer too small / size over a limit   */
+    TT_ERR_TOO_LARGE = -7,     /* output buffer too small / size over a limit   */
+    TT_ERR_NONFINITE = -8      /* a rounding met Inf/NaN (the run diverged, or a
+                                  field held one); the TT is then undefined and
+                                  the caller restores saved cores and T      */
 } tt_status;
 
 enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1, TT_BC_OUTFLOW = 2 };
@@ -188,7 +191,10 @@ tt_status tt_create_tt(int d, const int* n, const int* ranks, void* stream, tt_h
  * core plus one rank-one emission term (Sec. 4.4), Gram-SVD rounding to eps
  * (App. A.2), and the energy-conserving temperature update (Sec. 3.2).
  * info (nullable) receives the diagnostics of the last step.
- * Returns TT_WARN_RANK_CAPPED if max_rank bound in any step.
+ * Returns TT_WARN_RANK_CAPPED if max_rank bound in any step, and
+ * TT_ERR_NONFINITE (stopping at that step) if a rounding meets Inf or NaN:
+ * an unstable time step, or a non-finite field or state, would otherwise
+ * round to the zero tensor without notice.
  */
 tt_status tt_sn_step(tt_handle h, int nsteps, tt_step_info* info);
 
@@ -438,7 +444,8 @@ tt_status tt_wait_probe(void* stream);
  * to eps_mach times the largest initial diagonal entry.  W_dev (n x n,
  * row-major, leading dimension n) receives the rank_host rows of W (rows
  * beyond it are unspecified); G is not modified.  TT_ERR_TOO_LARGE if n x 8
- * bytes exceed the shared-memory limit of one CTA (n > 25600).
+ * bytes exceed the shared-memory limit of one CTA (n > 25600);
+ * TT_ERR_NONFINITE if the diagonal of G holds Inf or NaN.
  */
 tt_status tt_pchol(int n, const double* G_dev, int ldg, double* W_dev, void* stream, int* rank_host);
 

@@ -14,7 +14,7 @@ TT_MAX_D = 8
 TT_OK, TT_WARN_RANK_CAPPED = 0, 1
 STATUS_NAMES = {0: "TT_OK", 1: "TT_WARN_RANK_CAPPED", -1: "TT_ERR_ARG", -2: "TT_ERR_OOM",
                 -3: "TT_ERR_CUDA", -4: "TT_ERR_NOT_CONVERGED", -5: "TT_ERR_TIMEOUT",
-                -6: "TT_ERR_STATE", -7: "TT_ERR_TOO_LARGE"}
+                -6: "TT_ERR_STATE", -7: "TT_ERR_TOO_LARGE", -8: "TT_ERR_NONFINITE"}
 TT_BC_PERIODIC, TT_BC_VACUUM, TT_BC_OUTFLOW = 0, 1, 2
 TT_FP64, TT_MIXED = 0, 1
 TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT = 0, 1

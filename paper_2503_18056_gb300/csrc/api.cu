@@ -609,7 +609,12 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         TT_CUDA_TRY(cudaStreamSynchronize(s));
     }
     int kBs[TT_MAX_D];
-    for (int k = 0; k < d - 1; ++k) kBs[k] = h->h_int[HI_KB + k];
+    for (int k = 0; k < d - 1; ++k) {
+        kBs[k] = h->h_int[HI_KB + k];
+        if (kBs[k] < 0)
+            return fail(TT_ERR_NONFINITE, "rounding: a right Gram matrix holds Inf or NaN (the run diverged or "
+                                          "a field held one); restore saved cores and T before stepping again");
+    }
 
     // delta^2 is set from the first bond's ||X||^2
     h->h_dbl[HD_DELTA2] = -1.0;
@@ -658,6 +663,9 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_DEC, h->d_dbl + HD_DEC, 4 * sizeof(double),
                                     cudaMemcpyDeviceToHost, s));
         TT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h->h_int[HI_DEC + 2])
+            return fail(TT_ERR_NONFINITE, "rounding: the tensor holds Inf or NaN (the run diverged or a field "
+                                          "held one); restore saved cores and T before stepping again");
         const int rk = h->h_int[HI_DEC];
         if (h->h_int[HI_DEC + 1]) any_capped = true;
         if (info) {
@@ -2175,6 +2183,7 @@ tt_status tt_pchol(int n, const double* G, int ldg, double* W, void* stream, int
     if (st < 0) return st;
     if (e != cudaSuccess) return fail(TT_ERR_CUDA, std::string("tt_pchol: ") + cudaGetErrorString(e));
     if (hs[0] & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_pchol: grid barrier wait ran out");
+    if (hs[1] < 0) return fail(TT_ERR_NONFINITE, "tt_pchol: Inf or NaN on the diagonal of G");
     if (rank_host) *rank_host = hs[1];
     return TT_OK;
 }

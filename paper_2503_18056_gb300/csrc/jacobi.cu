@@ -320,10 +320,18 @@ pchol_small_kernel(int n, const double* __restrict__ G, long ldg, double* W, int
     __shared__ int s_p;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     double dm = 0.0;
+    int bad = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const double x = G[(long)j * ldg + j];
         dd[j] = x;
         dm = fmax(dm, x);
+        bad |= !isfinite(x);
+    }
+    // Inf or NaN on the diagonal (a Gram matrix shows any non-finite entry of
+    // its factor there): rank -1 reports it instead of factorising
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0) *kB_out = -1;
+        return;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
@@ -462,7 +470,18 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     // every CTA reads the initial diagonal (G is an input and is not written)
     double dm = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) dm = fmax(dm, G[(long)j * ldg + j]);
+    int bad = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double x = G[(long)j * ldg + j];
+        dm = fmax(dm, x);
+        bad |= !isfinite(x);
+    }
+    // Inf or NaN on the diagonal: every CTA reads all of it, so all leave here
+    // together (before the first grid barrier) and rank -1 reports it
+    if (__syncthreads_or(bad)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[3] = -1;
+        return;
+    }
     s_val[threadIdx.x] = dm;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -556,6 +575,9 @@ __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm
     // at zero, so the symmetric rounding noise of the Gram eigenvalues cancels
     double total = 0.0;
     for (int j = kB - 1; j >= 0; --j) total += lamK[j];
+    // an Inf or NaN anywhere in the tensor reaches the eigenvalues (or their
+    // sum); the host reports it instead of rounding to the zero tensor
+    dec_i[2] = isfinite(total) ? 0 : 1;
     total = fmax(total, 0.0);
     double delta2 = *delta2_dev;
     if (delta2 < 0.0) {

@@ -156,3 +156,53 @@ def test_run_log_records_each_step(ttsn, tmp_path):
     e0 = recs[0]["E_total"]
     assert all(abs(r["E_total"] - e0) <= 1e-12 * e0 for r in recs)
     assert a.compression() == recs[-1]["compression"]
+
+
+@pytest.mark.parametrize("where", ["T", "theta_core"])
+def test_non_finite_state_is_reported_and_a_checkpoint_restores(ttsn, where):
+    """Failure detection without a device fault: a NaN planted on the host in
+    the temperature (it reaches the emission column of the spatial core, so
+    the left Gram and its eigenvalues) or in the theta core (it reaches a
+    right Gram, so the pivoted Cholesky) makes the step return
+    TT_ERR_NONFINITE instead of rounding to the zero tensor; reloading a
+    checkpoint restores a handle that then steps exactly like an untouched
+    twin."""
+    p = workloads.problem("small_2d", n=(16, 12), n_theta=4, n_phi=8, eps=1e-6)
+    a = ttsn.TTSN.from_problem(p)
+    b = ttsn.TTSN.from_problem(p)
+    a.step(2)
+    b.step(2)
+    ckpt = a.state_dict()
+    if where == "T":
+        T = ckpt["T"].clone()
+        T[7] = float("nan")
+        a.set_T(T)
+    else:
+        cores = [c.clone() for c in ckpt["cores"]]
+        cores[1][0, 1, 0] = float("inf")
+        a.set_cores(cores)
+    with pytest.raises(ttsn.TTError) as e:
+        a.step()
+    assert e.value.status == -8
+    a.load_state_dict(ckpt)
+    a.step(2)
+    b.step(2)
+    assert torch.equal(a.full(), b.full())
+    assert torch.equal(a.energy()[1], b.energy()[1])
+
+
+@pytest.mark.parametrize("n", [40, 500])
+def test_pchol_of_a_non_finite_diagonal_is_reported(ttsn, n):
+    """One CTA (n <= 384) and the cooperative multi-CTA kernel both stop before
+    factorising when the diagonal holds NaN or Inf."""
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((n + 3, n))
+    G = X.T @ X
+    for bad in (float("nan"), float("inf")):
+        H = G.copy()
+        H[n // 2, n // 2] = bad
+        with pytest.raises(ttsn.TTError) as e:
+            ttsn.pchol(torch.tensor(H, device="cuda"))
+        assert e.value.status == -8
+    W, k = ttsn.pchol(torch.tensor(G, device="cuda"))
+    assert k == n
