@@ -13,9 +13,16 @@ fluxes, periodic / vacuum / outflow faces, inflow faces (``set_inflow``),
 fixed sources (``set_sources``), Gram-SVD or randomized rounding
 (``set_sketch``, ``set_rounding``), the adjoint tape (``tape_begin``,
 ``escape_gradient``) and ``EscapeEnergy`` as a torch.autograd.Function.
-``TTSNBatch`` steps many independent problems together; ``TensorTrain`` is a
-bare TT for the rounding entry points; ``dgemm``, ``gram``, ``gram_mixed``,
-``gemm_nt_mixed``, ``syev`` and ``pchol`` expose the kernel-level calls.
+``TTSN.run`` steps with a per-step record (ranks, discarded tails,
+compression factor, energies, GPU ms; JSON lines with ``log=``);
+``state_dict`` / ``load_state_dict`` checkpoint and resume a run; any object
+with ``alloc``/``free`` (``TorchAllocator`` for torch's caching allocator) can
+supply the device memory.  ``TTSNBatch`` steps many independent problems
+together; ``TensorTrain`` is a bare TT for the rounding entry points;
+``dgemm``, ``gram``, ``gram_mixed``, ``gemm_nt_mixed``, ``syev`` and ``pchol``
+expose the kernel-level calls.  Failures come back as ``TTError`` with the
+library's status (argument, out of memory, bounded wait ran out, eigensolver
+sweep limit, Inf/NaN met by a rounding).
 """
 import ctypes
 import os
