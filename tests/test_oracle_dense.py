@@ -85,6 +85,35 @@ def test_periodic_transport_conserves_each_ordinate(n):
     assert np.allclose(d.I.sum(axis=axes), I0.sum(axis=axes), rtol=1e-13, atol=0)
 
 
+def test_periodic_streaming_moves_each_centroid_by_c_dt_n():
+    """Donor-cell upwinding moves the first moment of every ordinate by
+    exactly c dt n per step, and keeps its mass, while the support stays clear
+    of the periodic seam: sum_i x_i I_{i-1} = sum_j (x_j + dx) I_j.  Catches
+    a swapped axis, direction cosine or sign."""
+    n, nt, npf = (40, 36), 4, 8
+    rng = np.random.default_rng(5)
+    I0 = np.zeros(n + (nt, npf))
+    I0[17:23, 15:21] = rng.uniform(0.5, 1.5, (6, 6, nt, npf))
+    dt = 0.01
+    d = _dense(n, nt, npf, dt, PERIODIC, a_r=0.0, I0=I0)
+    g = angles.grid(nt, npf)
+    nx, ny = angles.normals(g)[:2]
+    X, Y = np.meshgrid((np.arange(n[0]) + 0.5) / n[0], (np.arange(n[1]) + 0.5) / n[1], indexing="ij")
+
+    def centroid(I):
+        m = I.sum(axis=(0, 1))
+        return m, np.einsum("ij,ijlp->lp", X, I) / m, np.einsum("ij,ijlp->lp", Y, I) / m
+
+    m0, cx0, cy0 = centroid(I0)
+    steps = 6
+    for _ in range(steps):
+        d.step(with_source=False)
+    m1, cx1, cy1 = centroid(d.I)
+    assert np.abs(m1 - m0).max() <= 1e-13 * m0.max()
+    assert np.abs(cx1 - cx0 - steps * dt * nx).max() <= 1e-13
+    assert np.abs(cy1 - cy0 - steps * dt * ny).max() <= 1e-13
+
+
 def test_pure_absorption_decay_closed_form():
     # a_r = 0, uniform isotropic intensity, periodic: I^m = I^0 (1 + c dt sigma)^-m
     n, nt, npf = (8, 8), 4, 8

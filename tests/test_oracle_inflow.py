@@ -67,3 +67,23 @@ def test_hohlraum_error_falls_with_angles():
         assert nc == 64 * 64
     assert errs[0] > errs[1] > errs[2], errs
     assert errs[2] < 0.012, errs  # 7.4e-3 measured
+
+
+def test_hohlraum_error_halves_with_the_cell_width():
+    """Sec. 5.1: with enough ordinates the spatial error dominates, and halving
+    the cell width about halves the L1 error of J (a first-order scheme); here
+    16 x 32 ordinates, 32^2 -> 64^2 cells on [0, 2]^2 to t = 0.75."""
+    errs = []
+    for m in (32, 64):
+        p = workloads.hohlraum(n=(m, m), n_theta=16, n_phi=32)
+        d = DenseSN(p["n"], p["L"], 16, 32, p["c"], p["a_r"], p["dt"], p["bc"], p["sigma_a"], p["cv"],
+                    p["T0"], np.zeros(p["n"] + (16, 32)), inflow=p["inflow"])
+        steps = int(round(p["t_lim"] / p["dt"]))
+        for _ in range(steps):
+            d.step()
+        xc = workloads.cell_centres(p["n"], p["L"])
+        J = p["c"] * d.energy_density() / (4 * np.pi)
+        Ja = hohlraum_J(steps * p["dt"], xc[0], xc[1], p["c"])
+        sub = (xc[0] < 1.0) & (xc[1] < 1.0)
+        errs.append(float(np.mean(np.abs(J - Ja)[sub])))
+    assert 1.7 <= errs[0] / errs[1] <= 2.3, errs
