@@ -123,23 +123,32 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.flush()
-        rows = []
         with open(self.f.name) as fh:
-            for line in fh:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+            lines = fh.readlines()
         os.unlink(self.f.name)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
-        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
-                "power_w_median": statistics.median(pw) if pw else None}
+        return parse_clock_rows(lines)
+
+
+def parse_clock_rows(lines):
+    """Summary of nvidia-smi samples in ClockSampler.QUERY order (csv, no
+    header, no units): median SM clock under load, the largest max clock, the
+    throttle reasons seen active at least once, the sample count and the
+    median power; None without samples."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) >= 9:
+            rows.append(parts)
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+    pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+            "power_w_median": statistics.median(pw) if pw else None}
 
 
 # ---------------------------------------------------------------- ours
