@@ -58,3 +58,22 @@ def test_quartic_stiff_limit_reaches_equilibrium():
     # kappa -> infinity: C_v T + a_r T^4 = C_v T^m + E* (paper Sec. 5.2 with c_v = 8)
     T = float(t_dagger(2.0, 1.0, 1e12, 8.0, 1.0))
     assert abs(8 * T + T ** 4 - 17.0) < 1e-9
+
+
+@pytest.mark.parametrize("nt,npf", [(2, 4), (8, 16), (5, 7)])
+def test_isotropic_intensity_gives_E_equal_4pi_I_over_c(nt, npf):
+    """Sec. 4.1's quadrature of an isotropic intensity: E = 4 pi I / c exactly
+    (the weights sum to 4 pi), in the dense form and the grouped TT form."""
+    from oracle import tt
+    from oracle.dense import DenseSN
+
+    c = 2.5
+    I = np.array([0.3, 1.7, 4.0])
+    n = (3,)
+    d = DenseSN(n, [1.0], nt, npf, c, 1.0, 0.1, [0], np.ones(n), np.ones(n), np.ones(n),
+                I[:, None, None] * np.ones((nt, npf)))
+    assert np.allclose(d.energy_density(), 4 * np.pi * I / c, rtol=1e-14, atol=0)
+    g = angles.grid(nt, npf)
+    cores = [I.reshape(1, 3, 1), np.ones((1, nt, 1)), np.ones((1, npf, 1))]
+    E = tt.energy_density_grouped(cores, g["w"], g["v"], c)
+    assert np.allclose(E, 4 * np.pi * I / c, rtol=1e-14, atol=0)
