@@ -497,7 +497,10 @@ tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A_dev, int lda, co
  * stream capture begins.  All calls share the array, so calls that overlap on
  * the GPU race on it and must be serialised by the caller.  Results equal
  * tt_gram's up to the order of the floating-point sums (the split-K factor may
- * be smaller) and are exactly symmetric and reproducible.
+ * be smaller) and are exactly symmetric and reproducible.  The split over rows
+ * is capped so that its n x n partials fit the array (2^20 / n^2 splits): for
+ * n > 724 only one fits and the call runs without a row split, one CTA per
+ * upper-triangle tile, which is several times slower than tt_gram on tall A.
  */
 tt_status tt_gram_noalloc(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg,
                           void* stream);

@@ -102,7 +102,23 @@ class _Handle:
         return out
 
     def set_cores(self, cores):
+        """Replace the TT by ``cores`` (copied in).  The count and every shape
+        are checked against the handle's mode sizes before the library copies
+        anything: core k must be (r_{k-1}, n_k, r_k) with r_0 = r_d = 1 and each
+        r_{k-1} equal to the previous core's last dimension."""
+        d, n = self.dims()
         ts = [_dev(c) for c in cores]
+        if len(ts) != d:
+            raise ValueError("expected %d cores, got %d" % (d, len(ts)))
+        prev = 1
+        for k, t in enumerate(ts):
+            if t.dim() != 3:
+                raise ValueError("core %d must be 3-dimensional, got shape %s" % (k, tuple(t.shape)))
+            r0, nk, r1 = (int(x) for x in t.shape)
+            if r0 != prev or nk != n[k] or r1 < 1 or (k == d - 1 and r1 != 1):
+                raise ValueError("core %d has shape %s; expected (%d, %d, r) with r %s"
+                                 % (k, tuple(t.shape), prev, n[k], "= 1" if k == d - 1 else ">= 1"))
+            prev = r1
         ranks = [1] + [int(t.shape[2]) for t in ts[:-1]] + [1]
         ptrs = (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
         check(lib.tt_set_cores(self._h, ptrs, _int_array(ranks)))
@@ -455,13 +471,17 @@ class EscapeEnergy(torch.autograd.Function):
         tt.step(int(steps))
         q, _ = tt.escape_energy()
         ctx.tt = tt  # the taped run, reversed in backward
+        ctx.sigma_shape = sigma_a.shape
         return torch.tensor(q, dtype=torch.float64, device=sigma_a.device)
 
     @staticmethod
     def backward(ctx, gq):
+        if ctx.tt is None:
+            raise RuntimeError("EscapeEnergy: the taped run was already reversed and released; "
+                               "backward through it can run once (retain_graph cannot keep the tape)")
         _, grad = ctx.tt.escape_gradient()
         ctx.tt = None
-        return gq * grad, None, None, None
+        return (gq * grad).view(ctx.sigma_shape), None, None, None
 
 
 def escape_energy(sigma_a, problem, steps, checkpoint_every=1):
@@ -588,9 +608,21 @@ def gram_noalloc(A, G=None, stream=None):
     A = _dev(A)
     m, n = A.shape
     if G is None:
-        G = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        G = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    else:
+        # the library gets only a raw pointer and writes n rows of n doubles
+        # at stride ldg: refuse any G that cannot hold them
+        if not isinstance(G, torch.Tensor) or G.dtype != torch.float64:
+            raise ValueError("G must be a float64 tensor")
+        if G.device != A.device:
+            raise ValueError("G is on %s, A on %s" % (G.device, A.device))
+        if tuple(G.shape) != (n, n):
+            raise ValueError("G must have shape (%d, %d), got %s" % (n, n, tuple(G.shape)))
+        if n > 0 and (G.stride(1) != 1 or G.stride(0) < n):
+            raise ValueError("G must be row-major with unit column stride and row stride >= n")
+    ldg = int(G.stride(0)) if n > 0 else n
     check(lib.tt_gram_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), n, ctypes.c_void_p(G.data_ptr()),
-                              n, _stream_ptr(stream)))
+                              ldg, _stream_ptr(stream)))
     return G
 
 

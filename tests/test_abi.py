@@ -38,6 +38,9 @@ def test_error_message_without_gpu_is_reported_not_raised():
     assert b"null" in _native.lib.tt_last_error() or b"range" in _native.lib.tt_last_error()
 
 
+_KEEP = []
+
+
 def _valid_desc(_native):
     import ctypes
 
@@ -47,9 +50,12 @@ def _valid_desc(_native):
     d.L[0] = d.L[1] = d.L[2] = 1.0
     d.n_theta, d.n_phi = 4, 8
     d.c, d.a_r, d.cfl, d.dt = 1.0, 1.0, 0.5, 0.0
-    # never dereferenced: every case below is refused before any field is read
-    fake = ctypes.c_void_p(0x1000)
-    d.sigma_a = d.cv = d.T0 = fake
+    # a real buffer of N_c doubles (host memory; no device here): every case
+    # below is refused before any field is read, and were a check ever lost
+    # the call would read only memory that exists
+    field = (ctypes.c_double * (8 * 6))()
+    _KEEP.append(field)
+    d.sigma_a = d.cv = d.T0 = ctypes.cast(field, ctypes.c_void_p)
     d.eps, d.max_rank, d.rounds_per_step, d.precision = 1e-6, 0, 1, 0
     d.layout, d.flux = 0, 0
     return d
@@ -121,7 +127,10 @@ def test_null_handle_and_bad_sizes_are_refused_on_the_host():
     for i, call in enumerate(calls):
         assert call() == -1, i
         assert b"null" in lib.tt_last_error(), (i, lib.tt_last_error())
-    x = ctypes.c_void_p(0x1000)  # never dereferenced: each call below is refused first
+    # a real 64-double buffer, larger than any size below: each call is refused
+    # before touching it, and a lost check would still stay inside it
+    xbuf = (ctypes.c_double * 64)()
+    x = ctypes.cast(xbuf, ctypes.c_void_p)
     assert lib.tt_gram(-1, 4, x, 4, x, 4, None) == -1
     assert lib.tt_gram(8, 4, None, 4, x, 4, None) == -1
     assert lib.tt_gram(8, 4, x, 3, x, 4, None) == -1 and b"leading" in lib.tt_last_error()

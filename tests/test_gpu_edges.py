@@ -135,6 +135,38 @@ def test_checkpoint_and_resume_continue_bit_for_bit(ttsn, tmp_path):
     assert torch.equal(a.energy()[1], b.energy()[1])
 
 
+def test_mismatched_state_is_refused_before_any_copy(ttsn):
+    """load_state_dict / set_cores check the core count and every shape against
+    the handle's grid before the library copies anything: a state from another
+    grid, a short list or a misshaped core is a ValueError and the handle's
+    state is unchanged."""
+    p = workloads.problem("small_2d", n=(16, 12), n_theta=4, n_phi=8, eps=1e-6)
+    a = ttsn.TTSN.from_problem(p)
+    a.step(2)
+    full0 = a.full().clone()
+    good = a.state_dict()
+    other = ttsn.TTSN.from_problem(workloads.problem("small_2d", n=(8, 8), n_theta=4, n_phi=8, eps=1e-6))
+    other.step(1)
+    cores = good["cores"]
+    bad_states = [
+        other.state_dict()["cores"],                      # another grid
+        cores[:-1],                                       # a core short
+        cores + [cores[-1]],                              # a core too many
+        [cores[0][..., :-1]] + cores[1:],                 # r_1 disagrees with the next core
+        [cores[0]] + [cores[1][:, :-1]] + cores[2:],      # wrong n_theta
+        [c.reshape(-1) for c in cores],                   # not 3-dimensional
+        cores[:-1] + [torch.cat([cores[-1], cores[-1]], dim=2)],  # last rank not 1
+    ]
+    for bad in bad_states:
+        with pytest.raises(ValueError):
+            a.set_cores(bad)
+        with pytest.raises(ValueError):
+            a.load_state_dict({"cores": bad, "T": good["T"]})
+    assert torch.equal(a.full(), full0)
+    a.load_state_dict(good)
+    assert torch.equal(a.full(), full0)
+
+
 def test_run_log_records_each_step(ttsn, tmp_path):
     """TTSN.run: one JSON line per step with the step's ranks (as step()
     reports them), t = step dt, the compression factor of those ranks, and

@@ -122,11 +122,18 @@ def test_mixed_matches_fp64_with_sources_at_fp64_ranks(ttsn):
         gmx.step(forced=info["ranks"][1:-1])
     E64, T64, _ = g64.energy()
     Em, Tm, _ = gmx.energy()
-    # measured 1e-10 .. 2.2e-9 of their maxima depending on the summation order
-    # of the FP64 products (T sits near the 1e-3 background); the precision
-    # form's stated bound is 1e-6
-    assert float((Em - E64).abs().max() / E64.abs().max()) <= 1e-8
-    assert float((Tm - T64).abs().max() / T64.abs().max()) <= 1e-8
+    # The bound is the precision form's stated error target, 1e-6 relative to
+    # the FP64 run at equal ranks.  A tighter a-priori bound does not follow
+    # from the split's per-term error (<= 8 2^-48 m of the column scales,
+    # pinned in test_gpu_mixed): propagated through a Gram-SVD truncation it
+    # acts like a larger unit roundoff, and the Gram resolution argument
+    # (sqrt of the relative Gram error per bond and step) gives ~1e-5 over
+    # these 40 steps, looser than the target.  Measured 2e-13 (E) and
+    # 2e-12 (T, which sits near its 1e-3 background).
+    dE = float((Em - E64).abs().max() / E64.abs().max())
+    dT = float((Tm - T64).abs().max() / T64.abs().max())
+    print("precision form vs FP64 with sources, 40 steps: E %.1e, T %.1e" % (dE, dT))
+    assert dE <= 1e-6 and dT <= 1e-6
 
 
 @pytest.fixture(scope="module")

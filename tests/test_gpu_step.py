@@ -137,12 +137,25 @@ def _gap_ranks(sig, ranks, ratio=1.05):
     return out
 
 
-def test_small_2d_workload_at_resolvable_tolerance(ttsn):
-    # the same workload at eps = 1e-4, where every kept singular value is well
-    # above the Gram resolution and cuts sit at gaps: parity with the oracle to 1e-10
-    p = workloads.problem("small_2d", eps=1e-4)
+@pytest.mark.parametrize("eps", [1e-4, 1e-5, 1e-6, 1e-8])
+def test_small_2d_workload_cuts_at_gaps(ttsn, eps):
+    # The 32x32 workload with every cut moved to the next clear gap of the
+    # oracle's singular values, which separates the two sources of difference
+    # seen at free cuts: cuts inside the symmetric pairs, and the Gram
+    # resolution.  Where the kept singular values at the cut stay above the
+    # Gram resolution (eps >= 1e-6: sigma_cut / sigma_max ~ 1e-6 against
+    # sqrt(R eps_mach) ~ 1e-7) the step matches the TT-SVD oracle to 1e-10
+    # (measured 2e-11 at 1e-4, 1e-12 at 1e-5 and 1e-6).  At the stated
+    # eps = 1e-8 the cut lies below that resolution: the Gram eigenvalues near
+    # the cut (~1e-16 lambda_max) are at the absolute error of the Gram
+    # itself, so kept components there carry errors of their own size, and the
+    # per-step budget of the free-cut test applies (measured 7e-8 at gap cuts,
+    # the same as at free cuts: the difference at 1e-8 is the resolution, not
+    # the pairs).
+    p = workloads.problem("small_2d", eps=eps)
     ref = _oracle(p)
     g = ttsn.TTSN.from_problem(p)
+    budget = 0.0
     for _ in range(p["steps"]):
         grown, _, _ = ref.source(ref.transport(ref.cores))
         Z, sig = round_ttsvd(grown, eps=p["eps"])
@@ -150,9 +163,12 @@ def test_small_2d_workload_at_resolvable_tolerance(ttsn):
         ref.step(forced=forced)
         info = g.step(forced=forced)
         assert info["ranks"][1:-1] == tt.ranks(ref.cores)
+        budget += 2 * np.sqrt(2) * np.sqrt(p["eps"] ** 2 + max(info["grown"]) * EPS_MACH)
     F = g.full().cpu().numpy()
     Rf = ref.full()
-    assert np.linalg.norm(F - Rf) <= 1e-10 * np.linalg.norm(Rf)
+    err = np.linalg.norm(F - Rf) / np.linalg.norm(Rf)
+    print("small_2d eps %.0e, cuts at gaps: rel. difference to the TT-SVD oracle %.2e" % (eps, err))
+    assert err <= (1e-10 if eps >= 1e-6 else budget), (err, budget)
 
 
 def test_energy_conserved_periodic_free_ranks(ttsn):

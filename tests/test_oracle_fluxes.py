@@ -157,3 +157,70 @@ def test_gaussian_diffusion_dense_follows_the_analytic_solution():
     err = np.linalg.norm(d.energy_density() - Ea) / np.linalg.norm(Ea)
     moved = np.linalg.norm(E0 - Ea) / np.linalg.norm(Ea)
     assert err <= 1e-2 and err <= 0.2 * moved, (err, moved)
+
+
+def _hand_hll_face(n, tau, UL, UR, c=1.0, thr=1.0):
+    """One face's HLL flux written out from Sec. 3.1's four-case table (wave
+    speeds after Eq. hll), small-tau rows only (tau < thr):
+    n >= 0: S_R = c n sqrt(1 - tau^2/2), S_L = -c n tau;
+    n < 0:  S_R = -c n tau,              S_L = c n sqrt(1 - tau^2/2);
+    then Eq. hll, F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L)."""
+    assert 0.0 < tau < thr
+    if n >= 0.0:
+        S_R, S_L = c * n * (1.0 - tau * tau / 2.0) ** 0.5, -c * n * tau
+    else:
+        S_R, S_L = -c * n * tau, c * n * (1.0 - tau * tau / 2.0) ** 0.5
+    FL, FR = c * n * UL, c * n * UR
+    return (S_R * FL - S_L * FR + S_L * S_R * (UR - UL)) / (S_R - S_L)
+
+
+@pytest.mark.parametrize("beta,sigma", [(1.0, 3.0), (0.7, 5.0), (2.0, 0.25)])
+def test_hll_small_tau_branch_against_the_table_by_hand(beta, sigma):
+    """The small-tau rows of the wave-speed table (0 < tau_c < tau_threshold),
+    which neither limit pins: a 1D row of 6 cells with uniform opacity has
+    tau_c = beta sigma dx on every face (Eq. tauc, harmonic mean of equal
+    values; the vacuum faces take the boundary cell's own opacity), and the
+    dense transport must equal I_i - (dt/dx)(F_{i+1/2} - F_{i-1/2}) with each
+    face's flux computed here by hand from the table, for ordinates of both
+    signs (vacuum ghosts hold zero)."""
+    N, L = 6, 1.0
+    dx = L / N
+    tau = beta * sigma * dx
+    assert 0.0 < tau < 1.0
+    rng = np.random.default_rng(3)
+    normals = np.array([0.83, 0.21, -0.47, -0.95])
+    I0 = rng.uniform(0.5, 2.0, (N, 1, 4))
+    d = DenseSN((N,), [L], 1, 4, 1.0, 1.0, 0.3 * dx, [VACUUM], np.full(N, sigma), np.ones(N), np.ones(N), I0,
+                flux="hll", hll_beta=beta, hll_tau_threshold=1.0)
+    d.nvec = [normals.reshape(1, 4).copy()]
+    out = d.transport(d.I)
+    nu = d.dt / dx
+    for p, n in enumerate(normals):
+        U = np.concatenate([[0.0], I0[:, 0, p], [0.0]])  # ghost, cells, ghost
+        F = [_hand_hll_face(n, tau, U[k], U[k + 1]) for k in range(N + 1)]
+        want = [U[i + 1] - nu * (F[i + 1] - F[i]) for i in range(N)]
+        assert np.abs(out[:, 0, p] - np.array(want)).max() <= 1e-14
+
+
+def test_hll_small_tau_series_leaves_upwinding_at_third_order():
+    """Series identity of the small-tau branch: with S_R = c n a, S_L = -c n b
+    (n > 0) Eq. hll reduces to F = c n [U_L + b (1 - a)/(a + b) (U_R - U_L)];
+    the table's a = sqrt(1 - tau^2/2), b = tau make the departure from
+    upwinding (F - c n U_L) / (c n (U_R - U_L)) = tau^3/4 + O(tau^4), and the
+    mirrored n < 0 case departs from c n U_R by -tau^3/4.  A wrong coefficient
+    in either speed changes the tau^3 coefficient (b = tau/2 gives 1/8,
+    sqrt(1 - tau^2) gives 1/2)."""
+    d = _dense((10,), "hll", VACUUM, sigma=1.0)
+    UL, UR = 1.7, 0.6
+    for n in (0.4, -0.9):
+        coef = []
+        for tau in (2e-2, 1e-2, 5e-3):
+            S_R, S_L = d._hll_speeds(np.array([[n]]), np.array([tau]))
+            S_R, S_L = float(S_R.ravel()[0]), float(S_L.ravel()[0])
+            FL, FR = d.c * n * UL, d.c * n * UR
+            F = (S_R * FL - S_L * FR + S_L * S_R * (UR - UL)) / (S_R - S_L)
+            up = FL if n >= 0 else FR
+            coef.append((F - up) / (d.c * n * (UR - UL)) / tau ** 3)
+        want = 0.25 if n > 0 else -0.25
+        # O(tau) corrections shrink with tau
+        assert abs(coef[-1] - want) < 2e-3 and abs(coef[-1] - want) < abs(coef[0] - want)
