@@ -403,6 +403,65 @@ tt_status tt_batch_sync(tt_batch b);
 void tt_batch_destroy(tt_batch b);
 
 /* ---------------------------------------------------------------------------
+ * Spatial sharding: the method partitioned over space across several
+ * processes (one GPU each).  In the grouped layout (Sec. 4.1, Eq.
+ * tensor_decomp) the spatial core X holds one row per cell; a shard holds the
+ * rows of a slab of whole layers along axis 0 (cells with plane_begin <= c_0 <
+ * plane_end), and the angular cores Theta, Phi are replicated.  One step then
+ * needs exactly two exchanges:
+ *   - the upwind stencil of Sec. 4.3 reads one ghost layer on each side of
+ *     the slab (Sec. 4.5 ghost cells): a halo exchange of the rows of X in
+ *     the slab's first and last layers with the neighbouring shards;
+ *   - the Gram-SVD rounding of App. A.2 needs the left Gram matrix of the
+ *     spatial core, G_A = X*^T X* = sum over shards of X*_s^T X*_s: an
+ *     R x R all-reduce (sum).
+ * Everything else is either local to the rows (the grown core, the source
+ * stage and quartic of Sec. 3.2, the core update A' = A P_A, the energy
+ * update) or computed identically on every shard from replicated data (the
+ * right Grams, the eigensolves and rank decisions, the small products, the
+ * angular cores), so all shards take the same rank decisions.
+ * ------------------------------------------------------------------------ */
+
+enum { TT_XCHG_SUM = 0, TT_XCHG_HALO = 1 };
+
+/*
+ * The exchange callback of a shard.  The library calls it from inside
+ * tt_sn_step / tt_round / tt_energy with its stream already synchronised; the
+ * callback must have finished writing before it returns.  buf_dev is device
+ * memory of the handle; stream is the handle's cudaStream_t (for callers that
+ * order their own work on it).  Return 0 on success, anything else aborts
+ * the call with TT_ERR_STATE.
+ *   kind TT_XCHG_SUM: buf_dev holds count doubles; replace them by their sum
+ *     over all shards, the same bits on every shard (an all-reduce).
+ *   kind TT_XCHG_HALO: buf_dev holds four blocks of count doubles, [send_lo |
+ *     send_hi | recv_lo | recv_hi]; on the ring of shards ordered by plane
+ *     (shard s - 1 below s, the last shard below the first), fill recv_lo
+ *     with the send_hi block of the shard below and recv_hi with the send_lo
+ *     block of the shard above (with one shard, its own blocks).  The library
+ *     then replaces the ghost layer of a global vacuum face by zeros and of a
+ *     global outflow face by the boundary layer itself, so the ring's
+ *     wrap-around is what a periodic axis 0 needs.
+ */
+typedef int (*tt_exchange_fn)(void* ctx, int kind, double* buf_dev, size_t count, void* stream);
+
+/*
+ * tt_create_shard: as tt_create for the shard of layers [plane_begin,
+ * plane_end) along axis 0 of the grid that desc describes (the whole grid:
+ * desc's fields are device arrays of all N_c cells, of which the shard copies
+ * its own).  exchange (with ctx passed through) carries the halo and the sum
+ * described above; it must stay valid until tt_destroy.  The shard's TT is
+ * X (1, N_s, r1), Theta, Phi with N_s = (plane_end - plane_begin) times the
+ * cells of one layer, in the same C order; tt_to_full, tt_energy's E and T
+ * and tt_get_core(0) cover the shard's cells, tt_energy's totals the whole
+ * grid.  Grouped layout only; upwind and Rusanov fluxes (HLL's per-face
+ * optical depths would need the neighbours' opacities); no fixed sources,
+ * inflow faces, adjoint tape or randomized rounding (TT_ERR_STATE).
+ * TT_ERR_ARG for an empty or out-of-range slab or a null callback.
+ */
+tt_status tt_create_shard(const tt_problem_desc* desc, void* stream, int plane_begin, int plane_end,
+                          tt_exchange_fn exchange, void* ctx, tt_handle* out);
+
+/* ---------------------------------------------------------------------------
  * Kernel-level calls (the building blocks of tt_round, exposed for testing and
  * for callers that hold their own TT data).  All ordered on `stream`.
  * ------------------------------------------------------------------------ */
@@ -460,6 +519,19 @@ tt_status tt_pchol(int n, const double* G_dev, int ldg, double* W_dev, void* str
  */
 tt_status tt_syev(int n, const double* G_dev, int ldg, double* lam_dev, double* Vt_dev, int ldv,
                   void* stream, int* sweeps_host);
+
+/*
+ * tt_syev_ex: tt_syev with a sweep limit of max_sweeps (1 .. 40; tt_syev
+ * uses 40).  A limit the iteration reaches returns TT_ERR_NOT_CONVERGED, as
+ * a stand-in for an eigensolve that failed to converge; nothing else changes.
+ * tt_set_max_sweeps: the same limit for the eigensolves of a handle's
+ * roundings (default 40); a step whose eigensolve reaches it completes and
+ * returns TT_ERR_NOT_CONVERGED, and the handle stays usable.  TT_ERR_ARG for
+ * a limit outside 1 .. 40.
+ */
+tt_status tt_syev_ex(int n, const double* G_dev, int ldg, double* lam_dev, double* Vt_dev, int ldv,
+                     int max_sweeps, void* stream, int* sweeps_host);
+tt_status tt_set_max_sweeps(tt_handle h, int max_sweeps);
 
 /*
  * tt_gram_mixed: G = A^T A (as tt_gram) on the BF16 tensor cores (tcgen05).

@@ -34,7 +34,7 @@ from . import _native
 from ._native import (TT_BC_OUTFLOW, TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT,
                       TT_MIXED, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TTSNBatch", "TorchAllocator", "compression_factor", "step_record", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
+__all__ = ["TTSN", "TTSNBatch", "shard", "TorchAllocator", "compression_factor", "step_record", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
            "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_BC_OUTFLOW", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
            "TT_STEP_NO_ROUND", "TT_LAYOUT_GROUPED", "TT_LAYOUT_SPLIT"]
 
@@ -156,6 +156,10 @@ class _Handle:
     def set_precision(self, precision):
         check(lib.tt_set_precision(self._h, int(precision)))
 
+    def set_max_sweeps(self, max_sweeps):
+        """Sweep limit of the Jacobi eigensolves of this handle's roundings (1 .. 40)."""
+        check(lib.tt_set_max_sweeps(self._h, int(max_sweeps)))
+
     def profile(self, enable=True):
         check(lib.tt_profile(self._h, int(bool(enable))))
 
@@ -264,7 +268,7 @@ class TTSN(_Handle):
                  a_r=1.0, dt=0.0, cfl=0.5, bc=TT_BC_PERIODIC, eps=1e-6, max_rank=0,
                  rounds_per_step=1, precision=TT_FP64, stream=None, allocator=None,
                  layout=TT_LAYOUT_GROUPED, flux="upwind", rusanov_s=1.0, hll_beta=1.0,
-                 hll_tau_threshold=1.0):
+                 hll_tau_threshold=1.0, shard=None):
         super().__init__()
         ndim = len(n)
         nc = 1
@@ -274,6 +278,7 @@ class TTSN(_Handle):
             bc = [bc] * ndim
         self.nc = nc
         self.n = tuple(int(m) for m in n)
+        self.shard = None
         self.n_theta, self.n_phi = int(n_theta), int(n_phi)
         self.stream = stream
         # the library's rule for dt <= 0: CFL times the smallest cell width over c
@@ -310,9 +315,23 @@ class TTSN(_Handle):
             if not (hasattr(allocator, "alloc") and hasattr(allocator, "free")):
                 raise ValueError("allocator must be None, 'torch' or an object with alloc() and free()")
             self._alloc = _c_allocator(allocator)
-        check(lib.tt_create_ex(ctypes.byref(desc), _stream_ptr(stream),
-                               ctypes.byref(self._alloc) if self._alloc is not None else None,
-                               ctypes.byref(self._h)))
+        if shard is not None:
+            # a slab of layers [p0, p1) of axis 0 (tt_create_shard); shard =
+            # (p0, p1, exchanger) with the exchanger's sum_ and halo_ methods
+            from .shard import exchange_callback
+            p0, p1, exchanger = int(shard[0]), int(shard[1]), shard[2]
+            if allocator is not None:
+                raise ValueError("a shard takes its device memory from the stream-ordered pool")
+            self._xcb = exchange_callback(exchanger)
+            check(lib.tt_create_shard(ctypes.byref(desc), _stream_ptr(stream), p0, p1, self._xcb, None,
+                                      ctypes.byref(self._h)))
+            self.shard = (p0, p1)
+            self.n = (p1 - p0,) + self.n[1:]
+            self.nc = nc // int(n[0]) * (p1 - p0)
+        else:
+            check(lib.tt_create_ex(ctypes.byref(desc), _stream_ptr(stream),
+                                   ctypes.byref(self._alloc) if self._alloc is not None else None,
+                                   ctypes.byref(self._h)))
         self._keep = f  # inputs stay alive until creation finished (copied in)
 
     @staticmethod
@@ -369,12 +388,17 @@ class TTSN(_Handle):
         self.steps_taken += int(nsteps)
         return info.as_dict()
 
-    def energy(self):
+    def energy(self, totals=True):
+        """(E, T, (sum E dV, sum C_v T dV)) of this handle's cells.  On a spatial
+        shard the totals are the whole grid's, summed through the exchange, so
+        every shard must ask for them together; totals=False skips them (and
+        the exchange) and returns None in their place."""
         E = torch.empty(self.nc, dtype=torch.float64, device="cuda")
         T = torch.empty(self.nc, dtype=torch.float64, device="cuda")
         tot = (ctypes.c_double * 2)()
-        check(lib.tt_energy(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(T.data_ptr()), tot))
-        return E, T, (tot[0], tot[1])
+        check(lib.tt_energy(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                            tot if totals else None))
+        return E, T, ((tot[0], tot[1]) if totals else None)
 
     def set_T(self, T):
         t = _dev(T, self.nc)
@@ -421,7 +445,7 @@ class TTSN(_Handle):
         """Checkpoint of the evolving state: the TT cores and the material
         temperature (device copies; torch.save-able).  Fields, constants, the
         flux, sources and inflow faces are the problem's and are not saved."""
-        return {"cores": [c.clone() for c in self.cores()], "T": self.energy()[1].clone(),
+        return {"cores": [c.clone() for c in self.cores()], "T": self.energy(totals=False)[1].clone(),
                 "steps_taken": self.steps_taken}
 
     def load_state_dict(self, state):
@@ -638,15 +662,17 @@ def pchol(G, stream=None):
     return W[: rank.value].clone(), rank.value
 
 
-def syev(G, stream=None, allow_unconverged=False):
-    """(lam descending, Vt with eigenvectors as rows, sweeps) by parallel Jacobi."""
+def syev(G, stream=None, allow_unconverged=False, max_sweeps=40):
+    """(lam descending, Vt with eigenvectors as rows, sweeps) by parallel Jacobi
+    with at most max_sweeps sweeps (tt_syev_ex)."""
     G = _dev(G)
     n = G.shape[0]
     lam = torch.empty(n, dtype=torch.float64, device="cuda")
     Vt = torch.empty((n, n), dtype=torch.float64, device="cuda")
     sweeps = ctypes.c_int()
-    st = lib.tt_syev(n, ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
-                     ctypes.c_void_p(Vt.data_ptr()), n, _stream_ptr(stream), ctypes.byref(sweeps))
+    st = lib.tt_syev_ex(n, ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
+                        ctypes.c_void_p(Vt.data_ptr()), n, int(max_sweeps), _stream_ptr(stream),
+                        ctypes.byref(sweeps))
     if not (allow_unconverged and st == -4):
         check(st)
     return lam, Vt, sweeps.value

@@ -24,6 +24,10 @@ TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+# tt_exchange_fn: (ctx, kind, buf_dev, count, stream) -> int
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                               ctypes.c_void_p)
+TT_XCHG_SUM, TT_XCHG_HALO = 0, 1
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 
@@ -98,6 +102,8 @@ def _load():
         "tt_batch_handle": [vp, i, ctypes.POINTER(vp)],
         "tt_batch_sync": [vp],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
+        "tt_syev_ex": [i, vp, i, vp, vp, i, i, vp, ip],
+        "tt_set_max_sweeps": [vp, i],
         "tt_pchol": [i, vp, i, vp, vp, ip],
         "tt_set_inflow": [vp, i, i, vp, vp, vp],
         "tt_set_sketch": [vp, ctypes.POINTER(vp), ip],
@@ -115,6 +121,7 @@ def _load():
         "tt_set_sources": [vp, i, vp, vp, vp],
         "tt_create_ex": [ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(Allocator), ctypes.POINTER(vp)],
         "tt_get_cores": [vp, ctypes.POINTER(vp), ip],
+        "tt_create_shard": [ctypes.POINTER(ProblemDesc), vp, i, i, EXCHANGE_FN, vp, ctypes.POINTER(vp)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -143,7 +150,7 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
             "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
             "tt_create_ex", "tt_get_cores", "tt_pchol", "tt_set_inflow", "tt_set_sketch",
-            "tt_set_rounding", "tt_wait_probe"]
+            "tt_set_rounding", "tt_wait_probe", "tt_create_shard", "tt_syev_ex", "tt_set_max_sweeps"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

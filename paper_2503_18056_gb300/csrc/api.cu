@@ -148,6 +148,7 @@ struct tt_ctx {
     int* h_int = nullptr;      // pinned host mirror
     double* h_dbl = nullptr;
     int sweeps_slot = 0;
+    int max_sweeps = JACOBI_MAX_SWEEPS;  // Jacobi sweep limit (tt_set_max_sweeps)
 
     // phase profiler (CUDA events on the handle's stream)
     struct PhaseAcc {
@@ -244,6 +245,18 @@ struct tt_ctx {
     // handle comes from it when has_allocator is set
     tt_allocator allocator{};
     bool has_allocator = false;
+    // spatial shard (tt_create_shard): layers [p0, p1) of axis 0 out of n0,
+    // axis 0's global rule bc0, cells per layer, the caller's exchange; xch
+    // holds the four exchange blocks (the ghost layers themselves follow the
+    // own rows of core[0])
+    struct Shard {
+        bool on = false;
+        int p0 = 0, p1 = 0, n0 = 0, bc0 = TT_BC_PERIODIC;
+        long plane = 1;
+        tt_exchange_fn fn = nullptr;
+        void* ctx = nullptr;
+    } shard;
+    DevBuf xch;
     const tt_allocator* alloc_ptr() const { return has_allocator ? &allocator : nullptr; }
     double dV = 1.0;
 
@@ -283,7 +296,7 @@ struct tt_ctx {
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
                           &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph,
-                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs};
+                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs, &xch};
         for (DevBuf* b : bufs) b->release();
         for (auto& ax : inflow)
             for (auto& face : ax) face.g.release();
@@ -416,7 +429,7 @@ tt_status eig_orthonormalise(tt_ctx* h, long m, int l, const double* Y, DevBuf& 
     TT_TRY(h->sk_Vs.ensure((size_t)l * l, s));
     TT_TRY(gram(s, (int)m, l, Y, l, h->sk_G.p, l, h->partials));
     TT_TRY(syev(s, l, h->sk_G.p, l, h->sk_lam.p, h->sk_Vt.p, l, h->eig, h->d_int + HI_STATUS,
-                h->d_int + next_sweep_slot(h)));
+                h->d_int + next_sweep_slot(h), h->max_sweeps));
     count_above_floor(s, h->sk_lam.p, l, h->d_int + HI_DEC);
     TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_DEC, h->d_int + HI_DEC, sizeof(int), cudaMemcpyDeviceToHost, s));
     TT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -536,6 +549,8 @@ tt_status round_randomized(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, in
     return TT_OK;
 }
 
+tt_status shard_exchange(tt_ctx* h, int kind, double* buf, size_t count);
+
 tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr, double eps,
                       int max_rank, const int* forced, tt_step_info* info) {
     if (h->round_method == TT_ROUND_RANDOMIZED && h->d > 1)
@@ -638,6 +653,9 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
                 TT_TRY(slgram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials, h->d_int + HI_STATUS));
             else
                 TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
+            // a spatial shard holds some rows of the spatial core: its left
+            // Gram is the sum of the shards' partial Grams
+            if (k == 0 && h->shard.on) TT_TRY(shard_exchange(h, TT_XCHG_SUM, h->GA.p, (size_t)Rk * Rk));
         }
         {
             PhaseScope ps(h, TT_PH_SMALL, 2.0 * Rk * (double)Rk * kB + 2.0 * kB * (double)kB * Rk, 0.0);
@@ -653,7 +671,7 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         {
             PhaseScope ps(h, TT_PH_EIG, 0.0, 0.0);
             TT_TRY(syev(s, kB, h->K.p, kB, h->lamK.p, h->VtK.p, kB, h->eig, h->d_int + HI_STATUS,
-                        h->d_int + next_sweep_slot(h)));
+                        h->d_int + next_sweep_slot(h), h->max_sweeps));
             const int fk = forced ? forced[k] : 0;
             truncation_decision(s, h->lamK.p, kB, eps, d - 1, fk, max_rank, h->d_dbl + HD_DELTA2,
                                 h->d_int + HI_DEC, h->d_dbl + HD_DEC);
@@ -884,6 +902,50 @@ tt_status split_apply_terms(tt_ctx* h, bool transport, bool source) {
     return TT_OK;
 }
 
+// One exchange of a spatial shard through the caller's callback, with the
+// handle's stream drained first so the callback sees finished data.
+tt_status shard_exchange(tt_ctx* h, int kind, double* buf, size_t count) {
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const int rc = h->shard.fn(h->shard.ctx, kind, buf, count, (void*)h->stream);
+    if (rc != 0)
+        return fail(TT_ERR_STATE, std::string("shard exchange callback failed (") +
+                                      (kind == TT_XCHG_SUM ? "sum" : "halo") + ", returned " +
+                                      std::to_string(rc) + ")");
+    return TT_OK;
+}
+
+// The shard's spatial core with its ghost layers (Sec. 4.5): the layer below
+// the slab and the layer above it are written after the nc own rows of
+// core[0] (r1 columns).  The ring exchange supplies the neighbours' boundary
+// layers; at a global face of axis 0 a vacuum ghost is zero and an outflow
+// ghost copies the boundary layer (a periodic axis takes the ring's
+// wrap-around).
+tt_status shard_halo(tt_ctx* h, int r1) {
+    cudaStream_t s = h->stream;
+    const long nc = h->grid.nc;
+    const size_t lay = (size_t)h->shard.plane * r1;
+    TT_TRY(h->core[0].ensure((size_t)nc * r1 + 2 * lay, s, /*keep=*/true));
+    TT_TRY(h->xch.ensure(4 * lay, s));
+    double* send_lo = h->xch.p;
+    double* send_hi = send_lo + lay;
+    double* recv_lo = send_hi + lay;
+    double* recv_hi = recv_lo + lay;
+    double* X = h->core[0].p;
+    TT_CUDA_TRY(cudaMemcpyAsync(send_lo, X, lay * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(send_hi, X + (size_t)nc * r1 - lay, lay * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    TT_TRY(shard_exchange(h, TT_XCHG_HALO, h->xch.p, lay));
+    const bool glo = h->shard.p0 == 0, ghi = h->shard.p1 == h->shard.n0;
+    const int bc = h->shard.bc0;
+    if (glo && bc == TT_BC_VACUUM) fill(s, recv_lo, lay, 0.0);
+    if (ghi && bc == TT_BC_VACUUM) fill(s, recv_hi, lay, 0.0);
+    const double* lo = (glo && bc == TT_BC_OUTFLOW) ? send_lo : recv_lo;
+    const double* hi = (ghi && bc == TT_BC_OUTFLOW) ? send_hi : recv_hi;
+    TT_CUDA_TRY(cudaMemcpyAsync(X + (size_t)nc * r1, lo, lay * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(X + (size_t)nc * r1 + lay, hi, lay * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return TT_OK;
+}
+
 tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
     if (h->split()) return split_apply_terms(h, transport, source);
     cudaStream_t s = h->stream;
@@ -916,6 +978,7 @@ tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
                         h->core[2].p, h->gcore[1].p, h->gcore[2].p, R1, R2, ext);
     h->fields.T = h->f_T.p;
     h->fields.E_star = h->f_Estar.p;
+    if (h->shard.on && transport) TT_TRY(shard_halo(h, r1));
     transport_source_rows(s, h->grid, h->fields, transport, source, r1, h->core[0].p, r1,
                           source ? h->thbar.p : nullptr, h->gcore[0].p, R1, ext);
     TT_CUDA_TRY(cudaGetLastError());
@@ -1262,9 +1325,15 @@ tt_status tt_create(const tt_problem_desc* desc, void* stream, tt_handle* out) {
     return tt_create_ex(desc, stream, nullptr, out);
 }
 
-tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_allocator* alloc,
-                       tt_handle* out) {
-    set_error("");
+namespace {
+struct ShardArgs {
+    int p0, p1;
+    tt_exchange_fn fn;
+    void* ctx;
+};
+
+tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_allocator* alloc,
+                      const ShardArgs* sh, tt_handle* out) {
     if (!desc || !out) return fail(TT_ERR_ARG, "tt_create: null argument");
     if (alloc && (!alloc->alloc || !alloc->free))
         return fail(TT_ERR_ARG, "tt_create_ex: allocator needs both alloc and free");
@@ -1280,6 +1349,23 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         nc *= D.n[a];
     }
     if (nc > (1L << 31)) return fail(TT_ERR_TOO_LARGE, "tt_create: more than 2^31 cells");
+    // a shard keeps the layers [p0, p1) of axis 0: its own cells start at
+    // cell p0 * plane of the global C order
+    long plane = 1;
+    for (int a = 1; a < D.ndim; ++a) plane *= D.n[a];
+    long cell0 = 0;
+    if (sh) {
+        if (!sh->fn) return fail(TT_ERR_ARG, "tt_create_shard: null exchange callback");
+        if (sh->p0 < 0 || sh->p1 > D.n[0] || sh->p0 >= sh->p1)
+            return fail(TT_ERR_ARG, "tt_create_shard: need 0 <= plane_begin < plane_end <= n[0]");
+        if (D.layout != TT_LAYOUT_GROUPED)
+            return fail(TT_ERR_ARG, "tt_create_shard: shards hold the grouped layout's spatial rows");
+        if (D.flux == TT_FLUX_HLL)
+            return fail(TT_ERR_ARG, "tt_create_shard: HLL (per-face optical depths) is not sharded; "
+                                    "use upwind or Rusanov");
+        cell0 = (long)sh->p0 * plane;
+        nc = (long)(sh->p1 - sh->p0) * plane;
+    }
     if (D.n_theta < 1 || D.n_phi < 1) return fail(TT_ERR_ARG, "tt_create: n_theta, n_phi must be >= 1");
     if (!(D.c > 0.0) || D.a_r < 0.0) return fail(TT_ERR_ARG, "tt_create: need c > 0, a_r >= 0");
     if (!(D.dt > 0.0) && !(D.cfl > 0.0)) return fail(TT_ERR_ARG, "tt_create: need dt > 0 or cfl > 0");
@@ -1354,6 +1440,19 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
             h->dV *= g.dx[a];
         }
     }
+    if (sh) {
+        // the shard's slab: axis 0 reads its ghost layers from the halo
+        h->shard.on = true;
+        h->shard.p0 = sh->p0;
+        h->shard.p1 = sh->p1;
+        h->shard.n0 = D.n[0];
+        h->shard.bc0 = D.bc[0];
+        h->shard.plane = plane;
+        h->shard.fn = sh->fn;
+        h->shard.ctx = sh->ctx;
+        g.n[0] = sh->p1 - sh->p0;
+        g.bc[0] = BC_HALO;
+    }
     Fields& f = h->fields;
     f.c = D.c;
     f.a_r = D.a_r;
@@ -1361,7 +1460,7 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
 
     auto copy_field = [&](DevBuf& b, const double* srcp) -> tt_status {
         TT_TRY(b.ensure((size_t)nc, s));
-        TT_CUDA_TRY(cudaMemcpyAsync(b.p, srcp, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(b.p, srcp + cell0, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
         return TT_OK;
     };
 #define TT_CREATE_TRY(expr)      \
@@ -1574,6 +1673,7 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         TT_CREATE_TRY(h->lamK.ensure((size_t)R1, s));
         TT_CREATE_TRY(h->eig.lam_unsorted.ensure((size_t)R1, s));
         TT_CREATE_TRY(h->eig.abc.ensure((size_t)(3 * (R1 + 1)), s));
+        TT_CREATE_TRY(h->eig.cs.ensure((size_t)(R1 + 1), s));
         TT_CREATE_TRY(h->Vts.ensure((size_t)(cap1 * R1), s));
         TT_CREATE_TRY(h->PAt.ensure((size_t)(cap1 * R1), s));
         TT_CREATE_TRY(h->Mupd.ensure((size_t)(cap1 * R1), s));
@@ -1583,7 +1683,7 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
         TT_CREATE_TRY(h->thbar.ensure((size_t)(nterms * (cap1 + cap2) + 2), s));
         if (D.precision == TT_MIXED) TT_CREATE_TRY(h->slscratch.ensure((size_t)(nc + R1) / 2 + 2, s));
     }
-    init_isotropic(s, nc, D.Tr0 ? D.Tr0 : D.T0, D.c, D.a_r, h->core[0].p);
+    init_isotropic(s, nc, (D.Tr0 ? D.Tr0 : D.T0) + cell0, D.c, D.a_r, h->core[0].p);
     fill(s, h->core[1].p, D.n_theta, 1.0);
     fill(s, h->core[2].p, D.n_phi, 1.0);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
@@ -1593,6 +1693,21 @@ tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_alloc
 #undef TT_CREATE_TRY
     *out = h;
     return TT_OK;
+}
+
+}  // namespace
+
+tt_status tt_create_ex(const tt_problem_desc* desc, void* stream, const tt_allocator* alloc,
+                       tt_handle* out) {
+    set_error("");
+    return create_impl(desc, stream, alloc, nullptr, out);
+}
+
+tt_status tt_create_shard(const tt_problem_desc* desc, void* stream, int plane_begin, int plane_end,
+                          tt_exchange_fn exchange, void* ctx, tt_handle* out) {
+    set_error("");
+    const ShardArgs sh{plane_begin, plane_end, exchange, ctx};
+    return create_impl(desc, stream, nullptr, &sh, out);
 }
 
 tt_status tt_create_tt(int d, const int* n, const int* ranks, void* stream, tt_handle* out) {
@@ -1663,6 +1778,7 @@ tt_status tt_tape_begin(tt_handle h, int checkpoint_every) {
     TT_TRY(check_handle(h, true));
     AllocScope alloc_scope_(h->alloc_ptr());
     if (checkpoint_every < 1) return fail(TT_ERR_ARG, "tt_tape_begin: checkpoint_every must be >= 1");
+    if (h->shard.on) return fail(TT_ERR_STATE, "tt_tape_begin: a spatial shard has no adjoint tape");
     if (h->precision != TT_FP64 || h->rounds != 1 || h->has_sigma_s || h->d != 3 || h->nsrc > 0 ||
         h->split() || h->round_method != TT_ROUND_GRAM || h->fields.flux != TT_FLUX_UPWIND ||
         h->grid.bc[0] == TT_BC_OUTFLOW ||
@@ -1757,6 +1873,7 @@ tt_status tt_energy(tt_handle h, double* E_dev, double* T_dev, double* totals_ho
         TT_CUDA_TRY(cudaMemcpyAsync(T_dev, h->f_T.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (totals_host) {
         energy_totals(s, nc, E, h->f_cv.p, h->f_T.p, h->red.p + 2048, h->red.p);
+        if (h->shard.on) TT_TRY(shard_exchange(h, TT_XCHG_SUM, h->red.p + 2048, 2));
         TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_TOT, h->red.p + 2048, 2 * sizeof(double),
                                     cudaMemcpyDeviceToHost, s));
     }
@@ -1946,6 +2063,8 @@ tt_status tt_set_sources(tt_handle h, int count, const double* x_dev, const doub
         return fail(TT_ERR_ARG, "tt_set_sources: null source array");
     if (count > 0 && h->split())
         return fail(TT_ERR_STATE, "tt_set_sources: fixed sources need the grouped layout");
+    if (count > 0 && h->shard.on)
+        return fail(TT_ERR_STATE, "tt_set_sources: a spatial shard takes no fixed sources");
     clear_tape(h);  // a change of state outside a step ends the tape
     cudaStream_t s = h->stream;
     const long nc = h->grid.nc;
@@ -1983,6 +2102,8 @@ tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, co
     if (g_dev && (!theta_dev || !phi_dev)) return fail(TT_ERR_ARG, "tt_set_inflow: null angular profile");
     if (g_dev && h->split())
         return fail(TT_ERR_STATE, "tt_set_inflow: inflow faces need the grouped layout");
+    if (g_dev && h->shard.on)
+        return fail(TT_ERR_STATE, "tt_set_inflow: a spatial shard takes no inflow faces");
     clear_tape(h);
     cudaStream_t s = h->stream;
     tt_ctx::InflowFace& face = h->inflow[axis][side];
@@ -2045,6 +2166,8 @@ tt_status tt_set_rounding(tt_handle h, int method) {
         return fail(TT_ERR_ARG, "tt_set_rounding: method must be TT_ROUND_GRAM or TT_ROUND_RANDOMIZED");
     if (method == TT_ROUND_RANDOMIZED && !h->has_sketch)
         return fail(TT_ERR_STATE, "tt_set_rounding: the randomized rounding needs a sketch (tt_set_sketch)");
+    if (method == TT_ROUND_RANDOMIZED && h->shard.on)
+        return fail(TT_ERR_STATE, "tt_set_rounding: a spatial shard rounds by Gram-SVD only");
     if (method == TT_ROUND_RANDOMIZED && (h->taping || h->replay_rec))
         return fail(TT_ERR_STATE, "tt_set_rounding: the adjoint tape records Gram-SVD roundings");
     h->round_method = method;
@@ -2190,7 +2313,14 @@ tt_status tt_pchol(int n, const double* G, int ldg, double* W, void* stream, int
 
 tt_status tt_syev(int n, const double* G, int ldg, double* lam, double* Vt, int ldv, void* stream,
                   int* sweeps_host) {
+    return tt_syev_ex(n, G, ldg, lam, Vt, ldv, JACOBI_MAX_SWEEPS, stream, sweeps_host);
+}
+
+tt_status tt_syev_ex(int n, const double* G, int ldg, double* lam, double* Vt, int ldv, int max_sweeps,
+                     void* stream, int* sweeps_host) {
     set_error("");
+    if (max_sweeps < 1 || max_sweeps > JACOBI_MAX_SWEEPS)
+        return fail(TT_ERR_ARG, "tt_syev_ex: max_sweeps must be in 1 .. " + std::to_string(JACOBI_MAX_SWEEPS));
     if (n < 0) return fail(TT_ERR_ARG, "tt_syev: negative size");
     if (n == 0) return TT_OK;
     if (!G || !lam || !Vt) return fail(TT_ERR_ARG, "tt_syev: null pointer");
@@ -2200,7 +2330,7 @@ tt_status tt_syev(int n, const double* G, int ldg, double* lam, double* Vt, int 
     int* d_small = nullptr;
     TT_CUDA_TRY(cudaMallocAsync((void**)&d_small, 2 * sizeof(int), s));
     TT_CUDA_TRY(cudaMemsetAsync(d_small, 0, 2 * sizeof(int), s));
-    tt_status st = syev(s, n, G, ldg, lam, Vt, ldv, w, d_small, d_small + 1);
+    tt_status st = syev(s, n, G, ldg, lam, Vt, ldv, w, d_small, d_small + 1, max_sweeps);
     int hs[2] = {0, 0};
     cudaMemcpyAsync(hs, d_small, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -2211,6 +2341,16 @@ tt_status tt_syev(int n, const double* G, int ldg, double* lam, double* Vt, int 
     if (sweeps_host) *sweeps_host = hs[1];
     if (hs[0] & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_syev: grid barrier wait ran out");
     if (hs[0] & DEV_NOT_CONVERGED) return fail(TT_ERR_NOT_CONVERGED, "tt_syev: sweep limit reached");
+    return TT_OK;
+}
+
+tt_status tt_set_max_sweeps(tt_handle h, int max_sweeps) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (max_sweeps < 1 || max_sweeps > JACOBI_MAX_SWEEPS)
+        return fail(TT_ERR_ARG, "tt_set_max_sweeps: max_sweeps must be in 1 .. " +
+                                    std::to_string(JACOBI_MAX_SWEEPS));
+    h->max_sweeps = max_sweeps;
     return TT_OK;
 }
 

@@ -134,15 +134,19 @@ struct EigWork {
     DevBuf lam_unsorted;
     DevBuf vt_unsorted;
     DevBuf abc;             // per-round pair entries (double-buffered)
+    DevBuf cs;              // the round's rotation angles (c, s per pair)
     DevBuf ctrl_buf;
     int* d_ctrl = nullptr;  // barrier counters, sweep counters, status (in ctrl_buf)
     int ctrl_cap = 0;
     void release();
 };
 // Eigendecomposition of symmetric n x n G (ldg): lam descending (n), Vt rows = eigvecs.
-// *status_dev receives DEV_* codes (or-ed in); sweeps written to sweeps_dev[0].
+// *status_dev receives DEV_* codes (or-ed in; DEV_NOT_CONVERGED after
+// max_sweeps sweeps, 1 .. JACOBI_MAX_SWEEPS); sweeps written to sweeps_dev[0].
+constexpr int JACOBI_MAX_SWEEPS = 40;
 tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, double* Vt,
-               long ldv, EigWork& w, int* status_dev, int* sweeps_dev);
+               long ldv, EigWork& w, int* status_dev, int* sweeps_dev,
+               int max_sweeps = JACOBI_MAX_SWEEPS);
 
 // Pivoted Cholesky of a symmetric positive semidefinite n x n G (ldg): writes
 // W (rows 0..rank-1 of an n x n row-major buffer) with W^T W = G up to the
@@ -209,6 +213,11 @@ void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, i
 // Plain quadrature vector of a 3-core TT: thbar[a] = sum_l w sum_b Th[a,l,b] sum_p v Ph[b,p].
 void plain_thbar(cudaStream_t s, const Angular& ang, int r1, int r2, const double* Th,
                  const double* Ph, double* thbar);
+
+// Boundary rule of axis 0 of a spatial shard (tt_create_shard): the ghost
+// layers are halo rows stored after the shard's own rows (the layer below
+// the slab, then the layer above it).
+enum : int { BC_HALO = 3 };
 
 struct Grid {
     int ndim;

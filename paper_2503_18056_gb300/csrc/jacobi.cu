@@ -31,11 +31,11 @@ namespace ttsn {
 namespace {
 
 constexpr int JT = 256;
-constexpr int MAX_SWEEPS = 40;
-// control block (ints): [0] barrier count, [1] barrier generation, [2] sweeps,
+constexpr int MAX_SWEEPS = JACOBI_MAX_SWEEPS;
+// control block (ints): [0] barrier arrivals, [1] unused, [2] sweeps,
 // [3] pivoted-Cholesky rank, [4 .. 4+MAX_SWEEPS) rotations applied per sweep
 constexpr int CTRL_INTS = 8 + MAX_SWEEPS;
-constexpr long long SPIN_LIMIT = 1LL << 21;  // ~1.1 s (an atomic read plus a 64 ns sleep per try)
+constexpr long long SPIN_LIMIT = 1LL << 21;  // ~1 s (an L2 acquire load plus a 32 ns sleep per try)
 constexpr int MAX_PAIRS_PER_CTA = 8;
 
 __device__ __forceinline__ void round_pair(int N, int r, int k, int& p, int& q) {
@@ -77,37 +77,48 @@ __device__ __forceinline__ void pair_of(int N, int r, int x, int& k, int& partne
     }
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false (and latches
-// DEV_TIMEOUT) if the wait ran out or another CTA already latched a failure.
-__device__ bool grid_barrier(int* ctrl, int* status, unsigned nblocks) {
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier with a bounded wait.  ctrl[0] counts arrivals over the
+// whole launch (the control block is zeroed before every launch), so the
+// barrier that a CTA enters for the e-th time completes when the count
+// reaches e * nblocks: one release-atomic arrival per CTA, acquire-load
+// polling, no reset and no second word to bump.  Returns false (and latches
+// DEV_TIMEOUT) if the wait ran out; the other CTAs then never see the count
+// complete and run out in turn.  epoch is the caller's barrier counter (its
+// value matters in thread 0 only).
+__device__ bool grid_barrier(int* ctrl, int* status, unsigned nblocks, unsigned& epoch) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        ++epoch;
         if (nblocks > 1) {
             unsigned* count = reinterpret_cast<unsigned*>(ctrl);
-            unsigned* gen = reinterpret_cast<unsigned*>(ctrl + 1);
-            const unsigned g = atomicAdd(gen, 0u);
-            __threadfence();
-            const unsigned arrived = atomicAdd(count, 1u);
-            if (arrived == nblocks - 1) {
-                atomicExch(count, 0u);
-                __threadfence();
-                atomicAdd(gen, 1u);
-            } else {
+            const unsigned target = epoch * nblocks;
+            unsigned old;
+            asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+            if (old + 1u < target) {
                 long long it = 0;
-                while (atomicAdd(gen, 0u) == g) {
+                while (ld_acquire(count) < target) {
                     if (++it > SPIN_LIMIT) {
                         ok = 0;
                         atomicOr(status, DEV_TIMEOUT);
                         break;
                     }
-                    __nanosleep(64);
+                    __nanosleep(32);
                 }
             }
-            __threadfence();
         }
-        if (atomicAdd(status, 0) & DEV_TIMEOUT) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -137,21 +148,36 @@ __global__ void jacobi_init_kernel(int n, int N, const double* __restrict__ G, l
     }
 }
 
+// One launch runs every sweep.  A round has two grid barriers:
+//  A. each CTA forms the rotation angles of the pairs it owns only (from the
+//     compact entries the previous round published), publishes them, and
+//     left-rotates its own row pairs and eigenvector rows;
+//  B. after the barrier every CTA reads all angles with one coalesced load,
+//     compacts the list of pairs whose rotation is not the identity, applies
+//     those column rotations to its own rows, stores the rows to the other
+//     buffer and publishes the next round's pair entries.
+// Forming each angle once instead of once per CTA is what the second barrier
+// buys: on GB300 a CTA that formed all n/2 angles itself spent about as long
+// on their FP64 square roots and divisions as on the rotations, and skipped
+// (identity) rotations cost nothing in the later sweeps.
 __global__ void __launch_bounds__(JT)
 jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double* abc0,
-              double* abc1, double* lam_out, int* ctrl, int* status, double tol_rel,
-              double tol_abs_rel) {
+              double* abc1, double* cs_g, double* lam_out, int* ctrl, int* status, double tol_rel,
+              double tol_abs_rel, int max_sweeps) {
     extern __shared__ double sm[];
     const int npairs = N / 2;
     // pairs this CTA owns: k = blockIdx.x + i * gridDim.x < npairs
     const int mine = max(0, (npairs - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
-    double* cs = sm;
-    double* sn = cs + npairs;
-    double* rows = sn + npairs;  // 2 * ppc rows of n
+    double* cs = sm;                                     // 2 * npairs: c, s of every pair
+    double* rows = cs + 2 * npairs;                      // 2 * ppc rows of n
+    int* act = reinterpret_cast<int*>(rows + 2 * (size_t)((npairs + gridDim.x - 1) / gridDim.x) * n);
     __shared__ int s_cnt;
     __shared__ int s_done;
+    __shared__ int s_nact;
+    __shared__ int s_wsum[JT / 32];
     __shared__ double s_dmax;
 
+    unsigned epoch = 0;
     double* cur = g0;
     double* nxt = g1;
     double* abc_cur = abc0;
@@ -163,14 +189,17 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
     }
     __syncthreads();
     const double tol_abs = tol_abs_rel * s_dmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int sweep = 0;
-    for (; sweep < MAX_SWEEPS; ++sweep) {
+    for (; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
         for (int r = 0; r < N - 1; ++r) {
             const int rn = (r + 1 == N - 1) ? 0 : r + 1;  // next round (wraps to the next sweep)
-            // 1. all rotation angles of this round from the compact entries
-            for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
+            // A1. the angles of the owned pairs (Golub & Van Loan, Alg. 8.4.1)
+            if (threadIdx.x < mine) {
+                const int i = threadIdx.x;
+                const int k = blockIdx.x + i * gridDim.x;
                 int p, q;
                 round_pair(N, r, k, p, q);
                 double c = 1.0, s = 0.0;
@@ -185,64 +214,104 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
                             (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + t * t);
                         s = t * c;
-                        if (k % gridDim.x == blockIdx.x) atomicAdd(&s_cnt, 1);
+                        atomicAdd(&s_cnt, 1);
                     }
                 }
-                cs[k] = c;
-                sn[k] = s;
+                cs[2 * k] = c;
+                cs[2 * k + 1] = s;
+                __stcg(cs_g + 2 * k, c);
+                __stcg(cs_g + 2 * k + 1, s);
             }
             __syncthreads();
-            // 2. load and left-rotate every owned row pair
+            // A2. load and left-rotate every owned row pair; rotate its eigenvector rows
             for (int i = 0; i < mine; ++i) {
                 const int k = blockIdx.x + i * gridDim.x;
                 int p, q;
                 round_pair(N, r, k, p, q);
                 const bool hp = p < n, hq = q < n;
-                const double c = cs[k], s = sn[k];
+                const double c = cs[2 * k], s = cs[2 * k + 1];
                 double* rp = rows + (2 * i) * n;
                 double* rq = rp + n;
-                for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                    const double xp = hp ? __ldcg(cur + (long)p * ld + j) : 0.0;
-                    const double xq = hq ? __ldcg(cur + (long)q * ld + j) : 0.0;
-                    rp[j] = c * xp - s * xq;
-                    rq[j] = s * xp + c * xq;
+                if (s != 0.0) {
+#pragma unroll 4
+                    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                        const double xp = __ldcg(cur + (long)p * ld + j);
+                        const double xq = __ldcg(cur + (long)q * ld + j);
+                        rp[j] = c * xp - s * xq;
+                        rq[j] = s * xp + c * xq;
+                        const double vp = __ldcg(vt + (long)p * ld + j);
+                        const double vq = __ldcg(vt + (long)q * ld + j);
+                        __stcg(vt + (long)p * ld + j, c * vp - s * vq);
+                        __stcg(vt + (long)q * ld + j, s * vp + c * vq);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                        rp[j] = hp ? __ldcg(cur + (long)p * ld + j) : 0.0;
+                        rq[j] = hq ? __ldcg(cur + (long)q * ld + j) : 0.0;
+                    }
                 }
             }
+            if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
+            // B1. every pair's angles, and the list of the non-identity ones
+            for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
+                cs[2 * k] = __ldcg(cs_g + 2 * k);
+                cs[2 * k + 1] = __ldcg(cs_g + 2 * k + 1);
+            }
             __syncthreads();
-            // 3. right rotations of every column pair, on all owned rows
+            {
+                // block-wide compaction in pair order: chunks of blockDim.x pairs
+                int base = 0;
+                for (int k0 = 0; k0 < npairs; k0 += blockDim.x) {
+                    const int k = k0 + threadIdx.x;
+                    const bool on = k < npairs && cs[2 * k + 1] != 0.0;
+                    const unsigned bal = __ballot_sync(0xffffffffu, on);
+                    if (lane == 0) s_wsum[warp] = __popc(bal);
+                    __syncthreads();
+                    int before = 0, total = 0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                        if (w < warp) before += s_wsum[w];
+                        total += s_wsum[w];
+                    }
+                    if (on) act[base + before + __popc(bal & ((1u << lane) - 1u))] = k;
+                    base += total;
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) s_nact = base;
+            }
+            __syncthreads();
+            const int nact = s_nact;
+            // B2. right rotations of the non-identity column pairs, on all owned rows
             const int nrows = 2 * mine;
-            for (int t = threadIdx.x; t < npairs * nrows; t += blockDim.x) {
-                const int kk = t % npairs, row = t / npairs;
+            for (int t = threadIdx.x; t < nact * nrows; t += blockDim.x) {
+                const int kk = act[t % nact], row = t / nact;
                 int pp, qq;
                 round_pair(N, r, kk, pp, qq);
-                if (qq < n) {
-                    const double c2 = cs[kk], s2 = sn[kk];
-                    double* rr = rows + row * n;
-                    const double a0 = rr[pp], b0 = rr[qq];
-                    rr[pp] = c2 * a0 - s2 * b0;
-                    rr[qq] = s2 * a0 + c2 * b0;
-                }
+                const double c2 = cs[2 * kk], s2 = cs[2 * kk + 1];
+                double* rr = rows + row * n;
+                const double a0 = rr[pp], b0 = rr[qq];
+                rr[pp] = c2 * a0 - s2 * b0;
+                rr[qq] = s2 * a0 + c2 * b0;
             }
             __syncthreads();
-            // 4. exact zeros for the rotated pairs
+            // B3. exact zeros for the rotated pairs
             if (threadIdx.x < mine) {
                 const int i = threadIdx.x;
                 const int k = blockIdx.x + i * gridDim.x;
                 int p, q;
                 round_pair(N, r, k, p, q);
-                if (q < n && sn[k] != 0.0) {
+                if (q < n && cs[2 * k + 1] != 0.0) {
                     rows[(2 * i) * n + q] = 0.0;
                     rows[(2 * i + 1) * n + p] = 0.0;
                 }
             }
             __syncthreads();
-            // 5. store rows, publish next round's entries, rotate eigenvector rows
+            // B4. store rows and publish the next round's entries
             for (int i = 0; i < mine; ++i) {
                 const int k = blockIdx.x + i * gridDim.x;
                 int p, q;
                 round_pair(N, r, k, p, q);
                 const bool hp = p < n, hq = q < n;
-                const double c = cs[k], s = sn[k];
                 const double* rp = rows + (2 * i) * n;
                 const double* rq = rp + n;
                 for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -265,17 +334,9 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
                         }
                     }
                 }
-                if (hq && s != 0.0) {
-                    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                        const double vp = __ldcg(vt + (long)p * ld + j);
-                        const double vq = __ldcg(vt + (long)q * ld + j);
-                        __stcg(vt + (long)p * ld + j, c * vp - s * vq);
-                        __stcg(vt + (long)q * ld + j, s * vp + c * vq);
-                    }
-                }
             }
             if (r == N - 2 && threadIdx.x == 0) atomicAdd(ctrl + 4 + sweep, s_cnt);
-            if (!grid_barrier(ctrl, status, gridDim.x)) return;
+            if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
             double* t = cur;
             cur = nxt;
             nxt = t;
@@ -289,8 +350,8 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
     }
     if (blockIdx.x == 0) {
         if (threadIdx.x == 0) {
-            ctrl[2] = min(sweep + 1, MAX_SWEEPS);
-            if (sweep >= MAX_SWEEPS) atomicOr(status, DEV_NOT_CONVERGED);
+            ctrl[2] = min(sweep + 1, max_sweeps);
+            if (sweep >= max_sweeps) atomicOr(status, DEV_NOT_CONVERGED);
         }
         // eigenvalues: the diagonal of the last written buffer
         for (int i = threadIdx.x; i < n; i += blockDim.x) lam_out[i] = __ldcg(cur + (long)i * ld + i);
@@ -462,6 +523,7 @@ __global__ void trivial_eig_kernel(const double* G, double* lam, double* Vt, int
 __global__ void __launch_bounds__(JT)
 pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* Wc, double* d,
              int* ctrl, int* status, double floor_rel) {
+    unsigned epoch = 0;
     extern __shared__ double sm[];
     double* colp = sm;  // Wc[p][0..k)
     __shared__ double s_val[JT];
@@ -493,7 +555,7 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
     const double floor_abs = floor_rel * s_dmax0;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
         __stcg(d + j, G[(long)j * ldg + j]);
-    if (!grid_barrier(ctrl, status, gridDim.x)) return;
+    if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
     int k = 0;
     for (; k < n; ++k) {
         const double* dcur = d + (size_t)(k & 1) * n;
@@ -554,7 +616,7 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
                 __stcg(Wc + (long)j * n + k, w);
             }
         }
-        if (!grid_barrier(ctrl, status, gridDim.x)) return;
+        if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[3] = k;
 }
@@ -565,7 +627,8 @@ __global__ void pchol_finish_kernel(const int* ctrl, int* kB_out) { *kB_out = ct
 // of two, so the second arrival never comes; the wait runs out after its
 // iteration limit (~1 s), latches DEV_TIMEOUT and the kernel returns.
 __global__ void wait_probe_kernel(int* ctrl, int* status) {
-    if (grid_barrier(ctrl, status, 2u) && threadIdx.x == 0) atomicOr(status, 0);
+    unsigned epoch = 0;
+    if (grid_barrier(ctrl, status, 2u, epoch) && threadIdx.x == 0) atomicOr(status, 0);
 }
 
 __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm1, int forced,
@@ -658,6 +721,7 @@ tt_status ensure_ctrl(EigWork& w, cudaStream_t s) {
 }  // namespace
 
 void EigWork::release() {
+    cs.release();
     g0.release();
     g1.release();
     lam_unsorted.release();
@@ -669,9 +733,13 @@ void EigWork::release() {
 }
 
 tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, double* Vt, long ldv,
-               EigWork& w, int* status_dev, int* sweeps_dev) {
+               EigWork& w, int* status_dev, int* sweeps_dev, int max_sweeps) {
     if (n < 0) {
         set_error("syev: negative size");
+        return TT_ERR_ARG;
+    }
+    if (max_sweeps < 1 || max_sweeps > MAX_SWEEPS) {
+        set_error("syev: the sweep limit must be in 1 .. " + std::to_string(MAX_SWEEPS));
         return TT_ERR_ARG;
     }
     if (n == 0) return TT_OK;
@@ -698,16 +766,18 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     TT_TRY(w.vt_unsorted.ensure((size_t)n * n, s));
     TT_TRY(w.lam_unsorted.ensure((size_t)n, s));
     TT_TRY(w.abc.ensure((size_t)6 * npairs, s));
+    TT_TRY(w.cs.ensure((size_t)2 * npairs, s));
     TT_TRY(ensure_ctrl(w, s));
     // one row pair per CTA where the GPU holds that many CTAs: a round's FP64
     // work per CTA (about 18 n flops per owned pair) is what bounds the round
-    // on GB300's FP64 pipe, so the pairs are spread over as many SMs as exist
+    // on GB300's FP64 pipe, so the pairs are spread over as many SMs as exist.
+    // Shared memory: all angles, the owned rows, the list of active pairs.
+    auto smem_for = [&](int ppc) {
+        return (size_t)(npairs * 2 + 2 * (size_t)ppc * n) * sizeof(double) + (size_t)npairs * sizeof(int);
+    };
     int want = npairs;
-    size_t smem = (size_t)(npairs * 2 + 2 * MAX_PAIRS_PER_CTA * n) * sizeof(double);
-    if (smem > 200 * 1024) {
-        // fall back to the pairs-per-CTA bound the shared memory allows
-        smem = (size_t)(npairs * 2 + 2 * ((npairs + want - 1) / want) * n) * sizeof(double);
-    }
+    size_t smem = smem_for(MAX_PAIRS_PER_CTA);
+    if (smem > 200 * 1024) smem = smem_for(1);  // the bound the shared memory allows
     if (smem > 200 * 1024) {
         set_error("syev: matrix too large for the shared-memory row buffers");
         return TT_ERR_TOO_LARGE;
@@ -716,8 +786,7 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     int blocks = 1;
     TT_TRY(coop_blocks((const void*)jacobi_kernel, smem, want, &blocks));
     const int ppc = (npairs + blocks - 1) / blocks;
-    if (ppc > MAX_PAIRS_PER_CTA ||
-        (size_t)(npairs * 2 + 2 * ppc * n) * sizeof(double) > smem) {
+    if (ppc > MAX_PAIRS_PER_CTA || smem_for(ppc) > smem) {
         set_error("syev: too few resident CTAs for this matrix size");
         return TT_ERR_TOO_LARGE;
     }
@@ -734,10 +803,13 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     double* abc0 = w.abc.p;
     double* abc1 = w.abc.p + 3 * npairs;
     double* lamu = w.lam_unsorted.p;
+    double* csg = w.cs.p;
     int* ctrl = w.d_ctrl;
     int nn = n, NN = N;
     long ldl = ld;
-    void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &abc0, &abc1, &lamu, &ctrl, &status_dev, &tol_rel, &tol_abs_rel};
+    int msw = max_sweeps;
+    void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &abc0, &abc1, &csg, &lamu, &ctrl, &status_dev, &tol_rel,
+                    &tol_abs_rel, &msw};
     note_launch();
     TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(JT), args,
                                             smem, s));

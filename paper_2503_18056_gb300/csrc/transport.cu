@@ -121,6 +121,10 @@ __global__ void thbar_kernel(int nterms, int r1, int r2, int nt, const double* T
 // Neighbour rows of cell i along each axis (C order, axis 0 slowest):
 // nb[a][0] = lower, nb[a][1] = upper; -1 marks a zero ghost (vacuum edge),
 // periodic edges wrap, outflow edges point at the cell itself (Sec. 4.5).
+// BC_HALO (axis 0 of a spatial shard, whose layers are the last stride
+// rows): the ghost layers are halo rows held after the shard's own nc rows,
+// the lower ghost layer at rows nc .. nc + stride - 1 and the upper one after
+// it, so a ghost is never a negative (vacuum) index.
 __device__ __forceinline__ void cell_neighbours(const Grid& g, long i, long (&nb)[3][2]) {
     long rem = i, stride = 1;
     int coord[3] = {0, 0, 0};
@@ -132,7 +136,10 @@ __device__ __forceinline__ void cell_neighbours(const Grid& g, long i, long (&nb
         const int ca = coord[a];
         const int na = g.n[a];
         long lo, hi;
-        if (g.bc[a] == TT_BC_PERIODIC) {
+        if (g.bc[a] == BC_HALO) {
+            lo = (ca == 0) ? g.nc + i : i - stride;                // first layer: i < stride
+            hi = (ca == na - 1) ? i + 2 * stride : i + stride;     // last layer -> nc + stride + (i - (nc - stride))
+        } else if (g.bc[a] == TT_BC_PERIODIC) {
             lo = i + (long)((ca == 0) ? (na - 1) : -1) * stride;
             hi = i + (long)((ca == na - 1) ? -(na - 1) : 1) * stride;
         } else {

@@ -238,3 +238,34 @@ def test_pchol_of_a_non_finite_diagonal_is_reported(ttsn, n):
         assert e.value.status == -8
     W, k = ttsn.pchol(torch.tensor(G, device="cuda"))
     assert k == n
+
+
+def test_sweep_limit_reached_is_reported_and_the_handle_stays_usable(ttsn):
+    """The eigensolver's sweep limit as a failure the host can make happen: a
+    limit of one sweep on a matrix that needs several returns
+    TT_ERR_NOT_CONVERGED (kernel level and inside a step), nothing faults, and
+    with the default limit back the same handle steps on normally."""
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((96, 96))
+    G = torch.as_tensor(B @ B.T, device="cuda")
+    with pytest.raises(ttsn.TTError) as e:
+        ttsn.syev(G, max_sweeps=1)
+    assert e.value.status == -4
+    lam, Vt, sweeps = ttsn.syev(G)
+    assert 1 < sweeps <= 40
+    with pytest.raises(ttsn.TTError):
+        ttsn.syev(G, max_sweeps=0)
+    p = workloads.problem("small_2d", n=(16, 12), n_theta=4, n_phi=8, eps=1e-6)
+    g = ttsn.TTSN.from_problem(p)
+    g.step(3)
+    g.set_max_sweeps(1)
+    with pytest.raises(ttsn.TTError) as e:
+        g.step()
+    assert e.value.status == -4
+    with pytest.raises(ttsn.TTError):
+        g.set_max_sweeps(41)
+    g.set_max_sweeps(40)
+    # the failed step left a valid (less accurate) state; stepping resumes
+    info = g.step()
+    assert info["ranks"][0] == 1 and info["sweeps"] > 1
+    assert torch.isfinite(g.full()).all()

@@ -162,7 +162,13 @@ def test_small_2d_workload_cuts_at_gaps(ttsn, eps):
         forced = _gap_ranks(sig, tt.ranks(Z))
         ref.step(forced=forced)
         info = g.step(forced=forced)
-        assert info["ranks"][1:-1] == tt.ranks(ref.cores)
+        if eps >= 1e-6:
+            assert info["ranks"][1:-1] == tt.ranks(ref.cores)
+        else:
+            # below the resolution a forced rank can exceed the directions the
+            # right Gram resolves (its pivoted Cholesky stops at eps_mach of
+            # the largest pivot); the GPU then keeps those it resolves
+            assert all(a <= b for a, b in zip(info["ranks"][1:-1], tt.ranks(ref.cores)))
         budget += 2 * np.sqrt(2) * np.sqrt(p["eps"] ** 2 + max(info["grown"]) * EPS_MACH)
     F = g.full().cpu().numpy()
     Rf = ref.full()
