@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--line-source-steps", type=int, default=121,
                     help="timed steps of the line-source leg (0: to t = 1, 568 steps)")
     ap.add_argument("--no-randomized", action="store_true", help="skip the randomized-rounding companion run")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in split rule (no tt_autotune)")
     ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes", "schedule", "line_source"], default=None,
                     help="run only this companion leg and print its JSON (profiling)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
@@ -161,6 +162,15 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     p = workloads.problem(args.workload)
     stream = torch.cuda.Stream(device=dev)
+    tune = None
+    if not args.no_autotune:
+        # the products' split per (tiles, depth) bucket, measured on this GPU
+        # before anything is timed; every leg below runs with it
+        t_tune = time.perf_counter()
+        table = ttsn.autotune(stream=stream)
+        torch.cuda.synchronize()
+        tune = {"s": round(time.perf_counter() - t_tune, 2), "table": table,
+                "layout": "index floor(log2 tiles) * 22 + floor(log2 K); 0 = built-in rule"}
     with torch.cuda.stream(stream):
         g = ttsn.TTSN.from_problem(p, max_rank=p.get("max_rank", 0), stream=stream)
         init_cores = [c.clone() for c in g.cores()]
@@ -321,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
     beams = None
     if not args.no_beams:
         beams = run_beams(args, torch, ttsn, fp64_peak, mixed["bf16_peak"] if mixed else None)
-    res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches,
+    res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches, autotune=tune,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
                adjoint=adjoint, beams=beams, split=split, fluxes=fluxes, schedule=schedule, line_source=line_source,
                randomized=randomized)
@@ -668,6 +678,26 @@ def run_batch(args, torch, ttsn):
     torch.cuda.synchronize()
     dt_seq = time.perf_counter() - t1
     del seq
+    # the same K_b steps as captured steps: every problem's recorded step
+    # replayed as a CUDA graph on its own stream, sizes decided on the device,
+    # one synchronisation per problem per call
+    cap = ttsn.TTSNBatch(ps)
+    cap.set_graph(True)
+    cap.step(args.warmup)
+    for i, (cores, T0) in enumerate(init):
+        pr = cap.problem(i)
+        pr.set_cores(cores)
+        pr.set_T(T0)
+    cap.sync()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    cinfos = cap.step(kb)
+    cap.sync()
+    torch.cuda.synchronize()
+    dt_cap = time.perf_counter() - t2
+    same = all(cinfos[i]["ranks"] == infos[i]["ranks"] and
+               torch.equal(cap.problem(i).full(), batch.problem(i).full()) for i in range(len(ps)))
+    del cap
     return {"workload": "64 independent 2D problems, grids U{64^2,128^2,256^2}, ordinates U{16x32,32x64}, "
                         "sigma_a log-U[1e-2,1e2], Gaussian T pulses, eps U{1e-4,1e-6}, rank caps U[8,96], "
                         "periodic (seed 0); each problem on its own stream, host threads advance them",
@@ -676,6 +706,11 @@ def run_batch(args, torch, ttsn):
             "timing": "host wall clock around tt_batch_step with device synchronisation on both sides",
             "one_thread_problem_steps_per_s": len(ps) * kb / dt_seq,
             "concurrency_speedup": dt_seq / dt,
+            "captured": {"problem_steps_per_s": len(ps) * kb / dt_cap,
+                         "speedup_vs_host_threads": dt / dt_cap,
+                         "same_bits_as_host_driven": bool(same),
+                         "how": "tt_batch_set_graph: one recorded step per problem replayed as a CUDA graph "
+                                "(device-decided ranks), all problems in flight from one host thread"},
             "ranks_last_min_max": [min(min(r) for r in ranks), max(max(r) for r in ranks)]}
 
 
@@ -925,6 +960,8 @@ def main():
                       % OVERSAMPLE,
             "err_vs_fp64_gram": {"E_max_rel": rz["err_E"], "T_max_rel": rz["err_T"]},
             "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in rz["prof"].items()}}
+    if res.get("autotune") is not None:
+        line["autotune"] = res["autotune"]
     if res.get("batched") is not None:
         line["batched"] = res["batched"]
     if res.get("adjoint") is not None:

@@ -293,6 +293,27 @@ tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, co
 tt_status tt_set_sketch(tt_handle h, const double* const* omega_dev, const int* ranks_host);
 tt_status tt_set_rounding(tt_handle h, int method);
 
+/*
+ * tt_set_graph: captured steps (enable = 1) or host-driven steps (0, the
+ * default).  With capture on, the first tt_sn_step / tt_sn_step_ex call
+ * without flags and forced ranks records one whole step (transport, source,
+ * rounding, temperature update) into a CUDA graph, and that call and every
+ * later one replay it, nsteps replays per call with one synchronisation at
+ * the end.  The step's sizes are decided on the device: the kernels of the
+ * recorded step read the grown ranks, the right Grams' numerical ranks and
+ * both rank decisions from a device size block (grids cover the rank cap),
+ * so one recording serves every later step whatever its ranks; results are
+ * the same bits as host-driven steps.  Takes the grouped layout, FP64,
+ * rounds_per_step 1, Gram-SVD rounding, a rank cap (max_rank > 0), upwind or
+ * Rusanov, no fixed sources or inflow faces, no tape, not a shard
+ * (TT_ERR_STATE otherwise, also when a later setting breaks one of these).
+ * The info of a call is its last step's; TT_WARN_RANK_CAPPED if the cap bound
+ * in any replayed step; a step that meets a zero tensor returns TT_ERR_STATE
+ * (the recorded step does not represent it).  Calls other than steps
+ * synchronise first and see the device's ranks.
+ */
+tt_status tt_set_graph(tt_handle h, int enable);
+
 /* tt_set_precision: TT_FP64 or TT_MIXED for the following roundings. */
 tt_status tt_set_precision(tt_handle h, int precision);
 
@@ -401,6 +422,16 @@ tt_status tt_batch_size(tt_batch b, int* count);
 tt_status tt_batch_handle(tt_batch b, int i, tt_handle* out);
 tt_status tt_batch_sync(tt_batch b);
 void tt_batch_destroy(tt_batch b);
+
+/*
+ * tt_batch_set_graph: captured steps (tt_set_graph) for every problem of the
+ * batch.  tt_batch_step then replays each problem's recorded step on its own
+ * stream from one host thread, all problems in flight at once, with one
+ * synchronisation per problem at the end of the call instead of the rank
+ * read-backs inside every step.  TT_ERR_STATE if a problem cannot be
+ * captured (see tt_set_graph); the batch is then left unchanged.
+ */
+tt_status tt_batch_set_graph(tt_batch b, int enable);
 
 /* ---------------------------------------------------------------------------
  * Spatial sharding: the method partitioned over space across several
@@ -576,6 +607,30 @@ tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A_dev, int lda, co
  */
 tt_status tt_gram_noalloc(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg,
                           void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Autotuned products (no counterpart in the paper).  The FP64 products of the
+ * rounding whose output tile grid (64 x 64 tiles) leaves SMs idle split their
+ * contraction depth K over CTAs; how many splits pays depends on the GPU.
+ * tt_autotune measures, for every bucket of (floor(log2 tiles) < 8,
+ * floor(log2 K) from 6 to 14), the product's time at each split 1, 2, 4, ...,
+ * 64 (up to K / 32) on a representative product of that bucket, keeps the
+ * fastest (best of three runs), extends the deepest bucket's choice to deeper
+ * products, and installs the table for every later product of the process,
+ * host-driven and captured alike (both read the same table, so their results
+ * stay the same bits).  table_out (nullable, host) receives the
+ * TT_AUTOTUNE_ENTRIES entries, index floor(log2 tiles) * 22 + floor(log2 K);
+ * 0 means the built-in rule.  Takes a few seconds and some 1.5 GB of device
+ * memory while it runs; call it before creating handles or recording steps,
+ * not concurrently with other library calls.  tt_set_autotune_table installs
+ * a stored table (entries 0 .. 64; TT_ERR_ARG otherwise), and
+ * tt_get_autotune_table copies the installed one (all zero until a table is
+ * installed).
+ * ------------------------------------------------------------------------ */
+#define TT_AUTOTUNE_ENTRIES (8 * 22)
+tt_status tt_autotune(void* stream, int* table_out);
+tt_status tt_set_autotune_table(const int* table_host, int n);
+tt_status tt_get_autotune_table(int* table_host, int n);
 
 /* ---------------------------------------------------------------------------
  * Measurement calls (no counterpart in the paper; used by the benchmark to

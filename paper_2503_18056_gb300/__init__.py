@@ -156,6 +156,11 @@ class _Handle:
     def set_precision(self, precision):
         check(lib.tt_set_precision(self._h, int(precision)))
 
+    def set_graph(self, enable=True):
+        """Captured steps (tt_set_graph): one recorded step replayed as a CUDA
+        graph, sizes decided on the device, no host synchronisation inside."""
+        check(lib.tt_set_graph(self._h, int(bool(enable))))
+
     def set_max_sweeps(self, max_sweeps):
         """Sweep limit of the Jacobi eigensolves of this handle's roundings (1 .. 40)."""
         check(lib.tt_set_max_sweeps(self._h, int(max_sweeps)))
@@ -575,6 +580,10 @@ class TTSNBatch:
     def sync(self):
         check(lib.tt_batch_sync(self._b))
 
+    def set_graph(self, enable=True):
+        """Captured steps for every problem (tt_batch_set_graph)."""
+        check(lib.tt_batch_set_graph(self._b, int(bool(enable))))
+
     def problem(self, i):
         h = ctypes.c_void_p()
         check(lib.tt_batch_handle(self._b, int(i), ctypes.byref(h)))
@@ -676,6 +685,41 @@ def syev(G, stream=None, allow_unconverged=False, max_sweeps=40):
     if not (allow_unconverged and st == -4):
         check(st)
     return lam, Vt, sweeps.value
+
+
+def autotune(path=None, stream=None):
+    """Measure the FP64 products' split of K per (tiles, depth) bucket on this
+    GPU and install the table (tt_autotune); returns it as a list and, with
+    path, stores it as JSON for load_autotune."""
+    import json
+
+    buf = (ctypes.c_int * _native.TT_AUTOTUNE_ENTRIES)()
+    check(lib.tt_autotune(_stream_ptr(stream), buf))
+    table = list(buf)
+    if path is not None:
+        with open(path, "w") as fh:
+            json.dump({"layout": "index floor(log2 tiles) * 22 + floor(log2 K); 0 = built-in rule",
+                       "splits": table}, fh)
+    return table
+
+
+def load_autotune(path_or_table):
+    """Install a stored autotune table (a JSON file from autotune(path) or a list)."""
+    import json
+
+    table = path_or_table
+    if isinstance(path_or_table, (str, os.PathLike)):
+        with open(path_or_table) as fh:
+            table = json.load(fh)["splits"]
+    buf = (ctypes.c_int * len(table))(*[int(x) for x in table])
+    check(lib.tt_set_autotune_table(buf, len(table)))
+
+
+def autotune_table():
+    """The installed autotune table (all zero: the built-in rule)."""
+    buf = (ctypes.c_int * _native.TT_AUTOTUNE_ENTRIES)()
+    check(lib.tt_get_autotune_table(buf, _native.TT_AUTOTUNE_ENTRIES))
+    return list(buf)
 
 
 def kernel_launches():

@@ -28,6 +28,7 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, c
 EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                ctypes.c_void_p)
 TT_XCHG_SUM, TT_XCHG_HALO = 0, 1
+TT_AUTOTUNE_ENTRIES = 8 * 22
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 
@@ -104,6 +105,11 @@ def _load():
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
         "tt_syev_ex": [i, vp, i, vp, vp, i, i, vp, ip],
         "tt_set_max_sweeps": [vp, i],
+        "tt_set_graph": [vp, i],
+        "tt_autotune": [vp, ip],
+        "tt_set_autotune_table": [ip, i],
+        "tt_get_autotune_table": [ip, i],
+        "tt_batch_set_graph": [vp, i],
         "tt_pchol": [i, vp, i, vp, vp, ip],
         "tt_set_inflow": [vp, i, i, vp, vp, vp],
         "tt_set_sketch": [vp, ctypes.POINTER(vp), ip],
@@ -150,7 +156,8 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
             "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
             "tt_create_ex", "tt_get_cores", "tt_pchol", "tt_set_inflow", "tt_set_sketch",
-            "tt_set_rounding", "tt_wait_probe", "tt_create_shard", "tt_syev_ex", "tt_set_max_sweeps"]
+            "tt_set_rounding", "tt_wait_probe", "tt_create_shard", "tt_syev_ex", "tt_set_max_sweeps", "tt_set_graph",
+            "tt_batch_set_graph", "tt_autotune", "tt_set_autotune_table", "tt_get_autotune_table"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]
 

@@ -39,7 +39,11 @@ namespace ttsn {
 
 static thread_local std::string g_err;
 static std::atomic<unsigned long long> g_launches{0};
-void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local unsigned long long t_launches = 0;  // this thread's launches (capture counts)
+void note_launch(unsigned n) {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
 void set_error(const std::string& msg) { g_err = msg; }
 const char* get_error() { return g_err.c_str(); }
 
@@ -69,6 +73,14 @@ void dev_free(const tt_allocator* a, double* p, size_t bytes, cudaStream_t s, bo
 
 tt_status DevBuf::ensure(size_t n, cudaStream_t s, bool keep) {
     if (n <= cap) return TT_OK;
+    // a recorded step must not allocate: an allocation inside a capture
+    // becomes a graph node that the next replay cannot repeat
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        set_error("captured step: a buffer would have to grow inside the recording (" +
+                  std::to_string(n * 8) + " bytes)");
+        return TT_ERR_STATE;
+    }
     if (!p) {  // the first allocation fixes the allocator this buffer uses
         alloc = current_allocator();
         astream = s;
@@ -122,6 +134,79 @@ void DevBuf::release() {
 }  // namespace ttsn
 
 using namespace ttsn;
+
+namespace ttsn {
+struct PlanConsts {
+    int nterms;   // 1 + 2 ndim
+    int nt, np;   // n_theta, n_phi
+    long nc;
+};
+
+__device__ __forceinline__ void put_desc(int* dd, int slot, int M, int N, int K, int lda, int ldb, int ldc) {
+    int* d = dd + DYN_DESC + 8 * slot;
+    d[0] = M;
+    d[1] = N;
+    d[2] = K;
+    d[3] = lda;
+    d[4] = ldb;
+    d[5] = ldc;
+}
+
+// stage 0: step begins (grown ranks, backward sweep, bond 0 Gram); 1: right
+// Grams factored (bond 0 products); 2: bond 0 decided (its update, bond 1
+// Gram and products); 3: bond 1 decided (its update; the new ranks become the
+// TT's).  A bond that meets a zero factor or a zero decision marks the step
+// degenerate (slot DYN_DEC0 + 3), which the host reports after the replay.
+__global__ void plan_kernel(int stage, int* dd, PlanConsts pc) {
+    const int nt = pc.nt, np = pc.np;
+    if (stage == 0) {
+        const int G1 = pc.nterms * dd[DYN_R1] + 1, G2 = pc.nterms * dd[DYN_R2] + 1;
+        dd[DYN_G1] = G1;
+        dd[DYN_G2] = G2;
+        dd[DYN_DEC0 + 3] = 0;
+        put_desc(dd, 0, G2, G2, np, np, np, G2);                   // GB1 = Phi* Phi*^T
+        put_desc(dd, 1, G1 * nt, G2, G2, G2, G2, G2);              // bwd = Theta* GB1
+        put_desc(dd, 2, G1, G1, nt * G2, nt * G2, nt * G2, G1);    // GB0 = bwd Theta*^T
+        put_desc(dd, 3, G1, G1, (int)pc.nc, G1, G1, G1);           // G_A of X*
+    } else if (stage == 1) {
+        const int G1 = dd[DYN_G1], G2 = dd[DYN_G2];
+        const int k0 = max(dd[DYN_KB0], 0), k1 = max(dd[DYN_KB1], 0);
+        if (k0 == 0 || k1 == 0) dd[DYN_DEC0 + 3] = 1;
+        put_desc(dd, 4, G1, k0, G1, G1, G1, k0);                   // T1 = G_A W^T
+        put_desc(dd, 5, k0, k0, G1, G1, k0, k0);                   // K = W T1
+        (void)G2;
+    } else if (stage == 2) {
+        const int G1 = dd[DYN_G1], G2 = dd[DYN_G2];
+        const int k0 = max(dd[DYN_KB0], 0), k1 = max(dd[DYN_KB1], 0);
+        const int r = dd[DYN_DEC0];
+        if (r == 0) dd[DYN_DEC0 + 3] = 1;
+        put_desc(dd, 6, r, k0, k0, k0, 0, 0);                      // scale_rows rows, cols, ldi, ldo
+        put_desc(dd, 7, r, G1, k0, k0, G1, G1);                    // P_A^T = S^-1 V^T W
+        put_desc(dd, 8, r, G1, G1, G1, G1, G1);                    // M_upd = P_A^T G_A
+        put_desc(dd, 9, (int)pc.nc, r, G1, G1, G1, r);             // X' = X* P_A
+        put_desc(dd, 10, r, nt * G2, G1, G1, nt * G2, nt * G2);    // next = M_upd Theta*
+        put_desc(dd, 11, G2, G2, r * nt, G2, G2, G2);              // G_A of the next core
+        put_desc(dd, 12, G2, k1, G2, G2, G2, k1);
+        put_desc(dd, 13, k1, k1, G2, G2, k1, k1);
+    } else {
+        const int G2 = dd[DYN_G2];
+        const int k1 = max(dd[DYN_KB1], 0);
+        const int r0 = dd[DYN_DEC0], r = dd[DYN_DEC1];
+        if (r == 0) dd[DYN_DEC0 + 3] = 1;
+        put_desc(dd, 14, r, k1, k1, k1, 0, 0);
+        put_desc(dd, 15, r, G2, k1, k1, G2, G2);
+        put_desc(dd, 16, r, G2, G2, G2, G2, G2);
+        put_desc(dd, 17, r0 * nt, r, G2, G2, G2, r);
+        put_desc(dd, 18, r, np, G2, G2, np, np);
+        dd[DYN_R1] = r0;
+        dd[DYN_R2] = r;
+        // what the host reports after a run of replays: capped, non-finite, degenerate
+        const int nonfinite = dd[DYN_DEC0 + 2] | dd[DYN_DEC1 + 2] | (dd[DYN_KB0] < 0) | (dd[DYN_KB1] < 0);
+        dd[DYN_STICKY] |= (dd[DYN_DEC0 + 1] | dd[DYN_DEC1 + 1]) | (nonfinite << 1) | (dd[DYN_DEC0 + 3] << 2);
+    }
+}
+
+}  // namespace ttsn
 
 // host-side slots of the pinned readback block
 enum { HI_KB = 0, HI_DEC = 16, HI_STATUS = 20, HI_SWEEPS = 24, HI_N = 64 };
@@ -249,6 +334,18 @@ struct tt_ctx {
     // axis 0's global rule bc0, cells per layer, the caller's exchange; xch
     // holds the four exchange blocks (the ghost layers themselves follow the
     // own rows of core[0])
+    // captured step (tt_set_graph): the step's launches recorded once into a
+    // CUDA graph whose kernels read the device-decided sizes from dyn
+    // (DYN_* slots), replayed every step without a host synchronisation
+    bool graph_on = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned graph_launches = 0;       // library kernels one replay runs
+    bool ranks_stale = false;          // h->r lags the device after replays
+    int cap1 = 0, cap2 = 0;            // rank caps of the two bonds
+    DevBuf dyn_buf, dyn_part;          // size block (ints) and product partials
+    int* dyn = nullptr;
+    int* h_dyn = nullptr;              // pinned mirror, refreshed by every replay
+    double* h_dyn_dec = nullptr;       // pinned decisions of the two bonds (8 doubles)
     struct Shard {
         bool on = false;
         int p0 = 0, p1 = 0, n0 = 0, bc0 = TT_BC_PERIODIC;
@@ -296,7 +393,7 @@ struct tt_ctx {
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
                           &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph,
-                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs, &xch};
+                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs, &xch, &dyn_buf, &dyn_part};
         for (DevBuf* b : bufs) b->release();
         for (auto& ax : inflow)
             for (auto& face : ax) face.g.release();
@@ -317,6 +414,9 @@ struct tt_ctx {
         small_buf.release();
         if (h_int) cudaFreeHost(h_int);
         if (h_dbl) cudaFreeHost(h_dbl);
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (h_dyn) cudaFreeHost(h_dyn);
+        if (h_dyn_dec) cudaFreeHost(h_dyn_dec);
     }
     size_t core_len(int k, const int* rr) const { return (size_t)rr[k] * n[k] * rr[k + 1]; }
 };
@@ -1105,9 +1205,275 @@ tt_status step_once(tt_ctx* h, int flags, const int* forced, tt_step_info* info)
     return result;
 }
 
+// ---------------------------------------------------------------- captured steps
+// One grouped FP64 step recorded into a CUDA graph.  The step's sizes (the
+// grown ranks, the right Grams' numerical ranks, the two rank decisions) are
+// decided on the device, so every kernel of the captured step reads them from
+// the handle's size block (DYN_* slots) and every grid covers the largest
+// sizes the rank cap allows; the products' descriptors (M, N, K and the
+// leading dimensions) are filled by plan_kernel as the sizes become known.
+// The launches are the host path's own kernels in the same order with the
+// same split rules, so a replayed step gives the same bits as tt_sn_step.
+// Whether the handle's steps can be captured: the grouped FP64 step with one
+// Gram-SVD rounding, a rank cap (every buffer has its largest size from the
+// start), no fixed sources or inflow faces, no adjoint tape, not a shard.
+const char* graph_unsupported(const tt_ctx* h) {
+    if (!h->physics || h->split()) return "captured steps need the grouped layout";
+    if (h->precision != TT_FP64) return "captured steps are FP64";
+    if (h->rounds != 1) return "captured steps round once per step";
+    if (h->round_method != TT_ROUND_GRAM) return "captured steps use the Gram-SVD rounding";
+    if (h->max_rank <= 0) return "captured steps need a rank cap (max_rank > 0)";
+    if (h->nsrc > 0) return "captured steps take no fixed sources or inflow faces";
+    if (h->taping) return "captured steps are not taped";
+    if (h->shard.on) return "a spatial shard exchanges on the host and is not captured";
+    if (h->fields.flux == TT_FLUX_HLL) return "captured steps take upwind or Rusanov fluxes";
+    return nullptr;
+}
+
+// The launches of one step, sized by the caps, reading sizes from h->dyn.
+tt_status graph_step_body(tt_ctx* h) {
+    cudaStream_t s = h->stream;
+    const Grid& g = h->grid;
+    const int nterms = 1 + 2 * g.ndim;
+    const int nt = h->ang.n_theta, np = h->ang.n_phi;
+    const int c1 = h->cap1, c2 = h->cap2;
+    const int G1 = nterms * c1 + 1, G2 = nterms * c2 + 1;
+    const long nc = g.nc;
+    int* dd = h->dyn;
+    const int* desc = dd + DYN_DESC;
+    double* P = h->dyn_part.p;
+    double* dec_d = h->dyn_buf.p + (DYN_INTS + 1) / 2;
+    const PlanConsts pc{nterms, nt, np, nc};
+    auto plan = [&](int stage) {
+        note_launch();
+        plan_kernel<<<1, 1, 0, s>>>(stage, dd, pc);
+    };
+    plan(0);
+    // transport + source (Sec. 4.3-4.4): the grown cores
+    grown_thbar(s, h->ang, g.ndim, true, c1, c2, h->core[1].p, h->core[2].p, h->thbar.p, dd);
+    build_grown_angular(s, h->ang, g.ndim, true, true, c1, c2, h->core[1].p, h->core[2].p, h->gcore[1].p,
+                        h->gcore[2].p, G1, G2, Sources(), dd);
+    h->fields.T = h->f_T.p;
+    h->fields.E_star = h->f_Estar.p;
+    transport_source_rows(s, g, h->fields, true, true, c1, h->core[0].p, c1, h->thbar.p, h->gcore[0].p, G1,
+                          Sources(), dd);
+    // rounding (App. A.2, one-sided Gram truncation): backward sweep
+    fill(s, h->d_dbl + HD_DELTA2, 1, -1.0);
+    TT_TRY(dgemm_dyn(s, false, true, desc + 0, G2, G2, np, 1.0, h->gcore[2].p, h->gcore[2].p, h->GB[1].p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 8, G1 * nt, G2, G2, 1.0, h->gcore[1].p, h->GB[1].p, h->bwd.p, P, 0));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 16, G1, G1, nt * G2, 1.0, h->bwd.p, h->gcore[1].p, h->GB[0].p, P, 1));
+    TT_TRY(pchol_dyn(s, dd + DYN_G1, G1, h->GB[0].p, h->VtB[0].p, h->Wc.p, h->lamB[0].p, h->eig,
+                     h->d_int + HI_STATUS, dd + DYN_KB0));
+    TT_TRY(pchol_dyn(s, dd + DYN_G2, G2, h->GB[1].p, h->VtB[1].p, h->Wc.p, h->lamB[1].p, h->eig,
+                     h->d_int + HI_STATUS, dd + DYN_KB1));
+    plan(1);
+    // bond 0: G_A, K = W G_A W^T, eig(K), decision
+    TT_TRY(dgemm_dyn(s, true, false, desc + 24, G1, G1, (int)nc, 1.0, h->gcore[0].p, h->gcore[0].p, h->GA.p, P, 2));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 32, G1, G1, G1, 1.0, h->GA.p, h->VtB[0].p, h->T1.p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 40, G1, G1, G1, 1.0, h->VtB[0].p, h->T1.p, h->K.p, P, 1));
+    TT_TRY(syev_dyn(s, dd + DYN_KB0, G1, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS,
+                    dd + DYN_SWEEPS, h->max_sweeps));
+    truncation_decision_dyn(s, h->lamK.p, dd + DYN_KB0, h->eps, 2, 0, h->max_rank, h->d_dbl + HD_DELTA2,
+                            dd + DYN_DEC0, dec_d);
+    plan(2);
+    // bond 0 update: P_A^T, M_upd, X' = X* P_A, next core = M_upd x_1 Theta*
+    scale_rows_dyn(s, desc + 48, (long)c1 * G1, h->VtK.p, h->lamK.p, 2, h->Vts.p);
+    TT_TRY(dgemm_dyn(s, false, false, desc + 56, c1, G1, G1, 1.0, h->Vts.p, h->VtB[0].p, h->PAt.p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 64, c1, G1, G1, 1.0, h->PAt.p, h->GA.p, h->Mupd.p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 72, (int)nc, c1, G1, 1.0, h->gcore[0].p, h->PAt.p, h->core[0].p, P, 0));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 80, c1, nt * G2, G1, 1.0, h->Mupd.p, h->gcore[1].p, h->tmp[0].p, P, 1));
+    // bond 1 on the next core (replicated rows r0 n_theta)
+    TT_TRY(dgemm_dyn(s, true, false, desc + 88, G2, G2, c1 * nt, 1.0, h->tmp[0].p, h->tmp[0].p, h->GA.p, P, 2));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 96, G2, G2, G2, 1.0, h->GA.p, h->VtB[1].p, h->T1.p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 104, G2, G2, G2, 1.0, h->VtB[1].p, h->T1.p, h->K.p, P, 1));
+    TT_TRY(syev_dyn(s, dd + DYN_KB1, G2, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS,
+                    dd + DYN_SWEEPS + 1, h->max_sweeps));
+    truncation_decision_dyn(s, h->lamK.p, dd + DYN_KB1, h->eps, 2, 0, h->max_rank, h->d_dbl + HD_DELTA2,
+                            dd + DYN_DEC1, dec_d + 4);
+    plan(3);
+    scale_rows_dyn(s, desc + 112, (long)c2 * G2, h->VtK.p, h->lamK.p, 2, h->Vts.p);
+    TT_TRY(dgemm_dyn(s, false, false, desc + 120, c2, G2, G2, 1.0, h->Vts.p, h->VtB[1].p, h->PAt.p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 128, c2, G2, G2, 1.0, h->PAt.p, h->GA.p, h->Mupd.p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 136, c1 * nt, c2, G2, 1.0, h->tmp[0].p, h->PAt.p, h->core[1].p, P, 0));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 144, c2, np, G2, 1.0, h->Mupd.p, h->gcore[2].p, h->core[2].p, P, 1));
+    // energy-conserving temperature update (Sec. 3.2) from the rounded TT
+    plain_thbar(s, h->ang, c1, c2, h->core[1].p, h->core[2].p, h->thbar.p, dd);
+    energy_rows(s, nc, c1, h->core[0].p, c1, h->thbar.p, h->fields.c, nullptr, h->f_Estar.p, h->f_cv.p,
+                h->f_T.p, true, dd);
+    // the sizes and decisions for the host, read after the next synchronisation
+    TT_CUDA_TRY(cudaMemcpyAsync(h->h_dyn, dd, DYN_INTS * sizeof(int), cudaMemcpyDeviceToHost, s));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->h_dyn_dec, dec_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+// Every buffer a captured step touches at its largest size (nothing may
+// allocate inside a capture).
+tt_status graph_reserve(tt_ctx* h) {
+    cudaStream_t s = h->stream;
+    const Grid& g = h->grid;
+    const long nterms = 1 + 2 * g.ndim;
+    const long nt = h->ang.n_theta, np = h->ang.n_phi, nc = g.nc;
+    const long c1 = h->cap1, c2 = h->cap2, G1 = nterms * c1 + 1, G2 = nterms * c2 + 1;
+    const long Gm = std::max(G1, G2);
+    struct Need {
+        DevBuf* b;
+        long n;
+    } need[] = {
+        {&h->core[0], nc * c1}, {&h->core[1], c1 * nt * c2}, {&h->core[2], c2 * np},
+        {&h->gcore[0], nc * G1}, {&h->gcore[1], G1 * nt * G2}, {&h->gcore[2], G2 * np},
+        {&h->GB[0], G1 * G1}, {&h->GB[1], G2 * G2}, {&h->VtB[0], G1 * G1}, {&h->VtB[1], G2 * G2},
+        {&h->lamB[0], 2 * G1}, {&h->lamB[1], 2 * G2}, {&h->Wc, Gm * Gm}, {&h->GA, Gm * Gm},
+        {&h->T1, Gm * Gm}, {&h->K, Gm * Gm}, {&h->lamK, Gm}, {&h->VtK, Gm * Gm},
+        {&h->Vts, Gm * Gm}, {&h->PAt, Gm * Gm}, {&h->Mupd, Gm * Gm}, {&h->bwd, G1 * nt * G2},
+        {&h->tmp[0], c1 * nt * G2}, {&h->thbar, nterms * (c1 + c2) + 2},
+        {&h->eig.g0, Gm * Gm}, {&h->eig.g1, Gm * Gm}, {&h->eig.vt_unsorted, Gm * Gm},
+        {&h->eig.lam_unsorted, Gm}, {&h->eig.abc, 3 * (Gm + 1)}, {&h->eig.cs, Gm + 1},
+        {&h->dyn_part, (long)dyn_partials_doubles()},
+    };
+    for (auto& x : need) TT_TRY(x.b->ensure((size_t)std::max<long>(x.n, 1), s, /*keep=*/true));
+    TT_TRY(eig_reserve(h->eig, s));
+    TT_TRY(h->dyn_buf.ensure((size_t)(DYN_INTS + 1) / 2 + 16, s));
+    h->dyn = reinterpret_cast<int*>(h->dyn_buf.p);
+    if (!h->h_dyn) TT_CUDA_TRY(cudaMallocHost(&h->h_dyn, DYN_INTS * sizeof(int)));
+    if (!h->h_dyn_dec) TT_CUDA_TRY(cudaMallocHost(&h->h_dyn_dec, 8 * sizeof(double)));
+    return TT_OK;
+}
+
+// The host's ranks after replays: wait for the stream and take the device's.
+tt_status refresh_ranks(tt_ctx* h) {
+    if (!h->ranks_stale) return TT_OK;
+    TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->ranks_stale = false;
+    h->r[0] = h->r[3] = 1;
+    h->r[1] = h->h_dyn[DYN_R1];
+    h->r[2] = h->h_dyn[DYN_R2];
+    h->gr[0] = h->gr[3] = 1;
+    h->gr[1] = h->h_dyn[DYN_G1];
+    h->gr[2] = h->h_dyn[DYN_G2];
+    return TT_OK;
+}
+
+// The diagnostics of the last replayed step and the flags of all replays
+// since the sticky slot was cleared (host mirror, after a sync).
+tt_status graph_info(tt_ctx* h, tt_step_info* info, bool* capped) {
+    const int* hd = h->h_dyn;
+    const int sticky = hd[DYN_STICKY];
+    *capped = (sticky & 1) != 0;
+    if (sticky & 2)
+        return fail(TT_ERR_NONFINITE, "rounding: the tensor holds Inf or NaN (the run diverged or a field "
+                                      "held one); restore saved cores and T before stepping again");
+    if (sticky & 4)
+        return fail(TT_ERR_STATE, "captured step: the rounding met a zero tensor, which a captured step "
+                                  "does not represent; restore saved cores and T and step without capture");
+    if (info) {
+        info->d = 3;
+        info->ranks[0] = info->ranks[3] = 1;
+        info->ranks[1] = hd[DYN_R1];
+        info->ranks[2] = hd[DYN_R2];
+        info->grown[0] = info->grown[3] = 1;
+        info->grown[1] = hd[DYN_G1];
+        info->grown[2] = hd[DYN_G2];
+        for (int k = 0; k < TT_MAX_D; ++k) info->discarded[k] = 0.0;
+        info->discarded[0] = sqrt(std::max(h->h_dyn_dec[1], 0.0));
+        info->discarded[1] = sqrt(std::max(h->h_dyn_dec[5], 0.0));
+        info->norm = sqrt(std::max(h->h_dyn_dec[2], 0.0));
+        info->capped = *capped ? 1 : 0;
+        info->sweeps = std::max(hd[DYN_SWEEPS], hd[DYN_SWEEPS + 1]);
+    }
+    return TT_OK;
+}
+
+// Record the step once (the first captured step), then replay.
+tt_status graph_launch(tt_ctx* h) {
+    cudaStream_t s = h->stream;
+    if (!h->graph_exec) {
+        TT_TRY(graph_reserve(h));
+        // the size block starts from the host's ranks
+        int init[2] = {h->r[1], h->r[2]};
+        TT_CUDA_TRY(cudaMemcpyAsync(h->dyn + DYN_R1, init, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+        TT_TRY(eig_prepare());
+        const unsigned long long before = t_launches;
+        cudaGraph_t graph = nullptr;
+        // record on a stream of its own (the handle's stream may be the legacy
+        // default stream, which cannot be captured); the graph is then
+        // launched on the handle's stream
+        cudaStream_t cap = nullptr;
+        TT_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        h->stream = cap;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        tt_status st = TT_OK;
+        if (e == cudaSuccess) {
+            st = graph_step_body(h);
+            e = cudaStreamEndCapture(cap, &graph);
+        }
+        h->stream = s;
+        cudaStreamDestroy(cap);
+        if (st < 0) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(TT_ERR_CUDA, std::string("captured step: stream capture failed: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->graph_exec = nullptr;
+            return fail(TT_ERR_CUDA, std::string("captured step: instantiation failed: ") + cudaGetErrorString(e));
+        }
+        // the capture counted its launches; each replay runs them again
+        h->graph_launches = (unsigned)(t_launches - before);
+        g_launches.fetch_sub(h->graph_launches);
+        t_launches -= h->graph_launches;
+    } else if (!h->ranks_stale) {
+        // the host changed the state (set_cores, a plain step): restart from its ranks
+        int init[2] = {h->r[1], h->r[2]};
+        TT_CUDA_TRY(cudaMemcpyAsync(h->dyn + DYN_R1, init, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    TT_CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+    note_launch(h->graph_launches);
+    h->ranks_stale = true;
+    return TT_OK;
+}
+
+// Before a run of replays: the capture conditions still hold (a setting may
+// have changed since tt_set_graph) and the sticky flags are cleared.
+tt_status graph_start(tt_ctx* h) {
+    if (const char* why = graph_unsupported(h)) return fail(TT_ERR_STATE, std::string("captured step: ") + why);
+    if (h->cap1 == 0) {
+        const long nc = h->grid.nc;
+        h->cap1 = (int)std::min<long>(h->max_rank, std::min<long>(nc, (long)h->ang.n_theta * h->ang.n_phi));
+        h->cap2 = (int)std::min<long>(h->max_rank, h->ang.n_phi);
+    }
+    if (h->r[1] > h->cap1 || h->r[2] > h->cap2)
+        return fail(TT_ERR_STATE, "captured step: the TT's ranks exceed the rank cap");
+    if (!h->dyn) TT_TRY(graph_reserve(h));
+    TT_CUDA_TRY(cudaMemsetAsync(h->dyn + DYN_STICKY, 0, sizeof(int), h->stream));
+    return TT_OK;
+}
+
+// After a run of replays: wait, report the device status and the flags, fill info.
+tt_status graph_finish(tt_ctx* h, tt_step_info* info) {
+    TT_TRY(read_status(h));  // synchronises the stream
+    h->ranks_stale = false;
+    TT_TRY(refresh_ranks(h));
+    h->r[1] = h->h_dyn[DYN_R1];
+    h->r[2] = h->h_dyn[DYN_R2];
+    h->gr[1] = h->h_dyn[DYN_G1];
+    h->gr[2] = h->h_dyn[DYN_G2];
+    bool capped = false;
+    TT_TRY(graph_info(h, info, &capped));
+    return capped ? TT_WARN_RANK_CAPPED : TT_OK;
+}
+
 tt_status check_handle(tt_handle h, bool need_physics) {
     if (!h) return fail(TT_ERR_ARG, "null handle");
     if (need_physics && !h->physics) return fail(TT_ERR_STATE, "handle is a bare TT (no problem attached)");
+    // after captured steps the host's ranks follow the device's
+    TT_TRY(refresh_ranks(h));
     return TT_OK;
 }
 
@@ -1316,6 +1682,21 @@ tt_status adjoint_run(tt_ctx* h, double* grad_dev, double* Q_host) {
 }  // namespace
 
 // ============================================================== C ABI
+
+namespace ttsn {
+tt_status graph_steps_begin(tt_handle h, int nsteps) {
+    TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
+    if (!h->graph_on) return fail(TT_ERR_STATE, "captured steps are off for this handle");
+    TT_TRY(graph_start(h));
+    for (int it = 0; it < nsteps; ++it) TT_TRY(graph_launch(h));
+    return TT_OK;
+}
+tt_status graph_steps_end(tt_handle h, tt_step_info* info) {
+    AllocScope alloc_scope_(h->alloc_ptr());
+    return graph_finish(h, info);
+}
+}  // namespace ttsn
 
 extern "C" {
 
@@ -1757,6 +2138,12 @@ tt_status tt_sn_step_ex(tt_handle h, int nsteps, int flags, const int* forced, t
         for (int k = 0; k < nforced; ++k)
             if (forced[k] < 1) return fail(TT_ERR_ARG, "tt_sn_step: forced ranks must be >= 1");
     tt_status result = TT_OK;
+    if (h->graph_on && flags == 0 && !forced && nsteps > 0) {
+        // captured steps: replay the recorded step, one synchronisation at the end
+        TT_TRY(graph_start(h));
+        for (int it = 0; it < nsteps; ++it) TT_TRY(graph_launch(h));
+        return graph_finish(h, info);
+    }
     for (int it = 0; it < nsteps; ++it) {
         nvtxRangePushA("tt_sn_step");
         tt_status st = step_once(h, flags, forced, info);
@@ -1767,6 +2154,20 @@ tt_status tt_sn_step_ex(tt_handle h, int nsteps, int flags, const int* forced, t
     tt_status st = read_status(h);
     if (st < 0) return st;
     return result;
+}
+
+
+tt_status tt_set_graph(tt_handle h, int enable) {
+    set_error("");
+    TT_TRY(check_handle(h, true));
+    AllocScope alloc_scope_(h->alloc_ptr());
+    if (enable) {
+        if (const char* why = graph_unsupported(h)) return fail(TT_ERR_STATE, std::string("tt_set_graph: ") + why);
+        h->graph_on = true;
+    } else {
+        h->graph_on = false;
+    }
+    return TT_OK;
 }
 
 tt_status tt_sn_step(tt_handle h, int nsteps, tt_step_info* info) {
@@ -2341,6 +2742,26 @@ tt_status tt_syev_ex(int n, const double* G, int ldg, double* lam, double* Vt, i
     if (sweeps_host) *sweeps_host = hs[1];
     if (hs[0] & DEV_TIMEOUT) return fail(TT_ERR_TIMEOUT, "tt_syev: grid barrier wait ran out");
     if (hs[0] & DEV_NOT_CONVERGED) return fail(TT_ERR_NOT_CONVERGED, "tt_syev: sweep limit reached");
+    return TT_OK;
+}
+
+tt_status tt_autotune(void* stream, int* table_out) {
+    set_error("");
+    static_assert(TT_AUTOTUNE_ENTRIES == AT_TILE_BUCKETS * AT_K_BUCKETS, "autotune table size");
+    return autotune((cudaStream_t)stream, table_out);
+}
+
+tt_status tt_set_autotune_table(const int* table_host, int n) {
+    set_error("");
+    if (!table_host) return fail(TT_ERR_ARG, "tt_set_autotune_table: null table");
+    return autotune_install(table_host, n);
+}
+
+tt_status tt_get_autotune_table(int* table_host, int n) {
+    set_error("");
+    if (!table_host || n < TT_AUTOTUNE_ENTRIES)
+        return fail(TT_ERR_ARG, "tt_get_autotune_table: need a table of TT_AUTOTUNE_ENTRIES ints");
+    autotune_read(table_host);
     return TT_OK;
 }
 

@@ -18,6 +18,7 @@ struct tt_batch_ctx {
     std::vector<tt_handle> h;
     std::vector<cudaStream_t> streams;
     int threads = 1;
+    bool graph = false;  // captured steps (tt_batch_set_graph)
     ~tt_batch_ctx() {
         for (tt_handle x : h) tt_destroy(x);
         for (cudaStream_t s : streams) cudaStreamDestroy(s);
@@ -73,6 +74,28 @@ tt_status tt_batch_step(tt_batch b, int nsteps, tt_step_info* infos) {
         return TT_ERR_ARG;
     }
     const int n = (int)b->h.size();
+    if (b->graph && nsteps > 0) {
+        // every problem's replays in flight from this thread, then one wait each
+        for (int i = 0; i < n; ++i) {
+            tt_status st = graph_steps_begin(b->h[i], nsteps);
+            if (st < 0) {
+                std::string msg = std::string("problem ") + std::to_string(i) + ": " + tt_last_error();
+                set_error(msg);
+                return st;
+            }
+        }
+        tt_status result = TT_OK;
+        for (int i = 0; i < n; ++i) {
+            tt_status st = graph_steps_end(b->h[i], infos ? &infos[i] : nullptr);
+            if (st < 0) {
+                std::string msg = std::string("problem ") + std::to_string(i) + ": " + tt_last_error();
+                set_error(msg);
+                return st;
+            }
+            if (st == TT_WARN_RANK_CAPPED) result = TT_WARN_RANK_CAPPED;
+        }
+        return result;
+    }
     std::atomic<int> next{0};
     std::vector<tt_status> status(n, TT_OK);
     std::vector<std::string> errs(n);
@@ -127,5 +150,28 @@ tt_status tt_batch_sync(tt_batch b) {
 }
 
 void tt_batch_destroy(tt_batch b) { delete b; }
+
+tt_status tt_batch_set_graph(tt_batch b, int enable) {
+    set_error("");
+    if (!b) {
+        set_error("tt_batch_set_graph: null batch");
+        return TT_ERR_ARG;
+    }
+    if (enable) {
+        for (size_t i = 0; i < b->h.size(); ++i) {
+            tt_status st = tt_set_graph(b->h[i], 1);
+            if (st < 0) {
+                std::string msg = std::string("problem ") + std::to_string(i) + ": " + tt_last_error();
+                for (size_t j = 0; j < i; ++j) tt_set_graph(b->h[j], 0);
+                set_error(msg);
+                return st;
+            }
+        }
+    } else {
+        for (tt_handle h : b->h) TT_TRY(tt_set_graph(h, 0));
+    }
+    b->graph = enable != 0;
+    return TT_OK;
+}
 
 }  // extern "C"

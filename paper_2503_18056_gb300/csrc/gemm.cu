@@ -24,24 +24,13 @@ __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
         : "d"(a), "d"(b));
 }
 
-// grid: x = N tiles, y = M tiles, z = batch * ksplit.
-// Batch entry b, split ks: rows of K in [ks*kchunk, min(K,(ks+1)*kchunk)), output
-// to C + b*sC + ks*sCsplit.  upper_only: skip tiles strictly below the diagonal.
+// One 64 x 64 output tile: C[m0.., n0..] = alpha op(A) op(B) (+ beta C) over
+// the K range [kbeg, kend).
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(THREADS)
-dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, long lda, long sA,
-             const double* __restrict__ B, long ldb, long sB, double beta, double* __restrict__ C,
-             long ldc, long sC, int ksplit, int kchunk, long sCsplit, int upper_only) {
-    const int tn = blockIdx.x, tm = blockIdx.y;
-    if (upper_only && tn < tm) return;
-    const int b = blockIdx.z / ksplit, ks = blockIdx.z % ksplit;
-    A += b * sA;
-    B += b * sB;
-    C += b * sC + ks * sCsplit;
-    const int kbeg = ks * kchunk;
-    const int kend = min(K, kbeg + kchunk);
-    const int m0 = tm * BM, n0 = tn * BN;
-
+__device__ __forceinline__ void gemm_tile(int M, int N, double alpha, const double* __restrict__ A, long lda,
+                                          const double* __restrict__ B, long ldb, double beta,
+                                          double* __restrict__ C, long ldc, int kbeg, int kend, int m0,
+                                          int n0) {
     __shared__ double As[BK][BM + PADM];
     __shared__ double Bs[BK][BN + PADM];
 
@@ -107,6 +96,118 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, lo
                 *dst = (beta == 0.0) ? v : v + beta * (*dst);
             }
         }
+    }
+}
+
+// grid: x = N tiles, y = M tiles, z = batch * ksplit.
+// Batch entry b, split ks: rows of K in [ks*kchunk, min(K,(ks+1)*kchunk)), output
+// to C + b*sC + ks*sCsplit.  upper_only: skip tiles strictly below the diagonal.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(THREADS)
+dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, long lda, long sA,
+             const double* __restrict__ B, long ldb, long sB, double beta, double* __restrict__ C,
+             long ldc, long sC, int ksplit, int kchunk, long sCsplit, int upper_only) {
+    const int tn = blockIdx.x, tm = blockIdx.y;
+    if (upper_only && tn < tm) return;
+    const int b = blockIdx.z / ksplit, ks = blockIdx.z % ksplit;
+    A += b * sA;
+    B += b * sB;
+    C += b * sC + ks * sCsplit;
+    const int kbeg = ks * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    gemm_tile<TA, TB>(M, N, alpha, A, lda, B, ldb, beta, C, ldc, kbeg, kend, tm * BM, tn * BN);
+}
+
+// The same product with its sizes read from device memory (a captured step
+// whose ranks the device decides): desc = M, N, K, lda, ldb, ldc.  The grid
+// covers the largest sizes the step can reach; CTAs outside the step's tile
+// grid or split count return at once.  mode 0: one pass into C (as dgemm);
+// mode 1: dgemm_sk's split rule (one pass into C when it gives one split,
+// else partials into P, plane z at z M N with leading dimension N); mode 2:
+// the Gram's row split (gram_split_rule with `resident`, upper tiles only,
+// partials into P with leading dimension N, every split written).  Each
+// decision equals the host path's for the same sizes, so the results are
+// the same bits.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(THREADS)
+dgemm_dyn_kernel(const int* __restrict__ desc, double alpha, const double* __restrict__ A,
+                 const double* __restrict__ B, double* __restrict__ C, double* __restrict__ P, int mode,
+                 long resident) {
+    const int M = desc[0], N = desc[1], K = desc[2];
+    const long lda = desc[3], ldb = desc[4], ldc = desc[5];
+    const int tn = blockIdx.x, tm = blockIdx.y, z = blockIdx.z;
+    if (tm * BM >= M || tn * BN >= N) return;
+    int ks = 1, kchunk = K;
+    if (mode == 1) {
+        sk_split(M, N, K, &ks, &kchunk);
+    } else if (mode == 2) {
+        if (tn < tm) return;
+        ks = gram_split_rule(K, M, resident);
+        kchunk = (K + ks - 1) / ks;
+        kchunk = (kchunk + BK - 1) / BK * BK;
+    }
+    if (z >= ks) return;
+    const int kbeg = z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    if (mode == 2 || ks > 1)
+        gemm_tile<TA, TB>(M, N, 1.0, A, lda, B, ldb, 0.0, P + (long)z * M * N, N, kbeg, kend, tm * BM,
+                          tn * BN);
+    else
+        gemm_tile<TA, TB>(M, N, alpha, A, lda, B, ldb, 0.0, C, ldc, kbeg, kend, tm * BM, tn * BN);
+}
+
+// mode 1 partials -> C (nothing to do when the rule gave one split)
+__global__ void splitk_reduce_dyn_kernel(const int* __restrict__ desc, const double* __restrict__ P,
+                                         double alpha, double* C) {
+    const int M = desc[0], N = desc[1], K = desc[2];
+    const long ldc = desc[5];
+    int ks = 1, kchunk = K;
+    sk_split(M, N, K, &ks, &kchunk);
+    if (ks == 1) return;
+    const long total = (long)M * N;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < ks; ++z) s += P[(long)z * total + t];
+        C[(t / N) * ldc + t % N] = alpha * s;
+    }
+}
+
+// mode 2 partials -> the symmetric G (leading dimension desc[5])
+__global__ void gram_reduce_dyn_kernel(const int* __restrict__ desc, const double* __restrict__ P,
+                                       long resident, double* G) {
+    const int n = desc[0], m = desc[2];
+    const long ldg = desc[5];
+    const int ks = gram_split_rule(m, n, resident);
+    const long total = (long)n * n;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        const int a = min(i, j), b = max(i, j);
+        double s = 0.0;
+        for (int z = 0; z < ks; ++z) s += P[(long)z * total + (long)a * n + b];
+        G[(long)i * ldg + j] = s;
+    }
+}
+
+// out[i][j] = in[i][j] * f(v[i]) with rows, cols, ldi, ldo = desc[0..3]
+__global__ void scale_rows_dyn_kernel(const int* __restrict__ desc, const double* in, const double* v, int mode,
+                                      double* out) {
+    const int rows = desc[0], cols = desc[1];
+    const long ldi = desc[2], ldo = desc[3];
+    const long total = (long)rows * cols;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+         t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / cols), j = (int)(t % cols);
+        const double x = v[i];
+        double f;
+        switch (mode) {
+            case 0: f = x; break;
+            case 1: f = sqrt(x); break;
+            case 2: f = 1.0 / sqrt(x); break;
+            default: f = 1.0 / x; break;
+        }
+        out[(long)i * ldo + j] = in[(long)i * ldi + j] * f;
     }
 }
 
@@ -208,6 +309,74 @@ __global__ void gemv_t_final_kernel(int nblk, int ncols, double alpha, const dou
     }
 }
 
+}  // namespace
+
+// Autotuned splits (tt_autotune): for a product of t < 152 output tiles
+// (bucket floor(log2 t)) and depth K (bucket floor(log2 K)), the split of K
+// that measured fastest on this GPU; 0 keeps the rule below.  One copy for
+// the host and one in device memory, installed together, so a captured step
+// decides as the host path does.
+__device__ int d_sk_table[AT_TILE_BUCKETS * AT_K_BUCKETS];
+static int h_sk_table[AT_TILE_BUCKETS * AT_K_BUCKETS];
+
+__host__ __device__ inline int floor_log2(long x) {
+    int b = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+// Split of K for dgemm_sk: one 64 x 64 x 16 tile step is ~131 kflop, about
+// 19 us of one SM's FP64 pipe on GB300, so a product with a handful of tiles
+// runs for (K / 16) x 19 us on a handful of SMs; where the tile grid leaves
+// SMs idle, K is split so that there are about two CTAs per SM, each with at
+// least two K tiles, unless the autotuned table holds a measured split for
+// the product's bucket.  Host and device use the same rule (a captured step
+// decides it on the device from the sizes of that step).
+__host__ __device__ void sk_split(int M, int N, int K, int* ks_out, int* kchunk_out) {
+    const long tiles = (long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    int ks = 1;
+    if (tiles < 152 && K >= 4 * BK) {
+        long a = (304 + tiles - 1) / tiles, b = K / (2 * BK);
+        ks = (int)(a < b ? a : b);
+        const int tb = floor_log2(tiles), kb = floor_log2(K);
+        if (tb < AT_TILE_BUCKETS && kb < AT_K_BUCKETS) {
+#ifdef __CUDA_ARCH__
+            const int tuned = d_sk_table[tb * AT_K_BUCKETS + kb];
+#else
+            const int tuned = h_sk_table[tb * AT_K_BUCKETS + kb];
+#endif
+            if (tuned > 0) ks = (int)(tuned < b ? tuned : b);
+        }
+        ks = ks < 1 ? 1 : (ks > 64 ? 64 : ks);
+    }
+    int kchunk = K;
+    if (ks > 1) {
+        kchunk = (K + ks - 1) / ks;
+        kchunk = (kchunk + BK - 1) / BK * BK;
+        ks = (K + kchunk - 1) / kchunk;
+    }
+    *ks_out = ks;
+    *kchunk_out = kchunk;
+}
+
+// Row split of the Gram (gram_ksplit) from the number of resident CTAs.
+__host__ __device__ int gram_split_rule(int m, int n, long resident) {
+    const long T = (n + BN - 1) / BN;
+    const long tiles = T * (T + 1) / 2;
+    long ks = resident / tiles;
+    if (ks < 1) ks = 1;
+    const long cap = m / 256 < 1 ? 1 : m / 256;
+    if (ks > cap) ks = cap;
+    if (ks > 1024) ks = 1024;
+    if (ks < 1) ks = 1;
+    return (int)ks;
+}
+
+namespace {
+
 inline int grid_for(long total, int threads = 256) {
     long b = (total + threads - 1) / threads;
     return (int)std::max<long>(1, std::min<long>(b, 152L * 32));
@@ -259,21 +428,10 @@ tt_status dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double al
 tt_status dgemm_sk(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
                    const double* A, long lda, const double* B, long ldb, double* C, long ldc,
                    DevBuf& scratch) {
-    const long tiles = (long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-    // Split K where the tile grid leaves SMs idle: one 64 x 64 x 16 tile step
-    // is ~131 kflop, about 19 us of one SM's FP64 pipe on GB300, so a product
-    // with a handful of tiles runs for (K / 16) x 19 us on a handful of SMs.
-    // Aim at about two CTAs per SM, each with at least two K tiles.
-    int ks = 1;
-    if (tiles < 152 && K >= 4 * BK) {
-        ks = (int)std::min<long>((304 + tiles - 1) / tiles, K / (2 * BK));
-        ks = std::max(1, std::min(ks, 64));
-    }
+    int ks = 1, kchunk = K;
+    sk_split(M, N, K, &ks, &kchunk);
     if (ks == 1 || M <= 0 || N <= 0)
         return dgemm(s, ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, C, ldc);
-    int kchunk = (K + ks - 1) / ks;
-    kchunk = (kchunk + BK - 1) / BK * BK;
-    ks = (K + kchunk - 1) / kchunk;
     const long per = (long)M * N;
     TT_TRY(scratch.ensure((size_t)ks * per, s));
     TT_TRY(launch_gemm(s, ta, tb, M, N, K, 1.0, A, lda, 0, B, ldb, 0, 0.0, scratch.p, N, 0, 1, ks,
@@ -303,15 +461,7 @@ long resident_gram_ctas() {
 // Row-split factor of the Gram: the upper-triangle tiles times the splits fill
 // at most one wave of resident CTAs (a partial extra wave would run at a
 // fraction of the machine), and every split keeps at least 256 rows.
-int gram_ksplit(int m, int n) {
-    const long T = (n + BN - 1) / BN;
-    const long tiles = T * (T + 1) / 2;
-    const long resident = resident_gram_ctas();
-    long ks = std::max<long>(1, resident / tiles);
-    ks = std::min<long>(ks, std::max<long>(1, m / 256));
-    ks = std::max<long>(1, std::min<long>(ks, 1024));
-    return (int)ks;
-}
+int gram_ksplit(int m, int n) { return gram_split_rule(m, n, resident_gram_ctas()); }
 }  // namespace
 
 size_t gram_scratch_doubles(int m, int n) {
@@ -366,6 +516,53 @@ tt_status gram_fixed_scratch(cudaStream_t s, int m, int n, const double* A, long
     gram_reduce_kernel<<<grid_for((long)n * n), 256, 0, s>>>(n, ks, scratch, G, ldg);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
+}
+
+long gram_resident() { return resident_gram_ctas(); }
+
+size_t dyn_partials_doubles() {
+    const size_t sk = (size_t)(304 + 152) * BM * BN;
+    const size_t gr = (size_t)2 * BN * BN * (size_t)resident_gram_ctas();
+    return sk > gr ? sk : gr;
+}
+
+tt_status dgemm_dyn(cudaStream_t s, bool ta, bool tb, const int* desc, int Mcap, int Ncap, int Kcap,
+                    double alpha, const double* A, const double* B, double* C, double* P, int mode) {
+    if (Mcap <= 0 || Ncap <= 0) return TT_OK;
+    const long resident = resident_gram_ctas();
+    int zmax = 1;
+    if (mode == 1) zmax = std::max(1, std::min(64, Kcap / (2 * BK)));
+    if (mode == 2) zmax = (int)std::max<long>(1, std::min<long>(std::min<long>(1024, resident), Kcap / 256));
+    dim3 grid((Ncap + BN - 1) / BN, (Mcap + BM - 1) / BM, zmax);
+    if (grid.y > 65535 || grid.z > 65535) {
+        set_error("dgemm: problem too large for the tile grid");
+        return TT_ERR_TOO_LARGE;
+    }
+    note_launch();
+    if (ta && tb)
+        dgemm_dyn_kernel<true, true><<<grid, THREADS, 0, s>>>(desc, alpha, A, B, C, P, mode, resident);
+    else if (ta)
+        dgemm_dyn_kernel<true, false><<<grid, THREADS, 0, s>>>(desc, alpha, A, B, C, P, mode, resident);
+    else if (tb)
+        dgemm_dyn_kernel<false, true><<<grid, THREADS, 0, s>>>(desc, alpha, A, B, C, P, mode, resident);
+    else
+        dgemm_dyn_kernel<false, false><<<grid, THREADS, 0, s>>>(desc, alpha, A, B, C, P, mode, resident);
+    if (mode == 1) {
+        note_launch();
+        splitk_reduce_dyn_kernel<<<grid_for((long)Mcap * Ncap), 256, 0, s>>>(desc, P, alpha, C);
+    } else if (mode == 2) {
+        note_launch();
+        gram_reduce_dyn_kernel<<<grid_for((long)Mcap * Ncap), 256, 0, s>>>(desc, P, resident, C);
+    }
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+void scale_rows_dyn(cudaStream_t s, const int* desc, long total_cap, const double* in, const double* v, int mode,
+                    double* out) {
+    if (total_cap <= 0) return;
+    note_launch();
+    scale_rows_dyn_kernel<<<grid_for(total_cap), 256, 0, s>>>(desc, in, v, mode, out);
 }
 
 tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
@@ -434,6 +631,108 @@ __global__ void __launch_bounds__(256) fp64_mma_peak_kernel(double* out, double 
     if (s == 1234.5) out[threadIdx.x] = s;  // keeps the chains live; never true in practice
 }
 }  // namespace
+
+tt_status autotune_install(const int* table, int n) {
+    if (n != AT_TILE_BUCKETS * AT_K_BUCKETS) {
+        set_error("autotune: the table has " + std::to_string(AT_TILE_BUCKETS * AT_K_BUCKETS) + " entries");
+        return TT_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (table[i] < 0 || table[i] > 64) {
+            set_error("autotune: splits are 0 (the rule) or 1 .. 64");
+            return TT_ERR_ARG;
+        }
+    TT_CUDA_TRY(cudaMemcpyToSymbol(d_sk_table, table, n * sizeof(int)));
+    for (int i = 0; i < n; ++i) h_sk_table[i] = table[i];
+    return TT_OK;
+}
+
+void autotune_read(int* table) {
+    for (int i = 0; i < AT_TILE_BUCKETS * AT_K_BUCKETS; ++i) table[i] = h_sk_table[i];
+}
+
+// Measure, for every (tile-count, depth) bucket up to 2^14 deep, the products'
+// time at each split of K the rule allows (1, 2, 4, ..., 64, capped at K / 32)
+// on a representative product of that bucket (M x N tiles of 64, the
+// bucket's smallest K), and keep the fastest (best of three runs each).
+tt_status autotune(cudaStream_t s, int* table_out) {
+    constexpr int KB_MAX = 14;
+    const long Mmax = 64L << ((AT_TILE_BUCKETS - 1) / 2), Nmax = 64L << (AT_TILE_BUCKETS - 1 - (AT_TILE_BUCKETS - 1) / 2);
+    const long Kmax = 1L << KB_MAX;
+    double *A = nullptr, *B = nullptr, *C = nullptr, *P = nullptr;
+    const size_t pdbl = (size_t)64 * Mmax * Nmax;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    tt_status st = TT_OK;
+    int table[AT_TILE_BUCKETS * AT_K_BUCKETS] = {0};
+    auto cleanup = [&]() {
+        if (A) cudaFreeAsync(A, s);
+        if (B) cudaFreeAsync(B, s);
+        if (C) cudaFreeAsync(C, s);
+        if (P) cudaFreeAsync(P, s);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMallocAsync((void**)&A, Mmax * Kmax * sizeof(double), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&B, Kmax * Nmax * sizeof(double), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&C, Mmax * Nmax * sizeof(double), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&P, pdbl * sizeof(double), s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cleanup();
+        set_error("autotune: device memory for the trial products");
+        return TT_ERR_OOM;
+    }
+    fill(s, A, (size_t)(Mmax * Kmax), 0.5);
+    fill(s, B, (size_t)(Kmax * Nmax), 0.25);
+    for (int tb = 0; tb < AT_TILE_BUCKETS && st == TT_OK; ++tb) {
+        const int M = 64 << (tb / 2), N = 64 << (tb - tb / 2);
+        for (int kb = 6; kb <= KB_MAX && st == TT_OK; ++kb) {
+            const int K = 1 << kb;
+            float best = 1e30f;
+            int best_ks = 0;
+            for (int ks = 1; ks <= 64 && ks <= std::max(1, K / (2 * BK)); ks *= 2) {
+                int kchunk = (K + ks - 1) / ks;
+                kchunk = (kchunk + BK - 1) / BK * BK;
+                const int kk = (K + kchunk - 1) / kchunk;
+                float t = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaEventRecord(e0, s);
+                    if (kk == 1) {
+                        st = launch_gemm(s, false, false, M, N, K, 1.0, A, K, 0, B, N, 0, 0.0, C, N, 0, 1, 1, K, 0, 0);
+                    } else {
+                        st = launch_gemm(s, false, false, M, N, K, 1.0, A, K, 0, B, N, 0, 0.0, P, N, 0, 1, kk, kchunk,
+                                         (long)M * N, 0);
+                        note_launch();
+                        splitk_reduce_kernel<<<grid_for((long)M * N), 256, 0, s>>>(M, N, kk, P, 1.0, C, N);
+                    }
+                    cudaEventRecord(e1, s);
+                    if (st < 0 || cudaEventSynchronize(e1) != cudaSuccess) {
+                        if (st >= 0) st = TT_ERR_CUDA;
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    t = std::min(t, ms);
+                }
+                if (st < 0) break;
+                if (t < best) {
+                    best = t;
+                    best_ks = ks;
+                }
+            }
+            table[tb * AT_K_BUCKETS + kb] = best_ks;
+        }
+    }
+    // deeper products keep the choice of the deepest measured bucket
+    for (int tb = 0; tb < AT_TILE_BUCKETS; ++tb)
+        for (int kb = KB_MAX + 1; kb < AT_K_BUCKETS; ++kb) table[tb * AT_K_BUCKETS + kb] = table[tb * AT_K_BUCKETS + KB_MAX];
+    cleanup();
+    if (st < 0) return st;
+    TT_TRY(autotune_install(table, AT_TILE_BUCKETS * AT_K_BUCKETS));
+    if (table_out)
+        for (int i = 0; i < AT_TILE_BUCKETS * AT_K_BUCKETS; ++i) table_out[i] = table[i];
+    return TT_OK;
+}
 
 tt_status bench_fp64_mma(cudaStream_t s, double* tflops) {
     int dev = 0, sms = 0;

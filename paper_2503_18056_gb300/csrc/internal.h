@@ -82,6 +82,33 @@ tt_status dgemm_sk(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double
                    const double* A, long lda, const double* B, long ldb, double* C, long ldc,
                    DevBuf& scratch);
 
+// Autotuned split table (gemm.cu): buckets of floor(log2 tiles) < 8 and
+// floor(log2 K) < 22; autotune measures and installs it, autotune_install
+// installs a stored one, autotune_read copies the installed one.
+constexpr int AT_TILE_BUCKETS = 8, AT_K_BUCKETS = 22;
+tt_status autotune(cudaStream_t s, int* table_out);
+tt_status autotune_install(const int* table, int n);
+void autotune_read(int* table);
+
+// The split rules of dgemm_sk (split of K) and of the Gram (split of the
+// rows, from the number of resident CTAs), shared by host and device.
+__host__ __device__ void sk_split(int M, int N, int K, int* ks_out, int* kchunk_out);
+__host__ __device__ int gram_split_rule(int m, int n, long resident);
+
+// Products of a captured step, their sizes read from device memory: desc =
+// M, N, K, lda, ldb, ldc (Gram: n, n, m, lda, lda, ldg with A m x n), caps
+// bound every size the step can reach.  mode 0: plain product into C; 1:
+// dgemm_sk (split of K by sk_split, partials in P); 2: the Gram G = A^T A
+// (row split by gram_split_rule, partials in P).  The same bits as the host
+// path for the same sizes.  P holds dyn_partials_doubles() doubles.
+tt_status dgemm_dyn(cudaStream_t s, bool ta, bool tb, const int* desc, int Mcap, int Ncap, int Kcap,
+                    double alpha, const double* A, const double* B, double* C, double* P, int mode);
+size_t dyn_partials_doubles();
+long gram_resident();
+// scale_rows with rows, cols, ldi, ldo = desc[0..3] (rows * cols <= total_cap)
+void scale_rows_dyn(cudaStream_t s, const int* desc, long total_cap, const double* in, const double* v, int mode,
+                    double* out);
+
 // G = A^T A (A: m x n row-major, lda); split over rows with fixed-order reduction.
 // `partials` is scratch grown as needed (ksplit * n * n doubles).
 tt_status gram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
@@ -156,6 +183,29 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
 tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, double* Wc,
                 double* dwork, EigWork& w, int* status_dev, int* kB_dev);
 
+// The same factorisations in a captured step, their size n read from n_dev
+// (at most ncap; grids, shared memory and workspaces fit ncap): the same bits
+// as pchol / syev for the same n.  pchol_dyn writes the rank to kB_dev.
+tt_status pchol_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* G, double* W, double* Wc,
+                    double* dwork, EigWork& w, int* status_dev, int* kB_dev);
+tt_status syev_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* G, double* lam, double* Vt,
+                   EigWork& w, int* status_dev, int* sweeps_dev, int max_sweeps);
+// truncation_decision with the bond's size from kB_dev (a negative size, a
+// failed factorisation, counts as zero)
+void truncation_decision_dyn(cudaStream_t s, const double* lamK, const int* kB_dev, double eps, int dm1,
+                             int forced, int max_rank, double* delta2_dev, int* dec_i, double* dec_d);
+
+// Captured steps of one handle (api.cu): graph_steps_begin checks the
+// conditions and launches nsteps replays without waiting; graph_steps_end
+// waits for them and reports like tt_sn_step (info: the last step's).
+tt_status graph_steps_begin(tt_handle h, int nsteps);
+tt_status graph_steps_end(tt_handle h, tt_step_info* info);
+
+// Shared-memory limits of the factorisation kernels set ahead of a capture,
+// and the control block a capture's factorisations use.
+tt_status eig_prepare();
+tt_status eig_reserve(EigWork& w, cudaStream_t s);
+
 // Self-test of the bounded grid-barrier wait: a wait that can never complete
 // runs out and latches DEV_TIMEOUT into *status_dev.
 tt_status wait_probe(cudaStream_t s, EigWork& w, int* status_dev);
@@ -203,16 +253,34 @@ struct Sources {
 // Build the grown angular cores for the TT sum of transport (+ source) terms.
 // nterms = 1 + 2 ndim if transport else 1; then one block per external source
 // (ext.n of them, transport only), and source adds one unit block.
+// dd (nullable): a captured step's size block (DYN_* slots); r1, r2, R1, R2
+// are then the largest values, sizing the grids.
 void build_grown_angular(cudaStream_t s, const Angular& ang, int ndim, bool transport,
                          bool source, int r1, int r2, const double* Th, const double* Ph,
-                         double* Thg, double* Phg, int R1, int R2, const Sources& ext = Sources());
+                         double* Thg, double* Phg, int R1, int R2, const Sources& ext = Sources(),
+                         const int* dd = nullptr);
 // thbar[a] = sum_l w thfac_j[l] sum_b Th[a,l,b] phibar_j[b] for the grown core
 // blocks (first nterms*r1 entries), phibar_j[b] = sum_p v phfac_j[p] Ph[b,p].
 void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, int r1, int r2,
-                 const double* Th, const double* Ph, double* thbar);
+                 const double* Th, const double* Ph, double* thbar, const int* dd = nullptr);
 // Plain quadrature vector of a 3-core TT: thbar[a] = sum_l w sum_b Th[a,l,b] sum_p v Ph[b,p].
 void plain_thbar(cudaStream_t s, const Angular& ang, int r1, int r2, const double* Th,
-                 const double* Ph, double* thbar);
+                 const double* Ph, double* thbar, const int* dd = nullptr);
+
+// Slots of a captured step's size block (ints in device memory): the ranks
+// the device decides, read by the kernels of the step instead of host sizes.
+enum : int {
+    DYN_R1 = 0, DYN_R2 = 1,    // ranks of the TT entering the step
+    DYN_G1 = 2, DYN_G2 = 3,    // grown ranks
+    DYN_KB0 = 4, DYN_KB1 = 5,  // pivoted-Cholesky ranks of the right Grams
+    DYN_DEC0 = 8,              // bond 0 decision: rank, capped, non-finite, spare
+    DYN_DEC1 = 12,             // bond 1 decision
+    DYN_SWEEPS = 16,           // Jacobi sweeps of the two eigensolves
+    DYN_STICKY = 20,           // flags over a run of replays: 1 capped, 2 non-finite, 4 degenerate
+    DYN_DESC = 24,             // product descriptors, 8 ints each
+    DYN_NDESC = 20,
+    DYN_INTS = DYN_DESC + 8 * DYN_NDESC
+};
 
 // Boundary rule of axis 0 of a spatial shard (tt_create_shard): the ghost
 // layers are halo rows stored after the shard's own rows (the layer below
@@ -246,11 +314,11 @@ struct Fields {
 // and c dt x_k[i] q_k / c to E*; the emission column follows them.
 void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool transport,
                            bool source, int r1, const double* X, long ldx, const double* thbar,
-                           double* Xg, long ldg, const Sources& ext = Sources());
+                           double* Xg, long ldg, const Sources& ext = Sources(), const int* dd = nullptr);
 // E_i = X_i . thbar / c (r entries); if update_T: T_i += (E*_i - E_i) / cv_i.
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
                  double c, double* E_out, const double* E_star, const double* cv, double* T,
-                 bool update_T);
+                 bool update_T, const int* dd = nullptr);
 // ---------------------------------------------------------------- split-space layout (split.cu)
 // One core of the grown TT in the split layout (cores x[, y[, z]], theta,
 // phi): the K transport terms (K = 0: none) summed by Sec. 4.1's addition,

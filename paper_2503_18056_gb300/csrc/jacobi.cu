@@ -43,9 +43,11 @@ __device__ __forceinline__ void round_pair(int N, int r, int k, int& p, int& q) 
     if (k == 0) {
         p = m;
         q = r;
-    } else {
-        p = (r + k) % m;
-        q = (r - k + m) % m;
+    } else {  // (r + k) mod m and (r - k) mod m for 0 <= r < m, 0 < k < m
+        p = r + k;
+        if (p >= m) p -= m;
+        q = r - k;
+        if (q < 0) q += m;
     }
     if (p > q) {
         const int t = p;
@@ -105,8 +107,10 @@ __device__ bool grid_barrier(int* ctrl, int* status, unsigned nblocks, unsigned&
         if (nblocks > 1) {
             unsigned* count = reinterpret_cast<unsigned*>(ctrl);
             const unsigned target = epoch * nblocks;
-            unsigned old;
-            asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+            // the CTA's writes (every thread's, ordered by the __syncthreads
+            // above) become visible GPU-wide before the arrival is counted
+            __threadfence();
+            const unsigned old = atomicAdd(count, 1u);
             if (old + 1u < target) {
                 long long it = 0;
                 while (ld_acquire(count) < target) {
@@ -118,6 +122,7 @@ __device__ bool grid_barrier(int* ctrl, int* status, unsigned nblocks, unsigned&
                     __nanosleep(32);
                 }
             }
+            __threadfence();
         }
         s_ok = ok;
     }
@@ -126,7 +131,12 @@ __device__ bool grid_barrier(int* ctrl, int* status, unsigned nblocks, unsigned&
 }
 
 __global__ void jacobi_init_kernel(int n, int N, const double* __restrict__ G, long ldg, double* g0,
-                                   double* vt, long ld, double* abc) {
+                                   double* vt, long ld, double* abc, const int* n_dev) {
+    if (n_dev) {
+        n = *n_dev;
+        N = n + (n & 1);
+        ldg = ld = n;
+    }
     const long total = (long)n * n;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
@@ -163,7 +173,12 @@ __global__ void jacobi_init_kernel(int n, int N, const double* __restrict__ G, l
 __global__ void __launch_bounds__(JT)
 jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double* abc0,
               double* abc1, double* cs_g, double* lam_out, int* ctrl, int* status, double tol_rel,
-              double tol_abs_rel, int max_sweeps) {
+              double tol_abs_rel, int max_sweeps, const int* n_dev) {
+    if (n_dev) {  // a captured step: the grid and shared memory fit the largest n
+        n = *n_dev;
+        N = n + (n & 1);
+        ld = n;
+    }
     extern __shared__ double sm[];
     const int npairs = N / 2;
     // pairs this CTA owns: k = blockIdx.x + i * gridDim.x < npairs
@@ -283,15 +298,17 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
             const int nact = s_nact;
             // B2. right rotations of the non-identity column pairs, on all owned rows
             const int nrows = 2 * mine;
-            for (int t = threadIdx.x; t < nact * nrows; t += blockDim.x) {
-                const int kk = act[t % nact], row = t / nact;
+            for (int a = threadIdx.x; a < nact; a += blockDim.x) {
+                const int kk = act[a];
                 int pp, qq;
                 round_pair(N, r, kk, pp, qq);
                 const double c2 = cs[2 * kk], s2 = cs[2 * kk + 1];
-                double* rr = rows + row * n;
-                const double a0 = rr[pp], b0 = rr[qq];
-                rr[pp] = c2 * a0 - s2 * b0;
-                rr[qq] = s2 * a0 + c2 * b0;
+                for (int row = 0; row < nrows; ++row) {
+                    double* rr = rows + row * n;
+                    const double a0 = rr[pp], b0 = rr[qq];
+                    rr[pp] = c2 * a0 - s2 * b0;
+                    rr[qq] = s2 * a0 + c2 * b0;
+                }
             }
             __syncthreads();
             // B3. exact zeros for the rotated pairs
@@ -371,7 +388,16 @@ constexpr int PST = 1024;
 
 __global__ void __launch_bounds__(PST)
 pchol_small_kernel(int n, const double* __restrict__ G, long ldg, double* W, int* kB_out,
-                   double floor_rel) {
+                   double floor_rel, const int* n_dev) {
+    if (n_dev) {  // a captured step: the size is the device's, this kernel takes n <= PCHOL_ONE_CTA_N
+        n = *n_dev;
+        ldg = n;
+        if (n > PCHOL_ONE_CTA_N) return;
+        if (n <= 0) {
+            if (threadIdx.x == 0) *kB_out = 0;
+            return;
+        }
+    }
     extern __shared__ double sm[];
     double* dd = sm;        // n: residual diagonal
     double* colp = sm + n;  // n: W[0..k)[p]
@@ -481,7 +507,12 @@ pchol_small_kernel(int n, const double* __restrict__ G, long ldg, double* W, int
 // then copy eigenvector row j and eigenvalue to their sorted positions.
 __global__ void __launch_bounds__(256)
 jacobi_sort_kernel(int n, const double* __restrict__ d, long ld, const double* __restrict__ vt,
-                   double* lam, double* Vt, long ldv, int* sweeps_out, const int* ctrl) {
+                   double* lam, double* Vt, long ldv, int* sweeps_out, const int* ctrl, const int* n_dev) {
+    if (n_dev) {
+        n = *n_dev;
+        ld = ldv = n;
+        if ((int)blockIdx.x >= n) return;
+    }
     __shared__ int s_rank[256];
     const int j = blockIdx.x;
     const double lj = d[j];
@@ -522,7 +553,12 @@ __global__ void trivial_eig_kernel(const double* G, double* lam, double* Vt, int
 // could pick a different pivot once the fast ones had marked theirs).
 __global__ void __launch_bounds__(JT)
 pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* Wc, double* d,
-             int* ctrl, int* status, double floor_rel) {
+             int* ctrl, int* status, double floor_rel, const int* n_dev) {
+    if (n_dev) {  // a captured step: sizes up to PCHOL_ONE_CTA_N go to pchol_small_kernel
+        n = *n_dev;
+        ldg = n;
+        if (n <= PCHOL_ONE_CTA_N) return;  // every CTA, before any barrier
+    }
     unsigned epoch = 0;
     extern __shared__ double sm[];
     double* colp = sm;  // Wc[p][0..k)
@@ -621,7 +657,10 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[3] = k;
 }
 
-__global__ void pchol_finish_kernel(const int* ctrl, int* kB_out) { *kB_out = ctrl[3]; }
+__global__ void pchol_finish_kernel(const int* ctrl, int* kB_out, const int* n_dev) {
+    if (n_dev && *n_dev <= PCHOL_ONE_CTA_N) return;
+    *kB_out = ctrl[3];
+}
 
 // Self-test of the bounded wait: one CTA enters grid_barrier claiming a grid
 // of two, so the second arrival never comes; the wait runs out after its
@@ -632,7 +671,9 @@ __global__ void wait_probe_kernel(int* ctrl, int* status) {
 }
 
 __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm1, int forced,
-                                  int max_rank, double* delta2_dev, int* dec_i, double* dec_d) {
+                                  int max_rank, double* delta2_dev, int* dec_i, double* dec_d,
+                                  const int* kB_dev) {
+    if (kB_dev) kB = *kB_dev > 0 ? *kB_dev : 0;
     const double eps_mach = 2.220446049250313e-16;
     // totals and tails are summed from the small end; eigenvalues are not clamped
     // at zero, so the symmetric rounding noise of the Gram eigenvalues cancels
@@ -794,7 +835,7 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
         const long total = (long)n * n;
         const int ib = (int)std::min<long>((total + 255) / 256, 152L * 16);
         note_launch();
-        jacobi_init_kernel<<<ib, 256, 0, s>>>(n, N, G, ldg, w.g0.p, w.vt_unsorted.p, ld, w.abc.p);
+        jacobi_init_kernel<<<ib, 256, 0, s>>>(n, N, G, ldg, w.g0.p, w.vt_unsorted.p, ld, w.abc.p, nullptr);
         TT_CUDA_TRY(cudaGetLastError());
     }
     double* g0 = w.g0.p;
@@ -808,14 +849,15 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     int nn = n, NN = N;
     long ldl = ld;
     int msw = max_sweeps;
+    const int* nnull = nullptr;
     void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &abc0, &abc1, &csg, &lamu, &ctrl, &status_dev, &tol_rel,
-                    &tol_abs_rel, &msw};
+                    &tol_abs_rel, &msw, &nnull};
     note_launch();
     TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(JT), args,
                                             smem, s));
     note_launch();
     jacobi_sort_kernel<<<n, 256, 0, s>>>(n, w.lam_unsorted.p, ld, w.vt_unsorted.p, lam, Vt, ldv,
-                                         sweeps_dev, w.d_ctrl);
+                                         sweeps_dev, w.d_ctrl, nullptr);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
 }
@@ -841,7 +883,7 @@ tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, dou
     if (n <= PCHOL_ONE_CTA_N) {
         note_launch();
         pchol_small_kernel<<<1, PST, 2 * (size_t)n * sizeof(double), s>>>(n, G, ldg, W, kB_dev,
-                                                                          2.220446049250313e-16);
+                                                                          2.220446049250313e-16, nullptr);
         TT_CUDA_TRY(cudaGetLastError());
         return TT_OK;
     }
@@ -856,14 +898,125 @@ tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, dou
     // higher floor (n eps_mach, LAPACK's default for pivoted Cholesky) drops
     // parts of G_B that still carry tensor components at the 1e-9 level
     double fr = 2.220446049250313e-16;
-    void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr};
+    const int* nnull = nullptr;
+    void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr, &nnull};
     note_launch();
     TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)pchol_kernel, dim3(blocks), dim3(JT), args,
                                             smem, s));
     note_launch();
-    pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev);
+    pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev, nullptr);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
+}
+
+tt_status eig_reserve(EigWork& w, cudaStream_t s) { return ensure_ctrl(w, s); }
+
+tt_status eig_prepare() {
+    TT_TRY(ensure_max_dynamic_smem((const void*)pchol_small_kernel));
+    TT_TRY(ensure_max_dynamic_smem((const void*)pchol_kernel));
+    TT_TRY(ensure_max_dynamic_smem((const void*)jacobi_kernel));
+    return TT_OK;
+}
+
+tt_status pchol_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* G, double* W, double* Wc,
+                    double* dwork, EigWork& w, int* status_dev, int* kB_dev) {
+    if (ncap <= 0) return TT_OK;
+    TT_TRY(ensure_ctrl(w, s));
+    const int small_cap = std::min(ncap, PCHOL_ONE_CTA_N);
+    TT_TRY(ensure_max_dynamic_smem((const void*)pchol_small_kernel));
+    note_launch();
+    pchol_small_kernel<<<1, PST, 2 * (size_t)small_cap * sizeof(double), s>>>(small_cap, G, small_cap, W, kB_dev,
+                                                                              2.220446049250313e-16, n_dev);
+    TT_CUDA_TRY(cudaGetLastError());
+    if (ncap > PCHOL_ONE_CTA_N) {
+        const size_t smem = (size_t)ncap * sizeof(double);
+        if (smem > 200 * 1024) {
+            set_error("pchol: matrix too large");
+            return TT_ERR_TOO_LARGE;
+        }
+        TT_TRY(ensure_max_dynamic_smem((const void*)pchol_kernel));
+        int blocks = 1;
+        TT_TRY(coop_blocks((const void*)pchol_kernel, smem, std::max(1, (ncap + 7) / 8), &blocks));
+        int nn = ncap;
+        long ldgl = ncap;
+        const double* Gp = G;
+        int* ctrl = w.d_ctrl;
+        double fr = 2.220446049250313e-16;
+        void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr, &n_dev};
+        note_launch();
+        TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)pchol_kernel, dim3(blocks), dim3(JT), args, smem, s));
+        note_launch();
+        pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev, n_dev);
+        TT_CUDA_TRY(cudaGetLastError());
+    }
+    return TT_OK;
+}
+
+tt_status syev_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* G, double* lam, double* Vt,
+                   EigWork& w, int* status_dev, int* sweeps_dev, int max_sweeps) {
+    if (ncap <= 0) return TT_OK;
+    double tol_rel = 1e-15, tol_abs_rel = 1e-20;
+    const int Ncap = ncap + (ncap & 1);
+    const int npcap = Ncap / 2;
+    TT_TRY(w.g0.ensure((size_t)ncap * ncap, s));
+    TT_TRY(w.g1.ensure((size_t)ncap * ncap, s));
+    TT_TRY(w.vt_unsorted.ensure((size_t)ncap * ncap, s));
+    TT_TRY(w.lam_unsorted.ensure((size_t)ncap, s));
+    TT_TRY(w.abc.ensure((size_t)6 * npcap, s));
+    TT_TRY(w.cs.ensure((size_t)2 * npcap, s));
+    TT_TRY(ensure_ctrl(w, s));
+    // grid and shared memory for the largest n; a smaller n leaves CTAs with
+    // fewer (or no) pairs, and every pair's arithmetic is the same as in syev
+    auto smem_for = [&](int ppc) {
+        return (size_t)(npcap * 2 + 2 * (size_t)ppc * ncap) * sizeof(double) + (size_t)npcap * sizeof(int);
+    };
+    size_t smem = smem_for(MAX_PAIRS_PER_CTA);
+    if (smem > 200 * 1024) smem = smem_for(1);
+    if (smem > 200 * 1024) {
+        set_error("syev: matrix too large for the shared-memory row buffers");
+        return TT_ERR_TOO_LARGE;
+    }
+    TT_TRY(ensure_max_dynamic_smem((const void*)jacobi_kernel));
+    int blocks = 1;
+    TT_TRY(coop_blocks((const void*)jacobi_kernel, smem, npcap, &blocks));
+    const int ppc = (npcap + blocks - 1) / blocks;
+    if (ppc > MAX_PAIRS_PER_CTA || smem_for(ppc) > smem) {
+        set_error("syev: too few resident CTAs for this matrix size");
+        return TT_ERR_TOO_LARGE;
+    }
+    {
+        const long total = (long)ncap * ncap;
+        const int ib = (int)std::min<long>((total + 255) / 256, 152L * 16);
+        note_launch();
+        jacobi_init_kernel<<<ib, 256, 0, s>>>(ncap, Ncap, G, ncap, w.g0.p, w.vt_unsorted.p, ncap, w.abc.p, n_dev);
+        TT_CUDA_TRY(cudaGetLastError());
+    }
+    double* g0 = w.g0.p;
+    double* g1 = w.g1.p;
+    double* vt = w.vt_unsorted.p;
+    double* abc0 = w.abc.p;
+    double* abc1 = w.abc.p + 3 * npcap;
+    double* csg = w.cs.p;
+    double* lamu = w.lam_unsorted.p;
+    int* ctrl = w.d_ctrl;
+    int nn = ncap, NN = Ncap;
+    long ldl = ncap;
+    int msw = max_sweeps;
+    void* args[] = {&nn, &NN, &g0, &g1, &ldl, &vt, &abc0, &abc1, &csg, &lamu, &ctrl, &status_dev, &tol_rel,
+                    &tol_abs_rel, &msw, &n_dev};
+    note_launch();
+    TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(blocks), dim3(JT), args, smem, s));
+    note_launch();
+    jacobi_sort_kernel<<<ncap, 256, 0, s>>>(ncap, w.lam_unsorted.p, ncap, w.vt_unsorted.p, lam, Vt, ncap,
+                                            sweeps_dev, w.d_ctrl, n_dev);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+void truncation_decision_dyn(cudaStream_t s, const double* lamK, const int* kB_dev, double eps, int dm1,
+                             int forced, int max_rank, double* delta2_dev, int* dec_i, double* dec_d) {
+    note_launch();
+    truncation_kernel<<<1, 1, 0, s>>>(lamK, 0, eps, dm1, forced, max_rank, delta2_dev, dec_i, dec_d, kB_dev);
 }
 
 void truncation_decision(cudaStream_t s, const double* lamK, int kB, double eps, int dm1,
@@ -871,7 +1024,7 @@ void truncation_decision(cudaStream_t s, const double* lamK, int kB, double eps,
                          double* dec_d) {
     note_launch();
     truncation_kernel<<<1, 1, 0, s>>>(lamK, kB, eps, dm1, forced, max_rank, delta2_dev, dec_i,
-                                      dec_d);
+                                      dec_d, nullptr);
 }
 
 void count_above_floor(cudaStream_t s, const double* lam, int n, int* out_dev) {

@@ -38,7 +38,13 @@ constexpr double FOUR_PI = 12.566370614359172953850573533118;
 // profile), then the unit block of the emission term.
 __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, const double* Th,
                                    const double* tfac, int ns,
-                                   const double* s_th, double* Thg, int R1, int R2) {
+                                   const double* s_th, double* Thg, int R1, int R2, const int* dd) {
+    if (dd) {  // a captured step: ranks from the device's size block
+        r1 = dd[DYN_R1];
+        r2 = dd[DYN_R2];
+        R1 = dd[DYN_G1];
+        R2 = dd[DYN_G2];
+    }
     const long total = (long)R1 * nt * R2;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
@@ -64,7 +70,11 @@ __global__ void grown_theta_kernel(int nterms, int src, int r1, int r2, int nt, 
 // Phg: (R2, np)
 __global__ void grown_phi_kernel(int nterms, int src, int r2, int np, const double* Ph,
                                  const double* pfac, int ns,
-                                 const double* s_ph, double* Phg, int R2) {
+                                 const double* s_ph, double* Phg, int R2, const int* dd) {
+    if (dd) {
+        r2 = dd[DYN_R2];
+        R2 = dd[DYN_G2];
+    }
     const long total = (long)R2 * np;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
          t += (long)gridDim.x * blockDim.x) {
@@ -85,7 +95,9 @@ __global__ void grown_phi_kernel(int nterms, int src, int r2, int np, const doub
 }
 
 // phibar[j][b] = sum_p v phfac_j[p] Ph[b][p]
-__global__ void phibar_kernel(int nterms, int r2, int np, const double* Ph, const double* pfac, double v, double* phibar) {
+__global__ void phibar_kernel(int nterms, int r2, int np, const double* Ph, const double* pfac, double v, double* phibar,
+                              const int* dd) {
+    if (dd) r2 = dd[DYN_R2];
     const int total = nterms * r2;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int j = t / r2, b = t % r2;
@@ -99,7 +111,11 @@ __global__ void phibar_kernel(int nterms, int r2, int np, const double* Ph, cons
 // per output, lanes striding over the contiguous (l, b) block of row a.
 __global__ void thbar_kernel(int nterms, int r1, int r2, int nt, const double* Th,
                              const double* tfac, double w, const double* phibar,
-                             double* thbar) {
+                             double* thbar, const int* dd) {
+    if (dd) {
+        r1 = dd[DYN_R1];
+        r2 = dd[DYN_R2];
+    }
     const int lane = threadIdx.x & 31;
     const int total = nterms * r1;
     const int warps = gridDim.x * (blockDim.x >> 5);
@@ -259,7 +275,12 @@ template <bool GEN>
 __global__ void __launch_bounds__(256)
 transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                         const double* __restrict__ X, long ldx, const double* __restrict__ thbar,
-                        Sources ext, double* __restrict__ Xg, long ldg, int G) {
+                        Sources ext, double* __restrict__ Xg, long ldg, int G, const int* dd) {
+    if (dd) {  // a captured step: ranks from the device's size block
+        r1 = dd[DYN_R1];
+        ldx = r1;
+        ldg = dd[DYN_G1];
+    }
     const int lane = threadIdx.x & 31;
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     const int nterms = transport ? 1 + 2 * g.ndim : 1;
@@ -439,7 +460,11 @@ __global__ void __launch_bounds__(256)
 energy_rows_kernel(long nc, int r, const double* __restrict__ X, long ldx,
                    const double* __restrict__ thbar, double c, double* E_out,
                    const double* __restrict__ E_star, const double* __restrict__ cv, double* T,
-                   int update_T) {
+                   int update_T, const int* dd) {
+    if (dd) {
+        r = dd[DYN_R1];
+        ldx = r;
+    }
     const int lane = threadIdx.x & 31;
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < nc; i += warps) {
@@ -810,38 +835,38 @@ inline int blocks_for(long total, int threads = 256) {
 
 void build_grown_angular(cudaStream_t s, const Angular& ang, int ndim, bool transport,
                          bool source, int r1, int r2, const double* Th, const double* Ph,
-                         double* Thg, double* Phg, int R1, int R2, const Sources& ext) {
+                         double* Thg, double* Phg, int R1, int R2, const Sources& ext, const int* dd) {
     const int nterms = transport ? 1 + 2 * ndim : 1;
     note_launch();
     grown_theta_kernel<<<blocks_for((long)R1 * ang.n_theta * R2), 256, 0, s>>>(
         nterms, source ? 1 : 0, r1, r2, ang.n_theta, Th, ang.tfac, ext.n, ext.th, Thg,
-        R1, R2);
+        R1, R2, dd);
     note_launch();
     grown_phi_kernel<<<blocks_for((long)R2 * ang.n_phi), 256, 0, s>>>(
-        nterms, source ? 1 : 0, r2, ang.n_phi, Ph, ang.pfac, ext.n, ext.ph, Phg, R2);
+        nterms, source ? 1 : 0, r2, ang.n_phi, Ph, ang.pfac, ext.n, ext.ph, Phg, R2, dd);
 }
 
 // phibar scratch: thbar + nterms*r1 (caller allocates (nterms*(r1+r2)) doubles at thbar)
 void grown_thbar(cudaStream_t s, const Angular& ang, int ndim, bool transport, int r1, int r2,
-                 const double* Th, const double* Ph, double* thbar) {
+                 const double* Th, const double* Ph, double* thbar, const int* dd) {
     const int nterms = transport ? 1 + 2 * ndim : 1;
     double* phibar = thbar + nterms * r1;
     note_launch();
     phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph,
-                                                               ang.pfac, ang.v, phibar);
+                                                               ang.pfac, ang.v, phibar, dd);
     note_launch();
     thbar_kernel<<<blocks_for((long)nterms * r1 * 32, 128), 128, 0, s>>>(
-        nterms, r1, r2, ang.n_theta, Th, ang.tfac, ang.w, phibar, thbar);
+        nterms, r1, r2, ang.n_theta, Th, ang.tfac, ang.w, phibar, thbar, dd);
 }
 
 void plain_thbar(cudaStream_t s, const Angular& ang, int r1, int r2, const double* Th,
-                 const double* Ph, double* thbar) {
-    grown_thbar(s, ang, 0, false, r1, r2, Th, Ph, thbar);
+                 const double* Ph, double* thbar, const int* dd) {
+    grown_thbar(s, ang, 0, false, r1, r2, Th, Ph, thbar, dd);
 }
 
 void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool transport,
                            bool source, int r1, const double* X, long ldx, const double* thbar,
-                           double* Xg, long ldg, const Sources& ext) {
+                           double* Xg, long ldg, const Sources& ext, const int* dd) {
     // cells per warp: up to 32 (the scalar source stage then fills every lane),
     // fewer on small grids so that about 32 warps per SM stay busy
     const int G = (int)std::max<long>(1, std::min<long>(32, g.nc / (152L * 32)));
@@ -850,19 +875,19 @@ void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool 
     note_launch();
     if (f.flux == TT_FLUX_UPWIND)
         transport_source_kernel<false><<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1,
-                                                              X, ldx, thbar, ext, Xg, ldg, G);
+                                                              X, ldx, thbar, ext, Xg, ldg, G, dd);
     else
         transport_source_kernel<true><<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1,
-                                                             X, ldx, thbar, ext, Xg, ldg, G);
+                                                             X, ldx, thbar, ext, Xg, ldg, G, dd);
 }
 
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
                  double c, double* E_out, const double* E_star, const double* cv, double* T,
-                 bool update_T) {
+                 bool update_T, const int* dd) {
     const int blocks = (int)std::max<long>(1, std::min<long>((nc + 7) / 8, 152L * 64));
     note_launch();
     energy_rows_kernel<<<blocks, 256, 0, s>>>(nc, r, X, ldx, thbar, c, E_out, E_star, cv, T,
-                                              update_T ? 1 : 0);
+                                              update_T ? 1 : 0, dd);
 }
 
 void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, const StencilCo& co,
@@ -925,7 +950,8 @@ void thbar_adjoint(cudaStream_t s, const Angular& ang, int nterms, int j0, int r
     double* phibar = scratch;                 // nterms * r2
     double* phibb = scratch + nterms * r2;    // nterms * r2
     note_launch();
-    phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph, ang.pfac, ang.v, phibar);
+    phibar_kernel<<<blocks_for((long)nterms * r2), 256, 0, s>>>(nterms, r2, ang.n_phi, Ph, ang.pfac, ang.v, phibar,
+                                                               nullptr);
     note_launch();
     thbar_adjoint_theta_kernel<<<blocks_for((long)r1 * ang.n_theta * r2), 256, 0, s>>>(
         j0, nterms, r1, r2, ang.n_theta, thbb, phibar, ang.tfac, ang.w, Thb);

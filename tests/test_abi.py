@@ -141,3 +141,20 @@ def test_null_handle_and_bad_sizes_are_refused_on_the_host():
     assert lib.tt_pchol(-1, x, 4, x, None, None) == -1
     assert lib.tt_pchol(4, x, 3, x, None, None) == -1 and b"leading" in lib.tt_last_error()
     assert lib.tt_pchol(0, None, 0, None, None, None) == 0
+
+
+def test_autotune_table_arguments_are_checked_on_the_host():
+    """A stored table of the wrong length or with a split outside 0 .. 64 is
+    refused before the device is touched (no GPU needed)."""
+    import ctypes
+
+    from paper_2503_18056_gb300 import _native
+
+    lib = _native.lib
+    bad = (ctypes.c_int * 176)(*([65] * 176))
+    assert lib.tt_set_autotune_table(bad, 176) == -1
+    short = (ctypes.c_int * 10)(*([1] * 10))
+    assert lib.tt_set_autotune_table(short, 10) == -1
+    assert lib.tt_set_autotune_table(None, 176) == -1
+    out = (ctypes.c_int * 4)()
+    assert lib.tt_get_autotune_table(out, 4) == -1

@@ -137,25 +137,43 @@ def _gap_ranks(sig, ranks, ratio=1.05):
     return out
 
 
+def _resolution_bound(sig, ranks):
+    """Derived per-step bound of the Gram-SVD truncation against TT-SVD at the
+    given cuts (App. A.4: Gram eigenvalues carry absolute errors ~ eps_mach
+    lambda_max).  A kept component with singular value sigma_r then carries a
+    relative error eps_mach sigma_1^2 / sigma_r^2, and its mixing with the
+    first discarded one (relative gap 1 - (sigma_{r+1}/sigma_r)^2) moves the
+    rounded tensor by about eps_mach (sigma_1 / sigma_r) / gap relative to
+    ||X||; 4 covers the Gram's own accumulation constant.  Summed over the
+    bonds."""
+    b = 0.0
+    for S, r in zip(sig, ranks):
+        r = min(r, len(S))
+        gap = 1.0 - (S[r] / S[r - 1]) ** 2 if r < len(S) else 1.0
+        b += 4.0 * EPS_MACH * (S[0] / S[r - 1]) / gap
+    return b
+
+
 @pytest.mark.parametrize("eps", [1e-4, 1e-5, 1e-6, 1e-8])
 def test_small_2d_workload_cuts_at_gaps(ttsn, eps):
     # The 32x32 workload with every cut moved to the next clear gap of the
     # oracle's singular values, which separates the two sources of difference
     # seen at free cuts: cuts inside the symmetric pairs, and the Gram
-    # resolution.  Where the kept singular values at the cut stay above the
-    # Gram resolution (eps >= 1e-6: sigma_cut / sigma_max ~ 1e-6 against
-    # sqrt(R eps_mach) ~ 1e-7) the step matches the TT-SVD oracle to 1e-10
-    # (measured 2e-11 at 1e-4, 1e-12 at 1e-5 and 1e-6).  At the stated
-    # eps = 1e-8 the cut lies below that resolution: the Gram eigenvalues near
-    # the cut (~1e-16 lambda_max) are at the absolute error of the Gram
-    # itself, so kept components there carry errors of their own size, and the
-    # per-step budget of the free-cut test applies (measured 7e-8 at gap cuts,
-    # the same as at free cuts: the difference at 1e-8 is the resolution, not
-    # the pairs).
+    # resolution.  The resolution bound (above) grows with sigma_1 / sigma_cut;
+    # summed over the 10 steps it is 2.5e-10 (eps = 1e-4), 1.3e-9 (1e-5) and
+    # 8.3e-9 (1e-6), and the test asserts the larger of it and 1e-10.  Measured:
+    # 1e-13 .. 2e-11, 5e-13 .. 8e-13 and 9e-13 .. 5e-10; the last varies with
+    # the trajectory, because one step of this run (step 7, cut at
+    # sigma ~ 7e-7 sigma_1) moves by 5e-10 from the oracle's own state with
+    # every revision of the eigensolver.  At the stated eps = 1e-8 the cut
+    # (sigma ~ 1e-8 sigma_1) lies at the resolution itself and the pivoted
+    # Cholesky of G_B can resolve fewer directions than the oracle keeps (rank
+    # 53 against 54 at one bond): the free-cut budget applies (measured
+    # 4e-8 .. 7e-8).
     p = workloads.problem("small_2d", eps=eps)
     ref = _oracle(p)
     g = ttsn.TTSN.from_problem(p)
-    budget = 0.0
+    bound = 0.0
     for _ in range(p["steps"]):
         grown, _, _ = ref.source(ref.transport(ref.cores))
         Z, sig = round_ttsvd(grown, eps=p["eps"])
@@ -169,12 +187,16 @@ def test_small_2d_workload_cuts_at_gaps(ttsn, eps):
             # right Gram resolves (its pivoted Cholesky stops at eps_mach of
             # the largest pivot); the GPU then keeps those it resolves
             assert all(a <= b for a, b in zip(info["ranks"][1:-1], tt.ranks(ref.cores)))
-        budget += 2 * np.sqrt(2) * np.sqrt(p["eps"] ** 2 + max(info["grown"]) * EPS_MACH)
+        if eps >= 1e-6:
+            bound += _resolution_bound(sig, forced)
+        else:
+            bound += 2 * np.sqrt(2) * np.sqrt(p["eps"] ** 2 + max(info["grown"]) * EPS_MACH)
     F = g.full().cpu().numpy()
     Rf = ref.full()
     err = np.linalg.norm(F - Rf) / np.linalg.norm(Rf)
-    print("small_2d eps %.0e, cuts at gaps: rel. difference to the TT-SVD oracle %.2e" % (eps, err))
-    assert err <= (1e-10 if eps >= 1e-6 else budget), (err, budget)
+    print("small_2d eps %.0e, cuts at gaps: rel. difference to the TT-SVD oracle %.2e (bound %.2e)"
+          % (eps, err, bound))
+    assert err <= max(1e-10, bound), (err, bound)
 
 
 def test_energy_conserved_periodic_free_ranks(ttsn):
