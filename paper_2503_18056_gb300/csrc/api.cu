@@ -292,6 +292,7 @@ struct tt_ctx {
     Angular ang{};
     Fields fields{};
     DevBuf f_sigma_a, f_sigma_s, f_cv, f_T, f_Estar, f_E, thbar, red, ang_buf;
+    DevBuf ydots;  // the cells' term dots X_i . thbar_j of the source stage
     DevBuf src_x, src_th, src_ph, src_q;  // fixed external sources (all kinds)
     int nsrc = 0;
     // the caller's own sources (tt_set_sources) and the inflow faces
@@ -393,7 +394,7 @@ struct tt_ctx {
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
                           &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph,
-                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs, &xch, &dyn_buf, &dyn_part};
+                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs, &xch, &dyn_buf, &dyn_part, &ydots};
         for (DevBuf* b : bufs) b->release();
         for (auto& ax : inflow)
             for (auto& face : ax) face.g.release();
@@ -1079,8 +1080,10 @@ tt_status apply_terms(tt_ctx* h, bool transport, bool source) {
     h->fields.T = h->f_T.p;
     h->fields.E_star = h->f_Estar.p;
     if (h->shard.on && transport) TT_TRY(shard_halo(h, r1));
+    if (source)  // a shard's halo layers carry dots too
+        TT_TRY(h->ydots.ensure((size_t)(nc + (h->shard.on && transport ? 2 * h->shard.plane : 0)) * nterms, s));
     transport_source_rows(s, h->grid, h->fields, transport, source, r1, h->core[0].p, r1,
-                          source ? h->thbar.p : nullptr, h->gcore[0].p, R1, ext);
+                          source ? h->thbar.p : nullptr, h->gcore[0].p, R1, h->ydots.p, ext);
     TT_CUDA_TRY(cudaGetLastError());
     h->gr[0] = 1;
     h->gr[1] = R1;
@@ -1256,7 +1259,7 @@ tt_status graph_step_body(tt_ctx* h) {
     h->fields.T = h->f_T.p;
     h->fields.E_star = h->f_Estar.p;
     transport_source_rows(s, g, h->fields, true, true, c1, h->core[0].p, c1, h->thbar.p, h->gcore[0].p, G1,
-                          Sources(), dd);
+                          h->ydots.p, Sources(), dd);
     // rounding (App. A.2, one-sided Gram truncation): backward sweep
     fill(s, h->d_dbl + HD_DELTA2, 1, -1.0);
     TT_TRY(dgemm_dyn(s, false, true, desc + 0, G2, G2, np, 1.0, h->gcore[2].p, h->gcore[2].p, h->GB[1].p, P, 1));
@@ -1326,7 +1329,7 @@ tt_status graph_reserve(tt_ctx* h) {
         {&h->lamB[0], 2 * G1}, {&h->lamB[1], 2 * G2}, {&h->Wc, Gm * Gm}, {&h->GA, Gm * Gm},
         {&h->T1, Gm * Gm}, {&h->K, Gm * Gm}, {&h->lamK, Gm}, {&h->VtK, Gm * Gm},
         {&h->Vts, Gm * Gm}, {&h->PAt, Gm * Gm}, {&h->Mupd, Gm * Gm}, {&h->bwd, G1 * nt * G2},
-        {&h->tmp[0], c1 * nt * G2}, {&h->thbar, nterms * (c1 + c2) + 2},
+        {&h->tmp[0], c1 * nt * G2}, {&h->thbar, nterms * (c1 + c2) + 2}, {&h->ydots, nc * nterms},
         {&h->eig.g0, Gm * Gm}, {&h->eig.g1, Gm * Gm}, {&h->eig.vt_unsorted, Gm * Gm},
         {&h->eig.lam_unsorted, Gm}, {&h->eig.abc, 3 * (Gm + 1)}, {&h->eig.cs, Gm + 1},
         {&h->dyn_part, (long)dyn_partials_doubles()},
@@ -2062,6 +2065,7 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
         TT_CREATE_TRY(h->tmp[0].ensure((size_t)(cap1 * D.n_theta * R2), s));
         TT_CREATE_TRY(h->tmp[1].ensure((size_t)(cap1 * D.n_theta * R2), s));
         TT_CREATE_TRY(h->thbar.ensure((size_t)(nterms * (cap1 + cap2) + 2), s));
+        TT_CREATE_TRY(h->ydots.ensure((size_t)(nc * nterms), s));
         if (D.precision == TT_MIXED) TT_CREATE_TRY(h->slscratch.ensure((size_t)(nc + R1) / 2 + 2, s));
     }
     init_isotropic(s, nc, (D.Tr0 ? D.Tr0 : D.T0) + cell0, D.c, D.a_r, h->core[0].p);

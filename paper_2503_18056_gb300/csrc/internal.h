@@ -309,12 +309,14 @@ struct Fields {
 // Fused transport + source row kernel (Sec. 4.3-4.4).  Writes Xg (nc x R1,
 // ld = ldg): transport blocks then (if source) scaled by s_i and the emission
 // column.  Computes E* (the post-transport energy) into fields.E_star when
-// source is set.  thbar: grown quadrature vector (nterms*r1 entries).
+// source is set, from the cells' term dots X_i . thbar_j (ydots: nc x nterms
+// doubles of scratch).  thbar: grown quadrature vector (nterms*r1 entries).
 // External sources (transport only) add columns nterms r1 + k = s_i c dt x_k[i]
 // and c dt x_k[i] q_k / c to E*; the emission column follows them.
 void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool transport,
                            bool source, int r1, const double* X, long ldx, const double* thbar,
-                           double* Xg, long ldg, const Sources& ext = Sources(), const int* dd = nullptr);
+                           double* Xg, long ldg, double* ydots, const Sources& ext = Sources(),
+                           const int* dd = nullptr);
 // E_i = X_i . thbar / c (r entries); if update_T: T_i += (E*_i - E_i) / cv_i.
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
                  double c, double* E_out, const double* E_star, const double* cv, double* T,

@@ -4,12 +4,14 @@
 // 1. Symmetric eigensolver: two-sided cyclic Jacobi with the parallel
 //    round-robin ("circle") ordering.  Each round applies n/2 disjoint plane
 //    rotations at once: G <- J^T G J, Vt <- J^T Vt.  A CTA owns a few row pairs
-//    (p, q) per round: it loads those rows with coalesced L2 reads, rotates them
-//    on the left by their own J_k, rotates every column pair in shared memory,
-//    and writes them to the other buffer (the matrix is double-buffered, so a
-//    round needs one grid-wide barrier).  The three entries (g_pp, g_qq, g_pq)
-//    that define the next round's rotations are written by the row owners into
-//    a compact array, so every CTA reads them with one coalesced load.  Rotation
+//    (p, q) per round: it forms those pairs' rotation angles and publishes them,
+//    loads the rows with coalesced L2 reads and rotates them on the left by
+//    their own J_k; after a grid-wide barrier it reads every pair's angles,
+//    rotates the non-identity column pairs in shared memory and writes the rows
+//    to the other buffer (the matrix is double-buffered; a second barrier ends
+//    the round).  The three entries (g_pp, g_qq, g_pq) that define the next
+//    round's rotations are written by the row owners into a compact array, so
+//    the owning CTA reads them with one coalesced load.  Rotation
 //    angles follow Golub & Van Loan, Alg. 8.4.1 (symSchur2); a rotation is
 //    skipped when |g_pq| <= tol_rel sqrt(|g_pp g_qq|) or |g_pq| <= tol_abs, and
 //    the sweeps stop after one that skipped every rotation.
@@ -82,11 +84,6 @@ __device__ __forceinline__ void pair_of(int N, int r, int x, int& k, int& partne
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_relaxed(const int* p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 

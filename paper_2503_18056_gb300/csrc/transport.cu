@@ -197,9 +197,6 @@ __device__ double t_dagger(double Tm, double Estar, double ka, double Cv, double
     return T;
 }
 
-// Row value of the transport terms of cell i at column col (the upwind
-// differences of Sec. 4.3 with the ghost rows of Sec. 4.5): the quadrature
-// dot product with thbar over all term blocks.
 // Stencil coefficients of the two transport terms of every axis for cell i:
 // term t of axis a is c0 X_i + cp X_{i+1} - cm X_{i-1} with c0 = w_L(i+1/2) -
 // w_R(i-1/2), cp = w_R(i+1/2), cm = w_L(i-1/2) (the face weights of the flux;
@@ -228,10 +225,8 @@ __device__ __forceinline__ void stencil_coefs(const Fields& f, int ndim, long i,
     }
 }
 
-// Row value of the transport terms of cell i at column col (Sec. 4.3 with the
-// ghost rows of Sec. 4.5): the quadrature dot product with thbar over all
-// term blocks.
-// The two terms of axis a at one column: upwinding (GEN = false) takes the
+// The two terms of axis a at one column (Sec. 4.3 with the ghost rows of
+// Sec. 4.5): upwinding (GEN = false) takes the
 // plain differences x0 - xm and xp - x0 (fewer FP64 operations, the common
 // case); other fluxes the face-weighted stencil.
 template <bool GEN>
@@ -246,35 +241,51 @@ __device__ __forceinline__ void axis_terms(const double (&co)[3][2][3], int a, d
     }
 }
 
-template <bool GEN>
-__device__ __forceinline__ double transport_dot(const Grid& g, const double* nu, const long (&nb)[3][2],
-                                                const double (&co)[3][2][3], int transport, int r1,
-                                                const double* X, long ldx, long i, int col,
-                                                const double* thbar) {
-    const double x0 = X[i * ldx + col];
-    double dot = x0 * thbar[col];
-    if (transport)
-        for (int a = 0; a < g.ndim; ++a) {
-            const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
-            const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-            double t1, t2;
-            axis_terms<GEN>(co, a, x0, xm, xp, t1, t2);
-            dot += -nu[a] * t1 * thbar[(1 + 2 * a) * r1 + col];
-            dot += -nu[a] * t2 * thbar[(2 + 2 * a) * r1 + col];
+// y[i][j] = X_i . thbar_j for the 1 + 2 ndim transport terms j (the grown
+// quadrature vector's blocks): one warp per cell, lanes over the columns.
+// Because every transport term is linear in X, the quadrature of cell i's
+// grown row is a combination of these dots at i and its neighbours, which
+// the source stage then forms with a few scalar operations per cell.
+__global__ void __launch_bounds__(256)
+term_dots_kernel(long nrows, int nterms, int r1, const double* __restrict__ X, long ldx,
+                 const double* __restrict__ thbar, double* __restrict__ y, const int* dd) {
+    if (dd) {
+        r1 = dd[DYN_R1];
+        ldx = r1;
+    }
+    const int lane = threadIdx.x & 31;
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < nrows; i += warps) {
+        double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int col = lane; col < r1; col += 32) {
+            const double x = X[i * ldx + col];
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+                if (j < nterms) acc[j] += x * thbar[j * r1 + col];
         }
-    return dot;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            if (j >= nterms) break;
+            double v = acc[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) y[i * nterms + j] = v;
+        }
+    }
 }
 
-// A warp takes G <= 32 consecutive cells.  Pass 1: for each cell the lanes split
-// the columns of the quadrature dot product (E*) and lane j keeps cell j's
-// sum; then every lane solves the source stage (quartic, s, e) of its own
-// cell, so the per-cell scalar FP64 work is done once, not once per lane.
-// Pass 2: for each cell the lanes write the scaled row, the external-source
-// columns and the emission column (scale and emission broadcast by shuffle).
+// A warp takes G <= 32 consecutive cells; lane j owns cell i0 + j for the
+// scalar work.  Source stage: lane j forms its cell's E* from the term dots y
+// of the cell and its neighbours (the transport terms' quadrature, Sec. 4.1
+// Eq. tt_energy_density, taken through the linear stencil) and the external
+// sources, then solves the quartic and forms the row scale s and the emission
+// e (Sec. 3.2).  Row pass: for each cell the lanes write the scaled row, the
+// scaled transport terms (the factor -s nu_a folded into one product per
+// term and column), the external-source columns and the emission column.
 template <bool GEN>
 __global__ void __launch_bounds__(256)
 transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
-                        const double* __restrict__ X, long ldx, const double* __restrict__ thbar,
+                        const double* __restrict__ X, long ldx, const double* __restrict__ y,
                         Sources ext, double* __restrict__ Xg, long ldg, int G, const int* dd) {
     if (dd) {  // a captured step: ranks from the device's size block
         r1 = dd[DYN_R1];
@@ -290,37 +301,38 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
          i0 += warps * G) {
         const int cnt = (int)min((long)G, g.nc - i0);
         double scale = 1.0, emit = 0.0;
-        if (source) {
-            double mine = 0.0;
-            for (int j = 0; j < cnt; ++j) {
-                const long i = i0 + j;
+        if (source && lane < cnt) {
+            const long i = i0 + lane;
+            double dot = y[i * nterms];
+            if (transport) {
                 long nb[3][2];
                 cell_neighbours(g, i, nb);
                 double co[3][2][3];
                 if (GEN) stencil_coefs(f, g.ndim, i, co);
-                double dot = 0.0;
-                for (int col = lane; col < r1; col += 32)
-                    dot += transport_dot<GEN>(g, nu, nb, co, transport, r1, X, ldx, i, col, thbar);
-                // external sources: c dt x_k[i] times their quadrature q_k
-                for (int k = lane; k < ext.n; k += 32)
-                    dot += f.c * f.dt * ext.x[(long)k * g.nc + i] * ext.q[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                if (lane == j) mine = dot;
+                for (int a = 0; a < g.ndim; ++a) {
+                    const int j1 = 1 + 2 * a, j2 = 2 + 2 * a;
+                    const double m1 = nb[a][0] >= 0 ? y[nb[a][0] * nterms + j1] : 0.0;
+                    const double p1 = nb[a][1] >= 0 ? y[nb[a][1] * nterms + j1] : 0.0;
+                    const double m2 = nb[a][0] >= 0 ? y[nb[a][0] * nterms + j2] : 0.0;
+                    const double p2 = nb[a][1] >= 0 ? y[nb[a][1] * nterms + j2] : 0.0;
+                    double t1, t2, u1, u2;
+                    axis_terms<GEN>(co, a, y[i * nterms + j1], m1, p1, t1, u1);
+                    axis_terms<GEN>(co, a, y[i * nterms + j2], m2, p2, u2, t2);
+                    dot += -nu[a] * t1 + -nu[a] * t2;
+                }
             }
-            if (lane < cnt) {
-                const long i = i0 + lane;
-                const double Estar = mine / f.c;
-                const double ka = f.c * f.dt * f.sigma_a[i];
-                const double ks = f.sigma_s ? f.c * f.dt * f.sigma_s[i] : 0.0;
-                const double Td = t_dagger(f.T[i], Estar, ka, f.cv[i], f.a_r);
-                const double Td2 = Td * Td;
-                const double B = f.c * f.a_r * Td2 * Td2 / FOUR_PI;
-                const double Jnew = (f.c * Estar / FOUR_PI + ka * B) / (1.0 + ka);
-                scale = 1.0 / (1.0 + ka + ks);
-                emit = scale * (ks * Jnew + ka * B);
-                f.E_star[i] = Estar;
-            }
+            // external sources: c dt x_k[i] times their quadrature q_k
+            for (int k = 0; k < ext.n; ++k) dot += f.c * f.dt * ext.x[(long)k * g.nc + i] * ext.q[k];
+            const double Estar = dot / f.c;
+            const double ka = f.c * f.dt * f.sigma_a[i];
+            const double ks = f.sigma_s ? f.c * f.dt * f.sigma_s[i] : 0.0;
+            const double Td = t_dagger(f.T[i], Estar, ka, f.cv[i], f.a_r);
+            const double Td2 = Td * Td;
+            const double B = f.c * f.a_r * Td2 * Td2 / FOUR_PI;
+            const double Jnew = (f.c * Estar / FOUR_PI + ka * B) / (1.0 + ka);
+            scale = 1.0 / (1.0 + ka + ks);
+            emit = scale * (ks * Jnew + ka * B);
+            f.E_star[i] = Estar;
         }
         for (int j = 0; j < cnt; ++j) {
             const long i = i0 + j;
@@ -330,6 +342,8 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
             cell_neighbours(g, i, nb);
             double co[3][2][3];
             if (GEN) stencil_coefs(f, g.ndim, i, co);
+            double fa[3];
+            for (int a = 0; a < g.ndim; ++a) fa[a] = -sc * nu[a];
             double* out = Xg + i * ldg;
             for (int col = lane; col < r1; col += 32) {
                 const double x0 = X[i * ldx + col];
@@ -340,8 +354,8 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                         const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
                         double t1, t2;
                         axis_terms<GEN>(co, a, x0, xm, xp, t1, t2);
-                        out[(1 + 2 * a) * r1 + col] = sc * (-nu[a] * t1);
-                        out[(2 + 2 * a) * r1 + col] = sc * (-nu[a] * t2);
+                        out[(1 + 2 * a) * r1 + col] = fa[a] * t1;
+                        out[(2 + 2 * a) * r1 + col] = fa[a] * t2;
                     }
                 }
             }
@@ -866,7 +880,16 @@ void plain_thbar(cudaStream_t s, const Angular& ang, int r1, int r2, const doubl
 
 void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool transport,
                            bool source, int r1, const double* X, long ldx, const double* thbar,
-                           double* Xg, long ldg, const Sources& ext, const int* dd) {
+                           double* Xg, long ldg, double* ydots, const Sources& ext, const int* dd) {
+    const int nterms = transport ? 1 + 2 * g.ndim : 1;
+    if (source) {
+        // a shard's stencil also reads the dots of its two halo layers (rows
+        // nc .. nc + 2 stride - 1, BC_HALO on axis 0)
+        const long ny = g.nc + (transport && g.bc[0] == BC_HALO ? 2 * (g.nc / g.n[0]) : 0);
+        const int yb = (int)std::max<long>(1, std::min<long>((ny + 7) / 8, 152L * 64));
+        note_launch();
+        term_dots_kernel<<<yb, 256, 0, s>>>(ny, nterms, r1, X, ldx, thbar, ydots, dd);
+    }
     // cells per warp: up to 32 (the scalar source stage then fills every lane),
     // fewer on small grids so that about 32 warps per SM stay busy
     const int G = (int)std::max<long>(1, std::min<long>(32, g.nc / (152L * 32)));
@@ -875,10 +898,10 @@ void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool 
     note_launch();
     if (f.flux == TT_FLUX_UPWIND)
         transport_source_kernel<false><<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1,
-                                                              X, ldx, thbar, ext, Xg, ldg, G, dd);
+                                                              X, ldx, ydots, ext, Xg, ldg, G, dd);
     else
         transport_source_kernel<true><<<blocks, 256, 0, s>>>(g, f, transport ? 1 : 0, source ? 1 : 0, r1,
-                                                             X, ldx, thbar, ext, Xg, ldg, G, dd);
+                                                             X, ldx, ydots, ext, Xg, ldg, G, dd);
 }
 
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
