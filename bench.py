@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--line-source-steps", type=int, default=121,
                     help="timed steps of the line-source leg (0: to t = 1, 568 steps)")
     ap.add_argument("--no-randomized", action="store_true", help="skip the randomized-rounding companion run")
+    ap.add_argument("--no-ttsvd", action="store_true", help="skip the TT-SVD against Gram-SVD rounding comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in split rule (no tt_autotune)")
     ap.add_argument("--only", choices=["adjoint", "beams", "batch", "split", "fluxes", "schedule", "line_source"], default=None,
                     help="run only this companion leg and print its JSON (profiling)")
@@ -287,6 +288,43 @@ def run_ours(args, rank, world, local_rank):
             del gr
             torch.cuda.synchronize()
 
+        # QR-based TT-SVD rounding (App. A.1) against the Gram-SVD rounding on
+        # one step from the same capped state (the end of the FP64 run): the
+        # paper's cost comparison of the two roundings (Sec. 4.2, Table 3)
+        ttsvd = None
+        if not args.no_ttsvd:
+            cap_cores = [c.clone() for c in g.cores()]
+            _, cap_T, _ = g.energy()
+            cap_T = cap_T.clone()
+            legs = {}
+            for method in ("gram", "ttsvd"):
+                gt = ttsn.TTSN.from_problem(p, max_rank=p.get("max_rank", 0), stream=stream)
+                gt.set_rounding(method)
+                forced = legs["gram"]["ranks"] if method == "ttsvd" else None
+                for timed in (False, True):  # the first step sizes the buffers
+                    gt.set_cores(cap_cores)
+                    gt.set_T(cap_T)
+                    torch.cuda.synchronize()
+                    gt.profile(timed)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    info = gt.step(forced=forced)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                tprof = gt.profile_read()
+                gt.profile(False)
+                Et, _, _ = gt.energy()
+                legs[method] = dict(ms=e0.elapsed_time(e1), ranks=info["ranks"][1:-1], E=Et.clone(),
+                                    rounding_ms=sum(v["ms"] for k_, v in tprof.items()
+                                                    if k_ not in ("transport", "energy")),
+                                    phases={k_: round(v["ms"], 3) for k_, v in tprof.items()})
+                del gt
+                torch.cuda.synchronize()
+            Eg, Ets = legs["gram"].pop("E"), legs["ttsvd"].pop("E")
+            ttsvd = dict(legs=legs, err_E=((Ets - Eg).abs().max() / Eg.abs().max()).item(), step=args.steps + 1)
+            del cap_cores
+            torch.cuda.synchronize()
+
         # end to end through the public API: the state lives on the host between
         # steps (pinned), copied in before and out after every step
         e2e = None
@@ -334,7 +372,7 @@ def run_ours(args, rank, world, local_rank):
     res = dict(total_ms=total_ms, step_ms=step_ms, ranks=ranks_hist, prof=prof, launches=launches, autotune=tune,
                clocks=clk, e2e=e2e, fp64_peak=fp64_peak, totals=tot, p=p, mixed=mixed, batched=batched,
                adjoint=adjoint, beams=beams, split=split, fluxes=fluxes, schedule=schedule, line_source=line_source,
-               randomized=randomized)
+               randomized=randomized, ttsvd=ttsvd)
     return res
 
 
@@ -960,6 +998,18 @@ def main():
                       % OVERSAMPLE,
             "err_vs_fp64_gram": {"E_max_rel": rz["err_E"], "T_max_rel": rz["err_T"]},
             "phases": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in rz["prof"].items()}}
+    ts = res.get("ttsvd")
+    if ts is not None:
+        lg, lt = ts["legs"]["gram"], ts["legs"]["ttsvd"]
+        line["ttsvd"] = {
+            "workload": "one step (step %d of the trajectory) from the capped state at the end of the FP64 run, "
+                        "TT-SVD at the Gram-SVD step's ranks" % ts["step"],
+            "gram_step_ms": round(lg["ms"], 3), "ttsvd_step_ms": round(lt["ms"], 3),
+            "gram_rounding_ms": round(lg["rounding_ms"], 3), "ttsvd_rounding_ms": round(lt["rounding_ms"], 3),
+            "rounding_ratio": lt["rounding_ms"] / max(lg["rounding_ms"], 1e-9), "ranks": lt["ranks"],
+            "E_max_rel_diff": ts["err_E"], "phases": {"gram": lg["phases"], "ttsvd": lt["phases"]},
+            "how": "QR by three eigen-form Cholesky-QR passes (first shifted), SVD of Rf by the Jacobi "
+                   "eigensolver on its Jordan-Wielandt matrix; FP64"}
     if res.get("autotune") is not None:
         line["autotune"] = res["autotune"]
     if res.get("batched") is not None:

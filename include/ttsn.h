@@ -54,7 +54,7 @@ enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1, TT_BC_OUTFLOW = 2 };
 enum { TT_FP64 = 0, TT_MIXED = 1 };
 enum { TT_LAYOUT_GROUPED = 0, TT_LAYOUT_SPLIT = 1 };
 enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_HLL = 2 };
-enum { TT_ROUND_GRAM = 0, TT_ROUND_RANDOMIZED = 1 };
+enum { TT_ROUND_GRAM = 0, TT_ROUND_RANDOMIZED = 1, TT_ROUND_TTSVD = 2 };
 
 /* step flags for tt_sn_step_ex */
 enum {
@@ -289,6 +289,16 @@ tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, co
  * randfinal).  Its ranks are the forced ranks if a call gives them, else the
  * sketch's ranks (both capped by the bond); eps and max_rank are not used.
  * FP64 whatever the precision setting.  TT_ERR_STATE without a sketch.
+ * TT_ROUND_TTSVD: the QR-based TT-SVD rounding of App. A.1 with the same
+ * tolerance, forced-rank and cap rules as TT_ROUND_GRAM: a backward sweep of
+ * QR factorisations makes cores d-1 .. 1 right-orthonormal, then each left
+ * unfolding A = Q Rf is truncated by the SVD of Rf.  The QR factors come from
+ * three passes of eigen-form Cholesky QR (the first shifted), the SVD of Rf
+ * from the eigenpairs of its Jordan-Wielandt matrix, so singular values are
+ * resolved to eps_mach of the largest (App. A.4), at several times the Gram
+ * path's cost.  FP64 whatever the precision setting.  Neither non-Gram
+ * method is open to a spatial shard or while an adjoint tape records
+ * (TT_ERR_STATE), nor to captured steps.
  */
 tt_status tt_set_sketch(tt_handle h, const double* const* omega_dev, const int* ranks_host);
 tt_status tt_set_rounding(tt_handle h, int method);
@@ -603,7 +613,9 @@ tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A_dev, int lda, co
  * be smaller) and are exactly symmetric and reproducible.  The split over rows
  * is capped so that its n x n partials fit the array (2^20 / n^2 splits): for
  * n > 724 only one fits and the call runs without a row split, one CTA per
- * upper-triangle tile, which is several times slower than tt_gram on tall A.
+ * upper-triangle tile, which is slower than tt_gram on tall A (measured on
+ * GB300: 300,000 x 897 in 680 ms against 273 ms; 300,000 x 700, two splits,
+ * 341 against 152 ms).
  */
 tt_status tt_gram_noalloc(int m, int n, const double* A_dev, int lda, double* G_dev, int ldg,
                           void* stream);

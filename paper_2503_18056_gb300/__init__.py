@@ -134,8 +134,10 @@ class _Handle:
         check(lib.tt_set_sketch(self._h, ptrs, _int_array(ranks)))
 
     def set_rounding(self, method):
-        """'gram' (default) or 'randomized' for the following roundings (tt_set_rounding)."""
-        m = {"gram": _native.TT_ROUND_GRAM, "randomized": _native.TT_ROUND_RANDOMIZED}[method]
+        """'gram' (default), 'randomized' (App. A.3) or 'ttsvd' (the QR-based
+        rounding of App. A.1) for the following roundings (tt_set_rounding)."""
+        m = {"gram": _native.TT_ROUND_GRAM, "randomized": _native.TT_ROUND_RANDOMIZED,
+             "ttsvd": _native.TT_ROUND_TTSVD}[method]
         check(lib.tt_set_rounding(self._h, m))
 
     def full(self):

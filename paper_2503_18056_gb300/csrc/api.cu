@@ -210,7 +210,7 @@ __global__ void plan_kernel(int stage, int* dd, PlanConsts pc) {
 
 // host-side slots of the pinned readback block
 enum { HI_KB = 0, HI_DEC = 16, HI_STATUS = 20, HI_SWEEPS = 24, HI_N = 64 };
-enum { HD_DEC = 0, HD_DELTA2 = 4, HD_TOT = 8, HD_Q = 12, HD_ONE = 14, HD_N = 16 };
+enum { HD_DEC = 0, HD_DELTA2 = 4, HD_TOT = 8, HD_Q = 12, HD_ONE = 14, HD_JWC = 15, HD_N = 16 };
 
 struct tt_ctx {
     cudaStream_t stream = nullptr;
@@ -313,6 +313,10 @@ struct tt_ctx {
     DevBuf sketch[TT_MAX_D], sk_sub[TT_MAX_D], sk_W[TT_MAX_D], sk_Y, sk_Q, sk_G, sk_lam, sk_Vt, sk_Vs;
     int sk_L[TT_MAX_D + 1] = {0};
     bool has_sketch = false;
+    // QR-based rounding (TT-SVD, App. A.1): the right-orthonormalised cores,
+    // the two basis buffers of the Cholesky-QR passes, the transposed core,
+    // the small factor, its Jordan-Wielandt matrix and eigenpairs, U and S V^T
+    DevBuf ts_core[TT_MAX_D], ts_Qa, ts_Qb, ts_Y, ts_R, ts_J, ts_lam, ts_Vt, ts_U, ts_M;
     // split-space layout (cores x[, y[, z]], theta, phi): per-term angular
     // factors (theta rows then phi rows, 1 + 2 ndim terms each), the uniform
     // absorption factor s, the spatial contractions F (nc x terms) and the
@@ -384,6 +388,7 @@ struct tt_ctx {
             sketch[k].release();
             sk_sub[k].release();
             sk_W[k].release();
+            ts_core[k].release();
             core[k].release();
             gcore[k].release();
             GB[k].release();
@@ -394,7 +399,8 @@ struct tt_ctx {
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
                           &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph,
-                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs, &xch, &dyn_buf, &dyn_part, &ydots};
+                          &sk_Y, &sk_Q, &sk_G, &sk_lam, &sk_Vt, &sk_Vs, &xch, &dyn_buf, &dyn_part, &ydots,
+                          &ts_Qa, &ts_Qb, &ts_Y, &ts_R, &ts_J, &ts_lam, &ts_Vt, &ts_U, &ts_M};
         for (DevBuf* b : bufs) b->release();
         for (auto& ax : inflow)
             for (auto& face : ax) face.g.release();
@@ -650,12 +656,182 @@ tt_status round_randomized(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, in
     return TT_OK;
 }
 
+// Orthonormal basis Q (m x k) of the columns of Y (m x l, row-major) by three
+// passes of eigen-form Cholesky QR: the first with the shift of
+// shifted_scale_rows (no eigenvalue is inverted, whatever the condition of
+// Y), the next two with the eigenvalue floor of eig_orthonormalise.  The
+// basis ends in *Q (one of ts_Qa / ts_Qb, never Y's buffer); k = 0 for a zero Y.
+tt_status orth_qr3(tt_ctx* h, long m, int l, const double* Y, DevBuf** Q, int* k_out) {
+    cudaStream_t s = h->stream;
+    TT_TRY(h->sk_G.ensure((size_t)l * l, s));
+    TT_TRY(h->sk_lam.ensure((size_t)l, s));
+    TT_TRY(h->sk_Vt.ensure((size_t)l * l, s));
+    TT_TRY(h->sk_Vs.ensure((size_t)l * l, s));
+    TT_TRY(gram(s, (int)m, l, Y, l, h->sk_G.p, l, h->partials));
+    TT_TRY(syev(s, l, h->sk_G.p, l, h->sk_lam.p, h->sk_Vt.p, l, h->eig, h->d_int + HI_STATUS,
+                h->d_int + next_sweep_slot(h), h->max_sweeps));
+    shifted_scale_rows(s, l, h->sk_Vt.p, l, h->sk_lam.p, h->sk_Vs.p, l);
+    TT_TRY(h->ts_Qa.ensure((size_t)m * l, s));
+    TT_TRY(dgemm(s, false, true, (int)m, l, l, 1.0, Y, l, h->sk_Vs.p, l, 0.0, h->ts_Qa.p, l));
+    int k2 = 0, k3 = 0;
+    TT_TRY(eig_orthonormalise(h, m, l, h->ts_Qa.p, h->ts_Qb, &k2));
+    if (k2 == 0) {
+        *k_out = 0;
+        return TT_OK;
+    }
+    TT_TRY(eig_orthonormalise(h, m, k2, h->ts_Qb.p, h->ts_Qa, &k3));
+    *Q = &h->ts_Qa;
+    *k_out = k3;
+    return TT_OK;
+}
+
+// TT-SVD rounding (App. A.1; Oseledets 2011): a backward sweep makes cores
+// d-1 .. 1 right-orthonormal (C_k^T = Q Rf: core k <- Q^T, core k-1 <- core
+// k-1 Rf^T), then a forward sweep takes each left unfolding A = Q Rf, the SVD
+// Rf = U S V^T from the Jordan-Wielandt eigenproblem, keeps r singular
+// triplets by the tolerance rule of the Gram path (the same decision kernel
+// on sigma^2), writes A' = Q U_r and carries S_r V_r^T into the next core.
+// No Gram matrix of a core is factorised without the QR passes around it, so
+// singular values are resolved to eps_mach of the largest (App. A.4).  FP64.
+tt_status round_ttsvd(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr, double eps, int max_rank,
+                      const int* forced, tt_step_info* info) {
+    cudaStream_t s = h->stream;
+    const int d = h->d;
+    const int* n = h->n;
+    h->sweeps_slot = 0;
+    TT_CUDA_TRY(cudaMemsetAsync(h->d_int + HI_SWEEPS, 0, (HI_N - HI_SWEEPS) * sizeof(int), s));
+    if (info) {
+        info->d = d;
+        for (int k = 0; k <= d; ++k) info->grown[k] = R[k];
+        info->capped = 0;
+        info->norm = 0.0;
+        for (int k = 0; k < TT_MAX_D; ++k) info->discarded[k] = 0.0;
+    }
+    int Rb[TT_MAX_D + 1];
+    for (int k = 0; k <= d; ++k) Rb[k] = R[k];
+    // ---- backward sweep: right-orthonormalise cores d-1 .. 1
+    {
+        PhaseScope ps(h, TT_PH_GRAM_RIGHT, 0.0, 0.0);
+        for (int k = d - 1; k >= 1; --k) {
+            const double* C = (k == d - 1) ? src[k].p : h->ts_core[k].p;
+            const int rows = Rb[k];
+            const long ncols = (long)n[k] * Rb[k + 1];
+            TT_TRY(h->ts_Y.ensure((size_t)ncols * rows, s));
+            transpose(s, rows, ncols, C, ncols, h->ts_Y.p, rows);
+            DevBuf* Q = nullptr;
+            int q = 0;
+            TT_TRY(orth_qr3(h, ncols, rows, h->ts_Y.p, &Q, &q));
+            if (q == 0) return zero_tt(h, dst, rr);
+            TT_TRY(h->ts_R.ensure((size_t)q * rows, s));
+            TT_TRY(dgemm_sk(s, true, false, q, rows, (int)ncols, 1.0, Q->p, q, h->ts_Y.p, rows, h->ts_R.p, rows,
+                            h->partials));
+            TT_TRY(h->ts_core[k].ensure((size_t)q * ncols, s));
+            transpose(s, ncols, q, Q->p, q, h->ts_core[k].p, ncols);
+            const long prow = (long)Rb[k - 1] * n[k - 1];
+            TT_TRY(h->ts_core[k - 1].ensure((size_t)prow * q, s));
+            TT_TRY(dgemm(s, false, true, (int)prow, q, rows, 1.0, src[k - 1].p, rows, h->ts_R.p, rows, 0.0,
+                         h->ts_core[k - 1].p, q));
+            Rb[k] = q;
+        }
+    }
+    // ---- forward sweep: truncated SVDs of the left unfoldings
+    h->h_dbl[HD_DELTA2] = -1.0;
+    TT_CUDA_TRY(cudaMemcpyAsync(h->d_dbl + HD_DELTA2, h->h_dbl + HD_DELTA2, sizeof(double),
+                                cudaMemcpyHostToDevice, s));
+    rr[0] = 1;
+    const double* A = h->ts_core[0].p;
+    int rprev = 1, tmp_idx = 0;
+    bool any_capped = false;
+    for (int k = 0; k <= d - 2; ++k) {
+        const int l = Rb[k + 1];
+        const long m = (long)rprev * n[k];
+        DevBuf* Q = nullptr;
+        int q = 0;
+        {
+            PhaseScope ps(h, TT_PH_GRAM_LEFT, 0.0, 0.0);
+            TT_TRY(orth_qr3(h, m, l, A, &Q, &q));
+            if (q == 0) return zero_tt(h, dst, rr);
+            TT_TRY(h->ts_R.ensure((size_t)q * l, s));
+            TT_TRY(dgemm_sk(s, true, false, q, l, (int)m, 1.0, Q->p, q, A, l, h->ts_R.p, l, h->partials));
+        }
+        const int p = q + l, pm = std::min(q, l);
+        {
+            PhaseScope ps(h, TT_PH_EIG, 0.0, 0.0);
+            TT_TRY(h->ts_J.ensure((size_t)p * p, s));
+            TT_TRY(h->ts_lam.ensure((size_t)p, s));
+            TT_TRY(h->ts_Vt.ensure((size_t)p * p, s));
+            TT_TRY(h->lamK.ensure((size_t)pm, s));
+            jw_build(s, q, l, h->ts_R.p, h->d_dbl + HD_JWC, h->ts_J.p);
+            TT_TRY(syev(s, p, h->ts_J.p, p, h->ts_lam.p, h->ts_Vt.p, p, h->eig, h->d_int + HI_STATUS,
+                        h->d_int + next_sweep_slot(h), h->max_sweeps));
+            jw_sigma2(s, pm, h->ts_lam.p, h->d_dbl + HD_JWC, h->lamK.p);
+            const int fk = forced ? forced[k] : 0;
+            truncation_decision(s, h->lamK.p, pm, eps, d - 1, fk, max_rank, h->d_dbl + HD_DELTA2,
+                                h->d_int + HI_DEC, h->d_dbl + HD_DEC, /*singular_values=*/true);
+        }
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_DEC, h->d_int + HI_DEC, 4 * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_dbl + HD_DEC, h->d_dbl + HD_DEC, 4 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h->h_int[HI_DEC + 2])
+            return fail(TT_ERR_NONFINITE, "rounding: the tensor holds Inf or NaN (the run diverged or a field "
+                                          "held one); restore saved cores and T before stepping again");
+        const int rk = h->h_int[HI_DEC];
+        if (h->h_int[HI_DEC + 1]) any_capped = true;
+        if (info) {
+            info->discarded[k] = sqrt(std::max(h->h_dbl[HD_DEC + 1], 0.0));
+            if (k == 0) info->norm = sqrt(std::max(h->h_dbl[HD_DEC + 2], 0.0));
+        }
+        if (rk == 0) return zero_tt(h, dst, rr);
+        const long ncols = (long)n[k + 1] * Rb[k + 2];
+        double* next;
+        {
+            PhaseScope ps(h, TT_PH_UPDATE, 0.0, 0.0);
+            TT_TRY(h->ts_U.ensure((size_t)rk * q, s));
+            TT_TRY(h->ts_M.ensure((size_t)rk * l, s));
+            jw_split(s, rk, q, l, h->ts_lam.p, h->d_dbl + HD_JWC, h->ts_Vt.p, p, h->ts_U.p, h->ts_M.p);
+            // A' = Q U_r
+            TT_TRY(dst[k].ensure((size_t)m * rk, s));
+            TT_TRY(dgemm(s, false, true, (int)m, rk, q, 1.0, Q->p, q, h->ts_U.p, q, 0.0, dst[k].p, rk));
+            // next core = S_r V_r^T x_1 (right-orthonormal core k+1)
+            if (k == d - 2) {
+                TT_TRY(dst[d - 1].ensure((size_t)rk * ncols, s));
+                next = dst[d - 1].p;
+            } else {
+                TT_TRY(h->tmp[tmp_idx].ensure((size_t)rk * ncols, s));
+                next = h->tmp[tmp_idx].p;
+                tmp_idx ^= 1;
+            }
+            TT_TRY(dgemm_sk(s, false, false, rk, (int)ncols, l, 1.0, h->ts_M.p, l, h->ts_core[k + 1].p, ncols,
+                            next, ncols, h->partials));
+        }
+        rr[k + 1] = rk;
+        A = next;
+        rprev = rk;
+    }
+    rr[d] = 1;
+    if (info) {
+        info->capped = any_capped ? 1 : 0;
+        const int nslots = std::min(h->sweeps_slot, HI_N - HI_SWEEPS);
+        TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_SWEEPS, h->d_int + HI_SWEEPS, nslots * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s));
+        TT_CUDA_TRY(cudaStreamSynchronize(s));
+        int mx = 0;
+        for (int i = 0; i < nslots; ++i) mx = std::max(mx, h->h_int[HI_SWEEPS + i]);
+        info->sweeps = mx;
+    }
+    return any_capped ? TT_WARN_RANK_CAPPED : TT_OK;
+}
+
 tt_status shard_exchange(tt_ctx* h, int kind, double* buf, size_t count);
 
 tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr, double eps,
                       int max_rank, const int* forced, tt_step_info* info) {
     if (h->round_method == TT_ROUND_RANDOMIZED && h->d > 1)
         return round_randomized(h, src, R, dst, rr, forced, info);
+    if (h->round_method == TT_ROUND_TTSVD && h->d > 1)
+        return round_ttsvd(h, src, R, dst, rr, eps, max_rank, forced, info);
     cudaStream_t s = h->stream;
     const int d = h->d;
     const int* n = h->n;
@@ -2567,13 +2743,16 @@ tt_status tt_set_sketch(tt_handle h, const double* const* omega_dev, const int* 
 tt_status tt_set_rounding(tt_handle h, int method) {
     set_error("");
     TT_TRY(check_handle(h, false));
-    if (method != TT_ROUND_GRAM && method != TT_ROUND_RANDOMIZED)
-        return fail(TT_ERR_ARG, "tt_set_rounding: method must be TT_ROUND_GRAM or TT_ROUND_RANDOMIZED");
+    if (method != TT_ROUND_GRAM && method != TT_ROUND_RANDOMIZED && method != TT_ROUND_TTSVD)
+        return fail(TT_ERR_ARG,
+                    "tt_set_rounding: method must be TT_ROUND_GRAM, TT_ROUND_RANDOMIZED or TT_ROUND_TTSVD");
     if (method == TT_ROUND_RANDOMIZED && !h->has_sketch)
         return fail(TT_ERR_STATE, "tt_set_rounding: the randomized rounding needs a sketch (tt_set_sketch)");
-    if (method == TT_ROUND_RANDOMIZED && h->shard.on)
+    if (method != TT_ROUND_GRAM && h->shard.on)
         return fail(TT_ERR_STATE, "tt_set_rounding: a spatial shard rounds by Gram-SVD only");
-    if (method == TT_ROUND_RANDOMIZED && (h->taping || h->replay_rec))
+    if (method != TT_ROUND_GRAM && h->graph_on)
+        return fail(TT_ERR_STATE, "tt_set_rounding: captured steps use the Gram-SVD rounding (tt_set_graph 0 first)");
+    if (method != TT_ROUND_GRAM && (h->taping || h->replay_rec))
         return fail(TT_ERR_STATE, "tt_set_rounding: the adjoint tape records Gram-SVD roundings");
     h->round_method = method;
     return TT_OK;

@@ -155,6 +155,23 @@ tt_status gemv_t(cudaStream_t s, long m, int ncols, double alpha, const double* 
                  const double* v, double* out, DevBuf& scratch);
 void copy2d(cudaStream_t s, int rows, int cols, const double* in, long ldi, double* out, long ldo);
 
+// ---------------------------------------------------------------- QR-based rounding (ttsvd.cu)
+// out[i][j] = Vt[i][j] / sqrt(lam[i] + shift), i, j < l, lam descending, with
+// shift = l eps_mach max(lam[0], 0) + max(0, -lam[l-1]) formed on the device.
+void shifted_scale_rows(cudaStream_t s, int l, const double* Vt, long ldv, const double* lam, double* out,
+                        long ldo);
+// out (cols x rows, ldo) = in^T (in rows x cols, ldi)
+void transpose(cudaStream_t s, long rows, long cols, const double* in, long ldi, double* out, long ldo);
+// Jordan-Wielandt form of Rf (q x l, contiguous): c_dev[0] = ||Rf||_F and
+// J ((q + l) x (q + l)) = [[c I, Rf], [Rf^T, c I]].
+void jw_build(cudaStream_t s, int q, int l, const double* Rf, double* c_dev, double* J);
+// sig2[i] = max(lam[i] - c, 0)^2, i < pm (the squared singular values of Rf)
+void jw_sigma2(cudaStream_t s, int pm, const double* lam, const double* c_dev, double* sig2);
+// From the eigenvectors (rows of Vt, ld ldv) of the Jordan-Wielandt matrix:
+// U (r x q) rows sqrt(2) u_i^T, M (r x l) rows sigma_i sqrt(2) v_i^T.
+void jw_split(cudaStream_t s, int r, int q, int l, const double* lam, const double* c_dev, const double* Vt,
+              long ldv, double* U, double* M);
+
 // ---------------------------------------------------------------- eigensolver (jacobi.cu)
 struct EigWork {
     DevBuf g0, g1;          // double-buffered matrix
@@ -217,9 +234,11 @@ tt_status wait_probe(cudaStream_t s, EigWork& w, int* status_dev);
 // or forced rank (>0), and max_rank cap (<=0 none).
 // Output (device int/double array `dec`): dec_i[0] = r', dec_i[1] = capped,
 // dec_d[0] = delta2 used, dec_d[1] = discarded tail (sum sigma^2), dec_d[2] = ||X||^2.
+// singular_values: lamK holds squared singular values from an SVD (resolved
+// to kB eps_mach of the largest singular value) rather than Gram eigenvalues.
 void truncation_decision(cudaStream_t s, const double* lamK, int kB, double eps, int dm1,
                          int forced, int max_rank, double* delta2_dev, int* dec_i,
-                         double* dec_d);
+                         double* dec_d, bool singular_values = false);
 // Count of eigenvalues above the floor n * eps_mach * lam_max (lam descending).
 void count_above_floor(cudaStream_t s, const double* lam, int n, int* out_dev);
 

@@ -669,7 +669,7 @@ __global__ void wait_probe_kernel(int* ctrl, int* status) {
 
 __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm1, int forced,
                                   int max_rank, double* delta2_dev, int* dec_i, double* dec_d,
-                                  const int* kB_dev) {
+                                  const int* kB_dev, int sv) {
     if (kB_dev) kB = *kB_dev > 0 ? *kB_dev : 0;
     const double eps_mach = 2.220446049250313e-16;
     // totals and tails are summed from the small end; eigenvalues are not clamped
@@ -685,11 +685,14 @@ __global__ void truncation_kernel(const double* lamK, int kB, double eps, int dm
         delta2 = eps * eps * total / (double)(dm1 > 0 ? dm1 : 1);
         *delta2_dev = delta2;
     }
+    // floor: Gram eigenvalues are resolved to kB eps_mach of the largest;
+    // squared singular values from an SVD (sv) to the square of that
     int navail = 0;
     const double lmax = kB > 0 ? lamK[0] : 0.0;
+    const double fl = sv ? ((double)kB * eps_mach) * ((double)kB * eps_mach) : (double)kB * eps_mach;
     if (lmax > 0.0)
         for (int j = 0; j < kB; ++j)
-            if (lamK[j] > (double)kB * eps_mach * lmax) ++navail;
+            if (lamK[j] > fl * lmax) ++navail;
     int r, capped = 0;
     if (navail == 0) {
         r = 0;
@@ -814,8 +817,15 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
         return (size_t)(npairs * 2 + 2 * (size_t)ppc * n) * sizeof(double) + (size_t)npairs * sizeof(int);
     };
     int want = npairs;
+    // the row buffers for MAX_PAIRS_PER_CTA pairs where they fit; above that
+    // (n > ~1480) for the pairs each SM must own
     size_t smem = smem_for(MAX_PAIRS_PER_CTA);
-    if (smem > 200 * 1024) smem = smem_for(1);  // the bound the shared memory allows
+    if (smem > 200 * 1024) {
+        int dev = 0, sms = 1;
+        TT_CUDA_TRY(cudaGetDevice(&dev));
+        TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        smem = smem_for(std::min(MAX_PAIRS_PER_CTA, (npairs + sms - 1) / sms));
+    }
     if (smem > 200 * 1024) {
         set_error("syev: matrix too large for the shared-memory row buffers");
         return TT_ERR_TOO_LARGE;
@@ -1013,15 +1023,15 @@ tt_status syev_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* G, 
 void truncation_decision_dyn(cudaStream_t s, const double* lamK, const int* kB_dev, double eps, int dm1,
                              int forced, int max_rank, double* delta2_dev, int* dec_i, double* dec_d) {
     note_launch();
-    truncation_kernel<<<1, 1, 0, s>>>(lamK, 0, eps, dm1, forced, max_rank, delta2_dev, dec_i, dec_d, kB_dev);
+    truncation_kernel<<<1, 1, 0, s>>>(lamK, 0, eps, dm1, forced, max_rank, delta2_dev, dec_i, dec_d, kB_dev, 0);
 }
 
 void truncation_decision(cudaStream_t s, const double* lamK, int kB, double eps, int dm1,
                          int forced, int max_rank, double* delta2_dev, int* dec_i,
-                         double* dec_d) {
+                         double* dec_d, bool singular_values) {
     note_launch();
     truncation_kernel<<<1, 1, 0, s>>>(lamK, kB, eps, dm1, forced, max_rank, delta2_dev, dec_i,
-                                      dec_d, nullptr);
+                                      dec_d, nullptr, singular_values ? 1 : 0);
 }
 
 void count_above_floor(cudaStream_t s, const double* lam, int n, int* out_dev) {
