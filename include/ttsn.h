@@ -55,6 +55,7 @@ enum { TT_FP64 = 0, TT_MIXED = 1 };
 enum { TT_LAYOUT_GROUPED = 0, TT_LAYOUT_SPLIT = 1 };
 enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_HLL = 2 };
 enum { TT_ROUND_GRAM = 0, TT_ROUND_RANDOMIZED = 1, TT_ROUND_TTSVD = 2 };
+enum { TT_EIG_ONE_SIDED = 0, TT_EIG_TWO_SIDED = 1 };
 
 /* step flags for tt_sn_step_ex */
 enum {
@@ -302,6 +303,18 @@ tt_status tt_set_inflow(tt_handle h, int axis, int side, const double* g_dev, co
  */
 tt_status tt_set_sketch(tt_handle h, const double* const* omega_dev, const int* ranks_host);
 tt_status tt_set_rounding(tt_handle h, int method);
+
+/*
+ * tt_set_eigensolver: how the Gram-SVD rounding (App. A.2) takes the
+ * eigenpairs of its small positive semidefinite matrix K = W G_A W^T at each
+ * bond.  TT_EIG_ONE_SIDED (default): pivoted Cholesky K = W_K^T W_K, then
+ * one-sided Jacobi on the rows of W_K (tt_syev_psd).  TT_EIG_TWO_SIDED:
+ * two-sided Jacobi on K (tt_syev).  Both keep small eigenvalues to relative
+ * accuracy; the one-sided form does about half the FP64 work with one grid
+ * barrier per round.  TT_ERR_ARG for another value; TT_ERR_STATE for a change
+ * while captured steps are on.
+ */
+tt_status tt_set_eigensolver(tt_handle h, int method);
 
 /*
  * tt_set_graph: captured steps (enable = 1) or host-driven steps (0, the
@@ -572,6 +585,19 @@ tt_status tt_syev(int n, const double* G_dev, int ldg, double* lam_dev, double* 
  */
 tt_status tt_syev_ex(int n, const double* G_dev, int ldg, double* lam_dev, double* Vt_dev, int ldv,
                      int max_sweeps, void* stream, int* sweeps_host);
+
+/*
+ * tt_syev_psd: eigendecomposition K = V diag(lam) V^T of a symmetric positive
+ * semidefinite n x n matrix (the Gram-type matrices of App. A.2) by pivoted
+ * Cholesky K = W^T W followed by one-sided Jacobi on the rows of W (Demmel and
+ * Veselic 1992): small eigenvalues keep the relative accuracy of two-sided
+ * Jacobi at about half its work.  Same layout, ordering, sweep limit and
+ * status codes as tt_syev_ex.  Eigenvalues below the factorisation's floor
+ * (eps_mach max diag K) are returned as 0 with zero rows in Vt; an indefinite
+ * K is factorised only down to its first non-positive pivot.
+ */
+tt_status tt_syev_psd(int n, const double* K_dev, int ldk, double* lam_dev, double* Vt_dev, int ldv,
+                      int max_sweeps, void* stream, int* sweeps_host);
 tt_status tt_set_max_sweeps(tt_handle h, int max_sweeps);
 
 /*

@@ -34,7 +34,7 @@ from . import _native
 from ._native import (TT_BC_OUTFLOW, TT_BC_PERIODIC, TT_BC_VACUUM, TT_FP64, TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT,
                       TT_MIXED, TT_STEP_NO_ROUND, TT_STEP_NO_SOURCE, TTError, StepInfo, check, lib)
 
-__all__ = ["TTSN", "TTSNBatch", "shard", "TorchAllocator", "compression_factor", "step_record", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "pchol",
+__all__ = ["TTSN", "TTSNBatch", "shard", "TorchAllocator", "compression_factor", "step_record", "EscapeEnergy", "escape_energy", "TensorTrain", "dgemm", "gram", "gram_mixed", "gemm_nt_mixed", "syev", "syev_psd", "pchol",
            "TTError", "TT_BC_PERIODIC", "TT_BC_VACUUM", "TT_BC_OUTFLOW", "TT_FP64", "TT_MIXED", "TT_STEP_NO_SOURCE",
            "TT_STEP_NO_ROUND", "TT_LAYOUT_GROUPED", "TT_LAYOUT_SPLIT"]
 
@@ -162,6 +162,12 @@ class _Handle:
         """Captured steps (tt_set_graph): one recorded step replayed as a CUDA
         graph, sizes decided on the device, no host synchronisation inside."""
         check(lib.tt_set_graph(self._h, int(bool(enable))))
+
+    def set_eigensolver(self, method):
+        """'one_sided' (default: pivoted Cholesky + one-sided Jacobi) or
+        'two_sided' (Jacobi on K) for the rounding's eigensolves (tt_set_eigensolver)."""
+        m = {"one_sided": _native.TT_EIG_ONE_SIDED, "two_sided": _native.TT_EIG_TWO_SIDED}[method]
+        check(lib.tt_set_eigensolver(self._h, m))
 
     def set_max_sweeps(self, max_sweeps):
         """Sweep limit of the Jacobi eigensolves of this handle's roundings (1 .. 40)."""
@@ -684,6 +690,22 @@ def syev(G, stream=None, allow_unconverged=False, max_sweeps=40):
     st = lib.tt_syev_ex(n, ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
                         ctypes.c_void_p(Vt.data_ptr()), n, int(max_sweeps), _stream_ptr(stream),
                         ctypes.byref(sweeps))
+    if not (allow_unconverged and st == -4):
+        check(st)
+    return lam, Vt, sweeps.value
+
+
+def syev_psd(K, stream=None, allow_unconverged=False, max_sweeps=40):
+    """(lam descending, Vt with eigenvectors as rows, sweeps) of a positive
+    semidefinite K by pivoted Cholesky and one-sided Jacobi (tt_syev_psd)."""
+    K = _dev(K)
+    n = K.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    Vt = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    sweeps = ctypes.c_int()
+    st = lib.tt_syev_psd(n, ctypes.c_void_p(K.data_ptr()), n, ctypes.c_void_p(lam.data_ptr()),
+                         ctypes.c_void_p(Vt.data_ptr()), n, int(max_sweeps), _stream_ptr(stream),
+                         ctypes.byref(sweeps))
     if not (allow_unconverged and st == -4):
         check(st)
     return lam, Vt, sweeps.value

@@ -20,6 +20,7 @@ TT_FP64, TT_MIXED = 0, 1
 TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT = 0, 1
 TT_FLUX_UPWIND, TT_FLUX_RUSANOV, TT_FLUX_HLL = 0, 1, 2
 TT_ROUND_GRAM, TT_ROUND_RANDOMIZED, TT_ROUND_TTSVD = 0, 1, 2
+TT_EIG_ONE_SIDED, TT_EIG_TWO_SIDED = 0, 1
 TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2
 
 
@@ -104,6 +105,7 @@ def _load():
         "tt_batch_sync": [vp],
         "tt_syev": [i, vp, i, vp, vp, i, vp, ip],
         "tt_syev_ex": [i, vp, i, vp, vp, i, i, vp, ip],
+        "tt_syev_psd": [i, vp, i, vp, vp, i, i, vp, ip],
         "tt_set_max_sweeps": [vp, i],
         "tt_set_graph": [vp, i],
         "tt_autotune": [vp, ip],
@@ -114,6 +116,7 @@ def _load():
         "tt_set_inflow": [vp, i, i, vp, vp, vp],
         "tt_set_sketch": [vp, ctypes.POINTER(vp), ip],
         "tt_set_rounding": [vp, i],
+        "tt_set_eigensolver": [vp, i],
         "tt_wait_probe": [vp],
         "tt_profile": [vp, i],
         "tt_profile_read": [vp, i, dp, ctypes.POINTER(ctypes.c_longlong),
@@ -156,7 +159,7 @@ EXPORTED = ["tt_create", "tt_create_tt", "tt_sn_step", "tt_sn_step_ex", "tt_roun
             "tt_batch_handle", "tt_batch_sync", "tt_batch_destroy", "tt_tape_begin",
             "tt_tape_objective", "tt_sn_step_adjoint", "tt_tape_clear", "tt_set_sources",
             "tt_create_ex", "tt_get_cores", "tt_pchol", "tt_set_inflow", "tt_set_sketch",
-            "tt_set_rounding", "tt_wait_probe", "tt_create_shard", "tt_syev_ex", "tt_set_max_sweeps", "tt_set_graph",
+            "tt_set_rounding", "tt_set_eigensolver", "tt_wait_probe", "tt_create_shard", "tt_syev_ex", "tt_syev_psd", "tt_set_max_sweeps", "tt_set_graph",
             "tt_batch_set_graph", "tt_autotune", "tt_set_autotune_table", "tt_get_autotune_table"]
 
 PHASES = ["transport", "gram_right", "eig", "gram_left", "small", "update", "energy"]

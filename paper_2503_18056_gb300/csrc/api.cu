@@ -310,6 +310,7 @@ struct tt_ctx {
     // (L_{k-1}, n_k, L_k)), its leading blocks at a rounding's target ranks,
     // the right sketches W_k and the orthonormalisation workspace
     int round_method = TT_ROUND_GRAM;
+    int eig_method = TT_EIG_ONE_SIDED;  // eigensolver of the rounding's K
     DevBuf sketch[TT_MAX_D], sk_sub[TT_MAX_D], sk_W[TT_MAX_D], sk_Y, sk_Q, sk_G, sk_lam, sk_Vt, sk_Vs;
     int sk_L[TT_MAX_D + 1] = {0};
     bool has_sketch = false;
@@ -947,8 +948,12 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         TT_TRY(h->VtK.ensure((size_t)kB * kB, s));
         {
             PhaseScope ps(h, TT_PH_EIG, 0.0, 0.0);
-            TT_TRY(syev(s, kB, h->K.p, kB, h->lamK.p, h->VtK.p, kB, h->eig, h->d_int + HI_STATUS,
-                        h->d_int + next_sweep_slot(h), h->max_sweeps));
+            if (h->eig_method == TT_EIG_ONE_SIDED)
+                TT_TRY(syev_psd(s, kB, h->K.p, kB, h->lamK.p, h->VtK.p, kB, h->eig, h->d_int + HI_STATUS,
+                                h->d_int + next_sweep_slot(h), h->max_sweeps));
+            else
+                TT_TRY(syev(s, kB, h->K.p, kB, h->lamK.p, h->VtK.p, kB, h->eig, h->d_int + HI_STATUS,
+                            h->d_int + next_sweep_slot(h), h->max_sweeps));
             const int fk = forced ? forced[k] : 0;
             truncation_decision(s, h->lamK.p, kB, eps, d - 1, fk, max_rank, h->d_dbl + HD_DELTA2,
                                 h->d_int + HI_DEC, h->d_dbl + HD_DEC);
@@ -1450,8 +1455,9 @@ tt_status graph_step_body(tt_ctx* h) {
     TT_TRY(dgemm_dyn(s, true, false, desc + 24, G1, G1, (int)nc, 1.0, h->gcore[0].p, h->gcore[0].p, h->GA.p, P, 2));
     TT_TRY(dgemm_dyn(s, false, true, desc + 32, G1, G1, G1, 1.0, h->GA.p, h->VtB[0].p, h->T1.p, P, 1));
     TT_TRY(dgemm_dyn(s, false, false, desc + 40, G1, G1, G1, 1.0, h->VtB[0].p, h->T1.p, h->K.p, P, 1));
-    TT_TRY(syev_dyn(s, dd + DYN_KB0, G1, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS,
-                    dd + DYN_SWEEPS, h->max_sweeps));
+    TT_TRY((h->eig_method == TT_EIG_ONE_SIDED ? syev_psd_dyn : syev_dyn)(
+        s, dd + DYN_KB0, G1, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS, dd + DYN_SWEEPS,
+        h->max_sweeps));
     truncation_decision_dyn(s, h->lamK.p, dd + DYN_KB0, h->eps, 2, 0, h->max_rank, h->d_dbl + HD_DELTA2,
                             dd + DYN_DEC0, dec_d);
     plan(2);
@@ -1465,8 +1471,9 @@ tt_status graph_step_body(tt_ctx* h) {
     TT_TRY(dgemm_dyn(s, true, false, desc + 88, G2, G2, c1 * nt, 1.0, h->tmp[0].p, h->tmp[0].p, h->GA.p, P, 2));
     TT_TRY(dgemm_dyn(s, false, true, desc + 96, G2, G2, G2, 1.0, h->GA.p, h->VtB[1].p, h->T1.p, P, 1));
     TT_TRY(dgemm_dyn(s, false, false, desc + 104, G2, G2, G2, 1.0, h->VtB[1].p, h->T1.p, h->K.p, P, 1));
-    TT_TRY(syev_dyn(s, dd + DYN_KB1, G2, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS,
-                    dd + DYN_SWEEPS + 1, h->max_sweeps));
+    TT_TRY((h->eig_method == TT_EIG_ONE_SIDED ? syev_psd_dyn : syev_dyn)(
+        s, dd + DYN_KB1, G2, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS, dd + DYN_SWEEPS + 1,
+        h->max_sweeps));
     truncation_decision_dyn(s, h->lamK.p, dd + DYN_KB1, h->eps, 2, 0, h->max_rank, h->d_dbl + HD_DELTA2,
                             dd + DYN_DEC1, dec_d + 4);
     plan(3);
@@ -1508,6 +1515,7 @@ tt_status graph_reserve(tt_ctx* h) {
         {&h->tmp[0], c1 * nt * G2}, {&h->thbar, nterms * (c1 + c2) + 2}, {&h->ydots, nc * nterms},
         {&h->eig.g0, Gm * Gm}, {&h->eig.g1, Gm * Gm}, {&h->eig.vt_unsorted, Gm * Gm},
         {&h->eig.lam_unsorted, Gm}, {&h->eig.abc, 3 * (Gm + 1)}, {&h->eig.cs, Gm + 1},
+        {&h->eig.psd, 3 * Gm + 2},
         {&h->dyn_part, (long)dyn_partials_doubles()},
     };
     for (auto& x : need) TT_TRY(x.b->ensure((size_t)std::max<long>(x.n, 1), s, /*keep=*/true));
@@ -2740,6 +2748,17 @@ tt_status tt_set_sketch(tt_handle h, const double* const* omega_dev, const int* 
     return TT_OK;
 }
 
+tt_status tt_set_eigensolver(tt_handle h, int method) {
+    set_error("");
+    TT_TRY(check_handle(h, false));
+    if (method != TT_EIG_ONE_SIDED && method != TT_EIG_TWO_SIDED)
+        return fail(TT_ERR_ARG, "tt_set_eigensolver: method must be TT_EIG_ONE_SIDED or TT_EIG_TWO_SIDED");
+    if (h->graph_on && method != h->eig_method)
+        return fail(TT_ERR_STATE, "tt_set_eigensolver: captured steps are on (tt_set_graph 0 first)");
+    h->eig_method = method;
+    return TT_OK;
+}
+
 tt_status tt_set_rounding(tt_handle h, int method) {
     set_error("");
     TT_TRY(check_handle(h, false));
@@ -2900,7 +2919,20 @@ tt_status tt_syev(int n, const double* G, int ldg, double* lam, double* Vt, int 
     return tt_syev_ex(n, G, ldg, lam, Vt, ldv, JACOBI_MAX_SWEEPS, stream, sweeps_host);
 }
 
+static tt_status syev_entry(bool psd, int n, const double* G, int ldg, double* lam, double* Vt, int ldv, int max_sweeps,
+                     void* stream, int* sweeps_host);
+
 tt_status tt_syev_ex(int n, const double* G, int ldg, double* lam, double* Vt, int ldv, int max_sweeps,
+                     void* stream, int* sweeps_host) {
+    return syev_entry(false, n, G, ldg, lam, Vt, ldv, max_sweeps, stream, sweeps_host);
+}
+
+tt_status tt_syev_psd(int n, const double* K, int ldk, double* lam, double* Vt, int ldv, int max_sweeps,
+                      void* stream, int* sweeps_host) {
+    return syev_entry(true, n, K, ldk, lam, Vt, ldv, max_sweeps, stream, sweeps_host);
+}
+
+static tt_status syev_entry(bool psd, int n, const double* G, int ldg, double* lam, double* Vt, int ldv, int max_sweeps,
                      void* stream, int* sweeps_host) {
     set_error("");
     if (max_sweeps < 1 || max_sweeps > JACOBI_MAX_SWEEPS)
@@ -2914,7 +2946,8 @@ tt_status tt_syev_ex(int n, const double* G, int ldg, double* lam, double* Vt, i
     int* d_small = nullptr;
     TT_CUDA_TRY(cudaMallocAsync((void**)&d_small, 2 * sizeof(int), s));
     TT_CUDA_TRY(cudaMemsetAsync(d_small, 0, 2 * sizeof(int), s));
-    tt_status st = syev(s, n, G, ldg, lam, Vt, ldv, w, d_small, d_small + 1, max_sweeps);
+    tt_status st = psd ? syev_psd(s, n, G, ldg, lam, Vt, ldv, w, d_small, d_small + 1, max_sweeps)
+                       : syev(s, n, G, ldg, lam, Vt, ldv, w, d_small, d_small + 1, max_sweeps);
     int hs[2] = {0, 0};
     cudaMemcpyAsync(hs, d_small, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);

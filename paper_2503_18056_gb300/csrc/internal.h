@@ -179,6 +179,7 @@ struct EigWork {
     DevBuf vt_unsorted;
     DevBuf abc;             // per-round pair entries (double-buffered)
     DevBuf cs;              // the round's rotation angles (c, s per pair)
+    DevBuf psd;             // syev_psd: factor workspace, row norms, factor rank
     DevBuf ctrl_buf;
     int* d_ctrl = nullptr;  // barrier counters, sweep counters, status (in ctrl_buf)
     int ctrl_cap = 0;
@@ -191,6 +192,17 @@ constexpr int JACOBI_MAX_SWEEPS = 40;
 tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, double* Vt,
                long ldv, EigWork& w, int* status_dev, int* sweeps_dev,
                int max_sweeps = JACOBI_MAX_SWEEPS);
+
+// Eigendecomposition of a symmetric positive semidefinite K (n x n, ldk) as
+// syev returns it, by pivoted Cholesky K = W^T W and one-sided Jacobi on the
+// rows of W: eigenvalues with the relative accuracy of two-sided Jacobi at
+// about half its work and one grid barrier per round.  Eigenpairs below the
+// factorisation's floor (eps_mach max diag K) come back as 0 with a zero
+// vector; Inf/NaN in K as NaN eigenvalues.
+tt_status syev_psd(cudaStream_t s, int n, const double* K, long ldk, double* lam, double* Vt, long ldv,
+                   EigWork& w, int* status_dev, int* sweeps_dev, int max_sweeps = JACOBI_MAX_SWEEPS);
+tt_status syev_psd_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* K, double* lam, double* Vt,
+                       EigWork& w, int* status_dev, int* sweeps_dev, int max_sweeps = JACOBI_MAX_SWEEPS);
 
 // Pivoted Cholesky of a symmetric positive semidefinite n x n G (ldg): writes
 // W (rows 0..rank-1 of an n x n row-major buffer) with W^T W = G up to the

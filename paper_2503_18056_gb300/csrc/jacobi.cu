@@ -372,6 +372,188 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
     }
 }
 
+// One-sided Jacobi on the rows of a factor W (k x n, ld n) with W^T W = K
+// (Demmel & Veselic, SIAM J. Matrix Anal. Appl. 13, 1992: the eigenpairs of a
+// positive definite matrix from its Cholesky factor by one-sided Jacobi, as
+// accurate as two-sided Jacobi on K).  Row pairs follow the same round-robin
+// ordering; one warp owns a pair for the round: it forms c = w_p . w_q, and
+// if |c| > tol sqrt(a b) (a, b the squared row norms, kept in nrm) rotates the
+// two rows so that they become orthogonal and recomputes their norms from the
+// rotated rows.  A rotation touches only its own two rows, so a round needs
+// one grid barrier and no exchange of angles.  On convergence the rows are
+// orthogonal: K = sum_i w_i w_i^T, eigenvalue ||w_i||^2, eigenvector
+// w_i / ||w_i||; rows k .. n-1 (K's null space below the factor's floor)
+// get eigenvalue 0 and a zero vector.  A negative rank (the factorisation met
+// Inf or NaN) gives NaN eigenvalues, which the rank decision reports.
+constexpr int OSJ_MAX_WARPS = 8;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One pair: c = w_p . w_q, the rotation if it is needed, the rotated rows'
+// norms.  C > 0: the lane's n / 32 entries of both rows are held in registers
+// (all loads issued at once: one L2 round trip per pair); C == 0 streams the
+// rows (any n).  Returns whether it rotated.
+template <int C>
+__device__ __forceinline__ bool osj_pair(double* wp, double* wq, int n, int lane, double* nrm_p, double* nrm_q,
+                                         double tol) {
+    double x[C > 0 ? C : 1], y[C > 0 ? C : 1];
+    double c;
+    if (C > 0) {
+#pragma unroll
+        for (int t = 0; t < C; ++t) {
+            const int j = lane + 32 * t;
+            x[t] = j < n ? __ldcg(wp + j) : 0.0;
+            y[t] = j < n ? __ldcg(wq + j) : 0.0;
+        }
+        double c0 = 0.0, c1 = 0.0;
+#pragma unroll
+        for (int t = 0; t < C; t += 2) {
+            c0 = fma(x[t], y[t], c0);
+            if (t + 1 < C) c1 = fma(x[t + 1], y[t + 1], c1);
+        }
+        c = warp_sum(c0 + c1);
+    } else {
+        double c0 = 0.0, c1 = 0.0;
+        int j = lane;
+        for (; j + 32 < n; j += 64) {
+            c0 = fma(__ldcg(wp + j), __ldcg(wq + j), c0);
+            c1 = fma(__ldcg(wp + j + 32), __ldcg(wq + j + 32), c1);
+        }
+        if (j < n) c0 = fma(__ldcg(wp + j), __ldcg(wq + j), c0);
+        c = warp_sum(c0 + c1);
+    }
+    const double a = __ldcg(nrm_p), b = __ldcg(nrm_q);
+    if (!(a > 0.0 && b > 0.0 && fabs(c) > tol * sqrt(a * b))) return false;
+    // Golub & Van Loan, Alg. 8.4.1 on [[a, c], [c, b]]
+    const double tau = (b - a) / (2.0 * c);
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    const double cs = 1.0 / sqrt(1.0 + t * t);
+    const double sn = t * cs;
+    // the rotation moves t c from one squared norm to the other: the growing
+    // one is updated by that sum (no cancellation), the shrinking one is
+    // summed again from the rotated row
+    const bool p_shrinks = t * c > 0.0;
+    double ns = 0.0;
+    if (C > 0) {
+#pragma unroll
+        for (int t2 = 0; t2 < C; ++t2) {
+            const int j = lane + 32 * t2;
+            const double xn = cs * x[t2] - sn * y[t2];
+            const double yn = sn * x[t2] + cs * y[t2];
+            if (j < n) {
+                __stcg(wp + j, xn);
+                __stcg(wq + j, yn);
+            }
+            const double v = p_shrinks ? xn : yn;
+            ns = fma(v, v, ns);
+        }
+    } else {
+        for (int j = lane; j < n; j += 32) {
+            const double xo = __ldcg(wp + j), yo = __ldcg(wq + j);
+            const double xn = cs * xo - sn * yo;
+            const double yn = sn * xo + cs * yo;
+            __stcg(wp + j, xn);
+            __stcg(wq + j, yn);
+            const double v = p_shrinks ? xn : yn;
+            ns = fma(v, v, ns);
+        }
+    }
+    ns = warp_sum(ns);
+    if (lane == 0) {
+        __stcg(nrm_p, p_shrinks ? ns : a - t * c);
+        __stcg(nrm_q, p_shrinks ? b + t * c : ns);
+    }
+    return true;
+}
+
+// Squared norms of rows 0 .. k-1, summed from the rows (one warp per row).
+__device__ __forceinline__ void osj_norms(const double* W, int n, int k, double* nrm, int gw, int nw, int lane) {
+    for (int i = gw; i < k; i += nw) {
+        const double* wi = W + (long)i * n;
+        double a = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const double v = __ldcg(wi + j);
+            a = fma(v, v, a);
+        }
+        a = warp_sum(a);
+        if (lane == 0) __stcg(nrm + i, a);
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(32 * OSJ_MAX_WARPS)
+osj_kernel(int n, const int* __restrict__ k_dev, double* W, double* nrm, double* lam_u, double* vt_u, int* ctrl,
+           int* status, int max_sweeps, const int* n_dev) {
+    if (n_dev) n = *n_dev;
+    // relative skip threshold sqrt(n) eps_mach, the one of LAPACK's one-sided
+    // Jacobi SVD (dgesvj): the typical rounding error of a computed inner
+    // product of length n, so rounding noise does not keep pairs rotating
+    const double tol = sqrt((double)n) * 2.220446049250313e-16;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int nw = gridDim.x * wpb;
+    const int kraw = *k_dev;
+    if (kraw < 0) {  // every CTA returns before any barrier
+        for (int i = gw; i < n; i += nw) {
+            if (lane == 0) lam_u[i] = __longlong_as_double(0x7ff8000000000000LL);
+            for (int j = lane; j < n; j += 32) vt_u[(long)i * n + j] = 0.0;
+        }
+        return;
+    }
+    const int k = min(kraw, n);
+    unsigned epoch = 0;
+    __shared__ int s_cnt;
+    __shared__ int s_done;
+    const int N = k + (k & 1), npairs = N / 2;
+    int sweep = 0;
+    if (k >= 2) {
+        for (; sweep < max_sweeps; ++sweep) {
+            if (threadIdx.x == 0) s_cnt = 0;
+            // norms summed afresh at every sweep: the updates inside a sweep
+            // only steer the angles and the skip test
+            osj_norms(W, n, k, nrm, gw, nw, lane);
+            if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
+            int mine = 0;
+            for (int r = 0; r < N - 1; ++r) {
+                for (int kk = gw; kk < npairs; kk += nw) {
+                    int p, q;
+                    round_pair(N, r, kk, p, q);
+                    if (q >= k) continue;
+                    if (osj_pair<C>(W + (long)p * n, W + (long)q * n, n, lane, nrm + p, nrm + q, tol)) ++mine;
+                }
+                if (r == N - 2) {
+                    if (lane == 0 && mine) atomicAdd(&s_cnt, mine);
+                    __syncthreads();
+                    if (threadIdx.x == 0) atomicAdd(ctrl + 4 + sweep, s_cnt);
+                }
+                if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
+            }
+            if (threadIdx.x == 0) s_done = (atomicAdd(ctrl + 4 + sweep, 0) == 0);
+            __syncthreads();
+            if (s_done) break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl[2] = k >= 2 ? min(sweep + 1, max_sweeps) : 0;
+        if (k >= 2 && sweep >= max_sweeps) atomicOr(status, DEV_NOT_CONVERGED);
+    }
+    // eigenvalues: the converged rows' squared norms, summed from the rows
+    osj_norms(W, n, k, nrm, gw, nw, lane);
+    if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
+    for (int i = gw; i < n; i += nw) {
+        const double a = i < k ? __ldcg(nrm + i) : 0.0;
+        const double f = a > 0.0 ? 1.0 / sqrt(a) : 0.0;
+        if (lane == 0) lam_u[i] = a;
+        const double* wi = W + (long)i * n;
+        for (int j = lane; j < n; j += 32) vt_u[(long)i * n + j] = i < k ? f * __ldcg(wi + j) : 0.0;
+    }
+}
+
 // Pivoted Cholesky in one CTA for n <= PCHOL_ONE_CTA_N: the same factorisation
 // as pchol_kernel (pivot = largest remaining diagonal entry, stop at the
 // floor, -inf marks pivoted columns) with one thread per column: column j's
@@ -768,6 +950,7 @@ void EigWork::release() {
     lam_unsorted.release();
     vt_unsorted.release();
     abc.release();
+    psd.release();
     ctrl_buf.release();
     d_ctrl = nullptr;
     ctrl_cap = 0;
@@ -866,6 +1049,41 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     jacobi_sort_kernel<<<n, 256, 0, s>>>(n, w.lam_unsorted.p, ld, w.vt_unsorted.p, lam, Vt, ldv,
                                          sweeps_dev, w.d_ctrl, nullptr);
     TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status osj_launch(cudaStream_t s, int ncap, const int* k_dev, EigWork& w, int* status_dev, int max_sweeps,
+                     const int* n_dev, double* nrm) {
+    TT_TRY(ensure_ctrl(w, s));  // zero barrier and sweep counters (pchol used them)
+    // rows in registers up to n = 1024 (entries per lane: 8, 16 or 32)
+    const void* fn = ncap <= 256 ? (const void*)osj_kernel<8>
+                     : ncap <= 512 ? (const void*)osj_kernel<16>
+                     : ncap <= 1024 ? (const void*)osj_kernel<32> : (const void*)osj_kernel<0>;
+    // one CTA per SM with one warp per pair it owns, so every SM carries the
+    // same number of pairs in a round (the round ends at the slowest SM)
+    int blocks = 1, wpb = 1;
+    {
+        int dev = 0, sms = 0, per_sm = 0;
+        TT_CUDA_TRY(cudaGetDevice(&dev));
+        TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int npairs = (ncap + 1) / 2;
+        wpb = std::max(1, std::min(OSJ_MAX_WARPS, (npairs + sms - 1) / sms));
+        TT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, 0));
+        if (per_sm < 1) {
+            set_error("one-sided Jacobi kernel cannot be resident");
+            return TT_ERR_CUDA;
+        }
+        blocks = std::max(1, std::min((npairs + wpb - 1) / wpb, per_sm * sms));
+    }
+    int nn = ncap;
+    double* Wp = w.g0.p;
+    double* lamu = w.lam_unsorted.p;
+    double* vtu = w.vt_unsorted.p;
+    int* ctrl = w.d_ctrl;
+    int msw = max_sweeps;
+    void* args[] = {&nn, &k_dev, &Wp, &nrm, &lamu, &vtu, &ctrl, &status_dev, &msw, &n_dev};
+    note_launch();
+    TT_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(32 * wpb), args, 0, s));
     return TT_OK;
 }
 
@@ -1032,6 +1250,57 @@ void truncation_decision(cudaStream_t s, const double* lamK, int kB, double eps,
     note_launch();
     truncation_kernel<<<1, 1, 0, s>>>(lamK, kB, eps, dm1, forced, max_rank, delta2_dev, dec_i,
                                       dec_d, nullptr, singular_values ? 1 : 0);
+}
+
+tt_status syev_psd(cudaStream_t s, int n, const double* K, long ldk, double* lam, double* Vt, long ldv,
+                   EigWork& w, int* status_dev, int* sweeps_dev, int max_sweeps) {
+    if (n < 0) {
+        set_error("syev_psd: negative size");
+        return TT_ERR_ARG;
+    }
+    if (max_sweeps < 1 || max_sweeps > MAX_SWEEPS) {
+        set_error("syev_psd: the sweep limit must be in 1 .. " + std::to_string(MAX_SWEEPS));
+        return TT_ERR_ARG;
+    }
+    if (n == 0) return TT_OK;
+    if (n == 1) {
+        note_launch();
+        trivial_eig_kernel<<<1, 1, 0, s>>>(K, lam, Vt, sweeps_dev);
+        TT_CUDA_TRY(cudaGetLastError());
+        return TT_OK;
+    }
+    TT_TRY(w.g0.ensure((size_t)n * n, s));
+    TT_TRY(w.g1.ensure((size_t)n * n, s));
+    TT_TRY(w.vt_unsorted.ensure((size_t)n * n, s));
+    TT_TRY(w.lam_unsorted.ensure((size_t)n, s));
+    TT_TRY(w.psd.ensure((size_t)3 * n + 2, s));
+    int* k_dev = reinterpret_cast<int*>(w.psd.p + 3 * n);
+    // K = W^T W (pivoted, rows of W in pivot order), then its rows orthogonalised
+    TT_TRY(pchol(s, n, K, ldk, w.g0.p, w.g1.p, w.psd.p, w, status_dev, k_dev));
+    TT_TRY(osj_launch(s, n, k_dev, w, status_dev, max_sweeps, nullptr, w.psd.p + 2 * n));
+    note_launch();
+    jacobi_sort_kernel<<<n, 256, 0, s>>>(n, w.lam_unsorted.p, n, w.vt_unsorted.p, lam, Vt, ldv, sweeps_dev,
+                                         w.d_ctrl, nullptr);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
+}
+
+tt_status syev_psd_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* K, double* lam, double* Vt,
+                       EigWork& w, int* status_dev, int* sweeps_dev, int max_sweeps) {
+    if (ncap <= 0) return TT_OK;
+    TT_TRY(w.g0.ensure((size_t)ncap * ncap, s));
+    TT_TRY(w.g1.ensure((size_t)ncap * ncap, s));
+    TT_TRY(w.vt_unsorted.ensure((size_t)ncap * ncap, s));
+    TT_TRY(w.lam_unsorted.ensure((size_t)ncap, s));
+    TT_TRY(w.psd.ensure((size_t)3 * ncap + 2, s));
+    int* k_dev = reinterpret_cast<int*>(w.psd.p + 3 * ncap);
+    TT_TRY(pchol_dyn(s, n_dev, ncap, K, w.g0.p, w.g1.p, w.psd.p, w, status_dev, k_dev));
+    TT_TRY(osj_launch(s, ncap, k_dev, w, status_dev, max_sweeps, n_dev, w.psd.p + 2 * ncap));
+    note_launch();
+    jacobi_sort_kernel<<<ncap, 256, 0, s>>>(ncap, w.lam_unsorted.p, ncap, w.vt_unsorted.p, lam, Vt, ncap,
+                                            sweeps_dev, w.d_ctrl, n_dev);
+    TT_CUDA_TRY(cudaGetLastError());
+    return TT_OK;
 }
 
 void count_above_floor(cudaStream_t s, const double* lam, int n, int* out_dev) {
