@@ -1516,7 +1516,7 @@ tt_status graph_reserve(tt_ctx* h) {
         {&h->eig.g0, Gm * Gm}, {&h->eig.g1, Gm * Gm}, {&h->eig.vt_unsorted, Gm * Gm},
         {&h->eig.lam_unsorted, Gm}, {&h->eig.abc, 3 * (Gm + 1)}, {&h->eig.cs, Gm + 1},
         {&h->eig.psd, 3 * Gm + 2},
-        {&h->dyn_part, (long)dyn_partials_doubles()},
+        {&h->dyn_part, (long)dyn_partials_doubles(Gm)},
     };
     for (auto& x : need) TT_TRY(x.b->ensure((size_t)std::max<long>(x.n, 1), s, /*keep=*/true));
     TT_TRY(eig_reserve(h->eig, s));

@@ -25,17 +25,34 @@ __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
 }
 
 // One 64 x 64 output tile: C[m0.., n0..] = alpha op(A) op(B) (+ beta C) over
-// the K range [kbeg, kend).
+// the K range [kbeg, kend).  A warp skips the 8 x 8 products whose rows or
+// columns lie wholly outside M x N (a ragged last tile, e.g. the grown rank
+// 7 r + 1) and, with tri on a diagonal tile, those wholly below the diagonal
+// (a symmetric product whose lower triangle is never read): the stored
+// entries are the same bits, the tensor pipe does only the work that is read.
 template <bool TA, bool TB>
 __device__ __forceinline__ void gemm_tile(int M, int N, double alpha, const double* __restrict__ A, long lda,
                                           const double* __restrict__ B, long ldb, double beta,
                                           double* __restrict__ C, long ldc, int kbeg, int kend, int m0,
-                                          int n0) {
+                                          int n0, bool tri = false) {
     __shared__ double As[BK][BM + PADM];
     __shared__ double Bs[BK][BN + PADM];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    // live[i] bit j: the warp's 8 x 8 product (i, j) is needed
+    unsigned live = 0;
+    {
+        const bool diag = tri && m0 == n0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r0 = m0 + wm + i * 8, c0 = n0 + wn + j * 8;
+                const bool need = r0 < M && c0 < N && !(diag && r0 >= c0 + 8);
+                live |= (need ? 1u : 0u) << (i * 4 + j);
+            }
+    }
     double acc[4][4][2];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -74,10 +91,18 @@ __device__ __forceinline__ void gemm_tile(int M, int N, double alpha, const doub
             for (int i = 0; i < 4; ++i) a[i] = As[kk + (lane & 3)][wm + i * 8 + (lane >> 2)];
 #pragma unroll
             for (int j = 0; j < 4; ++j) bb[j] = Bs[kk + (lane & 3)][wn + j * 8 + (lane >> 2)];
+            if (live == 0xFFFFu) {  // a full tile: the unconditional chain
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) dmma(acc[i][j], a[i], bb[j]);
+                    for (int j = 0; j < 4; ++j) dmma(acc[i][j], a[i], bb[j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (live & (1u << (i * 4 + j))) dmma(acc[i][j], a[i], bb[j]);
+            }
         }
         __syncthreads();
     }
@@ -103,7 +128,7 @@ __device__ __forceinline__ void gemm_tile(int M, int N, double alpha, const doub
 // Batch entry b, split ks: rows of K in [ks*kchunk, min(K,(ks+1)*kchunk)), output
 // to C + b*sC + ks*sCsplit.  upper_only: skip tiles strictly below the diagonal.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 4)
 dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, long lda, long sA,
              const double* __restrict__ B, long ldb, long sB, double beta, double* __restrict__ C,
              long ldc, long sC, int ksplit, int kchunk, long sCsplit, int upper_only) {
@@ -115,7 +140,7 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, lo
     C += b * sC + ks * sCsplit;
     const int kbeg = ks * kchunk;
     const int kend = min(K, kbeg + kchunk);
-    gemm_tile<TA, TB>(M, N, alpha, A, lda, B, ldb, beta, C, ldc, kbeg, kend, tm * BM, tn * BN);
+    gemm_tile<TA, TB>(M, N, alpha, A, lda, B, ldb, beta, C, ldc, kbeg, kend, tm * BM, tn * BN, upper_only != 0);
 }
 
 // The same product with its sizes read from device memory (a captured step
@@ -129,7 +154,7 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, lo
 // decision equals the host path's for the same sizes, so the results are
 // the same bits.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 4)
 dgemm_dyn_kernel(const int* __restrict__ desc, double alpha, const double* __restrict__ A,
                  const double* __restrict__ B, double* __restrict__ C, double* __restrict__ P, int mode,
                  long resident) {
@@ -151,7 +176,7 @@ dgemm_dyn_kernel(const int* __restrict__ desc, double alpha, const double* __res
     const int kend = min(K, kbeg + kchunk);
     if (mode == 2 || ks > 1)
         gemm_tile<TA, TB>(M, N, 1.0, A, lda, B, ldb, 0.0, P + (long)z * M * N, N, kbeg, kend, tm * BM,
-                          tn * BN);
+                          tn * BN, mode == 2);
     else
         gemm_tile<TA, TB>(M, N, alpha, A, lda, B, ldb, 0.0, C, ldc, kbeg, kend, tm * BM, tn * BN);
 }
@@ -363,16 +388,34 @@ __host__ __device__ void sk_split(int M, int N, int K, int* ks_out, int* kchunk_
 }
 
 // Row split of the Gram (gram_ksplit) from the number of resident CTAs.
+// Small problems (16 or more splits fit in one wave of the resident slots)
+// take one wave.  For larger ones one wave leaves slots idle (105 upper tiles
+// at 5 splits fill 525 of 608) and the tiles differ in work: gemm_tile
+// computes only the 8 x 8 products of the upper triangle that the matrix
+// reaches, W = B (B + 1) / 2 of them for B = ceil(n / 8).  Dealt in many
+// waves (GRAM_MULTI_SPLITS splits), the slots stay busy and the time is
+// about W / (64 resident) + 1 / (2 splits) of one unsplit tile's, against
+// 1 / ks0 for one wave; the shorter is taken (integer arithmetic, so the
+// host and a captured step's device agree).  Every split keeps at least 256
+// rows.
 __host__ __device__ int gram_split_rule(int m, int n, long resident) {
     const long T = (n + BN - 1) / BN;
     const long tiles = T * (T + 1) / 2;
-    long ks = resident / tiles;
-    if (ks < 1) ks = 1;
-    const long cap = m / 256 < 1 ? 1 : m / 256;
-    if (ks > cap) ks = cap;
-    if (ks > 1024) ks = 1024;
-    if (ks < 1) ks = 1;
-    return (int)ks;
+    long cap = m / 256 < 1 ? 1 : m / 256;
+    if (cap > 1024) cap = 1024;
+    if (resident < 1) resident = 1;
+    long ks0 = resident / tiles;
+    if (ks0 < 1) ks0 = 1;
+    if (ks0 > cap) ks0 = cap;
+    if (ks0 >= 16) return (int)ks0;
+    const long km = cap < GRAM_MULTI_SPLITS ? cap : GRAM_MULTI_SPLITS;
+    if (km <= ks0) return (int)ks0;
+    const long long B = (n + 7) / 8;
+    const long long W = B * (B + 1) / 2;
+    const long long slots = 64LL * resident;
+    // (W / slots + 1 / (2 km)) < 0.97 / ks0, times 2 slots km ks0 100
+    if ((2 * W * km + slots) * ks0 * 100 < 97LL * 2 * slots * km) return (int)km;
+    return (int)ks0;
 }
 
 namespace {
@@ -458,9 +501,7 @@ long resident_gram_ctas() {
     return cached.load();
 }
 
-// Row-split factor of the Gram: the upper-triangle tiles times the splits fill
-// at most one wave of resident CTAs (a partial extra wave would run at a
-// fraction of the machine), and every split keeps at least 256 rows.
+// Row-split factor of the Gram (gram_split_rule on this GPU's resident slots).
 int gram_ksplit(int m, int n) { return gram_split_rule(m, n, resident_gram_ctas()); }
 }  // namespace
 
@@ -520,9 +561,13 @@ tt_status gram_fixed_scratch(cudaStream_t s, int m, int n, const double* A, long
 
 long gram_resident() { return resident_gram_ctas(); }
 
-size_t dyn_partials_doubles() {
+size_t dyn_partials_doubles(int nmax) {
     const size_t sk = (size_t)(304 + 152) * BM * BN;
-    const size_t gr = (size_t)2 * BN * BN * (size_t)resident_gram_ctas();
+    // one wave: ks n^2 <= (resident / tiles) n^2 <= 2 BN^2 resident; many
+    // waves: GRAM_MULTI_SPLITS n^2
+    size_t gr = (size_t)2 * BN * BN * (size_t)resident_gram_ctas();
+    const size_t mw = (size_t)GRAM_MULTI_SPLITS * (size_t)nmax * (size_t)nmax;
+    if (mw > gr) gr = mw;
     return sk > gr ? sk : gr;
 }
 

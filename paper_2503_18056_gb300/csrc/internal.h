@@ -94,16 +94,18 @@ void autotune_read(int* table);
 // rows, from the number of resident CTAs), shared by host and device.
 __host__ __device__ void sk_split(int M, int N, int K, int* ks_out, int* kchunk_out);
 __host__ __device__ int gram_split_rule(int m, int n, long resident);
+// splits of a large Gram dealt in many waves (gram_split_rule)
+constexpr int GRAM_MULTI_SPLITS = 64;
 
 // Products of a captured step, their sizes read from device memory: desc =
 // M, N, K, lda, ldb, ldc (Gram: n, n, m, lda, lda, ldg with A m x n), caps
 // bound every size the step can reach.  mode 0: plain product into C; 1:
 // dgemm_sk (split of K by sk_split, partials in P); 2: the Gram G = A^T A
 // (row split by gram_split_rule, partials in P).  The same bits as the host
-// path for the same sizes.  P holds dyn_partials_doubles() doubles.
+// path for the same sizes.  P holds dyn_partials_doubles(nmax) doubles.
 tt_status dgemm_dyn(cudaStream_t s, bool ta, bool tb, const int* desc, int Mcap, int Ncap, int Kcap,
                     double alpha, const double* A, const double* B, double* C, double* P, int mode);
-size_t dyn_partials_doubles();
+size_t dyn_partials_doubles(int nmax);  // nmax: the largest Gram order n
 long gram_resident();
 // scale_rows with rows, cols, ldi, ldo = desc[0..3] (rows * cols <= total_cap)
 void scale_rows_dyn(cudaStream_t s, const int* desc, long total_cap, const double* in, const double* v, int mode,
