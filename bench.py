@@ -754,8 +754,9 @@ def run_batch(args, torch, ttsn):
 
 # ncu DRAM read + write bytes of one left-Gram launch at the bench's rank cap
 # (2,097,152 x 897), scaled by the rows from an ncu capture (dram__bytes_read
-# and _write) of the same kernel on a 500,000 x 897 operand: 11.13 GB.
-GRAM_LEFT_CAP_TRAFFIC = (11104132608 + 24035072) * 2097152 / 500000
+# and _write) of the same kernel and split (64 row splits) on a 500,000 x 897
+# operand: 23.26 GB.
+GRAM_LEFT_CAP_TRAFFIC = (23020594176 + 235760896) * 2097152 / 500000
 
 
 def roofline_of(prof, fp64_peak, peaks):

@@ -536,8 +536,13 @@ tt_status eig_orthonormalise(tt_ctx* h, long m, int l, const double* Y, DevBuf& 
     TT_TRY(h->sk_Vt.ensure((size_t)l * l, s));
     TT_TRY(h->sk_Vs.ensure((size_t)l * l, s));
     TT_TRY(gram(s, (int)m, l, Y, l, h->sk_G.p, l, h->partials));
-    TT_TRY(syev(s, l, h->sk_G.p, l, h->sk_lam.p, h->sk_Vt.p, l, h->eig, h->d_int + HI_STATUS,
-                h->d_int + next_sweep_slot(h), h->max_sweeps));
+    // Y^T Y is positive semidefinite: the handle's eigensolver for such matrices
+    if (h->eig_method == TT_EIG_ONE_SIDED)
+        TT_TRY(syev_psd(s, l, h->sk_G.p, l, h->sk_lam.p, h->sk_Vt.p, l, h->eig, h->d_int + HI_STATUS,
+                        h->d_int + next_sweep_slot(h), h->max_sweeps));
+    else
+        TT_TRY(syev(s, l, h->sk_G.p, l, h->sk_lam.p, h->sk_Vt.p, l, h->eig, h->d_int + HI_STATUS,
+                    h->d_int + next_sweep_slot(h), h->max_sweeps));
     count_above_floor(s, h->sk_lam.p, l, h->d_int + HI_DEC);
     TT_CUDA_TRY(cudaMemcpyAsync(h->h_int + HI_DEC, h->d_int + HI_DEC, sizeof(int), cudaMemcpyDeviceToHost, s));
     TT_CUDA_TRY(cudaStreamSynchronize(s));
