@@ -20,9 +20,14 @@ written directly from its definitions with no tensor train involved:
 * interface fluxes (Sec. 3.1): ``upwind`` (Eq. upwind), ``rusanov`` (Eq.
   rusanov_flux_toro with S+ = rusanov_s c) or ``hll`` (Eq. hll with the wave
   speeds S_L, S_R of Sec. 3.1's piecewise definitions and the harmonic-mean
-  optical depth of Eq. tauc, constants beta and tau_threshold).  The ghost
-  cell of a vacuum face takes the boundary cell's own opacity for Eq. tauc;
-  a face with S_R = S_L (n_a = 0) carries no flux.
+  optical depth of Eq. tauc, constants beta and tau_threshold), or
+  ``rusanov_tau``: Eq. rusanov_flux_toro with a speed informed by the face's
+  optical depth (Sec. 3.1), S+ = c |n_a| min(1, 1 / tau_c) with tau_c from
+  Eq. tauc (constant beta = hll_beta): the thick-limit speed c |n_a| / tau_c
+  of the series expansion after Eq. hll where tau_c >= 1, and c |n_a| (the
+  flux is then upwinding) where the face is thin.  The ghost cell of a vacuum
+  face takes the boundary cell's own opacity for Eq. tauc; a face with
+  S_R = S_L (n_a = 0) carries no flux.
 
 The intensity array has shape (N_x[, N_y[, N_z]], N_theta, N_phi); spatial
 fields have shape (N_x[, N_y[, N_z]]).
@@ -161,6 +166,10 @@ class DenseSN:
                 F = np.where(na >= 0.0, FL, FR)
             elif self.flux == "rusanov":
                 F = 0.5 * (FL + FR) - 0.5 * self.rusanov_s * self.c * (UR - UL)
+            elif self.flux == "rusanov_tau":
+                tau = self._face_tau(a)[..., None, None]
+                w = np.where(tau > 1.0, 1.0 / np.where(tau > 1.0, tau, 1.0), 1.0)
+                F = 0.5 * (FL + FR) - 0.5 * self.c * np.abs(na) * w * (UR - UL)
             elif self.flux == "hll":
                 S_R, S_L = self._hll_speeds(na, self._face_tau(a))
                 den = S_R - S_L

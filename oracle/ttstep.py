@@ -43,7 +43,11 @@ g2 and (w_L2, w_R2), and its spatial core is
   with A = sqrt((1 - exp(-tau^2)) / tau^2) or sqrt(1 - tau^2 / 2) and
   B = sqrt((1 - exp(-tau^4)) / tau^2) or tau (tau >= or < tau_threshold),
   tau the face optical depth of Eq. tauc (ghost opacity: wrapped cell for
-  periodic axes, the boundary cell for vacuum).
+  periodic axes, the boundary cell for vacuum);
+* Rusanov with the optical-depth speed S+ = c |n_a| min(1, 1/tau) (Sec. 3.1,
+  the thick-limit speed of the expansion after Eq. hll): g = (n_a, |n_a|),
+  w = (1/2, 1/2) and (m/2, -m/2) with m = min(1, 1/tau) per face; |n_a| is
+  separable (sin(theta) |cos(phi)|, sin(theta) |sin(phi)|, |mu|).
 """
 import numpy as np
 
@@ -177,6 +181,13 @@ class TTSN:
             return A, B
 
         out = []
+        if self.flux == "rusanov_tau":
+            for t in (tau_with(shifted(-1)), tau_with(shifted(+1))):  # lo face, hi face
+                t = t.reshape(-1)
+                m = np.where(t > 1.0, 1.0 / np.where(t > 1.0, t, 1.0), 1.0)
+                out.append(((np.full(nc, 0.5), np.full(nc, 0.5)), (0.5 * m, -0.5 * m)))
+            (lo1, lo2), (hi1, hi2) = out
+            return (lo1, hi1), (lo2, hi2)
         for t in (tau_with(shifted(-1)), tau_with(shifted(+1))):  # lo face, hi face
             A, B = AB(t.reshape(-1))
             out.append(((A * (1.0 + B) / (A + B), B * (1.0 - A) / (A + B)),
@@ -186,7 +197,7 @@ class TTSN:
 
     def _angular(self, a):
         """Angular factors (theta, phi) of the two terms of axis a."""
-        if self.flux != "rusanov":
+        if self.flux not in ("rusanov", "rusanov_tau"):
             return self._masks(a)
         g = self.g
         one_t, one_p = np.ones_like(g["mu"]), np.ones_like(g["phi"])
@@ -196,7 +207,9 @@ class TTSN:
             n1 = (g["sin_theta"], np.sin(g["phi"]))
         else:
             n1 = (g["mu"], one_p)
-        return n1, (one_t, one_p)
+        if self.flux == "rusanov":
+            return n1, (one_t, one_p)
+        return n1, (np.abs(n1[0]), np.abs(n1[1]))
 
     def transport(self, cores):
         X, Th, Ph = cores

@@ -24,7 +24,7 @@ def _fields(n, seed, thick=False):
 def _pair(n, nt, npf, bc, seed, flux, **fk):
     nc = int(np.prod(n))
     cores = workloads.random_positive_tt([nc, nt, npf], [3, 2], seed)
-    f = _fields(n, seed + 100, thick=(flux == "hll"))
+    f = _fields(n, seed + 100, thick=(flux in ("hll", "rusanov_tau")))
     sigma_s = 0.5 * f["sigma_a"]
     dt = 0.3 * min(1.0 / m for m in n)
     args = dict(n=n, L=[1.0] * len(n), n_theta=nt, n_phi=npf, c=1.0, a_r=1.0, dt=dt,
@@ -36,7 +36,8 @@ def _pair(n, nt, npf, bc, seed, flux, **fk):
 
 
 FLUXES = [("rusanov", dict(rusanov_s=1.0)), ("rusanov", dict(rusanov_s=0.3)), ("rusanov", dict(rusanov_s=0.0)),
-          ("hll", dict(hll_beta=1.0, hll_tau_threshold=1.0)), ("hll", dict(hll_beta=5.0, hll_tau_threshold=0.5))]
+          ("hll", dict(hll_beta=1.0, hll_tau_threshold=1.0)), ("hll", dict(hll_beta=5.0, hll_tau_threshold=0.5)),
+          ("rusanov_tau", dict(hll_beta=1.0)), ("rusanov_tau", dict(hll_beta=20.0))]
 
 
 @pytest.mark.parametrize("n,bc", [((12,), VACUUM), ((8, 6), PERIODIC), ((8, 6), VACUUM),
@@ -224,3 +225,40 @@ def test_hll_small_tau_series_leaves_upwinding_at_third_order():
         want = 0.25 if n > 0 else -0.25
         # O(tau) corrections shrink with tau
         assert abs(coef[-1] - want) < 2e-3 and abs(coef[-1] - want) < abs(coef[0] - want)
+
+
+def test_rusanov_tau_on_thin_faces_is_upwind():
+    """tau_c <= 1 on every face (here no opacity): S+ = c |n_x| and Eq.
+    rusanov_flux_toro gives F_L for n_x > 0 and F_R for n_x < 0, upwinding."""
+    for bc in (VACUUM, PERIODIC):
+        up = _dense((9, 7), "upwind", bc, sigma=0.0)
+        rt = _dense((9, 7), "rusanov_tau", bc, sigma=0.0)
+        a, b = up.transport(up.I), rt.transport(rt.I)
+        assert np.abs(a - b).max() <= 1e-15 * np.abs(a).max()
+
+
+def test_rusanov_tau_on_thick_faces_is_the_hll_thick_limit():
+    """tau_c >> 1 on every face: S+ = c |n_x| / tau_c is the speed of the
+    series expansion of the HLL flux stated after Eq. hll, so the whole
+    transport step equals the (independently pinned) HLL step once
+    exp(-tau^2) underflows."""
+    for n in ((10,), (6, 5)):
+        hl = _dense(n, "hll", VACUUM, sigma=400.0, hll_beta=1.0, hll_tau_threshold=1.0)
+        rt = _dense(n, "rusanov_tau", VACUUM, sigma=400.0, hll_beta=1.0)
+        assert hl._face_tau(0).min() > 30.0
+        a, b = hl.transport(hl.I), rt.transport(rt.I)
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
+
+
+def test_rusanov_tau_matches_uniform_rusanov_for_unit_normals():
+    """Uniform tau_c = 3 and |n_x| = 1: the speed is c / 3 on every face, the
+    Rusanov flux of Eq. rusanov_flux_toro with S+ = c / 3."""
+    # dx = 1/12, beta = 1: tau = 2 dx / (2 / sigma) = dx sigma = 3 for sigma = 36
+    rt = _dense((12,), "rusanov_tau", PERIODIC, sigma=36.0, hll_beta=1.0)
+    ru = _dense((12,), "rusanov", PERIODIC, sigma=36.0, rusanov_s=1.0 / 3.0)
+    assert np.allclose(rt._face_tau(0), 3.0, rtol=1e-14)
+    sign = np.where(np.arange(8) < 4, 1.0, -1.0)
+    for d in (rt, ru):
+        d.nvec = [np.broadcast_to(sign, (4, 8)).copy()]
+    a, b = rt.transport(rt.I), ru.transport(ru.I)
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
