@@ -53,7 +53,7 @@ typedef enum {
 enum { TT_BC_PERIODIC = 0, TT_BC_VACUUM = 1, TT_BC_OUTFLOW = 2 };
 enum { TT_FP64 = 0, TT_MIXED = 1 };
 enum { TT_LAYOUT_GROUPED = 0, TT_LAYOUT_SPLIT = 1 };
-enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_HLL = 2 };
+enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_HLL = 2, TT_FLUX_RUSANOV_TAU = 3 };
 enum { TT_ROUND_GRAM = 0, TT_ROUND_RANDOMIZED = 1, TT_ROUND_TTSVD = 2 };
 enum { TT_EIG_ONE_SIDED = 0, TT_EIG_TWO_SIDED = 1 };
 
@@ -110,8 +110,13 @@ enum {
  * TT_FLUX_HLL (Eq. hll with the wave speeds that follow it and the optical
  * depth of Eq. tauc: flux_param[0] = beta > 0, flux_param[1] =
  * tau_threshold in (0, sqrt 2]; a vacuum face takes the boundary cell's own
- * opacity for Eq. tauc).  Every flux adds 1 + 2 ndim terms to the TT sum,
- * so the ranks grow as with upwinding.  The adjoint tape takes upwinding only.
+ * opacity for Eq. tauc); TT_FLUX_RUSANOV_TAU (Eq. rusanov_flux_toro with the
+ * speed informed by each face's optical depth, Sec. 3.1: S+ = c |n_a|
+ * min(1, 1 / tau_c), tau_c from Eq. tauc with flux_param[0] = beta > 0; the
+ * thick-limit speed c |n_a| / tau_c of the expansion after Eq. hll on thick
+ * faces, upwinding on faces with tau_c <= 1).  Every flux adds 1 + 2 ndim
+ * terms to the TT sum, so the ranks grow as with upwinding.  The adjoint tape
+ * takes upwinding only.
  */
 typedef struct {
     int ndim;

@@ -271,7 +271,9 @@ class TTSN(_Handle):
     """A TT-S_N problem on the current CUDA stream, in the paper's three-core
     layout (``layout=TT_LAYOUT_GROUPED``) or with one core per spatial axis
     (``TT_LAYOUT_SPLIT``; uniform sigma_a and sigma_s), with the upwind,
-    Rusanov (S+ = rusanov_s c) or HLL (hll_beta, hll_tau_threshold) flux.
+    Rusanov (S+ = rusanov_s c), HLL (hll_beta, hll_tau_threshold) or Rusanov
+    with the optical-depth speed S+ = c |n| min(1, 1/tau_c) ("rusanov_tau",
+    tau_c from Eq. tauc with beta = hll_beta) flux.
 
     Fields are array-likes of N_c values in C order of the grid (axis 0
     slowest); they are copied to the device and then into the library.
@@ -315,12 +317,14 @@ class TTSN(_Handle):
         desc.layout = int(layout)
         self.layout = int(layout)
         kinds = {"upwind": _native.TT_FLUX_UPWIND, "rusanov": _native.TT_FLUX_RUSANOV,
-                 "hll": _native.TT_FLUX_HLL}
+                 "hll": _native.TT_FLUX_HLL, "rusanov_tau": _native.TT_FLUX_RUSANOV_TAU}
         desc.flux = kinds[flux] if isinstance(flux, str) else int(flux)
         if desc.flux == _native.TT_FLUX_RUSANOV:
             desc.flux_param[0] = float(rusanov_s)
         elif desc.flux == _native.TT_FLUX_HLL:
             desc.flux_param[0], desc.flux_param[1] = float(hll_beta), float(hll_tau_threshold)
+        elif desc.flux == _native.TT_FLUX_RUSANOV_TAU:
+            desc.flux_param[0] = float(hll_beta)  # beta of Eq. tauc
         self._alloc = None
         if allocator == "torch":
             allocator = TorchAllocator()

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "TT_OK", 1: "TT_WARN_RANK_CAPPED", -1: "TT_ERR_ARG", -2: "TT_
 TT_BC_PERIODIC, TT_BC_VACUUM, TT_BC_OUTFLOW = 0, 1, 2
 TT_FP64, TT_MIXED = 0, 1
 TT_LAYOUT_GROUPED, TT_LAYOUT_SPLIT = 0, 1
-TT_FLUX_UPWIND, TT_FLUX_RUSANOV, TT_FLUX_HLL = 0, 1, 2
+TT_FLUX_UPWIND, TT_FLUX_RUSANOV, TT_FLUX_HLL, TT_FLUX_RUSANOV_TAU = 0, 1, 2, 3
 TT_ROUND_GRAM, TT_ROUND_RANDOMIZED, TT_ROUND_TTSVD = 0, 1, 2
 TT_EIG_ONE_SIDED, TT_EIG_TWO_SIDED = 0, 1
 TT_STEP_NO_SOURCE, TT_STEP_NO_ROUND = 1, 2

@@ -1415,7 +1415,8 @@ const char* graph_unsupported(const tt_ctx* h) {
     if (h->nsrc > 0) return "captured steps take no fixed sources or inflow faces";
     if (h->taping) return "captured steps are not taped";
     if (h->shard.on) return "a spatial shard exchanges on the host and is not captured";
-    if (h->fields.flux == TT_FLUX_HLL) return "captured steps take upwind or Rusanov fluxes";
+    if (h->fields.flux == TT_FLUX_HLL || h->fields.flux == TT_FLUX_RUSANOV_TAU)
+        return "captured steps take upwind or uniform-speed Rusanov fluxes";
     return nullptr;
 }
 
@@ -1933,9 +1934,9 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
             return fail(TT_ERR_ARG, "tt_create_shard: need 0 <= plane_begin < plane_end <= n[0]");
         if (D.layout != TT_LAYOUT_GROUPED)
             return fail(TT_ERR_ARG, "tt_create_shard: shards hold the grouped layout's spatial rows");
-        if (D.flux == TT_FLUX_HLL)
-            return fail(TT_ERR_ARG, "tt_create_shard: HLL (per-face optical depths) is not sharded; "
-                                    "use upwind or Rusanov");
+        if (D.flux == TT_FLUX_HLL || D.flux == TT_FLUX_RUSANOV_TAU)
+            return fail(TT_ERR_ARG, "tt_create_shard: fluxes with per-face optical depths (HLL, Rusanov with "
+                                    "the optical-depth speed) are not sharded; use upwind or Rusanov");
         cell0 = (long)sh->p0 * plane;
         nc = (long)(sh->p1 - sh->p0) * plane;
     }
@@ -1950,8 +1951,12 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
         return fail(TT_ERR_ARG, "tt_create: precision must be TT_FP64 or TT_MIXED");
     if (D.layout != TT_LAYOUT_GROUPED && D.layout != TT_LAYOUT_SPLIT)
         return fail(TT_ERR_ARG, "tt_create: layout must be TT_LAYOUT_GROUPED or TT_LAYOUT_SPLIT");
-    if (D.flux != TT_FLUX_UPWIND && D.flux != TT_FLUX_RUSANOV && D.flux != TT_FLUX_HLL)
-        return fail(TT_ERR_ARG, "tt_create: flux must be TT_FLUX_UPWIND, TT_FLUX_RUSANOV or TT_FLUX_HLL");
+    if (D.flux != TT_FLUX_UPWIND && D.flux != TT_FLUX_RUSANOV && D.flux != TT_FLUX_HLL &&
+        D.flux != TT_FLUX_RUSANOV_TAU)
+        return fail(TT_ERR_ARG, "tt_create: flux must be TT_FLUX_UPWIND, TT_FLUX_RUSANOV, TT_FLUX_HLL or "
+                                "TT_FLUX_RUSANOV_TAU");
+    if (D.flux == TT_FLUX_RUSANOV_TAU && !(D.flux_param[0] > 0.0 && D.flux_param[0] < 1e300))
+        return fail(TT_ERR_ARG, "tt_create: Rusanov with the optical-depth speed needs flux_param[0] = beta > 0");
     if (D.flux == TT_FLUX_RUSANOV && !(D.flux_param[0] >= 0.0 && D.flux_param[0] < 1e300))
         return fail(TT_ERR_ARG, "tt_create: Rusanov needs flux_param[0] = S+/c >= 0");
     if (D.flux == TT_FLUX_HLL && !(D.flux_param[0] > 0.0 && D.flux_param[0] < 1e300 &&
@@ -2075,6 +2080,12 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
                          D.flux_param[1], h->f_fw.p);
         f.fw = h->f_fw.p;
     }
+    if (D.flux == TT_FLUX_RUSANOV_TAU && D.layout == TT_LAYOUT_GROUPED) {
+        TT_CREATE_TRY(h->f_fw.ensure((size_t)nc * D.ndim * 8, s));
+        rusanov_tau_face_weights(s, g, h->f_sigma_a.p, h->has_sigma_s ? h->f_sigma_s.p : nullptr,
+                                 D.flux_param[0], h->f_fw.p);
+        f.fw = h->f_fw.p;
+    }
     for (int a = 0; a < D.ndim; ++a) {
         // the split layout's uniform stencils (all faces alike, opacities uniform)
         double w[4] = {f.wc[0], f.wc[1], f.wc[2], f.wc[3]};
@@ -2086,6 +2097,14 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
             const double B = tau >= thr ? sqrt((1.0 - exp(-tau * tau * tau * tau)) / (tau * tau)) : tau;
             w[0] = w[3] = A * (1.0 + B) / (A + B);
             w[1] = w[2] = B * (1.0 - A) / (A + B);
+        }
+        if (D.flux == TT_FLUX_RUSANOV_TAU) {
+            const double sig = sig_a_uniform + sig_s_uniform;
+            const double tau = sig > 0.0 ? D.flux_param[0] * g.dx[a] * sig : 0.0;
+            const double m = tau > 1.0 ? 1.0 / tau : 1.0;
+            w[0] = w[1] = 0.5;
+            w[2] = 0.5 * m;
+            w[3] = -0.5 * m;
         }
         for (int t = 0; t < 2; ++t) {
             h->split_co.c[a][t][0] = w[2 * t] - w[2 * t + 1];
@@ -2114,19 +2133,24 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
     }
     {
         // per-term angular factors (Sec. 4.3): term 0 is I itself; term (a, 1)
-        // and (a, 2) carry n_a^+ and n_a^- (upwind, HLL) or n_a and 1 (Rusanov),
-        // with n_x = sin(theta) cos(phi), n_y = sin(theta) sin(phi), n_z = mu
+        // and (a, 2) carry n_a^+ and n_a^- (upwind, HLL), n_a and 1 (Rusanov)
+        // or n_a and |n_a| (Rusanov with the optical-depth speed), with
+        // n_x = sin(theta) cos(phi), n_y = sin(theta) sin(phi), n_z = mu
         double* tf = hbuf.data() + 2 * D.n_theta + 2 * D.n_phi;
         double* pf = tf + (size_t)KT * D.n_theta;
-        const bool rus = D.flux == TT_FLUX_RUSANOV;
+        const bool rt = D.flux == TT_FLUX_RUSANOV_TAU;
+        const bool rus = D.flux == TT_FLUX_RUSANOV || rt;
         for (int j = 0; j < KT; ++j) {
             const int axis = (j - 1) >> 1, second = (j - 1) & 1;
+            const bool absn = rt && second;  // |n_a| = sin(theta) |cos phi|, sin(theta) |sin phi|, |mu|
             for (int l = 0; l < D.n_theta; ++l) {
                 const double mu = hbuf[l], st = hbuf[D.n_theta + l];
                 double v = 1.0;
-                if (j > 0 && !(rus && second)) {
+                if (j > 0 && !(rus && second && !absn)) {
                     if (axis < 2)
                         v = st;
+                    else if (absn)
+                        v = std::fabs(mu);
                     else
                         v = rus ? mu : (second ? std::min(mu, 0.0) : std::max(mu, 0.0));
                 }
@@ -2135,9 +2159,9 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
             for (int p = 0; p < D.n_phi; ++p) {
                 const double cp = hbuf[2 * D.n_theta + p], sp = hbuf[2 * D.n_theta + D.n_phi + p];
                 double v = 1.0;
-                if (j > 0 && !(rus && second) && axis < 2) {
+                if (j > 0 && !(rus && second && !absn) && axis < 2) {
                     const double n = axis == 0 ? cp : sp;
-                    v = rus ? n : (second ? std::min(n, 0.0) : std::max(n, 0.0));
+                    v = absn ? std::fabs(n) : (rus ? n : (second ? std::min(n, 0.0) : std::max(n, 0.0)));
                 }
                 pf[(size_t)j * D.n_phi + p] = v;
             }

@@ -395,6 +395,9 @@ void split_source_cells(cudaStream_t s, const Grid& g, const Fields& f, const St
 // periodic axes, the cell itself on vacuum faces).
 void hll_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, const double* sigma_s,
                       double beta, double tau_threshold, double* fw);
+// The same layout for Eq. rusanov_flux_toro with S+ = c |n_a| min(1, 1 / tau_c).
+void rusanov_tau_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, const double* sigma_s,
+                              double beta, double* fw);
 // Inflow face (axis, side) of a vacuum axis as a fixed-source column: x[i] =
 // w g[i] / dx_a on the face's layer of cells (0 elsewhere), w = +w_L(i-1/2) of
 // term t on the low face, -w_R(i+1/2) on the high face, so that c dt x is the

@@ -443,6 +443,32 @@ __global__ void hll_weights_kernel(Grid g, const double* __restrict__ sa, const 
     }
 }
 
+// Face weights of Eq. rusanov_flux_toro with S+ = c |n_a| m, m = min(1, 1 /
+// tau_c) (tau_c from Eq. tauc): F = c n_a (U_L + U_R) / 2 + c |n_a| (m U_L -
+// m U_R) / 2, i.e. (w_L1, w_R1, w_L2, w_R2) = (1/2, 1/2, m/2, -m/2).
+__global__ void rusanov_tau_weights_kernel(Grid g, const double* __restrict__ sa, const double* __restrict__ ss,
+                                           double beta, double* __restrict__ fw) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nc; i += (long)gridDim.x * blockDim.x) {
+        long nb[3][2];
+        cell_neighbours(g, i, nb);
+        const double si = sa[i] + (ss ? ss[i] : 0.0);
+        for (int a = 0; a < g.ndim; ++a) {
+            for (int side = 0; side < 2; ++side) {
+                const long j = nb[a][side] >= 0 ? nb[a][side] : i;
+                const double sj = sa[j] + (ss ? ss[j] : 0.0);
+                double tau = 0.0;
+                if (si > 0.0 && sj > 0.0) tau = 2.0 * beta * g.dx[a] / (1.0 / si + 1.0 / sj);
+                const double m = tau > 1.0 ? 1.0 / tau : 1.0;
+                double* p = fw + (i * g.ndim + a) * 8 + side * 4;
+                p[0] = 0.5;
+                p[1] = 0.5;
+                p[2] = 0.5 * m;
+                p[3] = -0.5 * m;
+            }
+        }
+    }
+}
+
 __global__ void inflow_source_kernel(Grid g, Fields f, int axis, int side, int term,
                                      const double* __restrict__ gface, double* __restrict__ x) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < g.nc; i += (long)gridDim.x * blockDim.x) {
@@ -925,6 +951,12 @@ void hll_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, cons
                       double beta, double tau_threshold, double* fw) {
     note_launch();
     hll_weights_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, sigma_a, sigma_s, beta, tau_threshold, fw);
+}
+
+void rusanov_tau_face_weights(cudaStream_t s, const Grid& g, const double* sigma_a, const double* sigma_s,
+                              double beta, double* fw) {
+    note_launch();
+    rusanov_tau_weights_kernel<<<blocks_for(g.nc), 256, 0, s>>>(g, sigma_a, sigma_s, beta, fw);
 }
 
 void inflow_source(cudaStream_t s, const Grid& g, const Fields& f, int axis, int side, int term,

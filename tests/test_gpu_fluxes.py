@@ -17,7 +17,8 @@ from oracle.ttstep import PERIODIC, VACUUM, TTSN as OracleTTSN
 pytestmark = pytest.mark.gpu
 
 FLUXES = [("rusanov", dict(rusanov_s=1.0)), ("rusanov", dict(rusanov_s=0.3)), ("rusanov", dict(rusanov_s=0.0)),
-          ("hll", dict(hll_beta=1.0, hll_tau_threshold=1.0)), ("hll", dict(hll_beta=5.0, hll_tau_threshold=0.5))]
+          ("hll", dict(hll_beta=1.0, hll_tau_threshold=1.0)), ("hll", dict(hll_beta=5.0, hll_tau_threshold=0.5)),
+          ("rusanov_tau", dict(hll_beta=1.0)), ("rusanov_tau", dict(hll_beta=20.0))]
 
 
 @pytest.fixture(scope="module")
@@ -146,7 +147,8 @@ def test_hll_mixed_matches_fp64_at_fp64_ranks(ttsn):
 
 @pytest.mark.parametrize("bad", [dict(flux=5), dict(flux="rusanov", rusanov_s=-0.1),
                                  dict(flux="hll", hll_beta=0.0), dict(flux="hll", hll_tau_threshold=1.5),
-                                 dict(flux="hll", hll_tau_threshold=0.0)])
+                                 dict(flux="hll", hll_tau_threshold=0.0), dict(flux="rusanov_tau", hll_beta=0.0),
+                                 dict(flux="rusanov_tau", hll_beta=-1.0)])
 def test_flux_parameter_errors(ttsn, bad):
     a = _args((6, 5), 4, 8, VACUUM, 31)
     with pytest.raises(ttsn.TTError) as e:
@@ -204,7 +206,8 @@ def test_gaussian_diffusion_32_matches_the_dense_oracle(ttsn):
 
 @pytest.mark.parametrize("layout", ["grouped", "split"])
 @pytest.mark.parametrize("n,bc", [((9, 7), [2, 2]), ((6, 5, 4), [2, 1, 0])])
-@pytest.mark.parametrize("flux,fk", [("upwind", {}), ("hll", dict(hll_beta=2.0, hll_tau_threshold=1.0))])
+@pytest.mark.parametrize("flux,fk", [("upwind", {}), ("hll", dict(hll_beta=2.0, hll_tau_threshold=1.0)),
+                                     ("rusanov_tau", dict(hll_beta=20.0))])
 def test_outflow_faces_untruncated_step_equals_dense(ttsn, layout, n, bc, flux, fk):
     """Outflow faces (ghost cells copy the boundary cell, Sec. 4.5)."""
     nt, npf = 4, 6
