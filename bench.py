@@ -494,8 +494,9 @@ def run_fluxes(args, torch, ttsn):
     """The Rusanov and HLL fluxes on the paper's Gaussian-diffusion setup, and
     the hohlraum of Sec. 5.1 (inflow faces).  Diffusion:
     (128^2 cells on 5 x 5, 8 x 16 ordinates, rho kappa_s = 1e3, no absorption,
-    t0 = 200, eps 1e-6): Rusanov at S+ = 0 (the paper's choice) and HLL
-    (beta 1, tau_threshold 1); K_f steps from the initial state timed with
+    t0 = 200, eps 1e-6): Rusanov at S+ = 0 (the paper's choice), HLL
+    (beta 1, tau_threshold 1) and Rusanov with the optical-depth speed
+    S+ = c |n| min(1, 1/tau_c) (beta 1); K_f steps from the initial state timed with
     CUDA events after an untimed run of the same length, then E compared
     with the analytic solution A / (4 pi D (t0 + t)) exp(-r^2 / (4 D (t0 + t)))."""
     p = workloads.gaussian_diffusion()
@@ -509,7 +510,8 @@ def run_fluxes(args, torch, ttsn):
                        "t0 200, vacuum, CFL 0.5, eps 1e-6; steps 1..%d" % kf}
     with torch.cuda.stream(stream):
         for name, kw in (("rusanov_s0", dict(flux="rusanov", rusanov_s=0.0)),
-                         ("hll", dict(flux="hll", hll_beta=1.0, hll_tau_threshold=1.0))):
+                         ("hll", dict(flux="hll", hll_beta=1.0, hll_tau_threshold=1.0)),
+                         ("rusanov_tau", dict(flux="rusanov_tau", hll_beta=1.0))):
             ttsn.TTSN.from_problem(p, stream=stream, **kw).step(kf)  # warm-up
             g = ttsn.TTSN.from_problem(p, stream=stream, **kw)
             torch.cuda.synchronize()
