@@ -25,6 +25,11 @@
 // the grid barrier is a bounded spin that latches DEV_TIMEOUT in the status
 // word instead of waiting forever.
 #include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include <cooperative_groups.h>
 
 #include "internal.h"
 
@@ -386,6 +391,7 @@ jacobi_kernel(int n, int N, double* g0, double* g1, long ld, double* vt, double*
 // get eigenvalue 0 and a zero vector.  A negative rank (the factorisation met
 // Inf or NaN) gives NaN eigenvalues, which the rank decision reports.
 constexpr int OSJ_MAX_WARPS = 8;
+constexpr int OSJ_CLUSTER_N = 256;  // sizes solved on one thread-block cluster
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -484,7 +490,18 @@ __device__ __forceinline__ void osj_norms(const double* W, int n, int k, double*
     }
 }
 
-template <int C>
+// The round barrier: the whole grid (bounded spin, DEV_TIMEOUT on expiry) or,
+// for a launch of one thread-block cluster, the hardware cluster barrier.
+template <bool CLUSTER>
+__device__ __forceinline__ bool osj_barrier(int* ctrl, int* status, unsigned& epoch) {
+    if (CLUSTER) {
+        cooperative_groups::this_cluster().sync();
+        return true;
+    }
+    return grid_barrier(ctrl, status, gridDim.x, epoch);
+}
+
+template <int C, bool CLUSTER>
 __global__ void __launch_bounds__(32 * OSJ_MAX_WARPS)
 osj_kernel(int n, const int* __restrict__ k_dev, double* W, double* nrm, double* lam_u, double* vt_u, int* ctrl,
            int* status, int max_sweeps, const int* n_dev) {
@@ -517,7 +534,7 @@ osj_kernel(int n, const int* __restrict__ k_dev, double* W, double* nrm, double*
             // norms summed afresh at every sweep: the updates inside a sweep
             // only steer the angles and the skip test
             osj_norms(W, n, k, nrm, gw, nw, lane);
-            if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
+            if (!osj_barrier<CLUSTER>(ctrl, status, epoch)) return;
             int mine = 0;
             for (int r = 0; r < N - 1; ++r) {
                 for (int kk = gw; kk < npairs; kk += nw) {
@@ -531,7 +548,7 @@ osj_kernel(int n, const int* __restrict__ k_dev, double* W, double* nrm, double*
                     __syncthreads();
                     if (threadIdx.x == 0) atomicAdd(ctrl + 4 + sweep, s_cnt);
                 }
-                if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
+                if (!osj_barrier<CLUSTER>(ctrl, status, epoch)) return;
             }
             if (threadIdx.x == 0) s_done = (atomicAdd(ctrl + 4 + sweep, 0) == 0);
             __syncthreads();
@@ -544,7 +561,7 @@ osj_kernel(int n, const int* __restrict__ k_dev, double* W, double* nrm, double*
     }
     // eigenvalues: the converged rows' squared norms, summed from the rows
     osj_norms(W, n, k, nrm, gw, nw, lane);
-    if (!grid_barrier(ctrl, status, gridDim.x, epoch)) return;
+    if (!osj_barrier<CLUSTER>(ctrl, status, epoch)) return;
     for (int i = gw; i < n; i += nw) {
         const double a = i < k ? __ldcg(nrm + i) : 0.0;
         const double f = a > 0.0 ? 1.0 / sqrt(a) : 0.0;
@@ -554,132 +571,161 @@ osj_kernel(int n, const int* __restrict__ k_dev, double* W, double* nrm, double*
     }
 }
 
-// Pivoted Cholesky in one CTA for n <= PCHOL_ONE_CTA_N: the same factorisation
-// as pchol_kernel (pivot = largest remaining diagonal entry, stop at the
-// floor, -inf marks pivoted columns) with one thread per column: column j's
-// dot product sum_m W[m][p] W[m][j] reads W row by row, so a warp's loads are
-// contiguous and every thread keeps several in flight.  The residual diagonal
-// lives in shared memory; a __syncthreads separates each pivot's search from
-// its updates.  A pivot costs n k FP64 FMAs on one SM: below ~384 columns that
-// is less than the grid-wide barrier the multi-CTA kernel pays per pivot.
-constexpr int PCHOL_ONE_CTA_N = 384;
-constexpr int PST = 1024;
+// Pivoted Cholesky on one thread-block cluster for n <= PCHOL_SMALL_N: the
+// same factorisation as pchol_kernel (pivot = largest remaining diagonal
+// entry, ties to the lowest index, stop at the floor, -inf marks pivoted
+// columns, the same per-column sums), with contiguous blocks of cpc columns
+// per CTA, one thread per column, and the CTA's columns of W held in its
+// shared memory.  A pivot: every CTA reads the CTAs' candidate (value,
+// column) pairs from distributed shared memory and takes the same pivot p,
+// reads W[0..k)[p] from the owner's shared memory, forms row k of W for its
+// columns, updates their residual diagonal and posts its candidate for the
+// next pivot; one hardware cluster barrier (release / acquire at cluster
+// scope) ends the pivot.  On GB300 a pivot's n k FP64 FMAs are more than one
+// SM absorbs (~1.7 FMA per clock) and a grid-wide barrier per pivot costs
+// microseconds; a cluster spreads the FMAs over CL SMs for a barrier well
+// under a microsecond.  Candidates are double-buffered by the pivot's
+// parity, so a CTA never overwrites a slot another CTA may still read.
+constexpr int PCHOL_SMALL_N = 384;
 
-__global__ void __launch_bounds__(PST)
-pchol_small_kernel(int n, const double* __restrict__ G, long ldg, double* W, int* kB_out,
-                   double floor_rel, const int* n_dev) {
-    if (n_dev) {  // a captured step: the size is the device's, this kernel takes n <= PCHOL_ONE_CTA_N
+__global__ void __launch_bounds__(256)
+pchol_cluster_kernel(int n, int cpc, const double* __restrict__ G, long ldg, double* W, int* kB_out,
+                     double floor_rel, const int* n_dev, int nsmall) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    if (n_dev) {  // a captured step: the size is the device's; larger sizes take pchol_kernel
         n = *n_dev;
         ldg = n;
-        if (n > PCHOL_ONE_CTA_N) return;
+        if (n > nsmall) return;  // every CTA of the cluster, before any barrier
         if (n <= 0) {
-            if (threadIdx.x == 0) *kB_out = 0;
+            if (rank == 0 && threadIdx.x == 0) *kB_out = 0;
             return;
         }
     }
     extern __shared__ double sm[];
-    double* dd = sm;        // n: residual diagonal
-    double* colp = sm + n;  // n: W[0..k)[p]
-    __shared__ double s_v[PST / 32];
-    __shared__ int s_i[PST / 32];
-    __shared__ double s_best;
-    __shared__ int s_p;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    double dm = 0.0;
-    int bad = 0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double x = G[(long)j * ldg + j];
-        dd[j] = x;
-        dm = fmax(dm, x);
-        bad |= !isfinite(x);
-    }
-    // Inf or NaN on the diagonal (a Gram matrix shows any non-finite entry of
-    // its factor there): rank -1 reports it instead of factorising
-    if (__syncthreads_or(bad)) {
-        if (threadIdx.x == 0) *kB_out = -1;
-        return;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-    if (lane == 0) s_v[warp] = dm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < nwarps; ++w) m = fmax(m, s_v[w]);
-        s_best = m;
-    }
-    __syncthreads();
-    const double floor_abs = floor_rel * s_best;
-    int k = 0;
-    for (; k < n; ++k) {
-        // argmax of the residual diagonal (ties -> lowest index)
-        double best = -1.0;
-        int bi = n;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double x = dd[j];
-            if (x > best) {
-                best = x;
-                bi = j;
-            }
-        }
+    double* Wl = sm;                         // rows 0..k) of this CTA's cpc columns (n x cpc)
+    double* colp = sm + (size_t)n * cpc;     // W[0..k)[p]
+    __shared__ double s_cv[2];  // candidate value per parity
+    __shared__ int s_ci[2];     // candidate column per parity
+    __shared__ double s_wv[8];
+    __shared__ int s_wi[8];
+    __shared__ int s_bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    const int jl = threadIdx.x;
+    const int j = rank * cpc + jl;
+    const bool own = jl < cpc && j < n;
+    double dj = own ? G[(long)j * ldg + j] : -1.0;
+    // block candidate of (value, index), ties to the lowest index
+    auto post = [&](double v, int idx, int par) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double b2 = __shfl_xor_sync(0xffffffffu, best, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (b2 > best || (b2 == best && i2 < bi)) {
-                best = b2;
-                bi = i2;
+            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (v2 > v || (v2 == v && i2 < idx)) {
+                v = v2;
+                idx = i2;
             }
         }
         if (lane == 0) {
-            s_v[warp] = best;
-            s_i[warp] = bi;
+            s_wv[warp] = v;
+            s_wi[warp] = idx;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double b = -1.0;
-            int p = n;
+            int bi = n;
             for (int w = 0; w < nwarps; ++w)
-                if (s_v[w] > b || (s_v[w] == b && s_i[w] < p)) {
-                    b = s_v[w];
-                    p = s_i[w];
+                if (s_wv[w] > b || (s_wv[w] == b && s_wi[w] < bi)) {
+                    b = s_wv[w];
+                    bi = s_wi[w];
                 }
-            s_best = b;
-            s_p = p;
+            s_cv[par] = b;
+            s_ci[par] = bi;
         }
-        __syncthreads();
-        const double dp = s_best;
-        const int p = s_p;
+    };
+    // the cluster's candidate, read from every CTA's slot (after a barrier):
+    // lane r of every warp reads CTA r's slot, a shuffle tree takes the best
+    auto gather = [&](int par, double& b, int& bi) {
+        b = -1.0;
+        bi = n;
+        if (lane < CL) {
+            b = *cl.map_shared_rank(&s_cv[par], lane);
+            bi = *cl.map_shared_rank(&s_ci[par], lane);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, b, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (v2 > b || (v2 == b && i2 < bi)) {
+                b = v2;
+                bi = i2;
+            }
+        }
+    };
+    // Inf or NaN on the diagonal (a Gram matrix shows any non-finite entry of
+    // its factor there): rank -1 reports it instead of factorising
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    if (own && !isfinite(dj)) atomicOr(&s_bad, 1);
+    __syncthreads();
+    // the largest diagonal entry (the floor's scale) and the first pivot
+    post(own ? dj : -1.0, own ? j : n, 0);
+    if (threadIdx.x == 0 && s_bad) s_cv[0] = __longlong_as_double(0x7ff8000000000000LL);  // NaN marks it
+    cl.sync();
+    const int anybad = __any_sync(0xffffffffu, lane < CL && isnan(*cl.map_shared_rank(&s_cv[0], lane)));
+    if (anybad) {
+        cl.sync();  // every CTA has read the slots before any CTA exits
+        if (rank == 0 && threadIdx.x == 0) *kB_out = -1;
+        return;
+    }
+    double dmax;
+    int p;
+    gather(0, dmax, p);
+    const double floor_abs = floor_rel * dmax;
+    double dp = dmax;
+    int par = 0;
+    int k = 0;
+    for (; k < n; ++k) {
         if (!(dp > floor_abs) || p >= n) break;
         const double l = sqrt(dp);
-        for (int m = threadIdx.x; m < k; m += blockDim.x) colp[m] = W[(long)m * n + p];
+        {
+            const double* Wo = cl.map_shared_rank(Wl, p / cpc);  // the owner's columns
+            const int pl = p % cpc;
+            for (int m = threadIdx.x; m < k; m += blockDim.x) colp[m] = Wo[(size_t)m * cpc + pl];
+        }
         __syncthreads();
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double dj = dd[j];
+        if (own) {
             double w;
             if (j == p) {
                 w = l;
-                dd[j] = -INFINITY;
+                dj = -INFINITY;
             } else if (dj == -INFINITY) {
                 w = 0.0;
             } else {
                 double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
                 int m = 0;
                 for (; m + 3 < k; m += 4) {
-                    a0 += colp[m] * W[(long)m * n + j];
-                    a1 += colp[m + 1] * W[(long)(m + 1) * n + j];
-                    a2 += colp[m + 2] * W[(long)(m + 2) * n + j];
-                    a3 += colp[m + 3] * W[(long)(m + 3) * n + j];
+                    a0 += colp[m] * Wl[(size_t)m * cpc + jl];
+                    a1 += colp[m + 1] * Wl[(size_t)(m + 1) * cpc + jl];
+                    a2 += colp[m + 2] * Wl[(size_t)(m + 2) * cpc + jl];
+                    a3 += colp[m + 3] * Wl[(size_t)(m + 3) * cpc + jl];
                 }
-                for (; m < k; ++m) a0 += colp[m] * W[(long)m * n + j];
+                for (; m < k; ++m) a0 += colp[m] * Wl[(size_t)m * cpc + jl];
                 w = (G[(long)p * ldg + j] - ((a0 + a1) + (a2 + a3))) / l;
-                dd[j] = dj - w * w;
+                dj = dj - w * w;
             }
-            W[(long)k * n + j] = w;
+            Wl[(size_t)k * cpc + jl] = w;
+            __stcg(W + (long)k * n + j, w);
         }
-        __syncthreads();
+        par ^= 1;
+        post(own && dj != -INFINITY ? dj : -1.0, own && dj != -INFINITY ? j : n, par);
+        cl.sync();
+        gather(par, dp, p);
     }
-    if (threadIdx.x == 0) *kB_out = k;
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+    if (rank == 0 && threadIdx.x == 0) *kB_out = k;
 }
 
 // One CTA per source row j: rank of lam_j among all (descending, ties by index),
@@ -732,11 +778,11 @@ __global__ void trivial_eig_kernel(const double* G, double* lam, double* Vt, int
 // could pick a different pivot once the fast ones had marked theirs).
 __global__ void __launch_bounds__(JT)
 pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* Wc, double* d,
-             int* ctrl, int* status, double floor_rel, const int* n_dev) {
-    if (n_dev) {  // a captured step: sizes up to PCHOL_ONE_CTA_N go to pchol_small_kernel
+             int* ctrl, int* status, double floor_rel, const int* n_dev, int nsmall) {
+    if (n_dev) {  // a captured step: sizes up to nsmall go to pchol_cluster_kernel
         n = *n_dev;
         ldg = n;
-        if (n <= PCHOL_ONE_CTA_N) return;  // every CTA, before any barrier
+        if (n <= nsmall) return;  // every CTA, before any barrier
     }
     unsigned epoch = 0;
     extern __shared__ double sm[];
@@ -836,8 +882,8 @@ pchol_kernel(int n, const double* __restrict__ G, long ldg, double* W, double* W
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl[3] = k;
 }
 
-__global__ void pchol_finish_kernel(const int* ctrl, int* kB_out, const int* n_dev) {
-    if (n_dev && *n_dev <= PCHOL_ONE_CTA_N) return;
+__global__ void pchol_finish_kernel(const int* ctrl, int* kB_out, const int* n_dev, int nsmall) {
+    if (n_dev && *n_dev <= nsmall) return;
     *kB_out = ctrl[3];
 }
 
@@ -1052,13 +1098,105 @@ tt_status syev(cudaStream_t s, int n, const double* G, long ldg, double* lam, do
     return TT_OK;
 }
 
+// Largest cluster (16, else 8) the GPU schedules for a kernel of `threads`
+// threads and no dynamic shared memory, found once per kernel.
+int cluster_size_for(const void* fn, int threads) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> known;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& kv : known)
+        if (kv.first == fn) return kv.second;
+    int cl = 8;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = 160 * 1024;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc > 0) cl = 16;
+    }
+    (void)cudaGetLastError();
+    known.emplace_back(fn, cl);
+    return cl;
+}
+
+// Largest n the cluster factorisation takes: at most PCHOL_SMALL_N, and its
+// columns of W must fit a CTA's shared memory (n ceil(n / CL) + n doubles).
+int pchol_small_limit() {
+    const int cl = cluster_size_for((const void*)pchol_cluster_kernel, 256);
+    int n = PCHOL_SMALL_N;
+    while (n > 0 && ((size_t)n * ((n + cl - 1) / cl) + n) * sizeof(double) > 200 * 1024) --n;
+    return n;
+}
+
+tt_status launch_pchol_cluster(cudaStream_t s, int n, const double* G, long ldg, double* W, int* kB_dev,
+                               const int* n_dev, int nsmall) {
+    const int cl = cluster_size_for((const void*)pchol_cluster_kernel, 256);
+    const int cpc = (n + cl - 1) / cl;
+    const int threads = std::max(32, (cpc + 31) / 32 * 32);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = ((size_t)n * cpc + n) * sizeof(double);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // stop at the rounding-noise level of G's entries (eps_mach max diag)
+    const double fr = 2.220446049250313e-16;
+    note_launch();
+    TT_CUDA_TRY(cudaLaunchKernelEx(&cfg, pchol_cluster_kernel, n, cpc, G, ldg, W, kB_dev, fr, n_dev, nsmall));
+    return TT_OK;
+}
+
 tt_status osj_launch(cudaStream_t s, int ncap, const int* k_dev, EigWork& w, int* status_dev, int max_sweeps,
                      const int* n_dev, double* nrm) {
     TT_TRY(ensure_ctrl(w, s));  // zero barrier and sweep counters (pchol used them)
+    int nn = ncap;
+    double* Wp = w.g0.p;
+    double* lamu = w.lam_unsorted.p;
+    double* vtu = w.vt_unsorted.p;
+    int* ctrl = w.d_ctrl;
+    int msw = max_sweeps;
+    if (ncap <= OSJ_CLUSTER_N) {
+        // one cluster: a round ends at a hardware cluster barrier instead of a
+        // grid-wide one; its CL SMs hold up to OSJ_MAX_WARPS pairs each
+        const int cl = cluster_size_for((const void*)osj_kernel<8, true>, 32 * OSJ_MAX_WARPS);
+        const int npairs = (ncap + 1) / 2;
+        const int wpb = std::max(1, std::min(OSJ_MAX_WARPS, (npairs + cl - 1) / cl));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cl);
+        cfg.blockDim = dim3(32 * wpb);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        note_launch();
+        TT_CUDA_TRY(cudaLaunchKernelEx(&cfg, osj_kernel<8, true>, nn, k_dev, Wp, nrm, lamu, vtu, ctrl, status_dev,
+                                       msw, n_dev));
+        return TT_OK;
+    }
     // rows in registers up to n = 1024 (entries per lane: 8, 16 or 32)
-    const void* fn = ncap <= 256 ? (const void*)osj_kernel<8>
-                     : ncap <= 512 ? (const void*)osj_kernel<16>
-                     : ncap <= 1024 ? (const void*)osj_kernel<32> : (const void*)osj_kernel<0>;
+    const void* fn = ncap <= 256 ? (const void*)osj_kernel<8, false>
+                     : ncap <= 512 ? (const void*)osj_kernel<16, false>
+                     : ncap <= 1024 ? (const void*)osj_kernel<32, false> : (const void*)osj_kernel<0, false>;
     // one CTA per SM with one warp per pair it owns, so every SM carries the
     // same number of pairs in a round (the round ends at the slowest SM)
     int blocks = 1, wpb = 1;
@@ -1075,12 +1213,6 @@ tt_status osj_launch(cudaStream_t s, int ncap, const int* k_dev, EigWork& w, int
         }
         blocks = std::max(1, std::min((npairs + wpb - 1) / wpb, per_sm * sms));
     }
-    int nn = ncap;
-    double* Wp = w.g0.p;
-    double* lamu = w.lam_unsorted.p;
-    double* vtu = w.vt_unsorted.p;
-    int* ctrl = w.d_ctrl;
-    int msw = max_sweeps;
     void* args[] = {&nn, &k_dev, &Wp, &nrm, &lamu, &vtu, &ctrl, &status_dev, &msw, &n_dev};
     note_launch();
     TT_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(32 * wpb), args, 0, s));
@@ -1105,13 +1237,8 @@ tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, dou
         return TT_ERR_TOO_LARGE;
     }
     TT_TRY(ensure_max_dynamic_smem((const void*)pchol_kernel));
-    if (n <= PCHOL_ONE_CTA_N) {
-        note_launch();
-        pchol_small_kernel<<<1, PST, 2 * (size_t)n * sizeof(double), s>>>(n, G, ldg, W, kB_dev,
-                                                                          2.220446049250313e-16, nullptr);
-        TT_CUDA_TRY(cudaGetLastError());
-        return TT_OK;
-    }
+    const int nsmall = pchol_small_limit();
+    if (n <= nsmall) return launch_pchol_cluster(s, n, G, ldg, W, kB_dev, nullptr, nsmall);
     int blocks = 1;
     // about eight columns per CTA (one warp each)
     TT_TRY(coop_blocks((const void*)pchol_kernel, smem, std::max(1, (n + 7) / 8), &blocks));
@@ -1124,12 +1251,13 @@ tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, dou
     // parts of G_B that still carry tensor components at the 1e-9 level
     double fr = 2.220446049250313e-16;
     const int* nnull = nullptr;
-    void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr, &nnull};
+    int nsm = nsmall;
+    void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr, &nnull, &nsm};
     note_launch();
     TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)pchol_kernel, dim3(blocks), dim3(JT), args,
                                             smem, s));
     note_launch();
-    pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev, nullptr);
+    pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev, nullptr, nsmall);
     TT_CUDA_TRY(cudaGetLastError());
     return TT_OK;
 }
@@ -1137,9 +1265,11 @@ tt_status pchol(cudaStream_t s, int n, const double* G, long ldg, double* W, dou
 tt_status eig_reserve(EigWork& w, cudaStream_t s) { return ensure_ctrl(w, s); }
 
 tt_status eig_prepare() {
-    TT_TRY(ensure_max_dynamic_smem((const void*)pchol_small_kernel));
     TT_TRY(ensure_max_dynamic_smem((const void*)pchol_kernel));
     TT_TRY(ensure_max_dynamic_smem((const void*)jacobi_kernel));
+    // cluster attributes set before any capture
+    cluster_size_for((const void*)pchol_cluster_kernel, 256);
+    cluster_size_for((const void*)osj_kernel<8, true>, 32 * OSJ_MAX_WARPS);
     return TT_OK;
 }
 
@@ -1147,13 +1277,9 @@ tt_status pchol_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* G,
                     double* dwork, EigWork& w, int* status_dev, int* kB_dev) {
     if (ncap <= 0) return TT_OK;
     TT_TRY(ensure_ctrl(w, s));
-    const int small_cap = std::min(ncap, PCHOL_ONE_CTA_N);
-    TT_TRY(ensure_max_dynamic_smem((const void*)pchol_small_kernel));
-    note_launch();
-    pchol_small_kernel<<<1, PST, 2 * (size_t)small_cap * sizeof(double), s>>>(small_cap, G, small_cap, W, kB_dev,
-                                                                              2.220446049250313e-16, n_dev);
-    TT_CUDA_TRY(cudaGetLastError());
-    if (ncap > PCHOL_ONE_CTA_N) {
+    const int nsmall = pchol_small_limit();
+    TT_TRY(launch_pchol_cluster(s, std::min(ncap, nsmall), G, ncap, W, kB_dev, n_dev, nsmall));
+    if (ncap > nsmall) {
         const size_t smem = (size_t)ncap * sizeof(double);
         if (smem > 200 * 1024) {
             set_error("pchol: matrix too large");
@@ -1167,11 +1293,12 @@ tt_status pchol_dyn(cudaStream_t s, const int* n_dev, int ncap, const double* G,
         const double* Gp = G;
         int* ctrl = w.d_ctrl;
         double fr = 2.220446049250313e-16;
-        void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr, &n_dev};
+        int nsm = nsmall;
+        void* args[] = {&nn, &Gp, &ldgl, &W, &Wc, &dwork, &ctrl, &status_dev, &fr, &n_dev, &nsm};
         note_launch();
         TT_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)pchol_kernel, dim3(blocks), dim3(JT), args, smem, s));
         note_launch();
-        pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev, n_dev);
+        pchol_finish_kernel<<<1, 1, 0, s>>>(w.d_ctrl, kB_dev, n_dev, nsmall);
         TT_CUDA_TRY(cudaGetLastError());
     }
     return TT_OK;
