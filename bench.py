@@ -39,6 +39,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# hardware work queues for the batched leg's 64 streams (the default 8 makes
+# unrelated streams wait on one another); read when the CUDA context is made
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import workloads  # noqa: E402
 

@@ -550,7 +550,11 @@ class _BorrowedTTSN(TTSN):
 
 class TTSNBatch:
     """Independent TT-S_N problems of uneven sizes stepped together (each on its
-    own stream, advanced concurrently by host threads in the library)."""
+    own stream, advanced concurrently by host threads in the library, or as
+    captured steps with set_graph).  Many streams share the GPU's hardware
+    work queues: with CUDA_DEVICE_MAX_CONNECTIONS (environment, read when the
+    CUDA context is created; default 8) raised to 32 the 64-problem batch of
+    the bench runs 1.25x (host threads) and 2x (captured) faster."""
 
     def __init__(self, problems, threads=0, precision=TT_FP64):
         keep = []

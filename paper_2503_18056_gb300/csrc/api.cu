@@ -1432,6 +1432,7 @@ tt_status graph_step_body(tt_ctx* h) {
     int* dd = h->dyn;
     const int* desc = dd + DYN_DESC;
     double* P = h->dyn_part.p;
+    const size_t PC = h->dyn_part.cap;
     double* dec_d = h->dyn_buf.p + (DYN_INTS + 1) / 2;
     const PlanConsts pc{nterms, nt, np, nc};
     auto plan = [&](int stage) {
@@ -1449,18 +1450,18 @@ tt_status graph_step_body(tt_ctx* h) {
                           h->ydots.p, Sources(), dd);
     // rounding (App. A.2, one-sided Gram truncation): backward sweep
     fill(s, h->d_dbl + HD_DELTA2, 1, -1.0);
-    TT_TRY(dgemm_dyn(s, false, true, desc + 0, G2, G2, np, 1.0, h->gcore[2].p, h->gcore[2].p, h->GB[1].p, P, 1));
-    TT_TRY(dgemm_dyn(s, false, false, desc + 8, G1 * nt, G2, G2, 1.0, h->gcore[1].p, h->GB[1].p, h->bwd.p, P, 0));
-    TT_TRY(dgemm_dyn(s, false, true, desc + 16, G1, G1, nt * G2, 1.0, h->bwd.p, h->gcore[1].p, h->GB[0].p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 0, G2, G2, np, 1.0, h->gcore[2].p, h->gcore[2].p, h->GB[1].p, P, PC, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 8, G1 * nt, G2, G2, 1.0, h->gcore[1].p, h->GB[1].p, h->bwd.p, P, PC, 0));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 16, G1, G1, nt * G2, 1.0, h->bwd.p, h->gcore[1].p, h->GB[0].p, P, PC, 1));
     TT_TRY(pchol_dyn(s, dd + DYN_G1, G1, h->GB[0].p, h->VtB[0].p, h->Wc.p, h->lamB[0].p, h->eig,
                      h->d_int + HI_STATUS, dd + DYN_KB0));
     TT_TRY(pchol_dyn(s, dd + DYN_G2, G2, h->GB[1].p, h->VtB[1].p, h->Wc.p, h->lamB[1].p, h->eig,
                      h->d_int + HI_STATUS, dd + DYN_KB1));
     plan(1);
     // bond 0: G_A, K = W G_A W^T, eig(K), decision
-    TT_TRY(dgemm_dyn(s, true, false, desc + 24, G1, G1, (int)nc, 1.0, h->gcore[0].p, h->gcore[0].p, h->GA.p, P, 2));
-    TT_TRY(dgemm_dyn(s, false, true, desc + 32, G1, G1, G1, 1.0, h->GA.p, h->VtB[0].p, h->T1.p, P, 1));
-    TT_TRY(dgemm_dyn(s, false, false, desc + 40, G1, G1, G1, 1.0, h->VtB[0].p, h->T1.p, h->K.p, P, 1));
+    TT_TRY(dgemm_dyn(s, true, false, desc + 24, G1, G1, (int)nc, 1.0, h->gcore[0].p, h->gcore[0].p, h->GA.p, P, PC, 2));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 32, G1, G1, G1, 1.0, h->GA.p, h->VtB[0].p, h->T1.p, P, PC, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 40, G1, G1, G1, 1.0, h->VtB[0].p, h->T1.p, h->K.p, P, PC, 1));
     TT_TRY((h->eig_method == TT_EIG_ONE_SIDED ? syev_psd_dyn : syev_dyn)(
         s, dd + DYN_KB0, G1, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS, dd + DYN_SWEEPS,
         h->max_sweeps));
@@ -1469,14 +1470,14 @@ tt_status graph_step_body(tt_ctx* h) {
     plan(2);
     // bond 0 update: P_A^T, M_upd, X' = X* P_A, next core = M_upd x_1 Theta*
     scale_rows_dyn(s, desc + 48, (long)c1 * G1, h->VtK.p, h->lamK.p, 2, h->Vts.p);
-    TT_TRY(dgemm_dyn(s, false, false, desc + 56, c1, G1, G1, 1.0, h->Vts.p, h->VtB[0].p, h->PAt.p, P, 1));
-    TT_TRY(dgemm_dyn(s, false, false, desc + 64, c1, G1, G1, 1.0, h->PAt.p, h->GA.p, h->Mupd.p, P, 1));
-    TT_TRY(dgemm_dyn(s, false, true, desc + 72, (int)nc, c1, G1, 1.0, h->gcore[0].p, h->PAt.p, h->core[0].p, P, 0));
-    TT_TRY(dgemm_dyn(s, false, false, desc + 80, c1, nt * G2, G1, 1.0, h->Mupd.p, h->gcore[1].p, h->tmp[0].p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 56, c1, G1, G1, 1.0, h->Vts.p, h->VtB[0].p, h->PAt.p, P, PC, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 64, c1, G1, G1, 1.0, h->PAt.p, h->GA.p, h->Mupd.p, P, PC, 1));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 72, (int)nc, c1, G1, 1.0, h->gcore[0].p, h->PAt.p, h->core[0].p, P, PC, 0));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 80, c1, nt * G2, G1, 1.0, h->Mupd.p, h->gcore[1].p, h->tmp[0].p, P, PC, 1));
     // bond 1 on the next core (replicated rows r0 n_theta)
-    TT_TRY(dgemm_dyn(s, true, false, desc + 88, G2, G2, c1 * nt, 1.0, h->tmp[0].p, h->tmp[0].p, h->GA.p, P, 2));
-    TT_TRY(dgemm_dyn(s, false, true, desc + 96, G2, G2, G2, 1.0, h->GA.p, h->VtB[1].p, h->T1.p, P, 1));
-    TT_TRY(dgemm_dyn(s, false, false, desc + 104, G2, G2, G2, 1.0, h->VtB[1].p, h->T1.p, h->K.p, P, 1));
+    TT_TRY(dgemm_dyn(s, true, false, desc + 88, G2, G2, c1 * nt, 1.0, h->tmp[0].p, h->tmp[0].p, h->GA.p, P, PC, 2));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 96, G2, G2, G2, 1.0, h->GA.p, h->VtB[1].p, h->T1.p, P, PC, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 104, G2, G2, G2, 1.0, h->VtB[1].p, h->T1.p, h->K.p, P, PC, 1));
     TT_TRY((h->eig_method == TT_EIG_ONE_SIDED ? syev_psd_dyn : syev_dyn)(
         s, dd + DYN_KB1, G2, h->K.p, h->lamK.p, h->VtK.p, h->eig, h->d_int + HI_STATUS, dd + DYN_SWEEPS + 1,
         h->max_sweeps));
@@ -1484,10 +1485,10 @@ tt_status graph_step_body(tt_ctx* h) {
                             dd + DYN_DEC1, dec_d + 4);
     plan(3);
     scale_rows_dyn(s, desc + 112, (long)c2 * G2, h->VtK.p, h->lamK.p, 2, h->Vts.p);
-    TT_TRY(dgemm_dyn(s, false, false, desc + 120, c2, G2, G2, 1.0, h->Vts.p, h->VtB[1].p, h->PAt.p, P, 1));
-    TT_TRY(dgemm_dyn(s, false, false, desc + 128, c2, G2, G2, 1.0, h->PAt.p, h->GA.p, h->Mupd.p, P, 1));
-    TT_TRY(dgemm_dyn(s, false, true, desc + 136, c1 * nt, c2, G2, 1.0, h->tmp[0].p, h->PAt.p, h->core[1].p, P, 0));
-    TT_TRY(dgemm_dyn(s, false, false, desc + 144, c2, np, G2, 1.0, h->Mupd.p, h->gcore[2].p, h->core[2].p, P, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 120, c2, G2, G2, 1.0, h->Vts.p, h->VtB[1].p, h->PAt.p, P, PC, 1));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 128, c2, G2, G2, 1.0, h->PAt.p, h->GA.p, h->Mupd.p, P, PC, 1));
+    TT_TRY(dgemm_dyn(s, false, true, desc + 136, c1 * nt, c2, G2, 1.0, h->tmp[0].p, h->PAt.p, h->core[1].p, P, PC, 0));
+    TT_TRY(dgemm_dyn(s, false, false, desc + 144, c2, np, G2, 1.0, h->Mupd.p, h->gcore[2].p, h->core[2].p, P, PC, 1));
     // energy-conserving temperature update (Sec. 3.2) from the rounded TT
     plain_thbar(s, h->ang, c1, c2, h->core[1].p, h->core[2].p, h->thbar.p, dd);
     energy_rows(s, nc, c1, h->core[0].p, c1, h->thbar.p, h->fields.c, nullptr, h->f_Estar.p, h->f_cv.p,
@@ -1508,6 +1509,17 @@ tt_status graph_reserve(tt_ctx* h) {
     const long nt = h->ang.n_theta, np = h->ang.n_phi, nc = g.nc;
     const long c1 = h->cap1, c2 = h->cap2, G1 = nterms * c1 + 1, G2 = nterms * c2 + 1;
     const long Gm = std::max(G1, G2);
+    // partials of the captured split products: the largest need over the
+    // (mode, M, N, K) capacities of graph_step_body's products
+    size_t part = 1;
+    {
+        const int c[][4] = {{1, (int)G2, (int)G2, (int)np},       {1, (int)G1, (int)G1, (int)(nt * G2)},
+                            {2, (int)G1, (int)G1, (int)nc},       {1, (int)G1, (int)G1, (int)G1},
+                            {1, (int)c1, (int)G1, (int)G1},       {1, (int)c1, (int)(nt * G2), (int)G1},
+                            {2, (int)G2, (int)G2, (int)(c1 * nt)}, {1, (int)G2, (int)G2, (int)G2},
+                            {1, (int)c2, (int)G2, (int)G2},       {1, (int)c2, (int)np, (int)G2}};
+        for (const auto& q : c) part = std::max(part, dyn_partials_need(q[0], q[1], q[2], q[3]));
+    }
     struct Need {
         DevBuf* b;
         long n;
@@ -1522,7 +1534,7 @@ tt_status graph_reserve(tt_ctx* h) {
         {&h->eig.g0, Gm * Gm}, {&h->eig.g1, Gm * Gm}, {&h->eig.vt_unsorted, Gm * Gm},
         {&h->eig.lam_unsorted, Gm}, {&h->eig.abc, 3 * (Gm + 1)}, {&h->eig.cs, Gm + 1},
         {&h->eig.psd, 3 * Gm + 2},
-        {&h->dyn_part, (long)dyn_partials_doubles(Gm)},
+        {&h->dyn_part, (long)part},
     };
     for (auto& x : need) TT_TRY(x.b->ensure((size_t)std::max<long>(x.n, 1), s, /*keep=*/true));
     TT_TRY(eig_reserve(h->eig, s));

@@ -160,18 +160,41 @@ dgemm_dyn_kernel(const int* __restrict__ desc, double alpha, const double* __res
                  long resident) {
     const int M = desc[0], N = desc[1], K = desc[2];
     const long lda = desc[3], ldb = desc[4], ldc = desc[5];
-    const int tn = blockIdx.x, tm = blockIdx.y, z = blockIdx.z;
-    if (tm * BM >= M || tn * BN >= N) return;
+    const int TM = (M + BM - 1) / BM, TN = (N + BN - 1) / BN;
+    int tm, tn, z = 0;
     int ks = 1, kchunk = K;
-    if (mode == 1) {
-        sk_split(M, N, K, &ks, &kchunk);
-    } else if (mode == 2) {
-        if (tn < tm) return;
-        ks = gram_split_rule(K, M, resident);
-        kchunk = (K + ks - 1) / ks;
-        kchunk = (kchunk + BK - 1) / BK * BK;
+    if (mode == 0) {  // a 2-D grid of tiles sized for the capacity
+        tn = blockIdx.x;
+        tm = blockIdx.y;
+        if (tm >= TM || tn >= TN) return;
+    } else {
+        // modes 1 and 2: a 1-D grid of (split, tile) items, sized on the host
+        // for the most items any size up to the capacity takes; items past
+        // this step's count return at once
+        if (mode == 1) {
+            sk_split(M, N, K, &ks, &kchunk);
+        } else {
+            ks = gram_split_rule(K, M, resident);
+            kchunk = (K + ks - 1) / ks;
+            kchunk = (kchunk + BK - 1) / BK * BK;
+        }
+        const int per = mode == 2 ? TM * (TM + 1) / 2 : TM * TN;  // Gram: upper-triangle tiles
+        const long item = blockIdx.x;
+        if (item >= (long)per * ks) return;
+        z = (int)(item / per);
+        int t = (int)(item % per);
+        if (mode == 2) {
+            tm = 0;
+            while (t >= TM - tm) {  // row tm of the upper triangle holds TM - tm tiles
+                t -= TM - tm;
+                ++tm;
+            }
+            tn = tm + t;
+        } else {
+            tm = t / TN;
+            tn = t % TN;
+        }
     }
-    if (z >= ks) return;
     const int kbeg = z * kchunk;
     const int kend = min(K, kbeg + kchunk);
     if (mode == 2 || ks > 1)
@@ -561,25 +584,74 @@ tt_status gram_fixed_scratch(cudaStream_t s, int m, int n, const double* A, long
 
 long gram_resident() { return resident_gram_ctas(); }
 
-size_t dyn_partials_doubles(int nmax) {
-    const size_t sk = (size_t)(304 + 152) * BM * BN;
-    // one wave: ks n^2 <= (resident / tiles) n^2 <= 2 BN^2 resident; many
-    // waves: GRAM_MULTI_SPLITS n^2
-    size_t gr = (size_t)2 * BN * BN * (size_t)resident_gram_ctas();
-    const size_t mw = (size_t)GRAM_MULTI_SPLITS * (size_t)nmax * (size_t)nmax;
-    if (mw > gr) gr = mw;
-    return sk > gr ? sk : gr;
+// The most (split, tile) items a split-mode product of sizes up to the
+// capacity can take (the split rules grow with K, so K = Kcap bounds them
+// per tile count; mode 1's tuned table is indexed by log2 K, so every K
+// bucket up to Kcap is tried).
+long dyn_items(int mode, int Mcap, int Ncap, int Kcap, long resident) {
+    long most = 1;
+    if (mode == 2) {
+        for (int n = 1; n <= Ncap; ++n) {
+            const long T = (n + BN - 1) / BN;
+            most = std::max(most, T * (T + 1) / 2 * (long)gram_split_rule(Kcap, n, resident));
+        }
+        return most;
+    }
+    // mode 1: sk_split's split is not monotone in K (the chunk is rounded to
+    // BK), so bound it instead: no split below 152 tiles exceeds the built-in
+    // ceil(304 / tiles), the tuned entries of every K bucket up to Kcap, 64,
+    // or ceil(Kcap / BK)
+    const int TMc = (Mcap + BM - 1) / BM, TNc = (Ncap + BN - 1) / BN;
+    const int kbmax = floor_log2(std::max(Kcap, 1));
+    for (int tm = 1; tm <= TMc; ++tm)
+        for (int tn = 1; tn <= TNc; ++tn) {
+            const long tiles = (long)tm * tn;
+            long ks = 1;
+            if (tiles < 152 && Kcap >= 4 * BK) {
+                ks = (304 + tiles - 1) / tiles;
+                const int tb = floor_log2((int)tiles);
+                if (tb < AT_TILE_BUCKETS)
+                    for (int kb = 0; kb <= kbmax && kb < AT_K_BUCKETS; ++kb)
+                        ks = std::max<long>(ks, h_sk_table[tb * AT_K_BUCKETS + kb]);
+                ks = std::min<long>(std::min<long>(ks, 64), (Kcap + BK - 1) / BK);
+                ks = std::max<long>(ks, 1);
+            }
+            most = std::max(most, tiles * ks);
+        }
+    return most;
+}
+
+size_t dyn_partials_need(int mode, int Mcap, int Ncap, int Kcap) {
+    if (mode == 0 || Mcap <= 0 || Ncap <= 0) return 0;
+    const long resident = resident_gram_ctas();
+    if (mode == 2) {  // ks(n) n^2 partial Grams for the most demanding n <= Ncap
+        size_t most = 0;
+        for (int n = 1; n <= Ncap; ++n)
+            most = std::max(most, (size_t)gram_split_rule(Kcap, n, resident) * (size_t)n * (size_t)n);
+        return most;
+    }
+    // ks M N <= ks tiles BM BN
+    return (size_t)dyn_items(1, Mcap, Ncap, Kcap, resident) * BM * BN;
 }
 
 tt_status dgemm_dyn(cudaStream_t s, bool ta, bool tb, const int* desc, int Mcap, int Ncap, int Kcap,
-                    double alpha, const double* A, const double* B, double* C, double* P, int mode) {
+                    double alpha, const double* A, const double* B, double* C, double* P, size_t pcap, int mode) {
     if (Mcap <= 0 || Ncap <= 0) return TT_OK;
+    if (dyn_partials_need(mode, Mcap, Ncap, Kcap) > pcap) {
+        set_error("dgemm: the partials buffer of a captured product is smaller than its split needs");
+        return TT_ERR_TOO_LARGE;
+    }
     const long resident = resident_gram_ctas();
-    int zmax = 1;
-    if (mode == 1) zmax = std::max(1, std::min(64, Kcap / (2 * BK)));
-    if (mode == 2) zmax = (int)std::max<long>(1, std::min<long>(std::min<long>(1024, resident), Kcap / 256));
-    dim3 grid((Ncap + BN - 1) / BN, (Mcap + BM - 1) / BM, zmax);
-    if (grid.y > 65535 || grid.z > 65535) {
+    dim3 grid((Ncap + BN - 1) / BN, (Mcap + BM - 1) / BM, 1);
+    if (mode != 0) {
+        const long items = dyn_items(mode, Mcap, Ncap, Kcap, resident);
+        if (items > 0x7fffffffL) {
+            set_error("dgemm: problem too large for the item grid");
+            return TT_ERR_TOO_LARGE;
+        }
+        grid = dim3((unsigned)items, 1, 1);
+    }
+    if (grid.y > 65535) {
         set_error("dgemm: problem too large for the tile grid");
         return TT_ERR_TOO_LARGE;
     }

@@ -102,10 +102,11 @@ constexpr int GRAM_MULTI_SPLITS = 64;
 // bound every size the step can reach.  mode 0: plain product into C; 1:
 // dgemm_sk (split of K by sk_split, partials in P); 2: the Gram G = A^T A
 // (row split by gram_split_rule, partials in P).  The same bits as the host
-// path for the same sizes.  P holds dyn_partials_doubles(nmax) doubles.
+// path for the same sizes.  P holds pcap doubles, at least
+// dyn_partials_need(mode, Mcap, Ncap, Kcap) (checked: TT_ERR_TOO_LARGE).
 tt_status dgemm_dyn(cudaStream_t s, bool ta, bool tb, const int* desc, int Mcap, int Ncap, int Kcap,
-                    double alpha, const double* A, const double* B, double* C, double* P, int mode);
-size_t dyn_partials_doubles(int nmax);  // nmax: the largest Gram order n
+                    double alpha, const double* A, const double* B, double* C, double* P, size_t pcap, int mode);
+size_t dyn_partials_need(int mode, int Mcap, int Ncap, int Kcap);
 long gram_resident();
 // scale_rows with rows, cols, ldi, ldo = desc[0..3] (rows * cols <= total_cap)
 void scale_rows_dyn(cudaStream_t s, const int* desc, long total_cap, const double* in, const double* v, int mode,

@@ -505,7 +505,10 @@ template <int C, bool CLUSTER>
 __global__ void __launch_bounds__(32 * OSJ_MAX_WARPS)
 osj_kernel(int n, const int* __restrict__ k_dev, double* W, double* nrm, double* lam_u, double* vt_u, int* ctrl,
            int* status, int max_sweeps, const int* n_dev) {
-    if (n_dev) n = *n_dev;
+    if (n_dev) {  // a captured step: sizes up to OSJ_CLUSTER_N take the cluster launch, larger the grid
+        n = *n_dev;
+        if (CLUSTER ? n > OSJ_CLUSTER_N : n <= OSJ_CLUSTER_N) return;  // every CTA, before any barrier
+    }
     // relative skip threshold sqrt(n) eps_mach, the one of LAPACK's one-sided
     // Jacobi SVD (dgesvj): the typical rounding error of a computed inner
     // product of length n, so rounding noise does not keep pairs rotating
@@ -1170,11 +1173,15 @@ tt_status osj_launch(cudaStream_t s, int ncap, const int* k_dev, EigWork& w, int
     double* vtu = w.vt_unsorted.p;
     int* ctrl = w.d_ctrl;
     int msw = max_sweeps;
-    if (ncap <= OSJ_CLUSTER_N) {
+    if (ncap <= OSJ_CLUSTER_N || n_dev) {
         // one cluster: a round ends at a hardware cluster barrier instead of a
-        // grid-wide one; its CL SMs hold up to OSJ_MAX_WARPS pairs each
+        // grid-wide one; its CL SMs hold up to OSJ_MAX_WARPS pairs each.  A
+        // captured step launches it for sizes up to OSJ_CLUSTER_N and the
+        // grid kernel after it for larger ones (each returns at once
+        // outside its range), so a replay takes the host path's kernel.
+        const int ncl = std::min(ncap, OSJ_CLUSTER_N);
         const int cl = cluster_size_for((const void*)osj_kernel<8, true>, 32 * OSJ_MAX_WARPS);
-        const int npairs = (ncap + 1) / 2;
+        const int npairs = (ncl + 1) / 2;
         const int wpb = std::max(1, std::min(OSJ_MAX_WARPS, (npairs + cl - 1) / cl));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cl);
@@ -1191,7 +1198,7 @@ tt_status osj_launch(cudaStream_t s, int ncap, const int* k_dev, EigWork& w, int
         note_launch();
         TT_CUDA_TRY(cudaLaunchKernelEx(&cfg, osj_kernel<8, true>, nn, k_dev, Wp, nrm, lamu, vtu, ctrl, status_dev,
                                        msw, n_dev));
-        return TT_OK;
+        if (ncap <= OSJ_CLUSTER_N) return TT_OK;
     }
     // rows in registers up to n = 1024 (entries per lane: 8, 16 or 32)
     const void* fn = ncap <= 256 ? (const void*)osj_kernel<8, false>
