@@ -752,8 +752,8 @@ def run_batch(args, torch, ttsn):
             "captured": {"problem_steps_per_s": len(ps) * kb / dt_cap,
                          "speedup_vs_host_threads": dt / dt_cap,
                          "same_bits_as_host_driven": bool(same),
-                         "how": "tt_batch_set_graph: one recorded step per problem replayed as a CUDA graph "
-                                "(device-decided ranks), all problems in flight from one host thread"},
+                         "how": "tt_batch_set_graph: every problem's recorded step a branch of one CUDA graph "
+                                "(device-decided ranks), one graph launch per batch step"},
             "ranks_last_min_max": [min(min(r) for r in ranks), max(max(r) for r in ranks)]}
 
 

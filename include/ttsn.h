@@ -453,11 +453,13 @@ void tt_batch_destroy(tt_batch b);
 
 /*
  * tt_batch_set_graph: captured steps (tt_set_graph) for every problem of the
- * batch.  tt_batch_step then replays each problem's recorded step on its own
- * stream from one host thread, all problems in flight at once, with one
- * synchronisation per problem at the end of the call instead of the rank
- * read-backs inside every step.  TT_ERR_STATE if a problem cannot be
- * captured (see tt_set_graph); the batch is then left unchanged.
+ * batch.  The first tt_batch_step then records one graph holding every
+ * problem's step as a branch of its own, and each batch step is one launch
+ * of it (the branches run concurrently, ordered with each problem's stream
+ * by events), with one synchronisation per problem at the end of the call
+ * instead of the rank read-backs inside every step.  TT_ERR_STATE if a
+ * problem cannot be captured (see tt_set_graph); the batch is then left
+ * unchanged.  Disabling drops the graph.
  */
 tt_status tt_batch_set_graph(tt_batch b, int enable);
 

@@ -1889,6 +1889,106 @@ tt_status adjoint_run(tt_ctx* h, double* grad_dev, double* Q_host) {
 // ============================================================== C ABI
 
 namespace ttsn {
+// One captured step for many handles: a graph with one branch per handle
+// (forked from and joined to an origin stream through events, each branch
+// the handle's graph_step_body on a capture stream of its own), so a batch
+// step is one graph launch.  The branches are independent and run
+// concurrently; every branch's arithmetic is its handle's captured step.
+tt_status graph_batch_build(tt_handle* hs, int n, cudaGraphExec_t* out, unsigned* launches) {
+    *out = nullptr;
+    *launches = 0;
+    for (int i = 0; i < n; ++i) {
+        TT_TRY(check_handle(hs[i], true));
+        if (!hs[i]->graph_on) return fail(TT_ERR_STATE, "captured steps are off for a handle of the batch");
+        TT_TRY(graph_start(hs[i]));
+        TT_CUDA_TRY(cudaStreamSynchronize(hs[i]->stream));
+    }
+    TT_TRY(eig_prepare());
+    cudaStream_t origin = nullptr;
+    TT_CUDA_TRY(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> caps(n, nullptr);
+    std::vector<cudaStream_t> saved(n, nullptr);
+    std::vector<cudaEvent_t> evs(n + 1, nullptr);
+    tt_status st = TT_OK;
+    cudaGraph_t graph = nullptr;
+    auto cleanup = [&]() {
+        for (int i = 0; i < n; ++i) {
+            if (saved[i]) hs[i]->stream = saved[i];
+            if (caps[i]) cudaStreamDestroy(caps[i]);
+        }
+        for (cudaEvent_t e : evs)
+            if (e) cudaEventDestroy(e);
+        cudaStreamDestroy(origin);
+    };
+    for (int i = 0; i < n && st == TT_OK; ++i) {
+        if (cudaStreamCreateWithFlags(&caps[i], cudaStreamNonBlocking) != cudaSuccess) st = TT_ERR_CUDA;
+        else if (cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming) != cudaSuccess) st = TT_ERR_CUDA;
+    }
+    if (st == TT_OK && cudaEventCreateWithFlags(&evs[n], cudaEventDisableTiming) != cudaSuccess) st = TT_ERR_CUDA;
+    if (st != TT_OK) {
+        cleanup();
+        return fail(st, "batched captured step: stream or event creation failed");
+    }
+    const unsigned long long before = t_launches;
+    cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(evs[n], origin);
+    for (int i = 0; i < n && e == cudaSuccess && st == TT_OK; ++i) {
+        e = cudaStreamWaitEvent(caps[i], evs[n], 0);  // the branch joins the capture
+        if (e != cudaSuccess) break;
+        saved[i] = hs[i]->stream;
+        hs[i]->stream = caps[i];
+        st = graph_step_body(hs[i]);
+        hs[i]->stream = saved[i];
+        saved[i] = nullptr;
+        if (st == TT_OK) e = cudaEventRecord(evs[i], caps[i]);
+        if (st == TT_OK && e == cudaSuccess) e = cudaStreamWaitEvent(origin, evs[i], 0);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(origin, &graph);
+    if (e == cudaSuccess) e = ee;
+    *launches = (unsigned)(t_launches - before);
+    g_launches.fetch_sub(*launches);
+    t_launches -= *launches;
+    if (st == TT_OK && e == cudaSuccess) {
+        e = cudaGraphInstantiate(out, graph, 0);
+        if (e != cudaSuccess) *out = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cleanup();
+    if (st < 0) return st;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(TT_ERR_CUDA, std::string("batched captured step: ") + cudaGetErrorString(e));
+    }
+    return TT_OK;
+}
+
+// nsteps replays of a batch graph on `origin`, ordered after every handle's
+// earlier work and before its later work (events on the handles' streams).
+tt_status graph_batch_launch(tt_handle* hs, int n, cudaGraphExec_t exec, unsigned launches, cudaStream_t origin,
+                             cudaEvent_t* evs, int nsteps) {
+    for (int i = 0; i < n; ++i) {
+        tt_ctx* h = hs[i];
+        TT_TRY(graph_start(h));
+        if (!h->ranks_stale) {  // the host's state: the size blocks start from its ranks
+            int init[2] = {h->r[1], h->r[2]};
+            TT_CUDA_TRY(cudaMemcpyAsync(h->dyn + DYN_R1, init, 2 * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+            TT_CUDA_TRY(cudaStreamSynchronize(h->stream));  // init lives on this frame
+        }
+        TT_CUDA_TRY(cudaEventRecord(evs[i], h->stream));
+        TT_CUDA_TRY(cudaStreamWaitEvent(origin, evs[i], 0));
+    }
+    for (int it = 0; it < nsteps; ++it) {
+        TT_CUDA_TRY(cudaGraphLaunch(exec, origin));
+        note_launch(launches);
+    }
+    TT_CUDA_TRY(cudaEventRecord(evs[n], origin));
+    for (int i = 0; i < n; ++i) {
+        TT_CUDA_TRY(cudaStreamWaitEvent(hs[i]->stream, evs[n], 0));
+        hs[i]->ranks_stale = true;
+    }
+    return TT_OK;
+}
+
 tt_status graph_steps_begin(tt_handle h, int nsteps) {
     TT_TRY(check_handle(h, true));
     AllocScope alloc_scope_(h->alloc_ptr());

@@ -2,7 +2,9 @@
 // together.  Each problem is a full handle (tt_create) on its own CUDA stream;
 // a pool of host threads advances the problems concurrently, so the small
 // per-problem kernels of different problems overlap on the GPU and each
-// problem's rank decisions wait only for its own stream.
+// problem's rank decisions wait only for its own stream.  With captured steps
+// (tt_batch_set_graph) a batch step is one launch of a graph that holds every
+// problem's recorded step as a branch of its own.
 #include <algorithm>
 #include <atomic>
 #include <string>
@@ -19,7 +21,22 @@ struct tt_batch_ctx {
     std::vector<cudaStream_t> streams;
     int threads = 1;
     bool graph = false;  // captured steps (tt_batch_set_graph)
+    // all problems' captured steps as one graph (a branch per problem),
+    // replayed on `origin` and ordered with the problems' streams by events
+    cudaGraphExec_t bexec = nullptr;
+    unsigned blaunches = 0;
+    cudaStream_t origin = nullptr;
+    std::vector<cudaEvent_t> evs;
+    void drop_graph() {
+        if (bexec) cudaGraphExecDestroy(bexec);
+        bexec = nullptr;
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
+        evs.clear();
+        if (origin) cudaStreamDestroy(origin);
+        origin = nullptr;
+    }
     ~tt_batch_ctx() {
+        drop_graph();
         for (tt_handle x : h) tt_destroy(x);
         for (cudaStream_t s : streams) cudaStreamDestroy(s);
     }
@@ -75,15 +92,24 @@ tt_status tt_batch_step(tt_batch b, int nsteps, tt_step_info* infos) {
     }
     const int n = (int)b->h.size();
     if (b->graph && nsteps > 0) {
-        // every problem's replays in flight from this thread, then one wait each
-        for (int i = 0; i < n; ++i) {
-            tt_status st = graph_steps_begin(b->h[i], nsteps);
-            if (st < 0) {
-                std::string msg = std::string("problem ") + std::to_string(i) + ": " + tt_last_error();
-                set_error(msg);
-                return st;
+        // one graph launch per batch step (every problem a branch of it), then
+        // one wait per problem
+        if (!b->bexec) {
+            TT_TRY(graph_batch_build(b->h.data(), n, &b->bexec, &b->blaunches));
+            if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) {
+                b->drop_graph();
+                set_error("tt_batch_step: stream creation failed");
+                return TT_ERR_CUDA;
             }
+            b->evs.assign(n + 1, nullptr);
+            for (auto& e : b->evs)
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                    b->drop_graph();
+                    set_error("tt_batch_step: event creation failed");
+                    return TT_ERR_CUDA;
+                }
         }
+        TT_TRY(graph_batch_launch(b->h.data(), n, b->bexec, b->blaunches, b->origin, b->evs.data(), nsteps));
         tt_status result = TT_OK;
         for (int i = 0; i < n; ++i) {
             tt_status st = graph_steps_end(b->h[i], infos ? &infos[i] : nullptr);
@@ -170,6 +196,7 @@ tt_status tt_batch_set_graph(tt_batch b, int enable) {
     } else {
         for (tt_handle h : b->h) TT_TRY(tt_set_graph(h, 0));
     }
+    if (!enable) b->drop_graph();
     b->graph = enable != 0;
     return TT_OK;
 }

@@ -232,6 +232,11 @@ void truncation_decision_dyn(cudaStream_t s, const double* lamK, const int* kB_d
 // waits for them and reports like tt_sn_step (info: the last step's).
 tt_status graph_steps_begin(tt_handle h, int nsteps);
 tt_status graph_steps_end(tt_handle h, tt_step_info* info);
+// The captured steps of many handles as one graph (a branch per handle) and
+// its replays: evs holds n + 1 events (the handles' and the origin's).
+tt_status graph_batch_build(tt_handle* hs, int n, cudaGraphExec_t* out, unsigned* launches);
+tt_status graph_batch_launch(tt_handle* hs, int n, cudaGraphExec_t exec, unsigned launches, cudaStream_t origin,
+                             cudaEvent_t* evs, int nsteps);
 
 // Shared-memory limits of the factorisation kernels set ahead of a capture,
 // and the control block a capture's factorisations use.
