@@ -242,10 +242,14 @@ __device__ __forceinline__ void axis_terms(const double (&co)[3][2][3], int a, d
 }
 
 // y[i][j] = X_i . thbar_j for the 1 + 2 ndim transport terms j (the grown
-// quadrature vector's blocks): one warp per cell, lanes over the columns.
+// quadrature vector's blocks): one lane per cell, each lane running over its
+// row (consecutive columns share L1 sectors) against the block-uniform thbar.
 // Because every transport term is linear in X, the quadrature of cell i's
 // grown row is a combination of these dots at i and its neighbours, which
-// the source stage then forms with a few scalar operations per cell.
+// the source stage then forms with a few scalar operations per cell.  A lane
+// per cell costs nterms FMAs per element and no reduction; a warp per cell
+// spent as many FP64 instructions again on the shuffle sums, and on GB300 the
+// FP64 issue rate, not HBM, bounds this kernel.
 __global__ void __launch_bounds__(256)
 term_dots_kernel(long nrows, int nterms, int r1, const double* __restrict__ X, long ldx,
                  const double* __restrict__ thbar, double* __restrict__ y, const int* dd) {
@@ -253,24 +257,18 @@ term_dots_kernel(long nrows, int nterms, int r1, const double* __restrict__ X, l
         r1 = dd[DYN_R1];
         ldx = r1;
     }
-    const int lane = threadIdx.x & 31;
-    const long warps = (long)gridDim.x * (blockDim.x >> 5);
-    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < nrows; i += warps) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nrows; i += (long)gridDim.x * blockDim.x) {
         double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int col = lane; col < r1; col += 32) {
-            const double x = X[i * ldx + col];
+        const double* xi = X + i * ldx;
+        for (int col = 0; col < r1; ++col) {
+            const double x = xi[col];
 #pragma unroll
             for (int j = 0; j < 7; ++j)
-                if (j < nterms) acc[j] += x * thbar[j * r1 + col];
+                if (j < nterms) acc[j] = fma(x, thbar[j * r1 + col], acc[j]);
         }
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            if (j >= nterms) break;
-            double v = acc[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) y[i * nterms + j] = v;
-        }
+        for (int j = 0; j < 7; ++j)
+            if (j < nterms) y[i * nterms + j] = acc[j];
     }
 }
 
@@ -342,8 +340,22 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
             cell_neighbours(g, i, nb);
             double co[3][2][3];
             if (GEN) stencil_coefs(f, g.ndim, i, co);
-            double fa[3];
-            for (int a = 0; a < g.ndim; ++a) fa[a] = -sc * nu[a];
+            // term (a, t) = -s nu_a (its stencil): the factor is folded into
+            // the stencil so that each output costs as few FP64 operations as
+            // possible (GB300's FP64 issue rate bounds this pass): upwinding
+            // writes fma(sn, xm, -sn x0) and fma(-sn, xp, sn x0), the other
+            // fluxes a two-FMA chain on the scaled coefficients
+            double sn[3] = {0.0, 0.0, 0.0};
+            double cf[3][2][3];
+            for (int a = 0; a < g.ndim; ++a) {
+                sn[a] = sc * nu[a];
+                if (GEN)
+                    for (int t = 0; t < 2; ++t) {
+                        cf[a][t][0] = -sn[a] * co[a][t][0];
+                        cf[a][t][1] = -sn[a] * co[a][t][1];
+                        cf[a][t][2] = sn[a] * co[a][t][2];
+                    }
+            }
             double* out = Xg + i * ldg;
             for (int col = lane; col < r1; col += 32) {
                 const double x0 = X[i * ldx + col];
@@ -352,10 +364,14 @@ transport_source_kernel(Grid g, Fields f, int transport, int source, int r1,
                     for (int a = 0; a < g.ndim; ++a) {
                         const double xm = nb[a][0] >= 0 ? X[nb[a][0] * ldx + col] : 0.0;
                         const double xp = nb[a][1] >= 0 ? X[nb[a][1] * ldx + col] : 0.0;
-                        double t1, t2;
-                        axis_terms<GEN>(co, a, x0, xm, xp, t1, t2);
-                        out[(1 + 2 * a) * r1 + col] = fa[a] * t1;
-                        out[(2 + 2 * a) * r1 + col] = fa[a] * t2;
+                        if (GEN) {
+                            out[(1 + 2 * a) * r1 + col] = fma(cf[a][0][0], x0, fma(cf[a][0][1], xp, cf[a][0][2] * xm));
+                            out[(2 + 2 * a) * r1 + col] = fma(cf[a][1][0], x0, fma(cf[a][1][1], xp, cf[a][1][2] * xm));
+                        } else {
+                            const double q = sn[a] * x0;
+                            out[(1 + 2 * a) * r1 + col] = fma(sn[a], xm, -q);
+                            out[(2 + 2 * a) * r1 + col] = fma(-sn[a], xp, q);
+                        }
                     }
                 }
             }
@@ -505,18 +521,19 @@ energy_rows_kernel(long nc, int r, const double* __restrict__ X, long ldx,
         r = dd[DYN_R1];
         ldx = r;
     }
-    const int lane = threadIdx.x & 31;
-    const long warps = (long)gridDim.x * (blockDim.x >> 5);
-    for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < nc; i += warps) {
-        double dot = 0.0;
-        for (int col = lane; col < r; col += 32) dot += X[i * ldx + col] * thbar[col];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) {
-            const double E = dot / c;
-            if (E_out) E_out[i] = E;
-            if (update_T) T[i] = T[i] + (E_star[i] - E) / cv[i];
+    // one lane per cell (see term_dots_kernel)
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nc; i += (long)gridDim.x * blockDim.x) {
+        const double* xi = X + i * ldx;
+        double d0 = 0.0, d1 = 0.0;
+        int col = 0;
+        for (; col + 1 < r; col += 2) {
+            d0 = fma(xi[col], thbar[col], d0);
+            d1 = fma(xi[col + 1], thbar[col + 1], d1);
         }
+        if (col < r) d0 = fma(xi[col], thbar[col], d0);
+        const double E = (d0 + d1) / c;
+        if (E_out) E_out[i] = E;
+        if (update_T) T[i] = T[i] + (E_star[i] - E) / cv[i];
     }
 }
 
@@ -912,7 +929,7 @@ void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool 
         // a shard's stencil also reads the dots of its two halo layers (rows
         // nc .. nc + 2 stride - 1, BC_HALO on axis 0)
         const long ny = g.nc + (transport && g.bc[0] == BC_HALO ? 2 * (g.nc / g.n[0]) : 0);
-        const int yb = (int)std::max<long>(1, std::min<long>((ny + 7) / 8, 152L * 64));
+        const int yb = (int)std::max<long>(1, std::min<long>((ny + 255) / 256, 152L * 8));
         note_launch();
         term_dots_kernel<<<yb, 256, 0, s>>>(ny, nterms, r1, X, ldx, thbar, ydots, dd);
     }
@@ -933,7 +950,7 @@ void transport_source_rows(cudaStream_t s, const Grid& g, const Fields& f, bool 
 void energy_rows(cudaStream_t s, long nc, int r, const double* X, long ldx, const double* thbar,
                  double c, double* E_out, const double* E_star, const double* cv, double* T,
                  bool update_T, const int* dd) {
-    const int blocks = (int)std::max<long>(1, std::min<long>((nc + 7) / 8, 152L * 64));
+    const int blocks = (int)std::max<long>(1, std::min<long>((nc + 255) / 256, 152L * 8));
     note_launch();
     energy_rows_kernel<<<blocks, 256, 0, s>>>(nc, r, X, ldx, thbar, c, E_out, E_star, cv, T,
                                               update_T ? 1 : 0, dd);
