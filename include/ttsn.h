@@ -611,7 +611,7 @@ tt_status tt_set_max_sweeps(tt_handle h, int max_sweeps);
  * tt_gram_mixed: G = A^T A (as tt_gram) on the BF16 tensor cores (tcgen05).
  * Each column of A is scaled by a power of two and cut into seven signed
  * 7-bit digits (exact in BF16); digit products are exact in FP32, summed
- * exactly over 128-row blocks in tensor memory, and accumulated in
+ * exactly over 512-row blocks in tensor memory, and accumulated in
  * double-float (about 48 bits); products of digit levels s + t >= 7 are
  * dropped.  Error about 2^-48 max|A_j| max|A_k| per row term.  Device scratch
  * (row splits x n x n doubles and the digit planes, 14 bytes per element of

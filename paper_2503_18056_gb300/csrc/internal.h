@@ -134,7 +134,7 @@ tt_status bench_bf16_mma(cudaStream_t s, double* tflops);
 size_t slgram_scratch_doubles(int m, int n);
 tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
                  DevBuf& scratch, int* status_dev = nullptr);
-// The left Gram on tcgen05 tensor cores (7-digit split, exact 128-row level
+// The left Gram on tcgen05 tensor cores (7-digit split, exact 512-row level
 // sums, TMEM accumulators): what slgram runs.  status_dev (nullable) latches
 // DEV_TIMEOUT if a bounded wait ran out.
 size_t tcgram_scratch_doubles(int m, int n);

@@ -10,9 +10,9 @@
 //   a = 2^e sum_s d_s 128^-(s+1),
 // every digit exact in BF16 and every digit product (|d_s d_t| <= 2^12)
 // exact in FP32.  Products of the same level w = s + t share the weight
-// 128^-(w+2); summed over a block of 128 contraction indices they stay below
-// 128 * 7 * 2^12 < 2^22, so the tensor cores' FP32 block sums are exact
-// integers.  Each block sum is scaled by 128^-w (exact) and added into a
+// 128^-(w+2); level w has at most 7 pairs, so summed over a block of 512
+// contraction indices they stay below 512 * 7 * 2^12 < 2^24 and the tensor
+// cores' FP32 block sums are exact integers.  Each block sum is scaled by 128^-w (exact) and added into a
 // double-float accumulator (hi + lo in FP32, TwoSum + renormalisation: about
 // 48 bits).  Levels w >= 7 are dropped: 28 BF16 products per term, about
 // 2^-48 of max|a| max|b| per term against 2^-53 for FP64.  No FP64 arithmetic
@@ -20,9 +20,10 @@
 //
 // Both kernels keep seven per-level FP32 accumulators of a 128 x 64 output
 // tile in tensor memory (448 of 512 columns), issue tcgen05.mma (kind::f16,
-// BF16 x BF16 -> FP32, M = 128, N = 64, K = 16) from one thread with both
-// operands K-major in shared memory (64-byte swizzle), and drain the
-// accumulators with tcgen05.ld every 128 contraction indices.
+// BF16 x BF16 -> FP32, M = 128, K = 16, N = 64 per B digit, up to four B
+// digits per MMA) from one thread with both operands K-major in shared memory
+// (64-byte swizzle), and drain the accumulators with tcgen05.ld every 512
+// contraction indices.
 #include <cuda.h>
 
 #include <algorithm>
@@ -132,27 +133,27 @@ __global__ void __launch_bounds__(256) bf16_mma_peak_kernel(float* out, unsigned
 // point and cut into S7 = 7 balanced base-128 digits (d_0 in [0, 64],
 // d_1..d_6 in [-64, 63]), a = 2^e sum_s d_s 128^-(s+1); every digit is exact
 // in BF16 and |d_s d_t| <= 2^12.  The products of level w = s + t (weight
-// 128^-(w+2)) summed over a 128-row block stay below 128 * 7 * 2^12 < 2^22,
+// 128^-(w+2)) summed over a 512-row block stay below 512 * 7 * 2^12 < 2^24,
 // so the tensor core's FP32 sums of them are exact integers; levels w >= 7
 // are dropped (about 2^-48 of the column scales per term, as the 8-bit form).
-// Exact sums over 128 rows instead of 32 cut the double-float drain work
-// four-fold; that drain runs on the FP32 pipe and is what bounds the
-// warp-level (mma.sync) kernel above.
+// The accumulators are drained (read, scaled, added in double-float on the
+// FP32 pipe) once per block, while the MMAs wait: 512-row blocks spend a
+// quarter of the drain time of 128-row ones.
 //
 // Tile.  A CTA owns a 128 (columns j) x 64 (columns k) tile of G and a range
 // of rows.  Seven FP32 accumulators (one per level, 128 lanes x 64 columns
-// each, 448 of the 512 TMEM columns) receive, per 32-row stage, 28 digit-pair
-// products x 2 K-steps of tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-// M = 128, N = 64, K = 16) issued by one thread with operands described in
-// shared memory (K-major, 64-byte swizzle).  A TMA producer thread streams
+// each, 448 of the 512 TMEM columns) receive, per 32-row stage, the 28
+// digit-pair products x 2 K-steps as 20 tcgen05.mma (kind::f16, BF16 x BF16
+// -> FP32, M = 128, N = 64 .. 256, K = 16; tc_stage_mmas) issued by one thread
+// with operands described in shared memory (K-major, 64-byte swizzle).  A TMA producer thread streams
 // the stages (all 7 digit planes of the tile's 128 + 64 columns in two
 // 3-D boxes per stage, double-buffered, mbarrier-tracked).  After every
-// 128-row block eight drain warps read the accumulators (tcgen05.ld, one TMEM
+// 512-row block eight drain warps read the accumulators (tcgen05.ld, one TMEM
 // lane and half the columns per thread), scale level w by 128^-w and add into double-float
 // accumulators.  Every wait is bounded and latches DEV_TIMEOUT.
 constexpr int TC_S = 7;
 constexpr int TC_M = 128, TC_N = 64, TC_K = 32;
-constexpr int TC_BLK = 4;  // stages per exact block (128 rows)
+constexpr int TC_BLK = 16;  // stages per exact block (512 rows)
 constexpr int TC_STAGES = 2;
 constexpr int TC_A_BYTES = TC_S * TC_M * TC_K * 2;  // 57344
 constexpr int TC_B_BYTES = TC_S * TC_N * TC_K * 2;  // 28672
@@ -196,12 +197,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity, int* stat
     if (status) atomicOr(status, DEV_TIMEOUT);
     return false;
 }
-__device__ __forceinline__ void tma_load_3d(unsigned dst, const void* map, int c0, int c1, int c2,
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const void* map, int c0, int c1, int c2, int c3,
                                             unsigned mbar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
         : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -223,16 +224,42 @@ __device__ __forceinline__ unsigned long long tc_sdesc(unsigned addr) {
     return d;
 }
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 64, M = 128.
-constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_N >> 3) << 17) |
-                              ((unsigned)(TC_M >> 4) << 24);
+// K-major, M = 128, N = nn (a multiple of 64 up to 256).
+__device__ __forceinline__ unsigned tc_idesc(int nn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(nn >> 3) << 17) | ((unsigned)(TC_M >> 4) << 24);
+}
 __device__ __forceinline__ void tc_mma(unsigned d_tmem, unsigned long long a, unsigned long long b,
-                                       unsigned accumulate) {
+                                       unsigned idesc, unsigned accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+// The digit-pair products of one 32-deep stage.  The seven B digit tiles sit
+// back to back in shared memory (64 rows each, 8-row groups 512 bytes apart),
+// so B digits t0 .. t0 + c - 1 form one K-major operand of N = 64 c rows; and
+// the accumulator of level w sits at TMEM column 64 w, so the products of A
+// digit s with B digits t0 .. t0 + c - 1 (levels s + t0 ..) land in one
+// contiguous column range.  Per A digit and K-step one MMA (two where more
+// than four B digits remain: N <= 256) does what 7 - s MMAs of N = 64 did:
+// 10 MMAs per K-step instead of 28, each A tile read once per MMA, so the
+// operand bytes per step fall from 168 KB to 96 KB.  The first stage of a
+// block overwrites every level (s = 0 covers levels 0 .. 6).
+__device__ __forceinline__ void tc_stage_mmas(unsigned tmem, unsigned aB, unsigned bB, bool first) {
+#pragma unroll 1
+    for (int s = 0; s < TC_S; ++s) {
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const unsigned long long ad = tc_sdesc(aB + (unsigned)(s * TC_M * TC_K * 2 + kk * 32));
+            const unsigned acc = (first && s == 0 && kk == 0) ? 0u : 1u;
+            for (int t0 = 0; t0 < TC_S - s; t0 += 4) {
+                const int c = min(4, TC_S - s - t0);
+                const unsigned long long bd = tc_sdesc(bB + (unsigned)(t0 * TC_N * TC_K * 2 + kk * 32));
+                tc_mma(tmem + (unsigned)((s + t0) * TC_N), ad, bd, tc_idesc(c * TC_N), acc);
+            }
+        }
+    }
 }
 __device__ __forceinline__ void tc_commit(unsigned mbar) {
     asm volatile(
@@ -300,9 +327,12 @@ __global__ void max_to_exp7_kernel(int n, const unsigned long long* cmax, int* e
         e[j] = exp_bound(__longlong_as_double((long long)cmax[j])) + 1;
 }
 
-// Digit planes D[s][j][i] (n x mp, i contiguous) of the 7-digit split, rows
-// i >= m zero; a CTA slices a 32 (i) x 64 (j) block through a shared-memory
-// transpose (writes of 64-byte runs along i).
+// Digit planes of the 7-digit split, stage-major: D[i / 32][s][j][i % 32]
+// (every 32-row stage of all n columns and digits one contiguous 14 n * 32
+// bytes; rows i >= m zero), so that a stage's TMA box of 7 x 128 column runs
+// of 64 bytes reads seven 8 KB spans of one region instead of 896 runs a
+// plane (2 mp bytes) apart.  A CTA slices a 32 (i) x 64 (j) block through a
+// shared-memory transpose and writes, per digit, 64 contiguous 64-byte runs.
 __global__ void __launch_bounds__(256)
 slice7_cols_kernel(int m, int n, long mp, const double* __restrict__ A, long lda,
                    const int* __restrict__ ecol, unsigned short* __restrict__ D) {
@@ -327,7 +357,7 @@ slice7_cols_kernel(int m, int n, long mp, const double* __restrict__ A, long lda
             const int gj = j0 + j;
             if (gj >= n) continue;
             const unsigned v = (unsigned)t[s][j][2 * w] | ((unsigned)t[s][j][2 * w + 1] << 16);
-            unsigned* dst = reinterpret_cast<unsigned*>(D + ((long)s * n + gj) * mp + i0) + w;
+            unsigned* dst = reinterpret_cast<unsigned*>(D + (((i0 / 32) * TC_S + s) * n + gj) * 32) + w;
             *dst = v;
         }
     }
@@ -424,9 +454,9 @@ tcgram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 const unsigned full = smem_u32(&bars[st]);
                 mbar_expect_tx(full, (unsigned)TC_STAGE_BYTES);
                 const unsigned dA = sb + (unsigned)(st * TC_STAGE_BYTES);
-                const int kx = (int)(kbeg + (long)it * TC_K);
-                tma_load_3d(dA, &tmA, kx, j0, 0, full);
-                tma_load_3d(dA + TC_A_BYTES, &tmB, kx, kc0, 0, full);
+                const int kst = (int)((kbeg + (long)it * TC_K) / TC_K);  // 32-row stage index
+                tma_load_4d(dA, &tmA, 0, j0, 0, kst, full);
+                tma_load_4d(dA + TC_A_BYTES, &tmB, 0, kc0, 0, kst, full);
                 flags[1] = it + 1;
             }
         }
@@ -446,23 +476,7 @@ tcgram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 tc_fence_after();
                 const unsigned aB = sb + (unsigned)(st * TC_STAGE_BYTES);
                 const unsigned bB = aB + TC_A_BYTES;
-                // A digit s outermost: consecutive MMAs share their A operand
-#pragma unroll 1
-                for (int s = 0; s < TC_S; ++s) {
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const unsigned long long ad =
-                            tc_sdesc(aB + (unsigned)(s * TC_M * TC_K * 2 + kk * 32));
-#pragma unroll 1
-                        for (int t = 0; t < TC_S - s; ++t) {
-                            const unsigned long long bd =
-                                tc_sdesc(bB + (unsigned)(t * TC_N * TC_K * 2 + kk * 32));
-                            // the first product of each level in a block overwrites
-                            const unsigned acc = (first && s == 0 && kk == 0) ? 0u : 1u;
-                            tc_mma(tmem + (unsigned)((s + t) * TC_N), ad, bd, acc);
-                        }
-                    }
-                }
+                tc_stage_mmas(tmem, aB, bB, first);
                 tc_commit(smem_u32(&bars[2 + st]));  // the stage is free once these MMAs finish
                 flags[2] = it + 1;
                 if ((it % TC_BLK) == TC_BLK - 1 || it == nslices - 1) tc_commit(smem_u32(&bars[4]));
@@ -535,8 +549,8 @@ tcgram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 // the seven 128 x 32 digit tiles of A, per (column block, stage) the seven
 // 64 x 32 tiles of B, each in the MMA's 64-byte swizzled K-major layout
 // (16-byte chunk index XOR (row / 2) mod 4) -- so one thread brings a stage in
-// with two bulk copies, one thread issues its 56 MMAs, and eight warps drain
-// the accumulators every fourth stage.  A persistent CTA walks (row block,
+// with two bulk copies, one thread issues its 20 MMAs (tc_stage_mmas), and eight warps drain
+// the accumulators every sixteenth stage.  A persistent CTA walks (row block,
 // column block) items.
 constexpr int TU_DRAIN_WARPS = 8;
 constexpr int TU_THREADS = 32 * (2 + TU_DRAIN_WARPS);  // warp 0 copies, warp 1 TMEM + MMA, 2-9 drain
@@ -705,21 +719,7 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
                     tc_fence_after();
                     const unsigned aB = sb + (unsigned)(st * TC_STAGE_BYTES);
                     const unsigned bB = aB + TC_A_BYTES;
-#pragma unroll 1
-                    for (int s = 0; s < TC_S; ++s) {
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const unsigned long long ad =
-                                tc_sdesc(aB + (unsigned)(s * TC_M * TC_K * 2 + kk * 32));
-#pragma unroll 1
-                            for (int t = 0; t < TC_S - s; ++t) {
-                                const unsigned long long bd =
-                                    tc_sdesc(bB + (unsigned)(t * TC_N * TC_K * 2 + kk * 32));
-                                const unsigned acc = (first && s == 0 && kk == 0) ? 0u : 1u;
-                                tc_mma(tmem + (unsigned)((s + t) * TC_N), ad, bd, acc);
-                            }
-                        }
-                    }
+                    tc_stage_mmas(tmem, aB, bB, first);
                     tc_commit(smem_u32(&bars[2 + st]));
                     if ((it % TC_BLK) == TC_BLK - 1 || it == nst - 1) {
                         tc_commit(smem_u32(&bars[4]));
@@ -873,14 +873,16 @@ tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double
     }
     CUtensorMap mapA, mapB;
     {
-        const cuuint64_t gdim[3] = {(cuuint64_t)mp, (cuuint64_t)n, (cuuint64_t)TC_S};
-        const cuuint64_t gstr[2] = {(cuuint64_t)mp * 2, (cuuint64_t)n * (cuuint64_t)mp * 2};
-        const cuuint32_t boxA[3] = {TC_K, TC_M, TC_S}, boxB[3] = {TC_K, TC_N, TC_S};
-        const cuuint32_t est[3] = {1, 1, 1};
-        CUresult r1 = enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes, gdim, gstr, boxA, est,
+        // (row in stage, column, digit, stage); strides 64 B, 64 n B, 448 n B
+        const cuuint64_t gdim[4] = {(cuuint64_t)TC_K, (cuuint64_t)n, (cuuint64_t)TC_S, (cuuint64_t)(mp / TC_K)};
+        const cuuint64_t gstr[3] = {(cuuint64_t)TC_K * 2, (cuuint64_t)n * TC_K * 2,
+                                    (cuuint64_t)n * TC_K * 2 * TC_S};
+        const cuuint32_t boxA[4] = {TC_K, TC_M, TC_S, 1}, boxB[4] = {TC_K, TC_N, TC_S, 1};
+        const cuuint32_t est[4] = {1, 1, 1, 1};
+        CUresult r1 = enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, planes, gdim, gstr, boxA, est,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        CUresult r2 = enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes, gdim, gstr, boxB, est,
+        CUresult r2 = enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, planes, gdim, gstr, boxB, est,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {

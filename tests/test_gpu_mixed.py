@@ -53,6 +53,62 @@ def test_gemm_nt_mixed_within_split_bound(ttsn, M, N, K):
     assert np.all(np.abs(C - ref) <= bound + 1e-16 * np.abs(ref))
 
 
+# Worst-case level sums.  A value whose seven balanced base-128 digits are
+# all 63 (the largest the split produces below the leading one) makes every
+# digit product of a level w equal 63^2, so a block of R contraction indices
+# sums (w + 1) 63^2 R at level w: 14.2M at w = 6 and 10.2M at w = 4 for
+# R = 512, above 2^23 and below 2^24.  The tensor cores must add these
+# integers exactly; a lost unit at level w <= 4 moves a term by >= 2^-38 of
+# its size, far above the double-float drain's rounding (the tolerance
+# below).  The expected value is the truncated scheme's own exact result:
+# sum over levels w <= 6 of (w + 1) 63^2 128^-(w+2), times 2^(e_j + e_k),
+# computed in rationals.
+_F63 = sum(63 * 128 ** (6 - s) for s in range(7))  # digits 63, 63, ..., 63
+
+
+def _digit63_values(count, seed):
+    """Values +-F 2^(k - 47) (F = _F63, so |v| in [1, 2) 2^k) with their split exponents e = k + 2."""
+    rng = np.random.default_rng(seed)
+    k = rng.integers(-6, 7, count)
+    sign = rng.choice([-1.0, 1.0], count)
+    v = sign * np.ldexp(float(_F63), k - 47)
+    assert np.all(np.abs(v) * 2.0 ** -(k + 2) < 0.5) and np.all(np.abs(v) * 2.0 ** -(k + 2) >= 0.25)
+    return v, sign, k + 2
+
+
+def _trunc_products(sign_a, e_a, sign_b, e_b):
+    from fractions import Fraction
+
+    unit = sum(Fraction((w + 1) * 63 * 63, 128 ** (w + 2)) for w in range(7))
+    out = np.empty((len(sign_a), len(sign_b)))
+    for i in range(len(sign_a)):
+        for j in range(len(sign_b)):
+            out[i, j] = float(int(sign_a[i] * sign_b[j]) * unit * Fraction(2) ** int(e_a[i] + e_b[j]))
+    return out
+
+
+def test_gram_mixed_exact_block_sums_at_the_digit_bound(ttsn):
+    m, n = 512 * 8 + 96, 70  # eight full 512-row blocks and a ragged one; two column tiles
+    v, sign, e = _digit63_values(n, 11)
+    A = np.tile(v, (m, 1))
+    G = ttsn.gram_mixed(A).cpu().numpy()
+    ref = m * _trunc_products(sign, e, sign, e)
+    assert np.all(np.abs(G - ref) <= 2.0 ** -44 * np.abs(ref))
+    exact = m * np.outer(v, v)  # the untruncated product: the split's stated bound
+    assert np.all(np.abs(G - exact) <= 8 * U * m * np.outer(np.abs(v), np.abs(v)))
+
+
+def test_gemm_nt_mixed_exact_block_sums_at_the_digit_bound(ttsn):
+    M, N, K = 300, 130, 512 * 2 + 40
+    va, sa, ea = _digit63_values(M, 12)
+    vb, sb, eb = _digit63_values(N, 13)
+    A = np.tile(va[:, None], (1, K))
+    B = np.tile(vb[:, None], (1, K))
+    C = ttsn.gemm_nt_mixed(A, B).cpu().numpy()
+    ref = K * _trunc_products(sa, ea, sb, eb)
+    assert np.all(np.abs(C - ref) <= 2.0 ** -44 * np.abs(ref))
+
+
 def _fp64_then_mixed(ttsn, p, steps):
     g64 = ttsn.TTSN.from_problem(p)
     ranks = []
