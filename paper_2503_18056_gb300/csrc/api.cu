@@ -224,7 +224,7 @@ struct tt_ctx {
 
     // rounding workspace
     DevBuf GB[TT_MAX_D], lamB[TT_MAX_D], VtB[TT_MAX_D];
-    DevBuf GA, Wc, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd, slscratch;
+    DevBuf GA, Wc, T1, K, lamK, VtK, Vts, PAt, Mupd, tmp[2], partials, bwd, slscratch, erowA;
     int precision = TT_FP64;
     EigWork eig;
     DevBuf small_buf;          // holds d_dbl then d_int
@@ -396,7 +396,7 @@ struct tt_ctx {
             lamB[k].release();
             VtB[k].release();
         }
-        DevBuf* bufs[] = {&slscratch, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
+        DevBuf* bufs[] = {&slscratch, &erowA, &GA, &Wc, &T1, &K, &lamK, &VtK, &Vts, &PAt, &Mupd, &tmp[0], &tmp[1],
                           &partials, &bwd, &f_sigma_a, &f_sigma_s, &f_cv, &f_T, &f_Estar, &f_E,
                           &thbar, &red, &ang_buf, &src_x, &src_th, &src_ph, &src_q,
                           &split_fac, &sp_F, &sp_tmp[0], &sp_tmp[1], &f_fw, &usr_x, &usr_th, &usr_ph,
@@ -932,8 +932,12 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
         TT_TRY(h->GA.ensure((size_t)Rk * Rk, s));
         {
             PhaseScope ps(h, TT_PH_GRAM_LEFT, (double)m * Rk * (Rk + 1.0), 8.0 * ((double)m * Rk + (double)Rk * Rk));
-            if (h->precision == TT_MIXED)
-                TT_TRY(slgram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials, h->d_int + HI_STATUS));
+            if (h->precision == TT_MIXED) {
+                // A's row exponents for the update below come from the same read
+                TT_TRY(h->erowA.ensure((size_t)(m + 1) / 2, s));
+                TT_TRY(slgram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials, h->d_int + HI_STATUS,
+                              reinterpret_cast<int*>(h->erowA.p)));
+            }
             else
                 TT_TRY(gram(s, (int)m, Rk, A, Rk, h->GA.p, Rk, h->partials));
             // a spatial shard holds some rows of the spatial core: its left
@@ -1008,7 +1012,7 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             if (h->precision == TT_MIXED)
                 // A's digit images go to the left Gram's scratch, free until the next bond
                 TT_TRY(slgemm_nt(s, m, rk, Rk, A, Rk, h->PAt.p, Rk, dst[k].p, rk, h->slscratch,
-                                 h->d_int + HI_STATUS, &h->partials));
+                                 h->d_int + HI_STATUS, &h->partials, reinterpret_cast<const int*>(h->erowA.p)));
             else
                 TT_TRY(dgemm(s, false, true, (int)m, rk, Rk, 1.0, A, Rk, h->PAt.p, Rk, 0.0, dst[k].p, rk));
         }
@@ -2391,7 +2395,10 @@ tt_status create_impl(const tt_problem_desc* desc, void* stream, const tt_alloca
         TT_CREATE_TRY(h->tmp[1].ensure((size_t)(cap1 * D.n_theta * R2), s));
         TT_CREATE_TRY(h->thbar.ensure((size_t)(nterms * (cap1 + cap2) + 2), s));
         TT_CREATE_TRY(h->ydots.ensure((size_t)(nc * nterms), s));
-        if (D.precision == TT_MIXED) TT_CREATE_TRY(h->slscratch.ensure((size_t)(nc + R1) / 2 + 2, s));
+        if (D.precision == TT_MIXED) {
+            TT_CREATE_TRY(h->slscratch.ensure((size_t)(nc + R1) / 2 + 2, s));
+            TT_CREATE_TRY(h->erowA.ensure((size_t)(nc + 1) / 2, s));
+        }
     }
     init_isotropic(s, nc, (D.Tr0 ? D.Tr0 : D.T0) + cell0, D.c, D.a_r, h->core[0].p);
     fill(s, h->core[1].p, D.n_theta, 1.0);

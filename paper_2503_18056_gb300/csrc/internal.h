@@ -132,20 +132,23 @@ tt_status bench_bf16_mma(cudaStream_t s, double* tflops);
 // Mixed-precision (exact BF16 digit products, double-float accumulation) left
 // Gram G = A^T A and product C = A B^T (slice.cu).  scratch grows as needed.
 size_t slgram_scratch_doubles(int m, int n);
+// erow_out (nullable, m ints): also the row exponents of A that slgemm_nt
+// takes as erowA for the same A, from the same read of A.
 tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
-                 DevBuf& scratch, int* status_dev = nullptr);
+                 DevBuf& scratch, int* status_dev = nullptr, int* erow_out = nullptr);
 // The left Gram on tcgen05 tensor cores (7-digit split, exact 512-row level
 // sums, TMEM accumulators): what slgram runs.  status_dev (nullable) latches
 // DEV_TIMEOUT if a bounded wait ran out.
 size_t tcgram_scratch_doubles(int m, int n);
 tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
-                 DevBuf& scratch, int* status_dev);
+                 DevBuf& scratch, int* status_dev, int* erow_out = nullptr);
 // planes (nullable): where A's digit images go (14 bytes per element of A,
 // padded to 128 rows x 32 columns), e.g. a buffer that is free at the time;
-// null puts them in scratch.
+// null puts them in scratch.  erowA (nullable): A's row exponents from
+// slgram's erow_out for this A (null: computed here).
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
                     long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev = nullptr,
-                    DevBuf* planes = nullptr);
+                    DevBuf* planes = nullptr, const int* erowA = nullptr);
 
 // Row scaling: out[i][j] = in[i][j] * f(v[i]) for i < rows, j < cols, where
 // mode 0: v, 1: sqrt(v), 2: 1/sqrt(v), 3: 1/v.  out may alias in.

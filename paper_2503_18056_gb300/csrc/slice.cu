@@ -36,12 +36,6 @@ namespace ttsn {
 namespace {
 
 
-__device__ __forceinline__ unsigned short bf16_bits_of_int(int v) {
-    // |v| <= 255: exact in bf16; take the top 16 bits of the fp32 value
-    const float f = (float)v;
-    return (unsigned short)(__float_as_uint(f) >> 16);
-}
-
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
@@ -78,8 +72,18 @@ __global__ void col_max_kernel(int m, int n, const double* __restrict__ A, long 
     const long rows_per = ((long)m + gridDim.y - 1) / gridDim.y;
     const long r0 = blockIdx.y * rows_per, r1 = min((long)m, r0 + rows_per);
     double mx = 0.0;
-    if (j < n)
-        for (long i = r0 + rlane; i < r1; i += rstride) mx = fmax(mx, fabs(A[i * lda + j]));
+    if (j < n) {
+        long i = r0 + rlane;
+        double m1 = 0.0, m2 = 0.0, m3 = 0.0;  // four loads in flight per thread
+        for (; i + 3 * rstride < r1; i += 4 * rstride) {
+            mx = fmax(mx, fabs(A[i * lda + j]));
+            m1 = fmax(m1, fabs(A[(i + rstride) * lda + j]));
+            m2 = fmax(m2, fabs(A[(i + 2 * rstride) * lda + j]));
+            m3 = fmax(m3, fabs(A[(i + 3 * rstride) * lda + j]));
+        }
+        for (; i < r1; i += rstride) mx = fmax(mx, fabs(A[i * lda + j]));
+        mx = fmax(fmax(mx, m1), fmax(m2, m3));
+    }
     if (j < n && mx > 0.0) atomicMax(cmax + j, (unsigned long long)__double_as_longlong(mx));
 }
 
@@ -87,11 +91,70 @@ __global__ void row_exp_kernel(long m, int n, const double* __restrict__ A, long
     const int lane = threadIdx.x & 31;
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += warps) {
-        double mx = 0.0;
-        for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(A[i * lda + j]));
+        double mx = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;  // four loads in flight per lane
+        int j = lane;
+        for (; j + 96 < n; j += 128) {
+            mx = fmax(mx, fabs(A[i * lda + j]));
+            m1 = fmax(m1, fabs(A[i * lda + j + 32]));
+            m2 = fmax(m2, fabs(A[i * lda + j + 64]));
+            m3 = fmax(m3, fabs(A[i * lda + j + 96]));
+        }
+        for (; j < n; j += 32) mx = fmax(mx, fabs(A[i * lda + j]));
+        mx = fmax(fmax(mx, m1), fmax(m2, m3));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) e[i] = exp_bound(mx);
+    }
+}
+
+// Column maxima (the Gram's column exponents) and row exponents (the
+// update's, for the same matrix) in one read of A, for n <= 1024.  Warps
+// sweep whole rows (grid-stride, so the GPU reads one contiguous window of
+// A): a lane loads its columns l + 32 k of the row all at once (up to 32
+// loads in flight), the row maximum is a warp reduction whose exponent bound
+// lane 0 writes, and each warp folds the row into its own column-maximum
+// slice in shared memory (no conflicts, no registers held across rows); the
+// block combines its eight slices at the end with one atomicMax per column.
+constexpr int CRM_MAXN = 1024;
+__global__ void __launch_bounds__(256)
+col_row_max_kernel(long m, int n, const double* __restrict__ A, long lda, unsigned long long* cmax,
+                   int* erow) {
+    extern __shared__ double crm_part[];  // [8][n]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nk = (n + 31) >> 5;
+    double* mine = crm_part + (long)warp * n;
+    for (int j = lane; j < n; j += 32) mine[j] = 0.0;
+    __syncwarp();
+    const long nw = (long)gridDim.x * 8;
+    for (long i = (long)blockIdx.x * 8 + warp; i < m; i += nw) {
+        const double* row = A + i * lda;
+        // unconditional loads (lanes past the last column re-read it, which
+        // leaves the row maximum unchanged): a select on a loaded value would
+        // wait for the load and serialise them
+        double v[CRM_MAXN / 32];
+#pragma unroll
+        for (int k = 0; k < CRM_MAXN / 32; ++k)
+            if (k < nk) v[k] = row[min(k * 32 + lane, n - 1)];
+        double rm = 0.0;
+#pragma unroll
+        for (int k = 0; k < CRM_MAXN / 32; ++k) {
+            if (k < nk) {
+                const double a = fabs(v[k]);
+                const int j = k * 32 + lane;
+                if (j < n) mine[j] = fmax(mine[j], a);
+                rm = fmax(rm, a);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+        if (lane == 0) erow[i] = exp_bound(rm);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double mx = crm_part[j];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) mx = fmax(mx, crm_part[(long)w * n + j]);
+        if (mx > 0.0) atomicMax(cmax + j, (unsigned long long)__double_as_longlong(mx));
     }
 }
 
@@ -284,6 +347,12 @@ __device__ __forceinline__ void tc_wait_ld() {
 // Seven balanced base-128 digits of v 2^-e (|v| 2^-e < 1/2): |v| 2^(49-e) =
 // M 2^(ev - e - 3) is rounded to the integer F (< 2^48), written as
 // F = sum_s d_s 128^(6-s), digits carrying the sign of v, as BF16 bit patterns.
+// Balanced digits without a carry chain: adding 64 at every lower digit
+// position, F + 64 (1 + 128 + ... + 128^5), makes the plain base-128 digits
+// d_s + 64 (s = 1 .. 6) and leaves d_0 on top.  A digit becomes a float
+// without an int-to-float conversion: the bits 0x4B000000 | u are the float
+// 2^23 + u, so subtracting 2^23 (+ 64) leaves u (- 64) exactly; its top 16 bits
+// are the BF16 pattern (at most 7 significant bits).
 __device__ __forceinline__ void digits7(double v, int e, unsigned short (&out)[TC_S]) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((bits >> 52) & 0x7FF);
@@ -296,28 +365,14 @@ __device__ __forceinline__ void digits7(double v, int e, unsigned short (&out)[T
         else if (shift < 55)
             F = (M + (1ull << (shift - 1))) >> shift;
     }
-    const unsigned short sign = (unsigned short)((bits >> 48) & 0x8000u);
-    int d[TC_S];
-#pragma unroll
-    for (int s = TC_S - 1; s >= 1; --s) {
-        int x = (int)(F & 0x7Full);
-        F >>= 7;
-        if (x >= 64) {
-            x -= 128;
-            F += 1;
-        }
-        d[s] = x;
-    }
-    d[0] = (int)F;  // 0 .. 64
+    const unsigned long long Fb = F + 0x20408102040ull;  // + 64 sum_{k<6} 128^k
+    const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
 #pragma unroll
     for (int s = 0; s < TC_S; ++s) {
-        const int x = d[s];
-        if (x == 0) {
-            out[s] = 0;
-        } else {
-            const unsigned short b = bf16_bits_of_int(x < 0 ? -x : x);
-            out[s] = (unsigned short)(b | (x < 0 ? (sign ^ 0x8000u) : sign));
-        }
+        const unsigned u = (unsigned)(Fb >> (7 * (6 - s)));
+        const float f = s == 0 ? __int_as_float((int)(0x4B000000u | u)) - 8388608.0f
+                               : __int_as_float((int)(0x4B000000u | (u & 127u))) - 8388672.0f;
+        out[s] = f == 0.0f ? (unsigned short)0 : (unsigned short)((__float_as_uint(f) ^ sgn) >> 16);
     }
 }
 
@@ -331,34 +386,36 @@ __global__ void max_to_exp7_kernel(int n, const unsigned long long* cmax, int* e
 // (every 32-row stage of all n columns and digits one contiguous 14 n * 32
 // bytes; rows i >= m zero), so that a stage's TMA box of 7 x 128 column runs
 // of 64 bytes reads seven 8 KB spans of one region instead of 896 runs a
-// plane (2 mp bytes) apart.  A CTA slices a 32 (i) x 64 (j) block through a
-// shared-memory transpose and writes, per digit, 64 contiguous 64-byte runs.
+// plane (2 mp bytes) apart.  A thread slices 16 rows of one column: a warp
+// reads 32 adjacent columns of a row at a time (256 bytes) and writes, per
+// digit, one 32-byte sector per lane.
 __global__ void __launch_bounds__(256)
 slice7_cols_kernel(int m, int n, long mp, const double* __restrict__ A, long lda,
                    const int* __restrict__ ecol, unsigned short* __restrict__ D) {
-    __shared__ unsigned short t[TC_S][64][34];
-    const int j0 = blockIdx.x * 64;
-    for (long ib = blockIdx.y; ib < mp / 32; ib += gridDim.y) {
-        const long i0 = ib * 32;
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < 32 * 64; idx += blockDim.x) {
-            const int j = idx % 64, i = idx / 64;
-            const long gi = i0 + i;
-            const int gj = j0 + j;
-            const double v = (gi < m && gj < n) ? A[gi * lda + gj] : 0.0;
-            unsigned short d[TC_S];
-            digits7(v, gj < n ? ecol[gj] : 0, d);
+    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (j >= n) return;
+    const int e = ecol[j];
+    const long ngroups = mp / 16;
+    for (long g = (long)blockIdx.y * 8 + (threadIdx.x >> 5); g < ngroups; g += (long)gridDim.y * 8) {
+        const long i0 = g * 16;
+        unsigned w[TC_S][8];
 #pragma unroll
-            for (int s = 0; s < TC_S; ++s) t[s][j][i] = d[s];
+        for (int r = 0; r < 16; r += 2) {
+            const double v0 = i0 + r < m ? A[(i0 + r) * lda + j] : 0.0;
+            const double v1 = i0 + r + 1 < m ? A[(i0 + r + 1) * lda + j] : 0.0;
+            unsigned short d0[TC_S], d1[TC_S];
+            digits7(v0, e, d0);
+            digits7(v1, e, d1);
+#pragma unroll
+            for (int s = 0; s < TC_S; ++s) w[s][r / 2] = (unsigned)d0[s] | ((unsigned)d1[s] << 16);
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < TC_S * 64 * 16; idx += blockDim.x) {
-            const int w = idx % 16, j = (idx / 16) % 64, s = idx / (16 * 64);
-            const int gj = j0 + j;
-            if (gj >= n) continue;
-            const unsigned v = (unsigned)t[s][j][2 * w] | ((unsigned)t[s][j][2 * w + 1] << 16);
-            unsigned* dst = reinterpret_cast<unsigned*>(D + (((i0 / 32) * TC_S + s) * n + gj) * 32) + w;
-            *dst = v;
+        const long st = i0 / 32;
+        const int half = (int)(g & 1);
+#pragma unroll
+        for (int s = 0; s < TC_S; ++s) {
+            uint4* dst = reinterpret_cast<uint4*>(D + ((st * TC_S + s) * n + j) * 32 + half * 16);
+            dst[0] = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+            dst[1] = make_uint4(w[s][4], w[s][5], w[s][6], w[s][7]);
         }
     }
 }
@@ -838,7 +895,7 @@ size_t tcgram_scratch_doubles(int m, int n) {
 }
 
 tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
-                 DevBuf& scratch, int* status_dev) {
+                 DevBuf& scratch, int* status_dev, int* erow_out) {
     if (n <= 0) return TT_OK;
     if (m <= 0) {
         for (int i = 0; i < n; ++i) fill(s, G + (long)i * ldg, n, 0.0);
@@ -855,19 +912,34 @@ tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double
     unsigned long long* cmax = reinterpret_cast<unsigned long long*>(scratch.p + (size_t)ks * n * n);
     int* ecol = reinterpret_cast<int*>(cmax + n);
     TT_CUDA_TRY(cudaMemsetAsync(cmax, 0, n * sizeof(unsigned long long), s));
-    {
+    if (erow_out && n <= CRM_MAXN) {  // the row exponents of A too, from the same read
+        TT_TRY(ensure_max_dynamic_smem((const void*)col_row_max_kernel));
+        int dev = 0, sms = 152, per_sm = 1;
+        const size_t smem = (size_t)8 * n * sizeof(double);
+        TT_CUDA_TRY(cudaGetDevice(&dev));
+        TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        TT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, col_row_max_kernel, 256, smem));
+        note_launch();
+        col_row_max_kernel<<<(int)std::max<long>(1, std::min<long>(((long)m + 7) / 8, (long)sms * std::max(per_sm, 1))),
+                             256, smem, s>>>(m, n, A, lda, cmax, erow_out);
+    } else {
         dim3 grid((n + 31) / 32, (unsigned)std::min<long>(std::max<long>(1, m / 4096), 256));
         note_launch();
         col_max_kernel<<<grid, 256, 0, s>>>(m, n, A, lda, cmax);
-        note_launch();
-        max_to_exp7_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cmax, ecol);
+        if (erow_out) {
+            note_launch();
+            row_exp_kernel<<<(int)std::max<long>(1, std::min<long>(((long)m + 7) / 8, 152L * 64)), 256, 0, s>>>(
+                m, n, A, lda, erow_out);
+        }
     }
+    note_launch();
+    max_to_exp7_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cmax, ecol);
     const long mp = ((long)m + TC_K - 1) / TC_K * TC_K;
     // planes start on a 1024-byte boundary (TMA wants 16)
     const size_t plane_off = ((size_t)ks * n * n + 2 * (size_t)n + 8 + 127) / 128 * 128;
     unsigned short* planes = reinterpret_cast<unsigned short*>(scratch.p + plane_off);
     {
-        dim3 grid((n + 63) / 64, (unsigned)std::min<long>(mp / 32, 16384));
+        dim3 grid((n + 31) / 32, (unsigned)std::min<long>((mp / 16 + 7) / 8, 2048));
         note_launch();
         slice7_cols_kernel<<<grid, 256, 0, s>>>(m, n, mp, A, lda, ecol, planes);
     }
@@ -939,12 +1011,13 @@ tt_status bench_bf16_mma(cudaStream_t s, double* tflops) {
 size_t slgram_scratch_doubles(int m, int n) { return tcgram_scratch_doubles(m, n); }
 
 tt_status slgram(cudaStream_t s, int m, int n, const double* A, long lda, double* G, long ldg,
-                 DevBuf& scratch, int* status_dev) {
-    return tcgram(s, m, n, A, lda, G, ldg, scratch, status_dev);
+                 DevBuf& scratch, int* status_dev, int* erow_out) {
+    return tcgram(s, m, n, A, lda, G, ldg, scratch, status_dev, erow_out);
 }
 
 tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long lda, const double* B,
-                    long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev, DevBuf* planes) {
+                    long ldb, double* C, long ldc, DevBuf& scratch, int* status_dev, DevBuf* planes,
+                    const int* erowA) {
     if (M <= 0 || N <= 0) return TT_OK;
     if (K <= 0) {  // empty contraction: C = 0
         if (ldc == N) {
@@ -965,10 +1038,16 @@ tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long 
     if (!own) TT_TRY(planes->ensure(at_bytes / 8, s));
     int* eA = reinterpret_cast<int*>(scratch.p);
     int* eB = eA + M;
+    const bool have_eA = erowA != nullptr;
     unsigned char* Bt = reinterpret_cast<unsigned char*>(scratch.p + e_dbl);
     unsigned char* At = own ? Bt + bt_bytes : reinterpret_cast<unsigned char*>(planes->p);
-    note_launch();
-    row_exp_kernel<<<(int)std::max<long>(1, std::min<long>((M + 7) / 8, 152L * 64)), 256, 0, s>>>(M, K, A, lda, eA);
+    if (have_eA) {
+        eA = const_cast<int*>(erowA);
+    } else {
+        note_launch();
+        row_exp_kernel<<<(int)std::max<long>(1, std::min<long>((M + 7) / 8, 152L * 64)), 256, 0, s>>>(M, K, A, lda,
+                                                                                                     eA);
+    }
     note_launch();
     row_exp_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, K, B, ldb, eB);
     {
