@@ -860,11 +860,29 @@ int tc_tiles(int n) {
     return t;
 }
 
+// Row splits of the tensor-core Gram: every CTA holds one tile for one row
+// range, one CTA per SM, so the launch runs in waves of 152 and a split count
+// that leaves SMs idle in the last wave costs the whole wave (64 tiles x 2
+// splits keep 128 of 152 SMs busy; x 19 splits fill 8 waves).  The first
+// count from 152 / tiles up whose waves are >= 95% full, else the fullest;
+// at most one split per 512-row block and 64M partial doubles.
 int tc_ksplit(int m, int n) {
     const long mp = ((long)std::max(m, 1) + TC_K - 1) / TC_K * TC_K;
     const long blocks = (mp + TC_K * TC_BLK - 1) / (TC_K * TC_BLK);
-    long ks = std::max(1L, 152L / tc_tiles(n));
-    return (int)std::max(1L, std::min(ks, blocks));
+    const long T = tc_tiles(n);
+    const long kmax = std::max(1L, std::min(std::min(blocks, 64L), (64L << 20) / std::max(1L, (long)n * n)));
+    long best = std::min(std::max(1L, 152L / T), kmax);
+    double best_eff = 0.0;
+    for (long k = best; k <= kmax; ++k) {
+        const long waves = (T * k + 151) / 152;
+        const double eff = (double)(T * k) / (double)(waves * 152);
+        if (eff > best_eff + 1e-12) {
+            best = k;
+            best_eff = eff;
+        }
+        if (eff >= 0.95) break;
+    }
+    return (int)best;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
