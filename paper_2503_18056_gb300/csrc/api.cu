@@ -873,11 +873,9 @@ tt_status round_cores(tt_ctx* h, DevBuf* src, const int* R, DevBuf* dst, int* rr
             TT_TRY(h->bwd.ensure((size_t)Ra * nn * Rb, s));
             TT_TRY(h->GB[k].ensure((size_t)Ra * Ra, s));
             // precision form: both products on the tensor cores (GB[k+1] is
-            // symmetric, so bwd = G_{k+1} GB[k+1] = G_{k+1} GB[k+1]^T) once the
-            // R x R output has enough 128 x 64 tiles to occupy the GPU (below
-            // that the split-K FP64 product is faster)
-            const long tiles = (long)((Ra + 127) / 128) * ((Ra + 63) / 64);
-            if (h->precision == TT_MIXED && tiles >= 64) {
+            // symmetric, so bwd = G_{k+1} GB[k+1] = G_{k+1} GB[k+1]^T); a small
+            // R x R output over the long contraction n R' runs split-K
+            if (h->precision == TT_MIXED) {
                 TT_TRY(slgemm_nt(s, (long)Ra * nn, Rb, Rb, src[k + 1].p, Rb, h->GB[k + 1].p, Rb,
                                  h->bwd.p, Rb, h->slscratch, h->d_int + HI_STATUS));
                 TT_TRY(slgemm_nt(s, Ra, Ra, nn * Rb, h->bwd.p, (long)nn * Rb, src[k + 1].p,

@@ -691,7 +691,8 @@ __device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, uns
 __global__ void __launch_bounds__(TU_THREADS, 1)
 tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
              const int* __restrict__ erowA, const unsigned char* __restrict__ Bt,
-             const int* __restrict__ erowB, double* __restrict__ C, long ldc, int* status) {
+             const int* __restrict__ erowB, double* __restrict__ C, long ldc, int spc, double* __restrict__ Pk,
+             int* status) {
     extern __shared__ unsigned char tc_raw[];
     const unsigned raw_s = smem_u32(tc_raw);
     const unsigned pad = ((raw_s + 1023u) & ~1023u) - raw_s;
@@ -706,8 +707,12 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long mblocks = (M + TC_M - 1) / TC_M;
     const int nblk = (N + TC_N - 1) / TC_N;
-    const long items = mblocks * nblk;
-    const int nst = (K + TC_K - 1) / TC_K;  // stages per item
+    const int nst = (K + TC_K - 1) / TC_K;  // stages of the whole contraction
+    // split-K: spc stages (a multiple of TC_BLK) per item; item = (split, row
+    // block, column block), split outermost; splits > 1 write their partial
+    // product to Pk[split] (M x N) instead of C
+    const int ksp = (nst + spc - 1) / spc;
+    const long items = mblocks * nblk * ksp;
     if ((long)blockIdx.x >= items) return;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 7; ++i) mbar_init(smem_u32(&bars[i]), i == 5 ? (unsigned)TU_DRAIN_WARPS : 1u);
@@ -733,9 +738,12 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
             long g = 0;
             bool stop = false;
             for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
-                const long mb = item / nblk;
-                const int nb = (int)(item % nblk);
-                for (int it = 0; it < nst; ++it, ++g) {
+                const long tile = item % (mblocks * nblk);
+                const int sp = (int)(item / (mblocks * nblk));
+                const long mb = tile / nblk;
+                const int nb = (int)(tile % nblk);
+                const int st1 = min(nst, (sp + 1) * spc);
+                for (int it = sp * spc; it < st1; ++it, ++g) {
                     const int st = (int)(g % TC_STAGES);
                     const unsigned ph = (unsigned)(g / TC_STAGES) & 1u;
                     if (!mbar_wait_or_abort(smem_u32(&bars[2 + st]), ph ^ 1u, status, flags)) {
@@ -757,10 +765,12 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
             long g = 0, gb = 0;  // stages and blocks issued by this CTA so far
             bool stop = false;
             for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
-                for (int it = 0; it < nst; ++it, ++g) {
+                const int sp = (int)(item / (mblocks * nblk));
+                const int st0 = sp * spc, st1 = min(nst, st0 + spc);
+                for (int it = st0; it < st1; ++it, ++g) {
                     const int st = (int)(g % TC_STAGES);
                     const unsigned ph = (unsigned)(g / TC_STAGES) & 1u;
-                    const bool first = (it % TC_BLK) == 0;
+                    const bool first = ((it - st0) % TC_BLK) == 0;
                     if (first && gb > 0) {
                         if (!mbar_wait_or_abort(smem_u32(&bars[5]), (unsigned)(gb - 1) & 1u, status, flags)) {
                             stop = true;
@@ -778,7 +788,7 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
                     const unsigned bB = aB + TC_A_BYTES;
                     tc_stage_mmas(tmem, aB, bB, first);
                     tc_commit(smem_u32(&bars[2 + st]));
-                    if ((it % TC_BLK) == TC_BLK - 1 || it == nst - 1) {
+                    if (((it - st0) % TC_BLK) == TC_BLK - 1 || it == st1 - 1) {
                         tc_commit(smem_u32(&bars[4]));
                         ++gb;
                     }
@@ -790,12 +800,16 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
     } else {  // drain warps: TMEM lanes 32 q .. 32 q + 31, columns c0 .. c0 + TC_DN - 1
         const int q = warp & 3;
         const int c0 = ((warp - 2) >> 2) * TC_DN;
-        const int nb_per_item = (nst + TC_BLK - 1) / TC_BLK;
         long gb = 0;
         bool stop = false;
         for (long item = blockIdx.x; item < items && !stop; item += gridDim.x) {
-            const long i0 = (item / nblk) * TC_M;
-            const int n0 = (int)(item % nblk) * TC_N;
+            const long tile = item % (mblocks * nblk);
+            const int sp = (int)(item / (mblocks * nblk));
+            const int nb_per_item = (min(nst, (sp + 1) * spc) - sp * spc + TC_BLK - 1) / TC_BLK;
+            double* Cd = ksp > 1 ? Pk + (long)sp * M * N : C;
+            const long ldd = ksp > 1 ? (long)N : ldc;
+            const long i0 = (tile / nblk) * TC_M;
+            const int n0 = (int)(tile % nblk) * TC_N;
             float hi[TC_DN], lo[TC_DN];
 #pragma unroll
             for (int c = 0; c < TC_DN; ++c) hi[c] = lo[c] = 0.f;
@@ -832,7 +846,7 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
                 for (int c = 0; c < TC_DN; ++c) {
                     const int col = n0 + c0 + c;
                     if (col < N)
-                        C[i * ldc + col] = ldexp((double)hi[c] + (double)lo[c], ea + erowB[col] + 1 - 14);
+                        Cd[i * ldd + col] = ldexp((double)hi[c] + (double)lo[c], ea + erowB[col] + 1 - 14);
                 }
             }
         }
@@ -850,6 +864,17 @@ tcupd_kernel(long M, int N, int K, const unsigned char* __restrict__ At,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TC_TMEM_COLS)
                      : "memory");
+    }
+}
+
+// C = sum over the splits of Pk[split] (M x N each), in split order.
+__global__ void splitk_sum_kernel(long M, int N, int ksp, const double* __restrict__ Pk, double* __restrict__ C,
+                                  long ldc) {
+    const long tot = M * N;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+        double v = Pk[e];
+        for (int k = 1; k < ksp; ++k) v += Pk[(long)k * tot + e];
+        C[(e / N) * ldc + e % N] = v;
     }
 }
 
@@ -1052,8 +1077,20 @@ tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long 
     const size_t bt_bytes = (size_t)nbt * nst * TC_B_BYTES;
     const size_t at_bytes = (size_t)mblocks * nst * TC_A_BYTES;
     const bool own = planes == nullptr;  // A's images in `scratch` too
-    TT_TRY(scratch.ensure(e_dbl + bt_bytes / 8 + (own ? at_bytes / 8 : 0), s));
+    int dev = 0, sms = 152;
+    TT_CUDA_TRY(cudaGetDevice(&dev));
+    TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // split-K when the output has too few 128 x 64 tiles to occupy the SMs
+    // (e.g. an R x R right Gram over a long contraction): spc stages per split
+    const long tiles0 = mblocks * nbt;
+    int spc = nst;
+    if (tiles0 < sms / 2 && nst >= 2) spc = (int)((nst + (sms + tiles0 - 1) / tiles0 - 1) / ((sms + tiles0 - 1) / tiles0));
+    const int ksp = (nst + spc - 1) / spc;
+    const size_t pk_dbl = ksp > 1 ? (size_t)ksp * M * N : 0;
+    const size_t pk_off = e_dbl + bt_bytes / 8 + (own ? at_bytes / 8 : 0);
+    TT_TRY(scratch.ensure(pk_off + pk_dbl, s));
     if (!own) TT_TRY(planes->ensure(at_bytes / 8, s));
+    double* Pk = ksp > 1 ? scratch.p + pk_off : nullptr;
     int* eA = reinterpret_cast<int*>(scratch.p);
     int* eB = eA + M;
     const bool have_eA = erowA != nullptr;
@@ -1078,15 +1115,18 @@ tt_status slgemm_nt(cudaStream_t s, long M, int N, int K, const double* A, long 
         slice7_atiles_kernel<<<(int)std::min<long>((tota + 255) / 256, 152L * 32), 256, 0, s>>>(
             M, K, nst, A, lda, eA, At);
     }
-    int dev = 0, sms = 152;
-    TT_CUDA_TRY(cudaGetDevice(&dev));
-    TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const long items = mblocks * nbt;
+    const long items = tiles0 * ksp;
     const int grid = (int)std::min<long>(items, sms);
     TT_TRY(ensure_max_dynamic_smem((const void*)tcupd_kernel));
     note_launch();
-    tcupd_kernel<<<grid, TU_THREADS, TU_SMEM, s>>>(M, N, K, At, eA, Bt, eB, C, ldc, status_dev);
+    tcupd_kernel<<<grid, TU_THREADS, TU_SMEM, s>>>(M, N, K, At, eA, Bt, eB, C, ldc, spc, Pk, status_dev);
     TT_CUDA_TRY(cudaGetLastError());
+    if (ksp > 1) {
+        const long tot = M * N;
+        note_launch();
+        splitk_sum_kernel<<<(int)std::min<long>((tot + 255) / 256, 152L * 16), 256, 0, s>>>(M, N, ksp, Pk, C, ldc);
+        TT_CUDA_TRY(cudaGetLastError());
+    }
     return TT_OK;
 }
 

@@ -42,7 +42,9 @@ def test_gram_mixed_within_split_bound(ttsn, m, n, spread):
     assert np.linalg.norm(G - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (100, 7, 33), (70000, 128, 897), (5000, 37, 64)])
+# (100, 7, 33), (5000, 37, 64) and (161, 161, 5184) -- an R x R right Gram
+# over a long contraction -- have few output tiles and run split-K
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (100, 7, 33), (70000, 128, 897), (5000, 37, 64), (161, 161, 5184)])
 def test_gemm_nt_mixed_within_split_bound(ttsn, M, N, K):
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K)) * 10.0 ** rng.uniform(-8, 0, (M, 1))
