@@ -64,6 +64,19 @@ __device__ __forceinline__ int exp_bound(double vmax) {
     return ilogb(vmax) + 1;
 }
 
+// |v| as its bit pattern: for non-negative doubles the patterns order as the
+// values, so the maxima below are integer compares (fmax and fabs would run on
+// GB300's FP64 pipe, a small fraction of its integer rate: a scan of 2.1M x
+// 897 kept it 83% busy).  NaN maps to 0, which ignores it as fmax does; Inf
+// stays the largest pattern.
+__device__ __forceinline__ unsigned long long mag_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    return b > 0x7FF0000000000000ull ? 0ull : b;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
 __global__ void col_max_kernel(int m, int n, const double* __restrict__ A, long lda,
                                unsigned long long* cmax) {
     // block: 32 columns x (blockDim/32) row lanes; grid.y splits the rows
@@ -71,39 +84,39 @@ __global__ void col_max_kernel(int m, int n, const double* __restrict__ A, long 
     const int rlane = threadIdx.x >> 5, rstride = blockDim.x >> 5;
     const long rows_per = ((long)m + gridDim.y - 1) / gridDim.y;
     const long r0 = blockIdx.y * rows_per, r1 = min((long)m, r0 + rows_per);
-    double mx = 0.0;
+    unsigned long long mx = 0;
     if (j < n) {
         long i = r0 + rlane;
-        double m1 = 0.0, m2 = 0.0, m3 = 0.0;  // four loads in flight per thread
+        unsigned long long m1 = 0, m2 = 0, m3 = 0;  // four loads in flight per thread
         for (; i + 3 * rstride < r1; i += 4 * rstride) {
-            mx = fmax(mx, fabs(A[i * lda + j]));
-            m1 = fmax(m1, fabs(A[(i + rstride) * lda + j]));
-            m2 = fmax(m2, fabs(A[(i + 2 * rstride) * lda + j]));
-            m3 = fmax(m3, fabs(A[(i + 3 * rstride) * lda + j]));
+            mx = umax64(mx, mag_bits(A[i * lda + j]));
+            m1 = umax64(m1, mag_bits(A[(i + rstride) * lda + j]));
+            m2 = umax64(m2, mag_bits(A[(i + 2 * rstride) * lda + j]));
+            m3 = umax64(m3, mag_bits(A[(i + 3 * rstride) * lda + j]));
         }
-        for (; i < r1; i += rstride) mx = fmax(mx, fabs(A[i * lda + j]));
-        mx = fmax(fmax(mx, m1), fmax(m2, m3));
+        for (; i < r1; i += rstride) mx = umax64(mx, mag_bits(A[i * lda + j]));
+        mx = umax64(umax64(mx, m1), umax64(m2, m3));
     }
-    if (j < n && mx > 0.0) atomicMax(cmax + j, (unsigned long long)__double_as_longlong(mx));
+    if (j < n && mx > 0) atomicMax(cmax + j, mx);
 }
 
 __global__ void row_exp_kernel(long m, int n, const double* __restrict__ A, long lda, int* e) {
     const int lane = threadIdx.x & 31;
     const long warps = (long)gridDim.x * (blockDim.x >> 5);
     for (long i = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += warps) {
-        double mx = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;  // four loads in flight per lane
+        unsigned long long mx = 0, m1 = 0, m2 = 0, m3 = 0;  // four loads in flight per lane
         int j = lane;
         for (; j + 96 < n; j += 128) {
-            mx = fmax(mx, fabs(A[i * lda + j]));
-            m1 = fmax(m1, fabs(A[i * lda + j + 32]));
-            m2 = fmax(m2, fabs(A[i * lda + j + 64]));
-            m3 = fmax(m3, fabs(A[i * lda + j + 96]));
+            mx = umax64(mx, mag_bits(A[i * lda + j]));
+            m1 = umax64(m1, mag_bits(A[i * lda + j + 32]));
+            m2 = umax64(m2, mag_bits(A[i * lda + j + 64]));
+            m3 = umax64(m3, mag_bits(A[i * lda + j + 96]));
         }
-        for (; j < n; j += 32) mx = fmax(mx, fabs(A[i * lda + j]));
-        mx = fmax(fmax(mx, m1), fmax(m2, m3));
+        for (; j < n; j += 32) mx = umax64(mx, mag_bits(A[i * lda + j]));
+        mx = umax64(umax64(mx, m1), umax64(m2, m3));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) e[i] = exp_bound(mx);
+        for (int o = 16; o > 0; o >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) e[i] = exp_bound(__longlong_as_double((long long)mx));
     }
 }
 
@@ -119,11 +132,11 @@ constexpr int CRM_MAXN = 1024;
 __global__ void __launch_bounds__(256)
 col_row_max_kernel(long m, int n, const double* __restrict__ A, long lda, unsigned long long* cmax,
                    int* erow) {
-    extern __shared__ double crm_part[];  // [8][n]
+    extern __shared__ unsigned long long crm_part[];  // [8][n], magnitude bit patterns
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nk = (n + 31) >> 5;
-    double* mine = crm_part + (long)warp * n;
-    for (int j = lane; j < n; j += 32) mine[j] = 0.0;
+    unsigned long long* mine = crm_part + (long)warp * n;
+    for (int j = lane; j < n; j += 32) mine[j] = 0;
     __syncwarp();
     const long nw = (long)gridDim.x * 8;
     for (long i = (long)blockIdx.x * 8 + warp; i < m; i += nw) {
@@ -135,26 +148,26 @@ col_row_max_kernel(long m, int n, const double* __restrict__ A, long lda, unsign
 #pragma unroll
         for (int k = 0; k < CRM_MAXN / 32; ++k)
             if (k < nk) v[k] = row[min(k * 32 + lane, n - 1)];
-        double rm = 0.0;
+        unsigned long long rm = 0;
 #pragma unroll
         for (int k = 0; k < CRM_MAXN / 32; ++k) {
             if (k < nk) {
-                const double a = fabs(v[k]);
+                const unsigned long long a = mag_bits(v[k]);
                 const int j = k * 32 + lane;
-                if (j < n) mine[j] = fmax(mine[j], a);
-                rm = fmax(rm, a);
+                if (j < n) mine[j] = umax64(mine[j], a);
+                rm = umax64(rm, a);
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
-        if (lane == 0) erow[i] = exp_bound(rm);
+        for (int o = 16; o > 0; o >>= 1) rm = umax64(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+        if (lane == 0) erow[i] = exp_bound(__longlong_as_double((long long)rm));
     }
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double mx = crm_part[j];
+        unsigned long long mx = crm_part[j];
 #pragma unroll
-        for (int w = 1; w < 8; ++w) mx = fmax(mx, crm_part[(long)w * n + j]);
-        if (mx > 0.0) atomicMax(cmax + j, (unsigned long long)__double_as_longlong(mx));
+        for (int w = 1; w < 8; ++w) mx = umax64(mx, crm_part[(long)w * n + j]);
+        if (mx > 0) atomicMax(cmax + j, mx);
     }
 }
 
@@ -958,7 +971,7 @@ tt_status tcgram(cudaStream_t s, int m, int n, const double* A, long lda, double
     if (erow_out && n <= CRM_MAXN) {  // the row exponents of A too, from the same read
         TT_TRY(ensure_max_dynamic_smem((const void*)col_row_max_kernel));
         int dev = 0, sms = 152, per_sm = 1;
-        const size_t smem = (size_t)8 * n * sizeof(double);
+        const size_t smem = (size_t)8 * n * sizeof(unsigned long long);
         TT_CUDA_TRY(cudaGetDevice(&dev));
         TT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         TT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, col_row_max_kernel, 256, smem));
