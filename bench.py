@@ -332,7 +332,17 @@ def run_ours(args, rank, world, local_rank):
         # steps (pinned), copied in before and out after every step
         e2e = None
         if not args.no_e2e:
-            host_cores = [c.cpu().pin_memory() for c in init_cores]
+            # pinned host buffers at the rank cap, allocated before the timed
+            # region; each step's cores are copied out into views of them
+            _, dims = g.dims()
+            cap = int(p.get("max_rank") or 0) or min(dims[0], dims[1] * dims[2])
+            caps = [dims[0] * cap, cap * dims[1] * cap, cap * dims[2]]
+            pool = [torch.empty(max(c_, 1), dtype=torch.float64).pin_memory() for c_ in caps]
+            host_cores = []
+            for k_, c in enumerate(init_cores):
+                hv = pool[k_][:c.numel()].view(c.shape)
+                hv.copy_(c)
+                host_cores.append(hv)
             host_T = T0.cpu().pin_memory()
             h2d = d2h = 0
             torch.cuda.synchronize()
@@ -343,9 +353,12 @@ def run_ours(args, rank, world, local_rank):
                 h2d += sum(c.numel() for c in host_cores) * 8 + host_T.numel() * 8
                 g.step()
                 dev_cores = g.cores()
-                host_cores = [c.to("cpu", non_blocking=False) for c in dev_cores]
+                host_cores = [pool[k_][:c.numel()].view(c.shape) for k_, c in enumerate(dev_cores)]
+                for hc, dc in zip(host_cores, dev_cores):
+                    hc.copy_(dc, non_blocking=True)
                 _, Td, _ = g.energy()
-                host_T = Td.cpu()
+                host_T.copy_(Td, non_blocking=True)
+                torch.cuda.synchronize()
                 d2h += sum(c.numel() for c in host_cores) * 8 + host_T.numel() * 8
             torch.cuda.synchronize()
             e2e_s = time.perf_counter() - t0
