@@ -12,9 +12,9 @@
 // exact in FP32.  Products of the same level w = s + t share the weight
 // 128^-(w+2); level w has at most 7 pairs, so summed over a block of 512
 // contraction indices they stay below 512 * 7 * 2^12 < 2^24 and the tensor
-// cores' FP32 block sums are exact integers.  Each block sum is scaled by 128^-w (exact) and added into a
-// double-float accumulator (hi + lo in FP32, TwoSum + renormalisation: about
-// 48 bits).  Levels w >= 7 are dropped: 28 BF16 products per term, about
+// cores' FP32 block sums are exact integers.  Each block sum is scaled by
+// 128^-w (exact) and added into a double-float accumulator (hi + lo in FP32,
+// TwoSum + renormalisation: about 48 bits).  Levels w >= 7 are dropped: 28 BF16 products per term, about
 // 2^-48 of max|a| max|b| per term against 2^-53 for FP64.  No FP64 arithmetic
 // runs in the inner loops (GB300's FP64 pipe is ~1/70 of its FP32 pipe).
 //
@@ -144,8 +144,7 @@ col_row_max_kernel(long m, int n, const double* __restrict__ A, long lda, unsign
     for (long i = (long)blockIdx.x * 8 + warp; i < m; i += nw) {
         const double* row = A + i * lda;
         // unconditional loads (lanes past the last column re-read it, which
-        // leaves the row maximum unchanged): a select on a loaded value would
-        // wait for the load and serialise them
+        // leaves the row maximum unchanged), all issued before the first use
         double v[CRM_MAXN / 32];
 #pragma unroll
         for (int k = 0; k < CRM_MAXN / 32; ++k)
