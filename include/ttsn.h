@@ -624,6 +624,10 @@ tt_status tt_gram_mixed(int m, int n, const double* A_dev, int lda, double* G_de
  * tt_gemm_nt_mixed: C = A B^T (A: M x K, B: N x K, C: M x N, row-major) with the
  * same exact split products on the tensor cores, each row of A and of B scaled
  * by its own power of two (error about 2^-48 max_k|A_ik| max_k|B_jk| per term).
+ * An output with too few 128 x 64 tiles to occupy the GPU is computed split-K
+ * over the contraction, the partial products added in a fixed order (results
+ * do not depend on scheduling).  Device scratch (digit images, 14 bytes per
+ * element of A and B, and the partials) is allocated per call.
  */
 tt_status tt_gemm_nt_mixed(int M, int N, int K, const double* A_dev, int lda, const double* B_dev,
                            int ldb, double* C_dev, int ldc, void* stream);
