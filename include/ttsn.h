@@ -244,7 +244,9 @@ tt_status tt_get_dims(tt_handle h, int* d_host, int* n_host);
 
 /*
  * tt_get_core: copy core k (0-based) into out_dev (r_{k-1} n_k r_k doubles);
- * TT_ERR_TOO_LARGE if out_len is smaller.
+ * TT_ERR_TOO_LARGE if out_len is smaller.  out_dev may be device memory or
+ * host memory (pinned host memory copies at the host link's speed); the call
+ * returns once the copy is complete.
  */
 tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len);
 
@@ -258,8 +260,10 @@ tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len);
 tt_status tt_get_cores(tt_handle h, double** cores_dev, int* shapes_host);
 
 /*
- * tt_set_cores: replace the TT by the d cores cores_dev[k] (device, shapes
- * (ranks[k], n_k, ranks[k+1])), copied in; ranks_host has d+1 entries.
+ * tt_set_cores: replace the TT by the d cores cores_dev[k] (shapes
+ * (ranks[k], n_k, ranks[k+1])), copied in; ranks_host has d+1 entries.  The
+ * cores may be in device memory or in host memory (pinned or pageable); the
+ * call returns once they are copied, so the caller may reuse the buffers.
  */
 tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* ranks_host);
 
@@ -345,7 +349,8 @@ tt_status tt_set_graph(tt_handle h, int enable);
 /* tt_set_precision: TT_FP64 or TT_MIXED for the following roundings. */
 tt_status tt_set_precision(tt_handle h, int precision);
 
-/* tt_set_T: replace the material temperature (N_c doubles, device). */
+/* tt_set_T: replace the material temperature (N_c doubles, device or host
+ * memory; copied before the call returns). */
 tt_status tt_set_T(tt_handle h, const double* T_dev);
 
 /*

@@ -51,6 +51,17 @@ def _dev(x, n=None):
     return t
 
 
+def _dev_or_host(x, n=None):
+    """A contiguous float64 CPU tensor as it is (the library copies host
+    memory itself, without a device staging tensor), anything else on the
+    device."""
+    if isinstance(x, torch.Tensor) and x.device.type == "cpu" and x.dtype == torch.float64 and x.is_contiguous():
+        if n is not None and x.numel() != n:
+            raise ValueError("expected %d values, got %d" % (n, x.numel()))
+        return x
+    return _dev(x, n)
+
+
 def _int_array(vals):
     if vals is None:
         return None
@@ -91,23 +102,37 @@ class _Handle:
         check(lib.tt_get_dims(self._h, ctypes.byref(d), n))
         return d.value, list(n[: d.value])
 
-    def cores(self):
+    def cores(self, into=None):
+        """Copies of the cores, (r_{k-1}, n_k, r_k) each: new device tensors,
+        or, with ``into`` (one flat float64 tensor per core, device or host --
+        pinned host memory copies at the host link's speed -- with room for
+        the core), views of those buffers written in place."""
         d, n = self.dims()
         r = self.ranks()
         out = []
         for k in range(d):
-            t = torch.empty((r[k], n[k], r[k + 1]), dtype=torch.float64, device="cuda")
+            shape = (r[k], n[k], r[k + 1])
+            if into is None:
+                t = torch.empty(shape, dtype=torch.float64, device="cuda")
+            else:
+                buf = into[k]
+                if buf.dtype != torch.float64 or not buf.is_contiguous() or buf.numel() < r[k] * n[k] * r[k + 1]:
+                    raise ValueError("into[%d] must be a contiguous float64 tensor of at least %d values"
+                                     % (k, r[k] * n[k] * r[k + 1]))
+                t = buf.view(-1)[: r[k] * n[k] * r[k + 1]].view(shape)
             check(lib.tt_get_core(self._h, k, ctypes.c_void_p(t.data_ptr()), t.numel()))
             out.append(t)
         return out
 
     def set_cores(self, cores):
-        """Replace the TT by ``cores`` (copied in).  The count and every shape
-        are checked against the handle's mode sizes before the library copies
-        anything: core k must be (r_{k-1}, n_k, r_k) with r_0 = r_d = 1 and each
-        r_{k-1} equal to the previous core's last dimension."""
+        """Replace the TT by ``cores`` (copied in; device tensors, or float64
+        CPU tensors -- pinned ones copy at the host link's speed -- which the
+        library reads directly).  The count and every shape are checked against
+        the handle's mode sizes before the library copies anything: core k must
+        be (r_{k-1}, n_k, r_k) with r_0 = r_d = 1 and each r_{k-1} equal to the
+        previous core's last dimension."""
         d, n = self.dims()
-        ts = [_dev(c) for c in cores]
+        ts = [_dev_or_host(c) for c in cores]
         if len(ts) != d:
             raise ValueError("expected %d cores, got %d" % (d, len(ts)))
         prev = 1
@@ -418,7 +443,7 @@ class TTSN(_Handle):
         return E, T, ((tot[0], tot[1]) if totals else None)
 
     def set_T(self, T):
-        t = _dev(T, self.nc)
+        t = _dev_or_host(T, self.nc)
         check(lib.tt_set_T(self._h, ctypes.c_void_p(t.data_ptr())))
 
     def compression(self):

@@ -2682,7 +2682,8 @@ tt_status tt_get_core(tt_handle h, int k, double* out_dev, size_t out_len) {
     if (k < 0 || k >= h->d) return fail(TT_ERR_ARG, "tt_get_core: k out of range");
     const size_t len = h->core_len(k, h->r);
     if (out_len < len) return fail(TT_ERR_TOO_LARGE, "tt_get_core: output buffer too small");
-    TT_CUDA_TRY(cudaMemcpyAsync(out_dev, h->core[k].p, len * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    // device or host destination (unified addressing infers the direction)
+    TT_CUDA_TRY(cudaMemcpyAsync(out_dev, h->core[k].p, len * sizeof(double), cudaMemcpyDefault, h->stream));
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return TT_OK;
 }
@@ -2714,8 +2715,9 @@ tt_status tt_set_cores(tt_handle h, const double* const* cores_dev, const int* r
     for (int k = 0; k < h->d; ++k) {
         const size_t len = h->core_len(k, ranks_host);
         TT_TRY(h->core[k].ensure(len, h->stream));
-        TT_CUDA_TRY(cudaMemcpyAsync(h->core[k].p, cores_dev[k], len * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, h->stream));
+        // device or host source (unified addressing infers the direction)
+        TT_CUDA_TRY(cudaMemcpyAsync(h->core[k].p, cores_dev[k], len * sizeof(double), cudaMemcpyDefault,
+                                    h->stream));
     }
     for (int k = 0; k <= h->d; ++k) h->r[k] = ranks_host[k];
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -2940,7 +2942,7 @@ tt_status tt_set_T(tt_handle h, const double* T_dev) {
     AllocScope alloc_scope_(h->alloc_ptr());
     clear_tape(h);  // a change of state outside a step ends the tape
     if (!T_dev) return fail(TT_ERR_ARG, "tt_set_T: null input");
-    TT_CUDA_TRY(cudaMemcpyAsync(h->f_T.p, T_dev, h->grid.nc * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    TT_CUDA_TRY(cudaMemcpyAsync(h->f_T.p, T_dev, h->grid.nc * sizeof(double), cudaMemcpyDefault, h->stream));
     TT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return TT_OK;
 }

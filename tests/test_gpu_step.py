@@ -240,3 +240,31 @@ def test_blob_3d_full_size_sampled(ttsn):
     assert np.abs(T[idx] - ref.T[idx]).max() <= 1e-12
     dV = 1.0 / E.size
     assert abs(tot[0] - Er.sum() * dV) <= 1e-10 * Er.sum() * dV
+
+
+def test_state_through_host_memory(ttsn):
+    # set_cores / set_T read float64 CPU tensors (pinned or pageable) straight
+    # from host memory and cores(into=...) writes into caller buffers: the
+    # steps that follow are bit for bit those from the device-held state
+    import torch
+
+    p = workloads.problem("small_2d", n=(16, 12), n_theta=4, n_phi=8, eps=1e-6)
+    g = ttsn.TTSN.from_problem(p)
+    g.step(3)
+    dev = [c.clone() for c in g.cores()]
+    T = g.energy()[1].clone()
+    pinned = [torch.empty(c.numel() + 5, dtype=torch.float64).pin_memory() for c in dev]
+    host = g.cores(into=pinned)
+    for h, d in zip(host, dev):
+        assert h.device.type == "cpu" and h.shape == d.shape and torch.equal(h, d.cpu())
+    with pytest.raises(ValueError):
+        g.cores(into=[torch.empty(1, dtype=torch.float64)] * len(dev))
+    runs = []
+    for cores, temp in ((dev, T), (host, T.cpu().pin_memory()), ([d.cpu() for d in dev], T.cpu())):
+        h = ttsn.TTSN.from_problem(p)
+        h.set_cores(cores)
+        h.set_T(temp)
+        h.step(2)
+        runs.append((h.full().cpu(), h.energy()[1].cpu()))
+    for F, Tn in runs[1:]:
+        assert torch.equal(F, runs[0][0]) and torch.equal(Tn, runs[0][1])
