@@ -109,6 +109,8 @@ class _Handle:
         the core), views of those buffers written in place."""
         d, n = self.dims()
         r = self.ranks()
+        if into is not None and len(into) < d:
+            raise ValueError("into needs one buffer per core (%d), got %d" % (d, len(into)))
         out = []
         for k in range(d):
             shape = (r[k], n[k], r[k + 1])
