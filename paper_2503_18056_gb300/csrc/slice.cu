@@ -221,13 +221,14 @@ __global__ void __launch_bounds__(256) bf16_mma_peak_kernel(float* out, unsigned
 // of rows.  Seven FP32 accumulators (one per level, 128 lanes x 64 columns
 // each, 448 of the 512 TMEM columns) receive, per 32-row stage, the 28
 // digit-pair products x 2 K-steps as 20 tcgen05.mma (kind::f16, BF16 x BF16
-// -> FP32, M = 128, N = 64 .. 256, K = 16; tc_stage_mmas) issued by one thread
-// with operands described in shared memory (K-major, 64-byte swizzle).  A TMA producer thread streams
-// the stages (all 7 digit planes of the tile's 128 + 64 columns in two
-// 3-D boxes per stage, double-buffered, mbarrier-tracked).  After every
+// -> FP32, M = 128, N = 64 .. 256, K = 16; tc_stage_mmas) issued by one
+// thread with operands described in shared memory (K-major, 64-byte
+// swizzle).  A TMA producer thread streams the stages (all 7 digit planes of
+// the tile's 128 + 64 columns in two 4-D boxes per stage from the
+// stage-major planes, double-buffered, mbarrier-tracked).  After every
 // 512-row block eight drain warps read the accumulators (tcgen05.ld, one TMEM
-// lane and half the columns per thread), scale level w by 128^-w and add into double-float
-// accumulators.  Every wait is bounded and latches DEV_TIMEOUT.
+// lane and half the columns per thread), scale level w by 128^-w and add into
+// double-float accumulators.  Every wait is bounded and latches DEV_TIMEOUT.
 constexpr int TC_S = 7;
 constexpr int TC_M = 128, TC_N = 64, TC_K = 32;
 constexpr int TC_BLK = 16;  // stages per exact block (512 rows)
